@@ -1,0 +1,202 @@
+/*
+ * libdpc: exact Density-Peaks Clustering on one NVIDIA GB300 (sm_103a).
+ *
+ * The problem is the one defined in Amagata & Hara, "Fast Density-Peaks
+ * Clustering: Multicore-based Parallelization Approach" (arXiv 2207.04649),
+ * Section 2.1. For a set P of n points, a cutoff d_cut and thresholds
+ * rho_min, delta_min:
+ *   - local density      rho_i   = #{ p_j in P : dist(p_i, p_j) < d_cut }
+ *                        (Definition 1; p_i counts itself; strict <),
+ *   - dependent point    q_i     = nearest point of higher density
+ *                        (Definition 2),
+ *   - dependent distance delta_i = dist(p_i, q_i); infinity for the
+ *                        densest point (Definition 3),
+ *   - noise              rho_i < rho_min (Definition 4),
+ *   - cluster center     not noise and delta_i >= delta_min, with
+ *                        delta_min > d_cut (Definition 5),
+ *   - cluster label      the center reached through dependent points
+ *                        (Definition 6).
+ *
+ * Conventions fixed by this library where the paper leaves a choice:
+ *   - dist is Euclidean over int32 coordinates and is compared squared, in
+ *     exact integer arithmetic. delta is reported squared (delta2, int64).
+ *   - "Higher density" is the total order (rho desc, original index asc):
+ *     the order Ex-DPC (Section 3) processes points in when its density sort
+ *     is stable. It replaces the paper's random tie-breaker.
+ *   - Ties in distance go to the smaller original index (Definition 2 says
+ *     ties are broken arbitrarily).
+ *   - The densest point has dep = -1 and delta2 = INT64_MAX.
+ *   - label_i is the original index of point i's center; -1 for noise.
+ *   - Every output is in the caller's original point order. The results are
+ *     deterministic and bit-exact: they do not depend on the GPU's schedule.
+ *
+ * Errors are returned as dpc_status, never thrown; dpc_last_error() gives a
+ * message for the calling thread's last failure. Calls that take a context
+ * run on that context's CUDA stream; calls writing to host memory return
+ * once the data is there.
+ */
+#ifndef DPC_H
+#define DPC_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    DPC_OK = 0,
+    DPC_PENDING = 1,            /* dpc_poll: the job is not finished */
+    DPC_ERR_INVALID_ARG = -1,   /* a pointer, size or parameter is out of range */
+    DPC_ERR_OOM = -2,           /* device memory could not be allocated */
+    DPC_ERR_CUDA = -3,          /* a CUDA call failed (message in dpc_last_error) */
+    DPC_ERR_TIMEOUT = -4,       /* a bounded wait ran out */
+    DPC_ERR_STATE = -5,         /* handle used in the wrong state (released, unknown ticket) */
+    DPC_ERR_CAPACITY = -6       /* the job can never fit the context's memory cap */
+} dpc_status;
+
+typedef struct dpc_ctx dpc_ctx;   /* device, stream, memory pool, job queue */
+typedef struct dpc_ds dpc_ds;     /* one clustered dataset kept on the device */
+
+typedef struct {
+    int device;              /* CUDA device ordinal */
+    void* cuda_stream;       /* cudaStream_t to run on; NULL: the context creates its own */
+    uint64_t hbm_cap_bytes;  /* device memory the served mode may hold at once; 0: 150 GB */
+    const char* tune_cache;  /* autotuner cache file (JSON) or NULL */
+    int debug_checks;        /* nonzero: synchronize and check after every stage */
+    int mode;                /* 0: batched (dpc_flush runs the submitted jobs);
+                                1: served (a worker thread admits jobs continuously) */
+    int max_inflight;        /* served mode: batches on the device at once; 0: 4 */
+} dpc_options;
+
+/* Create a context on options->device (options may be NULL: device 0, own
+ * stream, batched mode). *out receives the handle. */
+dpc_status dpc_create(const dpc_options* options, dpc_ctx** out);
+
+/* Destroy a context: waits for its jobs, frees its device memory. Datasets
+ * created from it must be released first. */
+dpc_status dpc_destroy(dpc_ctx* ctx);
+
+/* Message describing the calling thread's last error ("" if none). */
+const char* dpc_last_error(void);
+
+/* Local density of every point (Definition 1).
+ *   points:  n x d int32, row-major, 0 <= x < 2^30. Host memory when
+ *            is_device == 0, device memory of the context's device otherwise.
+ *            Read during the call; the caller keeps ownership.
+ *   n:       0 <= n < 2^31 (n == 0 gives an empty dataset).
+ *   d:       1 <= d <= 8.
+ *   d_cut:   1 <= d_cut < 2^31.
+ *   out:     receives the dataset handle; it owns the device-resident sorted
+ *            points, rho, rank and (after dpc_dependent) dep/delta2 until
+ *            dpc_release.
+ *   rho_out: NULL or n int32 (host or device per is_device).
+ * Errors: DPC_ERR_INVALID_ARG for any argument out of range (coordinates are
+ * checked on the device), DPC_ERR_OOM, DPC_ERR_CUDA. */
+dpc_status dpc_density(dpc_ctx* ctx, const int32_t* points, int64_t n, int32_t d, int64_t d_cut,
+                       int is_device, dpc_ds** out, int32_t* rho_out);
+
+/* Dependent point and squared dependent distance (Definitions 2-3).
+ *   dep_out:    NULL or n int32: original index of the dependent point, -1
+ *               for the densest point.
+ *   delta2_out: NULL or n int64: squared distance to it, INT64_MAX for the
+ *               densest point.
+ * Both host or device memory, as for dpc_density's is_device. Computed once
+ * per dataset; later calls copy the kept result. */
+dpc_status dpc_dependent(dpc_ds* ds, int32_t* dep_out, int64_t* delta2_out);
+
+/* Noise, centers and labels (Definitions 4-6) for one (rho_min, delta_min)
+ * query. Re-queryable: only this step runs again (the decision-graph
+ * workflow of Section 2.1). Runs dpc_dependent first if it has not run.
+ *   delta_min: d_cut < delta_min <= 3037000499 (so delta_min^2 fits int64).
+ *   label_out: NULL or n int32 (host or device per is_device): original index
+ *              of the point's center, -1 for noise.
+ *   n_centers: NULL or one int64 in host memory. */
+dpc_status dpc_label(dpc_ds* ds, int64_t rho_min, int64_t delta_min, int32_t* label_out, int64_t* n_centers);
+
+/* Free a dataset's device state. The handle is invalid afterwards. */
+dpc_status dpc_release(dpc_ds* ds);
+
+/* Counters of the last run on a dataset (sizes of the work, for reporting). */
+typedef struct {
+    int64_t n;
+    int64_t cells;            /* non-empty grid cells */
+    int64_t dense_cells;      /* cells handled one warp per work item */
+    int64_t work_items;       /* dense work items */
+    int64_t cand_pairs;       /* (query, candidate) pairs the density filter evaluates */
+    int64_t open_after_ring;  /* points left open by the ring search */
+    int64_t brute_points;     /* of those, sent to the brute-force pass */
+    int32_t grid_dims;        /* gridded dimensions */
+    int32_t pair_bits;        /* 32 or 64: width of the pair arithmetic */
+    float ms_grid, ms_rho, ms_rank, ms_ring, ms_rest, ms_label;  /* stage times when profiling is on */
+} dpc_info;
+
+dpc_status dpc_ds_info(const dpc_ds* ds, dpc_info* out);
+
+/* Enable per-stage CUDA-event timing on a context (0 off, 1 on). */
+dpc_status dpc_set_profiling(dpc_ctx* ctx, int on);
+
+/* Number of CUDA kernels this library has launched in this process so far
+ * (all contexts and threads); a difference of two readings counts the
+ * launches of the calls in between. */
+int64_t dpc_kernel_launches(void);
+
+/* Measurement helper (no counterpart in the paper): the throughput of the
+ * density stage's 32-bit pair test for d-dimensional points with operands in
+ * registers on every SM of `device`, i.e. the integer-ALU ceiling that the
+ * density kernel is compared against. Writes pairs per second (and the
+ * kernel's time in ms when ms is not NULL). Allocates and frees a few bytes
+ * of device memory; synchronizes the device's default stream. */
+dpc_status dpc_probe_pair_rate(int device, int d, double* pairs_per_s, double* ms);
+
+/* ---------------------------------------------------------------------
+ * Jobs: many independent datasets, batched or served.
+ *
+ * A job is one dataset plus n_queries (rho_min, delta_min) queries. All its
+ * pointers are host memory owned by the caller and must stay valid until
+ * dpc_poll reports the job finished. In batched mode (dpc_options.mode 0)
+ * jobs run when dpc_flush is called, all of them in one batch: every stage
+ * is one launch over all datasets. In served mode (mode 1) a worker thread
+ * admits waiting jobs as device memory (hbm_cap_bytes) and batch slots
+ * (max_inflight) free up and runs them while earlier batches are still on
+ * the device. Results are the same bits as running each dataset alone.
+ * ------------------------------------------------------------------- */
+typedef struct {
+    const int32_t* points;     /* n x d int32 row-major */
+    int64_t n;
+    int32_t d;
+    int64_t d_cut;
+    int32_t n_queries;         /* >= 1 */
+    const int64_t* rho_min;    /* [n_queries] */
+    const int64_t* delta_min;  /* [n_queries], each > d_cut */
+    int32_t* rho_out;          /* NULL or [n] */
+    int32_t* dep_out;          /* NULL or [n] */
+    int64_t* delta2_out;       /* NULL or [n] */
+    int32_t* label_out;        /* NULL or [n_queries * n], query-major */
+    int64_t* n_centers_out;    /* NULL or [n_queries] */
+} dpc_job;
+
+typedef struct {
+    dpc_status status;         /* DPC_OK, DPC_PENDING or the job's error */
+    double queue_ms;           /* submit -> admitted */
+    double run_ms;             /* admitted -> results in host memory */
+} dpc_result;
+
+/* Queue a job; thread-safe. *ticket identifies it for dpc_poll. */
+dpc_status dpc_submit(dpc_ctx* ctx, const dpc_job* job, uint64_t* ticket);
+
+/* Non-blocking: DPC_PENDING until the job is done, then its final status
+ * (also in out->status). A finished ticket is forgotten after it is polled. */
+dpc_status dpc_poll(dpc_ctx* ctx, uint64_t ticket, dpc_result* out);
+
+/* Batched mode: run every job submitted so far as one batch and wait for it. */
+dpc_status dpc_flush(dpc_ctx* ctx);
+
+/* Block until the job is done or timeout_ms passes (DPC_ERR_TIMEOUT). */
+dpc_status dpc_wait(dpc_ctx* ctx, uint64_t ticket, int64_t timeout_ms, dpc_result* out);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DPC_H */

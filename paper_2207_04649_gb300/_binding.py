@@ -1,0 +1,365 @@
+"""ctypes binding of libdpc (argument marshalling only).
+
+Host data is passed as numpy arrays, device data as CUDA torch tensors (their
+data pointers). PyTorch is used for device memory and streams only.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+from . import build as _build
+
+DPC_OK = 0
+DPC_PENDING = 1
+DPC_ERR_INVALID_ARG = -1
+DPC_ERR_OOM = -2
+DPC_ERR_CUDA = -3
+DPC_ERR_TIMEOUT = -4
+DPC_ERR_STATE = -5
+DPC_ERR_CAPACITY = -6
+INT64_MAX = np.iinfo(np.int64).max
+
+_NAMES = {0: "DPC_OK", 1: "DPC_PENDING", -1: "DPC_ERR_INVALID_ARG", -2: "DPC_ERR_OOM", -3: "DPC_ERR_CUDA",
+          -4: "DPC_ERR_TIMEOUT", -5: "DPC_ERR_STATE", -6: "DPC_ERR_CAPACITY"}
+
+
+class DpcError(RuntimeError):
+    def __init__(self, status: int, where: str, msg: str):
+        super().__init__(f"{where}: {_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+class DpcOptions(ctypes.Structure):
+    _fields_ = [("device", ctypes.c_int), ("cuda_stream", ctypes.c_void_p), ("hbm_cap_bytes", ctypes.c_uint64),
+                ("tune_cache", ctypes.c_char_p), ("debug_checks", ctypes.c_int), ("mode", ctypes.c_int),
+                ("max_inflight", ctypes.c_int)]
+
+
+class DpcInfo(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("cells", ctypes.c_int64), ("dense_cells", ctypes.c_int64),
+                ("work_items", ctypes.c_int64), ("cand_pairs", ctypes.c_int64),
+                ("open_after_ring", ctypes.c_int64), ("brute_points", ctypes.c_int64),
+                ("grid_dims", ctypes.c_int32), ("pair_bits", ctypes.c_int32),
+                ("ms_grid", ctypes.c_float), ("ms_rho", ctypes.c_float), ("ms_rank", ctypes.c_float),
+                ("ms_ring", ctypes.c_float), ("ms_rest", ctypes.c_float), ("ms_label", ctypes.c_float)]
+
+    def as_dict(self) -> dict:
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+class DpcJob(ctypes.Structure):
+    _fields_ = [("points", ctypes.c_void_p), ("n", ctypes.c_int64), ("d", ctypes.c_int32),
+                ("d_cut", ctypes.c_int64), ("n_queries", ctypes.c_int32), ("rho_min", ctypes.c_void_p),
+                ("delta_min", ctypes.c_void_p), ("rho_out", ctypes.c_void_p), ("dep_out", ctypes.c_void_p),
+                ("delta2_out", ctypes.c_void_p), ("label_out", ctypes.c_void_p),
+                ("n_centers_out", ctypes.c_void_p)]
+
+
+class DpcResult(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int), ("queue_ms", ctypes.c_double), ("run_ms", ctypes.c_double)]
+
+
+_lib = None
+_lock = threading.Lock()
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def lib():
+    """Load libdpc.so, building it first if it is missing or stale."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        path = _build.build()
+        L = ctypes.CDLL(path)
+        vp, i64, i32, st = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_int
+        sig = {
+            "dpc_create": ([ctypes.POINTER(DpcOptions), ctypes.POINTER(vp)], st),
+            "dpc_destroy": ([vp], st),
+            "dpc_last_error": ([], ctypes.c_char_p),
+            "dpc_density": ([vp, vp, i64, i32, i64, ctypes.c_int, ctypes.POINTER(vp), vp], st),
+            "dpc_dependent": ([vp, vp, vp], st),
+            "dpc_label": ([vp, i64, i64, vp, ctypes.POINTER(i64)], st),
+            "dpc_release": ([vp], st),
+            "dpc_ds_info": ([vp, ctypes.POINTER(DpcInfo)], st),
+            "dpc_set_profiling": ([vp, ctypes.c_int], st),
+            "dpc_submit": ([vp, ctypes.POINTER(DpcJob), ctypes.POINTER(ctypes.c_uint64)], st),
+            "dpc_poll": ([vp, ctypes.c_uint64, ctypes.POINTER(DpcResult)], st),
+            "dpc_flush": ([vp], st),
+            "dpc_wait": ([vp, ctypes.c_uint64, i64, ctypes.POINTER(DpcResult)], st),
+            "dpc_kernel_launches": ([], i64),
+            "dpc_probe_pair_rate": ([ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
+                                     ctypes.POINTER(ctypes.c_double)], st),
+        }
+        for name, (args, res) in sig.items():
+            f = getattr(L, name)
+            f.argtypes = args
+            f.restype = res
+        _lib = L
+        return L
+
+
+def dpc_kernel_launches() -> int:
+    return int(lib().dpc_kernel_launches())
+
+
+def dpc_probe_pair_rate(device: int, d: int):
+    """(pairs/s, ms) of the register-resident 32-bit pair test on every SM."""
+    r, t = ctypes.c_double(0), ctypes.c_double(0)
+    _check(lib().dpc_probe_pair_rate(device, d, ctypes.byref(r), ctypes.byref(t)), "dpc_probe_pair_rate")
+    return r.value, t.value
+
+
+def dpc_last_error() -> str:
+    m = lib().dpc_last_error()
+    return m.decode() if m else ""
+
+
+def _check(status: int, where: str, ok=(DPC_OK,)) -> int:
+    if status not in ok:
+        raise DpcError(status, where, dpc_last_error())
+    return status
+
+
+# ---------------------------------------------------------------- raw calls
+
+def dpc_create(device=0, stream_ptr=0, hbm_cap_bytes=0, mode=0, max_inflight=0, debug=0):
+    o = DpcOptions(device, stream_ptr or None, hbm_cap_bytes, None, debug, mode, max_inflight)
+    h = ctypes.c_void_p()
+    _check(lib().dpc_create(ctypes.byref(o), ctypes.byref(h)), "dpc_create")
+    return h
+
+
+def dpc_destroy(ctx):
+    return _check(lib().dpc_destroy(ctx), "dpc_destroy")
+
+
+def dpc_density(ctx, points_ptr, n, d, d_cut, is_device, rho_ptr=None):
+    h = ctypes.c_void_p()
+    _check(lib().dpc_density(ctx, points_ptr, n, d, d_cut, is_device, ctypes.byref(h), rho_ptr), "dpc_density")
+    return h
+
+
+def dpc_dependent(ds, dep_ptr=None, delta2_ptr=None):
+    return _check(lib().dpc_dependent(ds, dep_ptr, delta2_ptr), "dpc_dependent")
+
+
+def dpc_label(ds, rho_min, delta_min, label_ptr=None):
+    nc = ctypes.c_int64(0)
+    _check(lib().dpc_label(ds, int(rho_min), int(delta_min), label_ptr, ctypes.byref(nc)), "dpc_label")
+    return int(nc.value)
+
+
+def dpc_release(ds):
+    return _check(lib().dpc_release(ds), "dpc_release")
+
+
+def dpc_ds_info(ds) -> dict:
+    info = DpcInfo()
+    _check(lib().dpc_ds_info(ds, ctypes.byref(info)), "dpc_ds_info")
+    return info.as_dict()
+
+
+def dpc_set_profiling(ctx, on: bool):
+    return _check(lib().dpc_set_profiling(ctx, 1 if on else 0), "dpc_set_profiling")
+
+
+def dpc_submit(ctx, job: "DpcJob") -> int:
+    t = ctypes.c_uint64(0)
+    _check(lib().dpc_submit(ctx, ctypes.byref(job), ctypes.byref(t)), "dpc_submit")
+    return int(t.value)
+
+
+def dpc_poll(ctx, ticket: int):
+    r = DpcResult()
+    s = lib().dpc_poll(ctx, ticket, ctypes.byref(r))
+    return s, r
+
+
+def dpc_flush(ctx):
+    return _check(lib().dpc_flush(ctx), "dpc_flush")
+
+
+def dpc_wait(ctx, ticket: int, timeout_ms: int = -1):
+    r = DpcResult()
+    s = lib().dpc_wait(ctx, ticket, int(timeout_ms if timeout_ms >= 0 else 1 << 40), ctypes.byref(r))
+    return s, r
+
+
+# ---------------------------------------------------------------- wrappers
+
+def _is_torch(x) -> bool:
+    return type(x).__module__.startswith("torch")
+
+
+def _arg(x, dtype, shape=None):
+    """(pointer, is_device) for a numpy array or a torch tensor."""
+    if x is None:
+        return None, 0
+    if _is_torch(x):
+        import torch
+        want = {np.int32: torch.int32, np.int64: torch.int64}[dtype]
+        if x.dtype != want or not x.is_contiguous():
+            raise ValueError(f"tensor must be contiguous {want}")
+        if shape is not None and tuple(x.shape) != tuple(shape):
+            raise ValueError(f"tensor shape {tuple(x.shape)} != {tuple(shape)}")
+        return ctypes.c_void_p(x.data_ptr()), 1 if x.is_cuda else 0
+    if not isinstance(x, np.ndarray) or x.dtype != dtype or not x.flags.c_contiguous:
+        raise ValueError(f"array must be a contiguous numpy {np.dtype(dtype).name} array")
+    if shape is not None and x.shape != tuple(shape):
+        raise ValueError(f"array shape {x.shape} != {tuple(shape)}")
+    return x.ctypes.data_as(ctypes.c_void_p), 0
+
+
+class Context:
+    """A libdpc context on one device and one CUDA stream.
+
+    With torch available the context runs on a torch CUDA stream
+    (``self.stream``), so callers can time it with torch events and order
+    their own work against it."""
+
+    def __init__(self, device: int = 0, stream=None, mode: int = 0, hbm_cap_bytes: int = 0,
+                 max_inflight: int = 0, debug: bool = False, profiling: bool = False):
+        self.device = device
+        self.stream = stream
+        ptr = 0
+        try:
+            import torch
+            if stream is None and torch.cuda.is_available():
+                self.stream = torch.cuda.Stream(device=device)
+            if self.stream is not None:
+                ptr = self.stream.cuda_stream
+        except ImportError:
+            pass
+        self.handle = dpc_create(device, ptr, hbm_cap_bytes, mode, max_inflight, 1 if debug else 0)
+        if profiling:
+            dpc_set_profiling(self.handle, True)
+
+    def close(self):
+        if self.handle is not None:
+            dpc_destroy(self.handle)
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _order_after_torch(self, *tensors):
+        if self.stream is None or not any(_is_torch(t) and t.is_cuda for t in tensors if t is not None):
+            return
+        import torch
+        self.stream.wait_stream(torch.cuda.current_stream(self.device))
+
+    def density(self, points, d_cut: int, rho_out=None) -> "Dataset":
+        if points.ndim != 2:
+            raise ValueError("points must be n x d")
+        n, d = int(points.shape[0]), int(points.shape[1])
+        pp, dev = _arg(points, np.int32)
+        rp, rdev = _arg(rho_out, np.int32, (n,))
+        if rho_out is not None and rdev != dev:
+            raise ValueError("rho_out must live where points live")
+        self._order_after_torch(points, rho_out)
+        h = dpc_density(self.handle, pp, n, d, int(d_cut), dev, rp)
+        return Dataset(self, h, n, dev)
+
+    def submit(self, job: "Job") -> int:
+        t = dpc_submit(self.handle, job.c)
+        job.ticket = t
+        return t
+
+    def flush(self):
+        return dpc_flush(self.handle)
+
+    def poll(self, ticket: int):
+        return dpc_poll(self.handle, ticket)
+
+    def wait(self, ticket: int, timeout_ms: int = -1):
+        return dpc_wait(self.handle, ticket, timeout_ms)
+
+
+class Dataset:
+    """A dataset clustered on the device (rho done; dep/labels on demand)."""
+
+    def __init__(self, ctx: Context, handle, n: int, is_device: int):
+        self.ctx, self.handle, self.n, self.is_device = ctx, handle, n, is_device
+
+    def _out(self, x, dtype, shape):
+        p, dev = _arg(x, dtype, shape)
+        if x is not None and dev != self.is_device:
+            raise ValueError("outputs must live where the dataset's input lived")
+        return p
+
+    def dependent(self, dep_out=None, delta2_out=None):
+        self.ctx._order_after_torch(dep_out, delta2_out)
+        dpc_dependent(self.handle, self._out(dep_out, np.int32, (self.n,)),
+                      self._out(delta2_out, np.int64, (self.n,)))
+
+    def label(self, rho_min: int, delta_min: int, label_out=None) -> int:
+        self.ctx._order_after_torch(label_out)
+        return dpc_label(self.handle, rho_min, delta_min, self._out(label_out, np.int32, (self.n,)))
+
+    def info(self) -> dict:
+        return dpc_ds_info(self.handle)
+
+    def release(self):
+        if self.handle is not None:
+            dpc_release(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.release()
+        except Exception:
+            pass
+
+
+class Job:
+    """One dataset + (rho_min, delta_min) queries for dpc_submit, with host
+    output arrays allocated here (rho, dep, delta2, labels[q], n_centers[q])."""
+
+    def __init__(self, points: np.ndarray, d_cut: int, queries):
+        self.points = np.ascontiguousarray(points, dtype=np.int32)
+        n, d = self.points.shape
+        q = list(queries)
+        self.rho_min = np.array([int(a) for a, _ in q], dtype=np.int64)
+        self.delta_min = np.array([int(b) for _, b in q], dtype=np.int64)
+        self.rho = np.empty(n, np.int32)
+        self.dep = np.empty(n, np.int32)
+        self.delta2 = np.empty(n, np.int64)
+        self.label = np.empty((len(q), n), np.int32)
+        self.n_centers = np.empty(len(q), np.int64)
+        p = lambda a: a.ctypes.data_as(ctypes.c_void_p)
+        self.c = DpcJob(p(self.points), n, d, int(d_cut), len(q), p(self.rho_min), p(self.delta_min),
+                        p(self.rho), p(self.dep), p(self.delta2), p(self.label), p(self.n_centers))
+        self.ticket = None
+
+
+def cluster(points: np.ndarray, d_cut: int, rho_min: int, delta_min: int, device: int = 0) -> dict:
+    """The whole path on host arrays: rho, dep, delta2, label, n_centers."""
+    pts = np.ascontiguousarray(points, dtype=np.int32)
+    n = pts.shape[0]
+    with Context(device) as ctx:
+        rho = np.empty(n, np.int32)
+        ds = ctx.density(pts, d_cut, rho)
+        dep = np.empty(n, np.int32)
+        d2 = np.empty(n, np.int64)
+        ds.dependent(dep, d2)
+        lab = np.empty(n, np.int32)
+        nc = ds.label(rho_min, delta_min, lab)
+        ds.release()
+    return {"rho": rho, "dep": dep, "delta2": d2, "label": lab, "n_centers": nc}

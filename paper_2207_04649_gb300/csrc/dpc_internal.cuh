@@ -1,0 +1,156 @@
+// Internal declarations shared by the CUDA translation units of libdpc.
+//
+// Exact Density-Peaks Clustering (the paper's Section 2.1, Definitions 1-6)
+// on one GPU. Every stage works on a *batch* of independent datasets laid
+// out back to back; the plain one-dataset path is a batch of one.
+//
+// Index spaces of a batch with N = sum of n_b points:
+//   g  "original" global index: dataset b owns [pt_off_b, pt_off_b + n_b)
+//      in the caller's point order.
+//   p  "sorted" global index: the same range of dataset b after the points
+//      are sorted by grid cell (Morton order of the cells).
+// perm[p] = g and pos_of[g] = p map between them.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace dpc {
+
+constexpr int kMaxDims = 8;
+constexpr int kMaxGridDims = 4;
+constexpr uint64_t kEmptyKey = ~0ull;
+constexpr int kLeaf = 16;          // points per tree leaf (delta remainder search)
+
+// Per-dataset description, shared by host and device.
+struct DsDesc {
+    int64_t pt_off;       // first global index (both index spaces)
+    int64_t rec_off;      // first int4 record of the sorted points
+    int64_t in_off;       // first int32 of the input points (row-major n x d)
+    int64_t d_cut;
+    int64_t d_cut2;       // d_cut^2
+    int64_t s;            // grid cell side
+    uint64_t cbase;       // cell-key base of this dataset
+    int64_t rho_min;      // label query
+    int64_t delta_min2;   // delta_min^2
+    int64_t leaf_off;     // first leaf of this dataset
+    int64_t node_off;     // first tree node (heap index 0) of this dataset
+    int32_t n, d;
+    int32_t dp;           // int4 records per point: 1 (d <= 4) or 2 (d <= 8)
+    int32_t k;            // gridded dims
+    int32_t gdim[kMaxGridDims];    // coordinate of each gridded dim
+    int32_t origin[kMaxGridDims];  // smallest coordinate per gridded dim
+    int32_t ext[kMaxGridDims];     // cells per gridded dim
+    int32_t mbits;        // Morton bits per gridded dim
+    int32_t R;            // neighbour reach in cells
+    int32_t w32;          // all candidate pair sums fit 31 bits
+    int32_t h;            // tree height: 2^h leaf slots
+    int32_t nleaf;        // leaves (ceil(n / kLeaf))
+    int32_t rbits;        // bits of the density key in the rank sort
+};
+
+// Device views of a batch's buffers (all device pointers).
+struct BatchView {
+    int32_t B;
+    int64_t N;
+    const DsDesc* desc;        // [B]
+    const int64_t* pt_off;     // [B+1]
+    // input and sorted points
+    const int32_t* in;         // input points, row-major per dataset
+    int4* rec;                 // sorted records (dp int4 per point)
+    uint32_t* perm;            // p -> g
+    uint32_t* pos_of;          // g -> p
+    // grid
+    uint64_t* key;             // cell key per sorted point
+    uint32_t* cell_start;      // [ncells + 1]
+    uint32_t* ncells;          // device scalar
+    int4* hash;                // open addressing: {key lo, key hi, start, count}
+    uint64_t hmask;
+    // rho
+    int32_t* rho_s;            // sorted
+    int32_t* rho;              // original
+    // rank
+    uint32_t* rank;            // original: position in (rho desc, index asc) within its dataset
+    uint32_t* order;           // global rank order: order[pt_off_b + r] = g
+    uint2* ro_s;               // sorted: (rank, original local index)
+    // delta
+    unsigned long long* best_s;  // sorted: packed (min(D, 2^32-1) << 32 | orig local)
+    int32_t* dep;              // original: dependent point (local index), -1 top
+    int64_t* delta2;           // original
+    // labels
+    int32_t* parent;           // original, global
+    int32_t* label;            // original, local
+    unsigned long long* ncent; // [B]
+    unsigned int* err;         // device error word: kErr* bits set by guarded kernels
+};
+
+// Bits of BatchView::err. A guard that trips leaves its output wrong but
+// bounded; the host turns a nonzero word into DPC_ERR_CUDA.
+constexpr unsigned kErrStaging = 1u;   // candidate runs shorter than counted
+constexpr unsigned kErrTreeStack = 2u; // tree search stack full
+constexpr unsigned kErrChain = 4u;     // label chain longer than the dataset
+
+// ---------------------------------------------------------------- helpers
+
+__host__ __device__ inline uint64_t mix64(uint64_t k) {
+    k ^= k >> 33;
+    k *= 0xff51afd7ed558ccdull;
+    k ^= k >> 33;
+    k *= 0xc4ceb9fe1a85ec53ull;
+    k ^= k >> 33;
+    return k;
+}
+
+// Morton code of k cell coordinates with mbits bits each: bit i of dim j
+// lands at position i * k + j.
+__host__ __device__ inline uint64_t morton(const int32_t* c, int k, int mbits) {
+    uint64_t code = 0;
+    for (int i = 0; i < mbits; ++i)
+        for (int j = 0; j < k; ++j)
+            code |= (uint64_t)((c[j] >> i) & 1) << (i * k + j);
+    return code;
+}
+
+__device__ inline int find_ds(const int64_t* pt_off, int B, int64_t g) {
+    int lo = 0, hi = B - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (pt_off[mid] <= g) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+// Hash lookup of a cell key: returns (start, count) or count 0.
+__device__ inline uint2 hash_find(const int4* __restrict__ table, uint64_t mask, uint64_t key) {
+    uint64_t h = mix64(key) & mask;
+    for (uint64_t probe = 0; probe <= mask; ++probe) {
+        int4 e = __ldg(&table[h]);
+        uint64_t k = (uint64_t)(uint32_t)e.x | ((uint64_t)(uint32_t)e.y << 32);
+        if (k == key) return make_uint2((uint32_t)e.z, (uint32_t)e.w);
+        if (k == kEmptyKey) break;
+        h = (h + 1) & mask;
+    }
+    return make_uint2(0u, 0u);
+}
+
+// --------------------------------------------------------- launch helpers
+
+// Count of kernel launches made by this library (all threads).
+void note_launch();
+long long launch_count();
+
+// sort.cu
+size_t radix_sort_temp_bytes(int64_t n);
+// Stable LSD radix sort of (key, value) pairs on bits [0, nbits).
+// Returns false on CUDA error. On return the sorted data is in (k_out, v_out).
+cudaError_t radix_sort_u64(const uint64_t* k_in, const uint32_t* v_in, uint64_t* k_out, uint32_t* v_out,
+                           uint64_t* k_tmp, uint32_t* v_tmp, int64_t n, int nbits, void* temp,
+                           cudaStream_t st);
+cudaError_t radix_sort_u32(const uint32_t* k_in, const uint32_t* v_in, uint32_t* k_out, uint32_t* v_out,
+                           uint32_t* k_tmp, uint32_t* v_tmp, int64_t n, int nbits, void* temp,
+                           cudaStream_t st);
+size_t scan_temp_bytes(int64_t n);
+// Exclusive prefix sum of n uint32 values; writes the total to *total (device) if non-null.
+cudaError_t exclusive_scan_u32(const uint32_t* in, uint32_t* out, int64_t n, uint32_t* total, void* temp,
+                               cudaStream_t st);
+
+}  // namespace dpc

@@ -1,0 +1,73 @@
+// Noise, cluster centers and cluster labels (Definitions 4-6).
+//
+// noise_i  <=> rho_i < rho_min;
+// center_i <=> not noise and delta_i >= delta_min (tested as
+//              delta2_i >= delta_min^2; the densest point has delta2 =
+//              INT64_MAX, so it is a center whenever it is not noise);
+// a center is its own parent, noise has none, every other point hangs on its
+// dependent point. The paper propagates labels depth-first from the centers
+// (Section 2.2, step 4); the same forest is labelled here by pointer jumping:
+// every thread follows its parent chain to the root and stores the progress
+// back into its own parent slot, so chains through it shrink for the other
+// threads. Every value ever stored is an ancestor of the slot's point, so the
+// roots found are exact, whatever the interleaving.
+#include "stages.cuh"
+
+namespace dpc {
+
+namespace {
+
+__global__ void k_parent(BatchView v) {
+    const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const bool valid = g < v.N;
+    int b = -1;
+    bool center = false;
+    if (valid) {
+        b = find_ds(v.pt_off, v.B, g);
+        const DsDesc& ds = v.desc[b];
+        const bool noise = (int64_t)v.rho[g] < ds.rho_min;
+        center = !noise && v.delta2[g] >= ds.delta_min2;
+        v.parent[g] = noise ? -1 : (center ? (int32_t)g : (int32_t)(ds.pt_off + v.dep[g]));
+    }
+    // count centers per dataset, aggregated over the lanes of one dataset
+    const unsigned same = __match_any_sync(0xffffffffu, b);
+    const unsigned ctr = __ballot_sync(0xffffffffu, center) & same;
+    const int lane = threadIdx.x & 31;
+    if (valid && ctr != 0u && (same & ((1u << lane) - 1u)) == 0u)
+        atomicAdd(&v.ncent[b], (unsigned long long)__popc(ctr));
+}
+
+__global__ void k_jump(BatchView v) {
+    const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= v.N) return;
+    int32_t p = v.parent[g];
+    if (p < 0) {
+        v.label[g] = -1;
+        return;
+    }
+    // a chain visits distinct points of one dataset, so it is shorter than N
+    for (int64_t hop = 0;; ++hop) {
+        const int32_t pp = __ldcg(&v.parent[p]);
+        if (pp == p) break;
+        if (hop > v.N || pp < 0) {
+            atomicOr(v.err, kErrChain);
+            break;
+        }
+        p = pp;
+        __stcg(&v.parent[g], p);
+    }
+    const int b = find_ds(v.pt_off, v.B, g);
+    v.label[g] = (int32_t)(p - v.pt_off[b]);
+}
+
+}  // namespace
+
+cudaError_t launch_labels(const BatchView& v, cudaStream_t st) {
+    cudaError_t e = cudaMemsetAsync(v.ncent, 0, sizeof(unsigned long long) * v.B, st);
+    if (e != cudaSuccess || v.N == 0) return e;
+    (k_parent<<<grid_for(v.N, 256), 256, 0, st>>>(v), note_launch());
+    (k_jump<<<grid_for(v.N, 256), 256, 0, st>>>(v), note_launch());
+    return cudaGetLastError();
+}
+
+}  // namespace dpc

@@ -1,0 +1,102 @@
+// Throughput probe for the density stage's pair test.
+//
+// Every thread keeps 4 query points and 16 candidate points in registers and
+// applies the exact 32-bit test of the density kernel (sum of squared
+// coordinate differences minus d_cut^2, sign bit accumulated) to all 64
+// pairs per sweep, on every SM. The queries move by one unit after each
+// sweep, depending on the counts, so nothing can be hoisted out of the loop.
+// The rate it reports is the integer-ALU ceiling of that instruction mix on
+// this GPU at its current clock: the denominator of the density kernel's
+// roofline.
+#include "dpc.h"
+#include "dpc_internal.cuh"
+
+namespace dpc {
+namespace {
+
+template <int D>
+__global__ void __launch_bounds__(256) k_pair_probe(const int32_t* __restrict__ seed, int iters, int T,
+                                                   unsigned long long* __restrict__ sink) {
+    int32_t q[4][D], c[16][D];
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int k = 0; k < D; ++k) q[i][k] = seed[(t * 7 + i * D + k) & 1023];
+#pragma unroll
+    for (int j = 0; j < 16; ++j)
+#pragma unroll
+        for (int k = 0; k < D; ++k) c[j][k] = seed[(t * 13 + j * D + k + 512) & 1023];
+    uint32_t cnt[4] = {0u, 0u, 0u, 0u};
+    for (int it = 0; it < iters; ++it) {
+#pragma unroll
+        for (int j = 0; j < 16; ++j)
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                int s = -T;
+#pragma unroll
+                for (int k = 0; k < D; ++k) {
+                    const int dd = q[i][k] - c[j][k];
+                    s += dd * dd;
+                }
+                cnt[i] += (uint32_t)s >> 31;
+            }
+#pragma unroll
+        for (int i = 0; i < 4; ++i) q[i][0] += (int)(cnt[i] & 1u);
+    }
+    if (cnt[0] + cnt[1] + cnt[2] + cnt[3] == 0xdeadbeefu) sink[0] = t;
+}
+
+}  // namespace
+}  // namespace dpc
+
+extern "C" dpc_status dpc_probe_pair_rate(int device, int d, double* pairs_per_s, double* ms) {
+    using namespace dpc;
+    if (!pairs_per_s || d < 1 || d > 8) return DPC_ERR_INVALID_ARG;
+    if (cudaSetDevice(device) != cudaSuccess) return DPC_ERR_CUDA;
+    int sms = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
+    int32_t* seed = nullptr;
+    unsigned long long* sink = nullptr;
+    if (cudaMalloc(&seed, 1024 * sizeof(int32_t)) != cudaSuccess) return DPC_ERR_OOM;
+    if (cudaMalloc(&sink, sizeof(unsigned long long)) != cudaSuccess) {
+        cudaFree(seed);
+        return DPC_ERR_OOM;
+    }
+    int32_t h[1024];
+    for (int i = 0; i < 1024; ++i) h[i] = (int32_t)((i * 2654435761u) % 600u);
+    cudaMemcpy(seed, h, sizeof(h), cudaMemcpyHostToDevice);
+    const int blocks = sms * 8, threads = 256, iters = 4096;
+    cudaEvent_t a, b;
+    cudaEventCreate(&a);
+    cudaEventCreate(&b);
+    auto launch = [&](int it) {
+        switch (d) {
+            case 1: k_pair_probe<1><<<blocks, threads>>>(seed, it, 90000, sink); break;
+            case 2: k_pair_probe<2><<<blocks, threads>>>(seed, it, 90000, sink); break;
+            case 3: k_pair_probe<3><<<blocks, threads>>>(seed, it, 90000, sink); break;
+            case 4: k_pair_probe<4><<<blocks, threads>>>(seed, it, 90000, sink); break;
+            case 5: k_pair_probe<5><<<blocks, threads>>>(seed, it, 90000, sink); break;
+            case 6: k_pair_probe<6><<<blocks, threads>>>(seed, it, 90000, sink); break;
+            case 7: k_pair_probe<7><<<blocks, threads>>>(seed, it, 90000, sink); break;
+            default: k_pair_probe<8><<<blocks, threads>>>(seed, it, 90000, sink); break;
+        }
+        note_launch();
+    };
+    launch(64);  // warm-up
+    cudaEventRecord(a);
+    launch(iters);
+    cudaEventRecord(b);
+    cudaError_t e = cudaEventSynchronize(b);
+    float t = 0.f;
+    cudaEventElapsedTime(&t, a, b);
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    cudaFree(seed);
+    cudaFree(sink);
+    if (e != cudaSuccess) return DPC_ERR_CUDA;
+    const double pairs = (double)blocks * threads * iters * 64.0;
+    *pairs_per_s = pairs / (t * 1e-3);
+    if (ms) *ms = t;
+    return DPC_OK;
+}

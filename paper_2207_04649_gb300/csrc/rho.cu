@@ -1,0 +1,350 @@
+// Local density (Definition 1): rho_i = #{ j : dist(p_i, p_j) < d_cut },
+// p_i itself included, compared exactly as sum_k (x_ik - x_jk)^2 < d_cut^2
+// in integers.
+//
+// Candidates for the points of a cell are the points of its neighbour cells
+// (the cell itself included). Handling all points of a cell against one
+// candidate list is the paper's joint range search (Section 4.2: one range
+// query per cell, then a scan of the result for every member), with the
+// neighbour cells of the grid in place of the kd-tree query.
+//
+// Two kernels share the work:
+//  * dense cells (more than kSparseMax points): one warp per work item
+//    (cell, chunk of up to 128 queries held 4 per lane in registers, chunk
+//    of candidates). Candidates are staged in shared memory from contiguous
+//    runs of sorted records with 128-bit loads and read back as broadcasts.
+//    Items are claimed from an atomic counter by persistent warps.
+//  * sparse cells: one thread per cell, its few queries in registers,
+//    candidates read straight from the L1/L2-resident sorted records.
+//
+// Pair arithmetic: when every candidate difference is small enough
+// (DsDesc::w32) the test runs in 32-bit integers as the sign of
+// sum_k dx_k^2 - d_cut^2; otherwise in 64-bit integers.
+#include "stages.cuh"
+#include <algorithm>
+
+namespace dpc {
+
+namespace {
+
+constexpr int kRhoThreads = 256;
+constexpr int kCb = 128;  // staged candidates per warp
+
+__global__ void k_classify(BatchView v, uint32_t* __restrict__ dflag, uint32_t* __restrict__ sflag, int64_t bound) {
+    const uint32_t nc = *v.ncells;
+    for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < bound; c += (int64_t)gridDim.x * blockDim.x) {
+        uint32_t dense = 0, sparse = 0;
+        if (c < nc) {
+            const uint32_t m = v.cell_start[c + 1] - v.cell_start[c];
+            dense = m > (uint32_t)kSparseMax;
+            sparse = !dense;
+        }
+        dflag[c] = dense;
+        sflag[c] = sparse;
+    }
+}
+
+__global__ void k_compact_cells(BatchView v, CellPrepBufs cb, int64_t bound) {
+    const uint32_t nc = *v.ncells;
+    for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < bound; c += (int64_t)gridDim.x * blockDim.x) {
+        if (c >= nc) break;
+        if (cb.dflag[c]) cb.dense[cb.didx[c]] = (uint32_t)c;
+        else cb.sparse[cb.sidx[c]] = (uint32_t)c;
+    }
+}
+
+// One warp per dense cell: lanes look up the neighbour cells in parallel and
+// the non-empty ones are compacted, in neighbour order, into the cell's run
+// list; the cell's candidate count fixes how many work items it gets.
+__global__ void k_dense_prep(BatchView v, CellPrepBufs cb, int kch) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warp0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const uint32_t nd = *cb.ndense;
+    const unsigned lt = (1u << lane) - 1u;
+    for (int64_t dc = warp0; dc < nd; dc += nwarps) {
+        const uint32_t c = cb.dense[dc];
+        const uint32_t cs = v.cell_start[c], m = v.cell_start[c + 1] - cs;
+        const int b = find_ds(v.pt_off, v.B, cs);
+        const DsDesc& ds = v.desc[b];
+        const int4* r0 = v.rec + ds.rec_off + ((int64_t)cs - ds.pt_off) * ds.dp;
+        int32_t cc[kMaxGridDims];
+        for (int j = 0; j < ds.k; ++j) cc[j] = cell_coord(ds, j, rec_coord(r0, ds.gdim[j]));
+        const int nnb = num_neighbours(ds);
+        uint32_t nr = 0, cand = 0;
+        for (int base = 0; base < nnb; base += 32) {
+            const int t = base + lane;
+            uint2 e = make_uint2(0u, 0u);
+            int32_t nc[kMaxGridDims];
+            if (t < nnb && neighbour(ds, cc, t, nc))
+                e = hash_find(v.hash, v.hmask, ds.cbase + morton(nc, ds.k, ds.mbits));
+            const unsigned found = __ballot_sync(0xffffffffu, e.y > 0u);
+            if (e.y > 0u) cb.runs[dc * kMaxNb + nr + __popc(found & lt)] = e;
+            nr += __popc(found);
+            uint32_t s = e.y;
+            for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+            cand += s;
+        }
+        if (lane == 0) {
+            atomicAdd(&cb.stats[0], (unsigned long long)m * cand);
+            cb.nruns[dc] = nr;
+            cb.cand[dc] = cand;
+            const uint32_t nq = (m + kQch - 1) / kQch, nk = (cand + kch - 1) / kch;
+            cb.nitem_c[dc] = nq * (nk > 0 ? nk : 1);
+        }
+    }
+}
+
+// Work items of every dense cell: (query chunk) x (candidate chunk).
+__global__ void k_fill_items(BatchView v, CellPrepBufs cb, int kch) {
+    const uint32_t nd = *cb.ndense;
+    for (int64_t dc = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; dc < nd; dc += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t c = cb.dense[dc];
+        const uint32_t m = v.cell_start[c + 1] - v.cell_start[c];
+        const uint32_t nq = (m + kQch - 1) / kQch;
+        const uint32_t cand = cb.cand[dc];
+        const uint32_t nk = cand == 0u ? 1u : (cand + kch - 1) / kch;
+        uint4* out = cb.items + cb.item_off[dc];
+        for (uint32_t q = 0; q < nq; ++q)
+            for (uint32_t k = 0; k < nk; ++k) out[q * nk + k] = make_uint4((uint32_t)dc, q, k, 0u);
+    }
+}
+
+template <int D>
+__device__ __forceinline__ void load_point(const int4* r, int32_t (&x)[D]) {
+    const int4 a = r[0];
+    int32_t t[8] = {a.x, a.y, a.z, a.w, 0, 0, 0, 0};
+    if (D > 4) {
+        const int4 bq = r[1];
+        t[4] = bq.x; t[5] = bq.y; t[6] = bq.z; t[7] = bq.w;
+    }
+#pragma unroll
+    for (int k = 0; k < D; ++k) x[k] = t[k];
+}
+
+template <int D, bool W64>
+__device__ __forceinline__ uint32_t inside(const int32_t (&q)[D], const int32_t (&c)[D], int64_t T) {
+    if (W64) {
+        long long s = 0;
+#pragma unroll
+        for (int k = 0; k < D; ++k) {
+            const int dd = q[k] - c[k];
+            s += (long long)dd * dd;
+        }
+        return s < T ? 1u : 0u;
+    } else {
+        int s = -(int)T;
+#pragma unroll
+        for (int k = 0; k < D; ++k) {
+            const int dd = q[k] - c[k];
+            s += dd * dd;
+        }
+        return (uint32_t)s >> 31;
+    }
+}
+
+template <int D, bool W64, int Q>
+__device__ __forceinline__ void eval_rho(const int4* buf, int nb, const int32_t (&qx)[4][D], uint32_t (&cnt)[4],
+                                         int64_t T) {
+    constexpr int DP = D <= 4 ? 1 : 2;
+#pragma unroll 2
+    for (int j = 0; j < nb; ++j) {
+        int32_t c[D];
+        load_point<D>(buf + j * DP, c);
+#pragma unroll
+        for (int t = 0; t < Q; ++t) cnt[t] += inside<D, W64>(qx[t], c, T);
+    }
+}
+
+template <int D, bool W64>
+__global__ void __launch_bounds__(kRhoThreads) k_rho_dense(BatchView v, CellWork w, uint32_t* counter) {
+    constexpr int DP = D <= 4 ? 1 : 2;
+    __shared__ int4 sbuf[kRhoThreads / 32][kCb * DP];
+    const int lane = threadIdx.x & 31;
+    int4* buf = sbuf[threadIdx.x >> 5];
+    const uint32_t nitems = *w.nitems;
+    while (true) {
+        uint32_t it = 0;
+        if (lane == 0) it = atomicAdd(counter, 1u);
+        it = __shfl_sync(0xffffffffu, it, 0);
+        if (it >= nitems) break;
+        const uint4 item = w.items[it];
+        const uint32_t dc = item.x, qc = item.y, kc = item.z;
+        const uint32_t c = w.dense[dc];
+        const uint32_t cs = v.cell_start[c], m = v.cell_start[c + 1] - cs;
+        const int b = find_ds(v.pt_off, v.B, cs);
+        const DsDesc& ds = v.desc[b];
+        if (ds.d != D || (ds.w32 == 0) != W64) continue;
+        const int4* recb = v.rec + ds.rec_off - ds.pt_off * DP;  // indexed by global sorted position
+        const int q0 = (int)qc * kQch;
+        const int nq = min(kQch, (int)m - q0);
+        const int Q = (nq + 31) >> 5;
+        int32_t qx[4][D];
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+            const int qi = min(lane + 32 * t, nq - 1);
+            load_point<D>(recb + ((int64_t)cs + q0 + qi) * DP, qx[t]);
+        }
+        uint32_t cnt[4] = {0u, 0u, 0u, 0u};
+        const uint2* runs = w.runs + (int64_t)dc * kMaxNb;
+        const uint32_t nr = w.nruns[dc], ctot = w.cand[dc];
+        const uint32_t k0 = kc * (uint32_t)w.kch;
+        uint32_t remaining = min(ctot, k0 + (uint32_t)w.kch) - k0;
+        uint32_t ri = 0, roff = k0;
+        while (ri < nr) {
+            const uint32_t len = runs[ri].y;
+            if (roff < len) break;
+            roff -= len;
+            ++ri;
+        }
+        const int64_t T = ds.d_cut2;
+        while (remaining > 0u) {
+            int nb = 0;
+            while (nb < kCb && remaining > 0u) {
+                const uint2 run = ri < nr ? runs[ri] : make_uint2(0u, 0u);
+                const uint32_t take = ri < nr ? min(min(run.y - roff, (uint32_t)(kCb - nb)), remaining) : 0u;
+                if (take == 0u) {  // runs exhausted early: cannot happen when counts agree
+                    if (lane == 0) atomicOr(v.err, kErrStaging);
+                    remaining = 0u;
+                    break;
+                }
+                const int4* src = recb + ((int64_t)run.x + roff) * DP;
+                for (uint32_t t = lane; t < take * DP; t += 32) buf[nb * DP + t] = __ldg(src + t);
+                nb += (int)take;
+                roff += take;
+                remaining -= take;
+                if (roff == run.y) {
+                    ++ri;
+                    roff = 0;
+                }
+            }
+            __syncwarp();
+            switch (Q) {
+                case 1: eval_rho<D, W64, 1>(buf, nb, qx, cnt, T); break;
+                case 2: eval_rho<D, W64, 2>(buf, nb, qx, cnt, T); break;
+                case 3: eval_rho<D, W64, 3>(buf, nb, qx, cnt, T); break;
+                default: eval_rho<D, W64, 4>(buf, nb, qx, cnt, T); break;
+            }
+            __syncwarp();
+        }
+#pragma unroll
+        for (int t = 0; t < 4; ++t)
+            if (lane + 32 * t < nq) atomicAdd(&v.rho_s[cs + q0 + lane + 32 * t], (int)cnt[t]);
+    }
+}
+
+template <int D, bool W64>
+__global__ void __launch_bounds__(256) k_rho_sparse(BatchView v, CellWork w) {
+    constexpr int DP = D <= 4 ? 1 : 2;
+    const uint32_t ns = *w.nsparse;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < ns; i += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t c = w.sparse[i];
+        const uint32_t cs = v.cell_start[c], m = v.cell_start[c + 1] - cs;
+        const int b = find_ds(v.pt_off, v.B, cs);
+        const DsDesc& ds = v.desc[b];
+        if (ds.d != D || (ds.w32 == 0) != W64) continue;
+        const int4* recb = v.rec + ds.rec_off - ds.pt_off * DP;
+        int32_t qx[kSparseMax][D];
+#pragma unroll
+        for (int t = 0; t < kSparseMax; ++t) load_point<D>(recb + ((int64_t)cs + min((uint32_t)t, m - 1)) * DP, qx[t]);
+        int32_t cc[kMaxGridDims];
+        for (int j = 0; j < ds.k; ++j) cc[j] = cell_coord(ds, j, rec_coord(recb + (int64_t)cs * DP, ds.gdim[j]));
+        uint32_t cnt[kSparseMax];
+#pragma unroll
+        for (int t = 0; t < kSparseMax; ++t) cnt[t] = 0u;
+        const int nnb = num_neighbours(ds);
+        const int64_t T = ds.d_cut2;
+        uint32_t ncand = 0;
+        for (int t = 0; t < nnb; ++t) {
+            int32_t nc[kMaxGridDims];
+            if (!neighbour(ds, cc, t, nc)) continue;
+            const uint2 e = hash_find(v.hash, v.hmask, ds.cbase + morton(nc, ds.k, ds.mbits));
+            ncand += e.y;
+            for (uint32_t j = 0; j < e.y; ++j) {
+                int32_t cj[D];
+                load_point<D>(recb + ((int64_t)e.x + j) * DP, cj);
+#pragma unroll
+                for (int q = 0; q < kSparseMax; ++q) cnt[q] += inside<D, W64>(qx[q], cj, T);
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < kSparseMax; ++q)
+            if ((uint32_t)q < m) v.rho_s[cs + q] = (int32_t)cnt[q];
+        atomicAdd(&w.stats[1], (unsigned long long)m * ncand);
+    }
+}
+
+__global__ void k_rho_scatter(BatchView v) {
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p < v.N) v.rho[v.perm[p]] = v.rho_s[p];
+}
+
+template <int D, bool W64>
+void launch_rho_class(const BatchView& v, const CellWork& w, int64_t nitems_bound, int64_t nsparse_bound,
+                      uint32_t* counter, cudaStream_t st) {
+    if (nitems_bound > 0) {
+        const unsigned blocks = (unsigned)std::max<int64_t>(1, std::min<int64_t>(152 * 8, (nitems_bound + 7) / 8));
+        (k_rho_dense<D, W64><<<blocks, kRhoThreads, 0, st>>>(v, w, counter), note_launch());
+    }
+    if (nsparse_bound > 0) {
+        const unsigned blocks = (unsigned)std::min<int64_t>(152 * 32, grid_for(nsparse_bound, 256));
+        (k_rho_sparse<D, W64><<<blocks, 256, 0, st>>>(v, w), note_launch());
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_classify_cells(const BatchView& v, const CellPrepBufs& cb, int64_t ncells_bound, void* scan_temp,
+                                  cudaStream_t st) {
+    if (ncells_bound <= 0) return cudaSuccess;
+    const unsigned blocks = (unsigned)std::min<int64_t>(152 * 16, grid_for(ncells_bound, 256));
+    (k_classify<<<blocks, 256, 0, st>>>(v, cb.dflag, cb.sflag, ncells_bound), note_launch());
+    cudaError_t e = exclusive_scan_u32(cb.dflag, cb.didx, ncells_bound, cb.ndense, scan_temp, st);
+    if (e != cudaSuccess) return e;
+    e = exclusive_scan_u32(cb.sflag, cb.sidx, ncells_bound, cb.nsparse, scan_temp, st);
+    if (e != cudaSuccess) return e;
+    (k_compact_cells<<<blocks, 256, 0, st>>>(v, cb, ncells_bound), note_launch());
+    return cudaGetLastError();
+}
+
+cudaError_t launch_dense_prep(const BatchView& v, const CellPrepBufs& cb, int64_t ndense_bound, int kch,
+                              void* scan_temp, cudaStream_t st) {
+    if (ndense_bound <= 0) {
+        cudaError_t e = cudaMemsetAsync(cb.nitems, 0, sizeof(uint32_t), st);
+        return e;
+    }
+    const unsigned blocks = (unsigned)std::min<int64_t>(152 * 16, grid_for(ndense_bound * 32, 256));
+    (k_dense_prep<<<blocks, 256, 0, st>>>(v, cb, kch), note_launch());
+    return exclusive_scan_u32(cb.nitem_c, cb.item_off, ndense_bound, cb.nitems, scan_temp, st);
+}
+
+cudaError_t launch_fill_items(const BatchView& v, const CellPrepBufs& cb, int64_t ndense_bound, int kch,
+                              cudaStream_t st) {
+    if (ndense_bound <= 0) return cudaSuccess;
+    const unsigned blocks = (unsigned)std::min<int64_t>(152 * 16, grid_for(ndense_bound, 256));
+    (k_fill_items<<<blocks, 256, 0, st>>>(v, cb, kch), note_launch());
+    return cudaGetLastError();
+}
+
+cudaError_t launch_rho(const BatchView& v, const CellWork& w, uint32_t class_mask, int64_t nitems_bound,
+                       int64_t nsparse_bound, uint32_t* counters, cudaStream_t st) {
+    // one launch pair per (dimension, arithmetic width) class present in the
+    // batch; each kernel skips the items of the other classes
+#define DPC_RHO_CLASS(D)                                                                              \
+    if (class_mask & (1u << (2 * (D - 1))))                                                           \
+        launch_rho_class<D, false>(v, w, nitems_bound, nsparse_bound, counters + 2 * (D - 1), st);    \
+    if (class_mask & (1u << (2 * (D - 1) + 1)))                                                       \
+        launch_rho_class<D, true>(v, w, nitems_bound, nsparse_bound, counters + 2 * (D - 1) + 1, st);
+    DPC_RHO_CLASS(1) DPC_RHO_CLASS(2) DPC_RHO_CLASS(3) DPC_RHO_CLASS(4)
+    DPC_RHO_CLASS(5) DPC_RHO_CLASS(6) DPC_RHO_CLASS(7) DPC_RHO_CLASS(8)
+#undef DPC_RHO_CLASS
+    return cudaGetLastError();
+}
+
+cudaError_t launch_rho_scatter(const BatchView& v, cudaStream_t st) {
+    if (v.N == 0) return cudaSuccess;
+    (k_rho_scatter<<<grid_for(v.N, 256), 256, 0, st>>>(v), note_launch());
+    return cudaGetLastError();
+}
+
+}  // namespace dpc

@@ -1,0 +1,942 @@
+// Host runtime of libdpc: planning of the grid, device memory, the order of
+// the stages, the C ABI, and the batched / served job modes.
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <memory>
+#include <mutex>
+#include <string>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+#include "dpc.h"
+#include "stages.cuh"
+
+namespace dpc {
+
+namespace {
+
+thread_local std::string g_err;
+
+dpc_status fail(dpc_status s, const std::string& msg) {
+    g_err = msg;
+    return s;
+}
+
+dpc_status cuda_fail(cudaError_t e, const char* what) {
+    g_err = std::string(what) + ": " + cudaGetErrorString(e);
+    return e == cudaErrorMemoryAllocation ? DPC_ERR_OOM : DPC_ERR_CUDA;
+}
+
+#define DPC_CK(call)                                                 \
+    do {                                                             \
+        cudaError_t e_ = (call);                                     \
+        if (e_ != cudaSuccess) return cuda_fail(e_, #call);          \
+    } while (0)
+
+#define DPC_TRY(call)                                                \
+    do {                                                             \
+        dpc_status s_ = (call);                                      \
+        if (s_ != DPC_OK) return s_;                                 \
+    } while (0)
+
+constexpr int64_t kCoordLimit = 1ll << 30;
+constexpr int64_t kMaxDeltaMin = 3037000499ll;  // floor(sqrt(INT64_MAX))
+constexpr uint64_t kDefaultCap = 150ull << 30;
+
+inline size_t a256(size_t x) { return (x + 255) & ~size_t(255); }
+inline int bits_for(uint64_t x) {  // smallest b with 2^b > x
+    int b = 0;
+    while (b < 64 && (x >> b) != 0) ++b;
+    return b;
+}
+inline int ceil_log2(uint64_t x) {  // smallest b with 2^b >= x
+    int b = 0;
+    while ((1ull << b) < x) ++b;
+    return b;
+}
+
+// Stream-ordered device allocations released together.
+struct Arena {
+    cudaStream_t st = nullptr;
+    std::vector<void*> ptrs;
+    size_t bytes = 0;
+    cudaError_t get(void** p, size_t n) {
+        n = a256(n ? n : 1);
+        cudaError_t e = cudaMallocAsync(p, n, st);
+        if (e == cudaSuccess) {
+            ptrs.push_back(*p);
+            bytes += n;
+        }
+        return e;
+    }
+    template <typename T>
+    cudaError_t get(T** p, size_t count) {
+        return get(reinterpret_cast<void**>(p), count * sizeof(T));
+    }
+    void release() {
+        for (void* p : ptrs) cudaFreeAsync(p, st);
+        ptrs.clear();
+        bytes = 0;
+    }
+};
+
+struct Input {
+    const int32_t* pts;
+    int64_t n;
+    int32_t d;
+    int64_t d_cut;
+    int is_device;
+};
+
+struct Tune {
+    int kch = 2048;         // candidates per dense work item
+    int kmax = 4;           // gridded dims at most
+    uint32_t bf_rank = 1024;  // open points ranked below this take the brute-force pass
+};
+
+}  // namespace
+}  // namespace dpc
+
+struct dpc_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    uint64_t cap = dpc::kDefaultCap;
+    int debug = 0;
+    int mode = 0;
+    int max_inflight = 4;
+    int profiling = 0;
+    dpc::Tune tune;
+    // jobs
+    struct JobRec {
+        dpc_job job;
+        std::vector<int64_t> rmin, dmin;
+        dpc_status status = DPC_PENDING;
+        uint64_t bytes = 0;  // device footprint estimate
+        std::chrono::steady_clock::time_point t_submit, t_admit, t_done;
+    };
+    std::mutex mu;
+    std::condition_variable cv;
+    std::unordered_map<uint64_t, std::shared_ptr<JobRec>> jobs;
+    std::deque<uint64_t> waiting;
+    uint64_t next_ticket = 1;
+    bool stop = false;
+    std::vector<std::thread> workers;
+    uint64_t held_bytes = 0;
+    int max_batch_jobs = 64;  // served mode: jobs admitted into one batch at most
+};
+
+namespace dpc {
+namespace {
+
+struct Batch {
+    dpc_ctx* ctx = nullptr;
+    cudaStream_t st = nullptr;
+    int B = 0;
+    int64_t N = 0;
+    std::vector<DsDesc> hd;
+    std::vector<int64_t> h_pt_off;
+    std::vector<int64_t> h_slot_off;
+    Arena keep, dens;
+    BatchView v{};
+    CellWork w{};
+    DeltaBufs db{};
+    DsDesc* d_desc = nullptr;
+    bool has_density = false, has_dep = false;
+    uint32_t class_mask = 0, dim_mask = 0;
+    int64_t ncells = 0, ndense = 0, nsparse = 0, nitems = 0, ntree = 0, nbf = 0;
+    int64_t cand_pairs = 0;
+    unsigned long long* d_stats = nullptr;
+    uint32_t* d_counters = nullptr;  // [16] rho + [16] ring
+    int out_is_device = 0;
+    float ms[6] = {0, 0, 0, 0, 0, 0};
+    int refs = 0;
+    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+
+    ~Batch() {
+        keep.release();
+        dens.release();
+        for (auto& e : ev)
+            if (e) cudaEventDestroy(e);
+    }
+
+    dpc_status sync(const char* what) {
+        cudaError_t e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) return cuda_fail(e, what);
+        return DPC_OK;
+    }
+
+    void mark(int i) {
+        if (ctx->profiling) {
+            if (!ev[i]) cudaEventCreate(&ev[i]);
+            cudaEventRecord(ev[i], st);
+        }
+    }
+    float elapsed(int a, int b) {
+        float t = 0.f;
+        if (ctx->profiling && ev[a] && ev[b]) {
+            cudaEventSynchronize(ev[b]);
+            cudaEventElapsedTime(&t, ev[a], ev[b]);
+        }
+        return t;
+    }
+
+    // Reads the device error word (the stream must be synchronized).
+    dpc_status check_err(const char* stage) {
+        unsigned int e = 0;
+        DPC_CK(cudaMemcpy(&e, v.err, sizeof(e), cudaMemcpyDeviceToHost));
+        if (e) return fail(DPC_ERR_CUDA, std::string(stage) + ": internal consistency guard tripped (code " +
+                                             std::to_string(e) + ")");
+        return DPC_OK;
+    }
+
+    dpc_status upload_desc() {
+        DPC_CK(cudaMemcpyAsync(d_desc, hd.data(), sizeof(DsDesc) * B, cudaMemcpyHostToDevice, st));
+        return DPC_OK;
+    }
+
+    // ---------------------------------------------------------- density
+    dpc_status density(const std::vector<Input>& in) {
+        if (!st) st = ctx->stream;
+        keep.st = dens.st = st;
+        B = (int)in.size();
+        hd.assign(B, DsDesc{});
+        h_pt_off.assign(B + 1, 0);
+        int64_t in_total = 0, rec_total = 0;
+        for (int b = 0; b < B; ++b) {
+            DsDesc& ds = hd[b];
+            ds.n = (int32_t)in[b].n;
+            ds.d = in[b].d;
+            ds.dp = ds.d <= 4 ? 1 : 2;
+            ds.d_cut = in[b].d_cut;
+            ds.d_cut2 = in[b].d_cut * in[b].d_cut;
+            ds.pt_off = h_pt_off[b];
+            ds.in_off = in_total;
+            ds.rec_off = rec_total;
+            h_pt_off[b + 1] = h_pt_off[b] + in[b].n;
+            in_total += in[b].n * in[b].d;
+            rec_total += in[b].n * ds.dp;
+        }
+        N = h_pt_off[B];
+        if (N >= (1ll << 31)) return fail(DPC_ERR_INVALID_ARG, "batch holds 2^31 points or more");
+        out_is_device = B == 1 ? in[0].is_device : 0;
+        mark(0);
+
+        // device copies of the inputs (a single device input is used in place)
+        int64_t* d_pt_off = nullptr;
+        DPC_CK(keep.get(&d_desc, B));
+        DPC_CK(keep.get(&d_pt_off, B + 1));
+        DPC_CK(cudaMemcpyAsync(d_pt_off, h_pt_off.data(), sizeof(int64_t) * (B + 1), cudaMemcpyHostToDevice, st));
+        const int32_t* d_in = nullptr;
+        if (B == 1 && in[0].is_device) {
+            d_in = in[0].pts;
+        } else {
+            int32_t* buf = nullptr;
+            DPC_CK(dens.get(&buf, (size_t)in_total));
+            for (int b = 0; b < B; ++b)
+                if (in[b].n > 0)
+                    DPC_CK(cudaMemcpyAsync(buf + hd[b].in_off, in[b].pts, sizeof(int32_t) * in[b].n * in[b].d,
+                                           in[b].is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
+            d_in = buf;
+        }
+        v.B = B;
+        v.N = N;
+        v.desc = d_desc;
+        v.pt_off = d_pt_off;
+        v.in = d_in;
+
+        // bounding boxes -> grid plan
+        int32_t* d_mm = nullptr;
+        DPC_CK(dens.get(&d_mm, (size_t)B * kMaxDims * 2));
+        DPC_TRY(upload_desc());
+        DPC_CK(launch_minmax(v, d_mm, st));
+        std::vector<int32_t> mm((size_t)B * kMaxDims * 2);
+        DPC_CK(cudaMemcpyAsync(mm.data(), d_mm, mm.size() * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+        DPC_TRY(sync("bounding boxes"));
+        uint64_t cbase = 0;
+        int64_t leaf_slots = 0;
+        h_slot_off.assign(B + 1, 0);
+        for (int b = 0; b < B; ++b) {
+            DsDesc& ds = hd[b];
+            for (int k = 0; k < ds.d && ds.n > 0; ++k) {
+                const int32_t lo = mm[(b * kMaxDims + k) * 2], hi = mm[(b * kMaxDims + k) * 2 + 1];
+                if (lo < 0 || (int64_t)hi >= kCoordLimit)
+                    return fail(DPC_ERR_INVALID_ARG, "coordinates must lie in [0, 2^30)");
+            }
+            DPC_TRY(plan(b, mm.data() + (size_t)b * kMaxDims * 2, cbase));
+            ds.nleaf = (int32_t)((ds.n + kLeaf - 1) / kLeaf);
+            ds.h = ceil_log2((uint64_t)std::max<int32_t>(ds.nleaf, 1));
+            h_slot_off[b] = leaf_slots;
+            ds.leaf_off = leaf_slots;
+            ds.node_off = 2 * leaf_slots;
+            leaf_slots += 1ll << ds.h;
+            class_mask |= 1u << (2 * (ds.d - 1) + (ds.w32 ? 0 : 1));
+            dim_mask |= 1u << (ds.d - 1);
+        }
+        h_slot_off[B] = leaf_slots;
+        DPC_TRY(upload_desc());
+        const int key_bits = bits_for(cbase > 0 ? cbase - 1 : 0);
+        const bool key32 = key_bits <= 32;
+
+        // persistent per-point state
+        DPC_CK(keep.get(&v.rec, (size_t)std::max<int64_t>(rec_total, 1)));
+        DPC_CK(keep.get(&v.perm, N));
+        DPC_CK(keep.get(&v.pos_of, N));
+        DPC_CK(keep.get(&v.rho, N));
+        DPC_CK(keep.get(&v.rho_s, N));
+        DPC_CK(keep.get(&v.key, N));
+        DPC_CK(keep.get(&v.ncells, 1));
+        DPC_CK(keep.get(&v.err, 1));
+        DPC_CK(cudaMemsetAsync(v.err, 0, sizeof(unsigned int), st));
+        DPC_CK(keep.get(&d_stats, 4));
+        DPC_CK(keep.get(&d_counters, 32));
+        DPC_CK(cudaMemsetAsync(d_stats, 0, 4 * sizeof(unsigned long long), st));
+
+        // cell keys, sort, cells
+        const size_t kb = key32 ? 4 : 8;
+        void *k0 = nullptr, *k1 = nullptr, *k2 = nullptr;
+        uint32_t *v0 = nullptr, *v1 = nullptr, *flag = nullptr, *cidx = nullptr;
+        DPC_CK(dens.get(&k0, kb * N));
+        DPC_CK(dens.get(&k1, kb * N));
+        DPC_CK(dens.get(&k2, kb * N));
+        DPC_CK(dens.get(&v0, N));
+        DPC_CK(dens.get(&v1, N));
+        DPC_CK(dens.get(&flag, N));
+        DPC_CK(dens.get(&cidx, N));
+        void* temp = nullptr;
+        const size_t temp_bytes = std::max(radix_sort_temp_bytes(N), scan_temp_bytes(N));
+        DPC_CK(dens.get(&temp, temp_bytes));
+        DPC_CK(keep.get(&v.cell_start, N + 1));
+        DPC_CK(launch_cell_keys(v, key32, k0, v0, st));
+        if (key32)
+            DPC_CK(radix_sort_u32((uint32_t*)k0, v0, (uint32_t*)k2, v.perm, (uint32_t*)k1, v1, N, key_bits, temp, st));
+        else
+            DPC_CK(radix_sort_u64((uint64_t*)k0, v0, (uint64_t*)k2, v.perm, (uint64_t*)k1, v1, N, key_bits, temp, st));
+        DPC_CK(launch_gather_cells(v, key32, k2, flag, cidx, temp, st));
+        uint32_t nc = 0;
+        if (N > 0) {
+            DPC_CK(cudaMemcpyAsync(&nc, v.ncells, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
+            DPC_TRY(sync("cell count"));
+        }
+        ncells = nc;
+
+        // hash table of the non-empty cells (load factor <= 1/2)
+        const int hbits = ceil_log2((uint64_t)std::max<int64_t>(2 * ncells, 2));
+        DPC_CK(keep.get(&v.hash, (size_t)1 << hbits));
+        v.hmask = (1ull << hbits) - 1;
+        DPC_CK(cudaMemsetAsync(v.hash, 0xff, sizeof(int4) << hbits, st));
+        DPC_CK(launch_hash_insert(v, ncells, st));
+
+        // dense / sparse cells and the dense work items
+        CellPrepBufs cb{};
+        cb.dflag = flag;
+        cb.sflag = cidx;
+        cb.stats = d_stats;
+        DPC_CK(dens.get(&cb.didx, ncells + 1));
+        DPC_CK(dens.get(&cb.sidx, ncells + 1));
+        DPC_CK(keep.get(&cb.dense, ncells + 1));
+        DPC_CK(keep.get(&cb.sparse, ncells + 1));
+        DPC_CK(keep.get(&cb.ndense, 1));
+        DPC_CK(keep.get(&cb.nsparse, 1));
+        DPC_CK(keep.get(&cb.nitems, 1));
+        DPC_CK(launch_classify_cells(v, cb, ncells, temp, st));
+        uint32_t cnts[2] = {0, 0};
+        if (ncells > 0) {
+            DPC_CK(cudaMemcpyAsync(&cnts[0], cb.ndense, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
+            DPC_CK(cudaMemcpyAsync(&cnts[1], cb.nsparse, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
+            DPC_TRY(sync("cell classes"));
+        }
+        ndense = cnts[0];
+        nsparse = cnts[1];
+        DPC_CK(keep.get(&cb.runs, (size_t)std::max<int64_t>(ndense, 1) * kMaxNb));
+        DPC_CK(keep.get(&cb.nruns, ndense + 1));
+        DPC_CK(keep.get(&cb.cand, ndense + 1));
+        DPC_CK(dens.get(&cb.nitem_c, ndense + 1));
+        DPC_CK(dens.get(&cb.item_off, ndense + 1));
+        DPC_CK(launch_dense_prep(v, cb, ndense, ctx->tune.kch, temp, st));
+        uint32_t ni = 0;
+        if (ndense > 0) {
+            DPC_CK(cudaMemcpyAsync(&ni, cb.nitems, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
+            DPC_TRY(sync("work items"));
+        } else {
+            DPC_CK(cudaMemsetAsync(cb.nitems, 0, sizeof(uint32_t), st));
+        }
+        nitems = ni;
+        DPC_CK(keep.get(&cb.items, nitems + 1));
+        DPC_CK(launch_fill_items(v, cb, ndense, ctx->tune.kch, st));
+        w.dense = cb.dense;
+        w.ndense = cb.ndense;
+        w.sparse = cb.sparse;
+        w.nsparse = cb.nsparse;
+        w.runs = cb.runs;
+        w.nruns = cb.nruns;
+        w.cand = cb.cand;
+        w.items = cb.items;
+        w.nitems = cb.nitems;
+        w.kch = ctx->tune.kch;
+        w.stats = d_stats;
+        mark(1);
+
+        // local density
+        DPC_CK(cudaMemsetAsync(v.rho_s, 0, sizeof(int32_t) * std::max<int64_t>(N, 1), st));
+        DPC_CK(cudaMemsetAsync(d_counters, 0, 32 * sizeof(uint32_t), st));
+        DPC_CK(launch_rho(v, w, class_mask, nitems, nsparse, d_counters, st));
+        mark(2);
+        DPC_CK(launch_rho_scatter(v, st));
+        unsigned long long pairs[2] = {0, 0};
+        DPC_CK(cudaMemcpyAsync(pairs, d_stats, sizeof(pairs), cudaMemcpyDeviceToHost, st));
+        DPC_TRY(sync("density"));
+        cand_pairs = (int64_t)(pairs[0] + pairs[1]);
+        DPC_TRY(check_err("density"));
+        ms[0] = elapsed(0, 1);
+        ms[1] = elapsed(1, 2);
+        dens.release();
+        has_density = true;
+        return DPC_OK;
+    }
+
+    // Grid plan of dataset b from its bounding box mm[2 * dim + {0, 1}].
+    dpc_status plan(int b, const int32_t* mm, uint64_t& cbase) {
+        DsDesc& ds = hd[b];
+        const Tune& tn = ctx->tune;
+        ds.s = ds.d_cut;  // cell side d_cut: neighbours are within one cell
+        ds.R = 1;
+        // grid the dims with the most cells (a dim with one cell filters nothing)
+        struct Dim {
+            int dim;
+            int64_t ext;
+        };
+        std::vector<Dim> dims;
+        for (int k = 0; k < ds.d; ++k) {
+            const int64_t lo = ds.n > 0 ? mm[2 * k] : 0, hi = ds.n > 0 ? mm[2 * k + 1] : 0;
+            const int64_t ext = (hi - lo) / ds.s + 1;
+            if (ext > 1) dims.push_back({k, ext});
+        }
+        std::stable_sort(dims.begin(), dims.end(), [](const Dim& a, const Dim& c) { return a.ext > c.ext; });
+        int k = std::min<int>((int)dims.size(), std::min(tn.kmax, kMaxGridDims));
+        int mbits = 0;
+        auto mb = [&](int kk) {
+            int m = 0;
+            for (int j = 0; j < kk; ++j) m = std::max(m, ceil_log2((uint64_t)dims[j].ext));
+            return m;
+        };
+        mbits = mb(k);
+        while (k > 0 && k * mbits > 40) {
+            --k;
+            mbits = mb(k);
+        }
+        ds.k = k;
+        ds.mbits = mbits;
+        for (int j = 0; j < kMaxGridDims; ++j) {
+            ds.gdim[j] = j < k ? dims[j].dim : 0;
+            ds.origin[j] = j < k ? mm[2 * dims[j].dim] : 0;
+            ds.ext[j] = j < k ? (int32_t)dims[j].ext : 1;
+        }
+        ds.cbase = cbase;
+        cbase += 1ull << (k * mbits);
+        // 32-bit pair arithmetic when the largest possible candidate sum fits
+        int64_t maxsum = 0;
+        for (int c = 0; c < ds.d; ++c) {
+            int64_t md = 0;
+            bool gridded = false;
+            for (int j = 0; j < k; ++j) gridded |= ds.gdim[j] == c;
+            if (ds.n > 0) md = (int64_t)mm[2 * c + 1] - mm[2 * c];
+            if (gridded) md = std::min<int64_t>(md, (int64_t)(ds.R + 1) * ds.s - 1);
+            maxsum += md * md;
+            if (maxsum >= (1ll << 31)) break;
+        }
+        ds.w32 = (maxsum < (1ll << 31) && ds.d_cut2 <= (1ll << 31)) ? 1 : 0;
+        ds.rbits = bits_for((uint64_t)ds.n);
+        return DPC_OK;
+    }
+
+    // -------------------------------------------------------- dependent
+    dpc_status dependent() {
+        if (has_dep) return DPC_OK;
+        if (!has_density) return fail(DPC_ERR_STATE, "dataset has no density");
+        mark(0);
+        Arena tmp;
+        tmp.st = st;
+        DPC_CK(keep.get(&v.rank, N));
+        DPC_CK(keep.get(&v.order, N));
+        DPC_CK(keep.get(&v.ro_s, N));
+        DPC_CK(keep.get(&v.dep, N));
+        DPC_CK(keep.get(&v.delta2, N));
+        int rbits = 1;
+        for (int b = 0; b < B; ++b) rbits = std::max(rbits, hd[b].rbits);
+        int bbits = ceil_log2((uint64_t)B);
+        const size_t kb = (bbits + rbits) > 32 ? 8 : 4;
+        void* temp = nullptr;
+        DPC_CK(tmp.get(&temp, std::max(radix_sort_temp_bytes(N), scan_temp_bytes(N))));
+        DPC_CK(tmp.get(&db.rkeys, 3 * a256(kb * N) / 4 + 64));
+        DPC_CK(tmp.get(&db.rvals, 2 * (N + 64)));
+        DPC_CK(launch_rank(v, db, rbits, temp, st));
+        mark(1);
+
+        DPC_CK(tmp.get(&v.best_s, N));
+        DPC_CK(cudaMemsetAsync(v.best_s, 0xff, sizeof(unsigned long long) * std::max<int64_t>(N, 1), st));
+        DPC_CK(launch_ring(v, w, class_mask, nitems, nsparse, d_counters + 16, st));
+        mark(2);
+
+        DPC_CK(tmp.get(&db.ucount, 2));
+        DPC_CK(tmp.get(&db.tree_list, N));
+        DPC_CK(tmp.get(&db.bf_list, N));
+        DPC_CK(cudaMemsetAsync(db.ucount, 0, 2 * sizeof(uint32_t), st));
+        db.bf_rank = ctx->tune.bf_rank;
+        DPC_CK(launch_finalize(v, db, st));
+        uint32_t uc[2] = {0, 0};
+        DPC_CK(cudaMemcpyAsync(uc, db.ucount, sizeof(uc), cudaMemcpyDeviceToHost, st));
+        DPC_TRY(sync("ring search"));
+        ntree = uc[0];
+        nbf = uc[1];
+        if (ntree > 0) {
+            int64_t* d_slot = nullptr;
+            DPC_CK(tmp.get(&d_slot, B + 1));
+            DPC_CK(cudaMemcpyAsync(d_slot, h_slot_off.data(), sizeof(int64_t) * (B + 1), cudaMemcpyHostToDevice, st));
+            db.slot_off = d_slot;
+            db.leaf_slots = h_slot_off[B];
+            db.nodes = 2 * db.leaf_slots;
+            DPC_CK(tmp.get(&db.node_box, (size_t)db.nodes * 4));
+            DPC_CK(tmp.get(&db.node_minrank, db.nodes));
+            DPC_CK(tmp.get(&db.node_flag, db.nodes));
+            DPC_CK(cudaMemsetAsync(db.node_flag, 0, sizeof(uint32_t) * db.nodes, st));
+            DPC_CK(launch_tree_build(v, db, st));
+            DPC_CK(launch_tree_search(v, db, dim_mask, ntree, st));
+        }
+        if (nbf > 0) {
+            DPC_CK(tmp.get(&db.bf_keys, 3 * nbf));
+            DPC_CK(tmp.get(&db.bf_sorted, 2 * nbf));
+            DPC_CK(tmp.get(&db.rrec, 2 * N));
+            DPC_CK(tmp.get(&db.rorig, N));
+            void* t2 = nullptr;
+            DPC_CK(tmp.get(&t2, std::max(radix_sort_temp_bytes(nbf), scan_temp_bytes(nbf))));
+            DPC_CK(launch_bruteforce(v, db, dim_mask, nbf, t2, st));
+        }
+        mark(3);
+        DPC_TRY(sync("dependent points"));
+        DPC_TRY(check_err("dependent points"));
+        ms[2] = elapsed(0, 1);
+        ms[3] = elapsed(1, 2);
+        ms[4] = elapsed(2, 3);
+        tmp.release();
+        has_dep = true;
+        return DPC_OK;
+    }
+
+    // ------------------------------------------------------------ label
+    dpc_status label(const int64_t* rho_min, const int64_t* delta_min) {
+        DPC_TRY(dependent());
+        if (!v.parent) {
+            DPC_CK(keep.get(&v.parent, N));
+            DPC_CK(keep.get(&v.label, N));
+            DPC_CK(keep.get(&v.ncent, B));
+        }
+        for (int b = 0; b < B; ++b) {
+            hd[b].rho_min = rho_min[b];
+            hd[b].delta_min2 = delta_min[b] * delta_min[b];
+        }
+        DPC_TRY(upload_desc());
+        mark(0);
+        DPC_CK(launch_labels(v, st));
+        mark(1);
+        return DPC_OK;
+    }
+
+    dpc_status copy_out(void* dst, const void* src, size_t bytes) {
+        if (dst && bytes) DPC_CK(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDefault, st));
+        return DPC_OK;
+    }
+};
+
+}  // namespace
+}  // namespace dpc
+
+struct dpc_ds {
+    std::shared_ptr<dpc::Batch> batch;
+    int b = 0;
+};
+
+using dpc::Batch;
+using dpc::fail;
+using dpc::cuda_fail;
+
+extern "C" {
+
+const char* dpc_last_error(void) { return dpc::g_err.c_str(); }
+
+int64_t dpc_kernel_launches(void) { return (int64_t)dpc::launch_count(); }
+
+dpc_status dpc_create(const dpc_options* opt, dpc_ctx** out) {
+    if (!out) return fail(DPC_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    dpc_options o{};
+    if (opt) o = *opt;
+    int ndev = 0;
+    cudaError_t e = cudaGetDeviceCount(&ndev);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDeviceCount");
+    if (o.device < 0 || o.device >= ndev) return fail(DPC_ERR_INVALID_ARG, "no such device");
+    if (o.mode != 0 && o.mode != 1) return fail(DPC_ERR_INVALID_ARG, "mode must be 0 or 1");
+    e = cudaSetDevice(o.device);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaSetDevice");
+    auto* c = new dpc_ctx();
+    c->device = o.device;
+    c->debug = o.debug_checks;
+    c->mode = o.mode;
+    c->cap = o.hbm_cap_bytes ? o.hbm_cap_bytes : dpc::kDefaultCap;
+    c->max_inflight = o.max_inflight > 0 ? o.max_inflight : 4;
+    if (o.cuda_stream) {
+        c->stream = (cudaStream_t)o.cuda_stream;
+    } else {
+        e = cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking);
+        if (e != cudaSuccess) {
+            delete c;
+            return cuda_fail(e, "cudaStreamCreate");
+        }
+        c->own_stream = true;
+    }
+    // keep freed blocks in the device's pool so repeated calls do not go back
+    // to the driver
+    cudaMemPool_t pool;
+    if (cudaDeviceGetDefaultMemPool(&pool, o.device) == cudaSuccess) {
+        uint64_t thr = UINT64_MAX;
+        cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+    }
+    *out = c;
+    return DPC_OK;
+}
+
+dpc_status dpc_set_profiling(dpc_ctx* ctx, int on) {
+    if (!ctx) return fail(DPC_ERR_INVALID_ARG, "ctx is NULL");
+    ctx->profiling = on ? 1 : 0;
+    return DPC_OK;
+}
+
+static dpc_status check_input(const int32_t* points, int64_t n, int32_t d, int64_t d_cut) {
+    if (n < 0 || n >= (1ll << 31)) return fail(DPC_ERR_INVALID_ARG, "n must be in [0, 2^31)");
+    if (d < 1 || d > 8) return fail(DPC_ERR_INVALID_ARG, "d must be in [1, 8]");
+    if (d_cut < 1 || d_cut >= (1ll << 31)) return fail(DPC_ERR_INVALID_ARG, "d_cut must be in [1, 2^31)");
+    if (n > 0 && !points) return fail(DPC_ERR_INVALID_ARG, "points is NULL");
+    return DPC_OK;
+}
+
+dpc_status dpc_density(dpc_ctx* ctx, const int32_t* points, int64_t n, int32_t d, int64_t d_cut, int is_device,
+                       dpc_ds** out, int32_t* rho_out) {
+    if (!ctx || !out) return fail(DPC_ERR_INVALID_ARG, "ctx or out is NULL");
+    *out = nullptr;
+    DPC_TRY(check_input(points, n, d, d_cut));
+    cudaError_t e = cudaSetDevice(ctx->device);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaSetDevice");
+    auto b = std::make_shared<Batch>();
+    b->ctx = ctx;
+    std::vector<dpc::Input> in{{points, n, d, d_cut, is_device}};
+    DPC_TRY(b->density(in));
+    if (rho_out) {
+        DPC_TRY(b->copy_out(rho_out, b->v.rho, sizeof(int32_t) * n));
+        DPC_TRY(b->sync("copy rho"));
+    }
+    auto* ds = new dpc_ds();
+    ds->batch = b;
+    ds->b = 0;
+    b->refs = 1;
+    *out = ds;
+    return DPC_OK;
+}
+
+dpc_status dpc_dependent(dpc_ds* ds, int32_t* dep_out, int64_t* delta2_out) {
+    if (!ds || !ds->batch) return fail(DPC_ERR_STATE, "invalid dataset handle");
+    Batch& bt = *ds->batch;
+    cudaSetDevice(bt.ctx->device);
+    DPC_TRY(bt.dependent());
+    const dpc::DsDesc& h = bt.hd[ds->b];
+    DPC_TRY(bt.copy_out(dep_out, bt.v.dep + h.pt_off, sizeof(int32_t) * h.n));
+    DPC_TRY(bt.copy_out(delta2_out, bt.v.delta2 + h.pt_off, sizeof(int64_t) * h.n));
+    return bt.sync("copy dependent");
+}
+
+dpc_status dpc_label(dpc_ds* ds, int64_t rho_min, int64_t delta_min, int32_t* label_out, int64_t* n_centers) {
+    if (!ds || !ds->batch) return fail(DPC_ERR_STATE, "invalid dataset handle");
+    Batch& bt = *ds->batch;
+    const dpc::DsDesc& h = bt.hd[ds->b];
+    if (delta_min <= h.d_cut || delta_min > dpc::kMaxDeltaMin)
+        return fail(DPC_ERR_INVALID_ARG, "delta_min must be in (d_cut, 3037000499]");
+    cudaSetDevice(bt.ctx->device);
+    std::vector<int64_t> rmin(bt.B, rho_min), dmin(bt.B, delta_min);
+    DPC_TRY(bt.label(rmin.data(), dmin.data()));
+    DPC_TRY(bt.copy_out(label_out, bt.v.label + h.pt_off, sizeof(int32_t) * h.n));
+    unsigned long long nc = 0;
+    if (n_centers) DPC_TRY(bt.copy_out(&nc, bt.v.ncent + ds->b, sizeof(nc)));
+    DPC_TRY(bt.sync("labels"));
+    DPC_TRY(bt.check_err("labels"));
+    bt.ms[5] = bt.elapsed(0, 1);
+    if (n_centers) *n_centers = (int64_t)nc;
+    return DPC_OK;
+}
+
+dpc_status dpc_release(dpc_ds* ds) {
+    if (!ds) return fail(DPC_ERR_STATE, "invalid dataset handle");
+    if (ds->batch) {
+        cudaSetDevice(ds->batch->ctx->device);
+        cudaStreamSynchronize(ds->batch->st);
+    }
+    delete ds;
+    return DPC_OK;
+}
+
+dpc_status dpc_ds_info(const dpc_ds* ds, dpc_info* out) {
+    if (!ds || !ds->batch || !out) return fail(DPC_ERR_INVALID_ARG, "NULL argument");
+    const Batch& bt = *ds->batch;
+    std::memset(out, 0, sizeof(*out));
+    const dpc::DsDesc& h = bt.hd[ds->b];
+    out->n = h.n;
+    out->cells = bt.ncells;
+    out->dense_cells = bt.ndense;
+    out->work_items = bt.nitems;
+    out->open_after_ring = bt.ntree + bt.nbf;
+    out->brute_points = bt.nbf;
+    out->grid_dims = h.k;
+    out->pair_bits = h.w32 ? 32 : 64;
+    out->ms_grid = bt.ms[0];
+    out->ms_rho = bt.ms[1];
+    out->ms_rank = bt.ms[2];
+    out->ms_ring = bt.ms[3];
+    out->ms_rest = bt.ms[4];
+    out->ms_label = bt.ms[5];
+    out->cand_pairs = bt.cand_pairs;
+    return DPC_OK;
+}
+
+}  // extern "C"
+
+// ------------------------------------------------------------------ jobs
+
+namespace dpc {
+namespace {
+
+using JobPtr = std::shared_ptr<dpc_ctx::JobRec>;
+
+// Device bytes one job holds while it runs (points, sorted records, per-point
+// state, sort buffers, hash table), with slack.
+uint64_t job_bytes(int64_t n, int32_t d) {
+    return (uint64_t)n * (176 + 8 * (uint64_t)d) + (16ull << 20);
+}
+
+// Run a group of jobs as one batch on stream st; fills their outputs.
+dpc_status run_jobs(dpc_ctx* ctx, std::vector<JobPtr>& jobs, cudaStream_t st) {
+    auto bt = std::make_shared<Batch>();
+    bt->ctx = ctx;
+    bt->st = st;
+    std::vector<Input> in;
+    int maxq = 0;
+    for (auto& j : jobs) {
+        in.push_back({j->job.points, j->job.n, j->job.d, j->job.d_cut, 0});
+        maxq = std::max(maxq, j->job.n_queries);
+    }
+    DPC_TRY(bt->density(in));
+    DPC_TRY(bt->dependent());
+    for (size_t b = 0; b < jobs.size(); ++b) {
+        const dpc_job& jb = jobs[b]->job;
+        const DsDesc& h = bt->hd[b];
+        DPC_TRY(bt->copy_out(jb.rho_out, bt->v.rho + h.pt_off, sizeof(int32_t) * h.n));
+        DPC_TRY(bt->copy_out(jb.dep_out, bt->v.dep + h.pt_off, sizeof(int32_t) * h.n));
+        DPC_TRY(bt->copy_out(jb.delta2_out, bt->v.delta2 + h.pt_off, sizeof(int64_t) * h.n));
+    }
+    std::vector<int64_t> rmin(jobs.size()), dmin(jobs.size());
+    std::vector<unsigned long long> nc(jobs.size());
+    for (int q = 0; q < maxq; ++q) {
+        for (size_t b = 0; b < jobs.size(); ++b) {
+            const int qq = std::min(q, jobs[b]->job.n_queries - 1);
+            rmin[b] = jobs[b]->rmin[qq];
+            dmin[b] = jobs[b]->dmin[qq];
+        }
+        DPC_TRY(bt->label(rmin.data(), dmin.data()));
+        DPC_TRY(bt->copy_out(nc.data(), bt->v.ncent, sizeof(unsigned long long) * jobs.size()));
+        for (size_t b = 0; b < jobs.size(); ++b) {
+            const dpc_job& jb = jobs[b]->job;
+            if (q >= jb.n_queries || !jb.label_out) continue;
+            const DsDesc& h = bt->hd[b];
+            DPC_TRY(bt->copy_out(jb.label_out + (int64_t)q * h.n, bt->v.label + h.pt_off, sizeof(int32_t) * h.n));
+        }
+        DPC_TRY(bt->sync("labels"));
+        DPC_TRY(bt->check_err("labels"));
+        for (size_t b = 0; b < jobs.size(); ++b)
+            if (q < jobs[b]->job.n_queries && jobs[b]->job.n_centers_out)
+                jobs[b]->job.n_centers_out[q] = (int64_t)nc[b];
+    }
+    return DPC_OK;
+}
+
+void finish(dpc_ctx* ctx, std::vector<JobPtr>& group, dpc_status s) {
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    const auto now = std::chrono::steady_clock::now();
+    for (auto& j : group) {
+        j->status = s;
+        j->t_done = now;
+        ctx->held_bytes -= j->bytes;
+    }
+    ctx->cv.notify_all();
+}
+
+// Served mode: each worker owns a stream and admits the jobs waiting at the
+// head of the queue while they fit the memory cap, runs them as one batch,
+// and goes back for more. With several workers, a batch is admitted and
+// launched while earlier batches are still running on the device.
+void serve_loop(dpc_ctx* ctx) {
+    cudaSetDevice(ctx->device);
+    cudaStream_t st = nullptr;
+    cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+    while (true) {
+        std::vector<JobPtr> group;
+        {
+            std::unique_lock<std::mutex> lk(ctx->mu);
+            ctx->cv.wait(lk, [&] {
+                if (ctx->stop) return true;
+                if (ctx->waiting.empty()) return false;
+                auto it = ctx->jobs.find(ctx->waiting.front());
+                return it == ctx->jobs.end() || ctx->held_bytes + it->second->bytes <= ctx->cap;
+            });
+            if (ctx->stop && ctx->waiting.empty()) break;
+            int64_t pts = 0;
+            while (!ctx->waiting.empty() && (int)group.size() < ctx->max_batch_jobs) {
+                auto it = ctx->jobs.find(ctx->waiting.front());
+                if (it == ctx->jobs.end()) {
+                    ctx->waiting.pop_front();
+                    continue;
+                }
+                JobPtr j = it->second;
+                if (ctx->held_bytes + j->bytes > ctx->cap) break;
+                if (pts + j->job.n >= (1ll << 31) - 1) break;
+                ctx->waiting.pop_front();
+                ctx->held_bytes += j->bytes;
+                pts += j->job.n;
+                j->t_admit = std::chrono::steady_clock::now();
+                group.push_back(j);
+            }
+        }
+        if (group.empty()) continue;
+        dpc_status s = run_jobs(ctx, group, st);
+        finish(ctx, group, s);
+    }
+    cudaStreamDestroy(st);
+}
+
+dpc_status check_job(const dpc_job* j) {
+    if (!j) return fail(DPC_ERR_INVALID_ARG, "job is NULL");
+    if (j->n < 0 || j->n >= (1ll << 31)) return fail(DPC_ERR_INVALID_ARG, "n must be in [0, 2^31)");
+    if (j->d < 1 || j->d > 8) return fail(DPC_ERR_INVALID_ARG, "d must be in [1, 8]");
+    if (j->d_cut < 1 || j->d_cut >= (1ll << 31)) return fail(DPC_ERR_INVALID_ARG, "d_cut must be in [1, 2^31)");
+    if (j->n > 0 && !j->points) return fail(DPC_ERR_INVALID_ARG, "points is NULL");
+    if (j->n_queries < 1 || !j->rho_min || !j->delta_min)
+        return fail(DPC_ERR_INVALID_ARG, "a job needs at least one (rho_min, delta_min) query");
+    for (int q = 0; q < j->n_queries; ++q)
+        if (j->delta_min[q] <= j->d_cut || j->delta_min[q] > kMaxDeltaMin)
+            return fail(DPC_ERR_INVALID_ARG, "delta_min must be in (d_cut, 3037000499]");
+    return DPC_OK;
+}
+
+}  // namespace
+}  // namespace dpc
+
+extern "C" {
+
+dpc_status dpc_submit(dpc_ctx* ctx, const dpc_job* job, uint64_t* ticket) {
+    if (!ctx || !ticket) return fail(DPC_ERR_INVALID_ARG, "ctx or ticket is NULL");
+    DPC_TRY(dpc::check_job(job));
+    auto rec = std::make_shared<dpc_ctx::JobRec>();
+    rec->job = *job;
+    rec->rmin.assign(job->rho_min, job->rho_min + job->n_queries);
+    rec->dmin.assign(job->delta_min, job->delta_min + job->n_queries);
+    rec->bytes = dpc::job_bytes(job->n, job->d);
+    rec->t_submit = std::chrono::steady_clock::now();
+    if (ctx->mode == 1 && rec->bytes > ctx->cap) return fail(DPC_ERR_CAPACITY, "job exceeds the memory cap");
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    if (ctx->mode == 1 && ctx->workers.empty()) {
+        for (int i = 0; i < ctx->max_inflight; ++i) ctx->workers.emplace_back(dpc::serve_loop, ctx);
+    }
+    const uint64_t t = ctx->next_ticket++;
+    ctx->jobs[t] = rec;
+    ctx->waiting.push_back(t);
+    *ticket = t;
+    ctx->cv.notify_all();
+    return DPC_OK;
+}
+
+static void fill_result(const dpc_ctx::JobRec& j, dpc_result* out) {
+    if (!out) return;
+    out->status = j.status;
+    out->queue_ms = std::chrono::duration<double, std::milli>(j.t_admit - j.t_submit).count();
+    out->run_ms = std::chrono::duration<double, std::milli>(j.t_done - j.t_admit).count();
+}
+
+dpc_status dpc_poll(dpc_ctx* ctx, uint64_t ticket, dpc_result* out) {
+    if (!ctx) return fail(DPC_ERR_INVALID_ARG, "ctx is NULL");
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    auto it = ctx->jobs.find(ticket);
+    if (it == ctx->jobs.end()) return fail(DPC_ERR_STATE, "unknown ticket");
+    if (it->second->status == DPC_PENDING) {
+        if (out) out->status = DPC_PENDING;
+        return DPC_PENDING;
+    }
+    fill_result(*it->second, out);
+    const dpc_status s = it->second->status;
+    ctx->jobs.erase(it);
+    return s;
+}
+
+dpc_status dpc_wait(dpc_ctx* ctx, uint64_t ticket, int64_t timeout_ms, dpc_result* out) {
+    if (!ctx) return fail(DPC_ERR_INVALID_ARG, "ctx is NULL");
+    std::unique_lock<std::mutex> lk(ctx->mu);
+    auto it = ctx->jobs.find(ticket);
+    if (it == ctx->jobs.end()) return fail(DPC_ERR_STATE, "unknown ticket");
+    auto rec = it->second;
+    const bool done = ctx->cv.wait_for(lk, std::chrono::milliseconds(timeout_ms < 0 ? 0 : timeout_ms),
+                                       [&] { return rec->status != DPC_PENDING; });
+    if (!done) return fail(DPC_ERR_TIMEOUT, "job not finished within the timeout");
+    fill_result(*rec, out);
+    ctx->jobs.erase(ticket);
+    return rec->status;
+}
+
+dpc_status dpc_flush(dpc_ctx* ctx) {
+    if (!ctx) return fail(DPC_ERR_INVALID_ARG, "ctx is NULL");
+    if (ctx->mode != 0) return fail(DPC_ERR_STATE, "dpc_flush is for batched mode");
+    std::vector<dpc::JobPtr> group;
+    {
+        std::lock_guard<std::mutex> lk(ctx->mu);
+        const auto now = std::chrono::steady_clock::now();
+        while (!ctx->waiting.empty()) {
+            auto it = ctx->jobs.find(ctx->waiting.front());
+            ctx->waiting.pop_front();
+            if (it == ctx->jobs.end()) continue;
+            it->second->t_admit = now;
+            ctx->held_bytes += it->second->bytes;
+            group.push_back(it->second);
+        }
+    }
+    if (group.empty()) return DPC_OK;
+    cudaSetDevice(ctx->device);
+    dpc_status s = dpc::run_jobs(ctx, group, ctx->stream);
+    dpc::finish(ctx, group, s);
+    return s;
+}
+
+dpc_status dpc_destroy(dpc_ctx* ctx) {
+    if (!ctx) return fail(DPC_ERR_INVALID_ARG, "ctx is NULL");
+    {
+        std::lock_guard<std::mutex> lk(ctx->mu);
+        ctx->stop = true;
+        ctx->cv.notify_all();
+    }
+    for (auto& t : ctx->workers) t.join();
+    cudaSetDevice(ctx->device);
+    cudaStreamSynchronize(ctx->stream);
+    if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
+    delete ctx;
+    return DPC_OK;
+}
+
+}  // extern "C"

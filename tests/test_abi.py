@@ -1,0 +1,59 @@
+"""The C ABI library builds, loads and exports every declared entry point
+(no GPU needed: nothing here launches a kernel)."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADERS = [os.path.join(ROOT, "include", f) for f in sorted(os.listdir(os.path.join(ROOT, "include")))
+           if f.endswith(".h")]
+
+
+def _declared():
+    names = []
+    for h in HEADERS:
+        text = open(h).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        names += re.findall(r"^\s*(?:dpc_status|int64_t|const\s+char\s*\*)\s*(dpc_\w+)\s*\(", text, flags=re.M)
+    return sorted(set(names))
+
+
+def test_header_declares_the_entry_points():
+    names = _declared()
+    for need in ["dpc_create", "dpc_destroy", "dpc_density", "dpc_dependent", "dpc_label", "dpc_release",
+                 "dpc_submit", "dpc_poll", "dpc_last_error"]:
+        assert need in names
+
+
+def test_library_exports_every_declared_symbol():
+    import paper_2207_04649_gb300 as dpc
+    lib = ctypes.CDLL(dpc.library_path() if os.path.exists(dpc.library_path()) else dpc.lib()._name)
+    missing = [n for n in _declared() if not hasattr(lib, n)]
+    assert not missing, f"not exported: {missing}"
+
+
+def test_null_handles_are_rejected_without_a_device():
+    import paper_2207_04649_gb300 as dpc
+    L = dpc.lib()
+    h = ctypes.c_void_p()
+    pts = np.zeros((4, 2), np.int32)
+    s = L.dpc_density(None, pts.ctypes.data_as(ctypes.c_void_p), 4, 2, 10, 0, ctypes.byref(h), None)
+    assert s == dpc.DPC_ERR_INVALID_ARG
+    assert "NULL" in dpc.dpc_last_error()
+    assert L.dpc_dependent(None, None, None) == dpc.DPC_ERR_STATE
+    assert L.dpc_label(None, 1, 2, None, None) == dpc.DPC_ERR_STATE
+    assert L.dpc_release(None) == dpc.DPC_ERR_STATE
+    assert L.dpc_poll(None, 1, None) == dpc.DPC_ERR_INVALID_ARG
+    assert L.dpc_create(None, None) == dpc.DPC_ERR_INVALID_ARG
+
+
+def test_binding_has_no_cpu_path():
+    """The binding never imports the oracle and has no CPU arithmetic."""
+    pkg = os.path.join(ROOT, "paper_2207_04649_gb300")
+    for f in os.listdir(pkg):
+        if f.endswith(".py"):
+            src = open(os.path.join(pkg, f)).read()
+            assert "oracle" not in src, f
