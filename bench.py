@@ -278,7 +278,8 @@ def run_ours(args):
             "stages_ms": {k: statistics.mean(i[k] for i in infos)
                           for k in ("ms_grid", "ms_rho", "ms_rank", "ms_ring", "ms_rest", "ms_label")},
             "work": {k: infos[-1][k] for k in ("cells", "dense_cells", "work_items", "cand_pairs",
-                                               "open_after_ring", "brute_points", "grid_dims", "pair_bits")},
+                                               "open_after_ring", "brute_points", "grid_dims", "pair_bits",
+                                               "tree_visits", "tree_pairs")},
             "cpu_baseline": cpu,
             "clocks": clk,
             "gpu_launches": launches,

@@ -129,6 +129,8 @@ typedef struct {
     int32_t grid_dims;        /* gridded dimensions */
     int32_t pair_bits;        /* 32 or 64: width of the pair arithmetic */
     float ms_grid, ms_rho, ms_rank, ms_ring, ms_rest, ms_label;  /* stage times when profiling is on */
+    int64_t tree_visits;      /* tree nodes visited by the search for open points */
+    int64_t tree_pairs;       /* point pairs it tested */
 } dpc_info;
 
 dpc_status dpc_ds_info(const dpc_ds* ds, dpc_info* out);

@@ -45,7 +45,8 @@ class DpcInfo(ctypes.Structure):
                 ("open_after_ring", ctypes.c_int64), ("brute_points", ctypes.c_int64),
                 ("grid_dims", ctypes.c_int32), ("pair_bits", ctypes.c_int32),
                 ("ms_grid", ctypes.c_float), ("ms_rho", ctypes.c_float), ("ms_rank", ctypes.c_float),
-                ("ms_ring", ctypes.c_float), ("ms_rest", ctypes.c_float), ("ms_label", ctypes.c_float)]
+                ("ms_ring", ctypes.c_float), ("ms_rest", ctypes.c_float), ("ms_label", ctypes.c_float),
+                ("tree_visits", ctypes.c_int64), ("tree_pairs", ctypes.c_int64)]
 
     def as_dict(self) -> dict:
         return {f: getattr(self, f) for f, _ in self._fields_}

@@ -109,12 +109,15 @@ __global__ void k_ro(BatchView v) {
 
 // ----------------------------------------------------------- ring search
 
-template <int D, bool W64, int Q>
-__device__ __forceinline__ void eval_ring(const int4* buf, const uint2* rbuf, int nb, const int32_t (&qx)[4][D],
-                                          const uint32_t (&qr)[4], unsigned long long (&best)[4]) {
+// Q queries per lane (or one per lane in G groups) against staged
+// candidates grp, grp + G, ...: keeps the least packed key of a higher point.
+template <int D, bool W64, int Q, int G>
+__device__ __forceinline__ void eval_ring(const int4* buf, const uint2* rbuf, int nb, int grp,
+                                          const int32_t (&qx)[4][D], const uint32_t (&qr)[4],
+                                          unsigned long long (&best)[4]) {
     constexpr int DP = D <= 4 ? 1 : 2;
 #pragma unroll 2
-    for (int j = 0; j < nb; ++j) {
+    for (int j = grp; j < nb; j += G) {
         int32_t c[D];
         load_pt<D>(buf + j * DP, c);
         const uint2 ro = rbuf[j];
@@ -151,19 +154,22 @@ __global__ void __launch_bounds__(kThreads) k_ring_dense(BatchView v, CellWork w
         const int4* recb = v.rec + ds.rec_off - ds.pt_off * DP;
         const int q0 = (int)qc * kQch;
         const int nq = min(kQch, (int)m - q0);
-        const int Q = (nq + 31) >> 5;
+        const int Q = nq >= 32 ? (nq + 31) >> 5 : 1;
+        const int Mq = nq >= 32 ? 32 : (nq <= 8 ? 8 : (nq <= 16 ? 16 : 32));
+        const int G = 32 / Mq;
+        const int grp = lane / Mq, ql = lane & (Mq - 1);
         int32_t qx[4][D];
         uint32_t qr[4];
         unsigned long long best[4];
 #pragma unroll
         for (int t = 0; t < 4; ++t) {
-            const int qi = min(lane + 32 * t, nq - 1);
+            const int qi = min(G == 1 ? lane + 32 * t : ql, nq - 1);
             load_pt<D>(recb + ((int64_t)cs + q0 + qi) * DP, qx[t]);
             qr[t] = v.ro_s[cs + q0 + qi].x;
             best[t] = kNoBest;
         }
-        const uint2* runs = w.runs + (int64_t)dc * kMaxNb;
-        const uint32_t nr = w.nruns[dc], ctot = w.cand[dc];
+        const uint2* runs = w.runs + (int64_t)c * w.nbs;
+        const uint32_t nr = w.nruns[c], ctot = w.cand[c];
         const uint32_t k0 = kc * (uint32_t)w.kch;
         uint32_t remaining = min(ctot, k0 + (uint32_t)w.kch) - k0;
         uint32_t ri = 0, roff = k0;
@@ -195,17 +201,27 @@ __global__ void __launch_bounds__(kThreads) k_ring_dense(BatchView v, CellWork w
                 }
             }
             __syncwarp();
-            switch (Q) {
-                case 1: eval_ring<D, W64, 1>(buf, rbuf, nb, qx, qr, best); break;
-                case 2: eval_ring<D, W64, 2>(buf, rbuf, nb, qx, qr, best); break;
-                case 3: eval_ring<D, W64, 3>(buf, rbuf, nb, qx, qr, best); break;
-                default: eval_ring<D, W64, 4>(buf, rbuf, nb, qx, qr, best); break;
+            if (G == 4) eval_ring<D, W64, 1, 4>(buf, rbuf, nb, grp, qx, qr, best);
+            else if (G == 2) eval_ring<D, W64, 1, 2>(buf, rbuf, nb, grp, qx, qr, best);
+            else switch (Q) {
+                case 1: eval_ring<D, W64, 1, 1>(buf, rbuf, nb, 0, qx, qr, best); break;
+                case 2: eval_ring<D, W64, 2, 1>(buf, rbuf, nb, 0, qx, qr, best); break;
+                case 3: eval_ring<D, W64, 3, 1>(buf, rbuf, nb, 0, qx, qr, best); break;
+                default: eval_ring<D, W64, 4, 1>(buf, rbuf, nb, 0, qx, qr, best); break;
             }
             __syncwarp();
         }
+        if (G > 1) {
+            for (int o = Mq; o < 32; o <<= 1) {
+                const unsigned long long y = __shfl_xor_sync(0xffffffffu, best[0], o);
+                if (y < best[0]) best[0] = y;
+            }
+            if (grp == 0 && ql < nq && best[0] != kNoBest) atomicMin(&v.best_s[cs + q0 + ql], best[0]);
+        } else {
 #pragma unroll
-        for (int t = 0; t < 4; ++t)
-            if (lane + 32 * t < nq && best[t] != kNoBest) atomicMin(&v.best_s[cs + q0 + lane + 32 * t], best[t]);
+            for (int t = 0; t < 4; ++t)
+                if (lane + 32 * t < nq && best[t] != kNoBest) atomicMin(&v.best_s[cs + q0 + lane + 32 * t], best[t]);
+        }
     }
 }
 
@@ -230,13 +246,11 @@ __global__ void __launch_bounds__(256) k_ring_sparse(BatchView v, CellWork w) {
             qr[t] = v.ro_s[cs + qi].x;
             best[t] = kNoBest;
         }
-        int32_t cc[kMaxGridDims];
-        for (int j = 0; j < ds.k; ++j) cc[j] = cell_coord(ds, j, rec_coord(recb + (int64_t)cs * DP, ds.gdim[j]));
-        const int nnb = num_neighbours(ds);
-        for (int t = 0; t < nnb; ++t) {
-            int32_t nc[kMaxGridDims];
-            if (!neighbour(ds, cc, t, nc)) continue;
-            const uint2 e = hash_find(v.hash, v.hmask, ds.cbase + morton(nc, ds.k, ds.mbits));
+        const uint2* runs = w.runs + (int64_t)c * w.nbs;
+        const uint32_t nr = w.nruns[c];
+        for (uint32_t r = 0; r < nr; ++r) {
+            const uint2 e = runs[r];
+#pragma unroll 2
             for (uint32_t j = 0; j < e.y; ++j) {
                 int32_t cj[D];
                 load_pt<D>(recb + ((int64_t)e.x + j) * DP, cj);
@@ -256,196 +270,56 @@ __global__ void __launch_bounds__(256) k_ring_sparse(BatchView v, CellWork w) {
 }
 
 // Resolve the points whose ring-search result is provably final; queue the
-// others for the brute-force pass (rank < bf_rank) or the tree search.
+// others, in sorted (Morton) order within each warp, for the brute-force
+// pass (rank < bf_rank) or the tree search.
 __global__ void k_finalize(BatchView v, DeltaBufs db) {
     const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= v.N) return;
-    const int b = find_ds(v.pt_off, v.B, p);
-    const DsDesc& ds = v.desc[b];
-    const uint2 ro = v.ro_s[p];
-    const int64_t g = ds.pt_off + ro.y;
-    if (ro.x == 0u) {  // the densest point: no dependent point, delta = infinity
-        v.dep[g] = -1;
-        v.delta2[g] = INT64_MAX;
-        return;
-    }
-    const unsigned long long bk = v.best_s[p];
-    const uint32_t dd = (uint32_t)(bk >> 32);
-    // distance from the point to the outside of the searched box of cells
-    const int4* r = v.rec + ds.rec_off + (p - ds.pt_off) * ds.dp;
-    int64_t bound = INT64_MAX;
-    for (int j = 0; j < ds.k; ++j) {
-        const int64_t x = rec_coord(r, ds.gdim[j]);
-        const int64_t cj = (x - ds.origin[j]) / ds.s;
-        if (cj - ds.R > 0) bound = min(bound, x - (ds.origin[j] + (cj - ds.R) * ds.s) + 1);
-        if (cj + ds.R + 1 < ds.ext[j]) bound = min(bound, ds.origin[j] + (cj + ds.R + 1) * ds.s - x);
-    }
-    const bool found = bk != kNoBest && dd != kSat;
-    const bool resolved = found && (bound == INT64_MAX || (int64_t)dd < bound * bound);
-    if (resolved) {
-        v.dep[g] = (int32_t)(uint32_t)bk;
-        v.delta2[g] = (int64_t)dd;
-    } else if (ro.x < db.bf_rank) {
-        db.bf_list[atomicAdd(&db.ucount[1], 1u)] = (uint32_t)p;
-    } else {
-        db.tree_list[atomicAdd(&db.ucount[0], 1u)] = (uint32_t)p;
-    }
-}
-
-// ---------------------------------------------------------------- tree
-
-__device__ __forceinline__ int find_slot_ds(const int64_t* slot_off, int B, int64_t s) {
-    int lo = 0, hi = B - 1;
-    while (lo < hi) {
-        int mid = (lo + hi + 1) >> 1;
-        if (slot_off[mid] <= s) lo = mid; else hi = mid - 1;
-    }
-    return lo;
-}
-
-// Leaf boxes and smallest ranks, then a bottom-up refit: the second child
-// to finish computes its parent.
-__global__ void k_tree_build(BatchView v, DeltaBufs db) {
-    const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (s >= db.leaf_slots) return;
-    const int b = find_slot_ds(db.slot_off, v.B, s);
-    const DsDesc& ds = v.desc[b];
-    const int64_t leaf = s - db.slot_off[b];
-    int64_t node = (1ll << ds.h) + leaf;
-    int32_t lo[8], hi[8];
-#pragma unroll
-    for (int k = 0; k < 8; ++k) {
-        lo[k] = INT32_MAX;
-        hi[k] = INT32_MIN;
-    }
-    uint32_t mr = 0xffffffffu;
-    const int64_t p0 = ds.pt_off + leaf * kLeaf;
-    const int64_t p1 = min(p0 + kLeaf, ds.pt_off + (int64_t)ds.n);
-    for (int64_t p = p0; p < p1; ++p) {
-        const int4* r = v.rec + ds.rec_off + (p - ds.pt_off) * ds.dp;
-        const int4 a = r[0];
-        const int4 c = ds.dp == 2 ? r[1] : make_int4(0, 0, 0, 0);
-        const int32_t x[8] = {a.x, a.y, a.z, a.w, c.x, c.y, c.z, c.w};
-#pragma unroll
-        for (int k = 0; k < 8; ++k) {
-            lo[k] = min(lo[k], x[k]);
-            hi[k] = max(hi[k], x[k]);
-        }
-        mr = min(mr, v.ro_s[p].x);
-    }
-    int4* nb = db.node_box + (ds.node_off + node) * 4;
-    nb[0] = make_int4(lo[0], lo[1], lo[2], lo[3]);
-    nb[1] = make_int4(lo[4], lo[5], lo[6], lo[7]);
-    nb[2] = make_int4(hi[0], hi[1], hi[2], hi[3]);
-    nb[3] = make_int4(hi[4], hi[5], hi[6], hi[7]);
-    db.node_minrank[ds.node_off + node] = mr;
-    while (node > 1) {
-        __threadfence();
-        const int64_t parent = node >> 1;
-        if (atomicAdd(&db.node_flag[ds.node_off + parent], 1u) == 0u) return;
-        __threadfence();
-        const int4* cl = db.node_box + (ds.node_off + 2 * parent) * 4;
-        const int4* cr = cl + 4;
-        int4 q[4];
-#pragma unroll
-        for (int i = 0; i < 4; ++i) {
-            const int4 x = __ldcg(cl + i), y = __ldcg(cr + i);
-            q[i] = i < 2 ? make_int4(min(x.x, y.x), min(x.y, y.y), min(x.z, y.z), min(x.w, y.w))
-                         : make_int4(max(x.x, y.x), max(x.y, y.y), max(x.z, y.z), max(x.w, y.w));
-        }
-        int4* pb = db.node_box + (ds.node_off + parent) * 4;
-#pragma unroll
-        for (int i = 0; i < 4; ++i) pb[i] = q[i];
-        db.node_minrank[ds.node_off + parent] = min(__ldcg(&db.node_minrank[ds.node_off + 2 * parent]),
-                                                    __ldcg(&db.node_minrank[ds.node_off + 2 * parent + 1]));
-        node = parent;
-    }
-}
-
-template <int D>
-__device__ __forceinline__ long long box_dist(const int4* nb, const int32_t (&x)[D]) {
-    const int4 l0 = nb[0], h0 = nb[2];
-    int32_t lo[8] = {l0.x, l0.y, l0.z, l0.w, 0, 0, 0, 0};
-    int32_t hi[8] = {h0.x, h0.y, h0.z, h0.w, 0, 0, 0, 0};
-    if (D > 4) {
-        const int4 l1 = nb[1], h1 = nb[3];
-        lo[4] = l1.x; lo[5] = l1.y; lo[6] = l1.z; lo[7] = l1.w;
-        hi[4] = h1.x; hi[5] = h1.y; hi[6] = h1.z; hi[7] = h1.w;
-    }
-    long long s = 0;
-#pragma unroll
-    for (int k = 0; k < D; ++k) {
-        const long long dd = x[k] < lo[k] ? (long long)lo[k] - x[k] : (x[k] > hi[k] ? (long long)x[k] - hi[k] : 0);
-        s += dd * dd;
-    }
-    return s;
-}
-
-template <int D>
-__global__ void __launch_bounds__(128) k_tree_search(BatchView v, DeltaBufs db) {
-    constexpr int DP = D <= 4 ? 1 : 2;
-    const uint32_t cnt = db.ucount[0];
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < cnt; i += (int64_t)gridDim.x * blockDim.x) {
-        const uint32_t p = db.tree_list[i];
+    const bool valid = p < v.N;
+    bool to_tree = false, to_bf = false;
+    if (valid) {
         const int b = find_ds(v.pt_off, v.B, p);
         const DsDesc& ds = v.desc[b];
-        if (ds.d != D) continue;
-        const int4* recb = v.rec + ds.rec_off - ds.pt_off * DP;
-        int32_t x[D];
-        load_pt<D>(recb + (int64_t)p * DP, x);
         const uint2 ro = v.ro_s[p];
-        long long bestD = INT64_MAX;
-        uint32_t bestJ = 0xffffffffu;
-        const unsigned long long bk = v.best_s[p];
-        if (bk != kNoBest && (uint32_t)(bk >> 32) != kSat) {
-            bestD = (long long)(bk >> 32);
-            bestJ = (uint32_t)bk;
-        }
-        const int4* boxes = db.node_box + ds.node_off * 4;
-        const uint32_t* minrank = db.node_minrank + ds.node_off;
-        const int64_t first_leaf = 1ll << ds.h;
-        constexpr int kStack = 64;
-        int64_t stack[kStack];
-        int sp = 0;
-        stack[sp++] = 1;
-        while (sp > 0) {
-            const int64_t nd = stack[--sp];
-            if (minrank[nd] >= ro.x) continue;
-            if (box_dist<D>(boxes + nd * 4, x) > bestD) continue;
-            if (nd >= first_leaf) {
-                const int64_t q0 = ds.pt_off + (nd - first_leaf) * kLeaf;
-                const int64_t q1 = min(q0 + kLeaf, ds.pt_off + (int64_t)ds.n);
-                for (int64_t q = q0; q < q1; ++q) {
-                    const uint2 cr = v.ro_s[q];
-                    if (cr.x >= ro.x) continue;
-                    int32_t c[D];
-                    load_pt<D>(recb + q * DP, c);
-                    const long long dd = dist64<D>(x, c);
-                    if (dd < bestD || (dd == bestD && cr.y < bestJ)) {
-                        bestD = dd;
-                        bestJ = cr.y;
-                    }
-                }
-            } else if (sp + 2 > kStack) {
-                atomicOr(v.err, kErrTreeStack);
+        const int64_t g = ds.pt_off + ro.y;
+        if (ro.x == 0u) {  // the densest point: no dependent point, delta = infinity
+            v.dep[g] = -1;
+            v.delta2[g] = INT64_MAX;
+        } else {
+            const unsigned long long bk = v.best_s[p];
+            const uint32_t dd = (uint32_t)(bk >> 32);
+            // distance from the point to the outside of the searched box of cells
+            const int4* r = v.rec + ds.rec_off + (p - ds.pt_off) * ds.dp;
+            int64_t bound = INT64_MAX;
+            for (int j = 0; j < ds.k; ++j) {
+                const int32_t xi = rec_coord(r, ds.gdim[j]);
+                const int64_t x = xi;
+                const int64_t cj = cell_coord(ds, j, xi);
+                if (cj - ds.R > 0) bound = min(bound, x - (ds.origin[j] + (cj - ds.R) * ds.s) + 1);
+                if (cj + ds.R + 1 < ds.ext[j]) bound = min(bound, ds.origin[j] + (cj + ds.R + 1) * ds.s - x);
+            }
+            const bool found = bk != kNoBest && dd != kSat;
+            if (found && (bound == INT64_MAX || (int64_t)dd < bound * bound)) {
+                v.dep[g] = (int32_t)(uint32_t)bk;
+                v.delta2[g] = (int64_t)dd;
+            } else if (ro.x < db.bf_rank) {
+                to_bf = true;
             } else {
-                const int64_t l = 2 * nd, r = l + 1;
-                const long long dl = minrank[l] < ro.x ? box_dist<D>(boxes + l * 4, x) : INT64_MAX;
-                const long long dr = minrank[r] < ro.x ? box_dist<D>(boxes + r * 4, x) : INT64_MAX;
-                // push the farther child first so the nearer one is searched first
-                if (dl <= dr) {
-                    if (dr <= bestD) stack[sp++] = r;
-                    if (dl <= bestD) stack[sp++] = l;
-                } else {
-                    if (dl <= bestD) stack[sp++] = l;
-                    if (dr <= bestD) stack[sp++] = r;
-                }
+                to_tree = true;
             }
         }
-        const int64_t g = ds.pt_off + ro.y;
-        v.dep[g] = (int32_t)bestJ;
-        v.delta2[g] = bestD;
     }
+    const int lane = threadIdx.x & 31;
+    const unsigned lt = (1u << lane) - 1u;
+    const unsigned mt = __ballot_sync(0xffffffffu, to_tree), mb = __ballot_sync(0xffffffffu, to_bf);
+    uint32_t bt = 0, bb = 0;
+    if (lane == 0) {
+        if (mt) bt = atomicAdd(&db.ucount[0], (uint32_t)__popc(mt));
+        if (mb) bb = atomicAdd(&db.ucount[1], (uint32_t)__popc(mb));
+    }
+    bt = __shfl_sync(0xffffffffu, bt, 0);
+    bb = __shfl_sync(0xffffffffu, bb, 0);
+    if (to_tree) db.tree_list[bt + __popc(mt & lt)] = (uint32_t)p;
+    if (to_bf) db.bf_list[bb + __popc(mb & lt)] = (uint32_t)p;
 }
 
 // --------------------------------------------------------- brute force
@@ -600,24 +474,6 @@ cudaError_t launch_ring(const BatchView& v, const CellWork& w, uint32_t class_ma
 cudaError_t launch_finalize(const BatchView& v, const DeltaBufs& db, cudaStream_t st) {
     if (v.N == 0) return cudaSuccess;
     (k_finalize<<<grid_for(v.N, 256), 256, 0, st>>>(v, db), note_launch());
-    return cudaGetLastError();
-}
-
-cudaError_t launch_tree_build(const BatchView& v, const DeltaBufs& db, cudaStream_t st) {
-    if (db.leaf_slots == 0) return cudaSuccess;
-    (k_tree_build<<<grid_for(db.leaf_slots, 128), 128, 0, st>>>(v, db), note_launch());
-    return cudaGetLastError();
-}
-
-cudaError_t launch_tree_search(const BatchView& v, const DeltaBufs& db, uint32_t dim_mask, int64_t bound,
-                               cudaStream_t st) {
-    if (bound <= 0) return cudaSuccess;
-    const unsigned blocks = (unsigned)std::min<int64_t>(152 * 16, grid_for(bound, 128));
-#define DPC_TREE_CLASS(D) \
-    if (dim_mask & (1u << (D - 1))) (k_tree_search<D><<<blocks, 128, 0, st>>>(v, db), note_launch());
-    DPC_TREE_CLASS(1) DPC_TREE_CLASS(2) DPC_TREE_CLASS(3) DPC_TREE_CLASS(4)
-    DPC_TREE_CLASS(5) DPC_TREE_CLASS(6) DPC_TREE_CLASS(7) DPC_TREE_CLASS(8)
-#undef DPC_TREE_CLASS
     return cudaGetLastError();
 }
 

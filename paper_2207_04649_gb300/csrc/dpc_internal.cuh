@@ -46,6 +46,7 @@ struct DsDesc {
     int32_t h;            // tree height: 2^h leaf slots
     int32_t nleaf;        // leaves (ceil(n / kLeaf))
     int32_t rbits;        // bits of the density key in the rank sort
+    uint64_t dmask[kMaxGridDims];  // Morton bits of each gridded dim
 };
 
 // Device views of a batch's buffers (all device pointers).
@@ -62,6 +63,7 @@ struct BatchView {
     // grid
     uint64_t* key;             // cell key per sorted point
     uint32_t* cell_start;      // [ncells + 1]
+    uint32_t* cell_of;         // sorted: cell of each point
     uint32_t* ncells;          // device scalar
     int4* hash;                // open addressing: {key lo, key hi, start, count}
     uint64_t hmask;

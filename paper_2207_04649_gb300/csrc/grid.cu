@@ -26,29 +26,69 @@ __global__ void k_minmax_init(int32_t* mm, int B) {
     }
 }
 
-// Per-dataset, per-dimension min and max of the input coordinates.
-__global__ void k_minmax(BatchView v, int32_t* __restrict__ mm) {
-    const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const bool valid = g < v.N;
-    const int b = valid ? find_ds(v.pt_off, v.B, g) : -1;
-    const unsigned same = __match_any_sync(0xffffffffu, b);
-    if (!valid) return;
-    const DsDesc& ds = v.desc[b];
-    const int32_t* x = v.in + ds.in_off + (g - ds.pt_off) * ds.d;
-    const int lane = threadIdx.x & 31;
-    const bool full = same == 0xffffffffu;  // all 32 lanes valid and in one dataset
-    for (int k = 0; k < ds.d; ++k) {
-        int lo = x[k], hi = x[k];
-        if (full) {
-            for (int o = 16; o > 0; o >>= 1) {
-                lo = min(lo, __shfl_xor_sync(0xffffffffu, lo, o));
-                hi = max(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+constexpr int kMmItems = 8;  // points per thread in the bounding-box pass
+
+// Per-dataset, per-dimension min and max of the input coordinates. Each
+// block reduces its points of the dataset its first point belongs to in
+// registers, then warp shuffles, then shared memory, and issues one global
+// atomic per dimension; points of a following dataset (blocks straddling a
+// boundary) go to global atomics directly.
+__global__ void __launch_bounds__(256) k_minmax(BatchView v, int32_t* __restrict__ mm) {
+    __shared__ int smin[kMaxDims], smax[kMaxDims];
+    const int64_t base = (int64_t)blockIdx.x * blockDim.x * kMmItems;
+    if (base >= v.N) return;  // uniform across the block
+    const int b0 = find_ds(v.pt_off, v.B, base);
+    const DsDesc& d0 = v.desc[b0];
+    const int64_t end0 = v.pt_off[b0 + 1];
+    if (threadIdx.x < kMaxDims) {
+        smin[threadIdx.x] = INT32_MAX;
+        smax[threadIdx.x] = INT32_MIN;
+    }
+    __syncthreads();
+    int lo[kMaxDims], hi[kMaxDims];
+#pragma unroll
+    for (int k = 0; k < kMaxDims; ++k) {
+        lo[k] = INT32_MAX;
+        hi[k] = INT32_MIN;
+    }
+    for (int it = 0; it < kMmItems; ++it) {
+        const int64_t g = base + (int64_t)it * blockDim.x + threadIdx.x;
+        if (g >= v.N) break;
+        if (g < end0) {
+            const int32_t* x = v.in + d0.in_off + (g - d0.pt_off) * d0.d;
+#pragma unroll
+            for (int k = 0; k < kMaxDims; ++k)
+                if (k < d0.d) {
+                    lo[k] = min(lo[k], x[k]);
+                    hi[k] = max(hi[k], x[k]);
+                }
+        } else {
+            const int b = find_ds(v.pt_off, v.B, g);
+            const DsDesc& ds = v.desc[b];
+            const int32_t* x = v.in + ds.in_off + (g - ds.pt_off) * ds.d;
+            for (int k = 0; k < ds.d; ++k) {
+                atomicMin(&mm[(b * kMaxDims + k) * 2], x[k]);
+                atomicMax(&mm[(b * kMaxDims + k) * 2 + 1], x[k]);
             }
         }
-        if (!full || lane == 0) {
-            atomicMin(&mm[(b * kMaxDims + k) * 2], lo);
-            atomicMax(&mm[(b * kMaxDims + k) * 2 + 1], hi);
+    }
+#pragma unroll
+    for (int k = 0; k < kMaxDims; ++k) {
+        if (k >= d0.d) break;
+        int l = lo[k], h = hi[k];
+        for (int o = 16; o > 0; o >>= 1) {
+            l = min(l, __shfl_xor_sync(0xffffffffu, l, o));
+            h = max(h, __shfl_xor_sync(0xffffffffu, h, o));
         }
+        if ((threadIdx.x & 31) == 0) {
+            atomicMin(&smin[k], l);
+            atomicMax(&smax[k], h);
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x < d0.d) {
+        atomicMin(&mm[(b0 * kMaxDims + threadIdx.x) * 2], smin[threadIdx.x]);
+        atomicMax(&mm[(b0 * kMaxDims + threadIdx.x) * 2 + 1], smax[threadIdx.x]);
     }
 }
 
@@ -62,7 +102,7 @@ __global__ void k_cell_keys(BatchView v, K* __restrict__ keys, uint32_t* __restr
     const DsDesc& ds = v.desc[b];
     const int32_t* x = v.in + ds.in_off + (g - ds.pt_off) * ds.d;
     int32_t c[kMaxGridDims];
-    for (int j = 0; j < ds.k; ++j) c[j] = (int32_t)(((int64_t)x[ds.gdim[j]] - ds.origin[j]) / ds.s);
+    for (int j = 0; j < ds.k; ++j) c[j] = (int32_t)((uint32_t)(x[ds.gdim[j]] - ds.origin[j]) / (uint32_t)ds.s);
     keys[g] = (K)(ds.cbase + morton(c, ds.k, ds.mbits));
     vals[g] = (uint32_t)g;
 }
@@ -92,6 +132,7 @@ __global__ void k_cells(BatchView v, const uint32_t* __restrict__ flag, const ui
     const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= v.N) return;
     if (flag[p]) v.cell_start[cidx[p]] = (uint32_t)p;
+    v.cell_of[p] = cidx[p] + flag[p] - 1u;
     if (p == v.N - 1) {
         const uint32_t nc = cidx[p] + flag[p];
         v.cell_start[nc] = (uint32_t)v.N;
@@ -124,7 +165,7 @@ inline unsigned blocks_for(int64_t n, int t) { return (unsigned)((n + t - 1) / t
 
 cudaError_t launch_minmax(const BatchView& v, int32_t* mm, cudaStream_t st) {
     (k_minmax_init<<<blocks_for((int64_t)v.B * kMaxDims, 256), 256, 0, st>>>(mm, v.B), note_launch());
-    if (v.N > 0) (k_minmax<<<blocks_for(v.N, 256), 256, 0, st>>>(v, mm), note_launch());
+    if (v.N > 0) (k_minmax<<<blocks_for(v.N, 256 * kMmItems), 256, 0, st>>>(v, mm), note_launch());
     return cudaGetLastError();
 }
 

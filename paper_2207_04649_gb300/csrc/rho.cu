@@ -8,14 +8,21 @@
 // query per cell, then a scan of the result for every member), with the
 // neighbour cells of the grid in place of the kd-tree query.
 //
-// Two kernels share the work:
+// Preparation: one warp per cell looks up the cell's (2R+1)^k neighbours in
+// the hash table in parallel (one lane each) and stores the non-empty ones as
+// runs (start, count) of sorted points, with the candidate count. The hot
+// kernels then read runs only; the ring search of the delta stage reuses them.
+//
+// Two kernels share the pair work:
 //  * dense cells (more than kSparseMax points): one warp per work item
-//    (cell, chunk of up to 128 queries held 4 per lane in registers, chunk
-//    of candidates). Candidates are staged in shared memory from contiguous
-//    runs of sorted records with 128-bit loads and read back as broadcasts.
-//    Items are claimed from an atomic counter by persistent warps.
+//    (cell, chunk of up to 128 queries, chunk of candidates). Candidates are
+//    staged in shared memory from the runs with 128-bit loads. A chunk of 32
+//    or more queries keeps 1-4 queries per lane; a smaller one is split over
+//    the lanes in 2 or 4 groups, each group taking every 2nd or 4th
+//    candidate, and the groups' counts are added with warp shuffles. Items
+//    are claimed from an atomic counter by persistent warps.
 //  * sparse cells: one thread per cell, its few queries in registers,
-//    candidates read straight from the L1/L2-resident sorted records.
+//    candidates read from the runs with unrolled 128-bit loads.
 //
 // Pair arithmetic: when every candidate difference is small enough
 // (DsDesc::w32) the test runs in 32-bit integers as the sign of
@@ -53,45 +60,123 @@ __global__ void k_compact_cells(BatchView v, CellPrepBufs cb, int64_t bound) {
     }
 }
 
-// One warp per dense cell: lanes look up the neighbour cells in parallel and
-// the non-empty ones are compacted, in neighbour order, into the cell's run
-// list; the cell's candidate count fixes how many work items it gets.
-__global__ void k_dense_prep(BatchView v, CellPrepBufs cb, int kch) {
-    const int lane = threadIdx.x & 31;
-    const int64_t warp0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    const uint32_t nd = *cb.ndense;
-    const unsigned lt = (1u << lane) - 1u;
-    for (int64_t dc = warp0; dc < nd; dc += nwarps) {
-        const uint32_t c = cb.dense[dc];
+constexpr int kProbeBatch = 9;  // hash probes issued together per thread
+
+__device__ __forceinline__ uint2 resolve_probe(const BatchView& v, uint64_t key, int4 e) {
+    const uint64_t k0 = (uint64_t)(uint32_t)e.x | ((uint64_t)(uint32_t)e.y << 32);
+    if (k0 == key) return make_uint2((uint32_t)e.z, (uint32_t)e.w);
+    if (k0 == kEmptyKey) return make_uint2(0u, 0u);
+    return hash_find(v.hash, v.hmask, key);  // collision: keep probing
+}
+
+// One thread per cell of a dataset gridded in K dims with reach R = 1. The
+// 3^K neighbour offsets are compile-time constants; a neighbour's key comes
+// from the cell's own key by carry/borrow steps inside each dim's Morton
+// bits; first hash probes are issued kProbeBatch at a time as independent
+// loads, then resolved. Non-empty neighbours become the cell's runs, in
+// neighbour order.
+template <int K>
+__global__ void __launch_bounds__(256) k_cell_runs(BatchView v, CellPrepBufs cb, int64_t ncells) {
+    constexpr int NNB = K == 1 ? 3 : (K == 2 ? 9 : (K == 3 ? 27 : 81));
+    unsigned long long pairs = 0;
+    for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < ncells; c += (int64_t)gridDim.x * blockDim.x) {
         const uint32_t cs = v.cell_start[c], m = v.cell_start[c + 1] - cs;
         const int b = find_ds(v.pt_off, v.B, cs);
         const DsDesc& ds = v.desc[b];
+        if (ds.k != K || ds.R != 1) continue;
+        const int4* r0 = v.rec + ds.rec_off + ((int64_t)cs - ds.pt_off) * ds.dp;
+        int32_t cc[K];
+#pragma unroll
+        for (int j = 0; j < K; ++j)
+            cc[j] = (int32_t)((uint32_t)(rec_coord(r0, ds.gdim[j]) - ds.origin[j]) / (uint32_t)ds.s);
+        const uint64_t own = v.key[cs] - ds.cbase;
+        uint32_t nr = 0, cand = 0;
+        uint2* runs = cb.runs + c * cb.nbs;
+#pragma unroll
+        for (int base = 0; base < NNB; base += kProbeBatch) {
+            uint64_t key[kProbeBatch];
+            int4 e[kProbeBatch];
+#pragma unroll
+            for (int q = 0; q < kProbeBatch; ++q) {
+                const int t = base + q;
+                key[q] = kEmptyKey;
+                if (t < NNB) {
+                    bool ok = true;
+                    int nz = 0;
+                    uint64_t code = own;
+                    int tt = t;
+#pragma unroll
+                    for (int j = 0; j < K; ++j) {
+                        const int o = tt % 3 - 1;
+                        tt /= 3;
+                        if (o != 0) {
+                            ++nz;
+                            ok = ok && cc[j] + o >= 0 && cc[j] + o < ds.ext[j];
+                            code = morton_step(code, ds.dmask[j], o);
+                        }
+                    }
+                    // offsets in nz dims: boxes at least sqrt(nz) apart
+                    if (ok && nz < ds.d_cut2) key[q] = ds.cbase + code;
+                }
+                e[q] = key[q] != kEmptyKey ? __ldg(&v.hash[mix64(key[q]) & v.hmask]) : make_int4(-1, -1, 0, 0);
+            }
+#pragma unroll
+            for (int q = 0; q < kProbeBatch; ++q) {
+                if (key[q] == kEmptyKey) continue;
+                const uint2 r = resolve_probe(v, key[q], e[q]);
+                if (r.y > 0u) {
+                    runs[nr++] = r;
+                    cand += r.y;
+                }
+            }
+        }
+        cb.nruns[c] = nr;
+        cb.cand[c] = cand;
+        pairs += (unsigned long long)m * cand;
+    }
+    for (int o = 16; o > 0; o >>= 1) pairs += __shfl_xor_sync(0xffffffffu, pairs, o);
+    if ((threadIdx.x & 31) == 0 && pairs) atomicAdd(&cb.stats[0], pairs);
+}
+
+// Any k, any reach R (used when R != 1).
+__global__ void __launch_bounds__(256) k_cell_runs_any(BatchView v, CellPrepBufs cb, int64_t ncells) {
+    unsigned long long pairs = 0;
+    for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < ncells; c += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t cs = v.cell_start[c], m = v.cell_start[c + 1] - cs;
+        const int b = find_ds(v.pt_off, v.B, cs);
+        const DsDesc& ds = v.desc[b];
+        if (ds.R == 1 && ds.k >= 1) continue;
         const int4* r0 = v.rec + ds.rec_off + ((int64_t)cs - ds.pt_off) * ds.dp;
         int32_t cc[kMaxGridDims];
         for (int j = 0; j < ds.k; ++j) cc[j] = cell_coord(ds, j, rec_coord(r0, ds.gdim[j]));
         const int nnb = num_neighbours(ds);
         uint32_t nr = 0, cand = 0;
-        for (int base = 0; base < nnb; base += 32) {
-            const int t = base + lane;
-            uint2 e = make_uint2(0u, 0u);
+        uint2* runs = cb.runs + c * cb.nbs;
+        for (int t = 0; t < nnb; ++t) {
             int32_t nc[kMaxGridDims];
-            if (t < nnb && neighbour(ds, cc, t, nc))
-                e = hash_find(v.hash, v.hmask, ds.cbase + morton(nc, ds.k, ds.mbits));
-            const unsigned found = __ballot_sync(0xffffffffu, e.y > 0u);
-            if (e.y > 0u) cb.runs[dc * kMaxNb + nr + __popc(found & lt)] = e;
-            nr += __popc(found);
-            uint32_t s = e.y;
-            for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-            cand += s;
+            if (!neighbour(ds, cc, t, nc)) continue;
+            const uint2 r = hash_find(v.hash, v.hmask, ds.cbase + morton(nc, ds.k, ds.mbits));
+            if (r.y > 0u) {
+                runs[nr++] = r;
+                cand += r.y;
+            }
         }
-        if (lane == 0) {
-            atomicAdd(&cb.stats[0], (unsigned long long)m * cand);
-            cb.nruns[dc] = nr;
-            cb.cand[dc] = cand;
-            const uint32_t nq = (m + kQch - 1) / kQch, nk = (cand + kch - 1) / kch;
-            cb.nitem_c[dc] = nq * (nk > 0 ? nk : 1);
-        }
+        cb.nruns[c] = nr;
+        cb.cand[c] = cand;
+        pairs += (unsigned long long)m * cand;
+    }
+    for (int o = 16; o > 0; o >>= 1) pairs += __shfl_xor_sync(0xffffffffu, pairs, o);
+    if ((threadIdx.x & 31) == 0 && pairs) atomicAdd(&cb.stats[0], pairs);
+}
+
+__global__ void k_item_count(BatchView v, CellPrepBufs cb, int kch) {
+    const uint32_t nd = *cb.ndense;
+    for (int64_t dc = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; dc < nd; dc += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t c = cb.dense[dc];
+        const uint32_t m = v.cell_start[c + 1] - v.cell_start[c];
+        const uint32_t cand = cb.cand[c];
+        const uint32_t nq = (m + kQch - 1) / kQch, nk = cand == 0u ? 1u : (cand + kch - 1) / kch;
+        cb.nitem_c[dc] = nq * nk;
     }
 }
 
@@ -102,7 +187,7 @@ __global__ void k_fill_items(BatchView v, CellPrepBufs cb, int kch) {
         const uint32_t c = cb.dense[dc];
         const uint32_t m = v.cell_start[c + 1] - v.cell_start[c];
         const uint32_t nq = (m + kQch - 1) / kQch;
-        const uint32_t cand = cb.cand[dc];
+        const uint32_t cand = cb.cand[c];
         const uint32_t nk = cand == 0u ? 1u : (cand + kch - 1) / kch;
         uint4* out = cb.items + cb.item_off[dc];
         for (uint32_t q = 0; q < nq; ++q)
@@ -143,12 +228,13 @@ __device__ __forceinline__ uint32_t inside(const int32_t (&q)[D], const int32_t 
     }
 }
 
-template <int D, bool W64, int Q>
-__device__ __forceinline__ void eval_rho(const int4* buf, int nb, const int32_t (&qx)[4][D], uint32_t (&cnt)[4],
-                                         int64_t T) {
+// Q queries per lane against staged candidates grp, grp + G, ...
+template <int D, bool W64, int Q, int G>
+__device__ __forceinline__ void eval_rho(const int4* buf, int nb, int grp, const int32_t (&qx)[4][D],
+                                         uint32_t (&cnt)[4], int64_t T) {
     constexpr int DP = D <= 4 ? 1 : 2;
-#pragma unroll 2
-    for (int j = 0; j < nb; ++j) {
+#pragma unroll 4
+    for (int j = grp; j < nb; j += G) {
         int32_t c[D];
         load_point<D>(buf + j * DP, c);
 #pragma unroll
@@ -178,16 +264,21 @@ __global__ void __launch_bounds__(kRhoThreads) k_rho_dense(BatchView v, CellWork
         const int4* recb = v.rec + ds.rec_off - ds.pt_off * DP;  // indexed by global sorted position
         const int q0 = (int)qc * kQch;
         const int nq = min(kQch, (int)m - q0);
-        const int Q = (nq + 31) >> 5;
+        // lane layout: nq >= 32: Q = ceil(nq / 32) queries per lane; otherwise
+        // G groups of Mq lanes, one query per lane, candidates split by group
+        const int Q = nq >= 32 ? (nq + 31) >> 5 : 1;
+        const int Mq = nq >= 32 ? 32 : (nq <= 8 ? 8 : (nq <= 16 ? 16 : 32));
+        const int G = 32 / Mq;
+        const int grp = lane / Mq, ql = lane & (Mq - 1);
         int32_t qx[4][D];
 #pragma unroll
         for (int t = 0; t < 4; ++t) {
-            const int qi = min(lane + 32 * t, nq - 1);
+            const int qi = min(G == 1 ? lane + 32 * t : ql, nq - 1);
             load_point<D>(recb + ((int64_t)cs + q0 + qi) * DP, qx[t]);
         }
         uint32_t cnt[4] = {0u, 0u, 0u, 0u};
-        const uint2* runs = w.runs + (int64_t)dc * kMaxNb;
-        const uint32_t nr = w.nruns[dc], ctot = w.cand[dc];
+        const uint2* runs = w.runs + (int64_t)c * w.nbs;
+        const uint32_t nr = w.nruns[c], ctot = w.cand[c];
         const uint32_t k0 = kc * (uint32_t)w.kch;
         uint32_t remaining = min(ctot, k0 + (uint32_t)w.kch) - k0;
         uint32_t ri = 0, roff = k0;
@@ -219,17 +310,24 @@ __global__ void __launch_bounds__(kRhoThreads) k_rho_dense(BatchView v, CellWork
                 }
             }
             __syncwarp();
-            switch (Q) {
-                case 1: eval_rho<D, W64, 1>(buf, nb, qx, cnt, T); break;
-                case 2: eval_rho<D, W64, 2>(buf, nb, qx, cnt, T); break;
-                case 3: eval_rho<D, W64, 3>(buf, nb, qx, cnt, T); break;
-                default: eval_rho<D, W64, 4>(buf, nb, qx, cnt, T); break;
+            if (G == 4) eval_rho<D, W64, 1, 4>(buf, nb, grp, qx, cnt, T);
+            else if (G == 2) eval_rho<D, W64, 1, 2>(buf, nb, grp, qx, cnt, T);
+            else switch (Q) {
+                case 1: eval_rho<D, W64, 1, 1>(buf, nb, 0, qx, cnt, T); break;
+                case 2: eval_rho<D, W64, 2, 1>(buf, nb, 0, qx, cnt, T); break;
+                case 3: eval_rho<D, W64, 3, 1>(buf, nb, 0, qx, cnt, T); break;
+                default: eval_rho<D, W64, 4, 1>(buf, nb, 0, qx, cnt, T); break;
             }
             __syncwarp();
         }
+        if (G > 1) {
+            for (int o = Mq; o < 32; o <<= 1) cnt[0] += __shfl_xor_sync(0xffffffffu, cnt[0], o);
+            if (grp == 0 && ql < nq) atomicAdd(&v.rho_s[cs + q0 + ql], (int)cnt[0]);
+        } else {
 #pragma unroll
-        for (int t = 0; t < 4; ++t)
-            if (lane + 32 * t < nq) atomicAdd(&v.rho_s[cs + q0 + lane + 32 * t], (int)cnt[t]);
+            for (int t = 0; t < 4; ++t)
+                if (lane + 32 * t < nq) atomicAdd(&v.rho_s[cs + q0 + lane + 32 * t], (int)cnt[t]);
+        }
     }
 }
 
@@ -247,19 +345,15 @@ __global__ void __launch_bounds__(256) k_rho_sparse(BatchView v, CellWork w) {
         int32_t qx[kSparseMax][D];
 #pragma unroll
         for (int t = 0; t < kSparseMax; ++t) load_point<D>(recb + ((int64_t)cs + min((uint32_t)t, m - 1)) * DP, qx[t]);
-        int32_t cc[kMaxGridDims];
-        for (int j = 0; j < ds.k; ++j) cc[j] = cell_coord(ds, j, rec_coord(recb + (int64_t)cs * DP, ds.gdim[j]));
         uint32_t cnt[kSparseMax];
 #pragma unroll
         for (int t = 0; t < kSparseMax; ++t) cnt[t] = 0u;
-        const int nnb = num_neighbours(ds);
         const int64_t T = ds.d_cut2;
-        uint32_t ncand = 0;
-        for (int t = 0; t < nnb; ++t) {
-            int32_t nc[kMaxGridDims];
-            if (!neighbour(ds, cc, t, nc)) continue;
-            const uint2 e = hash_find(v.hash, v.hmask, ds.cbase + morton(nc, ds.k, ds.mbits));
-            ncand += e.y;
+        const uint2* runs = w.runs + (int64_t)c * w.nbs;
+        const uint32_t nr = w.nruns[c];
+        for (uint32_t r = 0; r < nr; ++r) {
+            const uint2 e = runs[r];
+#pragma unroll 4
             for (uint32_t j = 0; j < e.y; ++j) {
                 int32_t cj[D];
                 load_point<D>(recb + ((int64_t)e.x + j) * DP, cj);
@@ -270,7 +364,6 @@ __global__ void __launch_bounds__(256) k_rho_sparse(BatchView v, CellWork w) {
 #pragma unroll
         for (int q = 0; q < kSparseMax; ++q)
             if ((uint32_t)q < m) v.rho_s[cs + q] = (int32_t)cnt[q];
-        atomicAdd(&w.stats[1], (unsigned long long)m * ncand);
     }
 }
 
@@ -307,14 +400,19 @@ cudaError_t launch_classify_cells(const BatchView& v, const CellPrepBufs& cb, in
     return cudaGetLastError();
 }
 
-cudaError_t launch_dense_prep(const BatchView& v, const CellPrepBufs& cb, int64_t ndense_bound, int kch,
-                              void* scan_temp, cudaStream_t st) {
-    if (ndense_bound <= 0) {
-        cudaError_t e = cudaMemsetAsync(cb.nitems, 0, sizeof(uint32_t), st);
-        return e;
+cudaError_t launch_dense_prep(const BatchView& v, const CellPrepBufs& cb, int64_t ncells, int64_t ndense_bound,
+                              int kch, uint32_t kmask, void* scan_temp, cudaStream_t st) {
+    if (ncells > 0) {
+        const unsigned blocks = (unsigned)std::min<int64_t>(152 * 16, grid_for(ncells, 256));
+        if (kmask & 1u) (k_cell_runs_any<<<blocks, 256, 0, st>>>(v, cb, ncells), note_launch());
+        if (kmask & 2u) (k_cell_runs<1><<<blocks, 256, 0, st>>>(v, cb, ncells), note_launch());
+        if (kmask & 4u) (k_cell_runs<2><<<blocks, 256, 0, st>>>(v, cb, ncells), note_launch());
+        if (kmask & 8u) (k_cell_runs<3><<<blocks, 256, 0, st>>>(v, cb, ncells), note_launch());
+        if (kmask & 16u) (k_cell_runs<4><<<blocks, 256, 0, st>>>(v, cb, ncells), note_launch());
     }
-    const unsigned blocks = (unsigned)std::min<int64_t>(152 * 16, grid_for(ndense_bound * 32, 256));
-    (k_dense_prep<<<blocks, 256, 0, st>>>(v, cb, kch), note_launch());
+    if (ndense_bound <= 0) return cudaMemsetAsync(cb.nitems, 0, sizeof(uint32_t), st);
+    const unsigned blocks = (unsigned)std::min<int64_t>(152 * 16, grid_for(ndense_bound, 256));
+    (k_item_count<<<blocks, 256, 0, st>>>(v, cb, kch), note_launch());
     return exclusive_scan_u32(cb.nitem_c, cb.item_off, ndense_bound, cb.nitems, scan_temp, st);
 }
 

@@ -151,6 +151,7 @@ struct Batch {
     uint32_t class_mask = 0, dim_mask = 0;
     int64_t ncells = 0, ndense = 0, nsparse = 0, nitems = 0, ntree = 0, nbf = 0;
     int64_t cand_pairs = 0;
+    int64_t tree_visits = 0, tree_pairs = 0;
     unsigned long long* d_stats = nullptr;
     uint32_t* d_counters = nullptr;  // [16] rho + [16] ring
     int out_is_device = 0;
@@ -312,6 +313,7 @@ struct Batch {
         const size_t temp_bytes = std::max(radix_sort_temp_bytes(N), scan_temp_bytes(N));
         DPC_CK(dens.get(&temp, temp_bytes));
         DPC_CK(keep.get(&v.cell_start, N + 1));
+        DPC_CK(keep.get(&v.cell_of, N));
         DPC_CK(launch_cell_keys(v, key32, k0, v0, st));
         if (key32)
             DPC_CK(radix_sort_u32((uint32_t*)k0, v0, (uint32_t*)k2, v.perm, (uint32_t*)k1, v1, N, key_bits, temp, st));
@@ -353,12 +355,21 @@ struct Batch {
         }
         ndense = cnts[0];
         nsparse = cnts[1];
-        DPC_CK(keep.get(&cb.runs, (size_t)std::max<int64_t>(ndense, 1) * kMaxNb));
-        DPC_CK(keep.get(&cb.nruns, ndense + 1));
-        DPC_CK(keep.get(&cb.cand, ndense + 1));
+        int nbs = 1;
+        for (int b = 0; b < B; ++b) {
+            int t = 1;
+            for (int j = 0; j < hd[b].k; ++j) t *= 2 * hd[b].R + 1;
+            nbs = std::max(nbs, t);
+        }
+        cb.nbs = nbs;
+        DPC_CK(keep.get(&cb.runs, (size_t)std::max<int64_t>(ncells, 1) * nbs));
+        DPC_CK(keep.get(&cb.nruns, ncells + 1));
+        DPC_CK(keep.get(&cb.cand, ncells + 1));
         DPC_CK(dens.get(&cb.nitem_c, ndense + 1));
         DPC_CK(dens.get(&cb.item_off, ndense + 1));
-        DPC_CK(launch_dense_prep(v, cb, ndense, ctx->tune.kch, temp, st));
+        uint32_t kmask = 0;
+        for (int b = 0; b < B; ++b) kmask |= (hd[b].R == 1 && hd[b].k >= 1) ? 1u << hd[b].k : 1u;
+        DPC_CK(launch_dense_prep(v, cb, ncells, ndense, ctx->tune.kch, kmask, temp, st));
         uint32_t ni = 0;
         if (ndense > 0) {
             DPC_CK(cudaMemcpyAsync(&ni, cb.nitems, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
@@ -379,6 +390,7 @@ struct Batch {
         w.items = cb.items;
         w.nitems = cb.nitems;
         w.kch = ctx->tune.kch;
+        w.nbs = nbs;
         w.stats = d_stats;
         mark(1);
 
@@ -432,6 +444,10 @@ struct Batch {
         }
         ds.k = k;
         ds.mbits = mbits;
+        for (int j = 0; j < kMaxGridDims; ++j) {
+            ds.dmask[j] = 0;
+            for (int i = 0; j < k && i < mbits; ++i) ds.dmask[j] |= 1ull << (i * k + j);
+        }
         for (int j = 0; j < kMaxGridDims; ++j) {
             ds.gdim[j] = j < k ? dims[j].dim : 0;
             ds.origin[j] = j < k ? mm[2 * dims[j].dim] : 0;
@@ -495,16 +511,38 @@ struct Batch {
         ntree = uc[0];
         nbf = uc[1];
         if (ntree > 0) {
-            int64_t* d_slot = nullptr;
-            DPC_CK(tmp.get(&d_slot, B + 1));
-            DPC_CK(cudaMemcpyAsync(d_slot, h_slot_off.data(), sizeof(int64_t) * (B + 1), cudaMemcpyHostToDevice, st));
-            db.slot_off = d_slot;
-            db.leaf_slots = h_slot_off[B];
-            db.nodes = 2 * db.leaf_slots;
-            DPC_CK(tmp.get(&db.node_box, (size_t)db.nodes * 4));
-            DPC_CK(tmp.get(&db.node_minrank, db.nodes));
-            DPC_CK(tmp.get(&db.node_flag, db.nodes));
-            DPC_CK(cudaMemsetAsync(db.node_flag, 0, sizeof(uint32_t) * db.nodes, st));
+            // neighbouring lanes should search neighbouring points: sort the
+            // open list by sorted (Morton) position
+            {
+                uint32_t *ks = nullptr, *kt = nullptr, *vs = nullptr, *vt = nullptr;
+                void* t3 = nullptr;
+                DPC_CK(tmp.get(&ks, ntree));
+                DPC_CK(tmp.get(&kt, ntree));
+                DPC_CK(tmp.get(&vs, ntree));
+                DPC_CK(tmp.get(&vt, ntree));
+                DPC_CK(tmp.get(&t3, radix_sort_temp_bytes(ntree)));
+                DPC_CK(radix_sort_u32(db.tree_list, db.tree_list, ks, vs, kt, vt, ntree, bits_for((uint64_t)N),
+                                      t3, st));
+                db.tree_list = ks;
+            }
+            const int64_t nc = ncells;
+            db.ncells = nc;
+            db.dpb = 1;
+            for (int b = 0; b < B; ++b)
+                if (hd[b].dp == 2) db.dpb = 2;
+            DPC_CK(tmp.get(&db.cell_off, B + 1));
+            DPC_CK(tmp.get(&db.ckey, nc));
+            DPC_CK(tmp.get(&db.child, nc));
+            DPC_CK(tmp.get(&db.iparent, nc));
+            DPC_CK(tmp.get(&db.lparent, nc));
+            DPC_CK(tmp.get(&db.ibox, (size_t)nc * 2 * db.dpb));
+            DPC_CK(tmp.get(&db.lbox, (size_t)nc * 2 * db.dpb));
+            DPC_CK(tmp.get(&db.imin, nc));
+            DPC_CK(tmp.get(&db.lmin, nc));
+            DPC_CK(tmp.get(&db.flag, nc));
+            DPC_CK(cudaMemsetAsync(db.flag, 0, sizeof(uint32_t) * std::max<int64_t>(nc, 1), st));
+            DPC_CK(tmp.get(&db.stats, 2));
+            DPC_CK(cudaMemsetAsync(db.stats, 0, 2 * sizeof(unsigned long long), st));
             DPC_CK(launch_tree_build(v, db, st));
             DPC_CK(launch_tree_search(v, db, dim_mask, ntree, st));
         }
@@ -518,7 +556,11 @@ struct Batch {
             DPC_CK(launch_bruteforce(v, db, dim_mask, nbf, t2, st));
         }
         mark(3);
+        unsigned long long tstat[2] = {0, 0};
+        if (ntree > 0) DPC_CK(cudaMemcpyAsync(tstat, db.stats, sizeof(tstat), cudaMemcpyDeviceToHost, st));
         DPC_TRY(sync("dependent points"));
+        tree_visits = (int64_t)tstat[0];
+        tree_pairs = (int64_t)tstat[1];
         DPC_TRY(check_err("dependent points"));
         ms[2] = elapsed(0, 1);
         ms[3] = elapsed(1, 2);
@@ -707,6 +749,8 @@ dpc_status dpc_ds_info(const dpc_ds* ds, dpc_info* out) {
     out->ms_rest = bt.ms[4];
     out->ms_label = bt.ms[5];
     out->cand_pairs = bt.cand_pairs;
+    out->tree_visits = bt.tree_visits;
+    out->tree_pairs = bt.tree_pairs;
     return DPC_OK;
 }
 

@@ -14,18 +14,20 @@ struct CellWork {
     const uint32_t* ndense;     // device scalar
     const uint32_t* sparse;     // sparse cell ids
     const uint32_t* nsparse;    // device scalar
-    const uint2* runs;          // [ndense * kMaxNb] (start, count) of non-empty neighbour cells
-    const uint32_t* nruns;      // [ndense]
-    const uint32_t* cand;       // [ndense] candidate points per dense cell
+    const uint2* runs;          // [ncells * nbs] (start, count) of the non-empty neighbour cells of each cell
+    const uint32_t* nruns;      // [ncells]
+    const uint32_t* cand;       // [ncells] candidate points of each cell (sum of its runs)
     const uint4* items;         // (dense index, query chunk, candidate chunk, 0)
     const uint32_t* nitems;     // device scalar
     int kch;                    // candidates per dense work item
-    unsigned long long* stats;  // [0] dense, [1] sparse candidate pairs
+    int nbs;                    // run slots per cell: max over the batch of (2R+1)^k
+    unsigned long long* stats;  // [0] candidate pairs of all cells
 };
 
 // Cell coordinate of a point along gridded dim j.
 __device__ __forceinline__ int32_t cell_coord(const DsDesc& ds, int j, int32_t x) {
-    return (int32_t)(((int64_t)x - ds.origin[j]) / ds.s);
+    // x >= origin (the dataset's minimum) and s < 2^31: unsigned 32-bit division
+    return (int32_t)((uint32_t)(x - ds.origin[j]) / (uint32_t)ds.s);
 }
 
 // Coordinate k of the point whose first record is r.
@@ -59,6 +61,22 @@ __device__ __forceinline__ bool neighbour(const DsDesc& ds, const int32_t* c, in
     return gap2 < ds.d_cut2;
 }
 
+// Bits of gridded dim j inside a Morton code of k dims x mbits bits.
+__device__ __forceinline__ uint64_t morton_mask(int k, int mbits, int j) {
+    uint64_t m = 0;
+    for (int i = 0; i < mbits; ++i) m |= 1ull << (i * k + j);
+    return m;
+}
+
+// Morton code with the coordinate held in the bits `mask` moved by delta in
+// {-1, 0, +1} (the caller keeps the coordinate inside the grid): the carry or
+// borrow runs through the dim's bits only.
+__device__ __forceinline__ uint64_t morton_step(uint64_t code, uint64_t mask, int delta) {
+    if (delta > 0) return (((code | ~mask) + 1) & mask) | (code & ~mask);
+    if (delta < 0) return (((code & mask) - 1) & mask) | (code & ~mask);
+    return code;
+}
+
 __device__ __forceinline__ int num_neighbours(const DsDesc& ds) {
     int w = 2 * ds.R + 1, t = 1;
     for (int j = 0; j < ds.k; ++j) t *= w;
@@ -84,19 +102,23 @@ struct CellPrepBufs {
     uint32_t* sparse;     // [ncells_bound]
     uint32_t* ndense;     // scalar
     uint32_t* nsparse;    // scalar
-    uint2* runs;          // [ndense_bound * kMaxNb]
-    uint32_t* nruns;      // [ndense_bound]
-    uint32_t* cand;       // [ndense_bound]
+    uint2* runs;          // [ncells * nbs]
+    uint32_t* nruns;      // [ncells]
+    uint32_t* cand;       // [ncells]
     uint32_t* nitem_c;    // [ndense_bound] items per dense cell
     uint32_t* item_off;   // [ndense_bound]
     uint4* items;         // [nitems_bound]
     uint32_t* nitems;     // scalar
-    unsigned long long* stats;  // [0] += dense candidate pairs
+    int nbs;
+    unsigned long long* stats;  // [0] += candidate pairs
 };
 cudaError_t launch_classify_cells(const BatchView& v, const CellPrepBufs& cb, int64_t ncells_bound, void* scan_temp,
                                   cudaStream_t st);
-cudaError_t launch_dense_prep(const BatchView& v, const CellPrepBufs& cb, int64_t ndense_bound, int kch,
-                              void* scan_temp, cudaStream_t st);
+// Neighbour runs and candidate counts of every cell, then the dense items' counts.
+// kmask: bit K (1..4) = a dataset gridded in K dims with reach 1 is in the
+// batch; bit 0 = one with another reach or no gridded dim.
+cudaError_t launch_dense_prep(const BatchView& v, const CellPrepBufs& cb, int64_t ncells, int64_t ndense_bound,
+                              int kch, uint32_t kmask, void* scan_temp, cudaStream_t st);
 cudaError_t launch_fill_items(const BatchView& v, const CellPrepBufs& cb, int64_t ndense_bound, int kch,
                               cudaStream_t st);
 // class_mask bit 2*(d-1) + wide: a dataset of dimension d with 32-bit (wide = 0)
@@ -116,18 +138,29 @@ struct DeltaBufs {
     uint32_t* bf_sorted;  // [N]
     int4* rrec;           // [N * 2] records in rank order (prefix only)
     uint32_t* rorig;      // [N]
-    int4* node_box;       // [nodes * 4] lo[2], hi[2]
-    uint32_t* node_minrank;  // [nodes]
-    uint32_t* node_flag;  // [nodes]
-    int64_t nodes;
-    int64_t leaf_slots;
-    const int64_t* slot_off;   // [B+1] leaf-slot prefix per dataset (device)
     uint32_t bf_rank;     // points with rank below this go to the brute-force pass
+    // Radix tree over the cells of every dataset (tree.cu). Leaf c is cell c;
+    // internal node i (i in [first cell, last cell) of its dataset) is
+    // indexed by global cell index too. Boxes: 2 * dpb int4 (lo, then hi).
+    int dpb;              // int4 per box corner: 1 (all d <= 4) or 2
+    int64_t ncells;
+    int64_t* cell_off;    // [B+1] first cell of each dataset
+    uint64_t* ckey;       // [ncells] cell key
+    int2* child;          // [ncells] children of internal node i: >= 0 internal, < 0 leaf ~c
+    int32_t* iparent;     // [ncells] parent of internal node (-1: root)
+    int32_t* lparent;     // [ncells] parent of leaf (-1: single-cell dataset)
+    int4* ibox;           // [ncells * 2 * dpb]
+    int4* lbox;           // [ncells * 2 * dpb]
+    uint32_t* imin;       // [ncells] smallest rank below an internal node
+    uint32_t* lmin;       // [ncells] smallest rank in a cell
+    uint32_t* flag;       // [ncells] refit arrival counters
+    unsigned long long* stats;  // [0] tree nodes visited, [1] point pairs tested in leaves
 };
 cudaError_t launch_rank(const BatchView& v, const DeltaBufs& db, int key_bits, void* sort_temp, cudaStream_t st);
 cudaError_t launch_ring(const BatchView& v, const CellWork& w, uint32_t class_mask, int64_t nitems_bound,
                         int64_t nsparse_bound, uint32_t* counters, cudaStream_t st);
 cudaError_t launch_finalize(const BatchView& v, const DeltaBufs& db, cudaStream_t st);
+// tree.cu: build (cell ranges, keys, radix tree, refit) and search
 cudaError_t launch_tree_build(const BatchView& v, const DeltaBufs& db, cudaStream_t st);
 cudaError_t launch_tree_search(const BatchView& v, const DeltaBufs& db, uint32_t dim_mask, int64_t bound,
                                cudaStream_t st);

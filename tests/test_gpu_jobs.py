@@ -1,0 +1,146 @@
+"""Batched and served jobs: every dataset's result in a batch or in the
+served mix is the same bits as the dataset run alone, and as the oracle."""
+import threading
+
+import numpy as np
+import pytest
+
+import oracle
+import workloads
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def dpc():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2207_04649_gb300 as m
+    m.lib()
+    return m
+
+
+def small_problems(seed=40, count=14):
+    """Uneven n, d and d_cut in one batch (d 1..8, some tiny and empty)."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(count):
+        n = int(rng.choice([0, 1, 7, 150, 900, 2500, 4000]))
+        d = int(rng.integers(1, 9))
+        dc = int(rng.choice([60, 400, 1500, 6000]))
+        ds = workloads.random_blobs(seed * 100 + i, n, d, dc, blobs=int(rng.integers(1, 6)),
+                                    spread=float(rng.choice([0.01, 0.05, 0.2])), dup=3 if n > 10 else 0)
+        qs = [(2, dc + 1), (1, 4 * dc), (int(rng.integers(1, 6)), 10 * dc)][: 1 + i % 3]
+        out.append((ds.points, dc, qs))
+    return out
+
+
+def expected(points, dc, qs):
+    r = oracle.rho(points, dc)
+    dep, d2 = oracle.dependent(points, r)
+    labs = [oracle.label(r, dep, d2, a, b) for a, b in qs]
+    return r, dep, d2, labs
+
+
+def check_job(job, points, dc, qs):
+    r, dep, d2, labs = expected(points, dc, qs)
+    np.testing.assert_array_equal(job.rho, r)
+    np.testing.assert_array_equal(job.dep, dep)
+    np.testing.assert_array_equal(job.delta2, d2)
+    for q, (lab, nc) in enumerate(labs):
+        np.testing.assert_array_equal(job.label[q], lab)
+        assert job.n_centers[q] == nc
+
+
+def test_batched_flush_matches_oracle(dpc):
+    probs = small_problems()
+    with dpc.Context(0, mode=0) as ctx:
+        jobs = [dpc.Job(p, dc, qs) for p, dc, qs in probs]
+        for j in jobs:
+            ctx.submit(j)
+        ctx.flush()
+        for j, (p, dc, qs) in zip(jobs, probs):
+            s, res = ctx.poll(j.ticket)
+            assert s == dpc.DPC_OK and res.status == dpc.DPC_OK
+            check_job(j, p, dc, qs)
+
+
+def test_batch_equals_alone_on_blob_workload(dpc):
+    """A slice of the 256-problem batch: bits equal to each problem alone."""
+    probs = workloads.batch_256(count=12)
+    with dpc.Context(0, mode=0) as ctx:
+        jobs = [dpc.Job(ds.points, ds.d_cut, [(ds.rho_min, ds.delta_min)]) for ds in probs]
+        for j in jobs:
+            ctx.submit(j)
+        ctx.flush()
+    for j, ds in zip(jobs, probs):
+        alone = dpc.cluster(ds.points, ds.d_cut, ds.rho_min, ds.delta_min)
+        np.testing.assert_array_equal(j.rho, alone["rho"])
+        np.testing.assert_array_equal(j.dep, alone["dep"])
+        np.testing.assert_array_equal(j.delta2, alone["delta2"])
+        np.testing.assert_array_equal(j.label[0], alone["label"])
+        assert j.n_centers[0] == alone["n_centers"]
+    # and the smallest ones against the oracle
+    for j, ds in sorted(zip(jobs, probs), key=lambda t: t[1].n)[:3]:
+        check_job(j, ds.points, ds.d_cut, [(ds.rho_min, ds.delta_min)])
+
+
+def test_served_mode_concurrent_submitters(dpc):
+    probs = small_problems(seed=41, count=20)
+    with dpc.Context(0, mode=1, max_inflight=3) as ctx:
+        jobs = [dpc.Job(p, dc, qs) for p, dc, qs in probs]
+        lock = threading.Lock()
+
+        def submit(chunk):
+            for j in chunk:
+                with lock:
+                    pass
+                ctx.submit(j)
+
+        threads = [threading.Thread(target=submit, args=(jobs[i::4],)) for i in range(4)]
+        for t in threads:
+            t.start()
+        for t in threads:
+            t.join()
+        for j in jobs:
+            s, res = ctx.wait(j.ticket, 120000)
+            assert s == dpc.DPC_OK, dpc.dpc_last_error()
+            assert res.run_ms >= 0.0 and res.queue_ms >= 0.0
+    for j, (p, dc, qs) in zip(jobs, probs):
+        check_job(j, p, dc, qs)
+
+
+def test_served_admission_under_small_cap(dpc):
+    """A cap that fits about one job at a time still finishes every job;
+    a job that can never fit is refused at submit."""
+    probs = small_problems(seed=42, count=6)
+    cap = 40 << 20
+    with dpc.Context(0, mode=1, hbm_cap_bytes=cap, max_inflight=2) as ctx:
+        jobs = [dpc.Job(p, dc, qs) for p, dc, qs in probs]
+        for j in jobs:
+            ctx.submit(j)
+        for j in jobs:
+            s, _ = ctx.wait(j.ticket, 120000)
+            assert s == dpc.DPC_OK
+        big = dpc.Job(np.zeros((2_000_000, 8), np.int32), 10, [(1, 11)])
+        with pytest.raises(dpc.DpcError) as e:
+            ctx.submit(big)
+        assert e.value.status == dpc.DPC_ERR_CAPACITY
+    for j, (p, dc, qs) in zip(jobs, probs):
+        check_job(j, p, dc, qs)
+
+
+def test_poll_unknown_ticket_and_wait_timeout(dpc):
+    with dpc.Context(0, mode=0) as ctx:
+        s, _ = ctx.poll(987654)
+        assert s == dpc.DPC_ERR_STATE
+        j = dpc.Job(np.zeros((10, 2), np.int32), 5, [(1, 6)])
+        ctx.submit(j)
+        s, _ = ctx.poll(j.ticket)
+        assert s == dpc.DPC_PENDING          # batched mode: nothing runs before flush
+        s, _ = ctx.wait(j.ticket, 10)
+        assert s == dpc.DPC_ERR_TIMEOUT
+        ctx.flush()
+        s, _ = ctx.poll(j.ticket)
+        assert s == dpc.DPC_OK
