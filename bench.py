@@ -279,7 +279,7 @@ def run_ours(args):
                           for k in ("ms_grid", "ms_rho", "ms_rank", "ms_ring", "ms_rest", "ms_label")},
             "work": {k: infos[-1][k] for k in ("cells", "dense_cells", "work_items", "cand_pairs",
                                                "open_after_ring", "brute_points", "grid_dims", "pair_bits",
-                                               "tree_visits", "tree_pairs")},
+                                               "tree_visits", "tree_pairs", "open_after_coarse")},
             "cpu_baseline": cpu,
             "clocks": clk,
             "gpu_launches": launches,

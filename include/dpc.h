@@ -131,12 +131,26 @@ typedef struct {
     float ms_grid, ms_rho, ms_rank, ms_ring, ms_rest, ms_label;  /* stage times when profiling is on */
     int64_t tree_visits;      /* tree nodes visited by the search for open points */
     int64_t tree_pairs;       /* point pairs it tested */
+    int64_t open_after_coarse;  /* points the coarse ring left for the tree search */
 } dpc_info;
 
 dpc_status dpc_ds_info(const dpc_ds* ds, dpc_info* out);
 
 /* Enable per-stage CUDA-event timing on a context (0 off, 1 on). */
 dpc_status dpc_set_profiling(dpc_ctx* ctx, int on);
+
+/* Tuning knobs of a context (no counterpart in the paper; they change speed,
+ * never results). Keys and ranges:
+ *   "kch"     candidates per dense work item, 32 .. 2^20 (default 2048)
+ *   "kmax"    gridded dimensions at most, 1 .. 4 (default 4)
+ *   "bf_rank" points still open after the ring search whose rank is below
+ *             this take the brute-force pass (default 1024)
+ *   "clevel"  coarse ring over blocks of 2^clevel cells per gridded dim,
+ *             0 .. 8 (default 0: off)
+ *   "ccap"    coarse cells with more points are not scanned (default 512)
+ * DPC_ERR_INVALID_ARG for an unknown key or a value out of range. */
+dpc_status dpc_set_tuning(dpc_ctx* ctx, const char* key, int64_t value);
+dpc_status dpc_get_tuning(dpc_ctx* ctx, const char* key, int64_t* value);
 
 /* Number of CUDA kernels this library has launched in this process so far
  * (all contexts and threads); a difference of two readings counts the

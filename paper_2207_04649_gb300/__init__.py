@@ -16,5 +16,5 @@ from ._binding import (  # noqa: F401
     DPC_ERR_STATE, DPC_ERR_CAPACITY, INT64_MAX, DpcError, Context, Dataset, Job, cluster, lib,
     dpc_create, dpc_destroy, dpc_density, dpc_dependent, dpc_label, dpc_release, dpc_ds_info,
     dpc_set_profiling, dpc_submit, dpc_poll, dpc_flush, dpc_wait, dpc_last_error, library_path,
-    dpc_kernel_launches, dpc_probe_pair_rate,
+    dpc_kernel_launches, dpc_probe_pair_rate, dpc_set_tuning, dpc_get_tuning,
 )

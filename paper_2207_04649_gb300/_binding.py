@@ -46,7 +46,8 @@ class DpcInfo(ctypes.Structure):
                 ("grid_dims", ctypes.c_int32), ("pair_bits", ctypes.c_int32),
                 ("ms_grid", ctypes.c_float), ("ms_rho", ctypes.c_float), ("ms_rank", ctypes.c_float),
                 ("ms_ring", ctypes.c_float), ("ms_rest", ctypes.c_float), ("ms_label", ctypes.c_float),
-                ("tree_visits", ctypes.c_int64), ("tree_pairs", ctypes.c_int64)]
+                ("tree_visits", ctypes.c_int64), ("tree_pairs", ctypes.c_int64),
+                ("open_after_coarse", ctypes.c_int64)]
 
     def as_dict(self) -> dict:
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -96,6 +97,8 @@ def lib():
             "dpc_flush": ([vp], st),
             "dpc_wait": ([vp, ctypes.c_uint64, i64, ctypes.POINTER(DpcResult)], st),
             "dpc_kernel_launches": ([], i64),
+            "dpc_set_tuning": ([vp, ctypes.c_char_p, i64], st),
+            "dpc_get_tuning": ([vp, ctypes.c_char_p, ctypes.POINTER(i64)], st),
             "dpc_probe_pair_rate": ([ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
                                      ctypes.POINTER(ctypes.c_double)], st),
         }
@@ -170,6 +173,16 @@ def dpc_ds_info(ds) -> dict:
 
 def dpc_set_profiling(ctx, on: bool):
     return _check(lib().dpc_set_profiling(ctx, 1 if on else 0), "dpc_set_profiling")
+
+
+def dpc_set_tuning(ctx, key: str, value: int):
+    return _check(lib().dpc_set_tuning(ctx, key.encode(), int(value)), "dpc_set_tuning")
+
+
+def dpc_get_tuning(ctx, key: str) -> int:
+    v = ctypes.c_int64(0)
+    _check(lib().dpc_get_tuning(ctx, key.encode(), ctypes.byref(v)), "dpc_get_tuning")
+    return int(v.value)
 
 
 def dpc_submit(ctx, job: "DpcJob") -> int:
@@ -277,6 +290,14 @@ class Context:
         self._order_after_torch(points, rho_out)
         h = dpc_density(self.handle, pp, n, d, int(d_cut), dev, rp)
         return Dataset(self, h, n, dev)
+
+    def tune(self, **knobs):
+        """Set tuning knobs (speed only; results are unchanged)."""
+        for k, val in knobs.items():
+            dpc_set_tuning(self.handle, k, val)
+
+    def tuning(self, key: str) -> int:
+        return dpc_get_tuning(self.handle, key)
 
     def submit(self, job: "Job") -> int:
         t = dpc_submit(self.handle, job.c)

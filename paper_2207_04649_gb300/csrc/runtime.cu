@@ -97,6 +97,8 @@ struct Tune {
     int kch = 2048;         // candidates per dense work item
     int kmax = 4;           // gridded dims at most
     uint32_t bf_rank = 1024;  // open points ranked below this take the brute-force pass
+    int clevel = 0;           // coarse ring: blocks of 2^clevel cells per gridded dim (0: off)
+    uint32_t ccap = 512;      // coarse cells holding more points are not scanned
 };
 
 }  // namespace
@@ -151,7 +153,7 @@ struct Batch {
     uint32_t class_mask = 0, dim_mask = 0;
     int64_t ncells = 0, ndense = 0, nsparse = 0, nitems = 0, ntree = 0, nbf = 0;
     int64_t cand_pairs = 0;
-    int64_t tree_visits = 0, tree_pairs = 0;
+    int64_t tree_visits = 0, tree_pairs = 0, ntree2 = 0;
     unsigned long long* d_stats = nullptr;
     uint32_t* d_counters = nullptr;  // [16] rho + [16] ring
     int out_is_device = 0;
@@ -499,10 +501,11 @@ struct Batch {
         DPC_CK(launch_ring(v, w, class_mask, nitems, nsparse, d_counters + 16, st));
         mark(2);
 
-        DPC_CK(tmp.get(&db.ucount, 2));
+        DPC_CK(tmp.get(&db.ucount, 4));
         DPC_CK(tmp.get(&db.tree_list, N));
         DPC_CK(tmp.get(&db.bf_list, N));
-        DPC_CK(cudaMemsetAsync(db.ucount, 0, 2 * sizeof(uint32_t), st));
+        DPC_CK(cudaMemsetAsync(db.ucount, 0, 4 * sizeof(uint32_t), st));
+        db.tcount = db.ucount;
         db.bf_rank = ctx->tune.bf_rank;
         DPC_CK(launch_finalize(v, db, st));
         uint32_t uc[2] = {0, 0};
@@ -527,6 +530,36 @@ struct Batch {
             }
             const int64_t nc = ncells;
             db.ncells = nc;
+            // coarse ring over blocks of 2^clevel cells per gridded dim
+            if (ctx->tune.clevel > 0) {
+                db.clevel = ctx->tune.clevel;
+                db.ccap = ctx->tune.ccap;
+                uint32_t* d_nco = nullptr;
+                void* t4 = nullptr;
+                DPC_CK(tmp.get(&db.cflag, nc));
+                DPC_CK(tmp.get(&db.cidx, nc));
+                DPC_CK(tmp.get(&db.cfirst, nc + 1));
+                DPC_CK(tmp.get(&d_nco, 1));
+                DPC_CK(tmp.get(&t4, scan_temp_bytes(nc)));
+                DPC_CK(launch_coarse_cells(v, db, t4, st));
+                uint32_t nco = 0;
+                {
+                    uint32_t last[2] = {0, 0};
+                    DPC_CK(cudaMemcpyAsync(&last[0], db.cidx + nc - 1, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
+                    DPC_TRY(sync("coarse cells"));
+                    nco = last[0] + 1;  // coarse index of the last cell, plus one
+                }
+                db.ncoarse = nco;
+                const int cbits = ceil_log2((uint64_t)std::max<int64_t>(2 * (int64_t)nco, 2));
+                DPC_CK(tmp.get(&db.chash, (size_t)1 << cbits));
+                db.chmask = (1ull << cbits) - 1;
+                DPC_CK(cudaMemsetAsync(db.chash, 0xff, sizeof(int4) << cbits, st));
+                DPC_CK(launch_coarse_hash(v, db, st));
+                DPC_CK(tmp.get(&db.open2, ntree));
+                DPC_CK(launch_coarse_ring(v, db, dim_mask, ntree, st));
+                db.tree_list = db.open2;
+                db.tcount = db.ucount + 2;
+            }
             db.dpb = 1;
             for (int b = 0; b < B; ++b)
                 if (hd[b].dp == 2) db.dpb = 2;
@@ -535,10 +568,7 @@ struct Batch {
             DPC_CK(tmp.get(&db.child, nc));
             DPC_CK(tmp.get(&db.iparent, nc));
             DPC_CK(tmp.get(&db.lparent, nc));
-            DPC_CK(tmp.get(&db.ibox, (size_t)nc * 2 * db.dpb));
-            DPC_CK(tmp.get(&db.lbox, (size_t)nc * 2 * db.dpb));
-            DPC_CK(tmp.get(&db.imin, nc));
-            DPC_CK(tmp.get(&db.lmin, nc));
+            DPC_CK(tmp.get(&db.nodes, (size_t)2 * nc * (2 * db.dpb + 1)));
             DPC_CK(tmp.get(&db.flag, nc));
             DPC_CK(cudaMemsetAsync(db.flag, 0, sizeof(uint32_t) * std::max<int64_t>(nc, 1), st));
             DPC_CK(tmp.get(&db.stats, 2));
@@ -557,10 +587,15 @@ struct Batch {
         }
         mark(3);
         unsigned long long tstat[2] = {0, 0};
-        if (ntree > 0) DPC_CK(cudaMemcpyAsync(tstat, db.stats, sizeof(tstat), cudaMemcpyDeviceToHost, st));
+        uint32_t open2 = 0;
+        if (ntree > 0) {
+            DPC_CK(cudaMemcpyAsync(tstat, db.stats, sizeof(tstat), cudaMemcpyDeviceToHost, st));
+            DPC_CK(cudaMemcpyAsync(&open2, db.tcount, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
+        }
         DPC_TRY(sync("dependent points"));
         tree_visits = (int64_t)tstat[0];
         tree_pairs = (int64_t)tstat[1];
+        ntree2 = open2;
         DPC_TRY(check_err("dependent points"));
         ms[2] = elapsed(0, 1);
         ms[3] = elapsed(1, 2);
@@ -658,6 +693,32 @@ dpc_status dpc_set_profiling(dpc_ctx* ctx, int on) {
     return DPC_OK;
 }
 
+dpc_status dpc_set_tuning(dpc_ctx* ctx, const char* key, int64_t value) {
+    if (!ctx || !key) return fail(DPC_ERR_INVALID_ARG, "ctx or key is NULL");
+    const std::string k(key);
+    dpc::Tune& t = ctx->tune;
+    if (k == "kch" && value >= 32 && value <= (1 << 20)) t.kch = (int)value;
+    else if (k == "kmax" && value >= 1 && value <= dpc::kMaxGridDims) t.kmax = (int)value;
+    else if (k == "bf_rank" && value >= 0 && value <= UINT32_MAX) t.bf_rank = (uint32_t)value;
+    else if (k == "clevel" && value >= 0 && value <= 8) t.clevel = (int)value;
+    else if (k == "ccap" && value >= 1 && value <= (1 << 24)) t.ccap = (uint32_t)value;
+    else return fail(DPC_ERR_INVALID_ARG, "unknown tuning key or value out of range: " + k);
+    return DPC_OK;
+}
+
+dpc_status dpc_get_tuning(dpc_ctx* ctx, const char* key, int64_t* value) {
+    if (!ctx || !key || !value) return fail(DPC_ERR_INVALID_ARG, "NULL argument");
+    const std::string k(key);
+    const dpc::Tune& t = ctx->tune;
+    if (k == "kch") *value = t.kch;
+    else if (k == "kmax") *value = t.kmax;
+    else if (k == "bf_rank") *value = t.bf_rank;
+    else if (k == "clevel") *value = t.clevel;
+    else if (k == "ccap") *value = t.ccap;
+    else return fail(DPC_ERR_INVALID_ARG, "unknown tuning key: " + k);
+    return DPC_OK;
+}
+
 static dpc_status check_input(const int32_t* points, int64_t n, int32_t d, int64_t d_cut) {
     if (n < 0 || n >= (1ll << 31)) return fail(DPC_ERR_INVALID_ARG, "n must be in [0, 2^31)");
     if (d < 1 || d > 8) return fail(DPC_ERR_INVALID_ARG, "d must be in [1, 8]");
@@ -751,6 +812,7 @@ dpc_status dpc_ds_info(const dpc_ds* ds, dpc_info* out) {
     out->cand_pairs = bt.cand_pairs;
     out->tree_visits = bt.tree_visits;
     out->tree_pairs = bt.tree_pairs;
+    out->open_after_coarse = bt.ntree2;
     return DPC_OK;
 }
 

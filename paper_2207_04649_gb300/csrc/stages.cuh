@@ -131,8 +131,20 @@ cudaError_t launch_rho_scatter(const BatchView& v, cudaStream_t st);
 struct DeltaBufs {
     uint32_t* rkeys;      // rank sort keys [N] (u32 or u64 storage)
     uint32_t* rvals;      // [N]
-    uint32_t* ucount;     // [2] device counters: tree list, brute list
-    uint32_t* tree_list;  // [N]
+    uint32_t* ucount;     // [3] device counters: open list, brute list, open after the coarse ring
+    uint32_t* tree_list;  // [N] points open after the ring search
+    const uint32_t* tcount;  // count of the list the tree search reads
+    // coarse ring (coarse.cu): cells are aligned blocks of 2^clevel grid
+    // cells per gridded dim, contiguous in the Morton-sorted order
+    int clevel;
+    uint32_t ccap;        // coarse cells holding more points are not scanned
+    int64_t ncoarse;
+    uint32_t* cflag;      // [ncells] first fine cell of a coarse cell
+    uint32_t* cidx;       // [ncells] coarse cell of each fine cell
+    uint32_t* cfirst;     // [ncoarse + 1] first fine cell of each coarse cell
+    int4* chash;          // {key lo, key hi, point start, point count}
+    uint64_t chmask;
+    uint32_t* open2;      // [N] points still open after the coarse ring
     uint32_t* bf_list;    // [N]
     uint32_t* bf_keys;    // [N]
     uint32_t* bf_sorted;  // [N]
@@ -149,10 +161,11 @@ struct DeltaBufs {
     int2* child;          // [ncells] children of internal node i: >= 0 internal, < 0 leaf ~c
     int32_t* iparent;     // [ncells] parent of internal node (-1: root)
     int32_t* lparent;     // [ncells] parent of leaf (-1: single-cell dataset)
-    int4* ibox;           // [ncells * 2 * dpb]
-    int4* lbox;           // [ncells * 2 * dpb]
-    uint32_t* imin;       // [ncells] smallest rank below an internal node
-    uint32_t* lmin;       // [ncells] smallest rank in a cell
+    // Node records: internal node i at record i, leaf c at record ncells + c;
+    // each 2 * dpb + 1 int4: box lo, box hi, then {smallest rank, left, right,
+    // parent} for an internal node or {smallest rank, first point, end point,
+    // parent} for a leaf. One record is one memory round trip in the search.
+    int4* nodes;
     uint32_t* flag;       // [ncells] refit arrival counters
     unsigned long long* stats;  // [0] tree nodes visited, [1] point pairs tested in leaves
 };
@@ -160,6 +173,12 @@ cudaError_t launch_rank(const BatchView& v, const DeltaBufs& db, int key_bits, v
 cudaError_t launch_ring(const BatchView& v, const CellWork& w, uint32_t class_mask, int64_t nitems_bound,
                         int64_t nsparse_bound, uint32_t* counters, cudaStream_t st);
 cudaError_t launch_finalize(const BatchView& v, const DeltaBufs& db, cudaStream_t st);
+// coarse.cu: coarse cells (after the fine cell table), their hash, and the
+// coarse ring search of the open list (needs db.ncells, tree_list sorted)
+cudaError_t launch_coarse_cells(const BatchView& v, const DeltaBufs& db, void* scan_temp, cudaStream_t st);
+cudaError_t launch_coarse_hash(const BatchView& v, const DeltaBufs& db, cudaStream_t st);
+cudaError_t launch_coarse_ring(const BatchView& v, const DeltaBufs& db, uint32_t dim_mask, int64_t bound,
+                               cudaStream_t st);
 // tree.cu: build (cell ranges, keys, radix tree, refit) and search
 cudaError_t launch_tree_build(const BatchView& v, const DeltaBufs& db, cudaStream_t st);
 cudaError_t launch_tree_search(const BatchView& v, const DeltaBufs& db, uint32_t dim_mask, int64_t bound,

@@ -1,4 +1,4 @@
-// Expanding search for the dependent points the ring search left open.
+// Expanding search for the dependent points the ring searches left open.
 //
 // A binary radix tree over the Morton-ordered cells of each dataset: leaf c
 // is grid cell c (a contiguous run of sorted points), and every internal
@@ -7,9 +7,10 @@
 // sorted unique cell keys (each internal node finds its key range and split
 // point by binary searches on common-prefix lengths, the construction of
 // Karras, "Maximizing parallelism in the construction of BVHs, octrees, and
-// k-d trees", HPG 2012), then refitted bottom-up: every node stores the
-// bounding box of its points and the smallest rank (highest density) among
-// them.
+// k-d trees", HPG 2012), then refitted bottom-up: every node record holds
+// the bounding box of its points, the smallest rank (highest density) among
+// them, and its children (or, for a leaf, its run of points), so that one
+// node costs one memory round trip in the search.
 //
 // The search is the nearest-neighbour search among higher-ranked points that
 // Ex-DPC runs on its incrementally built kd-tree (Section 3, steps 3-4),
@@ -111,12 +112,17 @@ __global__ void k_radix_tree(BatchView v, DeltaBufs db) {
     if (i == c0) db.iparent[i] = -1;
 }
 
-// Leaf boxes and smallest ranks, then a bottom-up refit: the second child to
-// arrive at a node computes it.
+// Record index of a node reference: internal i >= 0, leaf ~c.
+__device__ __forceinline__ int64_t rec_of(const DeltaBufs& db, int32_t ref) {
+    return ref >= 0 ? (int64_t)ref : db.ncells + (int64_t)(~ref);
+}
+
+// Leaf records, then a bottom-up refit: the second child to arrive at a node
+// writes the node's record.
 __global__ void k_refit(BatchView v, DeltaBufs db) {
     const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= db.ncells) return;
-    const int dpb = db.dpb;
+    const int dpb = db.dpb, ns = 2 * dpb + 1;
     const int b = find_off(db.cell_off, v.B, c);
     const DsDesc& ds = v.desc[b];
     int32_t lo[8], hi[8];
@@ -139,62 +145,49 @@ __global__ void k_refit(BatchView v, DeltaBufs db) {
         }
         mr = min(mr, v.ro_s[p].x);
     }
-    int4* lb = db.lbox + c * 2 * dpb;
-    lb[0] = make_int4(lo[0], lo[1], lo[2], lo[3]);
-    if (dpb == 2) lb[1] = make_int4(lo[4], lo[5], lo[6], lo[7]);
-    lb[dpb] = make_int4(hi[0], hi[1], hi[2], hi[3]);
-    if (dpb == 2) lb[dpb + 1] = make_int4(hi[4], hi[5], hi[6], hi[7]);
-    db.lmin[c] = mr;
-    int32_t node = db.lparent[c];
+    const int32_t lpar = db.lparent[c];
+    int4* lr = db.nodes + (db.ncells + c) * ns;
+    lr[0] = make_int4(lo[0], lo[1], lo[2], lo[3]);
+    if (dpb == 2) lr[1] = make_int4(lo[4], lo[5], lo[6], lo[7]);
+    lr[dpb] = make_int4(hi[0], hi[1], hi[2], hi[3]);
+    if (dpb == 2) lr[dpb + 1] = make_int4(hi[4], hi[5], hi[6], hi[7]);
+    lr[2 * dpb] = make_int4((int)mr, (int)p0, (int)p1, lpar);
+    int32_t node = lpar;
     while (node >= 0) {
         __threadfence();
         if (atomicAdd(&db.flag[node], 1u) == 0u) return;
         __threadfence();
         const int2 ch = __ldcg(&db.child[node]);
-        const int4* cb[2];
-        uint32_t cm[2];
-        const int32_t kids[2] = {ch.x, ch.y};
-        for (int q = 0; q < 2; ++q) {
-            if (kids[q] < 0) {
-                cb[q] = db.lbox + (int64_t)(~kids[q]) * 2 * dpb;
-                cm[q] = __ldcg(&db.lmin[~kids[q]]);
-            } else {
-                cb[q] = db.ibox + (int64_t)kids[q] * 2 * dpb;
-                cm[q] = __ldcg(&db.imin[kids[q]]);
-            }
-        }
-        int4* nb = db.ibox + (int64_t)node * 2 * dpb;
+        const int4* ca = db.nodes + rec_of(db, ch.x) * ns;
+        const int4* cb = db.nodes + rec_of(db, ch.y) * ns;
+        int4* nr = db.nodes + (int64_t)node * ns;
         for (int q = 0; q < 2 * dpb; ++q) {
-            const int4 x = __ldcg(cb[0] + q), y = __ldcg(cb[1] + q);
-            nb[q] = q < dpb ? make_int4(min(x.x, y.x), min(x.y, y.y), min(x.z, y.z), min(x.w, y.w))
+            const int4 x = __ldcg(ca + q), y = __ldcg(cb + q);
+            nr[q] = q < dpb ? make_int4(min(x.x, y.x), min(x.y, y.y), min(x.z, y.z), min(x.w, y.w))
                             : make_int4(max(x.x, y.x), max(x.y, y.y), max(x.z, y.z), max(x.w, y.w));
         }
-        db.imin[node] = min(cm[0], cm[1]);
-        node = __ldcg(&db.iparent[node]);
+        const uint32_t m0 = (uint32_t)__ldcg(ca + 2 * dpb).x, m1 = (uint32_t)__ldcg(cb + 2 * dpb).x;
+        const int32_t par = __ldcg(&db.iparent[node]);
+        nr[2 * dpb] = make_int4((int)min(m0, m1), ch.x, ch.y, par);
+        node = par;
     }
 }
 
+// Loads a node record: squared distance from x to its box (INT64_MAX when
+// nothing in it ranks above `rank`) and its meta word.
 template <int D>
-__device__ __forceinline__ void load_box(const int4* box, int dpb, int32_t (&lo)[D], int32_t (&hi)[D]) {
-    const int4 l0 = box[0], h0 = box[dpb];
-    int32_t a[8] = {l0.x, l0.y, l0.z, l0.w, 0, 0, 0, 0};
-    int32_t z[8] = {h0.x, h0.y, h0.z, h0.w, 0, 0, 0, 0};
+__device__ __forceinline__ long long node_test(const int4* rec, int dpb, const int32_t (&x)[D], uint32_t rank,
+                                               int4& meta) {
+    const int4 l0 = rec[0], h0 = rec[dpb];
+    int32_t lo[8] = {l0.x, l0.y, l0.z, l0.w, 0, 0, 0, 0};
+    int32_t hi[8] = {h0.x, h0.y, h0.z, h0.w, 0, 0, 0, 0};
     if (D > 4) {
-        const int4 l1 = box[1], h1 = box[dpb + 1];
-        a[4] = l1.x; a[5] = l1.y; a[6] = l1.z; a[7] = l1.w;
-        z[4] = h1.x; z[5] = h1.y; z[6] = h1.z; z[7] = h1.w;
+        const int4 l1 = rec[1], h1 = rec[dpb + 1];
+        lo[4] = l1.x; lo[5] = l1.y; lo[6] = l1.z; lo[7] = l1.w;
+        hi[4] = h1.x; hi[5] = h1.y; hi[6] = h1.z; hi[7] = h1.w;
     }
-#pragma unroll
-    for (int k = 0; k < D; ++k) {
-        lo[k] = a[k];
-        hi[k] = z[k];
-    }
-}
-
-template <int D>
-__device__ __forceinline__ long long box_dist(const int4* box, int dpb, const int32_t (&x)[D]) {
-    int32_t lo[D], hi[D];
-    load_box<D>(box, dpb, lo, hi);
+    meta = rec[2 * dpb];
+    if ((uint32_t)meta.x >= rank) return INT64_MAX;
     long long s = 0;
 #pragma unroll
     for (int k = 0; k < D; ++k) {
@@ -204,29 +197,13 @@ __device__ __forceinline__ long long box_dist(const int4* box, int dpb, const in
     return s;
 }
 
-// The ball of squared radius r2 around x lies inside the box in every
-// gridded dimension (bit k of gmask).
-template <int D>
-__device__ __forceinline__ bool ball_inside(const int4* box, int dpb, const int32_t (&x)[D], uint32_t gmask,
-                                            long long r2) {
-    int32_t lo[D], hi[D];
-    load_box<D>(box, dpb, lo, hi);
-#pragma unroll
-    for (int k = 0; k < D; ++k) {
-        if (!((gmask >> k) & 1u)) continue;
-        const long long a = (long long)x[k] - lo[k], b = (long long)hi[k] - x[k];
-        if (a < 0 || b < 0 || a * a < r2 || b * b < r2) return false;
-    }
-    return true;
-}
-
 constexpr int kStack = 96;
 
 template <int D>
 __global__ void __launch_bounds__(128) k_tree_search(BatchView v, DeltaBufs db) {
     constexpr int DP = D <= 4 ? 1 : 2;
-    const uint32_t cnt = db.ucount[0];
-    const int dpb = db.dpb;
+    const uint32_t cnt = *db.tcount;
+    const int dpb = db.dpb, ns = 2 * dpb + 1;
     unsigned long long visits = 0, tests = 0;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < cnt; i += (int64_t)gridDim.x * blockDim.x) {
         const uint32_t p = db.tree_list[i];
@@ -246,56 +223,47 @@ __global__ void __launch_bounds__(128) k_tree_search(BatchView v, DeltaBufs db) 
         }
         int32_t stack[kStack];
         const int64_t c0 = db.cell_off[b], c1 = db.cell_off[b + 1];
-        {
-            int sp = 0;
-            stack[sp++] = c1 - c0 >= 2 ? (int32_t)c0 : ~(int32_t)c0;  // the dataset's root
-            while (sp > 0) {
-                const int32_t nd = stack[--sp];
-                ++visits;
-                if (nd < 0) {
-                    const int32_t c = ~nd;
-                    if (db.lmin[c] >= ro.x) continue;
-                    if (box_dist<D>(db.lbox + (int64_t)c * 2 * dpb, dpb, x) > bestD) continue;
-                    const uint32_t q1 = v.cell_start[c + 1];
-                    for (uint32_t q = v.cell_start[c]; q < q1; ++q) {
-                        const uint2 cr = v.ro_s[q];
-                        if (cr.x >= ro.x) continue;
-                        ++tests;
-                        int32_t cx[D];
-                        t_load<D>(recb + (int64_t)q * DP, cx);
-                        long long dd = 0;
+        int sp = 0;
+        stack[sp++] = c1 - c0 >= 2 ? (int32_t)c0 : ~(int32_t)c0;  // the dataset's root
+        while (sp > 0) {
+            const int32_t nd = stack[--sp];
+            ++visits;
+            int4 meta;
+            if (node_test<D>(db.nodes + rec_of(db, nd) * ns, dpb, x, ro.x, meta) > bestD) continue;
+            if (nd < 0) {  // a cell: scan its points
+                for (int32_t q = meta.y; q < meta.z; ++q) {
+                    const uint2 cr = v.ro_s[q];
+                    if (cr.x >= ro.x) continue;
+                    ++tests;
+                    int32_t cx[D];
+                    t_load<D>(recb + (int64_t)q * DP, cx);
+                    long long dd = 0;
 #pragma unroll
-                        for (int k = 0; k < D; ++k) {
-                            const long long e = (long long)x[k] - cx[k];
-                            dd += e * e;
-                        }
-                        if (dd < bestD || (dd == bestD && cr.y < bestJ)) {
-                            bestD = dd;
-                            bestJ = cr.y;
-                        }
+                    for (int k = 0; k < D; ++k) {
+                        const long long e = (long long)x[k] - cx[k];
+                        dd += e * e;
                     }
-                    continue;
+                    if (dd < bestD || (dd == bestD && cr.y < bestJ)) {
+                        bestD = dd;
+                        bestJ = cr.y;
+                    }
                 }
-                if (db.imin[nd] >= ro.x) continue;
-                if (box_dist<D>(db.ibox + (int64_t)nd * 2 * dpb, dpb, x) > bestD) continue;
-                if (sp + 2 > kStack) {
-                    atomicOr(v.err, kErrTreeStack);
-                    continue;
-                }
-                const int2 cc = db.child[nd];
-                long long dk[2];
-                const int32_t kid[2] = {cc.x, cc.y};
-#pragma unroll
-                for (int q = 0; q < 2; ++q) {
-                    const bool leaf = kid[q] < 0;
-                    const int64_t id = leaf ? ~kid[q] : kid[q];
-                    const uint32_t mr = leaf ? db.lmin[id] : db.imin[id];
-                    dk[q] = mr < ro.x ? box_dist<D>((leaf ? db.lbox : db.ibox) + id * 2 * dpb, dpb, x) : INT64_MAX;
-                }
-                // push the farther child first so the nearer one is searched first
-                const int nearer = dk[1] < dk[0] ? 1 : 0;
-                if (dk[1 - nearer] <= bestD) stack[sp++] = kid[1 - nearer];
-                if (dk[nearer] <= bestD) stack[sp++] = kid[nearer];
+                continue;
+            }
+            if (sp + 2 > kStack) {
+                atomicOr(v.err, kErrTreeStack);
+                continue;
+            }
+            // both children's records in one round; the nearer is searched first
+            int4 m0, m1;
+            const long long d0 = node_test<D>(db.nodes + rec_of(db, meta.y) * ns, dpb, x, ro.x, m0);
+            const long long d1 = node_test<D>(db.nodes + rec_of(db, meta.z) * ns, dpb, x, ro.x, m1);
+            if (d1 < d0) {
+                if (d0 <= bestD) stack[sp++] = meta.y;
+                if (d1 <= bestD) stack[sp++] = meta.z;
+            } else {
+                if (d1 <= bestD) stack[sp++] = meta.z;
+                if (d0 <= bestD) stack[sp++] = meta.y;
             }
         }
         const int64_t g = ds.pt_off + ro.y;

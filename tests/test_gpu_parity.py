@@ -250,3 +250,41 @@ def test_plain_5p8m_3d_sampled(dpc):
     """20k-point seeded sample, as specified for sets past 2M points."""
     info = check_sampled(dpc, workloads.plain_5p8m_3d(), 20_000, 32)
     assert info["n"] == 5_800_000
+
+
+# ------------------------------------------------------- tuning knobs
+
+@pytest.mark.parametrize("knobs", [dict(clevel=2, ccap=512), dict(clevel=1, ccap=64, bf_rank=0),
+                                   dict(kch=64, bf_rank=100000), dict(kmax=2), dict(kmax=1, clevel=3)],
+                         ids=lambda k: ",".join(f"{a}={b}" for a, b in k.items()))
+def test_tuning_knobs_do_not_change_results(dpc, knobs):
+    ds = workloads.random_blobs(77, 6000, 3, 900, blobs=5, spread=0.06, dup=8)
+    q = [(3, 3 * 900)]
+    base = run_host(dpc, ds.points, ds.d_cut, q)
+    pts = np.ascontiguousarray(ds.points)
+    n = pts.shape[0]
+    with dpc.Context(0) as ctx:
+        ctx.tune(**knobs)
+        for k, val in knobs.items():
+            assert ctx.tuning(k) == val
+        rho = np.empty(n, np.int32)
+        h = ctx.density(pts, ds.d_cut, rho)
+        dep = np.empty(n, np.int32)
+        d2 = np.empty(n, np.int64)
+        h.dependent(dep, d2)
+        lab = np.empty(n, np.int32)
+        nc = h.label(*q[0], lab)
+        h.release()
+    np.testing.assert_array_equal(rho, base[0])
+    np.testing.assert_array_equal(dep, base[1])
+    np.testing.assert_array_equal(d2, base[2])
+    np.testing.assert_array_equal(lab, base[3][0][0])
+    assert nc == base[3][0][1]
+
+
+def test_tuning_rejects_unknown_keys(dpc):
+    with dpc.Context(0) as ctx:
+        with pytest.raises(dpc.DpcError):
+            ctx.tune(nonsense=3)
+        with pytest.raises(dpc.DpcError):
+            ctx.tune(kmax=9)
