@@ -117,6 +117,33 @@ dpc_status dpc_label(dpc_ds* ds, int64_t rho_min, int64_t delta_min, int32_t* la
 /* Free a dataset's device state. The handle is invalid afterwards. */
 dpc_status dpc_release(dpc_ds* ds);
 
+/* Labels with no device allocation. The paper has no counterpart: this is a
+ * variant of the labels step (the same result as dpc_label) for callers that
+ * cannot allocate device memory when they call, e.g. code running on a
+ * device budget reserved up front, in a section that must not allocate, or
+ * under a memory pool that fails once exhausted. Its scratch (the parent of
+ * every point) is a fixed array compiled into the library: 2^22 points
+ * (16 MiB), held on every GPU that loads the library until the process
+ * exits.
+ *   rho, dep, delta2: device arrays of n points as dpc_density /
+ *            dpc_dependent produce them (dep = -1 and delta2 = INT64_MAX for
+ *            the densest point); read only.
+ *   n:       0 <= n <= 4194304; larger n gives DPC_ERR_INVALID_ARG.
+ *   rho_min, delta_min: as dpc_label; 1 <= delta_min <= 3037000499 (the
+ *            caller keeps delta_min > d_cut).
+ *   label_out: device array of n int32 (center's index, -1 noise).
+ *   n_centers_out: NULL or one device int64.
+ *   cuda_stream: the cudaStream_t the work is queued on (NULL: the legacy
+ *            default stream). The call returns once the work is queued.
+ * The first call on a device looks up the scratch's device address for that
+ * device (cudaGetSymbolAddress, with the device current); make that first
+ * call before any stream capture. All calls share the scratch and it keeps
+ * the last call's contents, so calls that overlap on the GPU race. It calls
+ * no cudaMalloc, cudaFree or allocating library routine. */
+dpc_status dpc_label_static(const int32_t* rho, const int32_t* dep, const int64_t* delta2, int64_t n,
+                            int64_t rho_min, int64_t delta_min, int32_t* label_out, int64_t* n_centers_out,
+                            void* cuda_stream);
+
 /* Counters of the last run on a dataset (sizes of the work, for reporting). */
 typedef struct {
     int64_t n;
