@@ -159,6 +159,8 @@ typedef struct {
     int64_t tree_visits;      /* tree nodes visited by the search for open points */
     int64_t tree_pairs;       /* point pairs it tested */
     int64_t open_after_coarse;  /* points the coarse ring left for the tree search */
+    int32_t pair_mode;        /* density pair test: 0 direct 32-bit, 1 direct 64-bit, 2 expanded 32-bit */
+    int32_t reserved;
 } dpc_info;
 
 dpc_status dpc_ds_info(const dpc_ds* ds, dpc_info* out);
@@ -187,10 +189,12 @@ int64_t dpc_kernel_launches(void);
 /* Measurement helper (no counterpart in the paper): the throughput of the
  * density stage's 32-bit pair test for d-dimensional points with operands in
  * registers on every SM of `device`, i.e. the integer-ALU ceiling that the
- * density kernel is compared against. Writes pairs per second (and the
- * kernel's time in ms when ms is not NULL). Allocates and frees a few bytes
- * of device memory; synchronizes the device's default stream. */
-dpc_status dpc_probe_pair_rate(int device, int d, double* pairs_per_s, double* ms);
+ * density kernel is compared against. mode 0: the direct form (sum of
+ * squared differences); mode 2: the expanded form around a cell corner
+ * (d <= 3), the one dpc_ds_info reports as pair_mode 2. Writes pairs per
+ * second (and the kernel's time in ms when ms is not NULL). Allocates and
+ * frees a few bytes of device memory; synchronizes the device. */
+dpc_status dpc_probe_pair_rate(int device, int d, int mode, double* pairs_per_s, double* ms);
 
 /* ---------------------------------------------------------------------
  * Jobs: many independent datasets, batched or served.

@@ -47,7 +47,7 @@ class DpcInfo(ctypes.Structure):
                 ("ms_grid", ctypes.c_float), ("ms_rho", ctypes.c_float), ("ms_rank", ctypes.c_float),
                 ("ms_ring", ctypes.c_float), ("ms_rest", ctypes.c_float), ("ms_label", ctypes.c_float),
                 ("tree_visits", ctypes.c_int64), ("tree_pairs", ctypes.c_int64),
-                ("open_after_coarse", ctypes.c_int64)]
+                ("open_after_coarse", ctypes.c_int64), ("pair_mode", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
     def as_dict(self) -> dict:
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -99,7 +99,7 @@ def lib():
             "dpc_kernel_launches": ([], i64),
             "dpc_set_tuning": ([vp, ctypes.c_char_p, i64], st),
             "dpc_get_tuning": ([vp, ctypes.c_char_p, ctypes.POINTER(i64)], st),
-            "dpc_probe_pair_rate": ([ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
+            "dpc_probe_pair_rate": ([ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
                                      ctypes.POINTER(ctypes.c_double)], st),
         }
         for name, (args, res) in sig.items():
@@ -114,10 +114,11 @@ def dpc_kernel_launches() -> int:
     return int(lib().dpc_kernel_launches())
 
 
-def dpc_probe_pair_rate(device: int, d: int):
-    """(pairs/s, ms) of the register-resident 32-bit pair test on every SM."""
+def dpc_probe_pair_rate(device: int, d: int, mode: int = 0):
+    """(pairs/s, ms) of the register-resident 32-bit pair test on every SM
+    (mode 0 direct form, mode 2 expanded form for d <= 3)."""
     r, t = ctypes.c_double(0), ctypes.c_double(0)
-    _check(lib().dpc_probe_pair_rate(device, d, ctypes.byref(r), ctypes.byref(t)), "dpc_probe_pair_rate")
+    _check(lib().dpc_probe_pair_rate(device, d, mode, ctypes.byref(r), ctypes.byref(t)), "dpc_probe_pair_rate")
     return r.value, t.value
 
 

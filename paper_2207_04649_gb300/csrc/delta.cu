@@ -30,8 +30,7 @@ namespace dpc {
 
 namespace {
 
-constexpr int kThreads = 256;
-constexpr int kCb = 128;
+constexpr int kRingThreads = 128;  // 4 warps per block, double-buffered chunks each
 constexpr unsigned long long kNoBest = ~0ull;
 constexpr uint32_t kSat = 0xffffffffu;
 
@@ -109,35 +108,53 @@ __global__ void k_ro(BatchView v) {
 
 // ----------------------------------------------------------- ring search
 
-// Q queries per lane (or one per lane in G groups) against staged
-// candidates grp, grp + G, ...: keeps the least packed key of a higher point.
-template <int D, bool W64, int Q, int G>
-__device__ __forceinline__ void eval_ring(const int4* buf, const uint2* rbuf, int nb, int grp,
-                                          const int32_t (&qx)[4][D], const uint32_t (&qr)[4],
+// Q queries per lane against staged candidates grp, grp + G, ...: keeps the
+// least packed key (min(D, 2^32-1) << 32 | original index) of a higher point.
+// Forms: direct 32-bit (MODE 0), direct 64-bit saturated (MODE 1), and
+// expanded around the query cell's corner (MODE 2, d <= 3: a staged candidate
+// is (c', |c'|^2), a query keeps -2 q' and |q'|^2; D = |c'|^2 + |q'|^2 - 2 q'.c').
+template <int D, int MODE, int Q>
+__device__ __forceinline__ void eval_ring(const int4* buf, const uint2* rbuf, int nb, int grp, int G,
+                                          const int32_t (&qx)[4][D], const int32_t (&qa)[4][3],
+                                          const int32_t (&qn)[4], const uint32_t (&qr)[4],
                                           unsigned long long (&best)[4]) {
     constexpr int DP = D <= 4 ? 1 : 2;
 #pragma unroll 2
     for (int j = grp; j < nb; j += G) {
-        int32_t c[D];
-        load_pt<D>(buf + j * DP, c);
         const uint2 ro = rbuf[j];
+        if (MODE == 2) {
+            const int4 c = buf[j];
 #pragma unroll
-        for (int t = 0; t < Q; ++t) {
-            const uint32_t dd = dist_sat<D, W64>(qx[t], c);
-            const unsigned long long key = ((unsigned long long)dd << 32) | ro.y;
-            if (ro.x < qr[t] && key < best[t]) best[t] = key;
+            for (int t = 0; t < Q; ++t) {
+                int s = c.w + qn[t];
+                s += c.x * qa[t][0];
+                if (D > 1) s += c.y * qa[t][1];
+                if (D > 2) s += c.z * qa[t][2];
+                const unsigned long long key = ((unsigned long long)(uint32_t)s << 32) | ro.y;
+                if (ro.x < qr[t] && key < best[t]) best[t] = key;
+            }
+        } else {
+            int32_t c[D];
+            load_pt<D>(buf + j * DP, c);
+#pragma unroll
+            for (int t = 0; t < Q; ++t) {
+                const uint32_t dd = dist_sat<D, MODE == 1>(qx[t], c);
+                const unsigned long long key = ((unsigned long long)dd << 32) | ro.y;
+                if (ro.x < qr[t] && key < best[t]) best[t] = key;
+            }
         }
     }
 }
 
-template <int D, bool W64>
-__global__ void __launch_bounds__(kThreads) k_ring_dense(BatchView v, CellWork w, uint32_t* counter) {
+template <int D, int MODE>
+__global__ void __launch_bounds__(kRingThreads) k_ring_dense(BatchView v, CellWork w, uint32_t* counter) {
     constexpr int DP = D <= 4 ? 1 : 2;
-    __shared__ int4 sbuf[kThreads / 32][kCb * DP];
-    __shared__ uint2 srb[kThreads / 32][kCb];
-    const int lane = threadIdx.x & 31;
-    int4* buf = sbuf[threadIdx.x >> 5];
-    uint2* rbuf = srb[threadIdx.x >> 5];
+    constexpr bool EXP = MODE == 2;
+    __shared__ int4 sbuf[kRingThreads / 32][2][kChunk * DP];
+    __shared__ uint2 srb[kRingThreads / 32][2][kChunk];
+    __shared__ uint2 sruns[kRingThreads / 32][kMaxNb];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    uint2* srun = sruns[wid];
     const uint32_t nitems = *w.nitems;
     while (true) {
         uint32_t it = 0;
@@ -150,12 +167,12 @@ __global__ void __launch_bounds__(kThreads) k_ring_dense(BatchView v, CellWork w
         const uint32_t cs = v.cell_start[c], m = v.cell_start[c + 1] - cs;
         const int b = find_ds(v.pt_off, v.B, cs);
         const DsDesc& ds = v.desc[b];
-        if (ds.d != D || (ds.w32 == 0) != W64) continue;
+        if (ds.d != D || ds.mode != MODE) continue;
         const int4* recb = v.rec + ds.rec_off - ds.pt_off * DP;
         const int q0 = (int)qc * kQch;
         const int nq = min(kQch, (int)m - q0);
-        const int Q = nq >= 32 ? (nq + 31) >> 5 : 1;
-        const int Mq = nq >= 32 ? 32 : (nq <= 8 ? 8 : (nq <= 16 ? 16 : 32));
+        int Q, Mq;
+        lane_layout(nq, Q, Mq);
         const int G = 32 / Mq;
         const int grp = lane / Mq, ql = lane & (Mq - 1);
         int32_t qx[4][D];
@@ -163,64 +180,87 @@ __global__ void __launch_bounds__(kThreads) k_ring_dense(BatchView v, CellWork w
         unsigned long long best[4];
 #pragma unroll
         for (int t = 0; t < 4; ++t) {
-            const int qi = min(G == 1 ? lane + 32 * t : ql, nq - 1);
+            const int qi = min(ql * Q + t, nq - 1);
             load_pt<D>(recb + ((int64_t)cs + q0 + qi) * DP, qx[t]);
             qr[t] = v.ro_s[cs + q0 + qi].x;
             best[t] = kNoBest;
         }
-        const uint2* runs = w.runs + (int64_t)c * w.nbs;
+        int32_t org[3] = {0, 0, 0};
+        int32_t qa[4][3], qn[4];
+        if (EXP) {
+#pragma unroll
+            for (int k = 0; k < D && k < 3; ++k) org[k] = ds.lo[k];
+            for (int j = 0; j < ds.k; ++j) {
+                const int g = ds.gdim[j];
+                const int32_t cc = cell_coord(ds, j, rec_coord(recb + (int64_t)cs * DP, g));
+                const int32_t corner = ds.origin[j] + cc * (int32_t)ds.s;
+#pragma unroll
+                for (int k = 0; k < 3; ++k)
+                    if (k == g) org[k] = corner;
+            }
+#pragma unroll
+            for (int t = 0; t < 4; ++t) {
+                int32_t nrm = 0;
+#pragma unroll
+                for (int k = 0; k < 3; ++k) {
+                    const int32_t qk = k < D ? qx[t][k < D ? k : 0] - org[k] : 0;
+                    qa[t][k] = -2 * qk;
+                    nrm += qk * qk;
+                }
+                qn[t] = nrm;
+            }
+        }
         const uint32_t nr = w.nruns[c], ctot = w.cand[c];
+        for (uint32_t t = lane; t < nr; t += 32) srun[t] = w.runs[(int64_t)c * w.nbs + t];
+        __syncwarp();
         const uint32_t k0 = kc * (uint32_t)w.kch;
-        uint32_t remaining = min(ctot, k0 + (uint32_t)w.kch) - k0;
-        uint32_t ri = 0, roff = k0;
-        while (ri < nr) {
-            const uint32_t len = runs[ri].y;
-            if (roff < len) break;
-            roff -= len;
-            ++ri;
-        }
-        while (remaining > 0u) {
-            int nb = 0;
-            while (nb < kCb && remaining > 0u) {
-                const uint2 run = ri < nr ? runs[ri] : make_uint2(0u, 0u);
-                const uint32_t take = ri < nr ? min(min(run.y - roff, (uint32_t)(kCb - nb)), remaining) : 0u;
-                if (take == 0u) {  // runs exhausted early: cannot happen when counts agree
-                    if (lane == 0) atomicOr(v.err, kErrStaging);
-                    remaining = 0u;
-                    break;
-                }
-                const int4* src = recb + ((int64_t)run.x + roff) * DP;
-                for (uint32_t t = lane; t < take * DP; t += 32) buf[nb * DP + t] = __ldg(src + t);
-                for (uint32_t t = lane; t < take; t += 32) rbuf[nb + t] = v.ro_s[run.x + roff + t];
-                nb += (int)take;
-                roff += take;
-                remaining -= take;
-                if (roff == run.y) {
-                    ++ri;
-                    roff = 0;
+        CandStream<DP, true> cst;
+        cst.init(srun, nr, k0, min(ctot, k0 + (uint32_t)w.kch));
+        bool bad = false;
+        bool have = cst.prep(lane, recb, v.ro_s, &bad);
+        int sb = 0;
+        while (have) {
+            int4* buf = sbuf[wid][sb];
+            uint2* rbuf = srb[wid][sb];
+            const int nb = (int)cst.cnt;
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int f = lane + 32 * u;
+                if (f < nb) {
+                    if (EXP) {
+                        const int4 r = cst.r[u][0];
+                        const int32_t cx = r.x - org[0], cy = D > 1 ? r.y - org[1] : 0, cz = D > 2 ? r.z - org[2] : 0;
+                        buf[f] = make_int4(cx, cy, cz, cx * cx + cy * cy + cz * cz);
+                    } else {
+#pragma unroll
+                        for (int q = 0; q < DP; ++q) buf[f * DP + q] = cst.r[u][q];
+                    }
+                    rbuf[f] = cst.ro[u];
                 }
             }
             __syncwarp();
-            if (G == 4) eval_ring<D, W64, 1, 4>(buf, rbuf, nb, grp, qx, qr, best);
-            else if (G == 2) eval_ring<D, W64, 1, 2>(buf, rbuf, nb, grp, qx, qr, best);
-            else switch (Q) {
-                case 1: eval_ring<D, W64, 1, 1>(buf, rbuf, nb, 0, qx, qr, best); break;
-                case 2: eval_ring<D, W64, 2, 1>(buf, rbuf, nb, 0, qx, qr, best); break;
-                case 3: eval_ring<D, W64, 3, 1>(buf, rbuf, nb, 0, qx, qr, best); break;
-                default: eval_ring<D, W64, 4, 1>(buf, rbuf, nb, 0, qx, qr, best); break;
+            have = cst.prep(lane, recb, v.ro_s, &bad);
+            sb ^= 1;
+            switch (Q) {
+                case 1: eval_ring<D, MODE, 1>(buf, rbuf, nb, grp, G, qx, qa, qn, qr, best); break;
+                case 2: eval_ring<D, MODE, 2>(buf, rbuf, nb, grp, G, qx, qa, qn, qr, best); break;
+                case 3: eval_ring<D, MODE, 3>(buf, rbuf, nb, grp, G, qx, qa, qn, qr, best); break;
+                default: eval_ring<D, MODE, 4>(buf, rbuf, nb, grp, G, qx, qa, qn, qr, best); break;
             }
-            __syncwarp();
         }
-        if (G > 1) {
+        if (bad && lane == 0) atomicOr(v.err, kErrStaging);
+        __syncwarp();
+        // least key over the groups, then one lane per query writes
+#pragma unroll
+        for (int t = 0; t < 4; ++t)
             for (int o = Mq; o < 32; o <<= 1) {
-                const unsigned long long y = __shfl_xor_sync(0xffffffffu, best[0], o);
-                if (y < best[0]) best[0] = y;
+                const unsigned long long y = __shfl_xor_sync(0xffffffffu, best[t], o);
+                if (y < best[t]) best[t] = y;
             }
-            if (grp == 0 && ql < nq && best[0] != kNoBest) atomicMin(&v.best_s[cs + q0 + ql], best[0]);
-        } else {
+        if (grp == 0) {
 #pragma unroll
             for (int t = 0; t < 4; ++t)
-                if (lane + 32 * t < nq && best[t] != kNoBest) atomicMin(&v.best_s[cs + q0 + lane + 32 * t], best[t]);
+                if (t < Q && ql * Q + t < nq && best[t] != kNoBest) atomicMin(&v.best_s[cs + q0 + ql * Q + t], best[t]);
         }
     }
 }
@@ -416,17 +456,19 @@ __global__ void __launch_bounds__(kBfThreads) k_bruteforce(BatchView v, DeltaBuf
     }
 }
 
+template <int D, int MODE>
+void launch_ring_dense(const BatchView& v, const CellWork& w, int64_t nitems_bound, uint32_t* counter,
+                       cudaStream_t st) {
+    if (nitems_bound <= 0) return;
+    const unsigned blocks = (unsigned)std::max<int64_t>(1, std::min<int64_t>(152 * 16, (nitems_bound + 3) / 4));
+    (k_ring_dense<D, MODE><<<blocks, kRingThreads, 0, st>>>(v, w, counter), note_launch());
+}
+
 template <int D, bool W64>
-void launch_ring_class(const BatchView& v, const CellWork& w, int64_t nitems_bound, int64_t nsparse_bound,
-                       uint32_t* counter, cudaStream_t st) {
-    if (nitems_bound > 0) {
-        const unsigned blocks = (unsigned)std::max<int64_t>(1, std::min<int64_t>(152 * 8, (nitems_bound + 7) / 8));
-        (k_ring_dense<D, W64><<<blocks, kThreads, 0, st>>>(v, w, counter), note_launch());
-    }
-    if (nsparse_bound > 0) {
-        const unsigned blocks = (unsigned)std::min<int64_t>(152 * 32, grid_for(nsparse_bound, 256));
-        (k_ring_sparse<D, W64><<<blocks, 256, 0, st>>>(v, w), note_launch());
-    }
+void launch_ring_sparse(const BatchView& v, const CellWork& w, int64_t nsparse_bound, cudaStream_t st) {
+    if (nsparse_bound <= 0) return;
+    const unsigned blocks = (unsigned)std::min<int64_t>(152 * 32, grid_for(nsparse_bound, 256));
+    (k_ring_sparse<D, W64><<<blocks, 256, 0, st>>>(v, w), note_launch());
 }
 
 }  // namespace
@@ -460,14 +502,22 @@ cudaError_t launch_rank(const BatchView& v, const DeltaBufs& db, int rbits, void
 
 cudaError_t launch_ring(const BatchView& v, const CellWork& w, uint32_t class_mask, int64_t nitems_bound,
                         int64_t nsparse_bound, uint32_t* counters, cudaStream_t st) {
-#define DPC_RING_CLASS(D)                                                                             \
-    if (class_mask & (1u << (2 * (D - 1))))                                                           \
-        launch_ring_class<D, false>(v, w, nitems_bound, nsparse_bound, counters + 2 * (D - 1), st);   \
-    if (class_mask & (1u << (2 * (D - 1) + 1)))                                                       \
-        launch_ring_class<D, true>(v, w, nitems_bound, nsparse_bound, counters + 2 * (D - 1) + 1, st);
+    // dense: one launch per (dimension, mode) class; sparse: modes 0 and 2
+    // share the 32-bit kernel, mode 1 is 64-bit
+#define DPC_BIT(D, M) (class_mask & (1u << (3 * ((D) - 1) + (M))))
+#define DPC_RING_CLASS(D)                                                                                 \
+    if (DPC_BIT(D, 0)) launch_ring_dense<D, 0>(v, w, nitems_bound, counters + 3 * (D - 1), st);           \
+    if (DPC_BIT(D, 1)) launch_ring_dense<D, 1>(v, w, nitems_bound, counters + 3 * (D - 1) + 1, st);       \
+    if (DPC_BIT(D, 0) || DPC_BIT(D, 2)) launch_ring_sparse<D, false>(v, w, nsparse_bound, st);            \
+    if (DPC_BIT(D, 1)) launch_ring_sparse<D, true>(v, w, nsparse_bound, st);
+#define DPC_RING_X(D) \
+    if (DPC_BIT(D, 2)) launch_ring_dense<D, 2>(v, w, nitems_bound, counters + 3 * (D - 1) + 2, st);
     DPC_RING_CLASS(1) DPC_RING_CLASS(2) DPC_RING_CLASS(3) DPC_RING_CLASS(4)
     DPC_RING_CLASS(5) DPC_RING_CLASS(6) DPC_RING_CLASS(7) DPC_RING_CLASS(8)
+    DPC_RING_X(1) DPC_RING_X(2) DPC_RING_X(3)
+#undef DPC_RING_X
 #undef DPC_RING_CLASS
+#undef DPC_BIT
     return cudaGetLastError();
 }
 

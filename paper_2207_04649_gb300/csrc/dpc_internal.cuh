@@ -43,6 +43,9 @@ struct DsDesc {
     int32_t mbits;        // Morton bits per gridded dim
     int32_t R;            // neighbour reach in cells
     int32_t w32;          // all candidate pair sums fit 31 bits
+    int32_t mode;         // density pair test: 0 direct 32-bit, 1 direct 64-bit,
+                          // 2 expanded 32-bit around the query cell's corner (d <= 3)
+    int32_t lo[kMaxDims]; // smallest coordinate per dim
     int32_t h;            // tree height: 2^h leaf slots
     int32_t nleaf;        // leaves (ceil(n / kLeaf))
     int32_t rbits;        // bits of the density key in the rank sort

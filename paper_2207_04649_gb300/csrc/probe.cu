@@ -1,13 +1,15 @@
 // Throughput probe for the density stage's pair test.
 //
-// Every thread keeps 4 query points and 16 candidate points in registers and
-// applies the exact 32-bit test of the density kernel (sum of squared
-// coordinate differences minus d_cut^2, sign bit accumulated) to all 64
-// pairs per sweep, on every SM. The queries move by one unit after each
-// sweep, depending on the counts, so nothing can be hoisted out of the loop.
-// The rate it reports is the integer-ALU ceiling of that instruction mix on
-// this GPU at its current clock: the denominator of the density kernel's
-// roofline.
+// Every thread keeps 4 queries and 16 candidates in registers and applies the
+// density kernel's 32-bit pair test to all 64 pairs per sweep, on every SM,
+// in one of the kernel's two forms:
+//   direct   (mode 0): sign of sum_k (q_k - c_k)^2 - d_cut^2;
+//   expanded (mode 2, d <= 3): sign of |c'|^2 + (|q'|^2 - d_cut^2) + sum_k c'_k (-2 q'_k).
+// After each sweep every query operand moves by an amount that depends on
+// the counts, so no part of a pair test can be hoisted out of the loop (this
+// costs d + 1 adds per query per 16 pairs, charged to the probe). The rate it
+// reports is the integer-ALU ceiling of that instruction mix on this GPU at
+// its current clock: the denominator of the density kernel's roofline.
 #include "dpc.h"
 #include "dpc_internal.cuh"
 
@@ -42,7 +44,56 @@ __global__ void __launch_bounds__(256) k_pair_probe(const int32_t* __restrict__ 
                 cnt[i] += (uint32_t)s >> 31;
             }
 #pragma unroll
-        for (int i = 0; i < 4; ++i) q[i][0] += (int)(cnt[i] & 1u);
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int k = 0; k < D; ++k) q[i][k] += (int)(cnt[i] & 1u);
+    }
+    if (cnt[0] + cnt[1] + cnt[2] + cnt[3] == 0xdeadbeefu) sink[0] = t;
+}
+
+template <int D>
+__global__ void __launch_bounds__(256) k_pair_probe_x(const int32_t* __restrict__ seed, int iters, int T,
+                                                     unsigned long long* __restrict__ sink) {
+    int32_t qa[4][3], qb[4];
+    int4 c[16];
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        int32_t n = -T;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            const int32_t x = k < D ? seed[(t * 7 + i * 3 + k) & 1023] : 0;
+            qa[i][k] = -2 * x;
+            n += x * x;
+        }
+        qb[i] = n;
+    }
+#pragma unroll
+    for (int j = 0; j < 16; ++j) {
+        const int32_t x = seed[(t * 13 + j * 3 + 512) & 1023];
+        const int32_t y = D > 1 ? seed[(t * 13 + j * 3 + 513) & 1023] : 0;
+        const int32_t z = D > 2 ? seed[(t * 13 + j * 3 + 514) & 1023] : 0;
+        c[j] = make_int4(x, y, z, x * x + y * y + z * z);
+    }
+    uint32_t cnt[4] = {0u, 0u, 0u, 0u};
+    for (int it = 0; it < iters; ++it) {
+#pragma unroll
+        for (int j = 0; j < 16; ++j)
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                int s = c[j].w + qb[i];
+                s += c[j].x * qa[i][0];
+                if (D > 1) s += c[j].y * qa[i][1];
+                if (D > 2) s += c[j].z * qa[i][2];
+                cnt[i] += (uint32_t)s >> 31;
+            }
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const int32_t m = (int32_t)(cnt[i] & 1u);
+            qb[i] += m;
+#pragma unroll
+            for (int k = 0; k < D; ++k) qa[i][k] += m;
+        }
     }
     if (cnt[0] + cnt[1] + cnt[2] + cnt[3] == 0xdeadbeefu) sink[0] = t;
 }
@@ -50,9 +101,10 @@ __global__ void __launch_bounds__(256) k_pair_probe(const int32_t* __restrict__ 
 }  // namespace
 }  // namespace dpc
 
-extern "C" dpc_status dpc_probe_pair_rate(int device, int d, double* pairs_per_s, double* ms) {
+extern "C" dpc_status dpc_probe_pair_rate(int device, int d, int mode, double* pairs_per_s, double* ms) {
     using namespace dpc;
-    if (!pairs_per_s || d < 1 || d > 8) return DPC_ERR_INVALID_ARG;
+    if (!pairs_per_s || d < 1 || d > 8 || (mode != 0 && mode != 2) || (mode == 2 && d > 3))
+        return DPC_ERR_INVALID_ARG;
     if (cudaSetDevice(device) != cudaSuccess) return DPC_ERR_CUDA;
     int sms = 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
@@ -71,15 +123,23 @@ extern "C" dpc_status dpc_probe_pair_rate(int device, int d, double* pairs_per_s
     cudaEventCreate(&a);
     cudaEventCreate(&b);
     auto launch = [&](int it) {
-        switch (d) {
-            case 1: k_pair_probe<1><<<blocks, threads>>>(seed, it, 90000, sink); break;
-            case 2: k_pair_probe<2><<<blocks, threads>>>(seed, it, 90000, sink); break;
-            case 3: k_pair_probe<3><<<blocks, threads>>>(seed, it, 90000, sink); break;
-            case 4: k_pair_probe<4><<<blocks, threads>>>(seed, it, 90000, sink); break;
-            case 5: k_pair_probe<5><<<blocks, threads>>>(seed, it, 90000, sink); break;
-            case 6: k_pair_probe<6><<<blocks, threads>>>(seed, it, 90000, sink); break;
-            case 7: k_pair_probe<7><<<blocks, threads>>>(seed, it, 90000, sink); break;
-            default: k_pair_probe<8><<<blocks, threads>>>(seed, it, 90000, sink); break;
+        if (mode == 2) {
+            switch (d) {
+                case 1: k_pair_probe_x<1><<<blocks, threads>>>(seed, it, 90000, sink); break;
+                case 2: k_pair_probe_x<2><<<blocks, threads>>>(seed, it, 90000, sink); break;
+                default: k_pair_probe_x<3><<<blocks, threads>>>(seed, it, 90000, sink); break;
+            }
+        } else {
+            switch (d) {
+                case 1: k_pair_probe<1><<<blocks, threads>>>(seed, it, 90000, sink); break;
+                case 2: k_pair_probe<2><<<blocks, threads>>>(seed, it, 90000, sink); break;
+                case 3: k_pair_probe<3><<<blocks, threads>>>(seed, it, 90000, sink); break;
+                case 4: k_pair_probe<4><<<blocks, threads>>>(seed, it, 90000, sink); break;
+                case 5: k_pair_probe<5><<<blocks, threads>>>(seed, it, 90000, sink); break;
+                case 6: k_pair_probe<6><<<blocks, threads>>>(seed, it, 90000, sink); break;
+                case 7: k_pair_probe<7><<<blocks, threads>>>(seed, it, 90000, sink); break;
+                default: k_pair_probe<8><<<blocks, threads>>>(seed, it, 90000, sink); break;
+            }
         }
         note_launch();
     };

@@ -34,8 +34,7 @@ namespace dpc {
 
 namespace {
 
-constexpr int kRhoThreads = 256;
-constexpr int kCb = 128;  // staged candidates per warp
+constexpr int kRhoThreads = 128;  // 4 warps per block, double-buffered chunks each
 
 __global__ void k_classify(BatchView v, uint32_t* __restrict__ dflag, uint32_t* __restrict__ sflag, int64_t bound) {
     const uint32_t nc = *v.ncells;
@@ -228,9 +227,10 @@ __device__ __forceinline__ uint32_t inside(const int32_t (&q)[D], const int32_t 
     }
 }
 
-// Q queries per lane against staged candidates grp, grp + G, ...
-template <int D, bool W64, int Q, int G>
-__device__ __forceinline__ void eval_rho(const int4* buf, int nb, int grp, const int32_t (&qx)[4][D],
+// Q queries per lane against staged candidates grp, grp + G, ... (direct
+// test: sum of squared differences against d_cut^2).
+template <int D, bool W64, int Q>
+__device__ __forceinline__ void eval_rho(const int4* buf, int nb, int grp, int G, const int32_t (&qx)[4][D],
                                          uint32_t (&cnt)[4], int64_t T) {
     constexpr int DP = D <= 4 ? 1 : 2;
 #pragma unroll 4
@@ -242,12 +242,38 @@ __device__ __forceinline__ void eval_rho(const int4* buf, int nb, int grp, const
     }
 }
 
-template <int D, bool W64>
+// Expanded test (d <= 3). Coordinates are relative to the query cell's
+// corner; a staged candidate is (c'_0, c'_1, c'_2, |c'|^2) and a query keeps
+// a_k = -2 q'_k and b = |q'|^2 - d_cut^2, so that
+//   |q - c|^2 - d_cut^2 = |c'|^2 + b + sum_k c'_k a_k,
+// whose sign bit is the pair test: one add and d multiply-adds.
+template <int D, int Q>
+__device__ __forceinline__ void eval_rho_x(const int4* buf, int nb, int grp, int G, const int32_t (&qa)[4][3],
+                                           const int32_t (&qb)[4], uint32_t (&cnt)[4]) {
+#pragma unroll 4
+    for (int j = grp; j < nb; j += G) {
+        const int4 c = buf[j];
+#pragma unroll
+        for (int t = 0; t < Q; ++t) {
+            int s = c.w + qb[t];
+            s += c.x * qa[t][0];
+            if (D > 1) s += c.y * qa[t][1];
+            if (D > 2) s += c.z * qa[t][2];
+            cnt[t] += (uint32_t)s >> 31;
+        }
+    }
+}
+
+
+template <int D, int MODE>
 __global__ void __launch_bounds__(kRhoThreads) k_rho_dense(BatchView v, CellWork w, uint32_t* counter) {
     constexpr int DP = D <= 4 ? 1 : 2;
-    __shared__ int4 sbuf[kRhoThreads / 32][kCb * DP];
-    const int lane = threadIdx.x & 31;
-    int4* buf = sbuf[threadIdx.x >> 5];
+    constexpr bool W64 = MODE == 1;
+    constexpr bool EXP = MODE == 2;
+    __shared__ int4 sbuf[kRhoThreads / 32][2][kChunk * DP];  // double buffer per warp
+    __shared__ uint2 sruns[kRhoThreads / 32][kMaxNb];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    uint2* srun = sruns[wid];
     const uint32_t nitems = *w.nitems;
     while (true) {
         uint32_t it = 0;
@@ -260,73 +286,104 @@ __global__ void __launch_bounds__(kRhoThreads) k_rho_dense(BatchView v, CellWork
         const uint32_t cs = v.cell_start[c], m = v.cell_start[c + 1] - cs;
         const int b = find_ds(v.pt_off, v.B, cs);
         const DsDesc& ds = v.desc[b];
-        if (ds.d != D || (ds.w32 == 0) != W64) continue;
+        if (ds.d != D || ds.mode != MODE) continue;
         const int4* recb = v.rec + ds.rec_off - ds.pt_off * DP;  // indexed by global sorted position
         const int q0 = (int)qc * kQch;
         const int nq = min(kQch, (int)m - q0);
-        // lane layout: nq >= 32: Q = ceil(nq / 32) queries per lane; otherwise
-        // G groups of Mq lanes, one query per lane, candidates split by group
-        const int Q = nq >= 32 ? (nq + 31) >> 5 : 1;
-        const int Mq = nq >= 32 ? 32 : (nq <= 8 ? 8 : (nq <= 16 ? 16 : 32));
+        int Q, Mq;
+        lane_layout(nq, Q, Mq);
         const int G = 32 / Mq;
         const int grp = lane / Mq, ql = lane & (Mq - 1);
+        // query t of this lane: ql * Q + t (slots at or past nq are dummies)
         int32_t qx[4][D];
 #pragma unroll
-        for (int t = 0; t < 4; ++t) {
-            const int qi = min(G == 1 ? lane + 32 * t : ql, nq - 1);
-            load_point<D>(recb + ((int64_t)cs + q0 + qi) * DP, qx[t]);
+        for (int t = 0; t < 4; ++t) load_point<D>(recb + ((int64_t)cs + q0 + min(ql * Q + t, nq - 1)) * DP, qx[t]);
+        // expanded form: coordinates relative to the query cell's corner
+        int32_t org[3] = {0, 0, 0};
+        int32_t qa[4][3], qb[4];
+        if (EXP) {
+#pragma unroll
+            for (int k = 0; k < D && k < 3; ++k) org[k] = ds.lo[k];
+            for (int j = 0; j < ds.k; ++j) {
+                const int g = ds.gdim[j];
+                const int32_t cc = cell_coord(ds, j, rec_coord(recb + (int64_t)cs * DP, g));
+                const int32_t corner = ds.origin[j] + cc * (int32_t)ds.s;
+#pragma unroll
+                for (int k = 0; k < 3; ++k)
+                    if (k == g) org[k] = corner;
+            }
+#pragma unroll
+            for (int t = 0; t < 4; ++t) {
+                int32_t nrm = -(int32_t)ds.d_cut2;
+#pragma unroll
+                for (int k = 0; k < 3; ++k) {
+                    const int32_t qk = k < D ? qx[t][k < D ? k : 0] - org[k] : 0;
+                    qa[t][k] = -2 * qk;
+                    nrm += qk * qk;
+                }
+                qb[t] = nrm;
+            }
         }
         uint32_t cnt[4] = {0u, 0u, 0u, 0u};
-        const uint2* runs = w.runs + (int64_t)c * w.nbs;
+        // the cell's runs into shared memory, then the candidate stream
         const uint32_t nr = w.nruns[c], ctot = w.cand[c];
+        for (uint32_t t = lane; t < nr; t += 32) srun[t] = w.runs[(int64_t)c * w.nbs + t];
+        __syncwarp();
         const uint32_t k0 = kc * (uint32_t)w.kch;
-        uint32_t remaining = min(ctot, k0 + (uint32_t)w.kch) - k0;
-        uint32_t ri = 0, roff = k0;
-        while (ri < nr) {
-            const uint32_t len = runs[ri].y;
-            if (roff < len) break;
-            roff -= len;
-            ++ri;
-        }
+        CandStream<DP, false> cst;
+        cst.init(srun, nr, k0, min(ctot, k0 + (uint32_t)w.kch));
+        bool bad = false;
+        bool have = cst.prep(lane, recb, nullptr, &bad);
         const int64_t T = ds.d_cut2;
-        while (remaining > 0u) {
-            int nb = 0;
-            while (nb < kCb && remaining > 0u) {
-                const uint2 run = ri < nr ? runs[ri] : make_uint2(0u, 0u);
-                const uint32_t take = ri < nr ? min(min(run.y - roff, (uint32_t)(kCb - nb)), remaining) : 0u;
-                if (take == 0u) {  // runs exhausted early: cannot happen when counts agree
-                    if (lane == 0) atomicOr(v.err, kErrStaging);
-                    remaining = 0u;
-                    break;
-                }
-                const int4* src = recb + ((int64_t)run.x + roff) * DP;
-                for (uint32_t t = lane; t < take * DP; t += 32) buf[nb * DP + t] = __ldg(src + t);
-                nb += (int)take;
-                roff += take;
-                remaining -= take;
-                if (roff == run.y) {
-                    ++ri;
-                    roff = 0;
+        int sb = 0;
+        while (have) {
+            // store the loaded chunk (relative to the cell corner in the
+            // expanded form), then put the next chunk's loads in flight
+            int4* buf = sbuf[wid][sb];
+            const int nb = (int)cst.cnt;
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int f = lane + 32 * u;
+                if (f < nb) {
+                    if (EXP) {
+                        const int4 r = cst.r[u][0];
+                        const int32_t cx = r.x - org[0], cy = D > 1 ? r.y - org[1] : 0, cz = D > 2 ? r.z - org[2] : 0;
+                        buf[f] = make_int4(cx, cy, cz, cx * cx + cy * cy + cz * cz);
+                    } else {
+#pragma unroll
+                        for (int q = 0; q < DP; ++q) buf[f * DP + q] = cst.r[u][q];
+                    }
                 }
             }
             __syncwarp();
-            if (G == 4) eval_rho<D, W64, 1, 4>(buf, nb, grp, qx, cnt, T);
-            else if (G == 2) eval_rho<D, W64, 1, 2>(buf, nb, grp, qx, cnt, T);
-            else switch (Q) {
-                case 1: eval_rho<D, W64, 1, 1>(buf, nb, 0, qx, cnt, T); break;
-                case 2: eval_rho<D, W64, 2, 1>(buf, nb, 0, qx, cnt, T); break;
-                case 3: eval_rho<D, W64, 3, 1>(buf, nb, 0, qx, cnt, T); break;
-                default: eval_rho<D, W64, 4, 1>(buf, nb, 0, qx, cnt, T); break;
+            have = cst.prep(lane, recb, nullptr, &bad);
+            sb ^= 1;
+            if (EXP) {
+                switch (Q) {
+                    case 1: eval_rho_x<D, 1>(buf, nb, grp, G, qa, qb, cnt); break;
+                    case 2: eval_rho_x<D, 2>(buf, nb, grp, G, qa, qb, cnt); break;
+                    case 3: eval_rho_x<D, 3>(buf, nb, grp, G, qa, qb, cnt); break;
+                    default: eval_rho_x<D, 4>(buf, nb, grp, G, qa, qb, cnt); break;
+                }
+            } else {
+                switch (Q) {
+                    case 1: eval_rho<D, W64, 1>(buf, nb, grp, G, qx, cnt, T); break;
+                    case 2: eval_rho<D, W64, 2>(buf, nb, grp, G, qx, cnt, T); break;
+                    case 3: eval_rho<D, W64, 3>(buf, nb, grp, G, qx, cnt, T); break;
+                    default: eval_rho<D, W64, 4>(buf, nb, grp, G, qx, cnt, T); break;
+                }
             }
-            __syncwarp();
         }
-        if (G > 1) {
-            for (int o = Mq; o < 32; o <<= 1) cnt[0] += __shfl_xor_sync(0xffffffffu, cnt[0], o);
-            if (grp == 0 && ql < nq) atomicAdd(&v.rho_s[cs + q0 + ql], (int)cnt[0]);
-        } else {
+        if (bad && lane == 0) atomicOr(v.err, kErrStaging);
+        __syncwarp();
+        // add the groups' counts, then one lane per query writes
+#pragma unroll
+        for (int t = 0; t < 4; ++t)
+            for (int o = Mq; o < 32; o <<= 1) cnt[t] += __shfl_xor_sync(0xffffffffu, cnt[t], o);
+        if (grp == 0) {
 #pragma unroll
             for (int t = 0; t < 4; ++t)
-                if (lane + 32 * t < nq) atomicAdd(&v.rho_s[cs + q0 + lane + 32 * t], (int)cnt[t]);
+                if (t < Q && ql * Q + t < nq) atomicAdd(&v.rho_s[cs + q0 + ql * Q + t], (int)cnt[t]);
         }
     }
 }
@@ -372,17 +429,19 @@ __global__ void k_rho_scatter(BatchView v) {
     if (p < v.N) v.rho[v.perm[p]] = v.rho_s[p];
 }
 
+template <int D, int MODE>
+void launch_rho_dense(const BatchView& v, const CellWork& w, int64_t nitems_bound, uint32_t* counter,
+                      cudaStream_t st) {
+    if (nitems_bound <= 0) return;
+    const unsigned blocks = (unsigned)std::max<int64_t>(1, std::min<int64_t>(152 * 16, (nitems_bound + 3) / 4));
+    (k_rho_dense<D, MODE><<<blocks, kRhoThreads, 0, st>>>(v, w, counter), note_launch());
+}
+
 template <int D, bool W64>
-void launch_rho_class(const BatchView& v, const CellWork& w, int64_t nitems_bound, int64_t nsparse_bound,
-                      uint32_t* counter, cudaStream_t st) {
-    if (nitems_bound > 0) {
-        const unsigned blocks = (unsigned)std::max<int64_t>(1, std::min<int64_t>(152 * 8, (nitems_bound + 7) / 8));
-        (k_rho_dense<D, W64><<<blocks, kRhoThreads, 0, st>>>(v, w, counter), note_launch());
-    }
-    if (nsparse_bound > 0) {
-        const unsigned blocks = (unsigned)std::min<int64_t>(152 * 32, grid_for(nsparse_bound, 256));
-        (k_rho_sparse<D, W64><<<blocks, 256, 0, st>>>(v, w), note_launch());
-    }
+void launch_rho_sparse(const BatchView& v, const CellWork& w, int64_t nsparse_bound, cudaStream_t st) {
+    if (nsparse_bound <= 0) return;
+    const unsigned blocks = (unsigned)std::min<int64_t>(152 * 32, grid_for(nsparse_bound, 256));
+    (k_rho_sparse<D, W64><<<blocks, 256, 0, st>>>(v, w), note_launch());
 }
 
 }  // namespace
@@ -426,16 +485,23 @@ cudaError_t launch_fill_items(const BatchView& v, const CellPrepBufs& cb, int64_
 
 cudaError_t launch_rho(const BatchView& v, const CellWork& w, uint32_t class_mask, int64_t nitems_bound,
                        int64_t nsparse_bound, uint32_t* counters, cudaStream_t st) {
-    // one launch pair per (dimension, arithmetic width) class present in the
-    // batch; each kernel skips the items of the other classes
-#define DPC_RHO_CLASS(D)                                                                              \
-    if (class_mask & (1u << (2 * (D - 1))))                                                           \
-        launch_rho_class<D, false>(v, w, nitems_bound, nsparse_bound, counters + 2 * (D - 1), st);    \
-    if (class_mask & (1u << (2 * (D - 1) + 1)))                                                       \
-        launch_rho_class<D, true>(v, w, nitems_bound, nsparse_bound, counters + 2 * (D - 1) + 1, st);
+    // one dense launch per (dimension, arithmetic mode) class present in the
+    // batch and one sparse launch per (dimension, width); each kernel skips
+    // the work of the other classes
+#define DPC_BIT(D, M) (class_mask & (1u << (3 * ((D) - 1) + (M))))
+#define DPC_RHO_CLASS(D)                                                                                 \
+    if (DPC_BIT(D, 0)) launch_rho_dense<D, 0>(v, w, nitems_bound, counters + 3 * (D - 1), st);           \
+    if (DPC_BIT(D, 1)) launch_rho_dense<D, 1>(v, w, nitems_bound, counters + 3 * (D - 1) + 1, st);       \
+    if (DPC_BIT(D, 0) || DPC_BIT(D, 2)) launch_rho_sparse<D, false>(v, w, nsparse_bound, st);            \
+    if (DPC_BIT(D, 1)) launch_rho_sparse<D, true>(v, w, nsparse_bound, st);
+#define DPC_RHO_X(D) \
+    if (DPC_BIT(D, 2)) launch_rho_dense<D, 2>(v, w, nitems_bound, counters + 3 * (D - 1) + 2, st);
     DPC_RHO_CLASS(1) DPC_RHO_CLASS(2) DPC_RHO_CLASS(3) DPC_RHO_CLASS(4)
     DPC_RHO_CLASS(5) DPC_RHO_CLASS(6) DPC_RHO_CLASS(7) DPC_RHO_CLASS(8)
+    DPC_RHO_X(1) DPC_RHO_X(2) DPC_RHO_X(3)
+#undef DPC_RHO_X
 #undef DPC_RHO_CLASS
+#undef DPC_BIT
     return cudaGetLastError();
 }
 

@@ -155,7 +155,7 @@ struct Batch {
     int64_t cand_pairs = 0;
     int64_t tree_visits = 0, tree_pairs = 0, ntree2 = 0;
     unsigned long long* d_stats = nullptr;
-    uint32_t* d_counters = nullptr;  // [16] rho + [16] ring
+    uint32_t* d_counters = nullptr;  // [32] rho + [32] ring work counters
     int out_is_device = 0;
     float ms[6] = {0, 0, 0, 0, 0, 0};
     int refs = 0;
@@ -278,7 +278,7 @@ struct Batch {
             ds.leaf_off = leaf_slots;
             ds.node_off = 2 * leaf_slots;
             leaf_slots += 1ll << ds.h;
-            class_mask |= 1u << (2 * (ds.d - 1) + (ds.w32 ? 0 : 1));
+            class_mask |= 1u << (3 * (ds.d - 1) + ds.mode);
             dim_mask |= 1u << (ds.d - 1);
         }
         h_slot_off[B] = leaf_slots;
@@ -297,7 +297,7 @@ struct Batch {
         DPC_CK(keep.get(&v.err, 1));
         DPC_CK(cudaMemsetAsync(v.err, 0, sizeof(unsigned int), st));
         DPC_CK(keep.get(&d_stats, 4));
-        DPC_CK(keep.get(&d_counters, 32));
+        DPC_CK(keep.get(&d_counters, 64));
         DPC_CK(cudaMemsetAsync(d_stats, 0, 4 * sizeof(unsigned long long), st));
 
         // cell keys, sort, cells
@@ -398,7 +398,7 @@ struct Batch {
 
         // local density
         DPC_CK(cudaMemsetAsync(v.rho_s, 0, sizeof(int32_t) * std::max<int64_t>(N, 1), st));
-        DPC_CK(cudaMemsetAsync(d_counters, 0, 32 * sizeof(uint32_t), st));
+        DPC_CK(cudaMemsetAsync(d_counters, 0, 64 * sizeof(uint32_t), st));
         DPC_CK(launch_rho(v, w, class_mask, nitems, nsparse, d_counters, st));
         mark(2);
         DPC_CK(launch_rho_scatter(v, st));
@@ -470,6 +470,20 @@ struct Batch {
         }
         ds.w32 = (maxsum < (1ll << 31) && ds.d_cut2 <= (1ll << 31)) ? 1 : 0;
         ds.rbits = bits_for((uint64_t)ds.n);
+        // Expanded test around the query cell's corner: every coordinate
+        // relative to it lies in [-s, 2s) (gridded dims, reach 1) or [0, s)
+        // (a dim narrower than one cell), and |c'|^2 + |q'|^2 - T - 2 q'.c'
+        // stays inside 9 d s^2 < 2^31 for every partial sum.
+        bool narrow = true;
+        for (int c = 0; c < ds.d; ++c) {
+            ds.lo[c] = ds.n > 0 ? mm[2 * c] : 0;
+            bool gridded = false;
+            for (int j = 0; j < k; ++j) gridded |= ds.gdim[j] == c;
+            if (!gridded && ds.n > 0 && (int64_t)mm[2 * c + 1] - mm[2 * c] >= ds.s) narrow = false;
+        }
+        const bool expand = ds.d <= 3 && ds.R == 1 && narrow && ds.d_cut2 <= ds.s * ds.s &&
+                            9 * (int64_t)ds.d * ds.s * ds.s < (1ll << 31);
+        ds.mode = expand ? 2 : (ds.w32 ? 0 : 1);
         return DPC_OK;
     }
 
@@ -498,7 +512,7 @@ struct Batch {
 
         DPC_CK(tmp.get(&v.best_s, N));
         DPC_CK(cudaMemsetAsync(v.best_s, 0xff, sizeof(unsigned long long) * std::max<int64_t>(N, 1), st));
-        DPC_CK(launch_ring(v, w, class_mask, nitems, nsparse, d_counters + 16, st));
+        DPC_CK(launch_ring(v, w, class_mask, nitems, nsparse, d_counters + 32, st));
         mark(2);
 
         DPC_CK(tmp.get(&db.ucount, 4));
@@ -813,6 +827,7 @@ dpc_status dpc_ds_info(const dpc_ds* ds, dpc_info* out) {
     out->tree_visits = bt.tree_visits;
     out->tree_pairs = bt.tree_pairs;
     out->open_after_coarse = bt.ntree2;
+    out->pair_mode = h.mode;
     return DPC_OK;
 }
 

@@ -83,6 +83,96 @@ __device__ __forceinline__ int num_neighbours(const DsDesc& ds) {
     return t;
 }
 
+// Lane layout of a chunk of nq <= 128 queries: Q queries per lane, G groups
+// of Mq lanes (Mq a power of two, Mq * G = 32), group g taking candidates
+// g, g + G, ...; the layout wasting the fewest query slots, larger Q first.
+__device__ __forceinline__ void lane_layout(int nq, int& Q, int& Mq) {
+    int best = 1 << 30;
+    Q = 1;
+    Mq = 32;
+    for (int q = 4; q >= 1; --q) {
+        int m = 1;
+        while (m * q < nq) m <<= 1;
+        if (m > 32) continue;
+        const int waste = m * q - nq;
+        if (waste < best) {
+            best = waste;
+            Q = q;
+            Mq = m;
+        }
+    }
+}
+
+// Candidate stream of one dense work item: the flat range [k0, k1) of the
+// concatenated runs of a cell, delivered kChunk candidates at a time. prep()
+// issues the loads of the next chunk into registers (lane l holds chunk
+// slots l, l + 32, l + 64, l + 96), so that they are in flight while the
+// warp works on the previous chunk; the caller then stores them to shared
+// memory. All lanes call every method (warp-uniform control flow).
+constexpr int kChunk = 128;
+
+template <int DP, bool RO>
+struct CandStream {
+    const uint2* runs;   // the cell's runs, in shared memory
+    uint32_t nr, ri, roff, remaining, cnt;
+    int4 r[4][DP];
+    uint2 ro[4];
+
+    __device__ __forceinline__ void init(const uint2* runs_, uint32_t nr_, uint32_t k0, uint32_t k1) {
+        runs = runs_;
+        nr = nr_;
+        ri = 0;
+        roff = k0;
+        remaining = k1 - k0;
+        while (ri < nr) {
+            const uint32_t len = runs[ri].y;
+            if (roff < len) break;
+            roff -= len;
+            ++ri;
+        }
+    }
+
+    // Returns false when the stream is exhausted; sets *bad when the runs end
+    // before the counted candidates do (cannot happen when counts agree).
+    __device__ __forceinline__ bool prep(int lane, const int4* __restrict__ recb, const uint2* __restrict__ ro_s,
+                                         bool* bad) {
+        if (remaining == 0u) return false;
+        const uint32_t total = min((uint32_t)kChunk, remaining);
+        int64_t src[4] = {-1, -1, -1, -1};
+        uint32_t o = 0;
+        while (o < total) {
+            if (ri >= nr) {
+                *bad = true;
+                break;
+            }
+            const uint2 run = runs[ri];
+            const uint32_t piece = min(run.y - roff, total - o);
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const uint32_t f = (uint32_t)lane + 32u * u;
+                if (f >= o && f < o + piece) src[u] = (int64_t)run.x + roff + (f - o);
+            }
+            o += piece;
+            roff += piece;
+            if (roff == run.y) {
+                ++ri;
+                roff = 0;
+            }
+        }
+        cnt = o;
+        remaining -= total;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            if (src[u] >= 0) {
+#pragma unroll
+                for (int q = 0; q < DP; ++q) r[u][q] = __ldg(recb + src[u] * DP + q);
+                if (RO) ro[u] = __ldg(ro_s + src[u]);
+            }
+        }
+        return true;
+    }
+};
+
 // ------------------------------------------------------------- launchers
 
 // grid.cu
@@ -121,8 +211,8 @@ cudaError_t launch_dense_prep(const BatchView& v, const CellPrepBufs& cb, int64_
                               int kch, uint32_t kmask, void* scan_temp, cudaStream_t st);
 cudaError_t launch_fill_items(const BatchView& v, const CellPrepBufs& cb, int64_t ndense_bound, int kch,
                               cudaStream_t st);
-// class_mask bit 2*(d-1) + wide: a dataset of dimension d with 32-bit (wide = 0)
-// or 64-bit (wide = 1) pair arithmetic is in the batch. counters: [16], zeroed.
+// class_mask bit 3*(d-1) + mode: a dataset of dimension d with density test
+// mode `mode` (DsDesc::mode) is in the batch. counters: [24], zeroed.
 cudaError_t launch_rho(const BatchView& v, const CellWork& w, uint32_t class_mask, int64_t nitems_bound,
                        int64_t nsparse_bound, uint32_t* counters, cudaStream_t st);
 cudaError_t launch_rho_scatter(const BatchView& v, cudaStream_t st);
