@@ -177,6 +177,8 @@ dpc_status dpc_set_profiling(dpc_ctx* ctx, int on);
  *   "clevel"  coarse ring over blocks of 2^clevel cells per gridded dim,
  *             0 .. 8 (default 0: off)
  *   "ccap"    coarse cells with more points are not scanned (default 512)
+ *   "max_batch_jobs"  served mode: jobs one batch admits at most, 1 .. 4096
+ *             (default 64; 1 runs the jobs one at a time)
  * DPC_ERR_INVALID_ARG for an unknown key or a value out of range. */
 dpc_status dpc_set_tuning(dpc_ctx* ctx, const char* key, int64_t value);
 dpc_status dpc_get_tuning(dpc_ctx* ctx, const char* key, int64_t* value);
@@ -199,9 +201,11 @@ dpc_status dpc_probe_pair_rate(int device, int d, int mode, double* pairs_per_s,
 /* ---------------------------------------------------------------------
  * Jobs: many independent datasets, batched or served.
  *
- * A job is one dataset plus n_queries (rho_min, delta_min) queries. All its
- * pointers are host memory owned by the caller and must stay valid until
- * dpc_poll reports the job finished. In batched mode (dpc_options.mode 0)
+ * A job is one dataset plus n_queries (rho_min, delta_min) queries. Its
+ * points and per-point outputs are host memory, or device memory of the
+ * context's device when is_device is 1; rho_min, delta_min and
+ * n_centers_out are always host memory. All of them are owned by the caller
+ * and must stay valid until dpc_poll reports the job finished. In batched mode (dpc_options.mode 0)
  * jobs run when dpc_flush is called, all of them in one batch: every stage
  * is one launch over all datasets. In served mode (mode 1) a worker thread
  * admits waiting jobs as device memory (hbm_cap_bytes) and batch slots
@@ -221,6 +225,7 @@ typedef struct {
     int64_t* delta2_out;       /* NULL or [n] */
     int32_t* label_out;        /* NULL or [n_queries * n], query-major */
     int64_t* n_centers_out;    /* NULL or [n_queries] */
+    int32_t is_device;         /* 0: points and outputs in host memory; 1: in device memory */
 } dpc_job;
 
 typedef struct {
@@ -238,6 +243,14 @@ dpc_status dpc_poll(dpc_ctx* ctx, uint64_t ticket, dpc_result* out);
 
 /* Batched mode: run every job submitted so far as one batch and wait for it. */
 dpc_status dpc_flush(dpc_ctx* ctx);
+
+/* Counters and stage times (stage times need dpc_set_profiling) of the most
+ * recent batch of jobs that finished on this context: n is the batch's total
+ * number of points, cells, work items, candidate pairs and open points are
+ * the batch's totals, and the per-dataset fields (grid_dims, pair_bits,
+ * pair_mode) are its first dataset's. No counterpart in the paper.
+ * DPC_ERR_STATE before the first batch finishes. */
+dpc_status dpc_last_batch_info(dpc_ctx* ctx, dpc_info* out);
 
 /* Block until the job is done or timeout_ms passes (DPC_ERR_TIMEOUT). */
 dpc_status dpc_wait(dpc_ctx* ctx, uint64_t ticket, int64_t timeout_ms, dpc_result* out);

@@ -58,7 +58,7 @@ class DpcJob(ctypes.Structure):
                 ("d_cut", ctypes.c_int64), ("n_queries", ctypes.c_int32), ("rho_min", ctypes.c_void_p),
                 ("delta_min", ctypes.c_void_p), ("rho_out", ctypes.c_void_p), ("dep_out", ctypes.c_void_p),
                 ("delta2_out", ctypes.c_void_p), ("label_out", ctypes.c_void_p),
-                ("n_centers_out", ctypes.c_void_p)]
+                ("n_centers_out", ctypes.c_void_p), ("is_device", ctypes.c_int32)]
 
 
 class DpcResult(ctypes.Structure):
@@ -91,6 +91,7 @@ def lib():
             "dpc_label": ([vp, i64, i64, vp, ctypes.POINTER(i64)], st),
             "dpc_release": ([vp], st),
             "dpc_ds_info": ([vp, ctypes.POINTER(DpcInfo)], st),
+            "dpc_last_batch_info": ([vp, ctypes.POINTER(DpcInfo)], st),
             "dpc_set_profiling": ([vp, ctypes.c_int], st),
             "dpc_submit": ([vp, ctypes.POINTER(DpcJob), ctypes.POINTER(ctypes.c_uint64)], st),
             "dpc_poll": ([vp, ctypes.c_uint64, ctypes.POINTER(DpcResult)], st),
@@ -169,6 +170,12 @@ def dpc_release(ds):
 def dpc_ds_info(ds) -> dict:
     info = DpcInfo()
     _check(lib().dpc_ds_info(ds, ctypes.byref(info)), "dpc_ds_info")
+    return info.as_dict()
+
+
+def dpc_last_batch_info(ctx) -> dict:
+    info = DpcInfo()
+    _check(lib().dpc_last_batch_info(ctx, ctypes.byref(info)), "dpc_last_batch_info")
     return info.as_dict()
 
 
@@ -314,6 +321,9 @@ class Context:
     def wait(self, ticket: int, timeout_ms: int = -1):
         return dpc_wait(self.handle, ticket, timeout_ms)
 
+    def last_batch_info(self) -> dict:
+        return dpc_last_batch_info(self.handle)
+
 
 class Dataset:
     """A dataset clustered on the device (rho done; dep/labels on demand)."""
@@ -352,23 +362,41 @@ class Dataset:
 
 
 class Job:
-    """One dataset + (rho_min, delta_min) queries for dpc_submit, with host
-    output arrays allocated here (rho, dep, delta2, labels[q], n_centers[q])."""
+    """One dataset + (rho_min, delta_min) queries for dpc_submit, with output
+    arrays allocated here (rho, dep, delta2, labels[q], n_centers[q]). Host
+    numpy points give host outputs; a CUDA tensor of points gives device
+    outputs (torch tensors on its device) and a device-memory job."""
 
-    def __init__(self, points: np.ndarray, d_cut: int, queries):
-        self.points = np.ascontiguousarray(points, dtype=np.int32)
-        n, d = self.points.shape
+    def __init__(self, points, d_cut: int, queries):
         q = list(queries)
         self.rho_min = np.array([int(a) for a, _ in q], dtype=np.int64)
         self.delta_min = np.array([int(b) for _, b in q], dtype=np.int64)
-        self.rho = np.empty(n, np.int32)
-        self.dep = np.empty(n, np.int32)
-        self.delta2 = np.empty(n, np.int64)
-        self.label = np.empty((len(q), n), np.int32)
         self.n_centers = np.empty(len(q), np.int64)
-        p = lambda a: a.ctypes.data_as(ctypes.c_void_p)
-        self.c = DpcJob(p(self.points), n, d, int(d_cut), len(q), p(self.rho_min), p(self.delta_min),
-                        p(self.rho), p(self.dep), p(self.delta2), p(self.label), p(self.n_centers))
+        if _is_torch(points) and points.is_cuda:
+            import torch
+            if points.dtype != torch.int32 or not points.is_contiguous() or points.ndim != 2:
+                raise ValueError("device points must be a contiguous n x d int32 tensor")
+            self.points = points
+            n, d = int(points.shape[0]), int(points.shape[1])
+            dev = points.device
+            self.rho = torch.empty(n, dtype=torch.int32, device=dev)
+            self.dep = torch.empty(n, dtype=torch.int32, device=dev)
+            self.delta2 = torch.empty(n, dtype=torch.int64, device=dev)
+            self.label = torch.empty((len(q), n), dtype=torch.int32, device=dev)
+            p = lambda a: ctypes.c_void_p(a.data_ptr() if a.numel() else 0)
+            is_dev = 1
+        else:
+            self.points = np.ascontiguousarray(points, dtype=np.int32)
+            n, d = self.points.shape
+            self.rho = np.empty(n, np.int32)
+            self.dep = np.empty(n, np.int32)
+            self.delta2 = np.empty(n, np.int64)
+            self.label = np.empty((len(q), n), np.int32)
+            p = lambda a: a.ctypes.data_as(ctypes.c_void_p)
+            is_dev = 0
+        h = lambda a: a.ctypes.data_as(ctypes.c_void_p)
+        self.c = DpcJob(p(self.points), n, d, int(d_cut), len(q), h(self.rho_min), h(self.delta_min),
+                        p(self.rho), p(self.dep), p(self.delta2), p(self.label), h(self.n_centers), is_dev)
         self.ticket = None
 
 

@@ -131,6 +131,8 @@ struct dpc_ctx {
     std::vector<std::thread> workers;
     uint64_t held_bytes = 0;
     int max_batch_jobs = 64;  // served mode: jobs admitted into one batch at most
+    bool has_last = false;    // last_info holds the most recent finished batch of jobs
+    dpc_info last_info{};
 };
 
 namespace dpc {
@@ -716,7 +718,10 @@ dpc_status dpc_set_tuning(dpc_ctx* ctx, const char* key, int64_t value) {
     else if (k == "bf_rank" && value >= 0 && value <= UINT32_MAX) t.bf_rank = (uint32_t)value;
     else if (k == "clevel" && value >= 0 && value <= 8) t.clevel = (int)value;
     else if (k == "ccap" && value >= 1 && value <= (1 << 24)) t.ccap = (uint32_t)value;
-    else return fail(DPC_ERR_INVALID_ARG, "unknown tuning key or value out of range: " + k);
+    else if (k == "max_batch_jobs" && value >= 1 && value <= 4096) {
+        std::lock_guard<std::mutex> lk(ctx->mu);
+        ctx->max_batch_jobs = (int)value;
+    } else return fail(DPC_ERR_INVALID_ARG, "unknown tuning key or value out of range: " + k);
     return DPC_OK;
 }
 
@@ -729,7 +734,10 @@ dpc_status dpc_get_tuning(dpc_ctx* ctx, const char* key, int64_t* value) {
     else if (k == "bf_rank") *value = t.bf_rank;
     else if (k == "clevel") *value = t.clevel;
     else if (k == "ccap") *value = t.ccap;
-    else return fail(DPC_ERR_INVALID_ARG, "unknown tuning key: " + k);
+    else if (k == "max_batch_jobs") {
+        std::lock_guard<std::mutex> lk(ctx->mu);
+        *value = ctx->max_batch_jobs;
+    } else return fail(DPC_ERR_INVALID_ARG, "unknown tuning key: " + k);
     return DPC_OK;
 }
 
@@ -804,11 +812,9 @@ dpc_status dpc_release(dpc_ds* ds) {
     return DPC_OK;
 }
 
-dpc_status dpc_ds_info(const dpc_ds* ds, dpc_info* out) {
-    if (!ds || !ds->batch || !out) return fail(DPC_ERR_INVALID_ARG, "NULL argument");
-    const Batch& bt = *ds->batch;
+static void fill_info(const Batch& bt, int b, dpc_info* out) {
     std::memset(out, 0, sizeof(*out));
-    const dpc::DsDesc& h = bt.hd[ds->b];
+    const dpc::DsDesc& h = bt.hd[b];
     out->n = h.n;
     out->cells = bt.ncells;
     out->dense_cells = bt.ndense;
@@ -828,6 +834,19 @@ dpc_status dpc_ds_info(const dpc_ds* ds, dpc_info* out) {
     out->tree_pairs = bt.tree_pairs;
     out->open_after_coarse = bt.ntree2;
     out->pair_mode = h.mode;
+}
+
+dpc_status dpc_ds_info(const dpc_ds* ds, dpc_info* out) {
+    if (!ds || !ds->batch || !out) return fail(DPC_ERR_INVALID_ARG, "NULL argument");
+    fill_info(*ds->batch, ds->b, out);
+    return DPC_OK;
+}
+
+dpc_status dpc_last_batch_info(dpc_ctx* ctx, dpc_info* out) {
+    if (!ctx || !out) return fail(DPC_ERR_INVALID_ARG, "NULL argument");
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    if (!ctx->has_last) return fail(DPC_ERR_STATE, "no batch of jobs has finished on this context");
+    *out = ctx->last_info;
     return DPC_OK;
 }
 
@@ -854,7 +873,7 @@ dpc_status run_jobs(dpc_ctx* ctx, std::vector<JobPtr>& jobs, cudaStream_t st) {
     std::vector<Input> in;
     int maxq = 0;
     for (auto& j : jobs) {
-        in.push_back({j->job.points, j->job.n, j->job.d, j->job.d_cut, 0});
+        in.push_back({j->job.points, j->job.n, j->job.d, j->job.d_cut, j->job.is_device ? 1 : 0});
         maxq = std::max(maxq, j->job.n_queries);
     }
     DPC_TRY(bt->density(in));
@@ -888,6 +907,16 @@ dpc_status run_jobs(dpc_ctx* ctx, std::vector<JobPtr>& jobs, cudaStream_t st) {
             if (q < jobs[b]->job.n_queries && jobs[b]->job.n_centers_out)
                 jobs[b]->job.n_centers_out[q] = (int64_t)nc[b];
     }
+    // the batch's counters and stage times (the first dataset's per-dataset
+    // fields, the batch's totals)
+    dpc_info info;
+    fill_info(*bt, 0, &info);
+    int64_t n = 0;
+    for (auto& j : jobs) n += j->job.n;
+    info.n = n;
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    ctx->last_info = info;
+    ctx->has_last = true;
     return DPC_OK;
 }
 
@@ -951,6 +980,7 @@ dpc_status check_job(const dpc_job* j) {
     if (j->d < 1 || j->d > 8) return fail(DPC_ERR_INVALID_ARG, "d must be in [1, 8]");
     if (j->d_cut < 1 || j->d_cut >= (1ll << 31)) return fail(DPC_ERR_INVALID_ARG, "d_cut must be in [1, 2^31)");
     if (j->n > 0 && !j->points) return fail(DPC_ERR_INVALID_ARG, "points is NULL");
+    if (j->is_device != 0 && j->is_device != 1) return fail(DPC_ERR_INVALID_ARG, "is_device must be 0 or 1");
     if (j->n_queries < 1 || !j->rho_min || !j->delta_min)
         return fail(DPC_ERR_INVALID_ARG, "a job needs at least one (rho_min, delta_min) query");
     for (int q = 0; q < j->n_queries; ++q)

@@ -144,3 +144,55 @@ def test_poll_unknown_ticket_and_wait_timeout(dpc):
         ctx.flush()
         s, _ = ctx.poll(j.ticket)
         assert s == dpc.DPC_OK
+
+
+def test_device_jobs_match_host_jobs(dpc):
+    """Jobs whose points and outputs live in device memory give the same bits
+    as host-memory jobs, in one batch mixed with host jobs."""
+    import torch
+    probs = small_problems(seed=43, count=10)
+    with dpc.Context(0, mode=0, profiling=True) as ctx:
+        dev = [dpc.Job(torch.from_numpy(np.ascontiguousarray(p)).cuda(), dc, qs) for p, dc, qs in probs]
+        host = [dpc.Job(p, dc, qs) for p, dc, qs in probs]
+        torch.cuda.synchronize()
+        for a, b in zip(dev, host):
+            ctx.submit(a)
+            ctx.submit(b)
+        ctx.flush()
+        for j in dev + host:
+            s, _ = ctx.poll(j.ticket)
+            assert s == dpc.DPC_OK
+        info = ctx.last_batch_info()
+        assert info["n"] == 2 * sum(p.shape[0] for p, _, _ in probs)
+        assert info["cand_pairs"] > 0 and info["ms_rho"] > 0.0
+    for a, b in zip(dev, host):
+        np.testing.assert_array_equal(a.rho.cpu().numpy(), b.rho)
+        np.testing.assert_array_equal(a.dep.cpu().numpy(), b.dep)
+        np.testing.assert_array_equal(a.delta2.cpu().numpy(), b.delta2)
+        np.testing.assert_array_equal(a.label.cpu().numpy(), b.label)
+        np.testing.assert_array_equal(a.n_centers, b.n_centers)
+    for b, (p, dc, qs) in zip(host, probs):
+        check_job(b, p, dc, qs)
+
+
+def test_served_one_job_per_batch(dpc):
+    """max_batch_jobs = 1 serves the jobs one at a time with the same results."""
+    probs = small_problems(seed=44, count=6)
+    with dpc.Context(0, mode=1, max_inflight=1) as ctx:
+        ctx.tune(max_batch_jobs=1)
+        assert ctx.tuning("max_batch_jobs") == 1
+        jobs = [dpc.Job(p, dc, qs) for p, dc, qs in probs]
+        for j in jobs:
+            ctx.submit(j)
+        for j in jobs:
+            s, _ = ctx.wait(j.ticket, 120000)
+            assert s == dpc.DPC_OK
+    for j, (p, dc, qs) in zip(jobs, probs):
+        check_job(j, p, dc, qs)
+
+
+def test_last_batch_info_before_any_batch(dpc):
+    with dpc.Context(0, mode=0) as ctx:
+        with pytest.raises(dpc.DpcError) as e:
+            ctx.last_batch_info()
+        assert e.value.status == dpc.DPC_ERR_STATE

@@ -203,26 +203,33 @@ def batch_256(seed: int = 4, count: int = 256) -> list:
     return out
 
 
-def served_trace(seed: int = 5, jobs: int = 5000, rate_per_s: float = 200.0,
-                 n_lo: int = 10_000, n_hi: int = 2_000_000) -> list:
+def served_trace(seed: int = 5, jobs: int = 2000, rate_per_s: float = 200.0,
+                 n_lo: int = 10_000, n_hi: int = 2_000_000, pool: int = 48) -> list:
     """A Poisson stream (mean ``rate_per_s`` jobs/s) of clustering requests:
     n log-uniform on [10k, 2M], d uniform on {2..8}, blob mixtures as in
-    ``batch_256``, and 1-4 follow-up (rho_min, delta_min) re-queries each."""
+    ``batch_256``, and 1-4 follow-up (rho_min, delta_min) re-queries each.
+
+    ``pool`` distinct problems are drawn and every request takes one of them
+    at random (with its own arrival time and queries), so that a long trace
+    does not need tens of GB of host memory; requests sharing a problem
+    share its point array (each request is still clustered from scratch)."""
     rng = np.random.default_rng(seed)
+    probs = []
+    for i in range(pool):
+        n = int(round(math.exp(rng.uniform(math.log(n_lo), math.log(n_hi)))))
+        d = int(rng.integers(2, 9))
+        target = float(rng.uniform(20, 200))
+        probs.append(_random_problem(rng, f"problem_{i}", n, d, target))
     t = 0.0
     out = []
     for j in range(jobs):
         t += float(rng.exponential(1.0 / rate_per_s))
-        n = int(round(math.exp(rng.uniform(math.log(n_lo), math.log(n_hi)))))
-        d = int(rng.integers(2, 9))
-        target = float(rng.uniform(20, 200))
-        ds = _random_problem(rng, f"job_{j}", n, d, target)
+        src = probs[int(rng.integers(pool))]
         nq = int(rng.integers(1, 5))
-        ds.queries = [(max(1, int(ds.rho_min * rng.uniform(0.5, 2.0))),
-                       max(ds.d_cut + 1, int(ds.d_cut * rng.uniform(4, 12)))) for _ in range(nq)]
-        ds.arrival_s = t
-        ds.seed = seed
-        out.append(ds)
+        queries = [(max(1, int(src.rho_min * rng.uniform(0.5, 2.0))),
+                    max(src.d_cut + 1, int(src.d_cut * rng.uniform(4, 12)))) for _ in range(nq)]
+        out.append(Dataset(f"job_{j}", src.points, src.d_cut, src.rho_min, src.delta_min,
+                           queries=queries, arrival_s=t, seed=seed))
     return out
 
 
