@@ -177,6 +177,10 @@ dpc_status dpc_set_profiling(dpc_ctx* ctx, int on);
  *   "clevel"  coarse ring over blocks of 2^clevel cells per gridded dim,
  *             0 .. 8 (default 0: off)
  *   "ccap"    coarse cells with more points are not scanned (default 512)
+ *   "tree_min_d"  datasets with at least this many dimensions skip the grid
+ *             and take the point tree (a kd-tree-like search over all
+ *             dimensions), 1 .. 9 (default 9: never; on the blob workloads
+ *             the projected grid is faster at every d measured, 5 to 8)
  *   "max_batch_jobs"  served mode: jobs one batch admits at most, 1 .. 4096
  *             (default 64; 1 runs the jobs one at a time)
  * DPC_ERR_INVALID_ARG for an unknown key or a value out of range. */

@@ -321,7 +321,9 @@ __global__ void k_finalize(BatchView v, DeltaBufs db) {
         const DsDesc& ds = v.desc[b];
         const uint2 ro = v.ro_s[p];
         const int64_t g = ds.pt_off + ro.y;
-        if (ro.x == 0u) {  // the densest point: no dependent point, delta = infinity
+        if (ds.ptree) {
+            // the point-tree search handles all of this dataset's points
+        } else if (ro.x == 0u) {  // the densest point: no dependent point, delta = infinity
             v.dep[g] = -1;
             v.delta2[g] = INT64_MAX;
         } else {

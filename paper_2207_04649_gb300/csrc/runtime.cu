@@ -99,6 +99,7 @@ struct Tune {
     uint32_t bf_rank = 1024;  // open points ranked below this take the brute-force pass
     int clevel = 0;           // coarse ring: blocks of 2^clevel cells per gridded dim (0: off)
     uint32_t ccap = 512;      // coarse cells holding more points are not scanned
+    int tree_min_d = 9;       // datasets with at least this many dims take the point tree (9: none)
 };
 
 }  // namespace
@@ -156,6 +157,10 @@ struct Batch {
     int64_t ncells = 0, ndense = 0, nsparse = 0, nitems = 0, ntree = 0, nbf = 0;
     int64_t cand_pairs = 0;
     int64_t tree_visits = 0, tree_pairs = 0, ntree2 = 0;
+    // point tree (datasets with DsDesc::ptree)
+    std::vector<int> pt_ds;
+    int64_t pt_range[kMaxDims + 1][2] = {};  // per d: [t0, t1) in the point-tree concatenation
+    PtBufs pb{};
     unsigned long long* d_stats = nullptr;
     uint32_t* d_counters = nullptr;  // [32] rho + [32] ring work counters
     int out_is_device = 0;
@@ -274,16 +279,48 @@ struct Batch {
                     return fail(DPC_ERR_INVALID_ARG, "coordinates must lie in [0, 2^30)");
             }
             DPC_TRY(plan(b, mm.data() + (size_t)b * kMaxDims * 2, cbase));
-            ds.nleaf = (int32_t)((ds.n + kLeaf - 1) / kLeaf);
-            ds.h = ceil_log2((uint64_t)std::max<int32_t>(ds.nleaf, 1));
-            h_slot_off[b] = leaf_slots;
-            ds.leaf_off = leaf_slots;
-            ds.node_off = 2 * leaf_slots;
-            leaf_slots += 1ll << ds.h;
+            if (ds.ptree) continue;
             class_mask |= 1u << (3 * (ds.d - 1) + ds.mode);
             dim_mask |= 1u << (ds.d - 1);
         }
-        h_slot_off[B] = leaf_slots;
+        // point-tree datasets, grouped by dimension: leaf slots and nodes
+        pt_ds.clear();
+        for (int d = 1; d <= kMaxDims; ++d)
+            for (int b = 0; b < B; ++b)
+                if (hd[b].ptree && hd[b].d == d) pt_ds.push_back(b);
+        std::vector<int64_t> pt_leaf(pt_ds.size() + 1, 0), pt_pts(pt_ds.size() + 1, 0);
+        for (int d = 0; d <= kMaxDims; ++d) pt_range[d][0] = pt_range[d][1] = 0;
+        for (size_t j = 0; j < pt_ds.size(); ++j) {
+            DsDesc& ds = hd[pt_ds[j]];
+            ds.leaf_off = pt_leaf[j];
+            ds.node_off = 2 * pt_leaf[j];
+            pt_leaf[j + 1] = pt_leaf[j] + (1ll << ds.h);
+            pt_pts[j + 1] = pt_pts[j] + ds.n;
+            if (pt_range[ds.d][1] == 0) pt_range[ds.d][0] = pt_pts[j];
+            pt_range[ds.d][1] = pt_pts[j + 1];
+        }
+        leaf_slots = pt_leaf.back();
+        pb = PtBufs{};
+        pb.m = (int)pt_ds.size();
+        pb.nslots = leaf_slots;
+        if (pb.m > 0) {
+            int32_t* d_idx = nullptr;
+            int64_t *d_leaf = nullptr, *d_pts = nullptr;
+            DPC_CK(keep.get(&d_idx, pb.m));
+            DPC_CK(keep.get(&d_leaf, pb.m + 1));
+            DPC_CK(keep.get(&d_pts, pb.m + 1));
+            DPC_CK(keep.get(&pb.nodes, (size_t)2 * leaf_slots * kPtRec));
+            DPC_CK(keep.get(&pb.flag, leaf_slots));
+            DPC_CK(keep.get(&pb.stats, 4));
+            DPC_CK(cudaMemcpyAsync(d_idx, pt_ds.data(), sizeof(int32_t) * pb.m, cudaMemcpyHostToDevice, st));
+            DPC_CK(cudaMemcpyAsync(d_leaf, pt_leaf.data(), sizeof(int64_t) * (pb.m + 1), cudaMemcpyHostToDevice, st));
+            DPC_CK(cudaMemcpyAsync(d_pts, pt_pts.data(), sizeof(int64_t) * (pb.m + 1), cudaMemcpyHostToDevice, st));
+            DPC_CK(cudaMemsetAsync(pb.flag, 0, sizeof(uint32_t) * leaf_slots, st));
+            DPC_CK(cudaMemsetAsync(pb.stats, 0, 4 * sizeof(unsigned long long), st));
+            pb.ds_idx = d_idx;
+            pb.leaf_off = d_leaf;
+            pb.pt_off = d_pts;
+        }
         DPC_TRY(upload_desc());
         const int key_bits = bits_for(cbase > 0 ? cbase - 1 : 0);
         const bool key32 = key_bits <= 32;
@@ -330,6 +367,7 @@ struct Batch {
             DPC_TRY(sync("cell count"));
         }
         ncells = nc;
+        DPC_CK(launch_pt_build(v, pb, st));
 
         // hash table of the non-empty cells (load factor <= 1/2)
         const int hbits = ceil_log2((uint64_t)std::max<int64_t>(2 * ncells, 2));
@@ -402,12 +440,15 @@ struct Batch {
         DPC_CK(cudaMemsetAsync(v.rho_s, 0, sizeof(int32_t) * std::max<int64_t>(N, 1), st));
         DPC_CK(cudaMemsetAsync(d_counters, 0, 64 * sizeof(uint32_t), st));
         DPC_CK(launch_rho(v, w, class_mask, nitems, nsparse, d_counters, st));
+        for (int d = 1; d <= kMaxDims; ++d)
+            DPC_CK(launch_rho_ptree(v, pb, d, pt_range[d][0], pt_range[d][1], st));
         mark(2);
         DPC_CK(launch_rho_scatter(v, st));
-        unsigned long long pairs[2] = {0, 0};
+        unsigned long long pairs[2] = {0, 0}, ptst[4] = {0, 0, 0, 0};
         DPC_CK(cudaMemcpyAsync(pairs, d_stats, sizeof(pairs), cudaMemcpyDeviceToHost, st));
+        if (pb.m > 0) DPC_CK(cudaMemcpyAsync(ptst, pb.stats, sizeof(ptst), cudaMemcpyDeviceToHost, st));
         DPC_TRY(sync("density"));
-        cand_pairs = (int64_t)(pairs[0] + pairs[1]);
+        cand_pairs = (int64_t)(pairs[0] + pairs[1] + ptst[1]);
         DPC_TRY(check_err("density"));
         ms[0] = elapsed(0, 1);
         ms[1] = elapsed(1, 2);
@@ -422,6 +463,33 @@ struct Batch {
         const Tune& tn = ctx->tune;
         ds.s = ds.d_cut;  // cell side d_cut: neighbours are within one cell
         ds.R = 1;
+        ds.ptree = 0;
+        if (ds.n > 0 && ds.d >= tn.tree_min_d) {
+            // point tree: no grid; the sort key is the Morton code of all d
+            // coordinates, tb bits each (at most 48 bits per dataset)
+            ds.ptree = 1;
+            ds.k = 0;
+            ds.mbits = 0;
+            ds.tb = std::min(10, 48 / ds.d);
+            for (int c = 0; c < ds.d; ++c) {
+                ds.lo[c] = mm[2 * c];
+                ds.span[c] = mm[2 * c + 1] - mm[2 * c] + 1;
+            }
+            for (int j = 0; j < kMaxGridDims; ++j) {
+                ds.dmask[j] = 0;
+                ds.gdim[j] = 0;
+                ds.origin[j] = 0;
+                ds.ext[j] = 1;
+            }
+            ds.cbase = cbase;
+            cbase += 1ull << (ds.d * ds.tb);
+            ds.w32 = 0;
+            ds.mode = 1;
+            ds.rbits = bits_for((uint64_t)ds.n);
+            ds.nleaf = (int32_t)((ds.n + kLeaf - 1) / kLeaf);
+            ds.h = ceil_log2((uint64_t)ds.nleaf);
+            return DPC_OK;
+        }
         // grid the dims with the most cells (a dim with one cell filters nothing)
         struct Dim {
             int dim;
@@ -515,6 +583,12 @@ struct Batch {
         DPC_CK(tmp.get(&v.best_s, N));
         DPC_CK(cudaMemsetAsync(v.best_s, 0xff, sizeof(unsigned long long) * std::max<int64_t>(N, 1), st));
         DPC_CK(launch_ring(v, w, class_mask, nitems, nsparse, d_counters + 32, st));
+        if (pb.m > 0) {
+            DPC_CK(cudaMemsetAsync(pb.flag, 0, sizeof(uint32_t) * pb.nslots, st));
+            DPC_CK(launch_pt_minrank(v, pb, st));
+            for (int d = 1; d <= kMaxDims; ++d)
+                DPC_CK(launch_delta_ptree(v, pb, d, pt_range[d][0], pt_range[d][1], st));
+        }
         mark(2);
 
         DPC_CK(tmp.get(&db.ucount, 4));
@@ -608,9 +682,11 @@ struct Batch {
             DPC_CK(cudaMemcpyAsync(tstat, db.stats, sizeof(tstat), cudaMemcpyDeviceToHost, st));
             DPC_CK(cudaMemcpyAsync(&open2, db.tcount, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
         }
+        unsigned long long ptst[4] = {0, 0, 0, 0};
+        if (pb.m > 0) DPC_CK(cudaMemcpyAsync(ptst, pb.stats, sizeof(ptst), cudaMemcpyDeviceToHost, st));
         DPC_TRY(sync("dependent points"));
-        tree_visits = (int64_t)tstat[0];
-        tree_pairs = (int64_t)tstat[1];
+        tree_visits = (int64_t)(tstat[0] + ptst[2]);
+        tree_pairs = (int64_t)(tstat[1] + ptst[3]);
         ntree2 = open2;
         DPC_TRY(check_err("dependent points"));
         ms[2] = elapsed(0, 1);
@@ -718,6 +794,7 @@ dpc_status dpc_set_tuning(dpc_ctx* ctx, const char* key, int64_t value) {
     else if (k == "bf_rank" && value >= 0 && value <= UINT32_MAX) t.bf_rank = (uint32_t)value;
     else if (k == "clevel" && value >= 0 && value <= 8) t.clevel = (int)value;
     else if (k == "ccap" && value >= 1 && value <= (1 << 24)) t.ccap = (uint32_t)value;
+    else if (k == "tree_min_d" && value >= 1 && value <= 9) t.tree_min_d = (int)value;
     else if (k == "max_batch_jobs" && value >= 1 && value <= 4096) {
         std::lock_guard<std::mutex> lk(ctx->mu);
         ctx->max_batch_jobs = (int)value;
@@ -734,6 +811,7 @@ dpc_status dpc_get_tuning(dpc_ctx* ctx, const char* key, int64_t* value) {
     else if (k == "bf_rank") *value = t.bf_rank;
     else if (k == "clevel") *value = t.clevel;
     else if (k == "ccap") *value = t.ccap;
+    else if (k == "tree_min_d") *value = t.tree_min_d;
     else if (k == "max_batch_jobs") {
         std::lock_guard<std::mutex> lk(ctx->mu);
         *value = ctx->max_batch_jobs;

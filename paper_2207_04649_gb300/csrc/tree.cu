@@ -133,7 +133,9 @@ __global__ void k_refit(BatchView v, DeltaBufs db) {
     }
     uint32_t mr = 0xffffffffu;
     const uint32_t p0 = v.cell_start[c], p1 = v.cell_start[c + 1];
-    for (uint32_t p = p0; p < p1; ++p) {
+    // a point-tree dataset's single cell stays empty here (its points are
+    // never searched through this tree)
+    for (uint32_t p = p0; p < p1 && !ds.ptree; ++p) {
         const int4* r = v.rec + ds.rec_off + ((int64_t)p - ds.pt_off) * ds.dp;
         const int4 a = r[0];
         const int4 e = ds.dp == 2 ? r[1] : make_int4(0, 0, 0, 0);

@@ -28,11 +28,13 @@ def dpc():
     return m
 
 
-def run_host(dpc, pts, d_cut, queries):
+def run_host(dpc, pts, d_cut, queries, knobs=None):
     """Whole path through the host-pointer ABI; several label queries."""
     pts = np.ascontiguousarray(pts, dtype=np.int32)
     n = pts.shape[0]
     with dpc.Context(0) as ctx:
+        if knobs:
+            ctx.tune(**knobs)
         rho = np.full(n, -7, np.int32)
         ds = ctx.density(pts, d_cut, rho)
         dep = np.full(n, -7, np.int32)
@@ -48,8 +50,8 @@ def run_host(dpc, pts, d_cut, queries):
     return rho, dep, d2, labs, info
 
 
-def assert_full_parity(dpc, pts, d_cut, queries):
-    rho, dep, d2, labs, info = run_host(dpc, pts, d_cut, queries)
+def assert_full_parity(dpc, pts, d_cut, queries, knobs=None):
+    rho, dep, d2, labs, info = run_host(dpc, pts, d_cut, queries, knobs)
     orho = oracle.rho(pts, d_cut)
     np.testing.assert_array_equal(rho, orho)
     odep, od2 = oracle.dependent(pts, orho)
@@ -109,6 +111,38 @@ def test_random_shapes_bit_exact(dpc, shape):
     ds = workloads.random_blobs(seed, n, d, dc, domain=dom, blobs=blobs, spread=spread, dup=dup)
     queries = [(2, dc + 1), (1, 3 * dc + 1), (5, 10 * dc)]
     assert_full_parity(dpc, ds.points, dc, queries)
+
+
+@pytest.mark.parametrize("shape", SHAPES, ids=lambda s: f"n{s[1]}_d{s[2]}_dc{s[3]}")
+def test_random_shapes_point_tree(dpc, shape):
+    """The point tree (every dimension, no grid) on the same shapes."""
+    seed, n, d, dc, dom, blobs, spread, dup = shape
+    ds = workloads.random_blobs(seed, n, d, dc, domain=dom, blobs=blobs, spread=spread, dup=dup)
+    info = assert_full_parity(dpc, ds.points, dc, [(2, dc + 1), (5, 10 * dc)], dict(tree_min_d=1))
+    assert info["grid_dims"] == 0
+
+
+@pytest.mark.parametrize("d", [5, 6, 7, 8])
+def test_high_dims_grid_path(dpc, d):
+    """The projected grid for d > 4 (the point tree switched off)."""
+    ds = workloads.random_blobs(60 + d, 2500, d, 9000, blobs=4, spread=0.05, dup=10)
+    info = assert_full_parity(dpc, ds.points, 9000, [(3, 27001)], dict(tree_min_d=9))
+    assert 1 <= info["grid_dims"] <= 4
+
+
+def test_point_tree_edge_cases(dpc):
+    knobs = dict(tree_min_d=1)
+    assert_full_parity(dpc, np.full((777, 3), 4242, np.int32), 10, [(1, 11), (778, 11)], knobs)
+    rng = np.random.default_rng(99)
+    pts = rng.integers(0, 50, size=(3000, 2)).astype(np.int32)
+    assert_full_parity(dpc, pts, 10_000_000, [(1, 10_000_001)], knobs)
+    base = rng.integers(0, (1 << 30) - 1, size=(4, 8))
+    pts = np.concatenate([np.clip(b + rng.normal(0, 3e6, size=(300, 8)), 0, (1 << 30) - 1)
+                          for b in base]).astype(np.int32)
+    assert_full_parity(dpc, pts, 2_000_000, [(2, 50_000_000)], knobs)
+    for n in (1, 2, 16, 17, 33):
+        pts = rng.integers(0, 1000, size=(n, 5)).astype(np.int32)
+        assert_full_parity(dpc, pts, 300, [(1, 301)], dict(tree_min_d=5))
 
 
 def test_all_points_identical(dpc):
@@ -255,7 +289,8 @@ def test_plain_5p8m_3d_sampled(dpc):
 # ------------------------------------------------------- tuning knobs
 
 @pytest.mark.parametrize("knobs", [dict(clevel=2, ccap=512), dict(clevel=1, ccap=64, bf_rank=0),
-                                   dict(kch=64, bf_rank=100000), dict(kmax=2), dict(kmax=1, clevel=3)],
+                                   dict(kch=64, bf_rank=100000), dict(kmax=2), dict(kmax=1, clevel=3),
+                                   dict(tree_min_d=3), dict(tree_min_d=1, bf_rank=0)],
                          ids=lambda k: ",".join(f"{a}={b}" for a, b in k.items()))
 def test_tuning_knobs_do_not_change_results(dpc, knobs):
     ds = workloads.random_blobs(77, 6000, 3, 900, blobs=5, spread=0.06, dup=8)
