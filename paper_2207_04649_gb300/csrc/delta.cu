@@ -393,63 +393,83 @@ constexpr int kBfThreads = 128;
 constexpr int kBfTile = 256;
 
 // One thread per open point, the block's points consecutive in global rank
-// order; the union of their higher-ranked prefixes streams through shared
-// memory in tiles and every thread keeps the candidates of its own prefix.
+// order (so grouped by dataset). For each dataset in the block, the longest
+// higher-ranked prefix among the block's points of that dataset streams
+// through shared memory in tiles, and every thread of that dataset keeps the
+// candidates of its own prefix.
 template <int D>
 __global__ void __launch_bounds__(kBfThreads) k_bruteforce(BatchView v, DeltaBufs db) {
     __shared__ int4 tile[kBfTile * 2];
     __shared__ uint32_t torig[kBfTile];
-    __shared__ int64_t s_lo, s_hi;
+    __shared__ int32_t s_b[kBfThreads];
+    __shared__ int64_t s_hi[kBfThreads];
+    __shared__ int32_t seg_b[kBfThreads];
+    __shared__ int64_t seg_hi[kBfThreads];
+    __shared__ int s_nseg;
     const uint32_t cnt = db.ucount[1];
     const int64_t i = (int64_t)blockIdx.x * kBfThreads + threadIdx.x;
     if ((int64_t)blockIdx.x * kBfThreads >= cnt) return;
-    if (threadIdx.x == 0) {
-        s_lo = INT64_MAX;
-        s_hi = 0;
-    }
-    __syncthreads();
     const bool valid = i < cnt;
     uint32_t p = 0;
-    int b = 0;
-    int64_t my_lo = 0, my_hi = 0;  // candidate positions [my_lo, my_hi) in global rank order
-    bool mine = false;
+    int b = -1;
+    int64_t my_hi = 0;  // candidates: global rank-order positions [pt_off[b], my_hi)
     if (valid) {
         p = db.bf_sorted[i];
         b = find_ds(v.pt_off, v.B, p);
-        my_lo = v.pt_off[b];
-        my_hi = my_lo + v.ro_s[p].x;
-        mine = v.desc[b].d == D;
-        atomicMin((unsigned long long*)&s_lo, (unsigned long long)my_lo);
-        atomicMax((unsigned long long*)&s_hi, (unsigned long long)my_hi);
+        my_hi = v.pt_off[b] + v.ro_s[p].x;
+    }
+    s_b[threadIdx.x] = b;
+    s_hi[threadIdx.x] = my_hi;
+    __syncthreads();
+    if (threadIdx.x == 0) {  // the block's datasets of dimension D and their longest prefixes
+        int ns = 0;
+        for (int t = 0; t < kBfThreads; ++t) {
+            const int bt = s_b[t];
+            if (bt < 0 || v.desc[bt].d != D) continue;
+            if (ns == 0 || seg_b[ns - 1] != bt) {
+                seg_b[ns] = bt;
+                seg_hi[ns] = s_hi[t];
+                ++ns;
+            } else {
+                seg_hi[ns - 1] = max(seg_hi[ns - 1], s_hi[t]);
+            }
+        }
+        s_nseg = ns;
     }
     __syncthreads();
+    const bool mine = valid && v.desc[b].d == D;
     int32_t x[D];
-    if (valid) {
+    if (mine) {
         const DsDesc& ds = v.desc[b];
         const int4* r = v.rec + ds.rec_off + ((int64_t)p - ds.pt_off) * ds.dp;
         load_pt<D>(r, x);
     }
     long long bestD = INT64_MAX;
     uint32_t bestJ = 0xffffffffu;
-    for (int64_t base = s_lo; base < s_hi; base += kBfTile) {
-        const int64_t nt = min((int64_t)kBfTile, s_hi - base);
-        for (int t = threadIdx.x; t < nt * 2; t += kBfThreads) tile[t] = db.rrec[base * 2 + t];
-        for (int t = threadIdx.x; t < nt; t += kBfThreads) torig[t] = db.rorig[base + t];
-        __syncthreads();
-        if (mine) {
-            const int64_t j0 = max((int64_t)0, my_lo - base), j1 = min(nt, my_hi - base);
-            for (int64_t j = j0; j < j1; ++j) {
-                int32_t c[D];
-                load_pt<D>(tile + 2 * j, c);
-                const long long dd = dist64<D>(x, c);
-                const uint32_t o = torig[j];
-                if (dd < bestD || (dd == bestD && o < bestJ)) {
-                    bestD = dd;
-                    bestJ = o;
+    const int nseg = s_nseg;
+    for (int sg = 0; sg < nseg; ++sg) {
+        const int sb = seg_b[sg];
+        const int64_t lo = v.pt_off[sb], hi = seg_hi[sg];
+        for (int64_t base = lo; base < hi; base += kBfTile) {
+            const int64_t nt = min((int64_t)kBfTile, hi - base);
+            for (int t = threadIdx.x; t < nt * 2; t += kBfThreads) tile[t] = db.rrec[base * 2 + t];
+            for (int t = threadIdx.x; t < nt; t += kBfThreads) torig[t] = db.rorig[base + t];
+            __syncthreads();
+            if (mine && b == sb) {
+                const int64_t j1 = min(nt, my_hi - base);
+                for (int64_t j = 0; j < j1; ++j) {
+                    int32_t c[D];
+                    load_pt<D>(tile + 2 * j, c);
+                    const long long dd = dist64<D>(x, c);
+                    const uint32_t o = torig[j];
+                    if (dd < bestD || (dd == bestD && o < bestJ)) {
+                        bestD = dd;
+                        bestJ = o;
+                    }
                 }
             }
+            __syncthreads();
         }
-        __syncthreads();
     }
     if (mine) {
         const int64_t g = v.pt_off[b] + v.ro_s[p].y;
