@@ -53,6 +53,22 @@ def dist_env():
     return ws, rank, local
 
 
+def max_over_ranks(x: float, dist=None, device="cpu") -> float:
+    """The largest of every rank's x (the whole job is as slow as its slowest
+    rank); x itself without a process group."""
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([x], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(ws: int, units_per_rank: float, steps: int, total_ms: float) -> float:
+    """Units all ranks processed per second over the slowest rank's time."""
+    return ws * units_per_rank * steps / (total_ms / 1e3)
+
+
 # ------------------------------------------------------------------ clocks
 
 class ClockSampler:
@@ -138,6 +154,47 @@ def auto_sample(ds) -> int:
 
 # ----------------------------------------------------------------- our arm
 
+def derived_pair_peak(d: int, form: int, sm_mhz) -> dict:
+    """Pair-test ceiling from unit counts: 152 SMs x 4 schedulers x 32
+    integer lanes at the SM clock seen under load (2070 MHz when none was
+    sampled), over the integer operations one pair takes in the kernel's
+    form: d + 3 for the expanded form (add, d multiply-adds, shift,
+    accumulate), 2d + 2 for the direct 32-bit form, 4d + 3 for 64-bit."""
+    mhz = sm_mhz or 2070.0
+    ops = d + 3 if form == 2 else (2 * d + 2 if form == 0 else 4 * d + 3)
+    lane_ops = 152 * 4 * 32 * mhz * 1e6
+    return {"value": lane_ops / ops / 1e9, "unit": "Gpair/s", "ops_per_pair": ops, "sm_mhz": mhz,
+            "derivation": f"152 SMs x 4 x 32 lanes x {mhz:.0f} MHz / {ops} integer ops per pair"}
+
+
+RHO_SOURCES = ("rho.cu", "stages.cuh", "dpc_internal.cuh")
+
+
+def rho_source_digest() -> str:
+    """sha256 over the density kernels' sources: DRAM counters taken on
+    another version of them do not describe this build."""
+    import hashlib
+    h = hashlib.sha256()
+    for f in RHO_SOURCES:
+        with open(os.path.join(ROOT, "paper_2207_04649_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
+def rho_traffic(workload: str):
+    """DRAM bytes (read + write) of one step's density pair launches, from
+    the ncu capture summarized in profiles/, or None when that capture was
+    of another workload or another version of the kernels."""
+    tpath = os.path.join(ROOT, "profiles", "rho_traffic.json")
+    if not os.path.exists(tpath):
+        return None
+    with open(tpath) as f:
+        tj = json.load(f)
+    if tj.get("workload") != workload or tj.get("source_sha256") != rho_source_digest():
+        return None
+    return tj.get("dram_bytes_per_launch")
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -205,12 +262,8 @@ def run_ours(args):
         dist.barrier()
     clk = clocks.stop()
     step_ms = [a.elapsed_time(b) for a, b in evs]
-    total_ms = sum(step_ms)
-    if dist:
-        t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-    value = ws * n * args.steps / (total_ms / 1e3)
+    total_ms = max_over_ranks(sum(step_ms), dist, dev)
+    value = whole_job_rate(ws, n, args.steps, total_ms)
 
     # end to end: pinned host input -> host results, through the same ABI
     h_pts = torch.from_numpy(ds.points).pin_memory().numpy()
@@ -229,24 +282,14 @@ def run_ours(args):
         t1 = time.perf_counter()
         if i >= args.warmup:
             e2e_s.append(t1 - t0)
-    e2e_total = sum(e2e_s)
-    if dist:
-        t = torch.tensor([e2e_total], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_total = float(t.item())
-    e2e_value = ws * n * len(e2e_s) / e2e_total
+    e2e_total = max_over_ranks(sum(e2e_s), dist, dev)
+    e2e_value = whole_job_rate(ws, n, len(e2e_s), 1e3 * e2e_total)
 
     # roofline of the dominant kernel: the density pair kernels (ALU bound)
     rho_ms = statistics.mean(i["ms_rho"] for i in infos)
     pairs = infos[-1]["cand_pairs"]
     achieved = pairs / (rho_ms / 1e3)
-    traffic = None
-    tpath = os.path.join(ROOT, "profiles", "rho_traffic.json")
-    if os.path.exists(tpath):
-        with open(tpath) as f:
-            tj = json.load(f)
-        if tj.get("workload") == args.workload:
-            traffic = tj.get("dram_bytes_per_launch")
+    traffic = rho_traffic(args.workload)
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
@@ -278,6 +321,7 @@ def run_ours(args):
                                         f"{pair_mode}) with operands in registers on all SMs "
                                         "(dpc_probe_pair_rate), same run",
                          "pair_mode": pair_mode,
+                         "peak_derived": derived_pair_peak(d, pair_mode, clk.get("sm_mhz")),
                          "pairs_per_launch": pairs, "ms_per_launch": rho_ms},
             "stages_ms": {k: statistics.mean(i[k] for i in infos)
                           for k in ("ms_grid", "ms_rho", "ms_rank", "ms_ring", "ms_rest", "ms_label")},
@@ -402,18 +446,14 @@ def run_batched(args):
     launches = dpc.dpc_kernel_launches() - l0
     clk = clocks.stop()
     info = ctx.last_batch_info()
-    total_ms = sum(ms)
-    if dist:
-        t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-    value = ws * len(probs) * args.steps / (total_ms / 1e3)
+    total_ms = max_over_ranks(sum(ms), dist, dev)
+    value = whole_job_rate(ws, len(probs), args.steps, total_ms)
     # the same datasets one at a time (device inputs), and host-buffer runs
     run(djobs, together=False)
     alone_ms = sum(timed(djobs, 1, together=False))
     run(hjobs)
-    e2e_ms = sum(timed(hjobs, args.steps, events=False))
-    e2e_value = ws * len(probs) * args.steps / (e2e_ms / 1e3)
+    e2e_ms = max_over_ranks(sum(timed(hjobs, args.steps, events=False)), dist, dev)
+    e2e_value = whole_job_rate(ws, len(probs), args.steps, e2e_ms)
     achieved = info["cand_pairs"] / (info["ms_rho"] / 1e3) if info["ms_rho"] > 0 else 0.0
     if rank == 0:
         line = {
@@ -493,6 +533,11 @@ def run_served(args):
 
     ws, rank, local = dist_env()
     torch.cuda.set_device(local)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    dev = torch.device("cuda", local)
     trace = workloads.served_trace()
     warm = workloads.served_trace(seed=6, jobs=max(8, args.warmup * 8), pool=8)
 
@@ -510,12 +555,16 @@ def run_served(args):
 
     clocks = ClockSampler(local)
     clocks.start()
+    if dist:
+        dist.barrier()
     lat, span, launches = serve(64)
     clk = clocks.stop()
+    span = max_over_ranks(span, dist, dev)
     lat1, span1, _ = serve(1)
+    span1 = max_over_ranks(span1, dist, dev)
     pts = sum(ds.n for ds in trace)
     q = lambda a, f: float(np.percentile(np.asarray(a), f))
-    value = len(trace) / span
+    value = whole_job_rate(ws, len(trace), 1, 1e3 * span)
     if rank == 0:
         line = {
             "metric": SERVED_METRIC, "value": value, "unit": "jobs/s", "n_gpus": ws, "steps": 1,
@@ -527,7 +576,8 @@ def run_served(args):
                        "parallelism": f"replicas x{ws}",
                        "l2": "inputs are copied from host memory for every job",
                        "p50_ms": q(lat, 50), "p99_ms": q(lat, 99),
-                       "one_at_a_time": {"jobs_per_s": len(trace) / span1, "p50_ms": q(lat1, 50),
+                       "one_at_a_time": {"jobs_per_s": whole_job_rate(ws, len(trace), 1, 1e3 * span1),
+                                         "p50_ms": q(lat1, 50),
                                          "p99_ms": q(lat1, 99)}},
             "e2e": {"value": value, "unit": "jobs/s", "h2d_bytes_per_step": sum(ds.n * ds.d * 4 for ds in trace),
                     "d2h_bytes_per_step": sum(ds.n * (16 + 4 * len(ds.queries)) + 8 * len(ds.queries)
@@ -538,6 +588,8 @@ def run_served(args):
             "gpu_launches": launches,
         }
         print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
 
 
 def main():

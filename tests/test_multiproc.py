@@ -1,0 +1,71 @@
+"""The N > 1 bench path on the CPU: world_size-2 gloo process groups for the
+rank reduction, and the reference arm under torchrun (rank 0 alone prints
+one line; the other rank exits 0 without work)."""
+import json
+import os
+import socket
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+
+
+def free_port() -> int:
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _rank_main(rank, ws, port, out_dir):
+    import torch.distributed as dist
+    import bench
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=ws)
+    # every rank timed its own replica; the job is as slow as the slowest
+    own_ms = 100.0 + 50.0 * rank
+    total = bench.max_over_ranks(own_ms, dist, "cpu")
+    value = bench.whole_job_rate(ws, 1000, 4, total)
+    dist.barrier()
+    with open(os.path.join(out_dir, f"rank{rank}.json"), "w") as f:
+        json.dump({"total": total, "value": value}, f)
+    dist.destroy_process_group()
+
+
+def test_max_over_ranks_with_gloo(tmp_path):
+    import torch.multiprocessing as mp
+    ws = 2
+    port = free_port()
+    mp.start_processes(_rank_main, args=(ws, port, str(tmp_path)), nprocs=ws, start_method="spawn")
+    res = [json.load(open(tmp_path / f"rank{r}.json")) for r in range(ws)]
+    for r in res:
+        assert r["total"] == 150.0
+        # 2 ranks x 1000 units x 4 steps in 150 ms
+        assert r["value"] == pytest.approx(2 * 1000 * 4 / 0.150)
+
+
+def test_single_process_helpers():
+    import bench
+    assert bench.max_over_ranks(3.5) == 3.5
+    assert bench.whole_job_rate(1, 5_800_000, 10, 111.5) == pytest.approx(5_800_000 * 10 / 0.1115)
+    p = bench.derived_pair_peak(3, 2, 2070.0)
+    assert p["ops_per_pair"] == 6 and p["value"] == pytest.approx(152 * 128 * 2.07e9 / 6 / 1e9)
+
+
+def test_reference_arm_under_torchrun():
+    port = free_port()
+    cmd = [sys.executable, "-m", "torch.distributed.run", "--nnodes=1", "--nproc-per-node", "2",
+           "--master-addr", "127.0.0.1", "--master-port", str(port), os.path.join(ROOT, "bench.py"),
+           "--impl", "reference", "--gpus", "2", "--workload", "plain_20k_2d", "--steps", "2",
+           "--warmup", "1", "--cpu-sample", "40"]
+    r = subprocess.run(cmd, cwd=ROOT, capture_output=True, text=True, timeout=300)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [ln for ln in r.stdout.splitlines() if ln.startswith("{")]
+    assert len(lines) == 1, r.stdout
+    line = json.loads(lines[0])
+    assert line["impl"] == "reference" and line["n_gpus"] == 2
+    assert line["cpu_baseline"]["kind"] == "oracle" and line["value"] > 0
+    assert line["e2e"]["h2d_bytes_per_step"] == 0

@@ -152,6 +152,18 @@ def plain_5p8m_3d(seed: int = 2, n: int = 5_800_000) -> Dataset:
     return Dataset("plain_5p8m_3d", pts, d_cut, 10, 10 * d_cut, seed=seed)
 
 
+def plain_2m_3d(seed: int = 2, n: int = 2_000_000) -> Dataset:
+    """A 2M-point draw of the same 3-d mixture (the profiling case: its
+    device footprint stays well under the bench case's); d_cut is the
+    5.8M set's calibrated cutoff scaled by (5.8M / n)^(1/3), which keeps the
+    expected neighbour count, and rho_min / delta_min follow it."""
+    big = _load_calibrated().get("plain_5p8m_3d")
+    base = int(big["d_cut"]) if big is not None else 178
+    d_cut = int(round(base * (5_800_000 / n) ** (1.0 / 3.0)))
+    pts, _, _ = _c2_draw(seed, n)
+    return Dataset("plain_2m_3d", pts, d_cut, 10, 10 * d_cut, seed=seed)
+
+
 def _c3_draw(seed: int, n: int):
     rng = np.random.default_rng(seed)
     centers = rng.uniform(10_000, 90_000, size=(20, 8))
@@ -255,5 +267,6 @@ def random_blobs(seed: int, n: int, d: int, d_cut: int, domain: int = DOMAIN,
 NAMED = {
     "plain_20k_2d": plain_20k_2d,
     "plain_5p8m_3d": plain_5p8m_3d,
+    "plain_2m_3d": plain_2m_3d,
     "plain_1m_8d": plain_1m_8d,
 }
