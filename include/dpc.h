@@ -62,7 +62,7 @@ typedef struct {
     int device;              /* CUDA device ordinal */
     void* cuda_stream;       /* cudaStream_t to run on; NULL: the context creates its own */
     uint64_t hbm_cap_bytes;  /* device memory the served mode may hold at once; 0: 150 GB */
-    const char* tune_cache;  /* autotuner cache file (JSON) or NULL */
+    const char* tune_cache;  /* autotuner cache file (text, see dpc_autotune) or NULL */
     int debug_checks;        /* nonzero: synchronize and check after every stage */
     int mode;                /* 0: batched (dpc_flush runs the submitted jobs);
                                 1: served (a worker thread admits jobs continuously) */
@@ -255,6 +255,24 @@ dpc_status dpc_flush(dpc_ctx* ctx);
  * pair_mode) are its first dataset's. No counterpart in the paper.
  * DPC_ERR_STATE before the first batch finishes. */
 dpc_status dpc_last_batch_info(dpc_ctx* ctx, dpc_info* out);
+
+/* Autotuner (no counterpart in the paper). Runs the n_jobs sample jobs as
+ * one batch under candidate settings of the knobs that change speed only
+ * (kch, bf_rank, clevel; kmax when some d >= 4; tree_min_d when some
+ * d >= 5): coordinate descent from the context's current knobs, each
+ * setting timed as the best of `repeats` (1 .. 100) synchronous runs, a
+ * change kept only when it is at least 2% faster. The fastest setting
+ * becomes the context's knobs and its entry for the sample's signature (the
+ * largest d and the rounded log2 of the mean n): later batches with that
+ * signature run with it. With a tune_cache path in dpc_options the entries
+ * are written there (one text line per signature) and read back by
+ * dpc_create. When report is not NULL it receives the chosen setting as
+ * "key=value ..." text, NUL-terminated, at most report_len bytes. The jobs'
+ * outputs are written by every run (same values each time). Errors: those
+ * of dpc_submit's checks and of a run; DPC_ERR_STATE when the cache file
+ * cannot be written. */
+dpc_status dpc_autotune(dpc_ctx* ctx, const dpc_job* jobs, int32_t n_jobs, int32_t repeats, char* report,
+                        size_t report_len);
 
 /* Block until the job is done or timeout_ms passes (DPC_ERR_TIMEOUT). */
 dpc_status dpc_wait(dpc_ctx* ctx, uint64_t ticket, int64_t timeout_ms, dpc_result* out);

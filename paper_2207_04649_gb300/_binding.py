@@ -92,6 +92,8 @@ def lib():
             "dpc_release": ([vp], st),
             "dpc_ds_info": ([vp, ctypes.POINTER(DpcInfo)], st),
             "dpc_last_batch_info": ([vp, ctypes.POINTER(DpcInfo)], st),
+            "dpc_autotune": ([vp, ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32, ctypes.c_char_p,
+                              ctypes.c_size_t], st),
             "dpc_set_profiling": ([vp, ctypes.c_int], st),
             "dpc_submit": ([vp, ctypes.POINTER(DpcJob), ctypes.POINTER(ctypes.c_uint64)], st),
             "dpc_poll": ([vp, ctypes.c_uint64, ctypes.POINTER(DpcResult)], st),
@@ -136,8 +138,9 @@ def _check(status: int, where: str, ok=(DPC_OK,)) -> int:
 
 # ---------------------------------------------------------------- raw calls
 
-def dpc_create(device=0, stream_ptr=0, hbm_cap_bytes=0, mode=0, max_inflight=0, debug=0):
-    o = DpcOptions(device, stream_ptr or None, hbm_cap_bytes, None, debug, mode, max_inflight)
+def dpc_create(device=0, stream_ptr=0, hbm_cap_bytes=0, mode=0, max_inflight=0, debug=0, tune_cache=None):
+    o = DpcOptions(device, stream_ptr or None, hbm_cap_bytes, tune_cache.encode() if tune_cache else None, debug,
+                   mode, max_inflight)
     h = ctypes.c_void_p()
     _check(lib().dpc_create(ctypes.byref(o), ctypes.byref(h)), "dpc_create")
     return h
@@ -171,6 +174,15 @@ def dpc_ds_info(ds) -> dict:
     info = DpcInfo()
     _check(lib().dpc_ds_info(ds, ctypes.byref(info)), "dpc_ds_info")
     return info.as_dict()
+
+
+def dpc_autotune(ctx, jobs, repeats: int = 2) -> str:
+    """Autotune on the sample jobs (a list of Job); returns the chosen setting."""
+    arr = (DpcJob * len(jobs))(*[j.c for j in jobs])
+    buf = ctypes.create_string_buffer(512)
+    _check(lib().dpc_autotune(ctx, ctypes.cast(arr, ctypes.c_void_p), len(jobs), int(repeats), buf, 512),
+           "dpc_autotune")
+    return buf.value.decode()
 
 
 def dpc_last_batch_info(ctx) -> dict:
@@ -248,7 +260,7 @@ class Context:
     their own work against it."""
 
     def __init__(self, device: int = 0, stream=None, mode: int = 0, hbm_cap_bytes: int = 0,
-                 max_inflight: int = 0, debug: bool = False, profiling: bool = False):
+                 max_inflight: int = 0, debug: bool = False, profiling: bool = False, tune_cache=None):
         self.device = device
         self.stream = stream
         ptr = 0
@@ -260,7 +272,7 @@ class Context:
                 ptr = self.stream.cuda_stream
         except ImportError:
             pass
-        self.handle = dpc_create(device, ptr, hbm_cap_bytes, mode, max_inflight, 1 if debug else 0)
+        self.handle = dpc_create(device, ptr, hbm_cap_bytes, mode, max_inflight, 1 if debug else 0, tune_cache)
         if profiling:
             dpc_set_profiling(self.handle, True)
 
@@ -323,6 +335,9 @@ class Context:
 
     def last_batch_info(self) -> dict:
         return dpc_last_batch_info(self.handle)
+
+    def autotune(self, jobs, repeats: int = 2) -> str:
+        return dpc_autotune(self.handle, jobs, repeats)
 
 
 class Dataset:

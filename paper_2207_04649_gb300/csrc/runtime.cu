@@ -3,8 +3,13 @@
 #include <algorithm>
 #include <atomic>
 #include <chrono>
+#include <cmath>
 #include <condition_variable>
+#include <cstdio>
 #include <cstring>
+#include <fstream>
+#include <map>
+#include <sstream>
 #include <deque>
 #include <memory>
 #include <mutex>
@@ -134,14 +139,77 @@ struct dpc_ctx {
     int max_batch_jobs = 64;  // served mode: jobs admitted into one batch at most
     bool has_last = false;    // last_info holds the most recent finished batch of jobs
     dpc_info last_info{};
+    std::string tune_cache;   // autotuner file ("" when none)
+    std::map<std::pair<int, int>, dpc::Tune> tuned;  // (largest d, log2 mean n) -> knobs
 };
 
 namespace dpc {
 namespace {
 
+// Signature of a batch for the autotuner's cache: the largest d and the
+// rounded log2 of the mean n.
+std::pair<int, int> tune_signature(const std::vector<Input>& in) {
+    int dmax = 1;
+    int64_t n = 0;
+    for (const auto& x : in) {
+        dmax = std::max(dmax, (int)x.d);
+        n += x.n;
+    }
+    const double mean = in.empty() ? 1.0 : std::max(1.0, (double)n / (double)in.size());
+    return {dmax, (int)std::lround(std::log2(mean))};
+}
+
+// The knobs a batch runs with: the autotuner's entry for its signature, else
+// the context's.
+Tune tune_for(dpc_ctx* ctx, const std::vector<Input>& in) {
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    auto it = ctx->tuned.find(tune_signature(in));
+    return it != ctx->tuned.end() ? it->second : ctx->tune;
+}
+
+std::string tune_line(const std::pair<int, int>& sig, const Tune& t) {
+    std::ostringstream o;
+    o << "dmax=" << sig.first << " nlog=" << sig.second << " kch=" << t.kch << " kmax=" << t.kmax
+      << " bf_rank=" << t.bf_rank << " clevel=" << t.clevel << " ccap=" << t.ccap << " tree_min_d=" << t.tree_min_d;
+    return o.str();
+}
+
+// Cache file: one tune_line per signature; unknown or malformed lines are
+// skipped.
+void load_tune_cache(dpc_ctx* ctx) {
+    std::ifstream f(ctx->tune_cache);
+    std::string line;
+    while (std::getline(f, line)) {
+        int dmax, nlog, kch, kmax, clevel, tmd;
+        unsigned bf, ccap;
+        if (std::sscanf(line.c_str(), "dmax=%d nlog=%d kch=%d kmax=%d bf_rank=%u clevel=%d ccap=%u tree_min_d=%d",
+                        &dmax, &nlog, &kch, &kmax, &bf, &clevel, &ccap, &tmd) != 8)
+            continue;
+        if (kch < 32 || kch > (1 << 20) || kmax < 1 || kmax > kMaxGridDims || clevel < 0 || clevel > 8 ||
+            ccap < 1 || tmd < 1 || tmd > 9)
+            continue;
+        Tune t;
+        t.kch = kch;
+        t.kmax = kmax;
+        t.bf_rank = bf;
+        t.clevel = clevel;
+        t.ccap = ccap;
+        t.tree_min_d = tmd;
+        ctx->tuned[{dmax, nlog}] = t;
+    }
+}
+
+bool save_tune_cache(dpc_ctx* ctx) {
+    std::ofstream f(ctx->tune_cache, std::ios::trunc);
+    if (!f) return false;
+    for (const auto& e : ctx->tuned) f << tune_line(e.first, e.second) << "\n";
+    return (bool)f;
+}
+
 struct Batch {
     dpc_ctx* ctx = nullptr;
     cudaStream_t st = nullptr;
+    Tune tune;  // the knobs this batch runs with (fixed when its density starts)
     int B = 0;
     int64_t N = 0;
     std::vector<DsDesc> hd;
@@ -213,6 +281,7 @@ struct Batch {
     // ---------------------------------------------------------- density
     dpc_status density(const std::vector<Input>& in) {
         if (!st) st = ctx->stream;
+        tune = tune_for(ctx, in);
         keep.st = dens.st = st;
         B = (int)in.size();
         hd.assign(B, DsDesc{});
@@ -411,7 +480,7 @@ struct Batch {
         DPC_CK(dens.get(&cb.item_off, ndense + 1));
         uint32_t kmask = 0;
         for (int b = 0; b < B; ++b) kmask |= (hd[b].R == 1 && hd[b].k >= 1) ? 1u << hd[b].k : 1u;
-        DPC_CK(launch_dense_prep(v, cb, ncells, ndense, ctx->tune.kch, kmask, temp, st));
+        DPC_CK(launch_dense_prep(v, cb, ncells, ndense, tune.kch, kmask, temp, st));
         uint32_t ni = 0;
         if (ndense > 0) {
             DPC_CK(cudaMemcpyAsync(&ni, cb.nitems, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
@@ -421,7 +490,7 @@ struct Batch {
         }
         nitems = ni;
         DPC_CK(keep.get(&cb.items, nitems + 1));
-        DPC_CK(launch_fill_items(v, cb, ndense, ctx->tune.kch, st));
+        DPC_CK(launch_fill_items(v, cb, ndense, tune.kch, st));
         w.dense = cb.dense;
         w.ndense = cb.ndense;
         w.sparse = cb.sparse;
@@ -431,7 +500,7 @@ struct Batch {
         w.cand = cb.cand;
         w.items = cb.items;
         w.nitems = cb.nitems;
-        w.kch = ctx->tune.kch;
+        w.kch = tune.kch;
         w.nbs = nbs;
         w.stats = d_stats;
         mark(1);
@@ -460,7 +529,7 @@ struct Batch {
     // Grid plan of dataset b from its bounding box mm[2 * dim + {0, 1}].
     dpc_status plan(int b, const int32_t* mm, uint64_t& cbase) {
         DsDesc& ds = hd[b];
-        const Tune& tn = ctx->tune;
+        const Tune& tn = tune;
         ds.s = ds.d_cut;  // cell side d_cut: neighbours are within one cell
         ds.R = 1;
         ds.ptree = 0;
@@ -596,7 +665,7 @@ struct Batch {
         DPC_CK(tmp.get(&db.bf_list, N));
         DPC_CK(cudaMemsetAsync(db.ucount, 0, 4 * sizeof(uint32_t), st));
         db.tcount = db.ucount;
-        db.bf_rank = ctx->tune.bf_rank;
+        db.bf_rank = tune.bf_rank;
         DPC_CK(launch_finalize(v, db, st));
         uint32_t uc[2] = {0, 0};
         DPC_CK(cudaMemcpyAsync(uc, db.ucount, sizeof(uc), cudaMemcpyDeviceToHost, st));
@@ -621,9 +690,9 @@ struct Batch {
             const int64_t nc = ncells;
             db.ncells = nc;
             // coarse ring over blocks of 2^clevel cells per gridded dim
-            if (ctx->tune.clevel > 0) {
-                db.clevel = ctx->tune.clevel;
-                db.ccap = ctx->tune.ccap;
+            if (tune.clevel > 0) {
+                db.clevel = tune.clevel;
+                db.ccap = tune.ccap;
                 uint32_t* d_nco = nullptr;
                 void* t4 = nullptr;
                 DPC_CK(tmp.get(&db.cflag, nc));
@@ -758,6 +827,10 @@ dpc_status dpc_create(const dpc_options* opt, dpc_ctx** out) {
     c->mode = o.mode;
     c->cap = o.hbm_cap_bytes ? o.hbm_cap_bytes : dpc::kDefaultCap;
     c->max_inflight = o.max_inflight > 0 ? o.max_inflight : 4;
+    if (o.tune_cache && o.tune_cache[0]) {
+        c->tune_cache = o.tune_cache;
+        dpc::load_tune_cache(c);
+    }
     if (o.cuda_stream) {
         c->stream = (cudaStream_t)o.cuda_stream;
     } else {
@@ -1151,6 +1224,94 @@ dpc_status dpc_flush(dpc_ctx* ctx) {
     dpc_status s = dpc::run_jobs(ctx, group, ctx->stream);
     dpc::finish(ctx, group, s);
     return s;
+}
+
+dpc_status dpc_autotune(dpc_ctx* ctx, const dpc_job* jobs, int32_t n_jobs, int32_t repeats, char* report,
+                        size_t report_len) {
+    if (!ctx || !jobs || n_jobs < 1) return fail(DPC_ERR_INVALID_ARG, "ctx or jobs is NULL, or n_jobs < 1");
+    if (repeats < 1 || repeats > 100) return fail(DPC_ERR_INVALID_ARG, "repeats must be in [1, 100]");
+    std::vector<dpc::JobPtr> group;
+    std::vector<dpc::Input> in;
+    for (int i = 0; i < n_jobs; ++i) {
+        DPC_TRY(dpc::check_job(&jobs[i]));
+        auto rec = std::make_shared<dpc_ctx::JobRec>();
+        rec->job = jobs[i];
+        rec->rmin.assign(jobs[i].rho_min, jobs[i].rho_min + jobs[i].n_queries);
+        rec->dmin.assign(jobs[i].delta_min, jobs[i].delta_min + jobs[i].n_queries);
+        group.push_back(rec);
+        in.push_back({jobs[i].points, jobs[i].n, jobs[i].d, jobs[i].d_cut, jobs[i].is_device ? 1 : 0});
+    }
+    const auto sig = dpc::tune_signature(in);
+    cudaSetDevice(ctx->device);
+    dpc::Tune best;
+    {
+        std::lock_guard<std::mutex> lk(ctx->mu);
+        best = ctx->tune;
+    }
+    dpc_status err = DPC_OK;
+    // best of `repeats` synchronous runs of the sample under knobs t
+    auto time_with = [&](const dpc::Tune& t) {
+        {
+            std::lock_guard<std::mutex> lk(ctx->mu);
+            ctx->tuned[sig] = t;
+        }
+        double ms = 1e300;
+        for (int r = 0; r < repeats && err == DPC_OK; ++r) {
+            const auto t0 = std::chrono::steady_clock::now();
+            err = dpc::run_jobs(ctx, group, ctx->stream);
+            const auto t1 = std::chrono::steady_clock::now();
+            ms = std::min(ms, std::chrono::duration<double, std::milli>(t1 - t0).count());
+        }
+        return ms;
+    };
+    // coordinate descent over the knobs that change speed only
+    double cur = time_with(best);
+    struct Knob {
+        const char* name;
+        std::vector<int64_t> values;
+    };
+    std::vector<Knob> knobs = {{"kch", {1024, 2048, 4096}}, {"bf_rank", {256, 1024, 4096}}, {"clevel", {0, 2}}};
+    if (sig.first >= 4) knobs.push_back({"kmax", {3, 4}});
+    if (sig.first >= 5) knobs.push_back({"tree_min_d", {9, 5}});
+    auto with = [](dpc::Tune t, const std::string& k, int64_t v) {
+        if (k == "kch") t.kch = (int)v;
+        else if (k == "bf_rank") t.bf_rank = (uint32_t)v;
+        else if (k == "clevel") t.clevel = (int)v;
+        else if (k == "kmax") t.kmax = (int)v;
+        else if (k == "tree_min_d") t.tree_min_d = (int)v;
+        return t;
+    };
+    for (const auto& k : knobs) {
+        for (int64_t v : k.values) {
+            if (err != DPC_OK) break;
+            const dpc::Tune t = with(best, k.name, v);
+            if (dpc::tune_line(sig, t) == dpc::tune_line(sig, best)) continue;
+            const double ms = time_with(t);
+            if (err == DPC_OK && ms < 0.98 * cur) {  // keep a change only when it is clearly faster
+                best = t;
+                cur = ms;
+            }
+        }
+    }
+    {
+        std::lock_guard<std::mutex> lk(ctx->mu);
+        ctx->tuned[sig] = best;
+        ctx->tune = best;
+    }
+    if (err != DPC_OK) return err;
+    if (!ctx->tune_cache.empty()) {
+        std::lock_guard<std::mutex> lk(ctx->mu);
+        if (!dpc::save_tune_cache(ctx)) return fail(DPC_ERR_STATE, "cannot write the tune cache " + ctx->tune_cache);
+    }
+    if (report && report_len > 0) {
+        std::ostringstream o;
+        o << dpc::tune_line(sig, best) << " ms=" << cur;
+        const std::string r = o.str();
+        const size_t m = std::min(report_len - 1, r.size());
+        std::memcpy(report, r.data(), m);
+        report[m] = '\0';
+    }
+    return DPC_OK;
 }
 
 dpc_status dpc_destroy(dpc_ctx* ctx) {

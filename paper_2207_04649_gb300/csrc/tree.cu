@@ -199,6 +199,13 @@ __device__ __forceinline__ long long node_test(const int4* rec, int dpb, const i
     return s;
 }
 
+// A node is skipped when nothing in it ranks higher (INT64_MAX from
+// node_test; real squared distances stay below it for coordinates under
+// 2^30) or when its box is farther than the best distance so far.
+__device__ __forceinline__ bool out_of_reach(long long d, long long best) {
+    return d == INT64_MAX || d > best;
+}
+
 constexpr int kStack = 96;
 
 template <int D>
@@ -231,7 +238,7 @@ __global__ void __launch_bounds__(128) k_tree_search(BatchView v, DeltaBufs db) 
             const int32_t nd = stack[--sp];
             ++visits;
             int4 meta;
-            if (node_test<D>(db.nodes + rec_of(db, nd) * ns, dpb, x, ro.x, meta) > bestD) continue;
+            if (out_of_reach(node_test<D>(db.nodes + rec_of(db, nd) * ns, dpb, x, ro.x, meta), bestD)) continue;
             if (nd < 0) {  // a cell: scan its points
                 for (int32_t q = meta.y; q < meta.z; ++q) {
                     const uint2 cr = v.ro_s[q];
@@ -261,11 +268,11 @@ __global__ void __launch_bounds__(128) k_tree_search(BatchView v, DeltaBufs db) 
             const long long d0 = node_test<D>(db.nodes + rec_of(db, meta.y) * ns, dpb, x, ro.x, m0);
             const long long d1 = node_test<D>(db.nodes + rec_of(db, meta.z) * ns, dpb, x, ro.x, m1);
             if (d1 < d0) {
-                if (d0 <= bestD) stack[sp++] = meta.y;
-                if (d1 <= bestD) stack[sp++] = meta.z;
+                if (!out_of_reach(d0, bestD)) stack[sp++] = meta.y;
+                if (!out_of_reach(d1, bestD)) stack[sp++] = meta.z;
             } else {
-                if (d1 <= bestD) stack[sp++] = meta.z;
-                if (d0 <= bestD) stack[sp++] = meta.y;
+                if (!out_of_reach(d1, bestD)) stack[sp++] = meta.z;
+                if (!out_of_reach(d0, bestD)) stack[sp++] = meta.y;
             }
         }
         const int64_t g = ds.pt_off + ro.y;

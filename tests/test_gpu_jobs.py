@@ -196,3 +196,41 @@ def test_last_batch_info_before_any_batch(dpc):
         with pytest.raises(dpc.DpcError) as e:
             ctx.last_batch_info()
         assert e.value.status == dpc.DPC_ERR_STATE
+
+
+def test_autotune_keeps_results_and_writes_cache(dpc, tmp_path):
+    probs = workloads.batch_256(count=16)
+    cache = str(tmp_path / "tune.txt")
+    with dpc.Context(0, mode=0) as ctx:
+        ref = [dpc.Job(ds.points, ds.d_cut, [(ds.rho_min, ds.delta_min)]) for ds in probs]
+        for j in ref:
+            ctx.submit(j)
+        ctx.flush()
+        for j in ref:
+            assert ctx.poll(j.ticket)[0] == dpc.DPC_OK
+    with dpc.Context(0, mode=0, tune_cache=cache) as ctx:
+        jobs = [dpc.Job(ds.points, ds.d_cut, [(ds.rho_min, ds.delta_min)]) for ds in probs]
+        rep = ctx.autotune(jobs, repeats=1)
+        assert "kch=" in rep and "dmax=" in rep
+        for k in ("kch", "bf_rank", "clevel"):
+            assert f"{k}={ctx.tuning(k)}" in rep
+        with pytest.raises(dpc.DpcError):
+            ctx.autotune(jobs, repeats=0)
+    lines = open(cache).read().splitlines()
+    assert len(lines) == 1 and lines[0].startswith("dmax=")
+    for a, b in zip(jobs, ref):
+        np.testing.assert_array_equal(a.rho, b.rho)
+        np.testing.assert_array_equal(a.dep, b.dep)
+        np.testing.assert_array_equal(a.delta2, b.delta2)
+        np.testing.assert_array_equal(a.label, b.label)
+    # a new context reads the cache and runs the same batch with its entry
+    with dpc.Context(0, mode=0, tune_cache=cache) as ctx:
+        again = [dpc.Job(ds.points, ds.d_cut, [(ds.rho_min, ds.delta_min)]) for ds in probs]
+        for j in again:
+            ctx.submit(j)
+        ctx.flush()
+        for j in again:
+            assert ctx.poll(j.ticket)[0] == dpc.DPC_OK
+    for a, b in zip(again, ref):
+        np.testing.assert_array_equal(a.label, b.label)
+        np.testing.assert_array_equal(a.dep, b.dep)
