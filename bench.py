@@ -181,10 +181,11 @@ def rho_source_digest() -> str:
     return h.hexdigest()
 
 
-def rho_traffic(workload: str):
-    """DRAM bytes (read + write) of one step's density pair launches, from
-    the ncu capture summarized in profiles/, or None when that capture was
-    of another workload or another version of the kernels."""
+def rho_traffic(workload: str, key: str = "dram_bytes_per_launch"):
+    """DRAM bytes (read + write) of one step's density pair launches (key
+    dram_bytes_per_launch: dense + sparse kernels; *_dense: the dense kernel),
+    from the ncu capture summarized in profiles/, or None when that capture
+    was of another workload or another version of the kernels."""
     tpath = os.path.join(ROOT, "profiles", "rho_traffic.json")
     if not os.path.exists(tpath):
         return None
@@ -192,7 +193,7 @@ def rho_traffic(workload: str):
         tj = json.load(f)
     if tj.get("workload") != workload or tj.get("source_sha256") != rho_source_digest():
         return None
-    return tj.get("dram_bytes_per_launch")
+    return tj.get(key)
 
 
 def run_ours(args):
@@ -285,11 +286,16 @@ def run_ours(args):
     e2e_total = max_over_ranks(sum(e2e_s), dist, dev)
     e2e_value = whole_job_rate(ws, n, len(e2e_s), 1e3 * e2e_total)
 
-    # roofline of the dominant kernel: the density pair kernels (ALU bound)
+    # roofline of the dominant density kernel (dense cells; ALU bound), and of
+    # the density stage as a whole (dense + sparse cells)
     rho_ms = statistics.mean(i["ms_rho"] for i in infos)
+    dense_ms = statistics.mean(i["ms_rho_dense"] for i in infos)
     pairs = infos[-1]["cand_pairs"]
+    dpairs = infos[-1]["dense_pairs"]
     achieved = pairs / (rho_ms / 1e3)
+    dachieved = dpairs / (dense_ms / 1e3)
     traffic = rho_traffic(args.workload)
+    dtraffic = rho_traffic(args.workload, "dram_bytes_per_launch_dense")
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
@@ -314,18 +320,21 @@ def run_ours(args):
                        "mean_rho": float(rho.double().mean().item()), "n_centers": int(nc)},
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": n * d * 4,
                     "d2h_bytes_per_step": n * (4 + 4 + 8 + 4) + 8},
-            "roofline": {"bound": "alu", "kernel": "density pair kernels (dense + sparse cells)",
-                         "achieved": achieved / 1e9, "peak": probe_rate / 1e9, "unit": "Gpair/s",
-                         "frac": achieved / probe_rate, "traffic": traffic,
+            "roofline": {"bound": "alu", "kernel": f"k_rho_dense (dense cells, pair form {pair_mode})",
+                         "achieved": dachieved / 1e9, "peak": probe_rate / 1e9, "unit": "Gpair/s",
+                         "frac": dachieved / probe_rate, "traffic": dtraffic,
+                         "pairs_per_launch": dpairs, "ms_per_launch": dense_ms,
+                         "density_stage": {"kernels": "k_rho_dense + k_rho_sparse", "achieved": achieved / 1e9,
+                                           "frac": achieved / probe_rate, "traffic": traffic,
+                                           "pairs_per_step": pairs, "ms_per_step": rho_ms},
                          "peak_source": "measured: the kernel's own 32-bit pair test (form "
                                         f"{pair_mode}) with operands in registers on all SMs "
                                         "(dpc_probe_pair_rate), same run",
                          "pair_mode": pair_mode,
-                         "peak_derived": derived_pair_peak(d, pair_mode, clk.get("sm_mhz")),
-                         "pairs_per_launch": pairs, "ms_per_launch": rho_ms},
+                         "peak_derived": derived_pair_peak(d, pair_mode, clk.get("sm_mhz"))},
             "stages_ms": {k: statistics.mean(i[k] for i in infos)
                           for k in ("ms_grid", "ms_rho", "ms_rank", "ms_ring", "ms_rest", "ms_label")},
-            "work": {k: infos[-1][k] for k in ("cells", "dense_cells", "work_items", "cand_pairs",
+            "work": {k: infos[-1][k] for k in ("cells", "dense_cells", "work_items", "cand_pairs", "dense_pairs",
                                                "open_after_ring", "brute_points", "grid_dims", "pair_bits",
                                                "tree_visits", "tree_pairs", "open_after_coarse")},
             "cpu_baseline": cpu,

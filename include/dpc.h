@@ -161,6 +161,9 @@ typedef struct {
     int64_t open_after_coarse;  /* points the coarse ring left for the tree search */
     int32_t pair_mode;        /* density pair test: 0 direct 32-bit, 1 direct 64-bit, 2 expanded 32-bit */
     int32_t reserved;
+    int64_t dense_pairs;      /* of cand_pairs, those of dense cells (one warp per work item) */
+    float ms_rho_dense;       /* of ms_rho, the dense cells' kernels (profiling on) */
+    int32_t reserved2;
 } dpc_info;
 
 dpc_status dpc_ds_info(const dpc_ds* ds, dpc_info* out);
@@ -170,7 +173,7 @@ dpc_status dpc_set_profiling(dpc_ctx* ctx, int on);
 
 /* Tuning knobs of a context (no counterpart in the paper; they change speed,
  * never results). Keys and ranges:
- *   "kch"     candidates per dense work item, 32 .. 2^20 (default 2048)
+ *   "kch"     candidates per dense work item, 32 .. 2^20 (default 1024)
  *   "kmax"    gridded dimensions at most, 1 .. 4 (default 4)
  *   "bf_rank" points still open after the ring search whose rank is below
  *             this take the brute-force pass (default 1024)

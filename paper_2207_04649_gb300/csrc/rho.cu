@@ -79,7 +79,7 @@ __device__ __forceinline__ uint2 resolve_probe(const BatchView& v, uint64_t key,
 template <int K>
 __global__ void __launch_bounds__(256) k_cell_runs(BatchView v, CellPrepBufs cb, int64_t ncells) {
     constexpr int NNB = K == 1 ? 3 : (K == 2 ? 9 : (K == 3 ? 27 : 81));
-    unsigned long long pairs = 0;
+    unsigned long long pairs = 0, spairs = 0;  // dense cells', sparse cells' candidate pairs
     for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < ncells; c += (int64_t)gridDim.x * blockDim.x) {
         const uint32_t cs = v.cell_start[c], m = v.cell_start[c + 1] - cs;
         const int b = find_ds(v.pt_off, v.B, cs);
@@ -133,15 +133,20 @@ __global__ void __launch_bounds__(256) k_cell_runs(BatchView v, CellPrepBufs cb,
         }
         cb.nruns[c] = nr;
         cb.cand[c] = cand;
-        pairs += (unsigned long long)m * cand;
+        if (m > (uint32_t)kSparseMax) pairs += (unsigned long long)m * cand;
+        else spairs += (unsigned long long)m * cand;
     }
-    for (int o = 16; o > 0; o >>= 1) pairs += __shfl_xor_sync(0xffffffffu, pairs, o);
+    for (int o = 16; o > 0; o >>= 1) {
+        pairs += __shfl_xor_sync(0xffffffffu, pairs, o);
+        spairs += __shfl_xor_sync(0xffffffffu, spairs, o);
+    }
     if ((threadIdx.x & 31) == 0 && pairs) atomicAdd(&cb.stats[0], pairs);
+    if ((threadIdx.x & 31) == 0 && spairs) atomicAdd(&cb.stats[1], spairs);
 }
 
 // Any k, any reach R (used when R != 1).
 __global__ void __launch_bounds__(256) k_cell_runs_any(BatchView v, CellPrepBufs cb, int64_t ncells) {
-    unsigned long long pairs = 0;
+    unsigned long long pairs = 0, spairs = 0;  // dense cells', sparse cells' candidate pairs
     for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < ncells; c += (int64_t)gridDim.x * blockDim.x) {
         const uint32_t cs = v.cell_start[c], m = v.cell_start[c + 1] - cs;
         const int b = find_ds(v.pt_off, v.B, cs);
@@ -169,10 +174,15 @@ __global__ void __launch_bounds__(256) k_cell_runs_any(BatchView v, CellPrepBufs
         }
         cb.nruns[c] = nr;
         cb.cand[c] = cand;
-        pairs += (unsigned long long)m * cand;
+        if (m > (uint32_t)kSparseMax) pairs += (unsigned long long)m * cand;
+        else spairs += (unsigned long long)m * cand;
     }
-    for (int o = 16; o > 0; o >>= 1) pairs += __shfl_xor_sync(0xffffffffu, pairs, o);
+    for (int o = 16; o > 0; o >>= 1) {
+        pairs += __shfl_xor_sync(0xffffffffu, pairs, o);
+        spairs += __shfl_xor_sync(0xffffffffu, spairs, o);
+    }
     if ((threadIdx.x & 31) == 0 && pairs) atomicAdd(&cb.stats[0], pairs);
+    if ((threadIdx.x & 31) == 0 && spairs) atomicAdd(&cb.stats[1], spairs);
 }
 
 __global__ void k_item_count(BatchView v, CellPrepBufs cb, int kch) {
@@ -282,18 +292,45 @@ __global__ void __launch_bounds__(kRhoThreads) k_rho_dense(BatchView v, CellWork
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     uint2* srun = sruns[wid];
     const uint32_t nitems = *w.nitems;
+    // the next item's index, record and cell are fetched in stages while the
+    // current item runs (one stage per candidate chunk)
+    uint32_t nx = 0, it_n = 0, c_n = 0, cs_n = 0, ce_n = 0, nr_n = 0, ct_n = 0;
+    uint4 item_n = make_uint4(0u, 0u, 0u, 0u);
+    auto stage = [&](int s) {
+        if (s == 0) {
+            it_n = __shfl_sync(0xffffffffu, nx, 0);
+            if (it_n < nitems) item_n = w.items[it_n];
+        } else if (s == 1) {
+            if (it_n < nitems) c_n = w.dense[item_n.x];
+        } else if (s == 2) {
+            if (it_n < nitems) {
+                cs_n = v.cell_start[c_n];
+                ce_n = v.cell_start[c_n + 1];
+                nr_n = w.nruns[c_n];
+                ct_n = w.cand[c_n];
+            }
+        }
+    };
+    if (lane == 0) nx = atomicAdd(counter, 1u);
+    stage(0);
+    stage(1);
+    stage(2);
     while (true) {
-        uint32_t it = 0;
-        if (lane == 0) it = atomicAdd(counter, 1u);
-        it = __shfl_sync(0xffffffffu, it, 0);
+        const uint32_t it = it_n;
         if (it >= nitems) break;
-        const uint4 item = w.items[it];
-        const uint32_t dc = item.x, qc = item.y, kc = item.z;
-        const uint32_t c = w.dense[dc];
-        const uint32_t cs = v.cell_start[c], m = v.cell_start[c + 1] - cs;
+        const uint4 item = item_n;  // (dense cell, query chunk, candidate chunk)
+        const uint32_t qc = item.y, kc = item.z;
+        const uint32_t c = c_n;
+        const uint32_t cs = cs_n, m = ce_n - cs_n;
+        const uint32_t nr_c = nr_n, ctot_c = ct_n;
+        if (lane == 0) nx = atomicAdd(counter, 1u);
+        int pf = 0;
         const int b = find_ds(v.pt_off, v.B, cs);
         const DsDesc& ds = v.desc[b];
-        if (ds.d != D || ds.mode != MODE) continue;
+        if (ds.d != D || ds.mode != MODE) {
+            for (; pf < 3; ++pf) stage(pf);
+            continue;
+        }
         const int4* recb = v.rec + ds.rec_off - ds.pt_off * DP;  // indexed by global sorted position
         const int q0 = (int)qc * kQch;
         const int nq = min(kQch, (int)m - q0);
@@ -333,7 +370,7 @@ __global__ void __launch_bounds__(kRhoThreads) k_rho_dense(BatchView v, CellWork
         }
         uint32_t cnt[4] = {0u, 0u, 0u, 0u};
         // the cell's runs into shared memory, then the candidate stream
-        const uint32_t nr = w.nruns[c], ctot = w.cand[c];
+        const uint32_t nr = nr_c, ctot = ctot_c;
         for (uint32_t t = lane; t < nr; t += 32) srun[t] = w.runs[(int64_t)c * w.nbs + t];
         __syncwarp();
         const uint32_t k0 = kc * (uint32_t)w.kch;
@@ -365,6 +402,7 @@ __global__ void __launch_bounds__(kRhoThreads) k_rho_dense(BatchView v, CellWork
             __syncwarp();
             have = cst.prep(lane, recb, nullptr, &bad);
             sb ^= 1;
+            if (pf < 3) stage(pf++);
             if (EXP) {
                 switch (Q) {
                     case 1: eval_rho_x<D, 1>(buf, nb, grp, G, qa, qb, cnt); break;
@@ -381,6 +419,7 @@ __global__ void __launch_bounds__(kRhoThreads) k_rho_dense(BatchView v, CellWork
                 }
             }
         }
+        for (; pf < 3; ++pf) stage(pf);
         if (bad && lane == 0) atomicOr(v.err, kErrStaging);
         __syncwarp();
         // add the groups' counts, then one lane per query writes
@@ -491,18 +530,19 @@ cudaError_t launch_fill_items(const BatchView& v, const CellPrepBufs& cb, int64_
 }
 
 cudaError_t launch_rho(const BatchView& v, const CellWork& w, uint32_t class_mask, int64_t nitems_bound,
-                       int64_t nsparse_bound, uint32_t* counters, cudaStream_t st) {
+                       int64_t nsparse_bound, uint32_t* counters, int parts, cudaStream_t st) {
     // one dense launch per (dimension, arithmetic mode) class present in the
     // batch and one sparse launch per (dimension, width); each kernel skips
-    // the work of the other classes
+    // the work of the other classes. parts: bit 0 dense kernels, bit 1 sparse
 #define DPC_BIT(D, M) (class_mask & (1u << (3 * ((D) - 1) + (M))))
-#define DPC_RHO_CLASS(D)                                                                                 \
-    if (DPC_BIT(D, 0)) launch_rho_dense<D, 0>(v, w, nitems_bound, counters + 3 * (D - 1), st);           \
-    if (DPC_BIT(D, 1)) launch_rho_dense<D, 1>(v, w, nitems_bound, counters + 3 * (D - 1) + 1, st);       \
-    if (DPC_BIT(D, 0) || DPC_BIT(D, 2)) launch_rho_sparse<D, false>(v, w, nsparse_bound, st);            \
-    if (DPC_BIT(D, 1)) launch_rho_sparse<D, true>(v, w, nsparse_bound, st);
+#define DPC_RHO_CLASS(D)                                                                                  \
+    if ((parts & 1) && DPC_BIT(D, 0)) launch_rho_dense<D, 0>(v, w, nitems_bound, counters + 3 * (D - 1), st); \
+    if ((parts & 1) && DPC_BIT(D, 1))                                                                     \
+        launch_rho_dense<D, 1>(v, w, nitems_bound, counters + 3 * (D - 1) + 1, st);                       \
+    if ((parts & 2) && (DPC_BIT(D, 0) || DPC_BIT(D, 2))) launch_rho_sparse<D, false>(v, w, nsparse_bound, st); \
+    if ((parts & 2) && DPC_BIT(D, 1)) launch_rho_sparse<D, true>(v, w, nsparse_bound, st);
 #define DPC_RHO_X(D) \
-    if (DPC_BIT(D, 2)) launch_rho_dense<D, 2>(v, w, nitems_bound, counters + 3 * (D - 1) + 2, st);
+    if ((parts & 1) && DPC_BIT(D, 2)) launch_rho_dense<D, 2>(v, w, nitems_bound, counters + 3 * (D - 1) + 2, st);
     DPC_RHO_CLASS(1) DPC_RHO_CLASS(2) DPC_RHO_CLASS(3) DPC_RHO_CLASS(4)
     DPC_RHO_CLASS(5) DPC_RHO_CLASS(6) DPC_RHO_CLASS(7) DPC_RHO_CLASS(8)
     DPC_RHO_X(1) DPC_RHO_X(2) DPC_RHO_X(3)

@@ -99,7 +99,7 @@ struct Input {
 };
 
 struct Tune {
-    int kch = 2048;         // candidates per dense work item
+    int kch = 1024;         // candidates per dense work item
     int kmax = 4;           // gridded dims at most
     uint32_t bf_rank = 1024;  // open points ranked below this take the brute-force pass
     int clevel = 0;           // coarse ring: blocks of 2^clevel cells per gridded dim (0: off)
@@ -234,7 +234,9 @@ struct Batch {
     int out_is_device = 0;
     float ms[6] = {0, 0, 0, 0, 0, 0};
     int refs = 0;
-    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+    cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+    int64_t dense_pairs = 0;
+    float ms_rho_dense = 0.f;
 
     ~Batch() {
         keep.release();
@@ -508,7 +510,9 @@ struct Batch {
         // local density
         DPC_CK(cudaMemsetAsync(v.rho_s, 0, sizeof(int32_t) * std::max<int64_t>(N, 1), st));
         DPC_CK(cudaMemsetAsync(d_counters, 0, 64 * sizeof(uint32_t), st));
-        DPC_CK(launch_rho(v, w, class_mask, nitems, nsparse, d_counters, st));
+        DPC_CK(launch_rho(v, w, class_mask, nitems, nsparse, d_counters, 1, st));
+        mark(4);
+        DPC_CK(launch_rho(v, w, class_mask, nitems, nsparse, d_counters, 2, st));
         for (int d = 1; d <= kMaxDims; ++d)
             DPC_CK(launch_rho_ptree(v, pb, d, pt_range[d][0], pt_range[d][1], st));
         mark(2);
@@ -518,9 +522,11 @@ struct Batch {
         if (pb.m > 0) DPC_CK(cudaMemcpyAsync(ptst, pb.stats, sizeof(ptst), cudaMemcpyDeviceToHost, st));
         DPC_TRY(sync("density"));
         cand_pairs = (int64_t)(pairs[0] + pairs[1] + ptst[1]);
+        dense_pairs = (int64_t)pairs[0];
         DPC_TRY(check_err("density"));
         ms[0] = elapsed(0, 1);
         ms[1] = elapsed(1, 2);
+        ms_rho_dense = elapsed(1, 4);
         dens.release();
         has_density = true;
         return DPC_OK;
@@ -985,6 +991,8 @@ static void fill_info(const Batch& bt, int b, dpc_info* out) {
     out->tree_pairs = bt.tree_pairs;
     out->open_after_coarse = bt.ntree2;
     out->pair_mode = h.mode;
+    out->dense_pairs = bt.dense_pairs;
+    out->ms_rho_dense = bt.ms_rho_dense;
 }
 
 dpc_status dpc_ds_info(const dpc_ds* ds, dpc_info* out) {

@@ -214,7 +214,7 @@ cudaError_t launch_fill_items(const BatchView& v, const CellPrepBufs& cb, int64_
 // class_mask bit 3*(d-1) + mode: a dataset of dimension d with density test
 // mode `mode` (DsDesc::mode) is in the batch. counters: [24], zeroed.
 cudaError_t launch_rho(const BatchView& v, const CellWork& w, uint32_t class_mask, int64_t nitems_bound,
-                       int64_t nsparse_bound, uint32_t* counters, cudaStream_t st);
+                       int64_t nsparse_bound, uint32_t* counters, int parts, cudaStream_t st);
 cudaError_t launch_rho_scatter(const BatchView& v, cudaStream_t st);
 
 // delta.cu
