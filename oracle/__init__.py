@@ -8,13 +8,15 @@ does, and it shares no code with the library.
 The arithmetic lives in ``dpc_oracle.c`` (plain C with OpenMP over points,
 built here with gcc); this module compiles it and wraps it with numpy. Every
 function follows the paper's problem definition (Section 2.1, Definitions
-1-6) and its straightforward Scan algorithm (Section 2.2). The readings of
-the paper it takes are listed at the top of ``dpc_oracle.c``.
+1-6) and its straightforward Scan algorithm (Section 2.2); the ``approx_*``
+functions follow Approx-DPC's dependent-point rules (Section 4.3). The
+readings of the paper it takes are listed in ``dpc_oracle.c``.
 
 Parity status: every function is pinned by the tests in
-``tests/test_oracle.py`` (hand-worked examples in ``tests/golden/``, closed
-forms, invariants and an independent brute force), so none is "parity
-unpinned".
+``tests/test_oracle.py`` and ``tests/test_oracle_approx.py`` (hand-worked
+examples in ``tests/golden/``, closed forms, invariants, an independent
+brute force, the paper's cluster-center guarantee for Approx-DPC, and
+planted mistakes), so none is "parity unpinned".
 """
 from __future__ import annotations
 
@@ -42,7 +44,7 @@ def build(force: bool = False) -> str:
             and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)):
         return _LIB_PATH
     tmp = _LIB_PATH + f".tmp{os.getpid()}"
-    cmd = ["gcc", "-O2", "-fopenmp", "-fPIC", "-shared", "-std=c99", _SRC, "-o", tmp]
+    cmd = ["gcc", "-O2", "-fopenmp", "-fPIC", "-shared", "-std=c99", _SRC, "-o", tmp, "-lm"]
     subprocess.run(cmd, check=True)
     os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
@@ -64,6 +66,10 @@ def _load():
         lib.oracle_dependent_subset.argtypes = [vp, i64, i32, vp, vp, i64, vp, vp]
         lib.oracle_label.argtypes = [i64, vp, vp, vp, i64, i64, vp]
         lib.oracle_label.restype = i64
+        lib.oracle_approx_side.argtypes = [i64, i32]
+        lib.oracle_approx_side.restype = i64
+        lib.oracle_approx_dependent.argtypes = [vp, i64, i32, i64, vp, vp, vp, vp]
+        lib.oracle_approx_dependent_subset.argtypes = [vp, i64, i32, i64, vp, vp, i64, vp, vp, vp]
         _lib = lib
         return lib
 
@@ -145,6 +151,47 @@ def label(rho_arr, dep, delta2, rho_min: int, delta_min: int):
     nc = _load().oracle_label(n, _ptr(r), _ptr(dp), _ptr(d2), int(rho_min), int(delta_min),
                               _ptr(lab))
     return lab, int(nc)
+
+
+def approx_side(d_cut: int, d: int) -> int:
+    """Approx-DPC's grid side: max(1, floor(d_cut / sqrt(d)))."""
+    return int(_load().oracle_approx_side(int(d_cut), int(d)))
+
+
+def approx_dependent(points, rho_arr, d_cut: int):
+    """Approx-DPC's dependent points (Section 4.3): (dep, delta2, exact) where
+    exact marks the points whose dependent point was computed exactly."""
+    p = _pts(points)
+    n, d = p.shape
+    r = np.ascontiguousarray(rho_arr, dtype=np.int32)
+    dep = np.empty(n, dtype=np.int32)
+    d2 = np.empty(n, dtype=np.int64)
+    ex = np.empty(n, dtype=np.int32)
+    _load().oracle_approx_dependent(_ptr(p), n, d, int(d_cut), _ptr(r), _ptr(dep), _ptr(d2), _ptr(ex))
+    return dep, d2, ex.astype(bool)
+
+
+def approx_dependent_subset(points, rho_arr, d_cut: int, idx):
+    """Approx-DPC's dependent points of the points listed in ``idx``."""
+    p = _pts(points)
+    n, d = p.shape
+    r = np.ascontiguousarray(rho_arr, dtype=np.int32)
+    ix = np.ascontiguousarray(idx, dtype=np.int64)
+    m = ix.shape[0]
+    dep = np.empty(m, dtype=np.int32)
+    d2 = np.empty(m, dtype=np.int64)
+    ex = np.empty(m, dtype=np.int32)
+    _load().oracle_approx_dependent_subset(_ptr(p), n, d, int(d_cut), _ptr(r), _ptr(ix), m, _ptr(dep), _ptr(d2),
+                                           _ptr(ex))
+    return dep, d2, ex.astype(bool)
+
+
+def run_approx(points, d_cut: int, rho_min: int, delta_min: int) -> dict:
+    """Approx-DPC: exact rho, approximate dependent points, labels."""
+    r = rho(points, d_cut)
+    dep, d2, ex = approx_dependent(points, r, d_cut)
+    lab, nc = label(r, dep, d2, rho_min, delta_min)
+    return {"rho": r, "dep": dep, "delta2": d2, "exact": ex, "label": lab, "n_centers": nc}
 
 
 def run(points, d_cut: int, rho_min: int, delta_min: int) -> dict:

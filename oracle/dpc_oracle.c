@@ -12,7 +12,9 @@
  * a linear scan for every local density, a sort by density, a scan of the
  * denser prefix for every dependent point, and a depth-first label
  * propagation from the cluster centers. OpenMP spreads the independent
- * per-point loops over the host cores; it changes no arithmetic.
+ * per-point loops over the host cores; it changes no arithmetic. The last
+ * part (oracle_approx_*) follows Approx-DPC's dependent-point rules
+ * (Section 4.3) on top of the same exact densities.
  *
  * Readings of the paper (it is silent or loose on these points):
  *  - dist() is Euclidean. It is compared squared, exactly, in 64-bit
@@ -36,6 +38,7 @@
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+#include <math.h>
 #ifdef _OPENMP
 #include <omp.h>
 #endif
@@ -204,4 +207,166 @@ int64_t oracle_label(int64_t n, const int32_t* rho, const int32_t* dep, const in
     free(child);
     free(stack);
     return n_centers;
+}
+
+/* ----------------------------------------------------------------------
+ * Approx-DPC's dependent points (Section 4.3, "Approximate computation"
+ * and "Exact computation"), on top of exact local densities.
+ *
+ * The grid G has non-empty cells of side d_cut / sqrt(d) (Section 4.1).
+ * Readings (the paper is silent or loose on these):
+ *  - The side is the integer s = max(1, floor(d_cut / sqrt(d))), anchored
+ *    at the per-dimension minimum of P: the cell of p has coordinates
+ *    floor((x_k - min_k) / s). Two points of one cell are then strictly
+ *    closer than d_cut, which is what the approximation rules rely on.
+ *  - p*(c) is the highest point of c in the total order (rho desc, index
+ *    asc) used everywhere else.
+ *  - "min over P(c') of rho > rho_i" reads, in that total order, as: every
+ *    point of c' is higher than p_i.
+ *  - N(c) is the set of cells other than c that hold a point p with
+ *    D(p*(c), p) < d_cut^2 (strict, as in Definition 1).
+ *  - When several cells of N(c) qualify, the one whose p* is highest wins.
+ *  - An approximated dependent distance is d_cut, i.e. delta2 = d_cut^2.
+ *  - A point left undecided gets its exact dependent point (Definitions 2-3,
+ *    ties to the smaller index); the top point keeps dep -1 and
+ *    delta2 = INT64_MAX.
+ * exact[i] is 1 when point i's dependent point is the exact one.
+ */
+
+/* floor(sqrt(a)) for 0 <= a < 2^62 (the library square root as a first
+ * guess, corrected in integers). */
+static int64_t isqrt_i64(int64_t a) {
+    int64_t r = (int64_t)sqrt((double)a);
+    while (r > 0 && r * r > a) --r;
+    while ((r + 1) * (r + 1) <= a) ++r;
+    return r;
+}
+
+int64_t oracle_approx_side(int64_t d_cut, int32_t d) {
+    int64_t s = isqrt_i64((d_cut * d_cut) / d);
+    return s < 1 ? 1 : s;
+}
+
+/* Cell coordinates of every point (n x d, int64). */
+static int64_t* approx_cells(const int32_t* P, int64_t n, int32_t d, int64_t s) {
+    int64_t* cc = (int64_t*)malloc((size_t)(n > 0 ? n : 1) * d * sizeof(int64_t));
+    for (int32_t k = 0; k < d; ++k) {
+        int64_t lo = 0;
+        for (int64_t i = 0; i < n; ++i)
+            if (i == 0 || P[i * d + k] < lo) lo = P[i * d + k];
+        for (int64_t i = 0; i < n; ++i) cc[i * d + k] = ((int64_t)P[i * d + k] - lo) / s;
+    }
+    return cc;
+}
+
+static const int64_t* g_cc;  /* qsort context: cell coordinates */
+static int32_t g_d;
+static int cmp_cells(const void* a, const void* b) {
+    const int64_t i = *(const int64_t*)a, j = *(const int64_t*)b;
+    for (int32_t k = 0; k < g_d; ++k) {
+        const int64_t x = g_cc[i * g_d + k], y = g_cc[j * g_d + k];
+        if (x != y) return x < y ? -1 : 1;
+    }
+    return i < j ? -1 : (i > j ? 1 : 0);
+}
+
+/* Dependent points of the m points listed in idx (all n when idx is NULL). */
+static void approx_dependent(const int32_t* P, int64_t n, int32_t d, int64_t d_cut, const int32_t* rho,
+                             const int64_t* idx, int64_t m, int32_t* dep_out, int64_t* delta2_out,
+                             int32_t* exact_out) {
+    if (n <= 0) return;
+    const int64_t r2 = d_cut * d_cut;
+    const int64_t s = oracle_approx_side(d_cut, d);
+    int64_t* cc = approx_cells(P, n, d, s);
+    /* rank of every point */
+    int64_t* order = (int64_t*)malloc((size_t)n * sizeof(int64_t));
+    int64_t* rank = (int64_t*)malloc((size_t)n * sizeof(int64_t));
+    oracle_rank_order(rho, n, order);
+    for (int64_t r = 0; r < n; ++r) rank[order[r]] = r;
+    /* group the points by cell: sort by cell coordinates, then number the cells */
+    int64_t* by_cell = (int64_t*)malloc((size_t)n * sizeof(int64_t));
+    for (int64_t i = 0; i < n; ++i) by_cell[i] = i;
+    g_cc = cc;
+    g_d = d;
+    qsort(by_cell, (size_t)n, sizeof(int64_t), cmp_cells);
+    int64_t* cell = (int64_t*)malloc((size_t)n * sizeof(int64_t));
+    int64_t* pstar = (int64_t*)malloc((size_t)n * sizeof(int64_t));    /* per cell: highest point */
+    int64_t* maxrank = (int64_t*)malloc((size_t)n * sizeof(int64_t));  /* per cell: lowest point's rank */
+    int64_t ncell = 0;
+    for (int64_t t = 0; t < n; ++t) {
+        const int64_t i = by_cell[t];
+        int same = 0;
+        if (t > 0) {
+            const int64_t j = by_cell[t - 1];
+            same = 1;
+            for (int32_t k = 0; k < d; ++k)
+                if (cc[i * d + k] != cc[j * d + k]) same = 0;
+        }
+        if (!same) {
+            pstar[ncell] = i;
+            maxrank[ncell] = rank[i];
+            ++ncell;
+        }
+        const int64_t c = ncell - 1;
+        cell[i] = c;
+        if (rank[i] < rank[pstar[c]]) pstar[c] = i;
+        if (rank[i] > maxrank[c]) maxrank[c] = rank[i];
+    }
+    const int64_t count = idx ? m : n;
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int64_t t = 0; t < count; ++t) {
+        const int64_t i = idx ? idx[t] : t;
+        const int64_t c = cell[i];
+        int64_t dp = -1, d2 = INT64_MAX;
+        int32_t ex = 0;
+        if (pstar[c] != i) {
+            /* rule 1: the highest point of the own cell */
+            dp = pstar[c];
+            d2 = r2;
+        } else {
+            /* rule 2: a cell of N(c) whose points are all higher than p_i */
+            int64_t best = -1;
+            for (int64_t j = 0; j < n; ++j) {
+                const int64_t cj = cell[j];
+                if (cj == c || sq_dist(P, d, i, j) >= r2) continue;
+                if (maxrank[cj] < rank[i] && (best < 0 || rank[pstar[cj]] < rank[best])) best = pstar[cj];
+            }
+            if (best >= 0) {
+                dp = best;
+                d2 = r2;
+            } else {
+                /* exact computation: the nearest higher point */
+                ex = 1;
+                for (int64_t j = 0; j < n; ++j) {
+                    if (rank[j] >= rank[i]) continue;
+                    const int64_t dij = sq_dist(P, d, i, j);
+                    if (dij < d2 || (dij == d2 && j < dp)) {
+                        d2 = dij;
+                        dp = j;
+                    }
+                }
+            }
+        }
+        dep_out[t] = (int32_t)dp;
+        delta2_out[t] = d2;
+        if (exact_out) exact_out[t] = ex;
+    }
+    free(cc);
+    free(order);
+    free(rank);
+    free(by_cell);
+    free(cell);
+    free(pstar);
+    free(maxrank);
+}
+
+void oracle_approx_dependent(const int32_t* P, int64_t n, int32_t d, int64_t d_cut, const int32_t* rho,
+                             int32_t* dep, int64_t* delta2, int32_t* exact) {
+    approx_dependent(P, n, d, d_cut, rho, NULL, n, dep, delta2, exact);
+}
+
+void oracle_approx_dependent_subset(const int32_t* P, int64_t n, int32_t d, int64_t d_cut, const int32_t* rho,
+                                    const int64_t* idx, int64_t m, int32_t* dep_sub, int64_t* delta2_sub,
+                                    int32_t* exact_sub) {
+    approx_dependent(P, n, d, d_cut, rho, idx, m, dep_sub, delta2_sub, exact_sub);
 }
