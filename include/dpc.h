@@ -105,9 +105,31 @@ dpc_status dpc_density(dpc_ctx* ctx, const int32_t* points, int64_t n, int32_t d
  * per dataset; later calls copy the kept result. */
 dpc_status dpc_dependent(dpc_ds* ds, int32_t* dep_out, int64_t* delta2_out);
 
+/* Approx-DPC's dependent points (Section 4.3) instead of the exact ones.
+ * The grid G of Section 4.1 has cells of side d_cut / sqrt(d), here the
+ * integer side max(1, floor(d_cut / sqrt(d))) anchored at the per-dimension
+ * minimum; p*(c) is a cell's highest point in the order (rho desc, index
+ * asc). A point other than its cell's p* depends on p*(c) at distance d_cut;
+ * a p* depends, at distance d_cut, on the highest p*(c') among the cells c'
+ * that hold a point strictly within d_cut of it and all of whose points rank
+ * higher; every other point gets its exact dependent point (Definitions
+ * 2-3). With delta_min > d_cut the centers are those of dpc_dependent
+ * (Section 4.4).
+ *   dep_out, delta2_out: as for dpc_dependent (delta2 = d_cut^2 for an
+ *               approximated point).
+ *   exact_out:  NULL or n uint8: 1 where the dependent point is exact.
+ * Host or device memory, as for dpc_density's is_device. Later dpc_label
+ * calls use these dependent points until dpc_dependent is called.
+ * Errors: DPC_ERR_INVALID_ARG when the grid keys of the dataset need more
+ * than 64 bits (sum over dims of the bits of span / side); DPC_ERR_STATE for
+ * a dataset on the point tree (tree_min_d at or below its d). */
+dpc_status dpc_dependent_approx(dpc_ds* ds, int32_t* dep_out, int64_t* delta2_out, uint8_t* exact_out);
+
 /* Noise, centers and labels (Definitions 4-6) for one (rho_min, delta_min)
  * query. Re-queryable: only this step runs again (the decision-graph
- * workflow of Section 2.1). Runs dpc_dependent first if it has not run.
+ * workflow of Section 2.1). Uses the dependent points of the last
+ * dpc_dependent or dpc_dependent_approx call; runs dpc_dependent first when
+ * neither has run.
  *   delta_min: d_cut < delta_min <= 3037000499 (so delta_min^2 fits int64).
  *   label_out: NULL or n int32 (host or device per is_device): original index
  *              of the point's center, -1 for noise.

@@ -93,6 +93,7 @@ def lib():
             "dpc_release": ([vp], st),
             "dpc_ds_info": ([vp, ctypes.POINTER(DpcInfo)], st),
             "dpc_last_batch_info": ([vp, ctypes.POINTER(DpcInfo)], st),
+            "dpc_dependent_approx": ([vp, vp, vp, vp], st),
             "dpc_autotune": ([vp, ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32, ctypes.c_char_p,
                               ctypes.c_size_t], st),
             "dpc_set_profiling": ([vp, ctypes.c_int], st),
@@ -159,6 +160,10 @@ def dpc_density(ctx, points_ptr, n, d, d_cut, is_device, rho_ptr=None):
 
 def dpc_dependent(ds, dep_ptr=None, delta2_ptr=None):
     return _check(lib().dpc_dependent(ds, dep_ptr, delta2_ptr), "dpc_dependent")
+
+
+def dpc_dependent_approx(ds, dep_ptr=None, delta2_ptr=None, exact_ptr=None):
+    return _check(lib().dpc_dependent_approx(ds, dep_ptr, delta2_ptr, exact_ptr), "dpc_dependent_approx")
 
 
 def dpc_label(ds, rho_min, delta_min, label_ptr=None):
@@ -240,7 +245,7 @@ def _arg(x, dtype, shape=None):
         return None, 0
     if _is_torch(x):
         import torch
-        want = {np.int32: torch.int32, np.int64: torch.int64}[dtype]
+        want = {np.int32: torch.int32, np.int64: torch.int64, np.uint8: torch.uint8}[dtype]
         if x.dtype != want or not x.is_contiguous():
             raise ValueError(f"tensor must be contiguous {want}")
         if shape is not None and tuple(x.shape) != tuple(shape):
@@ -358,6 +363,12 @@ class Dataset:
         dpc_dependent(self.handle, self._out(dep_out, np.int32, (self.n,)),
                       self._out(delta2_out, np.int64, (self.n,)))
 
+    def dependent_approx(self, dep_out=None, delta2_out=None, exact_out=None):
+        """Approx-DPC's dependent points (Section 4.3); later labels use them."""
+        self.ctx._order_after_torch(dep_out, delta2_out, exact_out)
+        dpc_dependent_approx(self.handle, self._out(dep_out, np.int32, (self.n,)),
+                             self._out(delta2_out, np.int64, (self.n,)), self._out(exact_out, np.uint8, (self.n,)))
+
     def label(self, rho_min: int, delta_min: int, label_out=None) -> int:
         self.ctx._order_after_torch(label_out)
         return dpc_label(self.handle, rho_min, delta_min, self._out(label_out, np.int32, (self.n,)))
@@ -414,6 +425,23 @@ class Job:
         self.c = DpcJob(p(self.points), n, d, int(d_cut), len(q), h(self.rho_min), h(self.delta_min),
                         p(self.rho), p(self.dep), p(self.delta2), p(self.label), h(self.n_centers), is_dev)
         self.ticket = None
+
+
+def cluster_approx(points: np.ndarray, d_cut: int, rho_min: int, delta_min: int, device: int = 0) -> dict:
+    """Approx-DPC on host arrays: rho, dep, delta2, exact, label, n_centers."""
+    pts = np.ascontiguousarray(points, dtype=np.int32)
+    n = pts.shape[0]
+    with Context(device) as ctx:
+        rho = np.empty(n, np.int32)
+        ds = ctx.density(pts, d_cut, rho)
+        dep = np.empty(n, np.int32)
+        d2 = np.empty(n, np.int64)
+        ex = np.empty(n, np.uint8)
+        ds.dependent_approx(dep, d2, ex)
+        lab = np.empty(n, np.int32)
+        nc = ds.label(rho_min, delta_min, lab)
+        ds.release()
+    return {"rho": rho, "dep": dep, "delta2": d2, "exact": ex.astype(bool), "label": lab, "n_centers": nc}
 
 
 def cluster(points: np.ndarray, d_cut: int, rho_min: int, delta_min: int, device: int = 0) -> dict:

@@ -50,6 +50,9 @@ struct DsDesc {
     int32_t nleaf;        // point tree leaves (ceil(n / kLeaf))
     int32_t rbits;        // bits of the density key in the rank sort
     uint64_t dmask[kMaxGridDims];  // Morton bits of each gridded dim
+    int32_t a_side;       // Approx-DPC grid: integer side max(1, floor(d_cut / sqrt(d)))
+    int32_t a_shift[kMaxDims];  // Approx-DPC grid: bit offset of each dim's cell coordinate in the key
+    uint64_t a_base;      // Approx-DPC grid: key base of this dataset
     int32_t ptree;        // 1: no grid; the point tree gives density and dependent points
     int32_t tb;           // point tree: Morton bits per dim of the sort key
     int32_t span[kMaxDims];  // point tree: max - min + 1 per dim
@@ -87,6 +90,7 @@ struct BatchView {
     // labels
     int32_t* parent;           // original, global
     int32_t* label;            // original, local
+    uint8_t* exact;            // original: 1 when the dependent point is exact (Approx-DPC)
     unsigned long long* ncent; // [B]
     unsigned int* err;         // device error word: kErr* bits set by guarded kernels
 };

@@ -220,7 +220,8 @@ struct Batch {
     CellWork w{};
     DeltaBufs db{};
     DsDesc* d_desc = nullptr;
-    bool has_density = false, has_dep = false;
+    bool has_density = false, has_rank = false;
+    int dep_kind = 0;  // dependent points held: 0 none, 1 exact, 2 Approx-DPC
     uint32_t class_mask = 0, dim_mask = 0;
     int64_t ncells = 0, ndense = 0, nsparse = 0, nitems = 0, ntree = 0, nbf = 0;
     int64_t cand_pairs = 0;
@@ -622,6 +623,7 @@ struct Batch {
         bool narrow = true;
         for (int c = 0; c < ds.d; ++c) {
             ds.lo[c] = ds.n > 0 ? mm[2 * c] : 0;
+            ds.span[c] = ds.n > 0 ? mm[2 * c + 1] - mm[2 * c] + 1 : 1;
             bool gridded = false;
             for (int j = 0; j < k; ++j) gridded |= ds.gdim[j] == c;
             if (!gridded && ds.n > 0 && (int64_t)mm[2 * c + 1] - mm[2 * c] >= ds.s) narrow = false;
@@ -632,50 +634,12 @@ struct Batch {
         return DPC_OK;
     }
 
-    // -------------------------------------------------------- dependent
-    dpc_status dependent() {
-        if (has_dep) return DPC_OK;
-        if (!has_density) return fail(DPC_ERR_STATE, "dataset has no density");
-        mark(0);
-        Arena tmp;
-        tmp.st = st;
-        DPC_CK(keep.get(&v.rank, N));
-        DPC_CK(keep.get(&v.order, N));
-        DPC_CK(keep.get(&v.ro_s, N));
-        DPC_CK(keep.get(&v.dep, N));
-        DPC_CK(keep.get(&v.delta2, N));
-        int rbits = 1;
-        for (int b = 0; b < B; ++b) rbits = std::max(rbits, hd[b].rbits);
-        int bbits = ceil_log2((uint64_t)B);
-        const size_t kb = (bbits + rbits) > 32 ? 8 : 4;
-        void* temp = nullptr;
-        DPC_CK(tmp.get(&temp, std::max(radix_sort_temp_bytes(N), scan_temp_bytes(N))));
-        DPC_CK(tmp.get(&db.rkeys, 3 * a256(kb * N) / 4 + 64));
-        DPC_CK(tmp.get(&db.rvals, 2 * (N + 64)));
-        DPC_CK(launch_rank(v, db, rbits, temp, st));
-        mark(1);
-
-        DPC_CK(tmp.get(&v.best_s, N));
-        DPC_CK(cudaMemsetAsync(v.best_s, 0xff, sizeof(unsigned long long) * std::max<int64_t>(N, 1), st));
-        DPC_CK(launch_ring(v, w, class_mask, nitems, nsparse, d_counters + 32, st));
-        if (pb.m > 0) {
-            DPC_CK(cudaMemsetAsync(pb.flag, 0, sizeof(uint32_t) * pb.nslots, st));
-            DPC_CK(launch_pt_minrank(v, pb, st));
-            for (int d = 1; d <= kMaxDims; ++d)
-                DPC_CK(launch_delta_ptree(v, pb, d, pt_range[d][0], pt_range[d][1], st));
-        }
-        mark(2);
-
-        DPC_CK(tmp.get(&db.ucount, 4));
-        DPC_CK(tmp.get(&db.tree_list, N));
-        DPC_CK(tmp.get(&db.bf_list, N));
-        DPC_CK(cudaMemsetAsync(db.ucount, 0, 4 * sizeof(uint32_t), st));
-        db.tcount = db.ucount;
-        db.bf_rank = tune.bf_rank;
-        DPC_CK(launch_finalize(v, db, st));
+    // The open points of db.tree_list / db.bf_list (counts in db.ucount[0..1],
+    // filled by the stream's previous kernels): tree search and brute force.
+    dpc_status open_points(Arena& tmp, const char* what, bool allow_coarse) {
         uint32_t uc[2] = {0, 0};
         DPC_CK(cudaMemcpyAsync(uc, db.ucount, sizeof(uc), cudaMemcpyDeviceToHost, st));
-        DPC_TRY(sync("ring search"));
+        DPC_TRY(sync(what));
         ntree = uc[0];
         nbf = uc[1];
         if (ntree > 0) {
@@ -696,7 +660,7 @@ struct Batch {
             const int64_t nc = ncells;
             db.ncells = nc;
             // coarse ring over blocks of 2^clevel cells per gridded dim
-            if (tune.clevel > 0) {
+            if (allow_coarse && tune.clevel > 0) {
                 db.clevel = tune.clevel;
                 db.ccap = tune.ccap;
                 uint32_t* d_nco = nullptr;
@@ -750,7 +714,10 @@ struct Batch {
             DPC_CK(tmp.get(&t2, std::max(radix_sort_temp_bytes(nbf), scan_temp_bytes(nbf))));
             DPC_CK(launch_bruteforce(v, db, dim_mask, nbf, t2, st));
         }
-        mark(3);
+        return DPC_OK;
+    }
+
+    dpc_status finish_stats(const char* what) {
         unsigned long long tstat[2] = {0, 0};
         uint32_t open2 = 0;
         if (ntree > 0) {
@@ -759,22 +726,160 @@ struct Batch {
         }
         unsigned long long ptst[4] = {0, 0, 0, 0};
         if (pb.m > 0) DPC_CK(cudaMemcpyAsync(ptst, pb.stats, sizeof(ptst), cudaMemcpyDeviceToHost, st));
-        DPC_TRY(sync("dependent points"));
+        DPC_TRY(sync(what));
         tree_visits = (int64_t)(tstat[0] + ptst[2]);
         tree_pairs = (int64_t)(tstat[1] + ptst[3]);
         ntree2 = open2;
-        DPC_TRY(check_err("dependent points"));
+        DPC_TRY(check_err(what));
+        return DPC_OK;
+    }
+
+    // -------------------------------------------------------- dependent
+    // The rank order (rho desc, index asc) and the per-point state the
+    // dependent-point passes write, once per batch.
+    dpc_status ensure_rank(Arena& tmp, void* temp) {
+        if (has_rank) return DPC_OK;
+        DPC_CK(keep.get(&v.rank, N));
+        DPC_CK(keep.get(&v.order, N));
+        DPC_CK(keep.get(&v.ro_s, N));
+        DPC_CK(keep.get(&v.dep, N));
+        DPC_CK(keep.get(&v.delta2, N));
+        DPC_CK(keep.get(&v.exact, N));
+        int rbits = 1;
+        for (int b = 0; b < B; ++b) rbits = std::max(rbits, hd[b].rbits);
+        int bbits = ceil_log2((uint64_t)B);
+        const size_t kb = (bbits + rbits) > 32 ? 8 : 4;
+        DPC_CK(tmp.get(&db.rkeys, 3 * a256(kb * N) / 4 + 64));
+        DPC_CK(tmp.get(&db.rvals, 2 * (N + 64)));
+        DPC_CK(launch_rank(v, db, rbits, temp, st));
+        has_rank = true;
+        return DPC_OK;
+    }
+
+    dpc_status dependent() {
+        if (dep_kind == 1) return DPC_OK;
+        if (!has_density) return fail(DPC_ERR_STATE, "dataset has no density");
+        mark(0);
+        Arena tmp;
+        tmp.st = st;
+        void* temp = nullptr;
+        DPC_CK(tmp.get(&temp, std::max(radix_sort_temp_bytes(N), scan_temp_bytes(N))));
+        DPC_TRY(ensure_rank(tmp, temp));
+        mark(1);
+
+        DPC_CK(tmp.get(&v.best_s, N));
+        DPC_CK(cudaMemsetAsync(v.best_s, 0xff, sizeof(unsigned long long) * std::max<int64_t>(N, 1), st));
+        DPC_CK(launch_ring(v, w, class_mask, nitems, nsparse, d_counters + 32, st));
+        if (pb.m > 0) {
+            DPC_CK(cudaMemsetAsync(pb.flag, 0, sizeof(uint32_t) * pb.nslots, st));
+            DPC_CK(launch_pt_minrank(v, pb, st));
+            for (int d = 1; d <= kMaxDims; ++d)
+                DPC_CK(launch_delta_ptree(v, pb, d, pt_range[d][0], pt_range[d][1], st));
+        }
+        mark(2);
+
+        DPC_CK(tmp.get(&db.ucount, 4));
+        DPC_CK(tmp.get(&db.tree_list, N));
+        DPC_CK(tmp.get(&db.bf_list, N));
+        DPC_CK(cudaMemsetAsync(db.ucount, 0, 4 * sizeof(uint32_t), st));
+        db.tcount = db.ucount;
+        db.bf_rank = tune.bf_rank;
+        DPC_CK(launch_finalize(v, db, st));
+        DPC_TRY(open_points(tmp, "ring search", true));
+        mark(3);
+        DPC_TRY(finish_stats("dependent points"));
         ms[2] = elapsed(0, 1);
         ms[3] = elapsed(1, 2);
         ms[4] = elapsed(2, 3);
         tmp.release();
-        has_dep = true;
+        dep_kind = 1;
+        return DPC_OK;
+    }
+
+    // ------------------------------------------------------- Approx-DPC
+    // Approx-DPC's dependent points (Section 4.3): see approx.cu. The grid of
+    // side max(1, floor(d_cut / sqrt(d))) covers all d dims; its keys pack
+    // each dim's cell coordinate at its own bit offset after a per-dataset
+    // base, and must fit 64 bits for the whole batch.
+    dpc_status dependent_approx() {
+        if (dep_kind == 2) return DPC_OK;
+        if (!has_density) return fail(DPC_ERR_STATE, "dataset has no density");
+        unsigned __int128 abase = 0;
+        for (int b = 0; b < B; ++b) {
+            DsDesc& ds = hd[b];
+            if (ds.ptree) return fail(DPC_ERR_STATE, "Approx-DPC needs the grid: set tree_min_d above the dimension");
+            const int64_t q = ds.d_cut2 / ds.d;
+            int64_t s = (int64_t)std::sqrt((double)q);
+            while (s > 0 && s * s > q) --s;
+            while ((s + 1) * (s + 1) <= q) ++s;
+            ds.a_side = (int32_t)std::max<int64_t>(1, s);
+            int off = 0;
+            for (int k = 0; k < kMaxDims; ++k) {
+                ds.a_shift[k] = off;
+                if (k < ds.d && ds.n > 0) off += bits_for((uint64_t)((ds.span[k] - 1) / ds.a_side));
+            }
+            ds.a_base = (uint64_t)abase;
+            abase += (unsigned __int128)1 << std::min(off, 100);
+            if (abase > ((unsigned __int128)1 << 64))
+                return fail(DPC_ERR_INVALID_ARG, "Approx-DPC grid keys need more than 64 bits for this batch");
+        }
+        const int key_bits = std::max(1, bits_for((uint64_t)(abase - 1)));
+        DPC_TRY(upload_desc());
+        mark(0);
+        Arena tmp;
+        tmp.st = st;
+        void* temp = nullptr;
+        DPC_CK(tmp.get(&temp, std::max(radix_sort_temp_bytes(N), scan_temp_bytes(N))));
+        DPC_TRY(ensure_rank(tmp, temp));
+        mark(1);
+        ApproxBufs ab{};
+        uint64_t *k0 = nullptr, *k1 = nullptr, *k2 = nullptr;
+        uint32_t *o0 = nullptr, *o1 = nullptr, *o2 = nullptr;
+        DPC_CK(tmp.get(&k0, N));
+        DPC_CK(tmp.get(&k1, N));
+        DPC_CK(tmp.get(&k2, N));
+        DPC_CK(tmp.get(&o0, N));
+        DPC_CK(tmp.get(&o1, N));
+        DPC_CK(tmp.get(&o2, N));
+        DPC_CK(tmp.get(&ab.flag, N));
+        DPC_CK(tmp.get(&ab.cidx, N));
+        DPC_CK(tmp.get(&ab.cell_of, N));
+        DPC_CK(tmp.get(&ab.start, N + 1));
+        DPC_CK(tmp.get(&ab.top, N));
+        DPC_CK(tmp.get(&ab.maxrank, N));
+        DPC_CK(tmp.get(&ab.ncells, 1));
+        DPC_CK(cudaMemsetAsync(ab.ncells, 0, sizeof(uint32_t), st));
+        ab.keys = k0;
+        ab.ord = o0;
+        DPC_CK(launch_approx_keys(v, ab, st));
+        DPC_CK(radix_sort_u64(k0, o0, k2, o2, k1, o1, N, key_bits, temp, st));
+        ab.keys = k2;
+        ab.ord = o2;
+        DPC_CK(launch_approx_cells(v, ab, temp, st));
+        DPC_CK(tmp.get(&v.best_s, N));
+        DPC_CK(cudaMemsetAsync(v.best_s, 0xff, sizeof(unsigned long long) * std::max<int64_t>(N, 1), st));
+        DPC_CK(tmp.get(&db.ucount, 4));
+        DPC_CK(tmp.get(&db.tree_list, N));
+        DPC_CK(tmp.get(&db.bf_list, N));
+        DPC_CK(cudaMemsetAsync(db.ucount, 0, 4 * sizeof(uint32_t), st));
+        db.tcount = db.ucount;
+        db.bf_rank = tune.bf_rank;
+        DPC_CK(launch_approx_rules(v, w, ab, db, dim_mask, N, st));
+        mark(2);
+        DPC_TRY(open_points(tmp, "approximate rules", false));
+        mark(3);
+        DPC_TRY(finish_stats("approximate dependent points"));
+        ms[2] = elapsed(0, 1);
+        ms[3] = elapsed(1, 2);
+        ms[4] = elapsed(2, 3);
+        tmp.release();
+        dep_kind = 2;
         return DPC_OK;
     }
 
     // ------------------------------------------------------------ label
     dpc_status label(const int64_t* rho_min, const int64_t* delta_min) {
-        DPC_TRY(dependent());
+        if (dep_kind == 0) DPC_TRY(dependent());  // else the dependent points already held
         if (!v.parent) {
             DPC_CK(keep.get(&v.parent, N));
             DPC_CK(keep.get(&v.label, N));
@@ -938,6 +1043,18 @@ dpc_status dpc_dependent(dpc_ds* ds, int32_t* dep_out, int64_t* delta2_out) {
     DPC_TRY(bt.copy_out(dep_out, bt.v.dep + h.pt_off, sizeof(int32_t) * h.n));
     DPC_TRY(bt.copy_out(delta2_out, bt.v.delta2 + h.pt_off, sizeof(int64_t) * h.n));
     return bt.sync("copy dependent");
+}
+
+dpc_status dpc_dependent_approx(dpc_ds* ds, int32_t* dep_out, int64_t* delta2_out, uint8_t* exact_out) {
+    if (!ds || !ds->batch) return fail(DPC_ERR_STATE, "invalid dataset handle");
+    Batch& bt = *ds->batch;
+    cudaSetDevice(bt.ctx->device);
+    DPC_TRY(bt.dependent_approx());
+    const dpc::DsDesc& h = bt.hd[ds->b];
+    DPC_TRY(bt.copy_out(dep_out, bt.v.dep + h.pt_off, sizeof(int32_t) * h.n));
+    DPC_TRY(bt.copy_out(delta2_out, bt.v.delta2 + h.pt_off, sizeof(int64_t) * h.n));
+    DPC_TRY(bt.copy_out(exact_out, bt.v.exact + h.pt_off, sizeof(uint8_t) * h.n));
+    return bt.sync("copy approximate dependent");
 }
 
 dpc_status dpc_label(dpc_ds* ds, int64_t rho_min, int64_t delta_min, int32_t* label_out, int64_t* n_centers) {

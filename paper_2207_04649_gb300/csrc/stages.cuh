@@ -302,6 +302,27 @@ cudaError_t launch_rho_ptree(const BatchView& v, const PtBufs& pb, int d, int64_
 cudaError_t launch_delta_ptree(const BatchView& v, const PtBufs& pb, int d, int64_t t0, int64_t t1,
                                cudaStream_t st);
 
+// approx.cu: Approx-DPC's dependent points (Section 4.3) on the grid of side
+// d_cut / sqrt(d). The points are sorted again by that grid's keys; per cell
+// the highest point (p*) and the lowest rank; rule 1 links every other point
+// to its cell's p*; rule 2 links a p* to the highest p* of the neighbouring
+// cells all of whose points rank higher; the rest go to the exact lists.
+struct ApproxBufs {
+    uint64_t* keys;       // [N] grid keys by sorted position, then sorted
+    uint32_t* ord;        // [N] sorted positions in grid-key order
+    uint32_t* flag;       // [N] temp: first point of a cell
+    uint32_t* cidx;       // [N] temp: exclusive scan of flag
+    uint32_t* cell_of;    // [N] grid cell of every sorted position
+    uint32_t* start;      // [ncells + 1] first index (in ord) of every cell
+    uint32_t* top;        // [ncells] sorted position of the cell's highest point
+    uint32_t* maxrank;    // [ncells] the cell's lowest rank
+    uint32_t* ncells;     // device scalar
+};
+cudaError_t launch_approx_keys(const BatchView& v, const ApproxBufs& ab, cudaStream_t st);
+cudaError_t launch_approx_cells(const BatchView& v, const ApproxBufs& ab, void* scan_temp, cudaStream_t st);
+cudaError_t launch_approx_rules(const BatchView& v, const CellWork& w, const ApproxBufs& ab, const DeltaBufs& db,
+                                uint32_t dim_mask, int64_t ncells_bound, cudaStream_t st);
+
 // label.cu
 cudaError_t launch_labels(const BatchView& v, cudaStream_t st);
 
