@@ -31,6 +31,11 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "exact DPC points/s (rho+delta+labels) at 5.8M x 3"
+APPROX_METRIC = "Approx-DPC points/s (rho+approximate delta+labels) at 5.8M x 3"
+
+
+def metric_for(args) -> str:
+    return APPROX_METRIC if args.method == "approx" else METRIC
 UNIT = "points/s"
 
 
@@ -41,6 +46,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="plain_5p8m_3d")
+    ap.add_argument("--method", choices=["exact", "approx"], default="exact",
+                    help="exact DPC, or Approx-DPC's dependent points (Section 4.3)")
     ap.add_argument("--cpu-sample", type=int, default=0, help="oracle sample size (0: automatic)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     return ap.parse_args()
@@ -129,20 +136,24 @@ class ClockSampler:
 
 # ------------------------------------------------------------- oracle leg
 
-def oracle_sample_rate(ds, m: int, seed: int = 7):
+def oracle_sample_rate(ds, m: int, seed: int = 7, method: str = "exact"):
     """The oracle, as it stands, on m sampled points of the workload: their
-    local density against all n points, then their dependent point by a scan
-    of all n points. Only the time is used. The scan's density order is the
-    index order here (the full density array would need the whole O(n^2)
-    oracle run); on a uniform sample it touches the same number of higher
-    points on average (half of them)."""
+    local density against all n points, then their dependent point (exact:
+    a scan of all n points; approx: Approx-DPC's rules, which scan all n
+    points for a cell's top). Only the time is used. The density order is
+    the index order here (the full density array would need the whole
+    O(n^2) oracle run); on a uniform sample the exact scan touches the same
+    number of higher points on average (half of them)."""
     import numpy as np
     import oracle
     idx = np.random.default_rng(seed).choice(ds.n, size=m, replace=False)
     flat = np.zeros(ds.n, dtype=np.int32)
     t0 = time.perf_counter()
     oracle.rho_subset(ds.points, ds.d_cut, idx)
-    oracle.dependent_subset(ds.points, flat, idx)
+    if method == "approx":
+        oracle.approx_dependent_subset(ds.points, flat, ds.d_cut, idx)
+    else:
+        oracle.dependent_subset(ds.points, flat, idx)
     dt = time.perf_counter() - t0
     return m / dt, dt
 
@@ -221,9 +232,14 @@ def run_ours(args):
     ctx = dpc.Context(device=local, profiling=True)
     st = ctx.stream
 
+    approx = args.method == "approx"
+
     def step():
         h = ctx.density(pts, ds.d_cut, rho)
-        h.dependent(dep, d2)
+        if approx:
+            h.dependent_approx(dep, d2)
+        else:
+            h.dependent(dep, d2)
         nc = h.label(ds.rho_min, ds.delta_min, lab)
         info = h.info()
         h.release()
@@ -277,7 +293,10 @@ def run_ours(args):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         h = ctx.density(h_pts, ds.d_cut, h_rho)
-        h.dependent(h_dep, h_d2)
+        if approx:
+            h.dependent_approx(h_dep, h_d2)
+        else:
+            h.dependent(h_dep, h_d2)
         h.label(ds.rho_min, ds.delta_min, h_lab)
         h.release()
         t1 = time.perf_counter()
@@ -301,20 +320,20 @@ def run_ours(args):
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         import oracle
         m = args.cpu_sample or auto_sample(ds)
-        rate, dt = oracle_sample_rate(ds, m)
+        rate, dt = oracle_sample_rate(ds, m, method=args.method)
         cpu = {"value": rate, "unit": UNIT, "cores": oracle.threads(), "kind": "oracle",
                "sample": f"{m} random points of the {n}-point set: rho against all n points and the "
-                         f"dependent-point scan over all n points ({dt:.1f} s)"}
+                         f"{args.method} dependent-point step over all n points ({dt:.1f} s)"}
 
     if dist:
         dist.barrier()
     if rank == 0:
         line = {
-            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "metric": metric_for(args), "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "int32",
             "data": "synthetic (seeded Gaussian-blob mixture, int32 coordinates)",
-            "config": {"workload": args.workload, "n": n, "d": d, "d_cut": ds.d_cut, "rho_min": ds.rho_min,
+            "config": {"workload": args.workload, "method": args.method, "n": n, "d": d, "d_cut": ds.d_cut, "rho_min": ds.rho_min,
                        "delta_min": ds.delta_min, "parallelism": f"replicas x{ws}",
                        "l2": "flushed between steps (256 MB write)",
                        "mean_rho": float(rho.double().mean().item()), "n_centers": int(nc)},
@@ -358,20 +377,20 @@ def run_reference(args):
     ds = workloads.NAMED[args.workload]()
     m = args.cpu_sample or max(100, auto_sample(ds) // 4)
     for _ in range(args.warmup):
-        oracle_sample_rate(ds, max(20, m // 10))
+        oracle_sample_rate(ds, max(20, m // 10), method=args.method)
     times = []
     for i in range(args.steps):
-        _, dt = oracle_sample_rate(ds, m, seed=100 + i)
+        _, dt = oracle_sample_rate(ds, m, seed=100 + i, method=args.method)
         times.append(dt)
     total = sum(times)
     value = m * len(times) / total
     sample = (f"{m} random points per step of the {ds.n}-point set: rho against all n points and the "
               f"dependent-point scan over all n points")
     line = {
-        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "impl": "reference", "metric": metric_for(args), "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * total / len(times), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
-        "config": {"workload": args.workload, "n": ds.n, "d": ds.d, "d_cut": ds.d_cut},
+        "config": {"workload": args.workload, "method": args.method, "n": ds.n, "d": ds.d, "d_cut": ds.d_cut},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.threads(), "kind": "oracle",
                          "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},

@@ -848,14 +848,18 @@ struct Batch {
         DPC_CK(tmp.get(&ab.top, N));
         DPC_CK(tmp.get(&ab.maxrank, N));
         DPC_CK(tmp.get(&ab.ncells, 1));
+        DPC_CK(tmp.get(&ab.light, N));
+        DPC_CK(tmp.get(&ab.heavy, N));
+        DPC_CK(tmp.get(&ab.nlh, 2));
         DPC_CK(cudaMemsetAsync(ab.ncells, 0, sizeof(uint32_t), st));
+        DPC_CK(cudaMemsetAsync(ab.nlh, 0, 2 * sizeof(uint32_t), st));
         ab.keys = k0;
         ab.ord = o0;
         DPC_CK(launch_approx_keys(v, ab, st));
         DPC_CK(radix_sort_u64(k0, o0, k2, o2, k1, o1, N, key_bits, temp, st));
         ab.keys = k2;
         ab.ord = o2;
-        DPC_CK(launch_approx_cells(v, ab, temp, st));
+        DPC_CK(launch_approx_cells(v, w, ab, temp, st));
         DPC_CK(tmp.get(&v.best_s, N));
         DPC_CK(cudaMemsetAsync(v.best_s, 0xff, sizeof(unsigned long long) * std::max<int64_t>(N, 1), st));
         DPC_CK(tmp.get(&db.ucount, 4));

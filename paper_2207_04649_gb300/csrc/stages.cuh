@@ -317,9 +317,13 @@ struct ApproxBufs {
     uint32_t* top;        // [ncells] sorted position of the cell's highest point
     uint32_t* maxrank;    // [ncells] the cell's lowest rank
     uint32_t* ncells;     // device scalar
+    uint32_t* light;      // [ncells] cells whose p* has few candidates (one thread each)
+    uint32_t* heavy;      // [ncells] the others (one warp each)
+    uint32_t* nlh;        // [2] device counts of light, heavy
 };
 cudaError_t launch_approx_keys(const BatchView& v, const ApproxBufs& ab, cudaStream_t st);
-cudaError_t launch_approx_cells(const BatchView& v, const ApproxBufs& ab, void* scan_temp, cudaStream_t st);
+cudaError_t launch_approx_cells(const BatchView& v, const CellWork& w, const ApproxBufs& ab, void* scan_temp,
+                                cudaStream_t st);
 cudaError_t launch_approx_rules(const BatchView& v, const CellWork& w, const ApproxBufs& ab, const DeltaBufs& db,
                                 uint32_t dim_mask, int64_t ncells_bound, cudaStream_t st);
 
