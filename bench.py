@@ -316,6 +316,24 @@ def run_ours(args):
     traffic = rho_traffic(args.workload)
     dtraffic = rho_traffic(args.workload, "dram_bytes_per_launch_dense")
 
+    accuracy = None
+    if approx:
+        # Rand index of the Approx-DPC labels against the exact labels of the
+        # same set (the paper's accuracy measure, Section 5), and the center
+        # guarantee of Section 4.4
+        from paper_2207_04649_gb300 import evaluate
+        h = ctx.density(pts, ds.d_cut)
+        elab = torch.empty_like(lab)
+        h.dependent()
+        h.label(ds.rho_min, ds.delta_min, elab)
+        h.release()
+        torch.cuda.synchronize()
+        a_np, e_np = lab.cpu().numpy(), elab.cpu().numpy()
+        idx = np.arange(n)
+        accuracy = {"rand_index_vs_exact": evaluate.rand_index(a_np, e_np),
+                    "same_centers": bool(np.array_equal(a_np == idx, e_np == idx)),
+                    "tops_to_exact_search": int(infos[-1]["open_after_ring"])}
+
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         import oracle
@@ -360,6 +378,8 @@ def run_ours(args):
             "clocks": clk,
             "gpu_launches": launches,
         }
+        if accuracy is not None:
+            line["accuracy"] = accuracy
         print(json.dumps(line), flush=True)
     ctx.close()
     if dist:

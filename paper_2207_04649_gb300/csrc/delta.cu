@@ -211,11 +211,16 @@ __global__ void __launch_bounds__(kRingThreads) k_ring_dense(BatchView v, CellWo
             }
         }
         const uint32_t nr = w.nruns[c], ctot = w.cand[c];
-        for (uint32_t t = lane; t < nr; t += 32) srun[t] = w.runs[(int64_t)c * w.nbs + t];
+        // the runs in shared memory when they fit (reach 1), else read in place
+        const uint2* runs_c = w.runs + (int64_t)c * w.nbs;
+        if (nr <= (uint32_t)kMaxNb) {
+            for (uint32_t t = lane; t < nr; t += 32) srun[t] = runs_c[t];
+            runs_c = srun;
+        }
         __syncwarp();
         const uint32_t k0 = kc * (uint32_t)w.kch;
         CandStream<DP, true> cst;
-        cst.init(srun, nr, k0, min(ctot, k0 + (uint32_t)w.kch));
+        cst.init(runs_c, nr, k0, min(ctot, k0 + (uint32_t)w.kch));
         bool bad = false;
         bool have = cst.prep(lane, recb, v.ro_s, &bad);
         int sb = 0;

@@ -105,6 +105,7 @@ struct Tune {
     int clevel = 0;           // coarse ring: blocks of 2^clevel cells per gridded dim (0: off)
     uint32_t ccap = 512;      // coarse cells holding more points are not scanned
     int tree_min_d = 9;       // datasets with at least this many dims take the point tree (9: none)
+    int hd_cell_factor = 1;   // datasets with d >= 5: cells of side d_cut / f searched to reach f
 };
 
 }  // namespace
@@ -537,8 +538,12 @@ struct Batch {
     dpc_status plan(int b, const int32_t* mm, uint64_t& cbase) {
         DsDesc& ds = hd[b];
         const Tune& tn = tune;
-        ds.s = ds.d_cut;  // cell side d_cut: neighbours are within one cell
-        ds.R = 1;
+        // cell side d_cut and reach 1: every point within d_cut lies in the 3^k
+        // neighbouring cells; with factor f (datasets with d >= 5), side
+        // ceil(d_cut / f) and reach f cover the same distance with a finer grid
+        const int f = ds.d >= 5 ? tn.hd_cell_factor : 1;
+        ds.R = f;
+        ds.s = (ds.d_cut + f - 1) / f;
         ds.ptree = 0;
         if (ds.n > 0 && ds.d >= tn.tree_min_d) {
             // point tree: no grid; the sort key is the Morton code of all d
@@ -983,6 +988,7 @@ dpc_status dpc_set_tuning(dpc_ctx* ctx, const char* key, int64_t value) {
     else if (k == "clevel" && value >= 0 && value <= 8) t.clevel = (int)value;
     else if (k == "ccap" && value >= 1 && value <= (1 << 24)) t.ccap = (uint32_t)value;
     else if (k == "tree_min_d" && value >= 1 && value <= 9) t.tree_min_d = (int)value;
+    else if (k == "hd_cell_factor" && value >= 1 && value <= 3) t.hd_cell_factor = (int)value;
     else if (k == "max_batch_jobs" && value >= 1 && value <= 4096) {
         std::lock_guard<std::mutex> lk(ctx->mu);
         ctx->max_batch_jobs = (int)value;
@@ -1000,6 +1006,7 @@ dpc_status dpc_get_tuning(dpc_ctx* ctx, const char* key, int64_t* value) {
     else if (k == "clevel") *value = t.clevel;
     else if (k == "ccap") *value = t.ccap;
     else if (k == "tree_min_d") *value = t.tree_min_d;
+    else if (k == "hd_cell_factor") *value = t.hd_cell_factor;
     else if (k == "max_batch_jobs") {
         std::lock_guard<std::mutex> lk(ctx->mu);
         *value = ctx->max_batch_jobs;

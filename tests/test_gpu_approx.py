@@ -90,6 +90,28 @@ def test_random_shapes_bit_exact(dpc, shape):
         assert nc == onc
 
 
+def test_high_dims_finer_grid(dpc):
+    """Approx-DPC on an 8-d set with the exact grid's cells of side d_cut / 2."""
+    ds = workloads.random_blobs(6, 1500, 8, 9000, blobs=5, spread=0.05, dup=20)
+    pts = np.ascontiguousarray(ds.points)
+    n = pts.shape[0]
+    with dpc.Context(0) as ctx:
+        ctx.tune(hd_cell_factor=2)
+        rho = np.empty(n, np.int32)
+        h = ctx.density(pts, 9000, rho)
+        dep = np.empty(n, np.int32)
+        d2 = np.empty(n, np.int64)
+        ex = np.empty(n, np.uint8)
+        h.dependent_approx(dep, d2, ex)
+        h.release()
+    orho = oracle.rho(pts, 9000)
+    odep, od2, oex = oracle.approx_dependent(pts, orho, 9000)
+    np.testing.assert_array_equal(rho, orho)
+    np.testing.assert_array_equal(dep, odep)
+    np.testing.assert_array_equal(d2, od2)
+    np.testing.assert_array_equal(ex.astype(bool), oex)
+
+
 def test_identical_points_and_tiny(dpc):
     for pts, dc in [(np.full((500, 3), 77, np.int32), 5), (np.array([[3, 4]], np.int32), 2),
                     (np.array([[0, 0], [0, 1]], np.int32), 2)]:

@@ -123,10 +123,12 @@ def test_random_shapes_point_tree(dpc, shape):
 
 
 @pytest.mark.parametrize("d", [5, 6, 7, 8])
-def test_high_dims_grid_path(dpc, d):
-    """The projected grid for d > 4 (the point tree switched off)."""
+@pytest.mark.parametrize("f", [1, 2, 3])
+def test_high_dims_grid_path(dpc, d, f):
+    """The projected grid for d > 4 (the point tree switched off), with
+    cells of side d_cut / f searched f cells away."""
     ds = workloads.random_blobs(60 + d, 2500, d, 9000, blobs=4, spread=0.05, dup=10)
-    info = assert_full_parity(dpc, ds.points, 9000, [(3, 27001)], dict(tree_min_d=9))
+    info = assert_full_parity(dpc, ds.points, 9000, [(3, 27001)], dict(tree_min_d=9, hd_cell_factor=f))
     assert 1 <= info["grid_dims"] <= 4
 
 
