@@ -206,10 +206,11 @@ dpc_status dpc_set_profiling(dpc_ctx* ctx, int on);
  *             and take the point tree (a kd-tree-like search over all
  *             dimensions), 1 .. 9 (default 9: never; on the blob workloads
  *             the projected grid is faster at every d measured, 5 to 8)
- *   "hd_cell_factor"  f for datasets with d >= 5: grid cells of side
- *             ceil(d_cut / f), neighbours searched f cells away (a finer
+ *   "hd_cell_factor"  f for datasets with d >= hd_min_d: grid cells of
+ *             side ceil(d_cut / f), neighbours searched f cells away (a finer
  *             grid, fewer candidate pairs, more neighbour cells), 1 .. 3
- *             (default 1)
+ *             (default 2)
+ *   "hd_min_d"  smallest d that takes hd_cell_factor, 1 .. 9 (default 7)
  *   "max_batch_jobs"  served mode: jobs one batch admits at most, 1 .. 4096
  *             (default 64; 1 runs the jobs one at a time)
  * DPC_ERR_INVALID_ARG for an unknown key or a value out of range. */

@@ -105,7 +105,8 @@ struct Tune {
     int clevel = 0;           // coarse ring: blocks of 2^clevel cells per gridded dim (0: off)
     uint32_t ccap = 512;      // coarse cells holding more points are not scanned
     int tree_min_d = 9;       // datasets with at least this many dims take the point tree (9: none)
-    int hd_cell_factor = 1;   // datasets with d >= 5: cells of side d_cut / f searched to reach f
+    int hd_cell_factor = 2;   // datasets with d >= hd_min_d: cells of side d_cut / f searched to reach f
+    int hd_min_d = 7;
 };
 
 }  // namespace
@@ -171,7 +172,8 @@ Tune tune_for(dpc_ctx* ctx, const std::vector<Input>& in) {
 std::string tune_line(const std::pair<int, int>& sig, const Tune& t) {
     std::ostringstream o;
     o << "dmax=" << sig.first << " nlog=" << sig.second << " kch=" << t.kch << " kmax=" << t.kmax
-      << " bf_rank=" << t.bf_rank << " clevel=" << t.clevel << " ccap=" << t.ccap << " tree_min_d=" << t.tree_min_d;
+      << " bf_rank=" << t.bf_rank << " clevel=" << t.clevel << " ccap=" << t.ccap << " tree_min_d=" << t.tree_min_d
+      << " hd_cell_factor=" << t.hd_cell_factor << " hd_min_d=" << t.hd_min_d;
     return o.str();
 }
 
@@ -181,13 +183,15 @@ void load_tune_cache(dpc_ctx* ctx) {
     std::ifstream f(ctx->tune_cache);
     std::string line;
     while (std::getline(f, line)) {
-        int dmax, nlog, kch, kmax, clevel, tmd;
+        int dmax, nlog, kch, kmax, clevel, tmd, hf, hm;
         unsigned bf, ccap;
-        if (std::sscanf(line.c_str(), "dmax=%d nlog=%d kch=%d kmax=%d bf_rank=%u clevel=%d ccap=%u tree_min_d=%d",
-                        &dmax, &nlog, &kch, &kmax, &bf, &clevel, &ccap, &tmd) != 8)
+        if (std::sscanf(line.c_str(),
+                        "dmax=%d nlog=%d kch=%d kmax=%d bf_rank=%u clevel=%d ccap=%u tree_min_d=%d hd_cell_factor=%d "
+                        "hd_min_d=%d",
+                        &dmax, &nlog, &kch, &kmax, &bf, &clevel, &ccap, &tmd, &hf, &hm) != 10)
             continue;
         if (kch < 32 || kch > (1 << 20) || kmax < 1 || kmax > kMaxGridDims || clevel < 0 || clevel > 8 ||
-            ccap < 1 || tmd < 1 || tmd > 9)
+            ccap < 1 || tmd < 1 || tmd > 9 || hf < 1 || hf > 3 || hm < 1 || hm > 9)
             continue;
         Tune t;
         t.kch = kch;
@@ -196,6 +200,8 @@ void load_tune_cache(dpc_ctx* ctx) {
         t.clevel = clevel;
         t.ccap = ccap;
         t.tree_min_d = tmd;
+        t.hd_cell_factor = hf;
+        t.hd_min_d = hm;
         ctx->tuned[{dmax, nlog}] = t;
     }
 }
@@ -539,9 +545,10 @@ struct Batch {
         DsDesc& ds = hd[b];
         const Tune& tn = tune;
         // cell side d_cut and reach 1: every point within d_cut lies in the 3^k
-        // neighbouring cells; with factor f (datasets with d >= 5), side
-        // ceil(d_cut / f) and reach f cover the same distance with a finer grid
-        const int f = ds.d >= 5 ? tn.hd_cell_factor : 1;
+        // neighbouring cells; with factor f (datasets with d >= hd_min_d, whose
+        // projection on at most 4 gridded dims lets many far points through),
+        // side ceil(d_cut / f) and reach f cover the same distance more finely
+        const int f = ds.d >= tn.hd_min_d ? tn.hd_cell_factor : 1;
         ds.R = f;
         ds.s = (ds.d_cut + f - 1) / f;
         ds.ptree = 0;
@@ -989,6 +996,7 @@ dpc_status dpc_set_tuning(dpc_ctx* ctx, const char* key, int64_t value) {
     else if (k == "ccap" && value >= 1 && value <= (1 << 24)) t.ccap = (uint32_t)value;
     else if (k == "tree_min_d" && value >= 1 && value <= 9) t.tree_min_d = (int)value;
     else if (k == "hd_cell_factor" && value >= 1 && value <= 3) t.hd_cell_factor = (int)value;
+    else if (k == "hd_min_d" && value >= 1 && value <= 9) t.hd_min_d = (int)value;
     else if (k == "max_batch_jobs" && value >= 1 && value <= 4096) {
         std::lock_guard<std::mutex> lk(ctx->mu);
         ctx->max_batch_jobs = (int)value;
@@ -1007,6 +1015,7 @@ dpc_status dpc_get_tuning(dpc_ctx* ctx, const char* key, int64_t* value) {
     else if (k == "ccap") *value = t.ccap;
     else if (k == "tree_min_d") *value = t.tree_min_d;
     else if (k == "hd_cell_factor") *value = t.hd_cell_factor;
+    else if (k == "hd_min_d") *value = t.hd_min_d;
     else if (k == "max_batch_jobs") {
         std::lock_guard<std::mutex> lk(ctx->mu);
         *value = ctx->max_batch_jobs;
@@ -1409,12 +1418,14 @@ dpc_status dpc_autotune(dpc_ctx* ctx, const dpc_job* jobs, int32_t n_jobs, int32
     std::vector<Knob> knobs = {{"kch", {1024, 2048, 4096}}, {"bf_rank", {256, 1024, 4096}}, {"clevel", {0, 2}}};
     if (sig.first >= 4) knobs.push_back({"kmax", {3, 4}});
     if (sig.first >= 5) knobs.push_back({"tree_min_d", {9, 5}});
+    if (sig.first >= 5) knobs.push_back({"hd_cell_factor", {1, 2}});
     auto with = [](dpc::Tune t, const std::string& k, int64_t v) {
         if (k == "kch") t.kch = (int)v;
         else if (k == "bf_rank") t.bf_rank = (uint32_t)v;
         else if (k == "clevel") t.clevel = (int)v;
         else if (k == "kmax") t.kmax = (int)v;
         else if (k == "tree_min_d") t.tree_min_d = (int)v;
+        else if (k == "hd_cell_factor") t.hd_cell_factor = (int)v;
         return t;
     };
     for (const auto& k : knobs) {

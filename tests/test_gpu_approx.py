@@ -96,7 +96,7 @@ def test_high_dims_finer_grid(dpc):
     pts = np.ascontiguousarray(ds.points)
     n = pts.shape[0]
     with dpc.Context(0) as ctx:
-        ctx.tune(hd_cell_factor=2)
+        ctx.tune(hd_cell_factor=2, hd_min_d=5)
         rho = np.empty(n, np.int32)
         h = ctx.density(pts, 9000, rho)
         dep = np.empty(n, np.int32)

@@ -128,7 +128,7 @@ def test_high_dims_grid_path(dpc, d, f):
     """The projected grid for d > 4 (the point tree switched off), with
     cells of side d_cut / f searched f cells away."""
     ds = workloads.random_blobs(60 + d, 2500, d, 9000, blobs=4, spread=0.05, dup=10)
-    info = assert_full_parity(dpc, ds.points, 9000, [(3, 27001)], dict(tree_min_d=9, hd_cell_factor=f))
+    info = assert_full_parity(dpc, ds.points, 9000, [(3, 27001)], dict(tree_min_d=9, hd_cell_factor=f, hd_min_d=5))
     assert 1 <= info["grid_dims"] <= 4
 
 
