@@ -211,6 +211,10 @@ dpc_status dpc_set_profiling(dpc_ctx* ctx, int on);
  *             grid, fewer candidate pairs, more neighbour cells), 1 .. 3
  *             (default 2)
  *   "hd_min_d"  smallest d that takes hd_cell_factor, 1 .. 9 (default 7)
+ *   "ring2"   1: points the first ring leaves open scan the cells at
+ *             distance 2 before the tree search, 0: straight to the tree
+ *             (default 0: on 5.8M x 3 it resolves 56% of them but costs more
+ *             than the tree search it saves)
  *   "max_batch_jobs"  served mode: jobs one batch admits at most, 1 .. 4096
  *             (default 64; 1 runs the jobs one at a time)
  * DPC_ERR_INVALID_ARG for an unknown key or a value out of range. */

@@ -193,6 +193,8 @@ __device__ __forceinline__ void rule2_finish(const BatchView& v, const DeltaBufs
         if (cj - ds.R > 0) bound = min(bound, (int64_t)xi - (ds.origin[j] + (cj - ds.R) * ds.s) + 1);
         if (cj + ds.R + 1 < ds.ext[j]) bound = min(bound, ds.origin[j] + (cj + ds.R + 1) * ds.s - (int64_t)xi);
     }
+    // cells the runs left out (at least d_cut away) were not scanned
+    if (ds.prune) bound = min(bound, ds.d_cut);
     const bool proven = r.bd != INT64_MAX && (bound == INT64_MAX || (bound < 3037000499ll && r.bd < bound * bound));
     if (proven) {
         v.dep[g] = (int32_t)r.bj;

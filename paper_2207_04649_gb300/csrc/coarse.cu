@@ -223,3 +223,158 @@ cudaError_t launch_coarse_ring(const BatchView& v, const DeltaBufs& db, uint32_t
 }
 
 }  // namespace dpc
+
+// ------------------------------------------------------------------ ring 2
+//
+// The second ring of the expanding search, on the fine grid itself: a point
+// the first ring left open (its nearest higher point among the 3^k
+// neighbouring cells, if any, is not proven) scans the shell of cells at
+// distance 2 (the 5^k block minus the 3^k one), one warp per point, lanes
+// taking shell cells, skipping those whose box is farther than the best
+// distance so far. It is resolved when the best higher point over both
+// rings lies strictly closer than the outside of the 5^k block; otherwise it
+// stays open for the tree search. Only datasets with cell side d_cut (reach
+// 1) take it.
+namespace dpc {
+namespace {
+
+template <int D>
+__device__ __forceinline__ void r2_load(const int4* r, int32_t (&x)[D]) {
+    const int4 a = r[0];
+    int32_t t[8] = {a.x, a.y, a.z, a.w, 0, 0, 0, 0};
+    if (D > 4) {
+        const int4 b = r[1];
+        t[4] = b.x; t[5] = b.y; t[6] = b.z; t[7] = b.w;
+    }
+#pragma unroll
+    for (int k = 0; k < D; ++k) x[k] = t[k];
+}
+
+template <int D>
+__global__ void __launch_bounds__(128) k_ring2(BatchView v, DeltaBufs db) {
+    constexpr int DP = D <= 4 ? 1 : 2;
+    const uint32_t cnt = db.ucount[0];
+    const int lane = threadIdx.x & 31;
+    const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t i = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); i < cnt; i += nwarps) {
+        const uint32_t p = db.tree_list[i];
+        const int b = find_ds(v.pt_off, v.B, p);
+        const DsDesc& ds = v.desc[b];
+        if (ds.d != D) continue;
+        bool keep = ds.R != 1 || ds.k == 0;
+        const int4* recb = v.rec + ds.rec_off - ds.pt_off * DP;
+        const int4* rp = recb + (int64_t)p * DP;
+        int32_t x[D];
+        r2_load<D>(rp, x);
+        const uint2 ro = v.ro_s[p];
+        // the first ring's best (unproven); a saturated distance is no candidate
+        long long bd = INT64_MAX;
+        uint32_t bj = 0xffffffffu;
+        const unsigned long long bk = v.best_s[p];
+        if (bk != ~0ull && (uint32_t)(bk >> 32) != 0xffffffffu) {
+            bd = (long long)(bk >> 32);
+            bj = (uint32_t)bk;
+        }
+        // a saturated first-ring distance lost its result: scan those cells again
+        const bool lost = bk != ~0ull && (uint32_t)(bk >> 32) == 0xffffffffu;
+        int32_t cc[kMaxGridDims];
+        int nsh = 1;
+        for (int j = 0; j < ds.k; ++j) {
+            cc[j] = cell_coord(ds, j, rec_coord(rp, ds.gdim[j]));
+            nsh *= 5;
+        }
+        const uint64_t own = v.key[p] - ds.cbase;
+        // lanes take the 5^k offsets; the inner 3^k were the first ring
+        for (int base = 0; base < nsh && !keep; base += 32) {
+            const int t = base + lane;
+            if (t < nsh) {
+                int tt = t;
+                bool inner = true, ok = true;
+                int nz = 0;
+                uint64_t code = own;
+                long long gap2 = 0;
+                for (int j = 0; j < ds.k; ++j) {
+                    const int o = tt % 5 - 2;
+                    tt /= 5;
+                    if (o < -1 || o > 1) inner = false;
+                    if (o != 0) {
+                        ++nz;
+                        ok = ok && cc[j] + o >= 0 && cc[j] + o < ds.ext[j];
+                        const int ao = o < 0 ? -o : o;
+                        for (int u = 0; u < ao; ++u) code = morton_step(code, ds.dmask[j], o);
+                        // distance from x to that cell's slab in this dim
+                        const int32_t xj = rec_coord(rp, ds.gdim[j]);
+                        const long long lo = ds.origin[j] + (long long)(cc[j] + o) * ds.s;
+                        const long long g = o > 0 ? lo - xj : xj - (lo + ds.s - 1);
+                        if (g > 0) gap2 += g * g;
+                    }
+                }
+                // an inner cell was the first ring's, unless its runs left it out
+                // (off in nz >= d_cut^2 dims: no point of it is within d_cut)
+                const bool todo = !inner || lost || (long long)nz >= ds.d_cut2;
+                if (todo && ok && gap2 <= bd) {
+                    const uint2 r = hash_find(v.hash, v.hmask, ds.cbase + code);
+                    for (uint32_t q = r.x; q < r.x + r.y; ++q) {
+                        const uint2 cr = v.ro_s[q];
+                        if (cr.x >= ro.x) continue;
+                        int32_t y[D];
+                        r2_load<D>(recb + (int64_t)q * DP, y);
+                        long long dd = 0;
+#pragma unroll
+                        for (int k = 0; k < D; ++k) {
+                            const long long e = (long long)x[k] - y[k];
+                            dd += e * e;
+                        }
+                        if (dd < bd || (dd == bd && cr.y < bj)) {
+                            bd = dd;
+                            bj = cr.y;
+                        }
+                    }
+                }
+            }
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            const long long d2 = __shfl_xor_sync(0xffffffffu, bd, o);
+            const uint32_t j2 = __shfl_xor_sync(0xffffffffu, bj, o);
+            if (d2 < bd || (d2 == bd && j2 < bj)) {
+                bd = d2;
+                bj = j2;
+            }
+        }
+        if (lane == 0) {
+            bool resolved = false;
+            if (!keep && bd != INT64_MAX) {
+                // distance to the outside of the 5^k block around the point
+                long long bound = INT64_MAX;
+                for (int j = 0; j < ds.k; ++j) {
+                    const long long xj = rec_coord(rp, ds.gdim[j]);
+                    if (cc[j] - 2 > 0) bound = min(bound, xj - (ds.origin[j] + (long long)(cc[j] - 2) * ds.s) + 1);
+                    if (cc[j] + 3 < ds.ext[j]) bound = min(bound, ds.origin[j] + (long long)(cc[j] + 3) * ds.s - xj);
+                }
+                resolved = bound == INT64_MAX || (bound < 3037000499ll && bd < bound * bound);
+            }
+            if (resolved) {
+                const int64_t g = ds.pt_off + ro.y;
+                v.dep[g] = (int32_t)bj;
+                v.delta2[g] = bd;
+            } else {
+                db.open2[atomicAdd(&db.ucount[2], 1u)] = p;
+            }
+        }
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_ring2(const BatchView& v, const DeltaBufs& db, uint32_t dim_mask, int64_t bound, cudaStream_t st) {
+    if (bound <= 0) return cudaSuccess;
+    const unsigned blocks = (unsigned)std::min<int64_t>(152 * 16, grid_for(bound, 4));
+#define DPC_RING2_CLASS(D) \
+    if (dim_mask & (1u << (D - 1))) (k_ring2<D><<<blocks, 128, 0, st>>>(v, db), note_launch());
+    DPC_RING2_CLASS(1) DPC_RING2_CLASS(2) DPC_RING2_CLASS(3) DPC_RING2_CLASS(4)
+    DPC_RING2_CLASS(5) DPC_RING2_CLASS(6) DPC_RING2_CLASS(7) DPC_RING2_CLASS(8)
+#undef DPC_RING2_CLASS
+    return cudaGetLastError();
+}
+
+}  // namespace dpc

@@ -344,6 +344,8 @@ __global__ void k_finalize(BatchView v, DeltaBufs db) {
                 if (cj - ds.R > 0) bound = min(bound, x - (ds.origin[j] + (cj - ds.R) * ds.s) + 1);
                 if (cj + ds.R + 1 < ds.ext[j]) bound = min(bound, ds.origin[j] + (cj + ds.R + 1) * ds.s - x);
             }
+            // cells the runs left out (at least d_cut away) were not searched
+            if (ds.prune) bound = min(bound, ds.d_cut);
             const bool found = bk != kNoBest && dd != kSat;
             if (found && (bound == INT64_MAX || (int64_t)dd < bound * bound)) {
                 v.dep[g] = (int32_t)(uint32_t)bk;

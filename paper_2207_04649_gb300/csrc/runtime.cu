@@ -107,6 +107,7 @@ struct Tune {
     int tree_min_d = 9;       // datasets with at least this many dims take the point tree (9: none)
     int hd_cell_factor = 2;   // datasets with d >= hd_min_d: cells of side d_cut / f searched to reach f
     int hd_min_d = 7;
+    int ring2 = 0;            // second ring (cells at distance 2) before the tree search
 };
 
 }  // namespace
@@ -615,6 +616,13 @@ struct Batch {
         }
         ds.cbase = cbase;
         cbase += 1ull << (k * mbits);
+        // the neighbour runs skip cells whose box is at least d_cut away: with
+        // reach 1 a cell off in n dims is at least sqrt(n) away, with reach R
+        // the farthest ring's corner cells at least sqrt(k) ((R - 1) s + 1)
+        {
+            const int64_t g = (int64_t)(ds.R - 1) * ds.s + 1;
+            ds.prune = (int64_t)k * g * g >= ds.d_cut2 ? 1 : 0;
+        }
         // 32-bit pair arithmetic when the largest possible candidate sum fits
         int64_t maxsum = 0;
         for (int c = 0; c < ds.d; ++c) {
@@ -698,6 +706,13 @@ struct Batch {
                 DPC_CK(launch_coarse_hash(v, db, st));
                 DPC_CK(tmp.get(&db.open2, ntree));
                 DPC_CK(launch_coarse_ring(v, db, dim_mask, ntree, st));
+                db.tree_list = db.open2;
+                db.tcount = db.ucount + 2;
+            } else if (allow_coarse && tune.ring2) {
+                // the second ring on the fine grid; the first ring's unproven
+                // best (v.best_s) is part of its search
+                DPC_CK(tmp.get(&db.open2, ntree));
+                DPC_CK(launch_ring2(v, db, dim_mask, ntree, st));
                 db.tree_list = db.open2;
                 db.tcount = db.ucount + 2;
             }
@@ -997,6 +1012,7 @@ dpc_status dpc_set_tuning(dpc_ctx* ctx, const char* key, int64_t value) {
     else if (k == "tree_min_d" && value >= 1 && value <= 9) t.tree_min_d = (int)value;
     else if (k == "hd_cell_factor" && value >= 1 && value <= 3) t.hd_cell_factor = (int)value;
     else if (k == "hd_min_d" && value >= 1 && value <= 9) t.hd_min_d = (int)value;
+    else if (k == "ring2" && value >= 0 && value <= 1) t.ring2 = (int)value;
     else if (k == "max_batch_jobs" && value >= 1 && value <= 4096) {
         std::lock_guard<std::mutex> lk(ctx->mu);
         ctx->max_batch_jobs = (int)value;
@@ -1016,6 +1032,7 @@ dpc_status dpc_get_tuning(dpc_ctx* ctx, const char* key, int64_t* value) {
     else if (k == "tree_min_d") *value = t.tree_min_d;
     else if (k == "hd_cell_factor") *value = t.hd_cell_factor;
     else if (k == "hd_min_d") *value = t.hd_min_d;
+    else if (k == "ring2") *value = t.ring2;
     else if (k == "max_batch_jobs") {
         std::lock_guard<std::mutex> lk(ctx->mu);
         *value = ctx->max_batch_jobs;

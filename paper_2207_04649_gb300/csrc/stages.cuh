@@ -269,6 +269,9 @@ cudaError_t launch_coarse_cells(const BatchView& v, const DeltaBufs& db, void* s
 cudaError_t launch_coarse_hash(const BatchView& v, const DeltaBufs& db, cudaStream_t st);
 cudaError_t launch_coarse_ring(const BatchView& v, const DeltaBufs& db, uint32_t dim_mask, int64_t bound,
                                cudaStream_t st);
+// Second ring on the fine grid (cells at distance 2) for the open list db.tree_list
+// (count db.ucount[0]); the still-open points go to db.open2 (count db.ucount[2]).
+cudaError_t launch_ring2(const BatchView& v, const DeltaBufs& db, uint32_t dim_mask, int64_t bound, cudaStream_t st);
 // tree.cu: build (cell ranges, keys, radix tree, refit) and search
 cudaError_t launch_tree_build(const BatchView& v, const DeltaBufs& db, cudaStream_t st);
 cudaError_t launch_tree_search(const BatchView& v, const DeltaBufs& db, uint32_t dim_mask, int64_t bound,

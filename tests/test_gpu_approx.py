@@ -69,6 +69,8 @@ SHAPES = [
     (7, 4000, 3, 1, 50, 2, 0.2, 100),       # d_cut = 1: side 1
     (8, 5000, 2, 30, 1000, 3, 0.2, 50),     # many points per cell
     (9, 2000, 3, 200, 100000, 40, 0.002, 0),
+    (10, 3000, 4, 2, 30, 3, 0.2, 50),      # corner cells of the d_cut grid left out
+    (11, 2500, 8, 3, 12, 3, 0.3, 30),
 ]
 
 

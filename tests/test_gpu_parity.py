@@ -147,6 +147,26 @@ def test_point_tree_edge_cases(dpc):
         assert_full_parity(dpc, pts, 300, [(1, 301)], dict(tree_min_d=5))
 
 
+SMALL_CUTOFFS = [
+    (71, 3000, 4, 2, 30, 3, 0.2, 50),   # k = 4, d_cut = 2: corner cells lie at least d_cut away
+    (72, 3000, 4, 1, 20, 3, 0.2, 50),
+    (73, 3000, 2, 1, 60, 3, 0.2, 50),
+    (74, 3000, 3, 2, 40, 3, 0.2, 50),
+    (75, 2500, 8, 3, 12, 3, 0.3, 30),   # reach 2 (d >= 7) with far corner cells left out
+    (76, 2500, 7, 4, 15, 3, 0.3, 30),
+]
+
+
+@pytest.mark.parametrize("ring2", [0, 1])
+@pytest.mark.parametrize("shape", SMALL_CUTOFFS, ids=lambda s: f"n{s[1]}_d{s[2]}_dc{s[3]}")
+def test_small_cutoffs_bit_exact(dpc, shape, ring2):
+    """Cutoffs so small that the neighbour runs leave out in-reach cells (no
+    point there is within d_cut, but one may be the nearest higher point)."""
+    seed, n, d, dc, dom, blobs, spread, dup = shape
+    ds = workloads.random_blobs(seed, n, d, dc, domain=dom, blobs=blobs, spread=spread, dup=dup)
+    assert_full_parity(dpc, ds.points, dc, [(1, dc + 1), (2, 3 * dc + 1)], dict(ring2=ring2))
+
+
 def test_all_points_identical(dpc):
     pts = np.full((777, 3), 4242, np.int32)
     assert_full_parity(dpc, pts, 10, [(1, 11), (778, 11)])
@@ -292,7 +312,8 @@ def test_plain_5p8m_3d_sampled(dpc):
 
 @pytest.mark.parametrize("knobs", [dict(clevel=2, ccap=512), dict(clevel=1, ccap=64, bf_rank=0),
                                    dict(kch=64, bf_rank=100000), dict(kmax=2), dict(kmax=1, clevel=3),
-                                   dict(tree_min_d=3), dict(tree_min_d=1, bf_rank=0)],
+                                   dict(tree_min_d=3), dict(tree_min_d=1, bf_rank=0), dict(ring2=0),
+                                   dict(ring2=1, bf_rank=0)],
                          ids=lambda k: ",".join(f"{a}={b}" for a, b in k.items()))
 def test_tuning_knobs_do_not_change_results(dpc, knobs):
     ds = workloads.random_blobs(77, 6000, 3, 900, blobs=5, spread=0.06, dup=8)
