@@ -9,14 +9,16 @@ The arithmetic lives in ``dpc_oracle.c`` (plain C with OpenMP over points,
 built here with gcc); this module compiles it and wraps it with numpy. Every
 function follows the paper's problem definition (Section 2.1, Definitions
 1-6) and its straightforward Scan algorithm (Section 2.2); the ``approx_*``
-functions follow Approx-DPC's dependent-point rules (Section 4.3). The
-readings of the paper it takes are listed in ``dpc_oracle.c``.
+functions follow Approx-DPC's dependent-point rules (Section 4.3); the
+``sapprox*`` functions follow S-Approx-DPC (Section 5). The readings of the
+paper it takes are listed in ``dpc_oracle.c``.
 
 Parity status: every function is pinned by the tests in
-``tests/test_oracle.py`` and ``tests/test_oracle_approx.py`` (hand-worked
-examples in ``tests/golden/``, closed forms, invariants, an independent
-brute force, the paper's cluster-center guarantee for Approx-DPC, and
-planted mistakes), so none is "parity unpinned".
+``tests/test_oracle.py``, ``tests/test_oracle_approx.py`` and
+``tests/test_oracle_sapprox.py`` (hand-worked examples in ``tests/golden/``,
+closed forms, invariants, an independent brute force, the paper's
+cluster-center guarantee for Approx-DPC, S-Approx-DPC reducing to exact DPC
+on cells of one point, and planted mistakes), so none is "parity unpinned".
 """
 from __future__ import annotations
 
@@ -70,6 +72,12 @@ def _load():
         lib.oracle_approx_side.restype = i64
         lib.oracle_approx_dependent.argtypes = [vp, i64, i32, i64, vp, vp, vp, vp]
         lib.oracle_approx_dependent_subset.argtypes = [vp, i64, i32, i64, vp, vp, i64, vp, vp, vp]
+        lib.oracle_sapprox_side.argtypes = [i64, i32, i64, i64]
+        lib.oracle_sapprox_side.restype = i64
+        lib.oracle_sapprox.argtypes = [vp, i64, i32, i64, i64, i64, vp, vp, vp, vp]
+        lib.oracle_sapprox_dependent_subset.argtypes = [vp, i64, i32, i64, i64, i64, vp, vp, i64, vp, vp, vp]
+        lib.oracle_sapprox_label.argtypes = [i64, vp, vp, vp, vp, i64, i64, vp]
+        lib.oracle_sapprox_label.restype = i64
         _lib = lib
         return lib
 
@@ -192,6 +200,54 @@ def run_approx(points, d_cut: int, rho_min: int, delta_min: int) -> dict:
     dep, d2, ex = approx_dependent(points, r, d_cut)
     lab, nc = label(r, dep, d2, rho_min, delta_min)
     return {"rho": r, "dep": dep, "delta2": d2, "exact": ex, "label": lab, "n_centers": nc}
+
+
+def sapprox_side(d_cut: int, d: int, eps_num: int, eps_den: int) -> int:
+    """S-Approx-DPC's grid side: max(1, floor(eps d_cut / sqrt(d))), eps = num / den."""
+    return int(_load().oracle_sapprox_side(int(d_cut), int(d), int(eps_num), int(eps_den)))
+
+
+def sapprox(points, d_cut: int, eps_num: int, eps_den: int):
+    """S-Approx-DPC (Section 5): (rho, dep, delta2, pick); rho is -1 and dep
+    the cell's pick for the points that are not picked."""
+    p = _pts(points)
+    n, d = p.shape
+    rho_ = np.empty(n, dtype=np.int32)
+    dep = np.empty(n, dtype=np.int32)
+    d2 = np.empty(n, dtype=np.int64)
+    pk = np.empty(n, dtype=np.int32)
+    _load().oracle_sapprox(_ptr(p), n, d, int(d_cut), int(eps_num), int(eps_den), _ptr(rho_), _ptr(dep), _ptr(d2),
+                           _ptr(pk))
+    return rho_, dep, d2, pk.astype(bool)
+
+
+def sapprox_dependent_subset(points, rho_arr, d_cut: int, eps_num: int, eps_den: int, idx):
+    """Sampled S-Approx-DPC links: (dep, delta2, pick) of the points idx,
+    given rho of every pick (other entries unused)."""
+    p = _pts(points)
+    n, d = p.shape
+    r = np.ascontiguousarray(rho_arr, dtype=np.int32)
+    ix = np.ascontiguousarray(idx, dtype=np.int64)
+    m = ix.shape[0]
+    dep = np.empty(m, dtype=np.int32)
+    d2 = np.empty(m, dtype=np.int64)
+    pk = np.empty(m, dtype=np.int32)
+    _load().oracle_sapprox_dependent_subset(_ptr(p), n, d, int(d_cut), int(eps_num), int(eps_den), _ptr(r), _ptr(ix),
+                                            m, _ptr(dep), _ptr(d2), _ptr(pk))
+    return dep, d2, pk.astype(bool)
+
+
+def sapprox_label(rho_arr, dep, delta2, pick, rho_min: int, delta_min: int):
+    """S-Approx-DPC labels: Definitions 4-6 over the picks, others take their pick's label."""
+    r = np.ascontiguousarray(rho_arr, dtype=np.int32)
+    dp = np.ascontiguousarray(dep, dtype=np.int32)
+    d2 = np.ascontiguousarray(delta2, dtype=np.int64)
+    pk = np.ascontiguousarray(pick, dtype=np.int32)
+    n = r.shape[0]
+    lab = np.empty(n, dtype=np.int32)
+    nc = _load().oracle_sapprox_label(n, _ptr(r), _ptr(dp), _ptr(d2), _ptr(pk), int(rho_min), int(delta_min),
+                                      _ptr(lab))
+    return lab, int(nc)
 
 
 def run(points, d_cut: int, rho_min: int, delta_min: int) -> dict:

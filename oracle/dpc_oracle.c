@@ -13,8 +13,9 @@
  * denser prefix for every dependent point, and a depth-first label
  * propagation from the cluster centers. OpenMP spreads the independent
  * per-point loops over the host cores; it changes no arithmetic. The last
- * part (oracle_approx_*) follows Approx-DPC's dependent-point rules
- * (Section 4.3) on top of the same exact densities.
+ * oracle_approx_* functions follow Approx-DPC's dependent-point rules
+ * (Section 4.3) on top of the same exact densities; the oracle_sapprox_*
+ * functions follow S-Approx-DPC (Section 5).
  *
  * Readings of the paper (it is silent or loose on these points):
  *  - dist() is Euclidean. It is compared squared, exactly, in 64-bit
@@ -369,4 +370,196 @@ void oracle_approx_dependent_subset(const int32_t* P, int64_t n, int32_t d, int6
                                     const int64_t* idx, int64_t m, int32_t* dep_sub, int64_t* delta2_sub,
                                     int32_t* exact_sub) {
     approx_dependent(P, n, d, d_cut, rho, idx, m, dep_sub, delta2_sub, exact_sub);
+}
+
+/* ----------------------------------------------------------------------
+ * S-Approx-DPC (Section 5): one picked point per cell of the grid G' of
+ * side eps * d_cut / sqrt(d); local densities and dependent points of the
+ * picked points only; every other point depends on its cell's pick.
+ *
+ * Readings (the paper leaves these choices open or loose):
+ *  - eps = eps_num / eps_den; the side is the integer
+ *    s = max(1, floor(eps * d_cut / sqrt(d))), anchored at the
+ *    per-dimension minimum of P.
+ *  - The picked point of a cell ("decided in an arbitrary way") is its point
+ *    with the smallest original index.
+ *  - A pick's local density is Definition 1 against all of P. Picks are
+ *    ordered by (rho desc, index asc); "higher" compares picks only.
+ *  - N(c): the cells other than c holding a point p' with
+ *    D(pick(c), p') < d_cut^2.
+ *  - First phase: among the picks of the cells in N(c) that are higher than
+ *    pick(c) (chosen "arbitrarily" in the paper), the nearest one, ties to
+ *    the smaller index; its exact squared distance is the delta2.
+ *  - Second phase: a pick without such a candidate gets its nearest higher
+ *    pick over all picks (what the paper's temporary-cluster pruning finds
+ *    exactly); the highest pick keeps dep -1 and delta2 INT64_MAX.
+ *  - A point that is not picked: dep = its cell's pick, delta2 = its exact
+ *    squared distance to it, rho = -1 (not computed).
+ * pick[i] is 1 for the picked points.
+ */
+int64_t oracle_sapprox_side(int64_t d_cut, int32_t d, int64_t eps_num, int64_t eps_den) {
+    /* floor(eps * d_cut / sqrt(d)) = floor(sqrt((eps_num d_cut)^2 / (eps_den^2 d))) */
+    const double num = (double)eps_num * (double)d_cut;
+    const int64_t q = (int64_t)((num * num) / ((double)eps_den * (double)eps_den * (double)d));
+    int64_t s = isqrt_i64(q);
+    /* q may be off by rounding of the double quotient: correct s exactly */
+    while (s > 0 && (__int128)s * s * eps_den * eps_den * d > (__int128)eps_num * eps_num * d_cut * d_cut) --s;
+    while ((__int128)(s + 1) * (s + 1) * eps_den * eps_den * d <= (__int128)eps_num * eps_num * d_cut * d_cut) ++s;
+    return s < 1 ? 1 : s;
+}
+
+/* The grid G' and its picks: cell[i] is the index of point i's cell (cells
+ * numbered in sorted cell order), cpick[c] the pick of cell c, pick[i] 1 for
+ * the picks. */
+static void sapprox_grid(const int32_t* P, int64_t n, int32_t d, int64_t d_cut, int64_t eps_num, int64_t eps_den,
+                         int64_t* cell, int64_t* cpick, int32_t* pick) {
+    const int64_t s = oracle_sapprox_side(d_cut, d, eps_num, eps_den);
+    int64_t* cc = approx_cells(P, n, d, s);
+    int64_t* by_cell = (int64_t*)malloc((size_t)n * sizeof(int64_t));
+    for (int64_t i = 0; i < n; ++i) by_cell[i] = i;
+    g_cc = cc;
+    g_d = d;
+    qsort(by_cell, (size_t)n, sizeof(int64_t), cmp_cells);
+    int64_t ncell = 0;
+    for (int64_t t = 0; t < n; ++t) {
+        const int64_t i = by_cell[t];
+        int same = 0;
+        if (t > 0) {
+            const int64_t j = by_cell[t - 1];
+            same = 1;
+            for (int32_t k = 0; k < d; ++k)
+                if (cc[i * d + k] != cc[j * d + k]) same = 0;
+        }
+        if (!same) cpick[ncell++] = i;
+        const int64_t c = ncell - 1;
+        cell[i] = c;
+        if (i < cpick[c]) cpick[c] = i;
+    }
+    for (int64_t i = 0; i < n; ++i) pick[i] = cpick[cell[i]] == i;
+    free(cc);
+    free(by_cell);
+}
+
+/* The dependent point of point i (rho given for every pick). */
+static void sapprox_link(const int32_t* P, int64_t n, int32_t d, int64_t d_cut, const int64_t* cell,
+                         const int64_t* cpick, const int32_t* pick, const int32_t* rho, int64_t i, int32_t* dep_i,
+                         int64_t* delta2_i) {
+    const int64_t r2 = d_cut * d_cut;
+    if (!pick[i]) {
+        *dep_i = (int32_t)cpick[cell[i]];
+        *delta2_i = sq_dist(P, d, i, cpick[cell[i]]);
+        return;
+    }
+    /* pick q is higher than pick i: rho_q > rho_i, or equal and q < i */
+    int64_t dp = -1, d2 = INT64_MAX;
+    /* first phase: picks of the cells of N(c) */
+    for (int64_t j = 0; j < n; ++j) {
+        if (cell[j] == cell[i] || sq_dist(P, d, i, j) >= r2) continue;
+        const int64_t q = cpick[cell[j]];
+        if (!(rho[q] > rho[i] || (rho[q] == rho[i] && q < i))) continue;
+        const int64_t dq = sq_dist(P, d, i, q);
+        if (dq < d2 || (dq == d2 && q < dp)) {
+            d2 = dq;
+            dp = q;
+        }
+    }
+    if (dp < 0) {
+        /* second phase: the nearest higher pick over all picks */
+        for (int64_t q = 0; q < n; ++q) {
+            if (!pick[q] || !(rho[q] > rho[i] || (rho[q] == rho[i] && q < i))) continue;
+            const int64_t dq = sq_dist(P, d, i, q);
+            if (dq < d2 || (dq == d2 && q < dp)) {
+                d2 = dq;
+                dp = q;
+            }
+        }
+    }
+    *dep_i = (int32_t)dp;
+    *delta2_i = d2;
+}
+
+void oracle_sapprox(const int32_t* P, int64_t n, int32_t d, int64_t d_cut, int64_t eps_num, int64_t eps_den,
+                    int32_t* rho, int32_t* dep, int64_t* delta2, int32_t* pick) {
+    if (n <= 0) return;
+    const int64_t r2 = d_cut * d_cut;
+    int64_t* cell = (int64_t*)malloc((size_t)n * sizeof(int64_t));
+    int64_t* cpick = (int64_t*)malloc((size_t)n * sizeof(int64_t));  /* per cell: its pick */
+    sapprox_grid(P, n, d, d_cut, eps_num, eps_den, cell, cpick, pick);
+    /* densities of the picks (Definition 1 against all points) */
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int64_t i = 0; i < n; ++i) {
+        if (!pick[i]) {
+            rho[i] = -1;
+            continue;
+        }
+        int32_t c = 0;
+        for (int64_t j = 0; j < n; ++j)
+            if (sq_dist(P, d, i, j) < r2) ++c;
+        rho[i] = c;
+    }
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int64_t i = 0; i < n; ++i) sapprox_link(P, n, d, d_cut, cell, cpick, pick, rho, i, &dep[i], &delta2[i]);
+    free(cell);
+    free(cpick);
+}
+
+/* The sampled form for sets too large for the full one: picks and links of
+ * the points idx[0..m), given rho for every pick (the other entries are not
+ * read). The picks' densities themselves are checked with oracle_rho_subset. */
+void oracle_sapprox_dependent_subset(const int32_t* P, int64_t n, int32_t d, int64_t d_cut, int64_t eps_num,
+                                     int64_t eps_den, const int32_t* rho, const int64_t* idx, int64_t m,
+                                     int32_t* dep_sub, int64_t* delta2_sub, int32_t* pick_sub) {
+    if (n <= 0) return;
+    int64_t* cell = (int64_t*)malloc((size_t)n * sizeof(int64_t));
+    int64_t* cpick = (int64_t*)malloc((size_t)n * sizeof(int64_t));
+    int32_t* pick = (int32_t*)malloc((size_t)n * sizeof(int32_t));
+    sapprox_grid(P, n, d, d_cut, eps_num, eps_den, cell, cpick, pick);
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int64_t t = 0; t < m; ++t) {
+        sapprox_link(P, n, d, d_cut, cell, cpick, pick, rho, idx[t], &dep_sub[t], &delta2_sub[t]);
+        pick_sub[t] = pick[idx[t]];
+    }
+    free(cell);
+    free(cpick);
+    free(pick);
+}
+
+/* Labels of S-Approx-DPC: Definitions 4-6 over the picks (noise: rho below
+ * rho_min; centers: non-noise picks with delta2 >= delta_min^2; labels along
+ * the dependent links among picks), then every other point takes its pick's
+ * label (rho_min does not apply to it). Returns the number of centers. */
+int64_t oracle_sapprox_label(int64_t n, const int32_t* rho, const int32_t* dep, const int64_t* delta2,
+                             const int32_t* pick, int64_t rho_min, int64_t delta_min, int32_t* label) {
+    const int64_t dmin2 = delta_min * delta_min;
+    int64_t n_centers = 0;
+    for (int64_t i = 0; i < n; ++i) label[i] = -2; /* not yet known */
+    for (int64_t i = 0; i < n; ++i) {
+        if (!pick[i]) continue;
+        if ((int64_t)rho[i] < rho_min) label[i] = -1;
+        else if (delta2[i] >= dmin2) {
+            label[i] = (int32_t)i;
+            ++n_centers;
+        }
+    }
+    /* follow each pick's chain to the first labelled pick (a center, or the
+     * densest pick, which is a center unless it is noise) */
+    for (int64_t i = 0; i < n; ++i) {
+        if (!pick[i] || label[i] != -2) continue;
+        int64_t q = i, hops = 0;
+        while (label[q] == -2 && dep[q] >= 0 && hops <= n) {
+            q = dep[q];
+            ++hops;
+        }
+        const int32_t l = label[q] == -2 ? -1 : label[q];
+        /* write the label along the chain */
+        int64_t r = i;
+        while (label[r] == -2) {
+            label[r] = l;
+            if (dep[r] < 0) break;
+            r = dep[r];
+        }
+    }
+    for (int64_t i = 0; i < n; ++i)
+        if (!pick[i]) label[i] = label[dep[i]];
+    return n_centers;
 }
