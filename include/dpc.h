@@ -125,6 +125,33 @@ dpc_status dpc_dependent(dpc_ds* ds, int32_t* dep_out, int64_t* delta2_out);
  * a dataset on the point tree (tree_min_d at or below its d). */
 dpc_status dpc_dependent_approx(dpc_ds* ds, int32_t* dep_out, int64_t* delta2_out, uint8_t* exact_out);
 
+/* S-Approx-DPC (Section 5): local densities and dependent points of one
+ * picked point per cell of a finer grid G', instead of every point's.
+ * G' has cells of side eps * d_cut / sqrt(d), here the integer side
+ * max(1, floor(eps * d_cut / sqrt(d))) with eps = eps_num / eps_den,
+ * anchored at the per-dimension minimum. A cell's pick is its point with the
+ * smallest original index. Picks get their exact local density (Definition
+ * 1) and are ordered by (rho desc, index asc). A pick's dependent point is
+ * the nearest higher pick among the picks of the cells (other than its own)
+ * that hold a point strictly within d_cut of it (first phase); without one,
+ * its nearest higher pick over all picks (second phase); the densest pick
+ * has none (-1, INT64_MAX). Ties in distance go to the smaller index. Every
+ * other point depends on its cell's pick, at its exact squared distance.
+ * dpc_label on the returned dataset labels the picks by Definitions 4-6 and
+ * gives every other point its pick's label; dpc_dependent copies the
+ * dependent points above; dpc_dependent_approx returns DPC_ERR_STATE.
+ *   points, n, d, d_cut, is_device, out: as for dpc_density.
+ *   eps_num, eps_den: 1 .. 2^20 each.
+ *   rho_out:    NULL or n int32: rho of the picks, -1 elsewhere.
+ *   dep_out, delta2_out: NULL or n int32 / int64, as for dpc_dependent.
+ *   pick_out:   NULL or n uint8: 1 for the picks.
+ * Host or device memory, as for is_device.
+ * Errors: those of dpc_density; DPC_ERR_STATE when tree_min_d is at or
+ * below d (no grid). */
+dpc_status dpc_sapprox(dpc_ctx* ctx, const int32_t* points, int64_t n, int32_t d, int64_t d_cut, int64_t eps_num,
+                       int64_t eps_den, int is_device, dpc_ds** out, int32_t* rho_out, int32_t* dep_out,
+                       int64_t* delta2_out, uint8_t* pick_out);
+
 /* Noise, centers and labels (Definitions 4-6) for one (rho_min, delta_min)
  * query. Re-queryable: only this step runs again (the decision-graph
  * workflow of Section 2.1). Uses the dependent points of the last
@@ -186,6 +213,8 @@ typedef struct {
     int64_t dense_pairs;      /* of cand_pairs, those of dense cells (one warp per work item) */
     float ms_rho_dense;       /* of ms_rho, the dense cells' kernels (profiling on) */
     int32_t reserved2;
+    int64_t picks;            /* S-Approx-DPC: cells of G' (picked points) */
+    int64_t second_phase;     /* S-Approx-DPC: picks without a first-phase dependent point */
 } dpc_info;
 
 dpc_status dpc_ds_info(const dpc_ds* ds, dpc_info* out);

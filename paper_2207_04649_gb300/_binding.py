@@ -48,7 +48,8 @@ class DpcInfo(ctypes.Structure):
                 ("ms_ring", ctypes.c_float), ("ms_rest", ctypes.c_float), ("ms_label", ctypes.c_float),
                 ("tree_visits", ctypes.c_int64), ("tree_pairs", ctypes.c_int64),
                 ("open_after_coarse", ctypes.c_int64), ("pair_mode", ctypes.c_int32), ("reserved", ctypes.c_int32),
-                ("dense_pairs", ctypes.c_int64), ("ms_rho_dense", ctypes.c_float), ("reserved2", ctypes.c_int32)]
+                ("dense_pairs", ctypes.c_int64), ("ms_rho_dense", ctypes.c_float), ("reserved2", ctypes.c_int32),
+                ("picks", ctypes.c_int64), ("second_phase", ctypes.c_int64)]
 
     def as_dict(self) -> dict:
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -94,6 +95,7 @@ def lib():
             "dpc_ds_info": ([vp, ctypes.POINTER(DpcInfo)], st),
             "dpc_last_batch_info": ([vp, ctypes.POINTER(DpcInfo)], st),
             "dpc_dependent_approx": ([vp, vp, vp, vp], st),
+            "dpc_sapprox": ([vp, vp, i64, i32, i64, i64, i64, ctypes.c_int, ctypes.POINTER(vp), vp, vp, vp, vp], st),
             "dpc_autotune": ([vp, ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32, ctypes.c_char_p,
                               ctypes.c_size_t], st),
             "dpc_set_profiling": ([vp, ctypes.c_int], st),
@@ -164,6 +166,14 @@ def dpc_dependent(ds, dep_ptr=None, delta2_ptr=None):
 
 def dpc_dependent_approx(ds, dep_ptr=None, delta2_ptr=None, exact_ptr=None):
     return _check(lib().dpc_dependent_approx(ds, dep_ptr, delta2_ptr, exact_ptr), "dpc_dependent_approx")
+
+
+def dpc_sapprox(ctx, points_ptr, n, d, d_cut, eps_num, eps_den, is_device, rho_ptr=None, dep_ptr=None,
+                delta2_ptr=None, pick_ptr=None):
+    h = ctypes.c_void_p()
+    _check(lib().dpc_sapprox(ctx, points_ptr, n, d, d_cut, int(eps_num), int(eps_den), is_device, ctypes.byref(h),
+                             rho_ptr, dep_ptr, delta2_ptr, pick_ptr), "dpc_sapprox")
+    return h
 
 
 def dpc_label(ds, rho_min, delta_min, label_ptr=None):
@@ -317,6 +327,26 @@ class Context:
         h = dpc_density(self.handle, pp, n, d, int(d_cut), dev, rp)
         return Dataset(self, h, n, dev)
 
+    def sapprox(self, points, d_cut: int, eps, rho_out=None, dep_out=None, delta2_out=None,
+                pick_out=None) -> "Dataset":
+        """S-Approx-DPC (Section 5) with eps = (num, den), or a float read as
+        num / 10^6; labels of the returned dataset follow its picks."""
+        if points.ndim != 2:
+            raise ValueError("points must be n x d")
+        num, den = eps_fraction(eps)
+        n, d = int(points.shape[0]), int(points.shape[1])
+        pp, dev = _arg(points, np.int32)
+        outs = [(rho_out, np.int32), (dep_out, np.int32), (delta2_out, np.int64), (pick_out, np.uint8)]
+        ptrs = []
+        for x, dt in outs:
+            p, xdev = _arg(x, dt, (n,))
+            if x is not None and xdev != dev:
+                raise ValueError("outputs must live where points live")
+            ptrs.append(p)
+        self._order_after_torch(points, rho_out, dep_out, delta2_out, pick_out)
+        h = dpc_sapprox(self.handle, pp, n, d, int(d_cut), num, den, dev, *ptrs)
+        return Dataset(self, h, n, dev)
+
     def tune(self, **knobs):
         """Set tuning knobs (speed only; results are unchanged)."""
         for k, val in knobs.items():
@@ -425,6 +455,38 @@ class Job:
         self.c = DpcJob(p(self.points), n, d, int(d_cut), len(q), h(self.rho_min), h(self.delta_min),
                         p(self.rho), p(self.dep), p(self.delta2), p(self.label), h(self.n_centers), is_dev)
         self.ticket = None
+
+
+def eps_fraction(eps):
+    """(num, den) of S-Approx-DPC's eps: a pair as given, or a float rounded
+    to a multiple of 10^-6 and reduced."""
+    import math
+    if isinstance(eps, tuple):
+        num, den = int(eps[0]), int(eps[1])
+    else:
+        num, den = int(round(float(eps) * 10 ** 6)), 10 ** 6
+        g = math.gcd(num, den)
+        num, den = num // g, den // g
+    if num < 1 or den < 1:
+        raise ValueError("eps must be positive")
+    return num, den
+
+
+def cluster_sapprox(points: np.ndarray, d_cut: int, eps, rho_min: int, delta_min: int, device: int = 0) -> dict:
+    """S-Approx-DPC on host arrays: rho (-1 where not picked), dep, delta2,
+    pick, label, n_centers."""
+    pts = np.ascontiguousarray(points, dtype=np.int32)
+    n = pts.shape[0]
+    with Context(device) as ctx:
+        rho = np.empty(n, np.int32)
+        dep = np.empty(n, np.int32)
+        d2 = np.empty(n, np.int64)
+        pk = np.empty(n, np.uint8)
+        ds = ctx.sapprox(pts, d_cut, eps, rho, dep, d2, pk)
+        lab = np.empty(n, np.int32)
+        nc = ds.label(rho_min, delta_min, lab)
+        ds.release()
+    return {"rho": rho, "dep": dep, "delta2": d2, "pick": pk.astype(bool), "label": lab, "n_centers": nc}
 
 
 def cluster_approx(points: np.ndarray, d_cut: int, rho_min: int, delta_min: int, device: int = 0) -> dict:

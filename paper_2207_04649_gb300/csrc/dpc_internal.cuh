@@ -50,7 +50,8 @@ struct DsDesc {
     int32_t nleaf;        // point tree leaves (ceil(n / kLeaf))
     int32_t rbits;        // bits of the density key in the rank sort
     uint64_t dmask[kMaxGridDims];  // Morton bits of each gridded dim
-    int32_t a_side;       // Approx-DPC grid: integer side max(1, floor(d_cut / sqrt(d)))
+    int32_t a_side;       // Approx-DPC grid: integer side max(1, floor(d_cut / sqrt(d)));
+                          // S-Approx-DPC grid: max(1, floor(eps d_cut / sqrt(d))), at most 2^30
     int32_t a_shift[kMaxDims];  // Approx-DPC grid: bit offset of each dim's cell coordinate in the key
     uint64_t a_base;      // Approx-DPC grid: key base of this dataset
     int32_t prune;        // 1: the neighbour runs may leave out in-reach cells whose box is at least
@@ -94,6 +95,7 @@ struct BatchView {
     int32_t* parent;           // original, global
     int32_t* label;            // original, local
     uint8_t* exact;            // original: 1 when the dependent point is exact (Approx-DPC)
+    uint8_t* pick;             // original: 1 for the picked points of S-Approx-DPC; NULL on other paths
     unsigned long long* ncent; // [B]
     unsigned int* err;         // device error word: kErr* bits set by guarded kernels
 };

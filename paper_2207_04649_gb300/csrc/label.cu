@@ -5,7 +5,8 @@
 //              delta2_i >= delta_min^2; the densest point has delta2 =
 //              INT64_MAX, so it is a center whenever it is not noise);
 // a center is its own parent, noise has none, every other point hangs on its
-// dependent point. The paper propagates labels depth-first from the centers
+// dependent point. On S-Approx-DPC's datasets (Section 5) these rules apply
+// to the picked points; every other point hangs on its pick. The paper propagates labels depth-first from the centers
 // (Section 2.2, step 4); the same forest is labelled here by pointer jumping:
 // every thread follows its parent chain to the root and stores the progress
 // back into its own parent slot, so chains through it shrink for the other
@@ -25,9 +26,16 @@ __global__ void k_parent(BatchView v) {
     if (valid) {
         b = find_ds(v.pt_off, v.B, g);
         const DsDesc& ds = v.desc[b];
-        const bool noise = (int64_t)v.rho[g] < ds.rho_min;
-        center = !noise && v.delta2[g] >= ds.delta_min2;
-        v.parent[g] = noise ? -1 : (center ? (int32_t)g : (int32_t)(ds.pt_off + v.dep[g]));
+        if (v.pick && !v.pick[g]) {
+            // S-Approx-DPC: a point that is not picked takes its pick's label
+            // (none when the pick is noise)
+            const int64_t k = ds.pt_off + v.dep[g];
+            v.parent[g] = (int64_t)v.rho[k] < ds.rho_min ? -1 : (int32_t)k;
+        } else {
+            const bool noise = (int64_t)v.rho[g] < ds.rho_min;
+            center = !noise && v.delta2[g] >= ds.delta_min2;
+            v.parent[g] = noise ? -1 : (center ? (int32_t)g : (int32_t)(ds.pt_off + v.dep[g]));
+        }
     }
     // count centers per dataset, aggregated over the lanes of one dataset
     const unsigned same = __match_any_sync(0xffffffffu, b);

@@ -59,6 +59,22 @@ inline int bits_for(uint64_t x) {  // smallest b with 2^b > x
     while (b < 64 && (x >> b) != 0) ++b;
     return b;
 }
+// S-Approx-DPC's grid side max(1, floor(eps d_cut / sqrt(d))), eps = num / den:
+// the largest s with (s den)^2 d <= (num d_cut)^2, in exact 128-bit integers.
+inline int64_t sapprox_side(int64_t d_cut, int32_t d, int64_t num, int64_t den) {
+    const unsigned __int128 rhs = (unsigned __int128)(num * d_cut) * (unsigned __int128)(num * d_cut);
+    auto fits = [&](int64_t s) {
+        const unsigned __int128 t = (unsigned __int128)s * (unsigned __int128)den;
+        return t * t * (unsigned)d <= rhs;
+    };
+    int64_t lo = 1, hi = num * d_cut / den + 1;  // fits(lo) or the side is 1; !fits(hi)
+    if (!fits(lo)) return 1;
+    while (hi - lo > 1) {
+        const int64_t mid = lo + (hi - lo) / 2;
+        (fits(mid) ? lo : hi) = mid;
+    }
+    return lo;
+}
 inline int ceil_log2(uint64_t x) {  // smallest b with 2^b >= x
     int b = 0;
     while ((1ull << b) < x) ++b;
@@ -229,7 +245,9 @@ struct Batch {
     DeltaBufs db{};
     DsDesc* d_desc = nullptr;
     bool has_density = false, has_rank = false;
-    int dep_kind = 0;  // dependent points held: 0 none, 1 exact, 2 Approx-DPC
+    int dep_kind = 0;  // dependent points held: 0 none, 1 exact, 2 Approx-DPC, 3 S-Approx-DPC
+    int64_t npicks = 0, nsecond = 0, sap_pairs = 0;  // S-Approx-DPC counters
+    int32_t* rho_pub = nullptr;  // S-Approx-DPC: rho as reported (-1 where not picked)
     uint32_t class_mask = 0, dim_mask = 0;
     int64_t ncells = 0, ndense = 0, nsparse = 0, nitems = 0, ntree = 0, nbf = 0;
     int64_t cand_pairs = 0;
@@ -243,7 +261,7 @@ struct Batch {
     int out_is_device = 0;
     float ms[6] = {0, 0, 0, 0, 0, 0};
     int refs = 0;
-    cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+    cudaEvent_t ev[8] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
     int64_t dense_pairs = 0;
     float ms_rho_dense = 0.f;
 
@@ -291,6 +309,42 @@ struct Batch {
 
     // ---------------------------------------------------------- density
     dpc_status density(const std::vector<Input>& in) {
+        DPC_TRY(build_grid(in));
+        DPC_TRY(rho_all());
+        unsigned long long pairs[2] = {0, 0}, ptst[4] = {0, 0, 0, 0};
+        DPC_CK(cudaMemcpyAsync(pairs, d_stats, sizeof(pairs), cudaMemcpyDeviceToHost, st));
+        if (pb.m > 0) DPC_CK(cudaMemcpyAsync(ptst, pb.stats, sizeof(ptst), cudaMemcpyDeviceToHost, st));
+        DPC_TRY(sync("density"));
+        cand_pairs = (int64_t)(pairs[0] + pairs[1] + ptst[1]);
+        dense_pairs = (int64_t)pairs[0];
+        DPC_TRY(check_err("density"));
+        ms[0] = elapsed(0, 1);
+        ms[1] = elapsed(1, 2);
+        ms_rho_dense = elapsed(1, 4);
+        dens.release();
+        has_density = true;
+        return DPC_OK;
+    }
+
+    // Local density of every point (sorted and original order).
+    dpc_status rho_all() {
+        DPC_CK(cudaMemsetAsync(v.rho_s, 0, sizeof(int32_t) * std::max<int64_t>(N, 1), st));
+        DPC_CK(cudaMemsetAsync(d_counters, 0, 64 * sizeof(uint32_t), st));
+        DPC_CK(launch_rho(v, w, class_mask, nitems, nsparse, d_counters, 1, st));
+        mark(4);
+        DPC_CK(launch_rho(v, w, class_mask, nitems, nsparse, d_counters, 2, st));
+        for (int d = 1; d <= kMaxDims; ++d)
+            DPC_CK(launch_rho_ptree(v, pb, d, pt_range[d][0], pt_range[d][1], st));
+        mark(2);
+        DPC_CK(launch_rho_scatter(v, st));
+        return DPC_OK;
+    }
+
+    // Uploads the inputs, plans the grid of every dataset, sorts the points
+    // by cell and builds the cells, their hash table, their neighbour runs and
+    // the dense work items. Leaves the temporaries in `dens` (v.in may live
+    // there) for the caller to release.
+    dpc_status build_grid(const std::vector<Input>& in) {
         if (!st) st = ctx->stream;
         tune = tune_for(ctx, in);
         keep.st = dens.st = st;
@@ -515,29 +569,6 @@ struct Batch {
         w.nbs = nbs;
         w.stats = d_stats;
         mark(1);
-
-        // local density
-        DPC_CK(cudaMemsetAsync(v.rho_s, 0, sizeof(int32_t) * std::max<int64_t>(N, 1), st));
-        DPC_CK(cudaMemsetAsync(d_counters, 0, 64 * sizeof(uint32_t), st));
-        DPC_CK(launch_rho(v, w, class_mask, nitems, nsparse, d_counters, 1, st));
-        mark(4);
-        DPC_CK(launch_rho(v, w, class_mask, nitems, nsparse, d_counters, 2, st));
-        for (int d = 1; d <= kMaxDims; ++d)
-            DPC_CK(launch_rho_ptree(v, pb, d, pt_range[d][0], pt_range[d][1], st));
-        mark(2);
-        DPC_CK(launch_rho_scatter(v, st));
-        unsigned long long pairs[2] = {0, 0}, ptst[4] = {0, 0, 0, 0};
-        DPC_CK(cudaMemcpyAsync(pairs, d_stats, sizeof(pairs), cudaMemcpyDeviceToHost, st));
-        if (pb.m > 0) DPC_CK(cudaMemcpyAsync(ptst, pb.stats, sizeof(ptst), cudaMemcpyDeviceToHost, st));
-        DPC_TRY(sync("density"));
-        cand_pairs = (int64_t)(pairs[0] + pairs[1] + ptst[1]);
-        dense_pairs = (int64_t)pairs[0];
-        DPC_TRY(check_err("density"));
-        ms[0] = elapsed(0, 1);
-        ms[1] = elapsed(1, 2);
-        ms_rho_dense = elapsed(1, 4);
-        dens.release();
-        has_density = true;
         return DPC_OK;
     }
 
@@ -784,7 +815,7 @@ struct Batch {
     }
 
     dpc_status dependent() {
-        if (dep_kind == 1) return DPC_OK;
+        if (dep_kind == 1 || dep_kind == 3) return DPC_OK;  // S-Approx-DPC keeps its own
         if (!has_density) return fail(DPC_ERR_STATE, "dataset has no density");
         mark(0);
         Arena tmp;
@@ -830,6 +861,7 @@ struct Batch {
     // base, and must fit 64 bits for the whole batch.
     dpc_status dependent_approx() {
         if (dep_kind == 2) return DPC_OK;
+        if (dep_kind == 3) return fail(DPC_ERR_STATE, "an S-Approx-DPC dataset has densities of its picks only");
         if (!has_density) return fail(DPC_ERR_STATE, "dataset has no density");
         unsigned __int128 abase = 0;
         for (int b = 0; b < B; ++b) {
@@ -905,6 +937,108 @@ struct Batch {
         ms[4] = elapsed(2, 3);
         tmp.release();
         dep_kind = 2;
+        return DPC_OK;
+    }
+
+    // ------------------------------------------------------ S-Approx-DPC
+    // S-Approx-DPC (Section 5): see sapprox.cu. Its grid G' covers all d
+    // dims like Approx-DPC's, with side max(1, floor(eps d_cut / sqrt(d))).
+    dpc_status sapprox(const std::vector<Input>& in, int64_t eps_num, int64_t eps_den) {
+        DPC_TRY(build_grid(in));
+        // key of G': every dim's cell coordinate at its own bit offset, the
+        // dataset's index above them (any width: sorted 64 bits at a time)
+        int bshift = 0;
+        for (int b = 0; b < B; ++b) {
+            DsDesc& ds = hd[b];
+            if (ds.ptree)
+                return fail(DPC_ERR_STATE, "S-Approx-DPC needs the grid: set tree_min_d above the dimension");
+            ds.a_side = (int32_t)std::min<int64_t>(sapprox_side(ds.d_cut, ds.d, eps_num, eps_den), 1ll << 30);
+            int off = 0;
+            for (int k = 0; k < kMaxDims; ++k) {
+                ds.a_shift[k] = off;
+                if (k < ds.d && ds.n > 0) off += bits_for((uint64_t)((ds.span[k] - 1) / ds.a_side));
+            }
+            bshift = std::max(bshift, off);
+        }
+        const int key_bits = bshift + bits_for((uint64_t)(B - 1));
+        DPC_TRY(upload_desc());
+        Arena tmp;
+        tmp.st = st;
+        SapproxBufs sb{};
+        void* temp = nullptr;
+        DPC_CK(tmp.get(&temp, std::max(radix_sort_temp_bytes(N), scan_temp_bytes(N))));
+        DPC_CK(tmp.get(&sb.keys, 3 * a256(N)));
+        DPC_CK(tmp.get(&sb.ord, 3 * a256(N)));
+        DPC_CK(tmp.get(&sb.flag, N));
+        DPC_CK(tmp.get(&sb.cidx, N));
+        DPC_CK(tmp.get(&sb.picks, N));
+        DPC_CK(tmp.get(&sb.pick_s, N));
+        DPC_CK(tmp.get(&sb.npicks, 1));
+        DPC_CK(tmp.get(&sb.scan, N));
+        DPC_CK(tmp.get(&sb.nscan, 1));
+        DPC_CK(tmp.get(&sb.stats, 2));
+        DPC_CK(keep.get(&v.pick, N));
+        DPC_CK(cudaMemsetAsync(sb.npicks, 0, sizeof(uint32_t), st));
+        DPC_CK(cudaMemsetAsync(sb.nscan, 0, sizeof(uint32_t), st));
+        DPC_CK(cudaMemsetAsync(sb.stats, 0, 2 * sizeof(unsigned long long), st));
+        DPC_CK(launch_sapprox_grid(v, sb, key_bits, bshift, temp, st));
+        uint32_t m = 0;
+        DPC_CK(cudaMemcpyAsync(&m, sb.npicks, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
+        DPC_TRY(sync("S-Approx-DPC grid"));
+        npicks = m;
+        mark(7);
+
+        // densities of the picks; the others get 0 and rank after every
+        // pick. With picks a quarter of the points or more, the dense
+        // all-point kernels cost less than a pass over the picks alone.
+        const bool all_points = 4 * npicks >= N;
+        if (all_points) {
+            DPC_TRY(rho_all());
+            DPC_CK(launch_sapprox_mask(v, st));
+        } else {
+            DPC_CK(cudaMemsetAsync(v.rho_s, 0, sizeof(int32_t) * std::max<int64_t>(N, 1), st));
+            DPC_CK(cudaMemsetAsync(v.rho, 0, sizeof(int32_t) * std::max<int64_t>(N, 1), st));
+            DPC_CK(cudaMemsetAsync(d_counters, 0, 64 * sizeof(uint32_t), st));
+            DPC_CK(launch_sapprox_rho(v, w, sb, dim_mask, npicks, st));
+            mark(2);
+        }
+        DPC_TRY(ensure_rank(tmp, temp));
+        mark(5);
+
+        // nearest higher pick of every point's searched block (the exact
+        // ring search over pick ranks), the first phase, then the second
+        // phase for the picks it leaves open
+        DPC_CK(tmp.get(&v.best_s, N));
+        DPC_CK(cudaMemsetAsync(v.best_s, 0xff, sizeof(unsigned long long) * std::max<int64_t>(N, 1), st));
+        DPC_CK(launch_ring(v, w, class_mask, nitems, nsparse, d_counters + 32, st));
+        DPC_CK(tmp.get(&db.ucount, 4));
+        DPC_CK(tmp.get(&db.tree_list, N));
+        DPC_CK(tmp.get(&db.bf_list, N));
+        DPC_CK(cudaMemsetAsync(db.ucount, 0, 4 * sizeof(uint32_t), st));
+        db.tcount = db.ucount;
+        db.bf_rank = tune.bf_rank;
+        DPC_CK(launch_sapprox_first(v, w, sb, db, dim_mask, npicks, npicks, st));
+        DPC_TRY(open_points(tmp, "S-Approx-DPC first phase", false));
+        mark(6);
+        DPC_CK(keep.get(&rho_pub, N));
+        DPC_CK(launch_sapprox_rho_out(v, rho_pub, st));
+        unsigned long long sst[2] = {0, 0}, pairs[2] = {0, 0};
+        DPC_CK(cudaMemcpyAsync(sst, sb.stats, sizeof(sst), cudaMemcpyDeviceToHost, st));
+        DPC_CK(cudaMemcpyAsync(pairs, d_stats, sizeof(pairs), cudaMemcpyDeviceToHost, st));
+        DPC_TRY(finish_stats("S-Approx-DPC dependent points"));
+        sap_pairs = (int64_t)sst[0];
+        nsecond = (int64_t)sst[1];
+        cand_pairs = all_points ? (int64_t)(pairs[0] + pairs[1]) : sap_pairs;
+        dense_pairs = all_points ? (int64_t)pairs[0] : 0;
+        ms_rho_dense = all_points ? elapsed(7, 4) : 0.f;
+        ms[0] = elapsed(0, 7);
+        ms[1] = elapsed(7, 2);
+        ms[2] = elapsed(2, 5);
+        ms[3] = elapsed(5, 6);
+        tmp.release();
+        dens.release();
+        has_density = true;
+        dep_kind = 3;
         return DPC_OK;
     }
 
@@ -1071,6 +1205,33 @@ dpc_status dpc_density(dpc_ctx* ctx, const int32_t* points, int64_t n, int32_t d
     return DPC_OK;
 }
 
+dpc_status dpc_sapprox(dpc_ctx* ctx, const int32_t* points, int64_t n, int32_t d, int64_t d_cut, int64_t eps_num,
+                       int64_t eps_den, int is_device, dpc_ds** out, int32_t* rho_out, int32_t* dep_out,
+                       int64_t* delta2_out, uint8_t* pick_out) {
+    if (!ctx || !out) return fail(DPC_ERR_INVALID_ARG, "ctx or out is NULL");
+    *out = nullptr;
+    DPC_TRY(check_input(points, n, d, d_cut));
+    if (eps_num < 1 || eps_num > (1 << 20) || eps_den < 1 || eps_den > (1 << 20))
+        return fail(DPC_ERR_INVALID_ARG, "eps_num and eps_den must be in [1, 2^20]");
+    cudaError_t e = cudaSetDevice(ctx->device);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaSetDevice");
+    auto b = std::make_shared<Batch>();
+    b->ctx = ctx;
+    std::vector<dpc::Input> in{{points, n, d, d_cut, is_device}};
+    DPC_TRY(b->sapprox(in, eps_num, eps_den));
+    DPC_TRY(b->copy_out(rho_out, b->rho_pub, sizeof(int32_t) * n));
+    DPC_TRY(b->copy_out(dep_out, b->v.dep, sizeof(int32_t) * n));
+    DPC_TRY(b->copy_out(delta2_out, b->v.delta2, sizeof(int64_t) * n));
+    DPC_TRY(b->copy_out(pick_out, b->v.pick, sizeof(uint8_t) * n));
+    DPC_TRY(b->sync("copy S-Approx-DPC results"));
+    auto* ds = new dpc_ds();
+    ds->batch = b;
+    ds->b = 0;
+    b->refs = 1;
+    *out = ds;
+    return DPC_OK;
+}
+
 dpc_status dpc_dependent(dpc_ds* ds, int32_t* dep_out, int64_t* delta2_out) {
     if (!ds || !ds->batch) return fail(DPC_ERR_STATE, "invalid dataset handle");
     Batch& bt = *ds->batch;
@@ -1147,6 +1308,8 @@ static void fill_info(const Batch& bt, int b, dpc_info* out) {
     out->pair_mode = h.mode;
     out->dense_pairs = bt.dense_pairs;
     out->ms_rho_dense = bt.ms_rho_dense;
+    out->picks = bt.npicks;
+    out->second_phase = bt.nsecond;
 }
 
 dpc_status dpc_ds_info(const dpc_ds* ds, dpc_info* out) {

@@ -330,6 +330,33 @@ cudaError_t launch_approx_cells(const BatchView& v, const CellWork& w, const App
 cudaError_t launch_approx_rules(const BatchView& v, const CellWork& w, const ApproxBufs& ab, const DeltaBufs& db,
                                 uint32_t dim_mask, int64_t ncells_bound, cudaStream_t st);
 
+// sapprox.cu: S-Approx-DPC (Section 5). Keys, orders and flags are over the
+// cells of the finer grid G' (side max(1, floor(eps d_cut / sqrt(d)))).
+struct SapproxBufs {
+    uint64_t* keys;       // [3N] one 64-bit word of the key of G' per pass; sort input, output, scratch
+    uint32_t* ord;        // [3N] original global indices in key order (three rotating buffers)
+    uint32_t* flag;       // [N] first point of a cell of G' in key order
+    uint32_t* cidx;       // [N] exclusive scan of flag
+    uint32_t* picks;      // [N] sorted position of the pick of every cell of G'
+    uint32_t* pick_s;     // [N] sorted position -> sorted position of its cell's pick
+    uint32_t* npicks;     // device scalar: cells of G'
+    uint32_t* scan;       // [N] picks that scan their neighbourhood for the first phase
+    uint32_t* nscan;      // device scalar: their count
+    unsigned long long* stats;  // [2] pairs the pick-only density pass evaluates; picks reaching the second phase
+};
+// key_bits: width of the key of G'; bshift: bit offset of the dataset index
+cudaError_t launch_sapprox_grid(const BatchView& v, const SapproxBufs& sb, int key_bits, int bshift, void* temp,
+                                cudaStream_t st);
+cudaError_t launch_sapprox_rho(const BatchView& v, const CellWork& w, const SapproxBufs& sb, uint32_t dim_mask,
+                               int64_t picks_bound, cudaStream_t st);
+// rho 0 for the points that are not picked (they rank after every pick)
+cudaError_t launch_sapprox_mask(const BatchView& v, cudaStream_t st);
+// after the rank and the ring search: the points that are not picked, then
+// the picks (resolved from the ring result or queued), then the first-phase scan
+cudaError_t launch_sapprox_first(const BatchView& v, const CellWork& w, const SapproxBufs& sb, const DeltaBufs& db,
+                                 uint32_t dim_mask, int64_t picks_bound, int64_t scan_bound, cudaStream_t st);
+cudaError_t launch_sapprox_rho_out(const BatchView& v, int32_t* out, cudaStream_t st);
+
 // label.cu
 cudaError_t launch_labels(const BatchView& v, cudaStream_t st);
 

@@ -57,3 +57,27 @@ def test_binding_has_no_cpu_path():
         if f.endswith(".py"):
             src = open(os.path.join(pkg, f)).read()
             assert "oracle" not in src, f
+
+
+def test_sapprox_argument_checks_without_a_device():
+    import paper_2207_04649_gb300 as dpc
+    L = dpc.lib()
+    h = ctypes.c_void_p()
+    pts = np.zeros((4, 2), np.int32)
+    p = pts.ctypes.data_as(ctypes.c_void_p)
+    assert L.dpc_sapprox(None, p, 4, 2, 10, 1, 1, 0, ctypes.byref(h), None, None, None, None) == dpc.DPC_ERR_INVALID_ARG
+    assert L.dpc_sapprox(ctypes.c_void_p(1), p, 4, 2, 10, 0, 1, 0, ctypes.byref(h), None, None, None, None) \
+        == dpc.DPC_ERR_INVALID_ARG
+    assert L.dpc_sapprox(ctypes.c_void_p(1), p, 4, 2, 10, 1, (1 << 20) + 1, 0, ctypes.byref(h), None, None, None,
+                         None) == dpc.DPC_ERR_INVALID_ARG
+    assert "eps" in dpc.dpc_last_error()
+
+
+def test_eps_fraction():
+    import paper_2207_04649_gb300 as dpc
+    assert dpc.eps_fraction(0.8) == (4, 5)
+    assert dpc.eps_fraction(1.0) == (1, 1)
+    assert dpc.eps_fraction((3, 7)) == (3, 7)
+    assert dpc.eps_fraction(0.000001) == (1, 1000000)
+    with pytest.raises(ValueError):
+        dpc.eps_fraction(0.0)
