@@ -34,8 +34,11 @@ METRIC = "exact DPC points/s (rho+delta+labels) at 5.8M x 3"
 APPROX_METRIC = "Approx-DPC points/s (rho+approximate delta+labels) at 5.8M x 3"
 
 
+SAPPROX_METRIC = "S-Approx-DPC points/s (rho of picks+approximate delta+labels) at 5.8M x 3"
+
+
 def metric_for(args) -> str:
-    return APPROX_METRIC if args.method == "approx" else METRIC
+    return {"approx": APPROX_METRIC, "sapprox": SAPPROX_METRIC}.get(args.method, METRIC)
 UNIT = "points/s"
 
 
@@ -46,11 +49,25 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="plain_5p8m_3d")
-    ap.add_argument("--method", choices=["exact", "approx"], default="exact",
-                    help="exact DPC, or Approx-DPC's dependent points (Section 4.3)")
+    ap.add_argument("--method", choices=["exact", "approx", "sapprox"], default="exact",
+                    help="exact DPC, Approx-DPC's dependent points (Section 4.3) or S-Approx-DPC (Section 5)")
+    ap.add_argument("--eps", default="0.8", help="S-Approx-DPC's eps (a decimal, or num/den)")
+    ap.add_argument("--eps-sweep", default="",
+                    help="S-Approx-DPC: comma-separated eps values for a time / Rand-index curve")
     ap.add_argument("--cpu-sample", type=int, default=0, help="oracle sample size (0: automatic)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     return ap.parse_args()
+
+
+def parse_eps(text: str):
+    """S-Approx-DPC's eps as (num, den): "num/den", or a decimal to 10^-6."""
+    import math
+    if "/" in text:
+        a, b = text.split("/")
+        return int(a), int(b)
+    num, den = int(round(float(text) * 10 ** 6)), 10 ** 6
+    g = math.gcd(num, den)
+    return num // g, den // g
 
 
 def dist_env():
@@ -136,11 +153,12 @@ class ClockSampler:
 
 # ------------------------------------------------------------- oracle leg
 
-def oracle_sample_rate(ds, m: int, seed: int = 7, method: str = "exact"):
+def oracle_sample_rate(ds, m: int, seed: int = 7, method: str = "exact", eps=(4, 5)):
     """The oracle, as it stands, on m sampled points of the workload: their
     local density against all n points, then their dependent point (exact:
     a scan of all n points; approx: Approx-DPC's rules, which scan all n
-    points for a cell's top). Only the time is used. The density order is
+    points for a cell's top; sapprox: S-Approx-DPC's grid of all n points
+    and both phases, which scan all n points). Only the time is used. The density order is
     the index order here (the full density array would need the whole
     O(n^2) oracle run); on a uniform sample the exact scan touches the same
     number of higher points on average (half of them)."""
@@ -152,6 +170,8 @@ def oracle_sample_rate(ds, m: int, seed: int = 7, method: str = "exact"):
     oracle.rho_subset(ds.points, ds.d_cut, idx)
     if method == "approx":
         oracle.approx_dependent_subset(ds.points, flat, ds.d_cut, idx)
+    elif method == "sapprox":
+        oracle.sapprox_dependent_subset(ds.points, flat, ds.d_cut, eps[0], eps[1], idx)
     else:
         oracle.dependent_subset(ds.points, flat, idx)
     dt = time.perf_counter() - t0
@@ -233,13 +253,19 @@ def run_ours(args):
     st = ctx.stream
 
     approx = args.method == "approx"
+    sapprox = args.method == "sapprox"
+    eps = parse_eps(args.eps)
+    pick = torch.empty(n, dtype=torch.uint8, device=dev)
 
     def step():
-        h = ctx.density(pts, ds.d_cut, rho)
-        if approx:
-            h.dependent_approx(dep, d2)
+        if sapprox:
+            h = ctx.sapprox(pts, ds.d_cut, eps, rho, dep, d2, pick)
         else:
-            h.dependent(dep, d2)
+            h = ctx.density(pts, ds.d_cut, rho)
+            if approx:
+                h.dependent_approx(dep, d2)
+            else:
+                h.dependent(dep, d2)
         nc = h.label(ds.rho_min, ds.delta_min, lab)
         info = h.info()
         h.release()
@@ -288,15 +314,19 @@ def run_ours(args):
     h_dep = torch.empty(n, dtype=torch.int32).pin_memory().numpy()
     h_d2 = torch.empty(n, dtype=torch.int64).pin_memory().numpy()
     h_lab = torch.empty(n, dtype=torch.int32).pin_memory().numpy()
+    h_pick = torch.empty(n, dtype=torch.uint8).pin_memory().numpy()
     e2e_s = []
     for i in range(args.warmup + args.steps):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        h = ctx.density(h_pts, ds.d_cut, h_rho)
-        if approx:
-            h.dependent_approx(h_dep, h_d2)
+        if sapprox:
+            h = ctx.sapprox(h_pts, ds.d_cut, eps, h_rho, h_dep, h_d2, h_pick)
         else:
-            h.dependent(h_dep, h_d2)
+            h = ctx.density(h_pts, ds.d_cut, h_rho)
+            if approx:
+                h.dependent_approx(h_dep, h_d2)
+            else:
+                h.dependent(h_dep, h_d2)
         h.label(ds.rho_min, ds.delta_min, h_lab)
         h.release()
         t1 = time.perf_counter()
@@ -311,13 +341,13 @@ def run_ours(args):
     dense_ms = statistics.mean(i["ms_rho_dense"] for i in infos)
     pairs = infos[-1]["cand_pairs"]
     dpairs = infos[-1]["dense_pairs"]
-    achieved = pairs / (rho_ms / 1e3)
-    dachieved = dpairs / (dense_ms / 1e3)
+    achieved = pairs / (rho_ms / 1e3) if rho_ms > 0 else 0.0
+    dachieved = dpairs / (dense_ms / 1e3) if dense_ms > 0 else 0.0
     traffic = rho_traffic(args.workload)
     dtraffic = rho_traffic(args.workload, "dram_bytes_per_launch_dense")
 
     accuracy = None
-    if approx:
+    if approx or sapprox:
         # Rand index of the Approx-DPC labels against the exact labels of the
         # same set (the paper's accuracy measure, Section 5), and the center
         # guarantee of Section 4.4
@@ -331,14 +361,24 @@ def run_ours(args):
         a_np, e_np = lab.cpu().numpy(), elab.cpu().numpy()
         idx = np.arange(n)
         accuracy = {"rand_index_vs_exact": evaluate.rand_index(a_np, e_np),
-                    "same_centers": bool(np.array_equal(a_np == idx, e_np == idx)),
-                    "tops_to_exact_search": int(infos[-1]["open_after_ring"])}
+                    "same_centers": bool(np.array_equal(a_np == idx, e_np == idx))}
+        if approx:
+            accuracy["tops_to_exact_search"] = int(infos[-1]["open_after_ring"])
+        else:
+            accuracy.update({"eps": list(eps), "picks": int(infos[-1]["picks"]),
+                             "second_phase": int(infos[-1]["second_phase"]),
+                             "to_tree_or_brute_force": int(infos[-1]["open_after_ring"])})
+
+    eps_curve = None
+    if sapprox and args.eps_sweep:
+        eps_curve = sapprox_eps_curve(ctx, pts, ds, [parse_eps(t) for t in args.eps_sweep.split(",")],
+                                      lab, elab, flush)
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         import oracle
         m = args.cpu_sample or auto_sample(ds)
-        rate, dt = oracle_sample_rate(ds, m, method=args.method)
+        rate, dt = oracle_sample_rate(ds, m, method=args.method, eps=eps)
         cpu = {"value": rate, "unit": UNIT, "cores": oracle.threads(), "kind": "oracle",
                "sample": f"{m} random points of the {n}-point set: rho against all n points and the "
                          f"{args.method} dependent-point step over all n points ({dt:.1f} s)"}
@@ -351,12 +391,14 @@ def run_ours(args):
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "int32",
             "data": "synthetic (seeded Gaussian-blob mixture, int32 coordinates)",
-            "config": {"workload": args.workload, "method": args.method, "n": n, "d": d, "d_cut": ds.d_cut, "rho_min": ds.rho_min,
+            "config": {"workload": args.workload, "method": args.method,
+                       **({"eps": f"{eps[0]}/{eps[1]}"} if sapprox else {}),
+                       "n": n, "d": d, "d_cut": ds.d_cut, "rho_min": ds.rho_min,
                        "delta_min": ds.delta_min, "parallelism": f"replicas x{ws}",
                        "l2": "flushed between steps (256 MB write)",
                        "mean_rho": float(rho.double().mean().item()), "n_centers": int(nc)},
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": n * d * 4,
-                    "d2h_bytes_per_step": n * (4 + 4 + 8 + 4) + 8},
+                    "d2h_bytes_per_step": n * (4 + 4 + 8 + 4 + (1 if sapprox else 0)) + 8},
             "roofline": {"bound": "alu", "kernel": f"k_rho_dense (dense cells, pair form {pair_mode})",
                          "achieved": dachieved / 1e9, "peak": probe_rate / 1e9, "unit": "Gpair/s",
                          "frac": dachieved / probe_rate, "traffic": dtraffic,
@@ -380,10 +422,59 @@ def run_ours(args):
         }
         if accuracy is not None:
             line["accuracy"] = accuracy
+        if eps_curve is not None:
+            line["eps_curve"] = eps_curve
         print(json.dumps(line), flush=True)
     ctx.close()
     if dist:
         dist.destroy_process_group()
+
+
+def sapprox_eps_curve(ctx, pts, ds, eps_list, lab, elab, flush, reps: int = 3):
+    """Time (device-resident, L2 flushed, mean of reps after one warm-up) and
+    Rand index against the exact labels of S-Approx-DPC for every eps (the
+    paper's Table 5 on this workload), plus the exact path's own time."""
+    import torch
+    from paper_2207_04649_gb300 import evaluate
+    st = ctx.stream
+    e_np = elab.cpu().numpy()
+
+    def timed(run):
+        run()
+        ms = []
+        for _ in range(reps):
+            with torch.cuda.stream(st):
+                flush.fill_(1)
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(st)
+            out = run()
+            b.record(st)
+            torch.cuda.synchronize()
+            ms.append(a.elapsed_time(b))
+        return statistics.mean(ms), out
+
+    def exact():
+        h = ctx.density(pts, ds.d_cut)
+        nc = h.label(ds.rho_min, ds.delta_min)
+        h.release()
+        return nc
+
+    ex_ms, ex_nc = timed(exact)
+    curve = [{"eps": "exact", "ms": ex_ms, "n_centers": ex_nc, "rand_index": 1.0}]
+    for eps in eps_list:
+        def run():
+            h = ctx.sapprox(pts, ds.d_cut, eps)
+            nc = h.label(ds.rho_min, ds.delta_min, lab)
+            info = h.info()
+            h.release()
+            return nc, info
+        ms, (nc, info) = timed(run)
+        a_np = lab.cpu().numpy()
+        curve.append({"eps": f"{eps[0]}/{eps[1]}", "ms": ms, "n_centers": nc, "picks": int(info["picks"]),
+                      "second_phase": int(info["second_phase"]),
+                      "rand_index": evaluate.rand_index(a_np, e_np)})
+    return curve
 
 
 # ----------------------------------------------------------- reference arm
@@ -396,11 +487,12 @@ def run_reference(args):
     import workloads
     ds = workloads.NAMED[args.workload]()
     m = args.cpu_sample or max(100, auto_sample(ds) // 4)
+    eps = parse_eps(args.eps)
     for _ in range(args.warmup):
-        oracle_sample_rate(ds, max(20, m // 10), method=args.method)
+        oracle_sample_rate(ds, max(20, m // 10), method=args.method, eps=eps)
     times = []
     for i in range(args.steps):
-        _, dt = oracle_sample_rate(ds, m, seed=100 + i, method=args.method)
+        _, dt = oracle_sample_rate(ds, m, seed=100 + i, method=args.method, eps=eps)
         times.append(dt)
     total = sum(times)
     value = m * len(times) / total

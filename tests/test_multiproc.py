@@ -69,3 +69,23 @@ def test_reference_arm_under_torchrun():
     assert line["impl"] == "reference" and line["n_gpus"] == 2
     assert line["cpu_baseline"]["kind"] == "oracle" and line["value"] > 0
     assert line["e2e"]["h2d_bytes_per_step"] == 0
+
+
+@pytest.mark.parametrize("method", ["approx", "sapprox"])
+def test_reference_arm_approximate_methods(method):
+    cmd = [sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--workload", "plain_20k_2d",
+           "--method", method, "--eps", "3/5", "--steps", "1", "--warmup", "1", "--cpu-sample", "30"]
+    r = subprocess.run(cmd, cwd=ROOT, capture_output=True, text=True, timeout=300)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [ln for ln in r.stdout.splitlines() if ln.startswith("{")]
+    line = json.loads(lines[-1])
+    assert line["impl"] == "reference" and line["config"]["method"] == method and line["value"] > 0
+    assert line["metric"].startswith("S-Approx-DPC" if method == "sapprox" else "Approx-DPC")
+
+
+def test_parse_eps():
+    sys.path.insert(0, ROOT)
+    import bench
+    assert bench.parse_eps("0.8") == (4, 5)
+    assert bench.parse_eps("3/7") == (3, 7)
+    assert bench.parse_eps("1") == (1, 1)
