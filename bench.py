@@ -279,7 +279,7 @@ def run_ours(args):
     # integer-ALU ceiling of the pair test in the form the kernel runs (before
     # anything is timed)
     pair_mode = winfo["pair_mode"] if winfo else 0
-    probe_rate, _ = dpc.dpc_probe_pair_rate(local, d, 2 if pair_mode == 2 else 0)
+    probe_rate, _ = dpc.dpc_probe_pair_rate(local, d, pair_mode)
 
     clocks = ClockSampler(local)
     clocks.start()
@@ -406,9 +406,9 @@ def run_ours(args):
                          "density_stage": {"kernels": "k_rho_dense + k_rho_sparse", "achieved": achieved / 1e9,
                                            "frac": achieved / probe_rate, "traffic": traffic,
                                            "pairs_per_step": pairs, "ms_per_step": rho_ms},
-                         "peak_source": "measured: the kernel's own 32-bit pair test (form "
-                                        f"{pair_mode}) with operands in registers on all SMs "
-                                        "(dpc_probe_pair_rate), same run",
+                         "peak_source": "measured: the kernel's own pair test (form "
+                                        f"{pair_mode}, {'64' if pair_mode == 1 else '32'}-bit) with operands "
+                                        "in registers on all SMs (dpc_probe_pair_rate), same run",
                          "pair_mode": pair_mode,
                          "peak_derived": derived_pair_peak(d, pair_mode, clk.get("sm_mhz"))},
             "stages_ms": {k: statistics.mean(i[k] for i in infos)

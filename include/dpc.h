@@ -244,6 +244,11 @@ dpc_status dpc_set_profiling(dpc_ctx* ctx, int on);
  *             distance 2 before the tree search, 0: straight to the tree
  *             (default 0: on 5.8M x 3 it resolves 56% of them but costs more
  *             than the tree search it saves)
+ *   "sparse_cand"  a cell of at most 4 points takes one thread (the sparse
+ *             kernels) only if it has at most this many candidates, else one
+ *             warp per work item like the larger cells, 0 .. 2^31 (default
+ *             512; high-dimensional sets have small cells facing thousands of
+ *             candidates)
  *   "max_batch_jobs"  served mode: jobs one batch admits at most, 1 .. 4096
  *             (default 64; 1 runs the jobs one at a time)
  * DPC_ERR_INVALID_ARG for an unknown key or a value out of range. */
@@ -256,11 +261,12 @@ dpc_status dpc_get_tuning(dpc_ctx* ctx, const char* key, int64_t* value);
 int64_t dpc_kernel_launches(void);
 
 /* Measurement helper (no counterpart in the paper): the throughput of the
- * density stage's 32-bit pair test for d-dimensional points with operands in
+ * density stage's pair test for d-dimensional points with operands in
  * registers on every SM of `device`, i.e. the integer-ALU ceiling that the
- * density kernel is compared against. mode 0: the direct form (sum of
- * squared differences); mode 2: the expanded form around a cell corner
- * (d <= 3), the one dpc_ds_info reports as pair_mode 2. Writes pairs per
+ * density kernel is compared against, in the form dpc_ds_info reports as
+ * pair_mode: 0 the direct 32-bit form (sum of squared differences), 1 the
+ * direct 64-bit form, 2 the expanded 32-bit form around a cell corner
+ * (d <= 3). Other modes give DPC_ERR_INVALID_ARG. Writes pairs per
  * second (and the kernel's time in ms when ms is not NULL). Allocates and
  * frees a few bytes of device memory; synchronizes the device. */
 dpc_status dpc_probe_pair_rate(int device, int d, int mode, double* pairs_per_s, double* ms);

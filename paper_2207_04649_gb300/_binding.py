@@ -122,8 +122,8 @@ def dpc_kernel_launches() -> int:
 
 
 def dpc_probe_pair_rate(device: int, d: int, mode: int = 0):
-    """(pairs/s, ms) of the register-resident 32-bit pair test on every SM
-    (mode 0 direct form, mode 2 expanded form for d <= 3)."""
+    """(pairs/s, ms) of the register-resident pair test on every SM (mode 0
+    direct 32-bit form, 1 direct 64-bit form, 2 expanded form for d <= 3)."""
     r, t = ctypes.c_double(0), ctypes.c_double(0)
     _check(lib().dpc_probe_pair_rate(device, d, mode, ctypes.byref(r), ctypes.byref(t)), "dpc_probe_pair_rate")
     return r.value, t.value

@@ -1,9 +1,10 @@
 // Throughput probe for the density stage's pair test.
 //
 // Every thread keeps 4 queries and 16 candidates in registers and applies the
-// density kernel's 32-bit pair test to all 64 pairs per sweep, on every SM,
-// in one of the kernel's two forms:
-//   direct   (mode 0): sign of sum_k (q_k - c_k)^2 - d_cut^2;
+// density kernel's pair test to all 64 pairs per sweep, on every SM, in one
+// of the kernel's three forms:
+//   direct   (mode 0): sign of sum_k (q_k - c_k)^2 - d_cut^2 in 32 bits;
+//   direct   (mode 1): sum_k (q_k - c_k)^2 < d_cut^2 in 64 bits;
 //   expanded (mode 2, d <= 3): sign of |c'|^2 + (|q'|^2 - d_cut^2) + sum_k c'_k (-2 q'_k).
 // After each sweep every query operand moves by an amount that depends on
 // the counts, so no part of a pair test can be hoisted out of the loop (this
@@ -16,7 +17,7 @@
 namespace dpc {
 namespace {
 
-template <int D>
+template <int D, bool W64>
 __global__ void __launch_bounds__(256) k_pair_probe(const int32_t* __restrict__ seed, int iters, int T,
                                                    unsigned long long* __restrict__ sink) {
     int32_t q[4][D], c[16][D];
@@ -35,13 +36,23 @@ __global__ void __launch_bounds__(256) k_pair_probe(const int32_t* __restrict__ 
         for (int j = 0; j < 16; ++j)
 #pragma unroll
             for (int i = 0; i < 4; ++i) {
-                int s = -T;
+                if (W64) {
+                    long long s = 0;
 #pragma unroll
-                for (int k = 0; k < D; ++k) {
-                    const int dd = q[i][k] - c[j][k];
-                    s += dd * dd;
+                    for (int k = 0; k < D; ++k) {
+                        const int dd = q[i][k] - c[j][k];
+                        s += (long long)dd * dd;
+                    }
+                    cnt[i] += s < (long long)T ? 1u : 0u;
+                } else {
+                    int s = -T;
+#pragma unroll
+                    for (int k = 0; k < D; ++k) {
+                        const int dd = q[i][k] - c[j][k];
+                        s += dd * dd;
+                    }
+                    cnt[i] += (uint32_t)s >> 31;
                 }
-                cnt[i] += (uint32_t)s >> 31;
             }
 #pragma unroll
         for (int i = 0; i < 4; ++i)
@@ -103,7 +114,7 @@ __global__ void __launch_bounds__(256) k_pair_probe_x(const int32_t* __restrict_
 
 extern "C" dpc_status dpc_probe_pair_rate(int device, int d, int mode, double* pairs_per_s, double* ms) {
     using namespace dpc;
-    if (!pairs_per_s || d < 1 || d > 8 || (mode != 0 && mode != 2) || (mode == 2 && d > 3))
+    if (!pairs_per_s || d < 1 || d > 8 || mode < 0 || mode > 2 || (mode == 2 && d > 3))
         return DPC_ERR_INVALID_ARG;
     if (cudaSetDevice(device) != cudaSuccess) return DPC_ERR_CUDA;
     int sms = 0;
@@ -129,16 +140,27 @@ extern "C" dpc_status dpc_probe_pair_rate(int device, int d, int mode, double* p
                 case 2: k_pair_probe_x<2><<<blocks, threads>>>(seed, it, 90000, sink); break;
                 default: k_pair_probe_x<3><<<blocks, threads>>>(seed, it, 90000, sink); break;
             }
+        } else if (mode == 1) {
+            switch (d) {
+                case 1: k_pair_probe<1, true><<<blocks, threads>>>(seed, it, 90000, sink); break;
+                case 2: k_pair_probe<2, true><<<blocks, threads>>>(seed, it, 90000, sink); break;
+                case 3: k_pair_probe<3, true><<<blocks, threads>>>(seed, it, 90000, sink); break;
+                case 4: k_pair_probe<4, true><<<blocks, threads>>>(seed, it, 90000, sink); break;
+                case 5: k_pair_probe<5, true><<<blocks, threads>>>(seed, it, 90000, sink); break;
+                case 6: k_pair_probe<6, true><<<blocks, threads>>>(seed, it, 90000, sink); break;
+                case 7: k_pair_probe<7, true><<<blocks, threads>>>(seed, it, 90000, sink); break;
+                default: k_pair_probe<8, true><<<blocks, threads>>>(seed, it, 90000, sink); break;
+            }
         } else {
             switch (d) {
-                case 1: k_pair_probe<1><<<blocks, threads>>>(seed, it, 90000, sink); break;
-                case 2: k_pair_probe<2><<<blocks, threads>>>(seed, it, 90000, sink); break;
-                case 3: k_pair_probe<3><<<blocks, threads>>>(seed, it, 90000, sink); break;
-                case 4: k_pair_probe<4><<<blocks, threads>>>(seed, it, 90000, sink); break;
-                case 5: k_pair_probe<5><<<blocks, threads>>>(seed, it, 90000, sink); break;
-                case 6: k_pair_probe<6><<<blocks, threads>>>(seed, it, 90000, sink); break;
-                case 7: k_pair_probe<7><<<blocks, threads>>>(seed, it, 90000, sink); break;
-                default: k_pair_probe<8><<<blocks, threads>>>(seed, it, 90000, sink); break;
+                case 1: k_pair_probe<1, false><<<blocks, threads>>>(seed, it, 90000, sink); break;
+                case 2: k_pair_probe<2, false><<<blocks, threads>>>(seed, it, 90000, sink); break;
+                case 3: k_pair_probe<3, false><<<blocks, threads>>>(seed, it, 90000, sink); break;
+                case 4: k_pair_probe<4, false><<<blocks, threads>>>(seed, it, 90000, sink); break;
+                case 5: k_pair_probe<5, false><<<blocks, threads>>>(seed, it, 90000, sink); break;
+                case 6: k_pair_probe<6, false><<<blocks, threads>>>(seed, it, 90000, sink); break;
+                case 7: k_pair_probe<7, false><<<blocks, threads>>>(seed, it, 90000, sink); break;
+                default: k_pair_probe<8, false><<<blocks, threads>>>(seed, it, 90000, sink); break;
             }
         }
         note_launch();

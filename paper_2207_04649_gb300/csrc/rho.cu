@@ -36,20 +36,35 @@ namespace {
 
 constexpr int kRhoThreads = 128;  // 4 warps per block, double-buffered chunks each
 
-__global__ void k_classify(BatchView v, uint32_t* __restrict__ dflag, uint32_t* __restrict__ sflag, int64_t bound) {
+// A cell is dense (one warp per work item) when it holds more than
+// kSparseMax points or has more than sparse_cand candidates (a few points
+// facing many candidates, as in high dimensions, would leave one thread
+// walking them all); the others take one thread each. Counts the candidate
+// pairs of both classes.
+__global__ void k_classify(BatchView v, CellPrepBufs cb, int64_t bound, uint32_t sparse_cand) {
     const uint32_t nc = *v.ncells;
+    unsigned long long pairs = 0, spairs = 0;
     for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < bound; c += (int64_t)gridDim.x * blockDim.x) {
         uint32_t dense = 0, sparse = 0;
         if (c < nc) {
             const uint32_t cs = v.cell_start[c], m = v.cell_start[c + 1] - cs;
             if (!v.desc[find_ds(v.pt_off, v.B, cs)].ptree) {  // point-tree datasets have no grid work
-                dense = m > (uint32_t)kSparseMax;
+                const uint32_t cand = cb.cand[c];
+                dense = m > (uint32_t)kSparseMax || cand > sparse_cand;
                 sparse = !dense;
+                if (dense) pairs += (unsigned long long)m * cand;
+                else spairs += (unsigned long long)m * cand;
             }
         }
-        dflag[c] = dense;
-        sflag[c] = sparse;
+        cb.dflag[c] = dense;
+        cb.sflag[c] = sparse;
     }
+    for (int o = 16; o > 0; o >>= 1) {
+        pairs += __shfl_xor_sync(0xffffffffu, pairs, o);
+        spairs += __shfl_xor_sync(0xffffffffu, spairs, o);
+    }
+    if ((threadIdx.x & 31) == 0 && pairs) atomicAdd(&cb.stats[0], pairs);
+    if ((threadIdx.x & 31) == 0 && spairs) atomicAdd(&cb.stats[1], spairs);
 }
 
 __global__ void k_compact_cells(BatchView v, CellPrepBufs cb, int64_t bound) {
@@ -79,9 +94,8 @@ __device__ __forceinline__ uint2 resolve_probe(const BatchView& v, uint64_t key,
 template <int K>
 __global__ void __launch_bounds__(256) k_cell_runs(BatchView v, CellPrepBufs cb, int64_t ncells) {
     constexpr int NNB = K == 1 ? 3 : (K == 2 ? 9 : (K == 3 ? 27 : 81));
-    unsigned long long pairs = 0, spairs = 0;  // dense cells', sparse cells' candidate pairs
     for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < ncells; c += (int64_t)gridDim.x * blockDim.x) {
-        const uint32_t cs = v.cell_start[c], m = v.cell_start[c + 1] - cs;
+        const uint32_t cs = v.cell_start[c];
         const int b = find_ds(v.pt_off, v.B, cs);
         const DsDesc& ds = v.desc[b];
         if (ds.k != K || ds.R != 1) continue;
@@ -133,22 +147,13 @@ __global__ void __launch_bounds__(256) k_cell_runs(BatchView v, CellPrepBufs cb,
         }
         cb.nruns[c] = nr;
         cb.cand[c] = cand;
-        if (m > (uint32_t)kSparseMax) pairs += (unsigned long long)m * cand;
-        else spairs += (unsigned long long)m * cand;
     }
-    for (int o = 16; o > 0; o >>= 1) {
-        pairs += __shfl_xor_sync(0xffffffffu, pairs, o);
-        spairs += __shfl_xor_sync(0xffffffffu, spairs, o);
-    }
-    if ((threadIdx.x & 31) == 0 && pairs) atomicAdd(&cb.stats[0], pairs);
-    if ((threadIdx.x & 31) == 0 && spairs) atomicAdd(&cb.stats[1], spairs);
 }
 
 // Any k, any reach R (used when R != 1).
 __global__ void __launch_bounds__(256) k_cell_runs_any(BatchView v, CellPrepBufs cb, int64_t ncells) {
-    unsigned long long pairs = 0, spairs = 0;  // dense cells', sparse cells' candidate pairs
     for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < ncells; c += (int64_t)gridDim.x * blockDim.x) {
-        const uint32_t cs = v.cell_start[c], m = v.cell_start[c + 1] - cs;
+        const uint32_t cs = v.cell_start[c];
         const int b = find_ds(v.pt_off, v.B, cs);
         const DsDesc& ds = v.desc[b];
         if (ds.R == 1 && ds.k >= 1) continue;
@@ -174,15 +179,7 @@ __global__ void __launch_bounds__(256) k_cell_runs_any(BatchView v, CellPrepBufs
         }
         cb.nruns[c] = nr;
         cb.cand[c] = cand;
-        if (m > (uint32_t)kSparseMax) pairs += (unsigned long long)m * cand;
-        else spairs += (unsigned long long)m * cand;
     }
-    for (int o = 16; o > 0; o >>= 1) {
-        pairs += __shfl_xor_sync(0xffffffffu, pairs, o);
-        spairs += __shfl_xor_sync(0xffffffffu, spairs, o);
-    }
-    if ((threadIdx.x & 31) == 0 && pairs) atomicAdd(&cb.stats[0], pairs);
-    if ((threadIdx.x & 31) == 0 && spairs) atomicAdd(&cb.stats[1], spairs);
 }
 
 __global__ void k_item_count(BatchView v, CellPrepBufs cb, int kch) {
@@ -497,11 +494,23 @@ void launch_rho_sparse(const BatchView& v, const CellWork& w, int64_t nsparse_bo
 
 }  // namespace
 
-cudaError_t launch_classify_cells(const BatchView& v, const CellPrepBufs& cb, int64_t ncells_bound, void* scan_temp,
-                                  cudaStream_t st) {
+cudaError_t launch_cell_runs(const BatchView& v, const CellPrepBufs& cb, int64_t ncells, uint32_t kmask,
+                            cudaStream_t st) {
+    if (ncells <= 0) return cudaSuccess;
+    const unsigned blocks = (unsigned)std::min<int64_t>(152 * 16, grid_for(ncells, 256));
+    if (kmask & 1u) (k_cell_runs_any<<<blocks, 256, 0, st>>>(v, cb, ncells), note_launch());
+    if (kmask & 2u) (k_cell_runs<1><<<blocks, 256, 0, st>>>(v, cb, ncells), note_launch());
+    if (kmask & 4u) (k_cell_runs<2><<<blocks, 256, 0, st>>>(v, cb, ncells), note_launch());
+    if (kmask & 8u) (k_cell_runs<3><<<blocks, 256, 0, st>>>(v, cb, ncells), note_launch());
+    if (kmask & 16u) (k_cell_runs<4><<<blocks, 256, 0, st>>>(v, cb, ncells), note_launch());
+    return cudaGetLastError();
+}
+
+cudaError_t launch_classify_cells(const BatchView& v, const CellPrepBufs& cb, int64_t ncells_bound,
+                                  uint32_t sparse_cand, void* scan_temp, cudaStream_t st) {
     if (ncells_bound <= 0) return cudaSuccess;
     const unsigned blocks = (unsigned)std::min<int64_t>(152 * 16, grid_for(ncells_bound, 256));
-    (k_classify<<<blocks, 256, 0, st>>>(v, cb.dflag, cb.sflag, ncells_bound), note_launch());
+    (k_classify<<<blocks, 256, 0, st>>>(v, cb, ncells_bound, sparse_cand), note_launch());
     cudaError_t e = exclusive_scan_u32(cb.dflag, cb.didx, ncells_bound, cb.ndense, scan_temp, st);
     if (e != cudaSuccess) return e;
     e = exclusive_scan_u32(cb.sflag, cb.sidx, ncells_bound, cb.nsparse, scan_temp, st);
@@ -510,16 +519,8 @@ cudaError_t launch_classify_cells(const BatchView& v, const CellPrepBufs& cb, in
     return cudaGetLastError();
 }
 
-cudaError_t launch_dense_prep(const BatchView& v, const CellPrepBufs& cb, int64_t ncells, int64_t ndense_bound,
-                              int kch, uint32_t kmask, void* scan_temp, cudaStream_t st) {
-    if (ncells > 0) {
-        const unsigned blocks = (unsigned)std::min<int64_t>(152 * 16, grid_for(ncells, 256));
-        if (kmask & 1u) (k_cell_runs_any<<<blocks, 256, 0, st>>>(v, cb, ncells), note_launch());
-        if (kmask & 2u) (k_cell_runs<1><<<blocks, 256, 0, st>>>(v, cb, ncells), note_launch());
-        if (kmask & 4u) (k_cell_runs<2><<<blocks, 256, 0, st>>>(v, cb, ncells), note_launch());
-        if (kmask & 8u) (k_cell_runs<3><<<blocks, 256, 0, st>>>(v, cb, ncells), note_launch());
-        if (kmask & 16u) (k_cell_runs<4><<<blocks, 256, 0, st>>>(v, cb, ncells), note_launch());
-    }
+cudaError_t launch_item_prep(const BatchView& v, const CellPrepBufs& cb, int64_t ndense_bound, int kch,
+                             void* scan_temp, cudaStream_t st) {
     if (ndense_bound <= 0) return cudaMemsetAsync(cb.nitems, 0, sizeof(uint32_t), st);
     const unsigned blocks = (unsigned)std::min<int64_t>(152 * 16, grid_for(ndense_bound, 256));
     (k_item_count<<<blocks, 256, 0, st>>>(v, cb, kch), note_launch());

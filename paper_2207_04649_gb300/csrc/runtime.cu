@@ -124,6 +124,7 @@ struct Tune {
     int hd_cell_factor = 2;   // datasets with d >= hd_min_d: cells of side d_cut / f searched to reach f
     int hd_min_d = 7;
     int ring2 = 0;            // second ring (cells at distance 2) before the tree search
+    int sparse_cand = 512;    // cells of at most 4 points with more candidates than this take the dense path
 };
 
 }  // namespace
@@ -522,15 +523,8 @@ struct Batch {
         DPC_CK(keep.get(&cb.ndense, 1));
         DPC_CK(keep.get(&cb.nsparse, 1));
         DPC_CK(keep.get(&cb.nitems, 1));
-        DPC_CK(launch_classify_cells(v, cb, ncells, temp, st));
-        uint32_t cnts[2] = {0, 0};
-        if (ncells > 0) {
-            DPC_CK(cudaMemcpyAsync(&cnts[0], cb.ndense, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
-            DPC_CK(cudaMemcpyAsync(&cnts[1], cb.nsparse, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
-            DPC_TRY(sync("cell classes"));
-        }
-        ndense = cnts[0];
-        nsparse = cnts[1];
+        // neighbour runs of every cell, then the classes (by size and by
+        // candidate count)
         int nbs = 1;
         for (int b = 0; b < B; ++b) {
             int t = 1;
@@ -541,11 +535,21 @@ struct Batch {
         DPC_CK(keep.get(&cb.runs, (size_t)std::max<int64_t>(ncells, 1) * nbs));
         DPC_CK(keep.get(&cb.nruns, ncells + 1));
         DPC_CK(keep.get(&cb.cand, ncells + 1));
-        DPC_CK(dens.get(&cb.nitem_c, ndense + 1));
-        DPC_CK(dens.get(&cb.item_off, ndense + 1));
         uint32_t kmask = 0;
         for (int b = 0; b < B; ++b) kmask |= (hd[b].R == 1 && hd[b].k >= 1) ? 1u << hd[b].k : 1u;
-        DPC_CK(launch_dense_prep(v, cb, ncells, ndense, tune.kch, kmask, temp, st));
+        DPC_CK(launch_cell_runs(v, cb, ncells, kmask, st));
+        DPC_CK(launch_classify_cells(v, cb, ncells, (uint32_t)tune.sparse_cand, temp, st));
+        uint32_t cnts[2] = {0, 0};
+        if (ncells > 0) {
+            DPC_CK(cudaMemcpyAsync(&cnts[0], cb.ndense, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
+            DPC_CK(cudaMemcpyAsync(&cnts[1], cb.nsparse, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
+            DPC_TRY(sync("cell classes"));
+        }
+        ndense = cnts[0];
+        nsparse = cnts[1];
+        DPC_CK(dens.get(&cb.nitem_c, ndense + 1));
+        DPC_CK(dens.get(&cb.item_off, ndense + 1));
+        DPC_CK(launch_item_prep(v, cb, ndense, tune.kch, temp, st));
         uint32_t ni = 0;
         if (ndense > 0) {
             DPC_CK(cudaMemcpyAsync(&ni, cb.nitems, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
@@ -1147,6 +1151,7 @@ dpc_status dpc_set_tuning(dpc_ctx* ctx, const char* key, int64_t value) {
     else if (k == "hd_cell_factor" && value >= 1 && value <= 3) t.hd_cell_factor = (int)value;
     else if (k == "hd_min_d" && value >= 1 && value <= 9) t.hd_min_d = (int)value;
     else if (k == "ring2" && value >= 0 && value <= 1) t.ring2 = (int)value;
+    else if (k == "sparse_cand" && value >= 0 && value <= (1ll << 31)) t.sparse_cand = (int)std::min<int64_t>(value, INT32_MAX);
     else if (k == "max_batch_jobs" && value >= 1 && value <= 4096) {
         std::lock_guard<std::mutex> lk(ctx->mu);
         ctx->max_batch_jobs = (int)value;
@@ -1167,6 +1172,7 @@ dpc_status dpc_get_tuning(dpc_ctx* ctx, const char* key, int64_t* value) {
     else if (k == "hd_cell_factor") *value = t.hd_cell_factor;
     else if (k == "hd_min_d") *value = t.hd_min_d;
     else if (k == "ring2") *value = t.ring2;
+    else if (k == "sparse_cand") *value = t.sparse_cand;
     else if (k == "max_batch_jobs") {
         std::lock_guard<std::mutex> lk(ctx->mu);
         *value = ctx->max_batch_jobs;

@@ -202,13 +202,18 @@ struct CellPrepBufs {
     int nbs;
     unsigned long long* stats;  // [0] += candidate pairs
 };
-cudaError_t launch_classify_cells(const BatchView& v, const CellPrepBufs& cb, int64_t ncells_bound, void* scan_temp,
-                                  cudaStream_t st);
-// Neighbour runs and candidate counts of every cell, then the dense items' counts.
+// Neighbour runs and candidate counts of every cell.
 // kmask: bit K (1..4) = a dataset gridded in K dims with reach 1 is in the
 // batch; bit 0 = one with another reach or no gridded dim.
-cudaError_t launch_dense_prep(const BatchView& v, const CellPrepBufs& cb, int64_t ncells, int64_t ndense_bound,
-                              int kch, uint32_t kmask, void* scan_temp, cudaStream_t st);
+cudaError_t launch_cell_runs(const BatchView& v, const CellPrepBufs& cb, int64_t ncells, uint32_t kmask,
+                            cudaStream_t st);
+// Dense and sparse cells (after the runs: a cell with more than sparse_cand
+// candidates is dense whatever its size) and their candidate pairs.
+cudaError_t launch_classify_cells(const BatchView& v, const CellPrepBufs& cb, int64_t ncells_bound,
+                                  uint32_t sparse_cand, void* scan_temp, cudaStream_t st);
+// Work items per dense cell and their offsets.
+cudaError_t launch_item_prep(const BatchView& v, const CellPrepBufs& cb, int64_t ndense_bound, int kch,
+                             void* scan_temp, cudaStream_t st);
 cudaError_t launch_fill_items(const BatchView& v, const CellPrepBufs& cb, int64_t ndense_bound, int kch,
                               cudaStream_t st);
 // class_mask bit 3*(d-1) + mode: a dataset of dimension d with density test

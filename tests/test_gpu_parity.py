@@ -122,13 +122,16 @@ def test_random_shapes_point_tree(dpc, shape):
     assert info["grid_dims"] == 0
 
 
+@pytest.mark.parametrize("sparse_cand", [512, 0, 2147483647])
 @pytest.mark.parametrize("d", [5, 6, 7, 8])
 @pytest.mark.parametrize("f", [1, 2, 3])
-def test_high_dims_grid_path(dpc, d, f):
+def test_high_dims_grid_path(dpc, d, f, sparse_cand):
     """The projected grid for d > 4 (the point tree switched off), with
-    cells of side d_cut / f searched f cells away."""
+    cells of side d_cut / f searched f cells away; small cells on the warp
+    path by their candidate count (sparse_cand 0: every cell)."""
     ds = workloads.random_blobs(60 + d, 2500, d, 9000, blobs=4, spread=0.05, dup=10)
-    info = assert_full_parity(dpc, ds.points, 9000, [(3, 27001)], dict(tree_min_d=9, hd_cell_factor=f, hd_min_d=5))
+    info = assert_full_parity(dpc, ds.points, 9000, [(3, 27001)],
+                              dict(tree_min_d=9, hd_cell_factor=f, hd_min_d=5, sparse_cand=sparse_cand))
     assert 1 <= info["grid_dims"] <= 4
 
 
@@ -313,7 +316,8 @@ def test_plain_5p8m_3d_sampled(dpc):
 @pytest.mark.parametrize("knobs", [dict(clevel=2, ccap=512), dict(clevel=1, ccap=64, bf_rank=0),
                                    dict(kch=64, bf_rank=100000), dict(kmax=2), dict(kmax=1, clevel=3),
                                    dict(tree_min_d=3), dict(tree_min_d=1, bf_rank=0), dict(ring2=0),
-                                   dict(ring2=1, bf_rank=0)],
+                                   dict(ring2=1, bf_rank=0), dict(sparse_cand=0), dict(sparse_cand=2147483647),
+                                   dict(sparse_cand=20, kch=64)],
                          ids=lambda k: ",".join(f"{a}={b}" for a, b in k.items()))
 def test_tuning_knobs_do_not_change_results(dpc, knobs):
     ds = workloads.random_blobs(77, 6000, 3, 900, blobs=5, spread=0.06, dup=8)

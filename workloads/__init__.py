@@ -186,6 +186,17 @@ def plain_1m_8d(seed: int = 3, n: int = 1_000_000) -> Dataset:
     return Dataset("plain_1m_8d", pts, d_cut, 5, 8 * d_cut, seed=seed)
 
 
+def plain_400k_8d(seed: int = 3, n: int = 400_000) -> Dataset:
+    """A 400k-point draw of the same 8-d mixture (a profiling case well
+    under the 1M set's footprint); d_cut is the 1M set's calibrated cutoff
+    scaled by (1M / n)^(1/8), which keeps the expected neighbour count."""
+    big = _load_calibrated().get("plain_1m_8d")
+    base = int(big["d_cut"]) if big is not None else 4040
+    d_cut = int(round(base * (1_000_000 / n) ** (1.0 / 8.0)))
+    pts, _, _ = _c3_draw(seed, n)
+    return Dataset("plain_400k_8d", pts, d_cut, 5, 8 * d_cut, seed=seed)
+
+
 def _random_problem(rng, name, n, d, target_rho, noise_frac=0.05):
     """A blob mixture (5-30 blobs) + uniform noise with its own cutoff."""
     nb = int(rng.integers(5, 31))
@@ -269,4 +280,5 @@ NAMED = {
     "plain_5p8m_3d": plain_5p8m_3d,
     "plain_2m_3d": plain_2m_3d,
     "plain_1m_8d": plain_1m_8d,
+    "plain_400k_8d": plain_400k_8d,
 }
