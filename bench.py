@@ -37,8 +37,14 @@ APPROX_METRIC = "Approx-DPC points/s (rho+approximate delta+labels) at 5.8M x 3"
 SAPPROX_METRIC = "S-Approx-DPC points/s (rho of picks+approximate delta+labels) at 5.8M x 3"
 
 
+# the single-dataset workloads' sizes, as the metric names them
+SIZE_NAME = {"plain_5p8m_3d": "5.8M x 3", "plain_2m_3d": "2M x 3", "plain_1m_8d": "1M x 8",
+             "plain_400k_8d": "400k x 8", "plain_20k_2d": "20k x 2"}
+
+
 def metric_for(args) -> str:
-    return {"approx": APPROX_METRIC, "sapprox": SAPPROX_METRIC}.get(args.method, METRIC)
+    m = {"approx": APPROX_METRIC, "sapprox": SAPPROX_METRIC}.get(args.method, METRIC)
+    return m.replace("5.8M x 3", SIZE_NAME.get(args.workload, args.workload))
 UNIT = "points/s"
 
 
