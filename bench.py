@@ -204,6 +204,51 @@ def derived_pair_peak(d: int, form: int, sm_mhz) -> dict:
             "derivation": f"152 SMs x 4 x 32 lanes x {mhz:.0f} MHz / {ops} integer ops per pair"}
 
 
+def hbm_peak():
+    """(GB/s, source) of the HBM roofline: the measured copy bandwidth, else
+    the profiling recipe's fallback."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+def e2e_roofline(n: int, d: int, info: dict, pair_rate: float, value: float) -> dict:
+    """End-to-end points/s roofline: n over the sum of the stages' roofline
+    times. Grid, rank sort and labels are HBM-bound, at algorithmic bytes per
+    point (kb = key bytes, P = radix passes = key bits / 8 rounded up, each
+    pass reading the keys twice and the values once and writing both:
+    3 kb + 8 bytes): grid = read the input 4d, write key and index kb + 4,
+    P passes, gather (index 4, input 4d, record 16 per 4 dims), cells and hash
+    8; rank = keys kb + 4, P passes, rank and (rank, index) 20; labels = read
+    rho, dep, delta2 (16), write parent and label (8), read parents (4). The
+    density and ring passes are ALU-bound: candidate pairs over the measured
+    pair rate, each. The open-point searches are data dependent and not
+    modelled (zero time), so the bound is optimistic."""
+    gbs, src = hbm_peak()
+    dp = 1 if d <= 4 else 2
+
+    def sort_bytes(bits):
+        kb = 4 if bits <= 32 else 8
+        return kb, max(1, (bits + 7) // 8) * (3 * kb + 8)
+
+    kb, gp = sort_bytes(info.get("grid_key_bits") or 32)
+    grid_b = n * (4 * d + kb + 4 + gp + 4 + 4 * d + 16 * dp + 8)
+    kr, rp = sort_bytes(info.get("rank_key_bits") or 32)
+    rank_b = n * (kr + 4 + rp + 20)
+    label_b = n * (16 + 8 + 4)
+    pairs = info["cand_pairs"]
+    ms = {"grid_hbm": grid_b / (gbs * 1e9) * 1e3, "rho_alu": pairs / pair_rate * 1e3,
+          "rank_hbm": rank_b / (gbs * 1e9) * 1e3, "ring_alu": pairs / pair_rate * 1e3,
+          "open_points": 0.0, "labels_hbm": label_b / (gbs * 1e9) * 1e3}
+    total = sum(ms.values())
+    bound = n / (total / 1e3)
+    return {"stages_ms": ms, "points_per_s": bound, "frac": value / bound, "hbm_gbs": gbs,
+            "hbm_source": src, "pair_rate": pair_rate,
+            "bytes_per_point": {"grid": grid_b / n, "rank": rank_b / n, "labels": label_b / n}}
+
+
 RHO_SOURCES = ("rho.cu", "stages.cuh", "dpc_internal.cuh")
 
 
@@ -387,7 +432,8 @@ def run_ours(args):
         rate, dt = oracle_sample_rate(ds, m, method=args.method, eps=eps)
         cpu = {"value": rate, "unit": UNIT, "cores": oracle.threads(), "kind": "oracle",
                "sample": f"{m} random points of the {n}-point set: rho against all n points and the "
-                         f"{args.method} dependent-point step over all n points ({dt:.1f} s)"}
+                         f"{args.method} dependent-point step over all n points ({dt:.1f} s)",
+               "full_run_s_extrapolated": n / rate}
 
     if dist:
         dist.barrier()
@@ -417,6 +463,7 @@ def run_ours(args):
                                         "in registers on all SMs (dpc_probe_pair_rate), same run",
                          "pair_mode": pair_mode,
                          "peak_derived": derived_pair_peak(d, pair_mode, clk.get("sm_mhz"))},
+            "e2e_roofline": e2e_roofline(n, d, infos[-1], probe_rate, value),
             "stages_ms": {k: statistics.mean(i[k] for i in infos)
                           for k in ("ms_grid", "ms_rho", "ms_rank", "ms_ring", "ms_rest", "ms_label")},
             "work": {k: infos[-1][k] for k in ("cells", "dense_cells", "work_items", "cand_pairs", "dense_pairs",

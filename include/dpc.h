@@ -209,10 +209,10 @@ typedef struct {
     int64_t tree_pairs;       /* point pairs it tested */
     int64_t open_after_coarse;  /* points the coarse ring left for the tree search */
     int32_t pair_mode;        /* density pair test: 0 direct 32-bit, 1 direct 64-bit, 2 expanded 32-bit */
-    int32_t reserved;
+    int32_t grid_key_bits;    /* width of the grid's sort key (radix passes: bits / 8, rounded up) */
     int64_t dense_pairs;      /* of cand_pairs, those of dense cells (one warp per work item) */
     float ms_rho_dense;       /* of ms_rho, the dense cells' kernels (profiling on) */
-    int32_t reserved2;
+    int32_t rank_key_bits;    /* width of the rank sort's key */
     int64_t picks;            /* S-Approx-DPC: cells of G' (picked points) */
     int64_t second_phase;     /* S-Approx-DPC: picks without a first-phase dependent point */
 } dpc_info;

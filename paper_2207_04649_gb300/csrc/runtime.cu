@@ -248,6 +248,7 @@ struct Batch {
     bool has_density = false, has_rank = false;
     int dep_kind = 0;  // dependent points held: 0 none, 1 exact, 2 Approx-DPC, 3 S-Approx-DPC
     int64_t npicks = 0, nsecond = 0, sap_pairs = 0;  // S-Approx-DPC counters
+    int grid_key_bits = 0, rank_key_bits = 0;
     int32_t* rho_pub = nullptr;  // S-Approx-DPC: rho as reported (-1 where not picked)
     uint32_t class_mask = 0, dim_mask = 0;
     int64_t ncells = 0, ndense = 0, nsparse = 0, nitems = 0, ntree = 0, nbf = 0;
@@ -458,6 +459,7 @@ struct Batch {
         }
         DPC_TRY(upload_desc());
         const int key_bits = bits_for(cbase > 0 ? cbase - 1 : 0);
+        grid_key_bits = key_bits;
         const bool key32 = key_bits <= 32;
 
         // persistent per-point state
@@ -810,6 +812,7 @@ struct Batch {
         int rbits = 1;
         for (int b = 0; b < B; ++b) rbits = std::max(rbits, hd[b].rbits);
         int bbits = ceil_log2((uint64_t)B);
+        rank_key_bits = bbits + rbits;
         const size_t kb = (bbits + rbits) > 32 ? 8 : 4;
         DPC_CK(tmp.get(&db.rkeys, 3 * a256(kb * N) / 4 + 64));
         DPC_CK(tmp.get(&db.rvals, 2 * (N + 64)));
@@ -1314,6 +1317,8 @@ static void fill_info(const Batch& bt, int b, dpc_info* out) {
     out->pair_mode = h.mode;
     out->dense_pairs = bt.dense_pairs;
     out->ms_rho_dense = bt.ms_rho_dense;
+    out->grid_key_bits = bt.grid_key_bits;
+    out->rank_key_bits = bt.rank_key_bits;
     out->picks = bt.npicks;
     out->second_phase = bt.nsecond;
 }

@@ -89,3 +89,17 @@ def test_parse_eps():
     assert bench.parse_eps("0.8") == (4, 5)
     assert bench.parse_eps("3/7") == (3, 7)
     assert bench.parse_eps("1") == (1, 1)
+
+
+def test_e2e_roofline_model():
+    sys.path.insert(0, ROOT)
+    import bench
+    info = {"grid_key_bits": 30, "rank_key_bits": 23, "cand_pairs": 3_694_000_000}
+    r = bench.e2e_roofline(5_800_000, 3, info, 5.1e12, 5.27e8)
+    # 3-d: 4 grid passes of 32-bit keys (20 B each), 3 rank passes
+    assert r["bytes_per_point"]["grid"] == 12 + 8 + 80 + 4 + 12 + 16 + 8
+    assert r["bytes_per_point"]["rank"] == 8 + 60 + 20
+    assert abs(r["stages_ms"]["rho_alu"] - 3.694e9 / 5.1e12 * 1e3) < 1e-9
+    assert r["stages_ms"]["open_points"] == 0.0
+    assert abs(r["points_per_s"] - 5_800_000 / (sum(r["stages_ms"].values()) / 1e3)) < 1e-3
+    assert 0 < r["frac"] < 1
