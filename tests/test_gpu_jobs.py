@@ -66,6 +66,23 @@ def test_batched_flush_matches_oracle(dpc):
             check_job(j, p, dc, qs)
 
 
+@pytest.mark.parametrize("knobs", [dict(bf_rank=0), dict(bf_rank=1 << 30)], ids=["tree_only", "brute_force_only"])
+def test_batched_open_point_passes(dpc, knobs):
+    """A batch of uneven datasets whose open points all go through the tree
+    search (bf_rank 0) or all through the brute force over the rank prefix."""
+    probs = small_problems(seed=42, count=16)
+    with dpc.Context(0, mode=0) as ctx:
+        ctx.tune(**knobs)
+        jobs = [dpc.Job(p, dc, qs) for p, dc, qs in probs]
+        for j in jobs:
+            ctx.submit(j)
+        ctx.flush()
+        for j, (p, dc, qs) in zip(jobs, probs):
+            s, res = ctx.poll(j.ticket)
+            assert s == dpc.DPC_OK and res.status == dpc.DPC_OK
+            check_job(j, p, dc, qs)
+
+
 def test_batch_equals_alone_on_blob_workload(dpc):
     """A slice of the 256-problem batch: bits equal to each problem alone."""
     probs = workloads.batch_256(count=12)
