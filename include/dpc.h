@@ -163,6 +163,23 @@ dpc_status dpc_sapprox(dpc_ctx* ctx, const int32_t* points, int64_t n, int32_t d
  *   n_centers: NULL or one int64 in host memory. */
 dpc_status dpc_label(dpc_ds* ds, int64_t rho_min, int64_t delta_min, int32_t* label_out, int64_t* n_centers);
 
+/* The whole path in one call (Definitions 1-6 for one (rho_min,
+ * delta_min) query): dpc_density, dpc_dependent and dpc_label on a dataset
+ * that is released before the call returns. The results leave the device as
+ * soon as each is final, on a second stream of the context, while the later
+ * stages run (rho during the dependent-point search, dep and delta2 during
+ * the labels); copies into page-locked host memory overlap, others are
+ * staged by the driver.
+ *   points, n, d, d_cut, is_device: as for dpc_density.
+ *   rho_min, delta_min: as for dpc_label.
+ *   rho_out, dep_out, delta2_out, label_out: NULL or n elements each, host or
+ *            device memory per is_device, as the separate calls write them.
+ *   n_centers: NULL or one int64 in host memory.
+ * Returns when every output is written. Errors: those of the three calls. */
+dpc_status dpc_cluster(dpc_ctx* ctx, const int32_t* points, int64_t n, int32_t d, int64_t d_cut, int is_device,
+                       int64_t rho_min, int64_t delta_min, int32_t* rho_out, int32_t* dep_out, int64_t* delta2_out,
+                       int32_t* label_out, int64_t* n_centers);
+
 /* Free a dataset's device state. The handle is invalid afterwards. */
 dpc_status dpc_release(dpc_ds* ds);
 

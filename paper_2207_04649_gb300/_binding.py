@@ -95,6 +95,7 @@ def lib():
             "dpc_ds_info": ([vp, ctypes.POINTER(DpcInfo)], st),
             "dpc_last_batch_info": ([vp, ctypes.POINTER(DpcInfo)], st),
             "dpc_dependent_approx": ([vp, vp, vp, vp], st),
+            "dpc_cluster": ([vp, vp, i64, i32, i64, ctypes.c_int, i64, i64, vp, vp, vp, vp, ctypes.POINTER(i64)], st),
             "dpc_sapprox": ([vp, vp, i64, i32, i64, i64, i64, ctypes.c_int, ctypes.POINTER(vp), vp, vp, vp, vp], st),
             "dpc_autotune": ([vp, ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32, ctypes.c_char_p,
                               ctypes.c_size_t], st),
@@ -174,6 +175,14 @@ def dpc_sapprox(ctx, points_ptr, n, d, d_cut, eps_num, eps_den, is_device, rho_p
     _check(lib().dpc_sapprox(ctx, points_ptr, n, d, d_cut, int(eps_num), int(eps_den), is_device, ctypes.byref(h),
                              rho_ptr, dep_ptr, delta2_ptr, pick_ptr), "dpc_sapprox")
     return h
+
+
+def dpc_cluster(ctx, points_ptr, n, d, d_cut, is_device, rho_min, delta_min, rho_ptr=None, dep_ptr=None,
+                delta2_ptr=None, label_ptr=None) -> int:
+    nc = ctypes.c_int64(0)
+    _check(lib().dpc_cluster(ctx, points_ptr, n, d, int(d_cut), is_device, int(rho_min), int(delta_min), rho_ptr,
+                             dep_ptr, delta2_ptr, label_ptr, ctypes.byref(nc)), "dpc_cluster")
+    return int(nc.value)
 
 
 def dpc_label(ds, rho_min, delta_min, label_ptr=None):
@@ -326,6 +335,23 @@ class Context:
         self._order_after_torch(points, rho_out)
         h = dpc_density(self.handle, pp, n, d, int(d_cut), dev, rp)
         return Dataset(self, h, n, dev)
+
+    def cluster(self, points, d_cut: int, rho_min: int, delta_min: int, rho_out=None, dep_out=None,
+                delta2_out=None, label_out=None) -> int:
+        """The whole path in one call (dpc_cluster); returns the number of
+        centers. Outputs live where the points live."""
+        if points.ndim != 2:
+            raise ValueError("points must be n x d")
+        n, d = int(points.shape[0]), int(points.shape[1])
+        pp, dev = _arg(points, np.int32)
+        ptrs = []
+        for x, dt in [(rho_out, np.int32), (dep_out, np.int32), (delta2_out, np.int64), (label_out, np.int32)]:
+            p, xdev = _arg(x, dt, (n,))
+            if x is not None and xdev != dev:
+                raise ValueError("outputs must live where points live")
+            ptrs.append(p)
+        self._order_after_torch(points, rho_out, dep_out, delta2_out, label_out)
+        return dpc_cluster(self.handle, pp, n, d, int(d_cut), dev, rho_min, delta_min, *ptrs)
 
     def sapprox(self, points, d_cut: int, eps, rho_out=None, dep_out=None, delta2_out=None,
                 pick_out=None) -> "Dataset":
@@ -507,16 +533,14 @@ def cluster_approx(points: np.ndarray, d_cut: int, rho_min: int, delta_min: int,
 
 
 def cluster(points: np.ndarray, d_cut: int, rho_min: int, delta_min: int, device: int = 0) -> dict:
-    """The whole path on host arrays: rho, dep, delta2, label, n_centers."""
+    """The whole path on host arrays (dpc_cluster): rho, dep, delta2, label,
+    n_centers."""
     pts = np.ascontiguousarray(points, dtype=np.int32)
     n = pts.shape[0]
     with Context(device) as ctx:
         rho = np.empty(n, np.int32)
-        ds = ctx.density(pts, d_cut, rho)
         dep = np.empty(n, np.int32)
         d2 = np.empty(n, np.int64)
-        ds.dependent(dep, d2)
         lab = np.empty(n, np.int32)
-        nc = ds.label(rho_min, delta_min, lab)
-        ds.release()
+        nc = ctx.cluster(pts, d_cut, rho_min, delta_min, rho, dep, d2, lab)
     return {"rho": rho, "dep": dep, "delta2": d2, "label": lab, "n_centers": nc}

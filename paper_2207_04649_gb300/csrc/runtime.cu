@@ -161,6 +161,8 @@ struct dpc_ctx {
     dpc_info last_info{};
     std::string tune_cache;   // autotuner file ("" when none)
     std::map<std::pair<int, int>, dpc::Tune> tuned;  // (largest d, log2 mean n) -> knobs
+    cudaStream_t copy_stream = nullptr;  // dpc_cluster: device-to-host copies beside the compute
+    cudaEvent_t copy_ev[2] = {nullptr, nullptr};
 };
 
 namespace dpc {
@@ -1241,6 +1243,61 @@ dpc_status dpc_sapprox(dpc_ctx* ctx, const int32_t* points, int64_t n, int32_t d
     return DPC_OK;
 }
 
+dpc_status dpc_cluster(dpc_ctx* ctx, const int32_t* points, int64_t n, int32_t d, int64_t d_cut, int is_device,
+                       int64_t rho_min, int64_t delta_min, int32_t* rho_out, int32_t* dep_out, int64_t* delta2_out,
+                       int32_t* label_out, int64_t* n_centers) {
+    if (!ctx) return fail(DPC_ERR_INVALID_ARG, "ctx is NULL");
+    DPC_TRY(check_input(points, n, d, d_cut));
+    if (delta_min <= d_cut || delta_min > dpc::kMaxDeltaMin)
+        return fail(DPC_ERR_INVALID_ARG, "delta_min must be in (d_cut, 3037000499]");
+    cudaError_t e = cudaSetDevice(ctx->device);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaSetDevice");
+    {
+        std::lock_guard<std::mutex> lk(ctx->mu);
+        if (!ctx->copy_stream) {
+            for (auto& ev : ctx->copy_ev)
+                if ((e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming)) != cudaSuccess)
+                    return cuda_fail(e, "cudaEventCreate");
+            if ((e = cudaStreamCreateWithFlags(&ctx->copy_stream, cudaStreamNonBlocking)) != cudaSuccess)
+                return cuda_fail(e, "cudaStreamCreate");
+        }
+    }
+    Batch bt;
+    bt.ctx = ctx;
+    // on every way out, the side copies end before the batch frees its buffers
+    struct CopyWait {
+        cudaStream_t s;
+        ~CopyWait() { cudaStreamSynchronize(s); }
+    } copy_wait{ctx->copy_stream};
+    std::vector<dpc::Input> in{{points, n, d, d_cut, is_device}};
+    DPC_TRY(bt.density(in));
+    cudaStream_t cs = ctx->copy_stream;
+    auto side_copy = [&](void* dst, const void* src, size_t bytes) -> dpc_status {
+        if (dst && bytes) DPC_CK(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDefault, cs));
+        return DPC_OK;
+    };
+    // rho is final: it travels while the dependent points are computed
+    DPC_CK(cudaEventRecord(ctx->copy_ev[0], bt.st));
+    DPC_CK(cudaStreamWaitEvent(cs, ctx->copy_ev[0], 0));
+    DPC_TRY(side_copy(rho_out, bt.v.rho, sizeof(int32_t) * n));
+    DPC_TRY(bt.dependent());
+    // the dependent points travel while the labels are computed
+    DPC_CK(cudaEventRecord(ctx->copy_ev[1], bt.st));
+    DPC_CK(cudaStreamWaitEvent(cs, ctx->copy_ev[1], 0));
+    DPC_TRY(side_copy(dep_out, bt.v.dep, sizeof(int32_t) * n));
+    DPC_TRY(side_copy(delta2_out, bt.v.delta2, sizeof(int64_t) * n));
+    DPC_TRY(bt.label(&rho_min, &delta_min));
+    DPC_TRY(bt.copy_out(label_out, bt.v.label, sizeof(int32_t) * n));
+    unsigned long long nc = 0;
+    if (n_centers) DPC_TRY(bt.copy_out(&nc, bt.v.ncent, sizeof(nc)));
+    DPC_TRY(bt.sync("labels"));
+    e = cudaStreamSynchronize(cs);
+    if (e != cudaSuccess) return cuda_fail(e, "copies");
+    DPC_TRY(bt.check_err("labels"));
+    if (n_centers) *n_centers = (int64_t)nc;
+    return DPC_OK;
+}
+
 dpc_status dpc_dependent(dpc_ds* ds, int32_t* dep_out, int64_t* delta2_out) {
     if (!ds || !ds->batch) return fail(DPC_ERR_STATE, "invalid dataset handle");
     Batch& bt = *ds->batch;
@@ -1662,6 +1719,12 @@ dpc_status dpc_destroy(dpc_ctx* ctx) {
     for (auto& t : ctx->workers) t.join();
     cudaSetDevice(ctx->device);
     cudaStreamSynchronize(ctx->stream);
+    if (ctx->copy_stream) {
+        cudaStreamSynchronize(ctx->copy_stream);
+        cudaStreamDestroy(ctx->copy_stream);
+    }
+    for (auto& e : ctx->copy_ev)
+        if (e) cudaEventDestroy(e);
     if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
     delete ctx;
     return DPC_OK;

@@ -350,3 +350,30 @@ def test_tuning_rejects_unknown_keys(dpc):
             ctx.tune(nonsense=3)
         with pytest.raises(dpc.DpcError):
             ctx.tune(kmax=9)
+
+
+def test_one_call_cluster_matches_the_separate_calls(dpc):
+    """dpc_cluster (copies beside the compute) gives the bits of density +
+    dependent + label, host and device buffers, and rejects bad queries."""
+    import torch
+    ds = workloads.random_blobs(91, 30000, 3, 1500, blobs=6, spread=0.05, dup=10)
+    pts = np.ascontiguousarray(ds.points)
+    n = pts.shape[0]
+    ref = run_host(dpc, pts, 1500, [(3, 4000)])
+    with dpc.Context(0) as ctx:
+        h_out = [np.full(n, -7, t) for t in (np.int32, np.int32, np.int64, np.int32)]
+        nc = ctx.cluster(pts, 1500, 3, 4000, *h_out)
+        dev = torch.device("cuda", 0)
+        d_out = [torch.full((n,), -7, dtype=t, device=dev) for t in (torch.int32, torch.int32, torch.int64, torch.int32)]
+        nc2 = ctx.cluster(torch.from_numpy(pts).to(dev), 1500, 3, 4000, *d_out)
+        ctx.stream.synchronize()
+        with pytest.raises(dpc.DpcError):
+            ctx.cluster(pts, 1500, 3, 1500)  # delta_min must exceed d_cut
+        empty = ctx.cluster(np.zeros((0, 3), np.int32), 5, 1, 6)
+    for got in (h_out, [t.cpu().numpy() for t in d_out]):
+        np.testing.assert_array_equal(got[0], ref[0])
+        np.testing.assert_array_equal(got[1], ref[1])
+        np.testing.assert_array_equal(got[2], ref[2])
+        np.testing.assert_array_equal(got[3], ref[3][0][0])
+    assert nc == nc2 == ref[3][0][1]
+    assert empty == 0
