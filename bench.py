@@ -39,7 +39,8 @@ SAPPROX_METRIC = "S-Approx-DPC points/s (rho of picks+approximate delta+labels) 
 
 # the single-dataset workloads' sizes, as the metric names them
 SIZE_NAME = {"plain_5p8m_3d": "5.8M x 3", "plain_2m_3d": "2M x 3", "plain_1m_8d": "1M x 8",
-             "plain_400k_8d": "400k x 8", "plain_20k_2d": "20k x 2"}
+             "plain_400k_8d": "400k x 8", "plain_20k_2d": "20k x 2",
+             "plain_5p8m_3d_dense": "5.8M x 3, d_cut x 4"}
 
 
 def metric_for(args) -> str:

@@ -266,6 +266,14 @@ dpc_status dpc_set_profiling(dpc_ctx* ctx, int on);
  *             warp per work item like the larger cells, 0 .. 2^31 (default
  *             512; high-dimensional sets have small cells facing thousands of
  *             candidates)
+ *   "sapprox_path"  dpc_sapprox: 1 the all-point path (the density kernels
+ *             for every point, the ring search over pick ranks, a
+ *             first-phase scan for the picks it leaves), 2 the pick path
+ *             (one warp per pick for the density and the first-phase scan),
+ *             0 chosen by the candidate pairs (default 0)
+ *   "sapprox_ratio"  with sapprox_path 0: the pick path when the points'
+ *             candidate pairs exceed this many times the picks', 1 .. 1024
+ *             (default 16)
  *   "max_batch_jobs"  served mode: jobs one batch admits at most, 1 .. 4096
  *             (default 64; 1 runs the jobs one at a time)
  * DPC_ERR_INVALID_ARG for an unknown key or a value out of range. */

@@ -125,6 +125,8 @@ struct Tune {
     int hd_min_d = 7;
     int ring2 = 0;            // second ring (cells at distance 2) before the tree search
     int sparse_cand = 512;    // cells of at most 4 points with more candidates than this take the dense path
+    int sapprox_path = 0;     // S-Approx-DPC: 0 by the pair counts, 1 all points, 2 picks only
+    int sapprox_ratio = 16;   // S-Approx-DPC: the pick path when the points' pairs exceed this many times the picks'
 };
 
 }  // namespace
@@ -249,7 +251,7 @@ struct Batch {
     DsDesc* d_desc = nullptr;
     bool has_density = false, has_rank = false;
     int dep_kind = 0;  // dependent points held: 0 none, 1 exact, 2 Approx-DPC, 3 S-Approx-DPC
-    int64_t npicks = 0, nsecond = 0, sap_pairs = 0;  // S-Approx-DPC counters
+    int64_t npicks = 0, nsecond = 0, sap_pairs = 0, pick_pairs = 0;  // S-Approx-DPC counters
     int grid_key_bits = 0, rank_key_bits = 0;
     int32_t* rho_pub = nullptr;  // S-Approx-DPC: rho as reported (-1 where not picked)
     uint32_t class_mask = 0, dim_mask = 0;
@@ -985,22 +987,35 @@ struct Batch {
         DPC_CK(tmp.get(&sb.npicks, 1));
         DPC_CK(tmp.get(&sb.scan, N));
         DPC_CK(tmp.get(&sb.nscan, 1));
-        DPC_CK(tmp.get(&sb.stats, 2));
+        DPC_CK(tmp.get(&sb.stats, 3));
         DPC_CK(keep.get(&v.pick, N));
         DPC_CK(cudaMemsetAsync(sb.npicks, 0, sizeof(uint32_t), st));
         DPC_CK(cudaMemsetAsync(sb.nscan, 0, sizeof(uint32_t), st));
-        DPC_CK(cudaMemsetAsync(sb.stats, 0, 2 * sizeof(unsigned long long), st));
+        DPC_CK(cudaMemsetAsync(sb.stats, 0, 3 * sizeof(unsigned long long), st));
         DPC_CK(launch_sapprox_grid(v, sb, key_bits, bshift, temp, st));
+        DPC_CK(launch_sapprox_pick_pairs(v, w, sb, N, st));
         uint32_t m = 0;
+        unsigned long long cnt3[3] = {0, 0, 0}, allp[2] = {0, 0};
         DPC_CK(cudaMemcpyAsync(&m, sb.npicks, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
+        DPC_CK(cudaMemcpyAsync(cnt3, sb.stats, sizeof(cnt3), cudaMemcpyDeviceToHost, st));
+        DPC_CK(cudaMemcpyAsync(allp, d_stats, sizeof(allp), cudaMemcpyDeviceToHost, st));
         DPC_TRY(sync("S-Approx-DPC grid"));
         npicks = m;
+        pick_pairs = (int64_t)cnt3[2];
+        const int64_t all_pairs = (int64_t)(allp[0] + allp[1]);
         mark(7);
 
         // densities of the picks; the others get 0 and rank after every
-        // pick. With picks a quarter of the points or more, the dense
-        // all-point kernels cost less than a pass over the picks alone.
-        const bool all_points = 4 * npicks >= N;
+        // pick. The all-point path (dense density kernels, then the ring
+        // search over pick ranks) evaluates all_pairs candidate pairs twice
+        // at a low cost per pair; the pick path (one warp per pick for the
+        // density and for the first-phase scan) evaluates pick_pairs twice
+        // at about ten times that cost, and both carry fixed costs per point
+        // (grid, ranks, the searches for open points). Measured crossovers
+        // in all_pairs / pick_pairs: about 4 (1M x 8), 15 (5.8M x 3 with
+        // mean rho in the thousands), 50 (5.8M x 3, mean rho 100).
+        const bool all_points = tune.sapprox_path == 1 ||
+                                (tune.sapprox_path == 0 && pick_pairs * (int64_t)tune.sapprox_ratio >= all_pairs);
         if (all_points) {
             DPC_TRY(rho_all());
             DPC_CK(launch_sapprox_mask(v, st));
@@ -1015,11 +1030,14 @@ struct Batch {
         mark(5);
 
         // nearest higher pick of every point's searched block (the exact
-        // ring search over pick ranks), the first phase, then the second
-        // phase for the picks it leaves open
+        // ring search over pick ranks, when picks are many), the first
+        // phase, then the second phase for the picks it leaves open
         DPC_CK(tmp.get(&v.best_s, N));
         DPC_CK(cudaMemsetAsync(v.best_s, 0xff, sizeof(unsigned long long) * std::max<int64_t>(N, 1), st));
-        DPC_CK(launch_ring(v, w, class_mask, nitems, nsparse, d_counters + 32, st));
+        // with few picks every pick scans its own neighbourhood instead (the
+        // scan keeps the block's nearest higher pick too): the cost follows
+        // the picks, not the points
+        if (all_points) DPC_CK(launch_ring(v, w, class_mask, nitems, nsparse, d_counters + 32, st));
         DPC_CK(tmp.get(&db.ucount, 4));
         DPC_CK(tmp.get(&db.tree_list, N));
         DPC_CK(tmp.get(&db.bf_list, N));
@@ -1156,6 +1174,8 @@ dpc_status dpc_set_tuning(dpc_ctx* ctx, const char* key, int64_t value) {
     else if (k == "hd_cell_factor" && value >= 1 && value <= 3) t.hd_cell_factor = (int)value;
     else if (k == "hd_min_d" && value >= 1 && value <= 9) t.hd_min_d = (int)value;
     else if (k == "ring2" && value >= 0 && value <= 1) t.ring2 = (int)value;
+    else if (k == "sapprox_path" && value >= 0 && value <= 2) t.sapprox_path = (int)value;
+    else if (k == "sapprox_ratio" && value >= 1 && value <= 1024) t.sapprox_ratio = (int)value;
     else if (k == "sparse_cand" && value >= 0 && value <= (1ll << 31)) t.sparse_cand = (int)std::min<int64_t>(value, INT32_MAX);
     else if (k == "max_batch_jobs" && value >= 1 && value <= 4096) {
         std::lock_guard<std::mutex> lk(ctx->mu);
@@ -1178,6 +1198,8 @@ dpc_status dpc_get_tuning(dpc_ctx* ctx, const char* key, int64_t* value) {
     else if (k == "hd_min_d") *value = t.hd_min_d;
     else if (k == "ring2") *value = t.ring2;
     else if (k == "sparse_cand") *value = t.sparse_cand;
+    else if (k == "sapprox_path") *value = t.sapprox_path;
+    else if (k == "sapprox_ratio") *value = t.sapprox_ratio;
     else if (k == "max_batch_jobs") {
         std::lock_guard<std::mutex> lk(ctx->mu);
         *value = ctx->max_batch_jobs;

@@ -17,15 +17,17 @@
 //  - first phase: the cells of G' (other than its own) holding a point
 //    strictly within d_cut of a pick form N(c); among their picks that rank
 //    higher, the nearest (ties to the smaller index) is the dependent point,
-//    at its exact distance. When the nearest higher pick of the pick's
-//    searched block of exact-grid cells (the ring search) lies strictly
+//    at its exact distance. With picks a quarter of the points or more, the
+//    exact ring search over pick ranks runs first: when the nearest higher
+//    pick of a pick's searched block of exact-grid cells lies strictly
 //    within d_cut, it is the nearest higher pick overall and belongs to
-//    N(c), so it is the first-phase answer; only the other picks scan
-//    their neighbourhood for N(c);
+//    N(c), so it is the first-phase answer, and only the other picks scan
+//    their neighbourhood for N(c). With fewer picks every pick scans (the
+//    cost then follows the picks, not the points);
 //  - second phase, for a pick without a first-phase candidate: its nearest
-//    higher pick over all picks, the ring result when it lies strictly
-//    closer than the outside of the searched block, else the tree search or
-//    the brute force;
+//    higher pick over all picks: the nearest higher pick of the searched
+//    block (kept by the scan, or the ring's) when it lies strictly closer
+//    than the outside of the block, else the tree search or the brute force;
 //  - a point that is not picked depends on its cell's pick, at its exact
 //    distance.
 #include "stages.cuh"
@@ -91,6 +93,17 @@ __global__ void k_sap_pick_of(BatchView v, SapproxBufs sb, int64_t n) {
     const uint32_t g = sb.ord[t];
     sb.pick_s[v.pos_of[g]] = sb.picks[c];
     v.pick[g] = (uint8_t)f;
+}
+
+// Candidate pairs a pass over the picks alone would evaluate: the sum over
+// picks of their exact-grid cell's candidates.
+__global__ void k_sap_pick_pairs(BatchView v, CellWork w, SapproxBufs sb) {
+    const uint32_t m = *sb.npicks;
+    unsigned long long s = 0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x)
+        s += w.cand[v.cell_of[sb.picks[i]]];
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) == 0 && s) atomicAdd(&sb.stats[2], s);
 }
 
 template <int D>
@@ -254,16 +267,20 @@ __global__ void __launch_bounds__(128) k_sap_first(BatchView v, CellWork w, Sapp
         const uint32_t e = v.cell_of[p];
         const uint2* runs = w.runs + (int64_t)e * w.nbs;
         const uint32_t nr = w.nruns[e];
-        long long fd = INT64_MAX;
-        uint32_t fj = 0xffffffffu;
+        long long fd = INT64_MAX, bd = INT64_MAX;
+        uint32_t fj = 0xffffffffu, bj = 0xffffffffu;
         for (uint32_t ri = 0; ri < nr; ++ri) {
             const uint2 run = runs[ri];
             for (uint32_t q = run.x + lane; q < run.x + run.y; q += 32) {
                 int32_t y[D];
                 sx_load<D>(recb + (int64_t)q * DP, y);
-                if (sx_dist<D>(x, y) >= ds.d_cut2) continue;
+                const long long dq = sx_dist<D>(x, y);
                 const uint32_t k = sb.pick_s[q];
-                if (k == p) continue;
+                if (k == q) {  // a pick: the nearest higher one of the block, for the second phase
+                    const uint2 cr = v.ro_s[q];
+                    if (cr.x < ro.x) keep_min(bd, bj, dq, cr.y);
+                }
+                if (dq >= ds.d_cut2 || k == p) continue;
                 const uint2 kr = v.ro_s[k];
                 if (kr.x >= ro.x) continue;
                 int32_t z[D];
@@ -275,6 +292,9 @@ __global__ void __launch_bounds__(128) k_sap_first(BatchView v, CellWork w, Sapp
             const long long f2 = __shfl_xor_sync(0xffffffffu, fd, o);
             const uint32_t fj2 = __shfl_xor_sync(0xffffffffu, fj, o);
             keep_min(fd, fj, f2, fj2);
+            const long long b2 = __shfl_xor_sync(0xffffffffu, bd, o);
+            const uint32_t bj2 = __shfl_xor_sync(0xffffffffu, bj, o);
+            keep_min(bd, bj, b2, bj2);
         }
         if (lane != 0) continue;
         if (fj != 0xffffffffu) {
@@ -282,17 +302,24 @@ __global__ void __launch_bounds__(128) k_sap_first(BatchView v, CellWork w, Sapp
             v.delta2[g] = fd;
             continue;
         }
-        // second phase: the ring result, when proven, else the exact passes
+        // second phase: the nearest higher pick of the searched block (this
+        // scan's, or the ring search's when it ran), when proven, else the
+        // exact passes
         atomicAdd(&sb.stats[1], 1ull);
         const unsigned long long bk = v.best_s[p];
-        const uint32_t bd = (uint32_t)(bk >> 32);
+        if (bk != ~0ull && (uint32_t)(bk >> 32) != 0xffffffffu)
+            keep_min(bd, bj, (long long)(bk >> 32), (uint32_t)bk);
         const int64_t bound = block_bound(ds, recb + (int64_t)p * DP);
-        const bool proven = bk != ~0ull && bd != 0xffffffffu &&
-                            (bound == INT64_MAX || (bound < 3037000499ll && (int64_t)bd < bound * bound));
+        const bool proven = bj != 0xffffffffu &&
+                            (bound == INT64_MAX || (bound < 3037000499ll && bd < bound * bound));
         if (proven) {
-            v.dep[g] = (int32_t)(uint32_t)bk;
-            v.delta2[g] = (int64_t)bd;
-        } else if (ro.x < db.bf_rank) {
+            v.dep[g] = (int32_t)bj;
+            v.delta2[g] = bd;
+            continue;
+        }
+        // the unproven best is a valid start for the tree search
+        if (bd < 0xffffffffll) v.best_s[p] = ((unsigned long long)bd << 32) | bj;
+        if (ro.x < db.bf_rank) {
             db.bf_list[atomicAdd(&db.ucount[1], 1u)] = p;
         } else {
             db.tree_list[atomicAdd(&db.ucount[0], 1u)] = p;
@@ -340,6 +367,14 @@ cudaError_t launch_sapprox_grid(const BatchView& v, const SapproxBufs& sb, int k
     if (e != cudaSuccess) return e;
     (k_sap_picks<<<grid_for(N, 256), 256, 0, st>>>(v, s2, N), note_launch());
     (k_sap_pick_of<<<grid_for(N, 256), 256, 0, st>>>(v, s2, N), note_launch());
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sapprox_pick_pairs(const BatchView& v, const CellWork& w, const SapproxBufs& sb,
+                                     int64_t picks_bound, cudaStream_t st) {
+    if (v.N == 0 || picks_bound <= 0) return cudaSuccess;
+    const unsigned blocks = (unsigned)std::min<int64_t>(152 * 8, grid_for(picks_bound, 256));
+    (k_sap_pick_pairs<<<blocks, 256, 0, st>>>(v, w, sb), note_launch());
     return cudaGetLastError();
 }
 

@@ -347,11 +347,15 @@ struct SapproxBufs {
     uint32_t* npicks;     // device scalar: cells of G'
     uint32_t* scan;       // [N] picks that scan their neighbourhood for the first phase
     uint32_t* nscan;      // device scalar: their count
-    unsigned long long* stats;  // [2] pairs the pick-only density pass evaluates; picks reaching the second phase
+    unsigned long long* stats;  // [3] pairs the pick-only density pass evaluates; picks reaching the second
+                                //     phase; candidate pairs of the picks (before choosing the path)
 };
 // key_bits: width of the key of G'; bshift: bit offset of the dataset index
 cudaError_t launch_sapprox_grid(const BatchView& v, const SapproxBufs& sb, int key_bits, int bshift, void* temp,
                                 cudaStream_t st);
+// sb.stats[2] += the candidate pairs of the picks' exact-grid cells
+cudaError_t launch_sapprox_pick_pairs(const BatchView& v, const CellWork& w, const SapproxBufs& sb,
+                                     int64_t picks_bound, cudaStream_t st);
 cudaError_t launch_sapprox_rho(const BatchView& v, const CellWork& w, const SapproxBufs& sb, uint32_t dim_mask,
                                int64_t picks_bound, cudaStream_t st);
 // rho 0 for the points that are not picked (they rank after every pick)

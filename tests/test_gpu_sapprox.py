@@ -238,12 +238,22 @@ def test_plain_1m_8d_sampled(dpc):
     check_sampled(dpc, workloads.plain_1m_8d(), (1, 5), 600, 52)
 
 
-def test_both_density_passes(dpc):
-    """Few picks (a quarter of the points or less): the pick-only density
-    pass; many picks: the all-point density kernels, masked."""
+def test_both_paths_by_pair_counts(dpc):
+    """Few picks facing many candidates: the pick path (no all-point density
+    pairs); many picks: the all-point path."""
     few = workloads.random_blobs(8, 5000, 2, 30, domain=1000, blobs=3, spread=0.2, dup=50)
     info = check_full(dpc, few.points, 30, (3, 1), [(2, 31)])
-    assert 4 * info["picks"] < few.n and info["dense_pairs"] == 0
+    assert info["dense_pairs"] == 0
     many = workloads.random_blobs(1, 2000, 2, 1000, domain=100000, blobs=4, spread=0.05)
     info = check_full(dpc, many.points, 1000, (1, 5), [(2, 1001)])
-    assert 4 * info["picks"] >= many.n
+    assert info["dense_pairs"] > 0
+
+
+@pytest.mark.parametrize("path", [1, 2])
+@pytest.mark.parametrize("shape", [SHAPES[i] for i in (1, 3, 5, 6, 7, 9, 10)], ids=lambda s: f"n{s[1]}_d{s[2]}_dc{s[3]}")
+def test_forced_paths(dpc, shape, path):
+    """Either path on any data gives the oracle's bits."""
+    seed, n, d, dc, dom, blobs, spread, dup = shape
+    ds = workloads.random_blobs(seed, n, d, dc, domain=dom, blobs=blobs, spread=spread, dup=dup)
+    for eps in [(4, 5), (3, 1)]:
+        check_full(dpc, ds.points, dc, eps, [(2, dc + 1), (1, 3 * dc + 1)], knobs={"sapprox_path": path})

@@ -164,6 +164,16 @@ def plain_2m_3d(seed: int = 2, n: int = 2_000_000) -> Dataset:
     return Dataset("plain_2m_3d", pts, d_cut, 10, 10 * d_cut, seed=seed)
 
 
+def plain_5p8m_3d_dense(seed: int = 2, n: int = 5_800_000) -> Dataset:
+    """The 5.8M x 3 set with a cutoff 4 times larger (mean rho about 64
+    times larger, several thousand): the dense regime in which S-Approx-DPC's
+    cells of G' hold many points each, as on the paper's data sets;
+    rho_min and delta_min scale with it."""
+    base = plain_5p8m_3d(seed, n)
+    d_cut = 4 * base.d_cut
+    return Dataset("plain_5p8m_3d_dense", base.points, d_cut, 640, 10 * d_cut, seed=seed)
+
+
 def _c3_draw(seed: int, n: int):
     rng = np.random.default_rng(seed)
     centers = rng.uniform(10_000, 90_000, size=(20, 8))
@@ -281,4 +291,5 @@ NAMED = {
     "plain_2m_3d": plain_2m_3d,
     "plain_1m_8d": plain_1m_8d,
     "plain_400k_8d": plain_400k_8d,
+    "plain_5p8m_3d_dense": plain_5p8m_3d_dense,
 }
