@@ -1044,7 +1044,14 @@ struct Batch {
         DPC_CK(cudaMemsetAsync(db.ucount, 0, 4 * sizeof(uint32_t), st));
         db.tcount = db.ucount;
         db.bf_rank = tune.bf_rank;
-        DPC_CK(launch_sapprox_first(v, w, sb, db, dim_mask, npicks, npicks, st));
+        if (!all_points) {
+            DPC_CK(tmp.get(&sb.pflag, N));
+            DPC_CK(tmp.get(&sb.ppos, N));
+            DPC_CK(tmp.get(&sb.plist, N));
+            DPC_CK(tmp.get(&sb.pstart, ncells + 1));
+            DPC_CK(launch_sapprox_plist(v, sb, ncells, temp, st));
+        }
+        DPC_CK(launch_sapprox_first(v, w, sb, db, dim_mask, npicks, npicks, !all_points, st));
         DPC_TRY(open_points(tmp, "S-Approx-DPC first phase", false));
         mark(6);
         DPC_CK(keep.get(&rho_pub, N));

@@ -22,8 +22,10 @@
 //    pick of a pick's searched block of exact-grid cells lies strictly
 //    within d_cut, it is the nearest higher pick overall and belongs to
 //    N(c), so it is the first-phase answer, and only the other picks scan
-//    their neighbourhood for N(c). With fewer picks every pick scans (the
-//    cost then follows the picks, not the points);
+//    their neighbourhood for N(c). With fewer picks a pass over the picks of
+//    each pick's block (no other points' records read) gives the same
+//    nearest higher pick of the block, and the cost follows the picks, not
+//    the points;
 //  - second phase, for a pick without a first-phase candidate: its nearest
 //    higher pick over all picks: the nearest higher pick of the searched
 //    block (kept by the scan, or the ring's) when it lies strictly closer
@@ -93,6 +95,21 @@ __global__ void k_sap_pick_of(BatchView v, SapproxBufs sb, int64_t n) {
     const uint32_t g = sb.ord[t];
     sb.pick_s[v.pos_of[g]] = sb.picks[c];
     v.pick[g] = (uint8_t)f;
+}
+
+// Picks of every exact-grid cell, contiguous: plist holds the picks in
+// sorted order, pstart[c] .. pstart[c + 1] those of cell c (pos is the
+// exclusive count of picks before each sorted position).
+__global__ void k_sap_pflag(BatchView v, SapproxBufs sb) {
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p < v.N) sb.pflag[p] = sb.pick_s[p] == (uint32_t)p ? 1u : 0u;
+}
+
+__global__ void k_sap_plist(BatchView v, SapproxBufs sb, int64_t ncells) {
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p < v.N && sb.pflag[p]) sb.plist[sb.ppos[p]] = (uint32_t)p;
+    if (p < ncells) sb.pstart[p] = sb.ppos[v.cell_start[p]];
+    if (p == 0) sb.pstart[ncells] = *sb.npicks;
 }
 
 // Candidate pairs a pass over the picks alone would evaluate: the sum over
@@ -245,6 +262,67 @@ __global__ void k_sap_resolve(BatchView v, SapproxBufs sb) {
     sb.scan[atomicAdd(&sb.nscan[0], 1u)] = p;
 }
 
+// Pick path, every pick, one warp each: the nearest higher pick among the
+// picks of its searched block (through the cells' pick lists: only the
+// picks' own records are read). When
+// it lies strictly within d_cut it is the nearest higher pick overall and
+// belongs to N(c): the first-phase answer. Otherwise it is kept for the
+// second phase and the pick queues for the full first-phase scan.
+template <int D>
+__global__ void __launch_bounds__(128) k_sap_near(BatchView v, CellWork w, SapproxBufs sb) {
+    constexpr int DP = D <= 4 ? 1 : 2;
+    const uint32_t m = *sb.npicks;
+    const int lane = threadIdx.x & 31;
+    const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t i = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); i < m; i += nwarps) {
+        const uint32_t p = sb.picks[i];
+        const DsDesc& ds = v.desc[find_ds(v.pt_off, v.B, p)];
+        if (ds.d != D) continue;
+        const uint2 ro = v.ro_s[p];
+        const int64_t g = ds.pt_off + ro.y;
+        if (ro.x == 0u) {  // the densest pick
+            if (lane == 0) {
+                v.dep[g] = -1;
+                v.delta2[g] = INT64_MAX;
+            }
+            continue;
+        }
+        const int4* recb = v.rec + ds.rec_off - ds.pt_off * DP;
+        int32_t x[D];
+        sx_load<D>(recb + (int64_t)p * DP, x);
+        const uint32_t e = v.cell_of[p];
+        const uint2* runs = w.runs + (int64_t)e * w.nbs;
+        const uint32_t nr = w.nruns[e];
+        long long bd = INT64_MAX;
+        uint32_t bj = 0xffffffffu;
+        for (uint32_t ri = 0; ri < nr; ++ri) {
+            // the picks of the run's cell (a run is one whole cell)
+            const uint32_t c = v.cell_of[runs[ri].x];
+            for (uint32_t t = sb.pstart[c] + lane; t < sb.pstart[c + 1]; t += 32) {
+                const uint32_t q = sb.plist[t];
+                const uint2 cr = v.ro_s[q];
+                if (cr.x >= ro.x) continue;
+                int32_t y[D];
+                sx_load<D>(recb + (int64_t)q * DP, y);
+                keep_min(bd, bj, sx_dist<D>(x, y), cr.y);
+            }
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            const long long b2 = __shfl_xor_sync(0xffffffffu, bd, o);
+            const uint32_t bj2 = __shfl_xor_sync(0xffffffffu, bj, o);
+            keep_min(bd, bj, b2, bj2);
+        }
+        if (lane != 0) continue;
+        if (bj != 0xffffffffu && bd < ds.d_cut2) {
+            v.dep[g] = (int32_t)bj;
+            v.delta2[g] = bd;
+            continue;
+        }
+        if (bd < 0xffffffffll) v.best_s[p] = ((unsigned long long)bd << 32) | bj;
+        sb.scan[atomicAdd(&sb.nscan[0], 1u)] = p;
+    }
+}
+
 // First phase for the queued picks: one warp per pick scans the neighbour
 // runs of its exact-grid cell for points strictly within d_cut in other
 // cells of G', and keeps the nearest of their cells' picks that rank
@@ -370,6 +448,16 @@ cudaError_t launch_sapprox_grid(const BatchView& v, const SapproxBufs& sb, int k
     return cudaGetLastError();
 }
 
+cudaError_t launch_sapprox_plist(const BatchView& v, const SapproxBufs& sb, int64_t ncells, void* temp,
+                                 cudaStream_t st) {
+    if (v.N == 0) return cudaSuccess;
+    (k_sap_pflag<<<grid_for(v.N, 256), 256, 0, st>>>(v, sb), note_launch());
+    cudaError_t e = exclusive_scan_u32(sb.pflag, sb.ppos, v.N, nullptr, temp, st);
+    if (e != cudaSuccess) return e;
+    (k_sap_plist<<<grid_for(std::max<int64_t>(v.N, ncells + 1), 256), 256, 0, st>>>(v, sb, ncells), note_launch());
+    return cudaGetLastError();
+}
+
 cudaError_t launch_sapprox_pick_pairs(const BatchView& v, const CellWork& w, const SapproxBufs& sb,
                                      int64_t picks_bound, cudaStream_t st) {
     if (v.N == 0 || picks_bound <= 0) return cudaSuccess;
@@ -397,10 +485,20 @@ cudaError_t launch_sapprox_mask(const BatchView& v, cudaStream_t st) {
 }
 
 cudaError_t launch_sapprox_first(const BatchView& v, const CellWork& w, const SapproxBufs& sb, const DeltaBufs& db,
-                                 uint32_t dim_mask, int64_t picks_bound, int64_t scan_bound, cudaStream_t st) {
+                                 uint32_t dim_mask, int64_t picks_bound, int64_t scan_bound, bool near_pass,
+                                 cudaStream_t st) {
     if (v.N == 0) return cudaSuccess;
     (k_sap_follow<<<grid_for(v.N, 256), 256, 0, st>>>(v, sb), note_launch());
-    (k_sap_resolve<<<grid_for(std::max<int64_t>(picks_bound, 1), 256), 256, 0, st>>>(v, sb), note_launch());
+    if (near_pass) {
+        const unsigned nb = warp_blocks(picks_bound);
+#define DPC_SAP_NEAR(D) \
+    if (dim_mask & (1u << (D - 1))) (k_sap_near<D><<<nb, 128, 0, st>>>(v, w, sb), note_launch());
+        DPC_SAP_NEAR(1) DPC_SAP_NEAR(2) DPC_SAP_NEAR(3) DPC_SAP_NEAR(4)
+        DPC_SAP_NEAR(5) DPC_SAP_NEAR(6) DPC_SAP_NEAR(7) DPC_SAP_NEAR(8)
+#undef DPC_SAP_NEAR
+    } else {
+        (k_sap_resolve<<<grid_for(std::max<int64_t>(picks_bound, 1), 256), 256, 0, st>>>(v, sb), note_launch());
+    }
     const unsigned blocks = warp_blocks(scan_bound);
 #define DPC_SAP_FIRST(D) \
     if (dim_mask & (1u << (D - 1))) (k_sap_first<D><<<blocks, 128, 0, st>>>(v, w, sb, db), note_launch());

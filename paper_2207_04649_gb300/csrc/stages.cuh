@@ -345,6 +345,10 @@ struct SapproxBufs {
     uint32_t* picks;      // [N] sorted position of the pick of every cell of G'
     uint32_t* pick_s;     // [N] sorted position -> sorted position of its cell's pick
     uint32_t* npicks;     // device scalar: cells of G'
+    uint32_t* pflag;      // [N] pick path: 1 at the sorted position of a pick
+    uint32_t* ppos;       // [N] pick path: exclusive scan of pflag
+    uint32_t* plist;      // [N] pick path: the picks in sorted order (each cell's together)
+    uint32_t* pstart;     // [ncells + 1] pick path: first entry of every exact-grid cell in plist
     uint32_t* scan;       // [N] picks that scan their neighbourhood for the first phase
     uint32_t* nscan;      // device scalar: their count
     unsigned long long* stats;  // [3] pairs the pick-only density pass evaluates; picks reaching the second
@@ -353,6 +357,9 @@ struct SapproxBufs {
 // key_bits: width of the key of G'; bshift: bit offset of the dataset index
 cudaError_t launch_sapprox_grid(const BatchView& v, const SapproxBufs& sb, int key_bits, int bshift, void* temp,
                                 cudaStream_t st);
+// The picks of every exact-grid cell (plist, pstart), for the pick path
+cudaError_t launch_sapprox_plist(const BatchView& v, const SapproxBufs& sb, int64_t ncells, void* temp,
+                                 cudaStream_t st);
 // sb.stats[2] += the candidate pairs of the picks' exact-grid cells
 cudaError_t launch_sapprox_pick_pairs(const BatchView& v, const CellWork& w, const SapproxBufs& sb,
                                      int64_t picks_bound, cudaStream_t st);
@@ -362,8 +369,10 @@ cudaError_t launch_sapprox_rho(const BatchView& v, const CellWork& w, const Sapp
 cudaError_t launch_sapprox_mask(const BatchView& v, cudaStream_t st);
 // after the rank and the ring search: the points that are not picked, then
 // the picks (resolved from the ring result or queued), then the first-phase scan
+// near_pass: the pick path's pass over the picks of each block (no ring search ran)
 cudaError_t launch_sapprox_first(const BatchView& v, const CellWork& w, const SapproxBufs& sb, const DeltaBufs& db,
-                                 uint32_t dim_mask, int64_t picks_bound, int64_t scan_bound, cudaStream_t st);
+                                 uint32_t dim_mask, int64_t picks_bound, int64_t scan_bound, bool near_pass,
+                                 cudaStream_t st);
 cudaError_t launch_sapprox_rho_out(const BatchView& v, int32_t* out, cudaStream_t st);
 
 // label.cu

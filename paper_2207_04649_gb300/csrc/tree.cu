@@ -117,44 +117,103 @@ __device__ __forceinline__ int64_t rec_of(const DeltaBufs& db, int32_t ref) {
     return ref >= 0 ? (int64_t)ref : db.ncells + (int64_t)(~ref);
 }
 
-// Leaf records, then a bottom-up refit: the second child to arrive at a node
-// writes the node's record.
-__global__ void k_refit(BatchView v, DeltaBufs db) {
-    const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= db.ncells) return;
+// Leaf records: every cell's box, smallest rank and point run. A lane takes
+// a cell of at most kLeafLane points; larger cells (dense data) are taken by
+// the whole warp, the lanes striding the points.
+constexpr uint32_t kLeafLane = 64;
+
+__device__ __forceinline__ void write_leaf(const DeltaBufs& db, int64_t c, const int32_t (&lo)[8],
+                                           const int32_t (&hi)[8], uint32_t mr, uint32_t p0, uint32_t p1) {
     const int dpb = db.dpb, ns = 2 * dpb + 1;
-    const int b = find_off(db.cell_off, v.B, c);
-    const DsDesc& ds = v.desc[b];
-    int32_t lo[8], hi[8];
-#pragma unroll
-    for (int k = 0; k < 8; ++k) {
-        lo[k] = INT32_MAX;
-        hi[k] = INT32_MIN;
-    }
-    uint32_t mr = 0xffffffffu;
-    const uint32_t p0 = v.cell_start[c], p1 = v.cell_start[c + 1];
-    // a point-tree dataset's single cell stays empty here (its points are
-    // never searched through this tree)
-    for (uint32_t p = p0; p < p1 && !ds.ptree; ++p) {
-        const int4* r = v.rec + ds.rec_off + ((int64_t)p - ds.pt_off) * ds.dp;
-        const int4 a = r[0];
-        const int4 e = ds.dp == 2 ? r[1] : make_int4(0, 0, 0, 0);
-        const int32_t x[8] = {a.x, a.y, a.z, a.w, e.x, e.y, e.z, e.w};
-#pragma unroll
-        for (int k = 0; k < 8; ++k) {
-            lo[k] = min(lo[k], x[k]);
-            hi[k] = max(hi[k], x[k]);
-        }
-        mr = min(mr, v.ro_s[p].x);
-    }
-    const int32_t lpar = db.lparent[c];
     int4* lr = db.nodes + (db.ncells + c) * ns;
     lr[0] = make_int4(lo[0], lo[1], lo[2], lo[3]);
     if (dpb == 2) lr[1] = make_int4(lo[4], lo[5], lo[6], lo[7]);
     lr[dpb] = make_int4(hi[0], hi[1], hi[2], hi[3]);
     if (dpb == 2) lr[dpb + 1] = make_int4(hi[4], hi[5], hi[6], hi[7]);
-    lr[2 * dpb] = make_int4((int)mr, (int)p0, (int)p1, lpar);
-    int32_t node = lpar;
+    lr[2 * dpb] = make_int4((int)mr, (int)p0, (int)p1, db.lparent[c]);
+}
+
+__device__ __forceinline__ void leaf_add(const BatchView& v, const DsDesc& ds, uint32_t p, int32_t (&lo)[8],
+                                         int32_t (&hi)[8], uint32_t& mr) {
+    const int4* r = v.rec + ds.rec_off + ((int64_t)p - ds.pt_off) * ds.dp;
+    const int4 a = r[0];
+    const int4 e = ds.dp == 2 ? r[1] : make_int4(0, 0, 0, 0);
+    const int32_t x[8] = {a.x, a.y, a.z, a.w, e.x, e.y, e.z, e.w};
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        lo[k] = min(lo[k], x[k]);
+        hi[k] = max(hi[k], x[k]);
+    }
+    mr = min(mr, v.ro_s[p].x);
+}
+
+__global__ void k_leaves(BatchView v, DeltaBufs db) {
+    const int lane = threadIdx.x & 31;
+    const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t base = ((int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * 32; base < db.ncells;
+         base += nwarps * 32) {
+        const int64_t c = base + lane;
+        const bool valid = c < db.ncells;
+        int b = 0;
+        uint32_t p0 = 0, p1 = 0;
+        bool big = false, pt = false;
+        if (valid) {
+            b = find_off(db.cell_off, v.B, c);
+            p0 = v.cell_start[c];
+            p1 = v.cell_start[c + 1];
+            // a point-tree dataset's single cell stays empty here (its points
+            // are never searched through this tree)
+            pt = v.desc[b].ptree != 0;
+            big = !pt && p1 - p0 > kLeafLane;
+        }
+        if (valid && !big) {
+            const DsDesc& ds = v.desc[b];
+            int32_t lo[8], hi[8];
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                lo[k] = INT32_MAX;
+                hi[k] = INT32_MIN;
+            }
+            uint32_t mr = 0xffffffffu;
+            for (uint32_t p = p0; p < p1 && !pt; ++p) leaf_add(v, ds, p, lo, hi, mr);
+            write_leaf(db, c, lo, hi, mr, p0, p1);
+        }
+        unsigned bigm = __ballot_sync(0xffffffffu, big);
+        while (bigm) {
+            const int src = __ffs(bigm) - 1;
+            bigm &= bigm - 1u;
+            const int64_t cc = __shfl_sync(0xffffffffu, c, src);
+            const int bb = __shfl_sync(0xffffffffu, b, src);
+            const uint32_t q0 = __shfl_sync(0xffffffffu, p0, src), q1 = __shfl_sync(0xffffffffu, p1, src);
+            const DsDesc& ds = v.desc[bb];
+            int32_t lo[8], hi[8];
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                lo[k] = INT32_MAX;
+                hi[k] = INT32_MIN;
+            }
+            uint32_t mr = 0xffffffffu;
+            for (uint32_t p = q0 + lane; p < q1; p += 32) leaf_add(v, ds, p, lo, hi, mr);
+            for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+                for (int k = 0; k < 8; ++k) {
+                    lo[k] = min(lo[k], __shfl_xor_sync(0xffffffffu, lo[k], o));
+                    hi[k] = max(hi[k], __shfl_xor_sync(0xffffffffu, hi[k], o));
+                }
+                mr = min(mr, __shfl_xor_sync(0xffffffffu, mr, o));
+            }
+            if (lane == 0) write_leaf(db, cc, lo, hi, mr, q0, q1);
+        }
+    }
+}
+
+// Bottom-up refit from the leaf records: the second child to arrive at a
+// node writes the node's record.
+__global__ void k_refit(BatchView v, DeltaBufs db) {
+    const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= db.ncells) return;
+    const int dpb = db.dpb, ns = 2 * dpb + 1;
+    int32_t node = db.lparent[c];
     while (node >= 0) {
         __threadfence();
         if (atomicAdd(&db.flag[node], 1u) == 0u) return;
@@ -296,6 +355,7 @@ cudaError_t launch_tree_build(const BatchView& v, const DeltaBufs& db, cudaStrea
     (k_cell_ranges<<<grid_for(v.B + 1, 128), 128, 0, st>>>(v, db), note_launch());
     (k_cell_key<<<grid_for(db.ncells, 256), 256, 0, st>>>(v, db), note_launch());
     (k_radix_tree<<<grid_for(db.ncells, 256), 256, 0, st>>>(v, db), note_launch());
+    (k_leaves<<<(unsigned)std::min<int64_t>(152 * 16, grid_for(db.ncells, 256)), 256, 0, st>>>(v, db), note_launch());
     (k_refit<<<grid_for(db.ncells, 256), 256, 0, st>>>(v, db), note_launch());
     return cudaGetLastError();
 }
