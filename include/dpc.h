@@ -120,9 +120,8 @@ dpc_status dpc_dependent(dpc_ds* ds, int32_t* dep_out, int64_t* delta2_out);
  *   exact_out:  NULL or n uint8: 1 where the dependent point is exact.
  * Host or device memory, as for dpc_density's is_device. Later dpc_label
  * calls use these dependent points until dpc_dependent is called.
- * Errors: DPC_ERR_INVALID_ARG when the grid keys of the dataset need more
- * than 64 bits (sum over dims of the bits of span / side); DPC_ERR_STATE for
- * a dataset on the point tree (tree_min_d at or below its d). */
+ * Errors: DPC_ERR_STATE for a dataset on the point tree (tree_min_d at or
+ * below its d). */
 dpc_status dpc_dependent_approx(dpc_ds* ds, int32_t* dep_out, int64_t* delta2_out, uint8_t* exact_out);
 
 /* S-Approx-DPC (Section 5): local densities and dependent points of one
@@ -309,6 +308,11 @@ dpc_status dpc_probe_pair_rate(int device, int d, int mode, double* pairs_per_s,
  * admits waiting jobs as device memory (hbm_cap_bytes) and batch slots
  * (max_inflight) free up and runs them while earlier batches are still on
  * the device. Results are the same bits as running each dataset alone.
+ * A job's method picks the dependent points: exact (dpc_dependent),
+ * Approx-DPC (dpc_dependent_approx) or S-Approx-DPC (dpc_sapprox, whose rho
+ * is -1 where not picked); a batch holds jobs of one method, so dpc_flush
+ * runs the queued jobs as consecutive batches of equal method and the
+ * served mode starts a new batch where the method changes.
  * ------------------------------------------------------------------- */
 typedef struct {
     const int32_t* points;     /* n x d int32 row-major */
@@ -324,6 +328,10 @@ typedef struct {
     int32_t* label_out;        /* NULL or [n_queries * n], query-major */
     int64_t* n_centers_out;    /* NULL or [n_queries] */
     int32_t is_device;         /* 0: points and outputs in host memory; 1: in device memory */
+    int32_t method;            /* 0 exact (Definitions 2-3), 1 Approx-DPC (Section 4.3), 2 S-Approx-DPC (Section 5) */
+    int64_t eps_num, eps_den;  /* method 2: eps = eps_num / eps_den, 1 .. 2^20 each; ignored otherwise */
+    uint8_t* aux_out;          /* NULL or [n]: method 1, 1 where the dependent point is exact; method 2, 1 for
+                                  the picks; unused for method 0 */
 } dpc_job;
 
 typedef struct {

@@ -60,7 +60,10 @@ class DpcJob(ctypes.Structure):
                 ("d_cut", ctypes.c_int64), ("n_queries", ctypes.c_int32), ("rho_min", ctypes.c_void_p),
                 ("delta_min", ctypes.c_void_p), ("rho_out", ctypes.c_void_p), ("dep_out", ctypes.c_void_p),
                 ("delta2_out", ctypes.c_void_p), ("label_out", ctypes.c_void_p),
-                ("n_centers_out", ctypes.c_void_p), ("is_device", ctypes.c_int32)]
+                ("n_centers_out", ctypes.c_void_p), ("is_device", ctypes.c_int32), ("method", ctypes.c_int32),
+                ("eps_num", ctypes.c_int64), ("eps_den", ctypes.c_int64), ("aux_out", ctypes.c_void_p)]
+
+METHODS = {"exact": 0, "approx": 1, "sapprox": 2}
 
 
 class DpcResult(ctypes.Structure):
@@ -446,11 +449,13 @@ class Dataset:
 
 class Job:
     """One dataset + (rho_min, delta_min) queries for dpc_submit, with output
-    arrays allocated here (rho, dep, delta2, labels[q], n_centers[q]). Host
-    numpy points give host outputs; a CUDA tensor of points gives device
-    outputs (torch tensors on its device) and a device-memory job."""
+    arrays allocated here (rho, dep, delta2, labels[q], n_centers[q], and
+    aux: Approx-DPC's exact flags or S-Approx-DPC's picks). Host numpy points
+    give host outputs; a CUDA tensor of points gives device outputs (torch
+    tensors on its device) and a device-memory job. method: "exact",
+    "approx" or "sapprox" (with eps as for Context.sapprox)."""
 
-    def __init__(self, points, d_cut: int, queries):
+    def __init__(self, points, d_cut: int, queries, method: str = "exact", eps=(4, 5)):
         q = list(queries)
         self.rho_min = np.array([int(a) for a, _ in q], dtype=np.int64)
         self.delta_min = np.array([int(b) for _, b in q], dtype=np.int64)
@@ -466,6 +471,7 @@ class Job:
             self.dep = torch.empty(n, dtype=torch.int32, device=dev)
             self.delta2 = torch.empty(n, dtype=torch.int64, device=dev)
             self.label = torch.empty((len(q), n), dtype=torch.int32, device=dev)
+            self.aux = torch.empty(n, dtype=torch.uint8, device=dev)
             p = lambda a: ctypes.c_void_p(a.data_ptr() if a.numel() else 0)
             is_dev = 1
         else:
@@ -475,11 +481,17 @@ class Job:
             self.dep = np.empty(n, np.int32)
             self.delta2 = np.empty(n, np.int64)
             self.label = np.empty((len(q), n), np.int32)
+            self.aux = np.empty(n, np.uint8)
             p = lambda a: a.ctypes.data_as(ctypes.c_void_p)
             is_dev = 0
         h = lambda a: a.ctypes.data_as(ctypes.c_void_p)
+        if method not in METHODS:
+            raise ValueError(f"method must be one of {sorted(METHODS)}")
+        self.method = method
+        num, den = eps_fraction(eps)
         self.c = DpcJob(p(self.points), n, d, int(d_cut), len(q), h(self.rho_min), h(self.delta_min),
-                        p(self.rho), p(self.dep), p(self.delta2), p(self.label), h(self.n_centers), is_dev)
+                        p(self.rho), p(self.dep), p(self.delta2), p(self.label), h(self.n_centers), is_dev,
+                        METHODS[method], num, den, p(self.aux))
         self.ticket = None
 
 

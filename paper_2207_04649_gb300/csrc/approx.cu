@@ -22,27 +22,43 @@ namespace dpc {
 
 namespace {
 
-// Grid key of every sorted position: dataset key base + the cell
-// coordinates packed at their per-dimension bit offsets.
-__global__ void k_approx_keys(BatchView v, ApproxBufs ab) {
-    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= v.N) return;
+// Word w (bits [64 w, 64 w + 64)) of the grid key of sorted position p:
+// each cell coordinate at its per-dimension bit offset, the dataset's index
+// above them all at bshift (keys of any width, sorted 64 bits at a time).
+__device__ __forceinline__ uint64_t a_word(const BatchView& v, int64_t p, int w, int bshift) {
     const int b = find_ds(v.pt_off, v.B, p);
     const DsDesc& ds = v.desc[b];
     const int4* r = v.rec + ds.rec_off + (p - ds.pt_off) * ds.dp;
-    uint64_t key = ds.a_base;
-    for (int k = 0; k < ds.d; ++k) {
-        const uint32_t c = (uint32_t)(rec_coord(r, k) - ds.lo[k]) / (uint32_t)ds.a_side;
-        key |= (uint64_t)c << ds.a_shift[k];
-    }
-    ab.keys[p] = key;
-    ab.ord[p] = (uint32_t)p;
+    const int lo = 64 * w;
+    uint64_t word = 0;
+    auto put = [&](uint64_t c, int pos) {  // c < 2^31: bits [pos, pos + 31) of the key
+        if (pos >= lo + 64 || pos + 31 <= lo) return;
+        word |= pos >= lo ? c << (pos - lo) : c >> (lo - pos);
+    };
+    for (int k = 0; k < ds.d; ++k)
+        put((uint32_t)(rec_coord(r, k) - ds.lo[k]) / (uint32_t)ds.a_side, ds.a_shift[k]);
+    put((uint64_t)b, bshift);
+    return word;
 }
 
-__global__ void k_approx_flags(const uint64_t* __restrict__ skeys, uint32_t* __restrict__ flag, int64_t n) {
+// Word w of the key of the position at key-order index t (the first pass
+// takes the sorted positions in order).
+__global__ void k_approx_keys(BatchView v, const uint32_t* __restrict__ prev, uint64_t* __restrict__ keys,
+                              uint32_t* __restrict__ vals, int w, int bshift) {
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= n) return;
-    flag[t] = (t == 0 || skeys[t] != skeys[t - 1]) ? 1u : 0u;
+    if (t >= v.N) return;
+    const uint32_t p = prev ? prev[t] : (uint32_t)t;
+    keys[t] = a_word(v, p, w, bshift);
+    vals[t] = p;
+}
+
+__global__ void k_approx_flags(BatchView v, const uint32_t* __restrict__ ord, uint32_t* __restrict__ flag, int words,
+                               int bshift) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= v.N) return;
+    bool first = t == 0;
+    for (int w = 0; w < words && !first; ++w) first = a_word(v, ord[t], w, bshift) != a_word(v, ord[t - 1], w, bshift);
+    flag[t] = first ? 1u : 0u;
 }
 
 __global__ void k_approx_cells(ApproxBufs ab, int64_t n) {
@@ -259,16 +275,35 @@ __global__ void __launch_bounds__(128) k_approx_rule2_heavy(BatchView v, CellWor
 
 }  // namespace
 
-cudaError_t launch_approx_keys(const BatchView& v, const ApproxBufs& ab, cudaStream_t st) {
+cudaError_t launch_approx_keys(const BatchView& v, int key_bits, int bshift, uint64_t* keys, uint32_t* ords,
+                               void* temp, uint32_t** ord_out, cudaStream_t st) {
+    *ord_out = ords;
     if (v.N == 0) return cudaSuccess;
-    (k_approx_keys<<<grid_for(v.N, 256), 256, 0, st>>>(v, ab), note_launch());
+    // LSD over 64-bit words: each pass sorts the previous order stably by
+    // the next more significant word; the three value buffers rotate
+    const int words = std::max(1, (key_bits + 63) / 64);
+    const int64_t N = v.N;
+    uint64_t *kin = keys, *kout = keys + N, *ktmp = keys + 2 * N;
+    uint32_t *vin = ords + N, *vout = ords, *vtmp = ords + 2 * N;
+    const uint32_t* prev = nullptr;
+    for (int w = 0; w < words; ++w) {
+        const int nbits = std::max(1, std::min(64, key_bits - 64 * w));
+        (k_approx_keys<<<grid_for(N, 256), 256, 0, st>>>(v, prev, kin, vin, w, bshift), note_launch());
+        cudaError_t e = radix_sort_u64(kin, vin, kout, vout, ktmp, vtmp, N, nbits, temp, st);
+        if (e != cudaSuccess) return e;
+        prev = vout;
+        std::swap(vin, vout);
+        std::swap(vin, vtmp);
+    }
+    *ord_out = const_cast<uint32_t*>(prev);
     return cudaGetLastError();
 }
 
-cudaError_t launch_approx_cells(const BatchView& v, const CellWork& w, const ApproxBufs& ab, void* scan_temp,
-                                cudaStream_t st) {
+cudaError_t launch_approx_cells(const BatchView& v, const CellWork& w, const ApproxBufs& ab, int key_bits,
+                                int bshift, void* scan_temp, cudaStream_t st) {
     if (v.N == 0) return cudaSuccess;
-    (k_approx_flags<<<grid_for(v.N, 256), 256, 0, st>>>(ab.keys, ab.flag, v.N), note_launch());
+    const int words = std::max(1, (key_bits + 63) / 64);
+    (k_approx_flags<<<grid_for(v.N, 256), 256, 0, st>>>(v, ab.ord, ab.flag, words, bshift), note_launch());
     cudaError_t e = exclusive_scan_u32(ab.flag, ab.cidx, v.N, nullptr, scan_temp, st);
     if (e != cudaSuccess) return e;
     (k_approx_cells<<<grid_for(v.N, 256), 256, 0, st>>>(ab, v.N), note_launch());

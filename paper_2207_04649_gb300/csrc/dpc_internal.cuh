@@ -53,7 +53,6 @@ struct DsDesc {
     int32_t a_side;       // Approx-DPC grid: integer side max(1, floor(d_cut / sqrt(d)));
                           // S-Approx-DPC grid: max(1, floor(eps d_cut / sqrt(d))), at most 2^30
     int32_t a_shift[kMaxDims];  // Approx-DPC grid: bit offset of each dim's cell coordinate in the key
-    uint64_t a_base;      // Approx-DPC grid: key base of this dataset
     int32_t prune;        // 1: the neighbour runs may leave out in-reach cells whose box is at least
                           // d_cut away (no point there counts in rho, but one may be nearer than the
                           // searched block's outside for the dependent-point search)

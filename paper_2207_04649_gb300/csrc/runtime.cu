@@ -874,7 +874,9 @@ struct Batch {
         if (dep_kind == 2) return DPC_OK;
         if (dep_kind == 3) return fail(DPC_ERR_STATE, "an S-Approx-DPC dataset has densities of its picks only");
         if (!has_density) return fail(DPC_ERR_STATE, "dataset has no density");
-        unsigned __int128 abase = 0;
+        // keys: every dim's cell coordinate at its own bit offset, the
+        // dataset's index above them (any width: sorted 64 bits at a time)
+        int bshift = 0;
         for (int b = 0; b < B; ++b) {
             DsDesc& ds = hd[b];
             if (ds.ptree) return fail(DPC_ERR_STATE, "Approx-DPC needs the grid: set tree_min_d above the dimension");
@@ -888,12 +890,9 @@ struct Batch {
                 ds.a_shift[k] = off;
                 if (k < ds.d && ds.n > 0) off += bits_for((uint64_t)((ds.span[k] - 1) / ds.a_side));
             }
-            ds.a_base = (uint64_t)abase;
-            abase += (unsigned __int128)1 << std::min(off, 100);
-            if (abase > ((unsigned __int128)1 << 64))
-                return fail(DPC_ERR_INVALID_ARG, "Approx-DPC grid keys need more than 64 bits for this batch");
+            bshift = std::max(bshift, off);
         }
-        const int key_bits = std::max(1, bits_for((uint64_t)(abase - 1)));
+        const int key_bits = bshift + bits_for((uint64_t)(B - 1));
         DPC_TRY(upload_desc());
         mark(0);
         Arena tmp;
@@ -903,14 +902,10 @@ struct Batch {
         DPC_TRY(ensure_rank(tmp, temp));
         mark(1);
         ApproxBufs ab{};
-        uint64_t *k0 = nullptr, *k1 = nullptr, *k2 = nullptr;
-        uint32_t *o0 = nullptr, *o1 = nullptr, *o2 = nullptr;
-        DPC_CK(tmp.get(&k0, N));
-        DPC_CK(tmp.get(&k1, N));
-        DPC_CK(tmp.get(&k2, N));
-        DPC_CK(tmp.get(&o0, N));
-        DPC_CK(tmp.get(&o1, N));
-        DPC_CK(tmp.get(&o2, N));
+        uint64_t* kbuf = nullptr;
+        uint32_t* obuf = nullptr;
+        DPC_CK(tmp.get(&kbuf, 3 * a256(N)));
+        DPC_CK(tmp.get(&obuf, 3 * a256(N)));
         DPC_CK(tmp.get(&ab.flag, N));
         DPC_CK(tmp.get(&ab.cidx, N));
         DPC_CK(tmp.get(&ab.cell_of, N));
@@ -923,13 +918,8 @@ struct Batch {
         DPC_CK(tmp.get(&ab.nlh, 2));
         DPC_CK(cudaMemsetAsync(ab.ncells, 0, sizeof(uint32_t), st));
         DPC_CK(cudaMemsetAsync(ab.nlh, 0, 2 * sizeof(uint32_t), st));
-        ab.keys = k0;
-        ab.ord = o0;
-        DPC_CK(launch_approx_keys(v, ab, st));
-        DPC_CK(radix_sort_u64(k0, o0, k2, o2, k1, o1, N, key_bits, temp, st));
-        ab.keys = k2;
-        ab.ord = o2;
-        DPC_CK(launch_approx_cells(v, w, ab, temp, st));
+        DPC_CK(launch_approx_keys(v, key_bits, bshift, kbuf, obuf, temp, &ab.ord, st));
+        DPC_CK(launch_approx_cells(v, w, ab, key_bits, bshift, temp, st));
         DPC_CK(tmp.get(&v.best_s, N));
         DPC_CK(cudaMemsetAsync(v.best_s, 0xff, sizeof(unsigned long long) * std::max<int64_t>(N, 1), st));
         DPC_CK(tmp.get(&db.ucount, 4));
@@ -954,7 +944,8 @@ struct Batch {
     // ------------------------------------------------------ S-Approx-DPC
     // S-Approx-DPC (Section 5): see sapprox.cu. Its grid G' covers all d
     // dims like Approx-DPC's, with side max(1, floor(eps d_cut / sqrt(d))).
-    dpc_status sapprox(const std::vector<Input>& in, int64_t eps_num, int64_t eps_den) {
+    dpc_status sapprox(const std::vector<Input>& in, const std::vector<int64_t>& eps_num,
+                       const std::vector<int64_t>& eps_den) {
         DPC_TRY(build_grid(in));
         // key of G': every dim's cell coordinate at its own bit offset, the
         // dataset's index above them (any width: sorted 64 bits at a time)
@@ -963,7 +954,7 @@ struct Batch {
             DsDesc& ds = hd[b];
             if (ds.ptree)
                 return fail(DPC_ERR_STATE, "S-Approx-DPC needs the grid: set tree_min_d above the dimension");
-            ds.a_side = (int32_t)std::min<int64_t>(sapprox_side(ds.d_cut, ds.d, eps_num, eps_den), 1ll << 30);
+            ds.a_side = (int32_t)std::min<int64_t>(sapprox_side(ds.d_cut, ds.d, eps_num[b], eps_den[b]), 1ll << 30);
             int off = 0;
             for (int k = 0; k < kMaxDims; ++k) {
                 ds.a_shift[k] = off;
@@ -1258,7 +1249,7 @@ dpc_status dpc_sapprox(dpc_ctx* ctx, const int32_t* points, int64_t n, int32_t d
     auto b = std::make_shared<Batch>();
     b->ctx = ctx;
     std::vector<dpc::Input> in{{points, n, d, d_cut, is_device}};
-    DPC_TRY(b->sapprox(in, eps_num, eps_den));
+    DPC_TRY(b->sapprox(in, {eps_num}, {eps_den}));
     DPC_TRY(b->copy_out(rho_out, b->rho_pub, sizeof(int32_t) * n));
     DPC_TRY(b->copy_out(dep_out, b->v.dep, sizeof(int32_t) * n));
     DPC_TRY(b->copy_out(delta2_out, b->v.delta2, sizeof(int64_t) * n));
@@ -1434,8 +1425,9 @@ using JobPtr = std::shared_ptr<dpc_ctx::JobRec>;
 
 // Device bytes one job holds while it runs (points, sorted records, per-point
 // state, sort buffers, hash table), with slack.
-uint64_t job_bytes(int64_t n, int32_t d) {
-    return (uint64_t)n * (176 + 8 * (uint64_t)d) + (16ull << 20);
+uint64_t job_bytes(int64_t n, int32_t d, int32_t method) {
+    // the approximate methods add a second grid's sort buffers and lists
+    return (uint64_t)n * (176 + 8 * (uint64_t)d + (method != 0 ? 96 : 0)) + (16ull << 20);
 }
 
 // Run a group of jobs as one batch on stream st; fills their outputs.
@@ -1449,14 +1441,28 @@ dpc_status run_jobs(dpc_ctx* ctx, std::vector<JobPtr>& jobs, cudaStream_t st) {
         in.push_back({j->job.points, j->job.n, j->job.d, j->job.d_cut, j->job.is_device ? 1 : 0});
         maxq = std::max(maxq, j->job.n_queries);
     }
-    DPC_TRY(bt->density(in));
-    DPC_TRY(bt->dependent());
+    // one method per batch (the callers group the jobs)
+    const int method = jobs.empty() ? 0 : jobs[0]->job.method;
+    if (method == 2) {
+        std::vector<int64_t> en, ed;
+        for (auto& j : jobs) {
+            en.push_back(j->job.eps_num);
+            ed.push_back(j->job.eps_den);
+        }
+        DPC_TRY(bt->sapprox(in, en, ed));
+    } else {
+        DPC_TRY(bt->density(in));
+        if (method == 1) DPC_TRY(bt->dependent_approx());
+        else DPC_TRY(bt->dependent());
+    }
     for (size_t b = 0; b < jobs.size(); ++b) {
         const dpc_job& jb = jobs[b]->job;
         const DsDesc& h = bt->hd[b];
-        DPC_TRY(bt->copy_out(jb.rho_out, bt->v.rho + h.pt_off, sizeof(int32_t) * h.n));
+        DPC_TRY(bt->copy_out(jb.rho_out, (method == 2 ? bt->rho_pub : bt->v.rho) + h.pt_off, sizeof(int32_t) * h.n));
         DPC_TRY(bt->copy_out(jb.dep_out, bt->v.dep + h.pt_off, sizeof(int32_t) * h.n));
         DPC_TRY(bt->copy_out(jb.delta2_out, bt->v.delta2 + h.pt_off, sizeof(int64_t) * h.n));
+        if (method != 0)
+            DPC_TRY(bt->copy_out(jb.aux_out, (method == 2 ? bt->v.pick : bt->v.exact) + h.pt_off, h.n));
     }
     std::vector<int64_t> rmin(jobs.size()), dmin(jobs.size());
     std::vector<unsigned long long> nc(jobs.size());
@@ -1532,6 +1538,7 @@ void serve_loop(dpc_ctx* ctx) {
                 }
                 JobPtr j = it->second;
                 if (ctx->held_bytes + j->bytes > ctx->cap) break;
+                if (!group.empty() && j->job.method != group[0]->job.method) break;  // one method per batch
                 if (pts + j->job.n >= (1ll << 31) - 1) break;
                 ctx->waiting.pop_front();
                 ctx->held_bytes += j->bytes;
@@ -1559,6 +1566,9 @@ dpc_status check_job(const dpc_job* j) {
     for (int q = 0; q < j->n_queries; ++q)
         if (j->delta_min[q] <= j->d_cut || j->delta_min[q] > kMaxDeltaMin)
             return fail(DPC_ERR_INVALID_ARG, "delta_min must be in (d_cut, 3037000499]");
+    if (j->method < 0 || j->method > 2) return fail(DPC_ERR_INVALID_ARG, "method must be 0, 1 or 2");
+    if (j->method == 2 && (j->eps_num < 1 || j->eps_num > (1 << 20) || j->eps_den < 1 || j->eps_den > (1 << 20)))
+        return fail(DPC_ERR_INVALID_ARG, "eps_num and eps_den must be in [1, 2^20]");
     return DPC_OK;
 }
 
@@ -1574,7 +1584,7 @@ dpc_status dpc_submit(dpc_ctx* ctx, const dpc_job* job, uint64_t* ticket) {
     rec->job = *job;
     rec->rmin.assign(job->rho_min, job->rho_min + job->n_queries);
     rec->dmin.assign(job->delta_min, job->delta_min + job->n_queries);
-    rec->bytes = dpc::job_bytes(job->n, job->d);
+    rec->bytes = dpc::job_bytes(job->n, job->d, job->method);
     rec->t_submit = std::chrono::steady_clock::now();
     if (ctx->mode == 1 && rec->bytes > ctx->cap) return fail(DPC_ERR_CAPACITY, "job exceeds the memory cap");
     std::lock_guard<std::mutex> lk(ctx->mu);
@@ -1643,9 +1653,18 @@ dpc_status dpc_flush(dpc_ctx* ctx) {
     }
     if (group.empty()) return DPC_OK;
     cudaSetDevice(ctx->device);
-    dpc_status s = dpc::run_jobs(ctx, group, ctx->stream);
-    dpc::finish(ctx, group, s);
-    return s;
+    // consecutive runs of one method, each one batch
+    dpc_status first_err = DPC_OK;
+    for (size_t a = 0; a < group.size();) {
+        size_t e = a + 1;
+        while (e < group.size() && group[e]->job.method == group[a]->job.method) ++e;
+        std::vector<dpc::JobPtr> part(group.begin() + a, group.begin() + e);
+        const dpc_status s = dpc::run_jobs(ctx, part, ctx->stream);
+        dpc::finish(ctx, part, s);
+        if (s != DPC_OK && first_err == DPC_OK) first_err = s;
+        a = e;
+    }
+    return first_err;
 }
 
 dpc_status dpc_autotune(dpc_ctx* ctx, const dpc_job* jobs, int32_t n_jobs, int32_t repeats, char* report,

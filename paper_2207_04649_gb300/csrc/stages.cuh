@@ -316,7 +316,6 @@ cudaError_t launch_delta_ptree(const BatchView& v, const PtBufs& pb, int d, int6
 // to its cell's p*; rule 2 links a p* to the highest p* of the neighbouring
 // cells all of whose points rank higher; the rest go to the exact lists.
 struct ApproxBufs {
-    uint64_t* keys;       // [N] grid keys by sorted position, then sorted
     uint32_t* ord;        // [N] sorted positions in grid-key order
     uint32_t* flag;       // [N] temp: first point of a cell
     uint32_t* cidx;       // [N] temp: exclusive scan of flag
@@ -329,9 +328,12 @@ struct ApproxBufs {
     uint32_t* heavy;      // [ncells] the others (one warp each)
     uint32_t* nlh;        // [2] device counts of light, heavy
 };
-cudaError_t launch_approx_keys(const BatchView& v, const ApproxBufs& ab, cudaStream_t st);
-cudaError_t launch_approx_cells(const BatchView& v, const CellWork& w, const ApproxBufs& ab, void* scan_temp,
-                                cudaStream_t st);
+// Sorts the sorted positions by grid key (key_bits wide, the dataset index at
+// bshift; keys [3N], ords [3N] scratch); *ord_out receives the key order.
+cudaError_t launch_approx_keys(const BatchView& v, int key_bits, int bshift, uint64_t* keys, uint32_t* ords,
+                               void* temp, uint32_t** ord_out, cudaStream_t st);
+cudaError_t launch_approx_cells(const BatchView& v, const CellWork& w, const ApproxBufs& ab, int key_bits,
+                                int bshift, void* scan_temp, cudaStream_t st);
 cudaError_t launch_approx_rules(const BatchView& v, const CellWork& w, const ApproxBufs& ab, const DeltaBufs& db,
                                 uint32_t dim_mask, int64_t ncells_bound, cudaStream_t st);
 

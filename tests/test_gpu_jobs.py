@@ -83,6 +83,79 @@ def test_batched_open_point_passes(dpc, knobs):
             check_job(j, p, dc, qs)
 
 
+def expected_method(method, points, dc, qs, eps):
+    """The oracle's rho, dep, delta2, aux and labels for one job."""
+    if method == "sapprox":
+        r, dep, d2, pk = oracle.sapprox(points, dc, *eps)
+        return r, dep, d2, pk, [oracle.sapprox_label(r, dep, d2, pk, a, b) for a, b in qs]
+    r = oracle.rho(points, dc)
+    if method == "approx":
+        dep, d2, ex = oracle.approx_dependent(points, r, dc)
+    else:
+        dep, d2 = oracle.dependent(points, r)
+        ex = None
+    return r, dep, d2, ex, [oracle.label(r, dep, d2, a, b) for a, b in qs]
+
+
+def check_method_job(job, method, points, dc, qs, eps):
+    r, dep, d2, aux, labs = expected_method(method, points, dc, qs, eps)
+    np.testing.assert_array_equal(job.rho, r)
+    np.testing.assert_array_equal(job.dep, dep)
+    np.testing.assert_array_equal(job.delta2, d2)
+    if aux is not None:
+        np.testing.assert_array_equal(job.aux.astype(bool), aux)
+    for q, (lab, nc) in enumerate(labs):
+        np.testing.assert_array_equal(job.label[q], lab)
+        assert job.n_centers[q] == nc
+
+
+METHOD_CYCLE = ["approx", "sapprox", "sapprox", "exact", "approx", "approx", "sapprox"]
+EPS_CYCLE = [(4, 5), (1, 5), (1, 1), (3, 1)]
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_jobs_of_every_method(dpc, mode):
+    """Approx-DPC, S-Approx-DPC and exact jobs mixed in one submission (runs
+    of one method become batches; uneven n, d 1..8, some empty), each job
+    against the oracle of its method."""
+    probs = small_problems(seed=43, count=21)
+    with dpc.Context(0, mode=mode, max_inflight=2) as ctx:
+        jobs = []
+        for i, (p, dc, qs) in enumerate(probs):
+            m = METHOD_CYCLE[i % len(METHOD_CYCLE)]
+            eps = EPS_CYCLE[i % len(EPS_CYCLE)]
+            j = dpc.Job(p, dc, qs, method=m, eps=eps)
+            jobs.append((j, m, eps))
+            ctx.submit(j)
+        if mode == 0:
+            ctx.flush()
+        for (j, m, eps), (p, dc, qs) in zip(jobs, probs):
+            s, res = ctx.wait(j.ticket, 120000)
+            assert s == dpc.DPC_OK and res.status == dpc.DPC_OK, (m, res.status)
+            check_method_job(j, m, p, dc, qs, eps)
+
+
+def test_approx_keys_wider_than_64_bits(dpc):
+    """Approx-DPC on an 8-d set whose grid keys need more than one word."""
+    rng = np.random.default_rng(72)
+    pts = rng.integers(0, 1 << 29, size=(2500, 8)).astype(np.int32)
+    pts[800:1300] = pts[:500] + rng.integers(-3, 4, size=(500, 8)).astype(np.int32)
+    pts = np.clip(pts, 0, (1 << 30) - 1)
+    dc = 40
+    with dpc.Context(0) as ctx:
+        h = ctx.density(pts, dc)
+        dep = np.empty(len(pts), np.int32)
+        d2 = np.empty(len(pts), np.int64)
+        ex = np.empty(len(pts), np.uint8)
+        h.dependent_approx(dep, d2, ex)
+        h.release()
+    r = oracle.rho(pts, dc)
+    odep, od2, oex = oracle.approx_dependent(pts, r, dc)
+    np.testing.assert_array_equal(dep, odep)
+    np.testing.assert_array_equal(d2, od2)
+    np.testing.assert_array_equal(ex.astype(bool), oex)
+
+
 def test_batch_equals_alone_on_blob_workload(dpc):
     """A slice of the 256-problem batch: bits equal to each problem alone."""
     probs = workloads.batch_256(count=12)
