@@ -401,6 +401,30 @@ def run_ours(args):
     traffic = rho_traffic(args.workload)
     dtraffic = rho_traffic(args.workload, "dram_bytes_per_launch_dense")
 
+    if dpairs > 0:
+        roofline = {"bound": "alu", "kernel": f"k_rho_dense (dense cells, pair form {pair_mode})",
+                    "achieved": dachieved / 1e9, "peak": probe_rate / 1e9, "unit": "Gpair/s",
+                    "frac": dachieved / probe_rate, "traffic": dtraffic,
+                    "pairs_per_launch": dpairs, "ms_per_launch": dense_ms,
+                    "density_stage": {"kernels": "k_rho_dense + k_rho_sparse", "achieved": achieved / 1e9,
+                                      "frac": achieved / probe_rate, "traffic": traffic,
+                                      "pairs_per_step": pairs, "ms_per_step": rho_ms},
+                    "peak_source": "measured: the kernel's own pair test (form "
+                                   f"{pair_mode}, {'64' if pair_mode == 1 else '32'}-bit) with operands "
+                                   "in registers on all SMs (dpc_probe_pair_rate), same run",
+                    "pair_mode": pair_mode,
+                    "peak_derived": derived_pair_peak(d, pair_mode, clk.get("sm_mhz"))}
+    else:
+        # S-Approx-DPC's pick path: its density kernel, one warp per pick,
+        # runs the direct 64-bit pair test
+        p64, _ = dpc.dpc_probe_pair_rate(local, d, 1)
+        roofline = {"bound": "alu", "kernel": "k_sap_rho (one warp per pick, direct 64-bit pair test)",
+                    "achieved": achieved / 1e9, "peak": p64 / 1e9, "unit": "Gpair/s",
+                    "frac": achieved / p64, "traffic": None, "pairs_per_launch": pairs, "ms_per_launch": rho_ms,
+                    "peak_source": "measured: the direct 64-bit pair test with operands in registers on all "
+                                   "SMs (dpc_probe_pair_rate mode 1), same run",
+                    "pair_mode": 1, "peak_derived": derived_pair_peak(d, 1, clk.get("sm_mhz"))}
+
     accuracy = None
     if approx or sapprox:
         # Rand index of the Approx-DPC labels against the exact labels of the
@@ -455,18 +479,7 @@ def run_ours(args):
                        "mean_rho": float(rho.double().mean().item()), "n_centers": int(nc)},
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": n * d * 4,
                     "d2h_bytes_per_step": n * (4 + 4 + 8 + 4 + (1 if sapprox else 0)) + 8},
-            "roofline": {"bound": "alu", "kernel": f"k_rho_dense (dense cells, pair form {pair_mode})",
-                         "achieved": dachieved / 1e9, "peak": probe_rate / 1e9, "unit": "Gpair/s",
-                         "frac": dachieved / probe_rate, "traffic": dtraffic,
-                         "pairs_per_launch": dpairs, "ms_per_launch": dense_ms,
-                         "density_stage": {"kernels": "k_rho_dense + k_rho_sparse", "achieved": achieved / 1e9,
-                                           "frac": achieved / probe_rate, "traffic": traffic,
-                                           "pairs_per_step": pairs, "ms_per_step": rho_ms},
-                         "peak_source": "measured: the kernel's own pair test (form "
-                                        f"{pair_mode}, {'64' if pair_mode == 1 else '32'}-bit) with operands "
-                                        "in registers on all SMs (dpc_probe_pair_rate), same run",
-                         "pair_mode": pair_mode,
-                         "peak_derived": derived_pair_peak(d, pair_mode, clk.get("sm_mhz"))},
+            "roofline": roofline,
             "e2e_roofline": e2e_roofline(n, d, infos[-1], probe_rate, value),
             "stages_ms": {k: statistics.mean(i[k] for i in infos)
                           for k in ("ms_grid", "ms_rho", "ms_rank", "ms_ring", "ms_rest", "ms_label")},
