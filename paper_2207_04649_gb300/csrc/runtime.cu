@@ -253,6 +253,11 @@ struct Batch {
     int dep_kind = 0;  // dependent points held: 0 none, 1 exact, 2 Approx-DPC, 3 S-Approx-DPC
     int64_t npicks = 0, nsecond = 0, sap_pairs = 0, pick_pairs = 0;  // S-Approx-DPC counters
     int grid_key_bits = 0, rank_key_bits = 0;
+    // the tree over the cells, built ahead on a second stream while the ring
+    // search runs (it needs the ranks only); tree_ev marks its end
+    bool tree_ready = false;
+    cudaStream_t side = nullptr;
+    cudaEvent_t side_ev[2] = {nullptr, nullptr};
     int32_t* rho_pub = nullptr;  // S-Approx-DPC: rho as reported (-1 where not picked)
     uint32_t class_mask = 0, dim_mask = 0;
     int64_t ncells = 0, ndense = 0, nsparse = 0, nitems = 0, ntree = 0, nbf = 0;
@@ -272,10 +277,14 @@ struct Batch {
     float ms_rho_dense = 0.f;
 
     ~Batch() {
+        if (side) cudaStreamSynchronize(side);
         keep.release();
         dens.release();
         for (auto& e : ev)
             if (e) cudaEventDestroy(e);
+        for (auto& e : side_ev)
+            if (e) cudaEventDestroy(e);
+        if (side) cudaStreamDestroy(side);
     }
 
     dpc_status sync(const char* what) {
@@ -695,9 +704,39 @@ struct Batch {
         return DPC_OK;
     }
 
+    // Allocates the cell tree's buffers (on st) and builds the tree on the
+    // side stream, to overlap the ring search; open_points waits for it.
+    dpc_status prebuild_tree(Arena& tmp) {
+        const int64_t nc = ncells;
+        if (nc == 0) return DPC_OK;
+        db.ncells = nc;
+        db.dpb = 1;
+        for (int b = 0; b < B; ++b)
+            if (hd[b].dp == 2) db.dpb = 2;
+        DPC_CK(tmp.get(&db.cell_off, B + 1));
+        DPC_CK(tmp.get(&db.ckey, nc));
+        DPC_CK(tmp.get(&db.child, nc));
+        DPC_CK(tmp.get(&db.iparent, nc));
+        DPC_CK(tmp.get(&db.lparent, nc));
+        DPC_CK(tmp.get(&db.nodes, (size_t)2 * nc * (2 * db.dpb + 1)));
+        DPC_CK(tmp.get(&db.flag, nc));
+        DPC_CK(cudaMemsetAsync(db.flag, 0, sizeof(uint32_t) * std::max<int64_t>(nc, 1), st));
+        if (!side) {
+            DPC_CK(cudaStreamCreateWithFlags(&side, cudaStreamNonBlocking));
+            for (auto& e : side_ev) DPC_CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+        }
+        DPC_CK(cudaEventRecord(side_ev[0], st));
+        DPC_CK(cudaStreamWaitEvent(side, side_ev[0], 0));
+        DPC_CK(launch_tree_build(v, db, side));
+        DPC_CK(cudaEventRecord(side_ev[1], side));
+        tree_ready = true;
+        return DPC_OK;
+    }
+
     // The open points of db.tree_list / db.bf_list (counts in db.ucount[0..1],
     // filled by the stream's previous kernels): tree search and brute force.
     dpc_status open_points(Arena& tmp, const char* what, bool allow_coarse) {
+        if (tree_ready) DPC_CK(cudaStreamWaitEvent(st, side_ev[1], 0));  // the tree built ahead
         uint32_t uc[2] = {0, 0};
         DPC_CK(cudaMemcpyAsync(uc, db.ucount, sizeof(uc), cudaMemcpyDeviceToHost, st));
         DPC_TRY(sync(what));
@@ -757,20 +796,22 @@ struct Batch {
                 db.tree_list = db.open2;
                 db.tcount = db.ucount + 2;
             }
-            db.dpb = 1;
-            for (int b = 0; b < B; ++b)
-                if (hd[b].dp == 2) db.dpb = 2;
-            DPC_CK(tmp.get(&db.cell_off, B + 1));
-            DPC_CK(tmp.get(&db.ckey, nc));
-            DPC_CK(tmp.get(&db.child, nc));
-            DPC_CK(tmp.get(&db.iparent, nc));
-            DPC_CK(tmp.get(&db.lparent, nc));
-            DPC_CK(tmp.get(&db.nodes, (size_t)2 * nc * (2 * db.dpb + 1)));
-            DPC_CK(tmp.get(&db.flag, nc));
-            DPC_CK(cudaMemsetAsync(db.flag, 0, sizeof(uint32_t) * std::max<int64_t>(nc, 1), st));
+            if (!tree_ready) {
+                db.dpb = 1;
+                for (int b = 0; b < B; ++b)
+                    if (hd[b].dp == 2) db.dpb = 2;
+                DPC_CK(tmp.get(&db.cell_off, B + 1));
+                DPC_CK(tmp.get(&db.ckey, nc));
+                DPC_CK(tmp.get(&db.child, nc));
+                DPC_CK(tmp.get(&db.iparent, nc));
+                DPC_CK(tmp.get(&db.lparent, nc));
+                DPC_CK(tmp.get(&db.nodes, (size_t)2 * nc * (2 * db.dpb + 1)));
+                DPC_CK(tmp.get(&db.flag, nc));
+                DPC_CK(cudaMemsetAsync(db.flag, 0, sizeof(uint32_t) * std::max<int64_t>(nc, 1), st));
+                DPC_CK(launch_tree_build(v, db, st));
+            }
             DPC_CK(tmp.get(&db.stats, 2));
             DPC_CK(cudaMemsetAsync(db.stats, 0, 2 * sizeof(unsigned long long), st));
-            DPC_CK(launch_tree_build(v, db, st));
             DPC_CK(launch_tree_search(v, db, dim_mask, ntree, st));
         }
         if (nbf > 0) {
@@ -838,6 +879,7 @@ struct Batch {
 
         DPC_CK(tmp.get(&v.best_s, N));
         DPC_CK(cudaMemsetAsync(v.best_s, 0xff, sizeof(unsigned long long) * std::max<int64_t>(N, 1), st));
+        DPC_TRY(prebuild_tree(tmp));
         DPC_CK(launch_ring(v, w, class_mask, nitems, nsparse, d_counters + 32, st));
         if (pb.m > 0) {
             DPC_CK(cudaMemsetAsync(pb.flag, 0, sizeof(uint32_t) * pb.nslots, st));
@@ -860,7 +902,8 @@ struct Batch {
         ms[2] = elapsed(0, 1);
         ms[3] = elapsed(1, 2);
         ms[4] = elapsed(2, 3);
-        tmp.release();
+        tmp.release();  // after open_points, whose stream waited for the side stream's tree
+        tree_ready = false;
         dep_kind = 1;
         return DPC_OK;
     }
