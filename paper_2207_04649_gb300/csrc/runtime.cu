@@ -104,6 +104,11 @@ struct Arena {
         ptrs.clear();
         bytes = 0;
     }
+    // an early return frees the buffers too (stream-ordered on st)
+    ~Arena() { release(); }
+    Arena() = default;
+    Arena(const Arena&) = delete;
+    Arena& operator=(const Arena&) = delete;
 };
 
 struct Input {
@@ -872,6 +877,15 @@ struct Batch {
         mark(0);
         Arena tmp;
         tmp.st = st;
+        // on every way out, st waits for the tree built on the side stream
+        // before tmp (which holds its buffers) is freed
+        struct SideWait {
+            Batch* b;
+            ~SideWait() {
+                if (b->tree_ready) cudaStreamWaitEvent(b->st, b->side_ev[1], 0);
+                b->tree_ready = false;
+            }
+        } side_wait{this};
         void* temp = nullptr;
         DPC_CK(tmp.get(&temp, std::max(radix_sort_temp_bytes(N), scan_temp_bytes(N))));
         DPC_TRY(ensure_rank(tmp, temp));
@@ -903,7 +917,6 @@ struct Batch {
         ms[3] = elapsed(1, 2);
         ms[4] = elapsed(2, 3);
         tmp.release();  // after open_points, whose stream waited for the side stream's tree
-        tree_ready = false;
         dep_kind = 1;
         return DPC_OK;
     }

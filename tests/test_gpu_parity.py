@@ -377,3 +377,31 @@ def test_one_call_cluster_matches_the_separate_calls(dpc):
         np.testing.assert_array_equal(got[3], ref[3][0][0])
     assert nc == nc2 == ref[3][0][1]
     assert empty == 0
+
+
+def test_errors_mid_call_leave_the_context_usable(dpc):
+    """Calls that fail after device work has started (coordinates out of
+    range found on the device, S-Approx-DPC and Approx-DPC refused on the
+    point tree) release their buffers and leave the context working."""
+    bad = np.array([[0, 0], [5, (1 << 30) + 3]], np.int32)
+    good = workloads.random_blobs(95, 3000, 3, 900, blobs=4, spread=0.05)
+    ref = run_host(dpc, good.points, 900, [(2, 2000)])
+    with dpc.Context(0) as ctx:
+        for _ in range(20):
+            with pytest.raises(dpc.DpcError):
+                ctx.density(bad, 10)
+        ctx.tune(tree_min_d=2)
+        for _ in range(5):
+            with pytest.raises(dpc.DpcError):
+                ctx.sapprox(good.points, 900, (4, 5))
+            h = ctx.density(good.points, 900)
+            with pytest.raises(dpc.DpcError):
+                h.dependent_approx()
+            h.release()
+        ctx.tune(tree_min_d=9)
+        out = [np.empty(good.n, t) for t in (np.int32, np.int32, np.int64, np.int32)]
+        nc = ctx.cluster(good.points, 900, 2, 2000, *out)
+    np.testing.assert_array_equal(out[0], ref[0])
+    np.testing.assert_array_equal(out[1], ref[1])
+    np.testing.assert_array_equal(out[3], ref[3][0][0])
+    assert nc == ref[3][0][1]
