@@ -273,6 +273,10 @@ dpc_status dpc_set_profiling(dpc_ctx* ctx, int on);
  *   "sapprox_ratio"  with sapprox_path 0: the pick path when the points'
  *             candidate pairs exceed this many times the picks', 1 .. 1024
  *             (default 16)
+ *   "sapprox_rho_cells"  the pick path's density: 1 one warp per grid cell
+ *             over its picks (candidates staged once per cell), 0 one warp
+ *             per pick, 2 by cell when picks face fewer than 512 candidates
+ *             each on average (default 2)
  *   "max_batch_jobs"  served mode: jobs one batch admits at most, 1 .. 4096
  *             (default 64; 1 runs the jobs one at a time)
  * DPC_ERR_INVALID_ARG for an unknown key or a value out of range. */

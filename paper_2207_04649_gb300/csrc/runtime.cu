@@ -131,6 +131,8 @@ struct Tune {
     int ring2 = 0;            // second ring (cells at distance 2) before the tree search
     int sparse_cand = 512;    // cells of at most 4 points with more candidates than this take the dense path
     int sapprox_path = 0;     // S-Approx-DPC: 0 by the pair counts, 1 all points, 2 picks only
+    int sapprox_rho_cells = 2;  // S-Approx-DPC pick path: density by cell (1), one warp per pick (0), by the
+                                //   candidates per pick (2)
     int sapprox_ratio = 16;   // S-Approx-DPC: the pick path when the points' pairs exceed this many times the picks'
 };
 
@@ -1070,7 +1072,19 @@ struct Batch {
             DPC_CK(cudaMemsetAsync(v.rho_s, 0, sizeof(int32_t) * std::max<int64_t>(N, 1), st));
             DPC_CK(cudaMemsetAsync(v.rho, 0, sizeof(int32_t) * std::max<int64_t>(N, 1), st));
             DPC_CK(cudaMemsetAsync(d_counters, 0, 64 * sizeof(uint32_t), st));
-            DPC_CK(launch_sapprox_rho(v, w, sb, dim_mask, npicks, st));
+            // each cell's picks, contiguous: the density and the near pass
+            // take them cell by cell
+            DPC_CK(tmp.get(&sb.pflag, N));
+            DPC_CK(tmp.get(&sb.ppos, N));
+            DPC_CK(tmp.get(&sb.plist, N));
+            DPC_CK(tmp.get(&sb.pstart, ncells + 1));
+            DPC_CK(launch_sapprox_plist(v, sb, ncells, temp, st));
+            // by cell when picks face few candidates each (one warp stages a
+            // cell's candidates once for all its picks); with thousands per
+            // pick, one warp per pick keeps more loads in flight
+            const bool by_cell = tune.sapprox_rho_cells == 1 ||
+                                 (tune.sapprox_rho_cells == 2 && pick_pairs < 512 * std::max<int64_t>(npicks, 1));
+            DPC_CK(launch_sapprox_rho(v, w, sb, dim_mask, npicks, ncells, by_cell, st));
             mark(2);
         }
         DPC_TRY(ensure_rank(tmp, temp));
@@ -1091,13 +1105,6 @@ struct Batch {
         DPC_CK(cudaMemsetAsync(db.ucount, 0, 4 * sizeof(uint32_t), st));
         db.tcount = db.ucount;
         db.bf_rank = tune.bf_rank;
-        if (!all_points) {
-            DPC_CK(tmp.get(&sb.pflag, N));
-            DPC_CK(tmp.get(&sb.ppos, N));
-            DPC_CK(tmp.get(&sb.plist, N));
-            DPC_CK(tmp.get(&sb.pstart, ncells + 1));
-            DPC_CK(launch_sapprox_plist(v, sb, ncells, temp, st));
-        }
         DPC_CK(launch_sapprox_first(v, w, sb, db, dim_mask, npicks, npicks, !all_points, st));
         DPC_TRY(open_points(tmp, "S-Approx-DPC first phase", false));
         mark(6);
@@ -1230,6 +1237,7 @@ dpc_status dpc_set_tuning(dpc_ctx* ctx, const char* key, int64_t value) {
     else if (k == "ring2" && value >= 0 && value <= 1) t.ring2 = (int)value;
     else if (k == "sapprox_path" && value >= 0 && value <= 2) t.sapprox_path = (int)value;
     else if (k == "sapprox_ratio" && value >= 1 && value <= 1024) t.sapprox_ratio = (int)value;
+    else if (k == "sapprox_rho_cells" && value >= 0 && value <= 2) t.sapprox_rho_cells = (int)value;
     else if (k == "sparse_cand" && value >= 0 && value <= (1ll << 31)) t.sparse_cand = (int)std::min<int64_t>(value, INT32_MAX);
     else if (k == "max_batch_jobs" && value >= 1 && value <= 4096) {
         std::lock_guard<std::mutex> lk(ctx->mu);
@@ -1254,6 +1262,7 @@ dpc_status dpc_get_tuning(dpc_ctx* ctx, const char* key, int64_t* value) {
     else if (k == "sparse_cand") *value = t.sparse_cand;
     else if (k == "sapprox_path") *value = t.sapprox_path;
     else if (k == "sapprox_ratio") *value = t.sapprox_ratio;
+    else if (k == "sapprox_rho_cells") *value = t.sapprox_rho_cells;
     else if (k == "max_batch_jobs") {
         std::lock_guard<std::mutex> lk(ctx->mu);
         *value = ctx->max_batch_jobs;

@@ -184,6 +184,73 @@ __global__ void __launch_bounds__(128) k_sap_rho(BatchView v, CellWork w, Sappro
     if (lane == 0 && pairs) atomicAdd(&sb.stats[0], pairs);
 }
 
+// Pick path, local density of every pick, one warp per exact-grid cell that
+// holds picks: the cell's neighbour runs are staged once per chunk in shared
+// memory and shared by all its picks. The lanes form S pick slots times
+// 32 / S candidate groups (S the smallest power of two at least the number
+// of picks, at most 32); each group takes every (32 / S)-th candidate of a
+// chunk and the groups' counts are added with shuffles.
+template <int D>
+__global__ void __launch_bounds__(128) k_sap_rho_cells(BatchView v, CellWork w, SapproxBufs sb, int64_t ncells) {
+    constexpr int DP = D <= 4 ? 1 : 2;
+    __shared__ int4 sbuf[128 / 32][kChunk * DP];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    int4* buf = sbuf[wid];
+    const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    unsigned long long pairs = 0;
+    for (int64_t c = (int64_t)blockIdx.x * (blockDim.x >> 5) + wid; c < ncells; c += nwarps) {
+        const uint32_t k0 = sb.pstart[c], k1 = sb.pstart[c + 1];
+        if (k0 == k1) continue;
+        const uint32_t cs = v.cell_start[c];
+        const DsDesc& ds = v.desc[find_ds(v.pt_off, v.B, cs)];
+        if (ds.d != D) continue;
+        const int4* recb = v.rec + ds.rec_off - ds.pt_off * DP;
+        const uint2* runs = w.runs + c * w.nbs;
+        const uint32_t nr = w.nruns[c], ctot = w.cand[c];
+        for (uint32_t g0 = k0; g0 < k1; g0 += 32) {
+            const uint32_t np = min(32u, k1 - g0);
+            int S = 1;
+            while (S < (int)np) S <<= 1;
+            const int G = 32 / S, slot = lane & (S - 1), grp = lane / S;
+            const bool mine = (uint32_t)slot < np;
+            const uint32_t p = sb.plist[g0 + (mine ? slot : 0)];
+            int32_t x[D];
+            sx_load<D>(recb + (int64_t)p * DP, x);
+            uint32_t cnt = 0;
+            CandStream<DP, false> cst;
+            cst.init(runs, nr, 0, ctot);
+            bool bad = false;
+            while (cst.prep(lane, recb, nullptr, &bad)) {
+                const int nb = (int)cst.cnt;
+                __syncwarp();  // every lane is done with the previous chunk
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int f = lane + 32 * u;
+                    if (f < nb) {
+#pragma unroll
+                        for (int q = 0; q < DP; ++q) buf[f * DP + q] = cst.r[u][q];
+                    }
+                }
+                __syncwarp();
+                for (int j = grp; j < nb; j += G) {
+                    int32_t y[D];
+                    sx_load<D>(buf + j * DP, y);
+                    cnt += sx_dist<D>(x, y) < ds.d_cut2 ? 1u : 0u;
+                }
+            }
+            for (int o = S; o < 32; o <<= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+            if (bad && lane == 0) atomicOr(v.err, kErrStaging);
+            if (mine && grp == 0) {
+                v.rho_s[p] = (int32_t)cnt;
+                v.rho[v.perm[p]] = (int32_t)cnt;
+                pairs += ctot;
+            }
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) pairs += __shfl_xor_sync(0xffffffffu, pairs, o);
+    if (lane == 0 && pairs) atomicAdd(&sb.stats[0], pairs);
+}
+
 // A point that is not picked depends on its cell's pick.
 __global__ void k_sap_follow(BatchView v, SapproxBufs sb) {
     const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -467,11 +534,14 @@ cudaError_t launch_sapprox_pick_pairs(const BatchView& v, const CellWork& w, con
 }
 
 cudaError_t launch_sapprox_rho(const BatchView& v, const CellWork& w, const SapproxBufs& sb, uint32_t dim_mask,
-                               int64_t picks_bound, cudaStream_t st) {
+                               int64_t picks_bound, int64_t ncells, bool by_cell, cudaStream_t st) {
     if (v.N == 0) return cudaSuccess;
-    const unsigned blocks = warp_blocks(picks_bound);
-#define DPC_SAP_RHO(D) \
-    if (dim_mask & (1u << (D - 1))) (k_sap_rho<D><<<blocks, 128, 0, st>>>(v, w, sb), note_launch());
+    const unsigned blocks = warp_blocks(by_cell ? ncells : picks_bound);
+#define DPC_SAP_RHO(D)                                                                          \
+    if (dim_mask & (1u << (D - 1))) {                                                           \
+        if (by_cell) (k_sap_rho_cells<D><<<blocks, 128, 0, st>>>(v, w, sb, ncells), note_launch()); \
+        else (k_sap_rho<D><<<blocks, 128, 0, st>>>(v, w, sb), note_launch());                   \
+    }
     DPC_SAP_RHO(1) DPC_SAP_RHO(2) DPC_SAP_RHO(3) DPC_SAP_RHO(4)
     DPC_SAP_RHO(5) DPC_SAP_RHO(6) DPC_SAP_RHO(7) DPC_SAP_RHO(8)
 #undef DPC_SAP_RHO

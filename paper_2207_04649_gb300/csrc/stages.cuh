@@ -365,8 +365,10 @@ cudaError_t launch_sapprox_plist(const BatchView& v, const SapproxBufs& sb, int6
 // sb.stats[2] += the candidate pairs of the picks' exact-grid cells
 cudaError_t launch_sapprox_pick_pairs(const BatchView& v, const CellWork& w, const SapproxBufs& sb,
                                      int64_t picks_bound, cudaStream_t st);
+// by_cell: one warp per exact-grid cell over its picks (needs plist, pstart),
+// else one warp per pick
 cudaError_t launch_sapprox_rho(const BatchView& v, const CellWork& w, const SapproxBufs& sb, uint32_t dim_mask,
-                               int64_t picks_bound, cudaStream_t st);
+                               int64_t picks_bound, int64_t ncells, bool by_cell, cudaStream_t st);
 // rho 0 for the points that are not picked (they rank after every pick)
 cudaError_t launch_sapprox_mask(const BatchView& v, cudaStream_t st);
 // after the rank and the ring search: the points that are not picked, then
