@@ -76,7 +76,7 @@ __global__ void k_compact_cells(BatchView v, CellPrepBufs cb, int64_t bound) {
     }
 }
 
-constexpr int kProbeBatch = 9;  // hash probes issued together per thread
+constexpr int kProbeBatch = 3;  // hash probes issued together per thread (3 to 6 measured alike, 9 and more slower)
 
 __device__ __forceinline__ uint2 resolve_probe(const BatchView& v, uint64_t key, int4 e) {
     const uint64_t k0 = (uint64_t)(uint32_t)e.x | ((uint64_t)(uint32_t)e.y << 32);
