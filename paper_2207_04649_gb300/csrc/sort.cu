@@ -20,8 +20,8 @@ constexpr int kScanItems = 8;                                  // per thread
 constexpr int kScanTile = kScanThreads * kScanItems;           // 2048
 
 constexpr int kRsThreads = 256;
-constexpr int kRsItems = 16;
-constexpr int kRsTile = kRsThreads * kRsItems;                 // 4096
+constexpr int kRsItems = 8;
+constexpr int kRsTile = kRsThreads * kRsItems;                 // 2048 (8 items measured faster than 4, 16 and 32)
 
 inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
 inline size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
