@@ -277,6 +277,9 @@ dpc_status dpc_set_profiling(dpc_ctx* ctx, int on);
  *             over its picks (candidates staged once per cell), 0 one warp
  *             per pick, 2 by cell when picks face fewer than 512 candidates
  *             each on average (default 2)
+ *   "sapprox_near_threads"  the pick path's first-phase scan over the
+ *             picks of a pick's neighbour blocks: 1 one thread per pick,
+ *             0 one warp per pick (default 1)
  *   "max_batch_jobs"  served mode: jobs one batch admits at most, 1 .. 4096
  *             (default 64; 1 runs the jobs one at a time)
  * DPC_ERR_INVALID_ARG for an unknown key or a value out of range. */

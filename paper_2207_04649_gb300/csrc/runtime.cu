@@ -133,6 +133,7 @@ struct Tune {
     int sapprox_path = 0;     // S-Approx-DPC: 0 by the pair counts, 1 all points, 2 picks only
     int sapprox_rho_cells = 2;  // S-Approx-DPC pick path: density by cell (1), one warp per pick (0), by the
                                 //   candidates per pick (2)
+    int sapprox_near_threads = 1;  // S-Approx-DPC pick path: near pass one thread (1) or one warp (0) per pick
     int sapprox_ratio = 16;   // S-Approx-DPC: the pick path when the points' pairs exceed this many times the picks'
 };
 
@@ -1105,7 +1106,8 @@ struct Batch {
         DPC_CK(cudaMemsetAsync(db.ucount, 0, 4 * sizeof(uint32_t), st));
         db.tcount = db.ucount;
         db.bf_rank = tune.bf_rank;
-        DPC_CK(launch_sapprox_first(v, w, sb, db, dim_mask, npicks, npicks, !all_points, st));
+        DPC_CK(launch_sapprox_first(v, w, sb, db, dim_mask, npicks, npicks, !all_points, tune.sapprox_near_threads != 0,
+                                    st));
         DPC_TRY(open_points(tmp, "S-Approx-DPC first phase", false));
         mark(6);
         DPC_CK(keep.get(&rho_pub, N));
@@ -1238,6 +1240,7 @@ dpc_status dpc_set_tuning(dpc_ctx* ctx, const char* key, int64_t value) {
     else if (k == "sapprox_path" && value >= 0 && value <= 2) t.sapprox_path = (int)value;
     else if (k == "sapprox_ratio" && value >= 1 && value <= 1024) t.sapprox_ratio = (int)value;
     else if (k == "sapprox_rho_cells" && value >= 0 && value <= 2) t.sapprox_rho_cells = (int)value;
+    else if (k == "sapprox_near_threads" && value >= 0 && value <= 1) t.sapprox_near_threads = (int)value;
     else if (k == "sparse_cand" && value >= 0 && value <= (1ll << 31)) t.sparse_cand = (int)std::min<int64_t>(value, INT32_MAX);
     else if (k == "max_batch_jobs" && value >= 1 && value <= 4096) {
         std::lock_guard<std::mutex> lk(ctx->mu);
@@ -1263,6 +1266,7 @@ dpc_status dpc_get_tuning(dpc_ctx* ctx, const char* key, int64_t* value) {
     else if (k == "sapprox_path") *value = t.sapprox_path;
     else if (k == "sapprox_ratio") *value = t.sapprox_ratio;
     else if (k == "sapprox_rho_cells") *value = t.sapprox_rho_cells;
+    else if (k == "sapprox_near_threads") *value = t.sapprox_near_threads;
     else if (k == "max_batch_jobs") {
         std::lock_guard<std::mutex> lk(ctx->mu);
         *value = ctx->max_batch_jobs;

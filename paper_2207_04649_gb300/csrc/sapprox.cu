@@ -390,6 +390,52 @@ __global__ void __launch_bounds__(128) k_sap_near(BatchView v, CellWork w, Sappr
     }
 }
 
+// The same near pass with one thread per pick (a pick's block holds few
+// picks on dense data: tens, against thousands of points).
+template <int D>
+__global__ void __launch_bounds__(128) k_sap_near_t(BatchView v, CellWork w, SapproxBufs sb) {
+    constexpr int DP = D <= 4 ? 1 : 2;
+    const uint32_t m = *sb.npicks;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t p = sb.picks[i];
+        const DsDesc& ds = v.desc[find_ds(v.pt_off, v.B, p)];
+        if (ds.d != D) continue;
+        const uint2 ro = v.ro_s[p];
+        const int64_t g = ds.pt_off + ro.y;
+        if (ro.x == 0u) {  // the densest pick
+            v.dep[g] = -1;
+            v.delta2[g] = INT64_MAX;
+            continue;
+        }
+        const int4* recb = v.rec + ds.rec_off - ds.pt_off * DP;
+        int32_t x[D];
+        sx_load<D>(recb + (int64_t)p * DP, x);
+        const uint32_t e = v.cell_of[p];
+        const uint2* runs = w.runs + (int64_t)e * w.nbs;
+        const uint32_t nr = w.nruns[e];
+        long long bd = INT64_MAX;
+        uint32_t bj = 0xffffffffu;
+        for (uint32_t ri = 0; ri < nr; ++ri) {
+            const uint32_t c = v.cell_of[runs[ri].x];
+            for (uint32_t t = sb.pstart[c], t1 = sb.pstart[c + 1]; t < t1; ++t) {
+                const uint32_t q = sb.plist[t];
+                const uint2 cr = v.ro_s[q];
+                if (cr.x >= ro.x) continue;
+                int32_t y[D];
+                sx_load<D>(recb + (int64_t)q * DP, y);
+                keep_min(bd, bj, sx_dist<D>(x, y), cr.y);
+            }
+        }
+        if (bj != 0xffffffffu && bd < ds.d_cut2) {
+            v.dep[g] = (int32_t)bj;
+            v.delta2[g] = bd;
+            continue;
+        }
+        if (bd < 0xffffffffll) v.best_s[p] = ((unsigned long long)bd << 32) | bj;
+        sb.scan[atomicAdd(&sb.nscan[0], 1u)] = p;
+    }
+}
+
 // First phase for the queued picks: one warp per pick scans the neighbour
 // runs of its exact-grid cell for points strictly within d_cut in other
 // cells of G', and keeps the nearest of their cells' picks that rank
@@ -556,13 +602,17 @@ cudaError_t launch_sapprox_mask(const BatchView& v, cudaStream_t st) {
 
 cudaError_t launch_sapprox_first(const BatchView& v, const CellWork& w, const SapproxBufs& sb, const DeltaBufs& db,
                                  uint32_t dim_mask, int64_t picks_bound, int64_t scan_bound, bool near_pass,
-                                 cudaStream_t st) {
+                                 bool near_threads, cudaStream_t st) {
     if (v.N == 0) return cudaSuccess;
     (k_sap_follow<<<grid_for(v.N, 256), 256, 0, st>>>(v, sb), note_launch());
     if (near_pass) {
-        const unsigned nb = warp_blocks(picks_bound);
-#define DPC_SAP_NEAR(D) \
-    if (dim_mask & (1u << (D - 1))) (k_sap_near<D><<<nb, 128, 0, st>>>(v, w, sb), note_launch());
+        const unsigned nb = near_threads ? (unsigned)std::max<int64_t>(1, std::min<int64_t>(152 * 32, grid_for(picks_bound, 128)))
+                                         : warp_blocks(picks_bound);
+#define DPC_SAP_NEAR(D)                                                                            \
+    if (dim_mask & (1u << (D - 1))) {                                                              \
+        if (near_threads) (k_sap_near_t<D><<<nb, 128, 0, st>>>(v, w, sb), note_launch());          \
+        else (k_sap_near<D><<<nb, 128, 0, st>>>(v, w, sb), note_launch());                        \
+    }
         DPC_SAP_NEAR(1) DPC_SAP_NEAR(2) DPC_SAP_NEAR(3) DPC_SAP_NEAR(4)
         DPC_SAP_NEAR(5) DPC_SAP_NEAR(6) DPC_SAP_NEAR(7) DPC_SAP_NEAR(8)
 #undef DPC_SAP_NEAR

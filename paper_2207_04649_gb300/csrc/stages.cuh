@@ -373,10 +373,11 @@ cudaError_t launch_sapprox_rho(const BatchView& v, const CellWork& w, const Sapp
 cudaError_t launch_sapprox_mask(const BatchView& v, cudaStream_t st);
 // after the rank and the ring search: the points that are not picked, then
 // the picks (resolved from the ring result or queued), then the first-phase scan
-// near_pass: the pick path's pass over the picks of each block (no ring search ran)
+// near_pass: the pick path's pass over the picks of each block (no ring search
+// ran), one thread (near_threads) or one warp per pick
 cudaError_t launch_sapprox_first(const BatchView& v, const CellWork& w, const SapproxBufs& sb, const DeltaBufs& db,
                                  uint32_t dim_mask, int64_t picks_bound, int64_t scan_bound, bool near_pass,
-                                 cudaStream_t st);
+                                 bool near_threads, cudaStream_t st);
 cudaError_t launch_sapprox_rho_out(const BatchView& v, int32_t* out, cudaStream_t st);
 
 // label.cu
