@@ -398,15 +398,19 @@ def run_ours(args):
     dpairs = infos[-1]["dense_pairs"]
     achieved = pairs / (rho_ms / 1e3) if rho_ms > 0 else 0.0
     dachieved = dpairs / (dense_ms / 1e3) if dense_ms > 0 else 0.0
-    traffic = rho_traffic(args.workload)
-    dtraffic = rho_traffic(args.workload, "dram_bytes_per_launch_dense")
+    # the DRAM capture covers the density kernels over every point only
+    all_points = infos[-1].get("density_path", 0) == 0
+    traffic = rho_traffic(args.workload) if all_points else None
+    dtraffic = rho_traffic(args.workload, "dram_bytes_per_launch_dense") if all_points else None
 
     if dpairs > 0:
-        roofline = {"bound": "alu", "kernel": f"k_rho_dense (dense cells, pair form {pair_mode})",
+        queries = "each grid cell's picks" if infos[-1].get("density_path") == 3 else "dense cells"
+        roofline = {"bound": "alu", "kernel": f"k_rho_dense ({queries}, pair form {pair_mode})",
                     "achieved": dachieved / 1e9, "peak": probe_rate / 1e9, "unit": "Gpair/s",
                     "frac": dachieved / probe_rate, "traffic": dtraffic,
                     "pairs_per_launch": dpairs, "ms_per_launch": dense_ms,
-                    "density_stage": {"kernels": "k_rho_dense + k_rho_sparse", "achieved": achieved / 1e9,
+                    "density_stage": {"kernels": "k_rho_dense + k_rho_sparse" if all_points else
+                                      "pick lists, pick items, k_rho_dense", "achieved": achieved / 1e9,
                                       "frac": achieved / probe_rate, "traffic": traffic,
                                       "pairs_per_step": pairs, "ms_per_step": rho_ms},
                     "peak_source": "measured: the kernel's own pair test (form "
@@ -415,10 +419,13 @@ def run_ours(args):
                     "pair_mode": pair_mode,
                     "peak_derived": derived_pair_peak(d, pair_mode, clk.get("sm_mhz"))}
     else:
-        # S-Approx-DPC's pick path: its density kernel, one warp per pick,
-        # runs the direct 64-bit pair test
+        # S-Approx-DPC's pick path with few candidates per pick: its density
+        # kernel (one warp per pick, or per grid cell) runs the direct 64-bit
+        # pair test
         p64, _ = dpc.dpc_probe_pair_rate(local, d, 1)
-        roofline = {"bound": "alu", "kernel": "k_sap_rho (one warp per pick, direct 64-bit pair test)",
+        kname = ("k_sap_rho_cells (one warp per grid cell" if infos[-1].get("density_path") == 2
+                 else "k_sap_rho (one warp per pick")
+        roofline = {"bound": "alu", "kernel": f"{kname}, direct 64-bit pair test)",
                     "achieved": achieved / 1e9, "peak": p64 / 1e9, "unit": "Gpair/s",
                     "frac": achieved / p64, "traffic": None, "pairs_per_launch": pairs, "ms_per_launch": rho_ms,
                     "peak_source": "measured: the direct 64-bit pair test with operands in registers on all "

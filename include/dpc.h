@@ -231,6 +231,9 @@ typedef struct {
     int32_t rank_key_bits;    /* width of the rank sort's key */
     int64_t picks;            /* S-Approx-DPC: cells of G' (picked points) */
     int64_t second_phase;     /* S-Approx-DPC: picks without a first-phase dependent point */
+    int32_t density_path;     /* the density's path: 0 every point (exact, Approx-DPC, S-Approx-DPC's
+                                 all-point path); S-Approx-DPC's pick path: 1 one warp per pick,
+                                 2 one warp per grid cell, 3 the dense kernels over pick items */
 } dpc_info;
 
 dpc_status dpc_ds_info(const dpc_ds* ds, dpc_info* out);
@@ -275,8 +278,9 @@ dpc_status dpc_set_profiling(dpc_ctx* ctx, int on);
  *             (default 16)
  *   "sapprox_rho_cells"  the pick path's density: 1 one warp per grid cell
  *             over its picks (candidates staged once per cell), 0 one warp
- *             per pick, 2 by cell when picks face fewer than 512 candidates
- *             each on average (default 2)
+ *             per pick, 3 the dense density kernels with each cell's picks
+ *             as queries, 2 by cell when picks face fewer than 512
+ *             candidates each on average, else 3 (default 2)
  *   "sapprox_near_threads"  the pick path's first-phase scan over the
  *             picks of a pick's neighbour blocks: 1 one thread per pick,
  *             0 one warp per pick (default 1)

@@ -49,7 +49,7 @@ class DpcInfo(ctypes.Structure):
                 ("tree_visits", ctypes.c_int64), ("tree_pairs", ctypes.c_int64),
                 ("open_after_coarse", ctypes.c_int64), ("pair_mode", ctypes.c_int32), ("grid_key_bits", ctypes.c_int32),
                 ("dense_pairs", ctypes.c_int64), ("ms_rho_dense", ctypes.c_float), ("rank_key_bits", ctypes.c_int32),
-                ("picks", ctypes.c_int64), ("second_phase", ctypes.c_int64)]
+                ("picks", ctypes.c_int64), ("second_phase", ctypes.c_int64), ("density_path", ctypes.c_int32)]
 
     def as_dict(self) -> dict:
         return {f: getattr(self, f) for f, _ in self._fields_}

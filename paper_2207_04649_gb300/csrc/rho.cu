@@ -279,8 +279,14 @@ __device__ __forceinline__ void eval_rho_x(const int4* buf, int nb, int grp, int
 }
 
 
-template <int D, int MODE>
-__global__ void __launch_bounds__(kRhoThreads) k_rho_dense(BatchView v, CellWork w, uint32_t* counter) {
+// QL: the queries of a cell are the points qlist[qstart[c] .. qstart[c + 1])
+// (S-Approx-DPC's picks, all of them points of cell c) and an item's first
+// field is the cell itself; otherwise the queries are all the cell's points
+// and the first field indexes the dense cell list.
+template <int D, int MODE, bool QL>
+__global__ void __launch_bounds__(kRhoThreads) k_rho_dense(BatchView v, CellWork w, uint32_t* counter,
+                                                           const uint32_t* __restrict__ qlist,
+                                                           const uint32_t* __restrict__ qstart) {
     constexpr int DP = D <= 4 ? 1 : 2;
     constexpr bool W64 = MODE == 1;
     constexpr bool EXP = MODE == 2;
@@ -291,20 +297,24 @@ __global__ void __launch_bounds__(kRhoThreads) k_rho_dense(BatchView v, CellWork
     const uint32_t nitems = *w.nitems;
     // the next item's index, record and cell are fetched in stages while the
     // current item runs (one stage per candidate chunk)
-    uint32_t nx = 0, it_n = 0, c_n = 0, cs_n = 0, ce_n = 0, nr_n = 0, ct_n = 0;
+    uint32_t nx = 0, it_n = 0, c_n = 0, cs_n = 0, ce_n = 0, nr_n = 0, ct_n = 0, qs_n = 0, qe_n = 0;
     uint4 item_n = make_uint4(0u, 0u, 0u, 0u);
     auto stage = [&](int s) {
         if (s == 0) {
             it_n = __shfl_sync(0xffffffffu, nx, 0);
             if (it_n < nitems) item_n = w.items[it_n];
         } else if (s == 1) {
-            if (it_n < nitems) c_n = w.dense[item_n.x];
+            if (it_n < nitems) c_n = QL ? item_n.x : w.dense[item_n.x];
         } else if (s == 2) {
             if (it_n < nitems) {
                 cs_n = v.cell_start[c_n];
                 ce_n = v.cell_start[c_n + 1];
                 nr_n = w.nruns[c_n];
                 ct_n = w.cand[c_n];
+                if (QL) {
+                    qs_n = qstart[c_n];
+                    qe_n = qstart[c_n + 1];
+                }
             }
         }
     };
@@ -318,7 +328,7 @@ __global__ void __launch_bounds__(kRhoThreads) k_rho_dense(BatchView v, CellWork
         const uint4 item = item_n;  // (dense cell, query chunk, candidate chunk)
         const uint32_t qc = item.y, kc = item.z;
         const uint32_t c = c_n;
-        const uint32_t cs = cs_n, m = ce_n - cs_n;
+        const uint32_t cs = cs_n, m = QL ? qe_n - qs_n : ce_n - cs_n, qs = qs_n;
         const uint32_t nr_c = nr_n, ctot_c = ct_n;
         if (lane == 0) nx = atomicAdd(counter, 1u);
         int pf = 0;
@@ -335,10 +345,16 @@ __global__ void __launch_bounds__(kRhoThreads) k_rho_dense(BatchView v, CellWork
         lane_layout(nq, Q, Mq);
         const int G = 32 / Mq;
         const int grp = lane / Mq, ql = lane & (Mq - 1);
-        // query t of this lane: ql * Q + t (slots at or past nq are dummies)
+        // query t of this lane: ql * Q + t (slots at or past nq are dummies),
+        // the point at sorted position cs + q0 + ql * Q + t (QL: qpos[t])
+        uint32_t qpos[4];
         int32_t qx[4][D];
 #pragma unroll
-        for (int t = 0; t < 4; ++t) load_point<D>(recb + ((int64_t)cs + q0 + min(ql * Q + t, nq - 1)) * DP, qx[t]);
+        for (int t = 0; t < 4; ++t) {
+            const uint32_t i = (uint32_t)(q0 + min(ql * Q + t, nq - 1));
+            if (QL) qpos[t] = qlist[qs + i];
+            load_point<D>(recb + (int64_t)(QL ? qpos[t] : cs + i) * DP, qx[t]);
+        }
         // expanded form: coordinates relative to the query cell's corner
         int32_t org[3] = {0, 0, 0};
         int32_t qa[4][3], qb[4];
@@ -431,7 +447,8 @@ __global__ void __launch_bounds__(kRhoThreads) k_rho_dense(BatchView v, CellWork
         if (grp == 0) {
 #pragma unroll
             for (int t = 0; t < 4; ++t)
-                if (t < Q && ql * Q + t < nq) atomicAdd(&v.rho_s[cs + q0 + ql * Q + t], (int)cnt[t]);
+                if (t < Q && ql * Q + t < nq)
+                    atomicAdd(&v.rho_s[QL ? qpos[t] : cs + q0 + ql * Q + t], (int)cnt[t]);
         }
     }
 }
@@ -477,12 +494,12 @@ __global__ void k_rho_scatter(BatchView v) {
     if (p < v.N) v.rho[v.perm[p]] = v.rho_s[p];
 }
 
-template <int D, int MODE>
+template <int D, int MODE, bool QL = false>
 void launch_rho_dense(const BatchView& v, const CellWork& w, int64_t nitems_bound, uint32_t* counter,
-                      cudaStream_t st) {
+                      cudaStream_t st, const uint32_t* qlist = nullptr, const uint32_t* qstart = nullptr) {
     if (nitems_bound <= 0) return;
     const unsigned blocks = (unsigned)std::max<int64_t>(1, std::min<int64_t>(152 * 16, (nitems_bound + 3) / 4));
-    (k_rho_dense<D, MODE><<<blocks, kRhoThreads, 0, st>>>(v, w, counter), note_launch());
+    (k_rho_dense<D, MODE, QL><<<blocks, kRhoThreads, 0, st>>>(v, w, counter, qlist, qstart), note_launch());
 }
 
 template <int D, bool W64>
@@ -554,6 +571,23 @@ cudaError_t launch_rho(const BatchView& v, const CellWork& w, uint32_t class_mas
     DPC_RHO_X(1) DPC_RHO_X(2) DPC_RHO_X(3)
 #undef DPC_RHO_X
 #undef DPC_RHO_CLASS
+#undef DPC_BIT
+    return cudaGetLastError();
+}
+
+cudaError_t launch_rho_picks(const BatchView& v, const CellWork& w, uint32_t class_mask, int64_t nitems_bound,
+                             uint32_t* counters, const uint32_t* plist, const uint32_t* pstart, cudaStream_t st) {
+    // the dense kernels of every (dimension, arithmetic mode) class present,
+    // over the items of the cells' picks
+#define DPC_BIT(D, M) (class_mask & (1u << (3 * ((D) - 1) + (M))))
+#define DPC_RHOP(D, M) \
+    if (DPC_BIT(D, M)) launch_rho_dense<D, M, true>(v, w, nitems_bound, counters + 3 * (D - 1) + M, st, plist, pstart);
+#define DPC_RHOP_CLASS(D) DPC_RHOP(D, 0) DPC_RHOP(D, 1)
+    DPC_RHOP_CLASS(1) DPC_RHOP_CLASS(2) DPC_RHOP_CLASS(3) DPC_RHOP_CLASS(4)
+    DPC_RHOP_CLASS(5) DPC_RHOP_CLASS(6) DPC_RHOP_CLASS(7) DPC_RHOP_CLASS(8)
+    DPC_RHOP(1, 2) DPC_RHOP(2, 2) DPC_RHOP(3, 2)
+#undef DPC_RHOP_CLASS
+#undef DPC_RHOP
 #undef DPC_BIT
     return cudaGetLastError();
 }

@@ -131,8 +131,8 @@ struct Tune {
     int ring2 = 0;            // second ring (cells at distance 2) before the tree search
     int sparse_cand = 512;    // cells of at most 4 points with more candidates than this take the dense path
     int sapprox_path = 0;     // S-Approx-DPC: 0 by the pair counts, 1 all points, 2 picks only
-    int sapprox_rho_cells = 2;  // S-Approx-DPC pick path: density by cell (1), one warp per pick (0), by the
-                                //   candidates per pick (2)
+    int sapprox_rho_cells = 2;  // S-Approx-DPC pick path: density by cell (1), one warp per pick (0), the
+                                //   dense kernels over pick items (3), 1 or 3 by the candidates per pick (2)
     int sapprox_near_threads = 1;  // S-Approx-DPC pick path: near pass one thread (1) or one warp (0) per pick
     int sapprox_ratio = 16;   // S-Approx-DPC: the pick path when the points' pairs exceed this many times the picks'
 };
@@ -260,6 +260,7 @@ struct Batch {
     bool has_density = false, has_rank = false;
     int dep_kind = 0;  // dependent points held: 0 none, 1 exact, 2 Approx-DPC, 3 S-Approx-DPC
     int64_t npicks = 0, nsecond = 0, sap_pairs = 0, pick_pairs = 0;  // S-Approx-DPC counters
+    int density_path = 0;                                            // as dpc_info::density_path
     int grid_key_bits = 0, rank_key_bits = 0;
     // the tree over the cells, built ahead on a second stream while the ring
     // search runs (it needs the ranks only); tree_ev marks its end
@@ -1064,6 +1065,8 @@ struct Batch {
         // (grid, ranks, the searches for open points). Measured crossovers
         // in all_pairs / pick_pairs: about 4 (1M x 8), 15 (5.8M x 3 with
         // mean rho in the thousands), 50 (5.8M x 3, mean rho 100).
+        bool pick_items = false;
+        density_path = 0;
         const bool all_points = tune.sapprox_path == 1 ||
                                 (tune.sapprox_path == 0 && pick_pairs * (int64_t)tune.sapprox_ratio >= all_pairs);
         if (all_points) {
@@ -1080,12 +1083,34 @@ struct Batch {
             DPC_CK(tmp.get(&sb.plist, N));
             DPC_CK(tmp.get(&sb.pstart, ncells + 1));
             DPC_CK(launch_sapprox_plist(v, sb, ncells, temp, st));
-            // by cell when picks face few candidates each (one warp stages a
-            // cell's candidates once for all its picks); with thousands per
-            // pick, one warp per pick keeps more loads in flight
-            const bool by_cell = tune.sapprox_rho_cells == 1 ||
-                                 (tune.sapprox_rho_cells == 2 && pick_pairs < 512 * std::max<int64_t>(npicks, 1));
-            DPC_CK(launch_sapprox_rho(v, w, sb, dim_mask, npicks, ncells, by_cell, st));
+            // picks facing fewer than 512 candidates each: one warp per cell
+            // stages its candidates once for all its picks; more: the dense
+            // density kernels over (cell, pick chunk, candidate chunk) items,
+            // up to 4 picks per lane in the exact grid's pair form
+            int rho_mode = tune.sapprox_rho_cells;
+            if (rho_mode == 2) rho_mode = pick_pairs < 512 * std::max<int64_t>(npicks, 1) ? 1 : 3;
+            if (rho_mode == 3) {
+                // items per cell <= picks x (candidates / kch + 1), so their
+                // sum is at most npicks + pick_pairs / kch
+                const int64_t cap = npicks + pick_pairs / tune.kch + 1;
+                uint32_t *nitem_c = nullptr, *item_off = nullptr, *pn = nullptr;
+                uint4* pitems = nullptr;
+                DPC_CK(tmp.get(&nitem_c, std::max<int64_t>(ncells, 1)));
+                DPC_CK(tmp.get(&item_off, std::max<int64_t>(ncells, 1)));
+                DPC_CK(tmp.get(&pitems, cap));
+                DPC_CK(tmp.get(&pn, 1));
+                DPC_CK(launch_sapprox_items(v, w, sb, ncells, tune.kch, nitem_c, item_off, pitems, pn, cap, temp, st));
+                CellWork wp = w;
+                wp.items = pitems;
+                wp.nitems = pn;
+                mark(4);
+                DPC_CK(launch_rho_picks(v, wp, class_mask, cap, d_counters, sb.plist, sb.pstart, st));
+                DPC_CK(launch_rho_scatter(v, st));
+                pick_items = true;
+            } else {
+                DPC_CK(launch_sapprox_rho(v, w, sb, dim_mask, npicks, ncells, rho_mode == 1, st));
+            }
+            density_path = rho_mode == 3 ? 3 : (rho_mode == 1 ? 2 : 1);
             mark(2);
         }
         DPC_TRY(ensure_rank(tmp, temp));
@@ -1116,11 +1141,11 @@ struct Batch {
         DPC_CK(cudaMemcpyAsync(sst, sb.stats, sizeof(sst), cudaMemcpyDeviceToHost, st));
         DPC_CK(cudaMemcpyAsync(pairs, d_stats, sizeof(pairs), cudaMemcpyDeviceToHost, st));
         DPC_TRY(finish_stats("S-Approx-DPC dependent points"));
-        sap_pairs = (int64_t)sst[0];
+        sap_pairs = pick_items ? pick_pairs : (int64_t)sst[0];
         nsecond = (int64_t)sst[1];
         cand_pairs = all_points ? (int64_t)(pairs[0] + pairs[1]) : sap_pairs;
-        dense_pairs = all_points ? (int64_t)pairs[0] : 0;
-        ms_rho_dense = all_points ? elapsed(7, 4) : 0.f;
+        dense_pairs = all_points ? (int64_t)pairs[0] : (pick_items ? pick_pairs : 0);
+        ms_rho_dense = all_points ? elapsed(7, 4) : (pick_items ? elapsed(4, 2) : 0.f);
         ms[0] = elapsed(0, 7);
         ms[1] = elapsed(7, 2);
         ms[2] = elapsed(2, 5);
@@ -1239,7 +1264,7 @@ dpc_status dpc_set_tuning(dpc_ctx* ctx, const char* key, int64_t value) {
     else if (k == "ring2" && value >= 0 && value <= 1) t.ring2 = (int)value;
     else if (k == "sapprox_path" && value >= 0 && value <= 2) t.sapprox_path = (int)value;
     else if (k == "sapprox_ratio" && value >= 1 && value <= 1024) t.sapprox_ratio = (int)value;
-    else if (k == "sapprox_rho_cells" && value >= 0 && value <= 2) t.sapprox_rho_cells = (int)value;
+    else if (k == "sapprox_rho_cells" && value >= 0 && value <= 3) t.sapprox_rho_cells = (int)value;
     else if (k == "sapprox_near_threads" && value >= 0 && value <= 1) t.sapprox_near_threads = (int)value;
     else if (k == "sparse_cand" && value >= 0 && value <= (1ll << 31)) t.sparse_cand = (int)std::min<int64_t>(value, INT32_MAX);
     else if (k == "max_batch_jobs" && value >= 1 && value <= 4096) {
@@ -1467,6 +1492,7 @@ static void fill_info(const Batch& bt, int b, dpc_info* out) {
     out->rank_key_bits = bt.rank_key_bits;
     out->picks = bt.npicks;
     out->second_phase = bt.nsecond;
+    out->density_path = bt.density_path;
 }
 
 dpc_status dpc_ds_info(const dpc_ds* ds, dpc_info* out) {

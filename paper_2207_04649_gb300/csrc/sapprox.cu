@@ -251,6 +251,38 @@ __global__ void __launch_bounds__(128) k_sap_rho_cells(BatchView v, CellWork w, 
     if (lane == 0 && pairs) atomicAdd(&sb.stats[0], pairs);
 }
 
+// Work items of the pick path's density in the dense kernels: for every
+// exact-grid cell holding picks, (cell, chunk of kQch picks, chunk of kch
+// candidates).
+__global__ void k_sap_item_count(CellWork w, SapproxBufs sb, int64_t ncells, int kch, uint32_t* nitem_c) {
+    for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < ncells; c += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t np = sb.pstart[c + 1] - sb.pstart[c];
+        const uint32_t cand = w.cand[c];
+        const uint32_t nk = cand == 0u ? 1u : (cand + kch - 1) / kch;
+        nitem_c[c] = np == 0u ? 0u : (np + kQch - 1) / kQch * nk;
+    }
+}
+
+// Writes the items; a total above cap (which the host's bound rules out)
+// raises the consistency flag and leaves no item to run.
+__global__ void k_sap_fill_items(BatchView v, CellWork w, SapproxBufs sb, int64_t ncells, int kch,
+                                 const uint32_t* item_off, uint4* items, uint32_t* nitems, int64_t cap) {
+    if (blockIdx.x == 0 && threadIdx.x == 0 && (int64_t)*nitems > cap) {
+        *nitems = 0u;
+        atomicOr(v.err, kErrStaging);
+    }
+    for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < ncells; c += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t np = sb.pstart[c + 1] - sb.pstart[c];
+        if (np == 0u) continue;
+        const uint32_t cand = w.cand[c];
+        const uint32_t nq = (np + kQch - 1) / kQch, nk = cand == 0u ? 1u : (cand + kch - 1) / kch;
+        if ((int64_t)item_off[c] + (int64_t)nq * nk > cap) continue;
+        uint4* out = items + item_off[c];
+        for (uint32_t q = 0; q < nq; ++q)
+            for (uint32_t k = 0; k < nk; ++k) out[q * nk + k] = make_uint4((uint32_t)c, q, k, 0u);
+    }
+}
+
 // A point that is not picked depends on its cell's pick.
 __global__ void k_sap_follow(BatchView v, SapproxBufs sb) {
     const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -568,6 +600,18 @@ cudaError_t launch_sapprox_plist(const BatchView& v, const SapproxBufs& sb, int6
     cudaError_t e = exclusive_scan_u32(sb.pflag, sb.ppos, v.N, nullptr, temp, st);
     if (e != cudaSuccess) return e;
     (k_sap_plist<<<grid_for(std::max<int64_t>(v.N, ncells + 1), 256), 256, 0, st>>>(v, sb, ncells), note_launch());
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sapprox_items(const BatchView& v, const CellWork& w, const SapproxBufs& sb, int64_t ncells, int kch,
+                                 uint32_t* nitem_c, uint32_t* item_off, uint4* items, uint32_t* nitems, int64_t cap,
+                                 void* temp, cudaStream_t st) {
+    if (ncells <= 0) return cudaMemsetAsync(nitems, 0, sizeof(uint32_t), st);
+    const unsigned blocks = (unsigned)std::min<int64_t>(152 * 16, grid_for(ncells, 256));
+    (k_sap_item_count<<<blocks, 256, 0, st>>>(w, sb, ncells, kch, nitem_c), note_launch());
+    cudaError_t e = exclusive_scan_u32(nitem_c, item_off, ncells, nitems, temp, st);
+    if (e != cudaSuccess) return e;
+    (k_sap_fill_items<<<blocks, 256, 0, st>>>(v, w, sb, ncells, kch, item_off, items, nitems, cap), note_launch());
     return cudaGetLastError();
 }
 

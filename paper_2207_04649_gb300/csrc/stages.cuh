@@ -221,6 +221,11 @@ cudaError_t launch_fill_items(const BatchView& v, const CellPrepBufs& cb, int64_
 cudaError_t launch_rho(const BatchView& v, const CellWork& w, uint32_t class_mask, int64_t nitems_bound,
                        int64_t nsparse_bound, uint32_t* counters, int parts, cudaStream_t st);
 cudaError_t launch_rho_scatter(const BatchView& v, cudaStream_t st);
+// the dense density kernels with the picks of each cell as its queries
+// (plist[pstart[c] .. pstart[c + 1]), the points of cell c); w.items holds
+// (cell, pick chunk, candidate chunk) items
+cudaError_t launch_rho_picks(const BatchView& v, const CellWork& w, uint32_t class_mask, int64_t nitems_bound,
+                             uint32_t* counters, const uint32_t* plist, const uint32_t* pstart, cudaStream_t st);
 
 // delta.cu
 struct DeltaBufs {
@@ -367,6 +372,10 @@ cudaError_t launch_sapprox_pick_pairs(const BatchView& v, const CellWork& w, con
                                      int64_t picks_bound, cudaStream_t st);
 // by_cell: one warp per exact-grid cell over its picks (needs plist, pstart),
 // else one warp per pick
+// items of launch_rho_picks for every cell holding picks; cap bounds their number
+cudaError_t launch_sapprox_items(const BatchView& v, const CellWork& w, const SapproxBufs& sb, int64_t ncells, int kch,
+                                 uint32_t* nitem_c, uint32_t* item_off, uint4* items, uint32_t* nitems, int64_t cap,
+                                 void* temp, cudaStream_t st);
 cudaError_t launch_sapprox_rho(const BatchView& v, const CellWork& w, const SapproxBufs& sb, uint32_t dim_mask,
                                int64_t picks_bound, int64_t ncells, bool by_cell, cudaStream_t st);
 // rho 0 for the points that are not picked (they rank after every pick)

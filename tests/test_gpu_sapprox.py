@@ -249,11 +249,12 @@ def test_both_paths_by_pair_counts(dpc):
     assert info["dense_pairs"] > 0
 
 
-@pytest.mark.parametrize("path,by_cell,near_threads", [(1, 1, 1), (2, 1, 1), (2, 0, 1), (2, 1, 0)])
+@pytest.mark.parametrize("path,by_cell,near_threads", [(1, 1, 1), (2, 1, 1), (2, 0, 1), (2, 1, 0), (2, 3, 1)])
 @pytest.mark.parametrize("shape", [SHAPES[i] for i in (1, 3, 5, 6, 7, 9, 10)], ids=lambda s: f"n{s[1]}_d{s[2]}_dc{s[3]}")
 def test_forced_paths(dpc, shape, path, by_cell, near_threads):
-    """Either path (the pick path's density by cell or by pick, its near pass
-    by thread or by warp) on any data gives the oracle's bits."""
+    """Either path (the pick path's density by cell, by pick or in the dense
+    kernels over pick items, its near pass by thread or by warp) on any data
+    gives the oracle's bits."""
     seed, n, d, dc, dom, blobs, spread, dup = shape
     ds = workloads.random_blobs(seed, n, d, dc, domain=dom, blobs=blobs, spread=spread, dup=dup)
     for eps in [(4, 5), (3, 1)]:
