@@ -265,6 +265,8 @@ struct Batch {
     // the tree over the cells, built ahead on a second stream while the ring
     // search runs (it needs the ranks only); tree_ev marks its end
     bool tree_ready = false;
+    bool items_filled = false;
+    CellPrepBufs item_prep{};  // the grid build's cell buffers, for fill_items
     cudaStream_t side = nullptr;
     cudaEvent_t side_ev[2] = {nullptr, nullptr};
     int32_t* rho_pub = nullptr;  // S-Approx-DPC: rho as reported (-1 where not picked)
@@ -350,8 +352,18 @@ struct Batch {
         return DPC_OK;
     }
 
+    // The dense cells' work items, once (the density and ring passes over
+    // every point run them; S-Approx-DPC's pick path does not).
+    dpc_status fill_items() {
+        if (items_filled) return DPC_OK;
+        DPC_CK(launch_fill_items(v, item_prep, ndense, tune.kch, st));
+        items_filled = true;
+        return DPC_OK;
+    }
+
     // Local density of every point (sorted and original order).
     dpc_status rho_all() {
+        DPC_TRY(fill_items());
         DPC_CK(cudaMemsetAsync(v.rho_s, 0, sizeof(int32_t) * std::max<int64_t>(N, 1), st));
         DPC_CK(cudaMemsetAsync(d_counters, 0, 64 * sizeof(uint32_t), st));
         DPC_CK(launch_rho(v, w, class_mask, nitems, nsparse, d_counters, 1, st));
@@ -583,7 +595,8 @@ struct Batch {
         }
         nitems = ni;
         DPC_CK(keep.get(&cb.items, nitems + 1));
-        DPC_CK(launch_fill_items(v, cb, ndense, tune.kch, st));
+        items_filled = false;  // written by the first pass that runs them
+        item_prep = cb;
         w.dense = cb.dense;
         w.ndense = cb.ndense;
         w.sparse = cb.sparse;
@@ -1133,7 +1146,13 @@ struct Batch {
         db.bf_rank = tune.bf_rank;
         DPC_CK(launch_sapprox_first(v, w, sb, db, dim_mask, npicks, npicks, !all_points, tune.sapprox_near_threads != 0,
                                     st));
-        DPC_TRY(open_points(tmp, "S-Approx-DPC first phase", false));
+        // the pick path's tree leaves hold the cells' picks only: every point
+        // that ranks above a pick is a pick (the others have rho 0)
+        db.lplist = all_points ? nullptr : sb.plist;
+        db.lpstart = all_points ? nullptr : sb.pstart;
+        const dpc_status ost = open_points(tmp, "S-Approx-DPC first phase", false);
+        db.lplist = db.lpstart = nullptr;
+        DPC_TRY(ost);
         mark(6);
         DPC_CK(keep.get(&rho_pub, N));
         DPC_CK(launch_sapprox_rho_out(v, rho_pub, st));

@@ -495,17 +495,18 @@ __global__ void __launch_bounds__(128) k_sap_first(BatchView v, CellWork w, Sapp
         for (uint32_t ri = 0; ri < nr; ++ri) {
             const uint2 run = runs[ri];
             for (uint32_t q = run.x + lane; q < run.x + run.y; q += 32) {
+                // only a point whose cell of G' has a higher pick matters
+                // (its rank first: the pick's record is shared by its cell)
+                const uint32_t k = sb.pick_s[q];
+                if (k == p) continue;
+                const uint2 kr = v.ro_s[k];
+                if (kr.x >= ro.x) continue;
                 int32_t y[D];
                 sx_load<D>(recb + (int64_t)q * DP, y);
                 const long long dq = sx_dist<D>(x, y);
-                const uint32_t k = sb.pick_s[q];
-                if (k == q) {  // a pick: the nearest higher one of the block, for the second phase
-                    const uint2 cr = v.ro_s[q];
-                    if (cr.x < ro.x) keep_min(bd, bj, dq, cr.y);
-                }
-                if (dq >= ds.d_cut2 || k == p) continue;
-                const uint2 kr = v.ro_s[k];
-                if (kr.x >= ro.x) continue;
+                // a higher pick: the nearest of the block, for the second phase
+                if (k == q) keep_min(bd, bj, dq, kr.y);
+                if (dq >= ds.d_cut2) continue;
                 int32_t z[D];
                 sx_load<D>(recb + (int64_t)k * DP, z);
                 keep_min(fd, fj, sx_dist<D>(x, z), kr.y);

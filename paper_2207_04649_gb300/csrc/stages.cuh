@@ -264,8 +264,15 @@ struct DeltaBufs {
     // Node records: internal node i at record i, leaf c at record ncells + c;
     // each 2 * dpb + 1 int4: box lo, box hi, then {smallest rank, left, right,
     // parent} for an internal node or {smallest rank, first point, end point,
-    // parent} for a leaf. One record is one memory round trip in the search.
+    // parent} for a leaf (with leaf point lists: first and end list entry).
+    // One record is one memory round trip in the search.
     int4* nodes;
+    // Leaf point lists (null: a leaf holds its cell's points, a run of sorted
+    // positions). S-Approx-DPC's pick path: leaf c holds the picks
+    // lplist[lpstart[c] .. lpstart[c + 1]), the only points that can rank
+    // above a pick.
+    const uint32_t* lplist;
+    const uint32_t* lpstart;
     uint32_t* flag;       // [ncells] refit arrival counters
     unsigned long long* stats;  // [0] tree nodes visited, [1] point pairs tested in leaves
 };

@@ -117,9 +117,10 @@ __device__ __forceinline__ int64_t rec_of(const DeltaBufs& db, int32_t ref) {
     return ref >= 0 ? (int64_t)ref : db.ncells + (int64_t)(~ref);
 }
 
-// Leaf records: every cell's box, smallest rank and point run. A lane takes
-// a cell of at most kLeafLane points; larger cells (dense data) are taken by
-// the whole warp, the lanes striding the points.
+// Leaf records: every cell's box, smallest rank and point run (or its range
+// of the leaf point list). A lane takes a cell of at most kLeafLane points;
+// larger cells (dense data) are taken by the whole warp, the lanes striding
+// the points.
 constexpr uint32_t kLeafLane = 64;
 
 __device__ __forceinline__ void write_leaf(const DeltaBufs& db, int64_t c, const int32_t (&lo)[8],
@@ -159,8 +160,8 @@ __global__ void k_leaves(BatchView v, DeltaBufs db) {
         bool big = false, pt = false;
         if (valid) {
             b = find_off(db.cell_off, v.B, c);
-            p0 = v.cell_start[c];
-            p1 = v.cell_start[c + 1];
+            p0 = db.lplist ? db.lpstart[c] : v.cell_start[c];
+            p1 = db.lplist ? db.lpstart[c + 1] : v.cell_start[c + 1];
             // a point-tree dataset's single cell stays empty here (its points
             // are never searched through this tree)
             pt = v.desc[b].ptree != 0;
@@ -175,7 +176,7 @@ __global__ void k_leaves(BatchView v, DeltaBufs db) {
                 hi[k] = INT32_MIN;
             }
             uint32_t mr = 0xffffffffu;
-            for (uint32_t p = p0; p < p1 && !pt; ++p) leaf_add(v, ds, p, lo, hi, mr);
+            for (uint32_t p = p0; p < p1 && !pt; ++p) leaf_add(v, ds, db.lplist ? db.lplist[p] : p, lo, hi, mr);
             write_leaf(db, c, lo, hi, mr, p0, p1);
         }
         unsigned bigm = __ballot_sync(0xffffffffu, big);
@@ -193,7 +194,7 @@ __global__ void k_leaves(BatchView v, DeltaBufs db) {
                 hi[k] = INT32_MIN;
             }
             uint32_t mr = 0xffffffffu;
-            for (uint32_t p = q0 + lane; p < q1; p += 32) leaf_add(v, ds, p, lo, hi, mr);
+            for (uint32_t p = q0 + lane; p < q1; p += 32) leaf_add(v, ds, db.lplist ? db.lplist[p] : p, lo, hi, mr);
             for (int o = 16; o > 0; o >>= 1) {
 #pragma unroll
                 for (int k = 0; k < 8; ++k) {
@@ -299,7 +300,8 @@ __global__ void __launch_bounds__(128) k_tree_search(BatchView v, DeltaBufs db) 
             int4 meta;
             if (out_of_reach(node_test<D>(db.nodes + rec_of(db, nd) * ns, dpb, x, ro.x, meta), bestD)) continue;
             if (nd < 0) {  // a cell: scan its points
-                for (int32_t q = meta.y; q < meta.z; ++q) {
+                for (int32_t t = meta.y; t < meta.z; ++t) {
+                    const uint32_t q = db.lplist ? db.lplist[t] : (uint32_t)t;
                     const uint2 cr = v.ro_s[q];
                     if (cr.x >= ro.x) continue;
                     ++tests;
