@@ -274,13 +274,18 @@ dpc_status dpc_set_profiling(dpc_ctx* ctx, int on);
  *             (one warp per pick for the density and the first-phase scan),
  *             0 chosen by the candidate pairs (default 0)
  *   "sapprox_ratio"  with sapprox_path 0: the pick path when the points'
- *             candidate pairs exceed this many times the picks', 1 .. 1024
+ *             candidate pairs exceed this many times the picks' (at most 4
+ *             times when the points' pairs number 2e10 or more), 1 .. 1024
  *             (default 16)
  *   "sapprox_rho_cells"  the pick path's density: 1 one warp per grid cell
  *             over its picks (candidates staged once per cell), 0 one warp
  *             per pick, 3 the dense density kernels with each cell's picks
  *             as queries, 2 by cell when picks face fewer than 512
  *             candidates each on average, else 3 (default 2)
+ *   "rho_bulk"  dense density kernels of d <= 4 in a 32-bit pair form: 1
+ *             stages the candidates in shared memory by bulk copies
+ *             (cp.async.bulk completed on an mbarrier, one copy per run
+ *             piece), 0 by 128-bit loads through registers (default 0)
  *   "sapprox_near_threads"  the pick path's first-phase scan over the
  *             picks of a pick's neighbour blocks: 1 one thread per pick,
  *             0 one warp per pick (default 1)

@@ -104,6 +104,7 @@ struct BatchView {
 constexpr unsigned kErrStaging = 1u;   // candidate runs shorter than counted
 constexpr unsigned kErrTreeStack = 2u; // tree search stack full
 constexpr unsigned kErrChain = 4u;     // label chain longer than the dataset
+constexpr unsigned kErrBulkWait = 8u;  // a bulk copy into shared memory did not complete in time
 
 // ---------------------------------------------------------------- helpers
 

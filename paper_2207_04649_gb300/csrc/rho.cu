@@ -453,6 +453,312 @@ __global__ void __launch_bounds__(kRhoThreads) k_rho_dense(BatchView v, CellWork
     }
 }
 
+// ------------------------------------------------ bulk-copy staging
+//
+// The same dense pass with its candidates staged by the copy engine: a warp
+// walks its runs for the next chunk of up to kChunk records, and every run
+// piece (a contiguous range of records, 16 bytes each) goes to shared memory
+// as one cp.async.bulk, completed on the chunk buffer's mbarrier by byte
+// count (lane 0 announces the chunk's bytes before any piece is issued).
+// The copy of chunk i + 1 is in flight while chunk i is evaluated. Waits are
+// bounded: a buffer whose bytes do not arrive in time raises kErrBulkWait
+// and the warp stops after a bounded wait for its other buffer. Records of
+// one int4 only (d <= 4), direct 32-bit (mode 0) or expanded (mode 2) form.
+
+constexpr int kBulkSpin = 1 << 22;                 // try_wait rounds before a wait gives up
+constexpr unsigned long long kBulkWaitNs = 1000000000ull;  // or this much wall time (1 s)
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+
+// One test of the phase of the given parity; a thread left waiting is
+// suspended for at most about 1 us.
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity), "r"(1000u)
+        : "memory");
+    return ok != 0u;
+}
+
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Bounded wait for the phase of the given parity: kBulkSpin tests or
+// kBulkWaitNs of wall time, whichever ends first.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const unsigned long long t0 = global_ns();
+    for (int i = 0; i < kBulkSpin; ++i) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if ((i & 255) == 255 && global_ns() - t0 > kBulkWaitNs) return false;
+    }
+    return false;
+}
+
+__device__ __forceinline__ void bulk_copy_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+
+// Orders this thread's earlier generic accesses to shared memory before
+// later copy-engine writes to it.
+__device__ __forceinline__ void fence_proxy_async() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+// Run walk of one item's candidate range, as CandStream's (warp-uniform).
+struct BulkWalk {
+    const uint2* runs;
+    uint32_t nr, ri, roff, remaining;
+
+    __device__ __forceinline__ void init(const uint2* runs_, uint32_t nr_, uint32_t k0, uint32_t k1) {
+        runs = runs_;
+        nr = nr_;
+        ri = 0;
+        roff = k0;
+        remaining = k1 - k0;
+        while (ri < nr) {
+            const uint32_t len = runs[ri].y;
+            if (roff < len) break;
+            roff -= len;
+            ++ri;
+        }
+    }
+
+    // Announces and issues the copies of the next chunk into buf (bar its
+    // mbarrier); returns the records staged (0 when the range is done).
+    // Piece t of the chunk is issued by lane t % 32.
+    __device__ __forceinline__ uint32_t issue(int lane, const int4* __restrict__ recb, int4* buf, uint64_t* bar,
+                                              bool* bad) {
+        if (remaining == 0u) return 0u;
+        const uint32_t total = min((uint32_t)kChunk, remaining);
+        // this lane's pieces (at most 4: a chunk has at most kChunk pieces)
+        uint32_t s0 = 0, s1 = 0, s2 = 0, s3 = 0, d0 = 0, d1 = 0, d2 = 0, d3 = 0, l0 = 0, l1 = 0, l2 = 0, l3 = 0;
+        uint32_t o = 0, t = 0;
+        while (o < total) {
+            if (ri >= nr) {
+                *bad = true;
+                break;
+            }
+            const uint2 run = runs[ri];
+            const uint32_t piece = min(run.y - roff, total - o);
+            if ((t & 31u) == (uint32_t)lane) {
+                const uint32_t sx = run.x + roff, u = t >> 5;
+                if (u == 0u) { s0 = sx; d0 = o; l0 = piece; }
+                else if (u == 1u) { s1 = sx; d1 = o; l1 = piece; }
+                else if (u == 2u) { s2 = sx; d2 = o; l2 = piece; }
+                else { s3 = sx; d3 = o; l3 = piece; }
+            }
+            ++t;
+            o += piece;
+            roff += piece;
+            if (roff == run.y) {
+                ++ri;
+                roff = 0;
+            }
+        }
+        remaining -= total;
+        if (o == 0u) return 0u;
+        if (lane == 0) mbar_arrive_expect(bar, o * (uint32_t)sizeof(int4));
+        __syncwarp();
+        if (l0) bulk_copy_g2s(buf + d0, recb + s0, l0 * (uint32_t)sizeof(int4), bar);
+        if (l1) bulk_copy_g2s(buf + d1, recb + s1, l1 * (uint32_t)sizeof(int4), bar);
+        if (l2) bulk_copy_g2s(buf + d2, recb + s2, l2 * (uint32_t)sizeof(int4), bar);
+        if (l3) bulk_copy_g2s(buf + d3, recb + s3, l3 * (uint32_t)sizeof(int4), bar);
+        return o;
+    }
+};
+
+template <int D, int MODE>
+__global__ void __launch_bounds__(kRhoThreads) k_rho_dense_bulk(BatchView v, CellWork w, uint32_t* counter) {
+    static_assert(D <= 4 && (MODE == 0 || MODE == 2), "one int4 per record, 32-bit forms");
+    constexpr bool EXP = MODE == 2;
+    __shared__ __align__(128) int4 sbuf[kRhoThreads / 32][2][kChunk];  // double buffer per warp
+    __shared__ uint2 sruns[kRhoThreads / 32][kMaxNb];
+    __shared__ __align__(8) uint64_t sbar[kRhoThreads / 32][2];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    uint2* srun = sruns[wid];
+    uint64_t* bar = sbar[wid];
+    if (lane == 0) {
+        mbar_init(&bar[0], 1u);
+        mbar_init(&bar[1], 1u);
+    }
+    fence_proxy_async();
+    __syncwarp();
+    uint32_t par = 0u;  // bit b: parity of buffer b's next phase
+    const uint32_t nitems = *w.nitems;
+    uint32_t nx = 0, it_n = 0, c_n = 0, cs_n = 0, ce_n = 0, nr_n = 0, ct_n = 0;
+    uint4 item_n = make_uint4(0u, 0u, 0u, 0u);
+    auto stage = [&](int s) {
+        if (s == 0) {
+            it_n = __shfl_sync(0xffffffffu, nx, 0);
+            if (it_n < nitems) item_n = w.items[it_n];
+        } else if (s == 1) {
+            if (it_n < nitems) c_n = w.dense[item_n.x];
+        } else if (s == 2) {
+            if (it_n < nitems) {
+                cs_n = v.cell_start[c_n];
+                ce_n = v.cell_start[c_n + 1];
+                nr_n = w.nruns[c_n];
+                ct_n = w.cand[c_n];
+            }
+        }
+    };
+    if (lane == 0) nx = atomicAdd(counter, 1u);
+    stage(0);
+    stage(1);
+    stage(2);
+    bool stop = false;
+    while (!stop) {
+        const uint32_t it = it_n;
+        if (it >= nitems) break;
+        const uint4 item = item_n;  // (dense cell, query chunk, candidate chunk)
+        const uint32_t qc = item.y, kc = item.z;
+        const uint32_t c = c_n;
+        const uint32_t cs = cs_n, m = ce_n - cs_n;
+        const uint32_t nr_c = nr_n, ctot_c = ct_n;
+        if (lane == 0) nx = atomicAdd(counter, 1u);
+        int pf = 0;
+        const int b = find_ds(v.pt_off, v.B, cs);
+        const DsDesc& ds = v.desc[b];
+        if (ds.d != D || ds.mode != MODE) {
+            for (; pf < 3; ++pf) stage(pf);
+            continue;
+        }
+        const int4* recb = v.rec + ds.rec_off - ds.pt_off;  // indexed by global sorted position
+        const int q0 = (int)qc * kQch;
+        const int nq = min(kQch, (int)m - q0);
+        int Q, Mq;
+        lane_layout(nq, Q, Mq);
+        const int G = 32 / Mq;
+        const int grp = lane / Mq, ql = lane & (Mq - 1);
+        int32_t qx[4][D];
+#pragma unroll
+        for (int t = 0; t < 4; ++t) load_point<D>(recb + ((int64_t)cs + q0 + min(ql * Q + t, nq - 1)), qx[t]);
+        int32_t org[3] = {0, 0, 0};
+        int32_t qa[4][3], qb[4];
+        if (EXP) {
+#pragma unroll
+            for (int k = 0; k < D && k < 3; ++k) org[k] = ds.lo[k];
+            for (int j = 0; j < ds.k; ++j) {
+                const int g = ds.gdim[j];
+                const int32_t cc = cell_coord(ds, j, rec_coord(recb + (int64_t)cs, g));
+                const int32_t corner = ds.origin[j] + cc * (int32_t)ds.s;
+#pragma unroll
+                for (int k = 0; k < 3; ++k)
+                    if (k == g) org[k] = corner;
+            }
+#pragma unroll
+            for (int t = 0; t < 4; ++t) {
+                int32_t nrm = -(int32_t)ds.d_cut2;
+#pragma unroll
+                for (int k = 0; k < 3; ++k) {
+                    const int32_t qk = k < D ? qx[t][k < D ? k : 0] - org[k] : 0;
+                    qa[t][k] = -2 * qk;
+                    nrm += qk * qk;
+                }
+                qb[t] = nrm;
+            }
+        }
+        uint32_t cnt[4] = {0u, 0u, 0u, 0u};
+        const uint32_t nr = nr_c, ctot = ctot_c;
+        const uint2* runs_c = w.runs + (int64_t)c * w.nbs;
+        if (nr <= (uint32_t)kMaxNb) {
+            for (uint32_t t = lane; t < nr; t += 32) srun[t] = runs_c[t];
+            runs_c = srun;
+        }
+        __syncwarp();
+        const uint32_t k0 = kc * (uint32_t)w.kch;
+        BulkWalk walk;
+        walk.init(runs_c, nr, k0, min(ctot, k0 + (uint32_t)w.kch));
+        bool bad = false;
+        const int64_t T = ds.d_cut2;
+        int sb = 0;
+        uint32_t cur = walk.issue(lane, recb, sbuf[wid][sb], &bar[sb], &bad);
+        while (cur > 0u) {
+            // the next chunk's copies go out before this chunk is used
+            const uint32_t nxt = walk.issue(lane, recb, sbuf[wid][sb ^ 1], &bar[sb ^ 1], &bad);
+            const bool ok = mbar_wait(&bar[sb], (par >> sb) & 1u);
+            par ^= 1u << sb;
+            if (!ok) {
+                if (lane == 0) atomicOr(v.err, kErrBulkWait);
+                if (nxt > 0u) mbar_wait(&bar[sb ^ 1], (par >> (sb ^ 1)) & 1u);
+                stop = true;
+                break;
+            }
+            int4* buf = sbuf[wid][sb];
+            const int nb = (int)cur;
+            if (EXP) {
+                // relative to the cell corner, |c'|^2 in the w lane
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int f = lane + 32 * u;
+                    if (f < nb) {
+                        const int4 r = buf[f];
+                        const int32_t cx = r.x - org[0], cy = D > 1 ? r.y - org[1] : 0, cz = D > 2 ? r.z - org[2] : 0;
+                        buf[f] = make_int4(cx, cy, cz, cx * cx + cy * cy + cz * cz);
+                    }
+                }
+                __syncwarp();
+            }
+            if (pf < 3) stage(pf++);
+            if (EXP) {
+                switch (Q) {
+                    case 1: eval_rho_x<D, 1>(buf, nb, grp, G, qa, qb, cnt); break;
+                    case 2: eval_rho_x<D, 2>(buf, nb, grp, G, qa, qb, cnt); break;
+                    case 3: eval_rho_x<D, 3>(buf, nb, grp, G, qa, qb, cnt); break;
+                    default: eval_rho_x<D, 4>(buf, nb, grp, G, qa, qb, cnt); break;
+                }
+            } else {
+                switch (Q) {
+                    case 1: eval_rho<D, false, 1>(buf, nb, grp, G, qx, cnt, T); break;
+                    case 2: eval_rho<D, false, 2>(buf, nb, grp, G, qx, cnt, T); break;
+                    case 3: eval_rho<D, false, 3>(buf, nb, grp, G, qx, cnt, T); break;
+                    default: eval_rho<D, false, 4>(buf, nb, grp, G, qx, cnt, T); break;
+                }
+            }
+            // every lane is done with this buffer before copies refill it
+            fence_proxy_async();
+            __syncwarp();
+            sb ^= 1;
+            cur = nxt;
+        }
+        if (stop) break;
+        for (; pf < 3; ++pf) stage(pf);
+        if (bad && lane == 0) atomicOr(v.err, kErrStaging);
+        __syncwarp();
+#pragma unroll
+        for (int t = 0; t < 4; ++t)
+            for (int o = Mq; o < 32; o <<= 1) cnt[t] += __shfl_xor_sync(0xffffffffu, cnt[t], o);
+        if (grp == 0) {
+#pragma unroll
+            for (int t = 0; t < 4; ++t)
+                if (t < Q && ql * Q + t < nq) atomicAdd(&v.rho_s[cs + q0 + ql * Q + t], (int)cnt[t]);
+        }
+    }
+}
+
 template <int D, bool W64>
 __global__ void __launch_bounds__(256) k_rho_sparse(BatchView v, CellWork w) {
     constexpr int DP = D <= 4 ? 1 : 2;
@@ -500,6 +806,14 @@ void launch_rho_dense(const BatchView& v, const CellWork& w, int64_t nitems_boun
     if (nitems_bound <= 0) return;
     const unsigned blocks = (unsigned)std::max<int64_t>(1, std::min<int64_t>(152 * 16, (nitems_bound + 3) / 4));
     (k_rho_dense<D, MODE, QL><<<blocks, kRhoThreads, 0, st>>>(v, w, counter, qlist, qstart), note_launch());
+}
+
+template <int D, int MODE>
+void launch_rho_dense_bulk(const BatchView& v, const CellWork& w, int64_t nitems_bound, uint32_t* counter,
+                           cudaStream_t st) {
+    if (nitems_bound <= 0) return;
+    const unsigned blocks = (unsigned)std::max<int64_t>(1, std::min<int64_t>(152 * 16, (nitems_bound + 3) / 4));
+    (k_rho_dense_bulk<D, MODE><<<blocks, kRhoThreads, 0, st>>>(v, w, counter), note_launch());
 }
 
 template <int D, bool W64>
@@ -552,20 +866,37 @@ cudaError_t launch_fill_items(const BatchView& v, const CellPrepBufs& cb, int64_
     return cudaGetLastError();
 }
 
+// The dense kernel of class (D, M): with bulk, the copy-engine staging where
+// it exists (one int4 per record, a 32-bit form).
+template <int D, int M>
+void launch_dense_class(const BatchView& v, const CellWork& w, int64_t nitems_bound, uint32_t* counter, bool bulk,
+                        cudaStream_t st) {
+    if constexpr (D <= 4 && M != 1) {
+        if (bulk) {
+            launch_rho_dense_bulk<D, M>(v, w, nitems_bound, counter, st);
+            return;
+        }
+    }
+    launch_rho_dense<D, M>(v, w, nitems_bound, counter, st);
+}
+
 cudaError_t launch_rho(const BatchView& v, const CellWork& w, uint32_t class_mask, int64_t nitems_bound,
                        int64_t nsparse_bound, uint32_t* counters, int parts, cudaStream_t st) {
     // one dense launch per (dimension, arithmetic mode) class present in the
     // batch and one sparse launch per (dimension, width); each kernel skips
-    // the work of the other classes. parts: bit 0 dense kernels, bit 1 sparse
+    // the work of the other classes. parts: bit 0 dense kernels, bit 1
+    // sparse, bit 2 bulk-copy staging in the dense kernels that have it
+    const bool bulk = (parts & 4) != 0;
 #define DPC_BIT(D, M) (class_mask & (1u << (3 * ((D) - 1) + (M))))
 #define DPC_RHO_CLASS(D)                                                                                  \
-    if ((parts & 1) && DPC_BIT(D, 0)) launch_rho_dense<D, 0>(v, w, nitems_bound, counters + 3 * (D - 1), st); \
+    if ((parts & 1) && DPC_BIT(D, 0))                                                                     \
+        launch_dense_class<D, 0>(v, w, nitems_bound, counters + 3 * (D - 1), bulk, st);                  \
     if ((parts & 1) && DPC_BIT(D, 1))                                                                     \
-        launch_rho_dense<D, 1>(v, w, nitems_bound, counters + 3 * (D - 1) + 1, st);                       \
+        launch_dense_class<D, 1>(v, w, nitems_bound, counters + 3 * (D - 1) + 1, bulk, st);              \
     if ((parts & 2) && (DPC_BIT(D, 0) || DPC_BIT(D, 2))) launch_rho_sparse<D, false>(v, w, nsparse_bound, st); \
     if ((parts & 2) && DPC_BIT(D, 1)) launch_rho_sparse<D, true>(v, w, nsparse_bound, st);
 #define DPC_RHO_X(D) \
-    if ((parts & 1) && DPC_BIT(D, 2)) launch_rho_dense<D, 2>(v, w, nitems_bound, counters + 3 * (D - 1) + 2, st);
+    if ((parts & 1) && DPC_BIT(D, 2)) launch_dense_class<D, 2>(v, w, nitems_bound, counters + 3 * (D - 1) + 2, bulk, st);
     DPC_RHO_CLASS(1) DPC_RHO_CLASS(2) DPC_RHO_CLASS(3) DPC_RHO_CLASS(4)
     DPC_RHO_CLASS(5) DPC_RHO_CLASS(6) DPC_RHO_CLASS(7) DPC_RHO_CLASS(8)
     DPC_RHO_X(1) DPC_RHO_X(2) DPC_RHO_X(3)

@@ -133,6 +133,8 @@ struct Tune {
     int sapprox_path = 0;     // S-Approx-DPC: 0 by the pair counts, 1 all points, 2 picks only
     int sapprox_rho_cells = 2;  // S-Approx-DPC pick path: density by cell (1), one warp per pick (0), the
                                 //   dense kernels over pick items (3), 1 or 3 by the candidates per pick (2)
+    int rho_bulk = 0;              // dense density kernels (d <= 4, 32-bit forms): candidates staged by bulk
+                                   //   copies (cp.async.bulk) instead of 128-bit loads through registers
     int sapprox_near_threads = 1;  // S-Approx-DPC pick path: near pass one thread (1) or one warp (0) per pick
     int sapprox_ratio = 16;   // S-Approx-DPC: the pick path when the points' pairs exceed this many times the picks'
 };
@@ -366,7 +368,7 @@ struct Batch {
         DPC_TRY(fill_items());
         DPC_CK(cudaMemsetAsync(v.rho_s, 0, sizeof(int32_t) * std::max<int64_t>(N, 1), st));
         DPC_CK(cudaMemsetAsync(d_counters, 0, 64 * sizeof(uint32_t), st));
-        DPC_CK(launch_rho(v, w, class_mask, nitems, nsparse, d_counters, 1, st));
+        DPC_CK(launch_rho(v, w, class_mask, nitems, nsparse, d_counters, 1 | (tune.rho_bulk ? 4 : 0), st));
         mark(4);
         DPC_CK(launch_rho(v, w, class_mask, nitems, nsparse, d_counters, 2, st));
         for (int d = 1; d <= kMaxDims; ++d)
@@ -1072,16 +1074,20 @@ struct Batch {
         // densities of the picks; the others get 0 and rank after every
         // pick. The all-point path (dense density kernels, then the ring
         // search over pick ranks) evaluates all_pairs candidate pairs twice
-        // at a low cost per pair; the pick path (one warp per pick for the
-        // density and for the first-phase scan) evaluates pick_pairs twice
-        // at about ten times that cost, and both carry fixed costs per point
-        // (grid, ranks, the searches for open points). Measured crossovers
-        // in all_pairs / pick_pairs: about 4 (1M x 8), 15 (5.8M x 3 with
-        // mean rho in the thousands), 50 (5.8M x 3, mean rho 100).
+        // at a low cost per pair; the pick path (the picks' density, then
+        // the first-phase scan per queued pick) evaluates pick_pairs twice
+        // at a few times that cost, and both carry fixed costs per point
+        // (grid, ranks, the searches for open points). Measured: at 5.8M x 3
+        // with mean rho 100 (ratio 6.3) the all-point path is faster, 13.3
+        // vs 15.4 ms; on the same points with mean rho in the thousands the
+        // pick path is, from ratio 5.0 (eps 0.2) on.
         bool pick_items = false;
         density_path = 0;
-        const bool all_points = tune.sapprox_path == 1 ||
-                                (tune.sapprox_path == 0 && pick_pairs * (int64_t)tune.sapprox_ratio >= all_pairs);
+        // With many pairs (2e10 and more) their cost outweighs the paths'
+        // fixed costs and the pick path wins from a ratio of 4 (dense
+        // 5.8M x 3 at eps 0.2: ratio 5.0, 80 vs 122 ms).
+        const int64_t ratio = all_pairs >= 20000000000ll ? std::min<int64_t>(4, tune.sapprox_ratio) : tune.sapprox_ratio;
+        const bool all_points = tune.sapprox_path == 1 || (tune.sapprox_path == 0 && pick_pairs * ratio >= all_pairs);
         if (all_points) {
             DPC_TRY(rho_all());
             DPC_CK(launch_sapprox_mask(v, st));
@@ -1285,6 +1291,7 @@ dpc_status dpc_set_tuning(dpc_ctx* ctx, const char* key, int64_t value) {
     else if (k == "sapprox_ratio" && value >= 1 && value <= 1024) t.sapprox_ratio = (int)value;
     else if (k == "sapprox_rho_cells" && value >= 0 && value <= 3) t.sapprox_rho_cells = (int)value;
     else if (k == "sapprox_near_threads" && value >= 0 && value <= 1) t.sapprox_near_threads = (int)value;
+    else if (k == "rho_bulk" && value >= 0 && value <= 1) t.rho_bulk = (int)value;
     else if (k == "sparse_cand" && value >= 0 && value <= (1ll << 31)) t.sparse_cand = (int)std::min<int64_t>(value, INT32_MAX);
     else if (k == "max_batch_jobs" && value >= 1 && value <= 4096) {
         std::lock_guard<std::mutex> lk(ctx->mu);
@@ -1311,6 +1318,7 @@ dpc_status dpc_get_tuning(dpc_ctx* ctx, const char* key, int64_t* value) {
     else if (k == "sapprox_ratio") *value = t.sapprox_ratio;
     else if (k == "sapprox_rho_cells") *value = t.sapprox_rho_cells;
     else if (k == "sapprox_near_threads") *value = t.sapprox_near_threads;
+    else if (k == "rho_bulk") *value = t.rho_bulk;
     else if (k == "max_batch_jobs") {
         std::lock_guard<std::mutex> lk(ctx->mu);
         *value = ctx->max_batch_jobs;

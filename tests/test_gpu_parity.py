@@ -122,6 +122,20 @@ def test_random_shapes_point_tree(dpc, shape):
     assert info["grid_dims"] == 0
 
 
+@pytest.mark.parametrize("knobs", [dict(rho_bulk=1), dict(rho_bulk=1, sparse_cand=0, kch=64),
+                                   dict(rho_bulk=1, hd_min_d=1, hd_cell_factor=2, sparse_cand=0)],
+                         ids=["bulk", "bulk_all_dense_small_items", "bulk_reach2"])
+@pytest.mark.parametrize("shape", SHAPES, ids=lambda s: f"n{s[1]}_d{s[2]}_dc{s[3]}")
+def test_random_shapes_bulk_staging(dpc, shape, knobs):
+    """The dense density kernels with candidates staged by bulk copies into
+    shared memory (d <= 4): every cell on that path, items of 64
+    candidates (many chunks, ragged tails), and reach 2 (runs read in
+    place) give the oracle's bits."""
+    seed, n, d, dc, dom, blobs, spread, dup = shape
+    ds = workloads.random_blobs(seed, n, d, dc, domain=dom, blobs=blobs, spread=spread, dup=dup)
+    assert_full_parity(dpc, ds.points, dc, [(2, dc + 1), (5, 10 * dc)], knobs)
+
+
 @pytest.mark.parametrize("sparse_cand", [512, 0, 2147483647])
 @pytest.mark.parametrize("d", [5, 6, 7, 8])
 @pytest.mark.parametrize("f", [1, 2, 3])
@@ -317,7 +331,7 @@ def test_plain_5p8m_3d_sampled(dpc):
                                    dict(kch=64, bf_rank=100000), dict(kmax=2), dict(kmax=1, clevel=3),
                                    dict(tree_min_d=3), dict(tree_min_d=1, bf_rank=0), dict(ring2=0),
                                    dict(ring2=1, bf_rank=0), dict(sparse_cand=0), dict(sparse_cand=2147483647),
-                                   dict(sparse_cand=20, kch=64)],
+                                   dict(sparse_cand=20, kch=64), dict(rho_bulk=1)],
                          ids=lambda k: ",".join(f"{a}={b}" for a, b in k.items()))
 def test_tuning_knobs_do_not_change_results(dpc, knobs):
     ds = workloads.random_blobs(77, 6000, 3, 900, blobs=5, spread=0.06, dup=8)
