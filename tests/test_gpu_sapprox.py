@@ -260,3 +260,27 @@ def test_forced_paths(dpc, shape, path, by_cell, near_threads):
     for eps in [(4, 5), (3, 1)]:
         check_full(dpc, ds.points, dc, eps, [(2, dc + 1), (1, 3 * dc + 1)],
                    knobs={"sapprox_path": path, "sapprox_rho_cells": by_cell, "sapprox_near_threads": near_threads})
+
+
+@pytest.mark.parametrize("eps", [(1, 20), (1, 5)], ids=lambda e: f"eps{e[0]}_{e[1]}")
+@pytest.mark.parametrize("kch", [64, 2048])
+def test_pick_items_chunks(dpc, eps, kch):
+    """The pick path's density in the dense kernels over pick items: cells
+    with more than 128 picks (several pick chunks per cell, small eps) and
+    items of 64 candidates (several candidate chunks) give the oracle's
+    bits, and the info names the path."""
+    ds = workloads.random_blobs(91, 6000, 3, 400, domain=20000, blobs=3, spread=0.01, dup=4)
+    info = check_full(dpc, ds.points, 400, eps, [(2, 401), (1, 1201)],
+                      knobs={"sapprox_path": 2, "sapprox_rho_cells": 3, "kch": kch})
+    assert info["density_path"] == 3
+    assert info["dense_pairs"] == info["cand_pairs"] > 0
+
+
+def test_density_path_reported(dpc):
+    """dpc_info.density_path follows the path each call took."""
+    ds = workloads.random_blobs(92, 3000, 2, 300, domain=30000, blobs=3, spread=0.03, dup=2)
+    for knobs, path in [({"sapprox_path": 1}, 0), ({"sapprox_path": 2, "sapprox_rho_cells": 0}, 1),
+                        ({"sapprox_path": 2, "sapprox_rho_cells": 1}, 2),
+                        ({"sapprox_path": 2, "sapprox_rho_cells": 3}, 3)]:
+        info = check_full(dpc, ds.points, 300, (4, 5), [(2, 301)], knobs=knobs)
+        assert info["density_path"] == path, knobs
