@@ -63,6 +63,8 @@ def parse():
                     help="S-Approx-DPC: comma-separated eps values for a time / Rand-index curve")
     ap.add_argument("--cpu-sample", type=int, default=0, help="oracle sample size (0: automatic)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--tune", default="",
+                    help="tuning knobs for the timed context, key=value[,key=value...] (dpc_set_tuning)")
     return ap.parse_args()
 
 
@@ -75,6 +77,17 @@ def parse_eps(text: str):
     num, den = int(round(float(text) * 10 ** 6)), 10 ** 6
     g = math.gcd(num, den)
     return num // g, den // g
+
+
+def parse_tune(text: str) -> dict:
+    """Tuning knobs "key=value,key=value" as {key: int}."""
+    out = {}
+    for item in filter(None, (t.strip() for t in text.split(","))):
+        key, sep, val = item.partition("=")
+        if not sep or not key.strip():
+            raise ValueError(f"--tune expects key=value, got {item!r}")
+        out[key.strip()] = int(val)
+    return out
 
 
 def dist_env():
@@ -304,6 +317,9 @@ def run_ours(args):
     lab = torch.empty(n, dtype=torch.int32, device=dev)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)  # > L2 (126 MB)
     ctx = dpc.Context(device=local, profiling=True)
+    knobs = parse_tune(args.tune)
+    if knobs:
+        ctx.tune(**knobs)
     st = ctx.stream
 
     approx = args.method == "approx"
@@ -398,14 +414,16 @@ def run_ours(args):
     dpairs = infos[-1]["dense_pairs"]
     achieved = pairs / (rho_ms / 1e3) if rho_ms > 0 else 0.0
     dachieved = dpairs / (dense_ms / 1e3) if dense_ms > 0 else 0.0
-    # the DRAM capture covers the density kernels over every point only
+    # the DRAM capture covers the density kernels over every point, with the
+    # default knobs, only
     all_points = infos[-1].get("density_path", 0) == 0
-    traffic = rho_traffic(args.workload) if all_points else None
-    dtraffic = rho_traffic(args.workload, "dram_bytes_per_launch_dense") if all_points else None
+    traffic = rho_traffic(args.workload) if all_points and not knobs else None
+    dtraffic = rho_traffic(args.workload, "dram_bytes_per_launch_dense") if all_points and not knobs else None
 
     if dpairs > 0:
         queries = "each grid cell's picks" if infos[-1].get("density_path") == 3 else "dense cells"
-        roofline = {"bound": "alu", "kernel": f"k_rho_dense ({queries}, pair form {pair_mode})",
+        kname = "k_rho_dense_bulk" if knobs.get("rho_bulk") and all_points and d <= 4 and pair_mode != 1 else "k_rho_dense"
+        roofline = {"bound": "alu", "kernel": f"{kname} ({queries}, pair form {pair_mode})",
                     "achieved": dachieved / 1e9, "peak": probe_rate / 1e9, "unit": "Gpair/s",
                     "frac": dachieved / probe_rate, "traffic": dtraffic,
                     "pairs_per_launch": dpairs, "ms_per_launch": dense_ms,
@@ -483,7 +501,8 @@ def run_ours(args):
                        "n": n, "d": d, "d_cut": ds.d_cut, "rho_min": ds.rho_min,
                        "delta_min": ds.delta_min, "parallelism": f"replicas x{ws}",
                        "l2": "flushed between steps (256 MB write)",
-                       "mean_rho": float(rho.double().mean().item()), "n_centers": int(nc)},
+                       "mean_rho": float(rho.double().mean().item()), "n_centers": int(nc),
+                       **({"tune": knobs} if knobs else {})},
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": n * d * 4,
                     "d2h_bytes_per_step": n * (4 + 4 + 8 + 4 + (1 if sapprox else 0)) + 8},
             "roofline": roofline,

@@ -83,6 +83,17 @@ def test_reference_arm_approximate_methods(method):
     assert line["metric"].startswith("S-Approx-DPC" if method == "sapprox" else "Approx-DPC")
 
 
+def test_parse_tune():
+    import bench
+    assert bench.parse_tune("") == {}
+    assert bench.parse_tune("rho_bulk=1") == {"rho_bulk": 1}
+    assert bench.parse_tune(" kch=64, sapprox_path=2 ,") == {"kch": 64, "sapprox_path": 2}
+    with pytest.raises(ValueError):
+        bench.parse_tune("kch")
+    with pytest.raises(ValueError):
+        bench.parse_tune("kch=x")
+
+
 def test_parse_eps():
     sys.path.insert(0, ROOT)
     import bench
