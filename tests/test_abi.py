@@ -81,3 +81,13 @@ def test_eps_fraction():
     assert dpc.eps_fraction(0.000001) == (1, 1000000)
     with pytest.raises(ValueError):
         dpc.eps_fraction(0.0)
+
+
+def test_tuning_keys_documented():
+    """Every key dpc_set_tuning accepts is documented in the header, and
+    every documented key is accepted (read from the sources: no device)."""
+    src = open(os.path.join(ROOT, "paper_2207_04649_gb300", "csrc", "runtime.cu")).read()
+    accepted = set(re.findall(r'k == "([a-z_0-9]+)"', src))
+    doc = open(os.path.join(ROOT, "include", "dpc.h")).read()
+    documented = set(re.findall(r'^ \*\s+"([a-z_0-9]+)"', doc, flags=re.M))
+    assert accepted and accepted == documented, (accepted ^ documented)
