@@ -183,23 +183,36 @@ dpc_status dpc_cluster(dpc_ctx* ctx, const int32_t* points, int64_t n, int32_t d
 dpc_status dpc_release(dpc_ds* ds);
 
 /* Labels with no device allocation. The paper has no counterpart: this is a
- * variant of the labels step (the same result as dpc_label) for callers that
- * cannot allocate device memory when they call, e.g. code running on a
- * device budget reserved up front, in a section that must not allocate, or
- * under a memory pool that fails once exhausted. Its scratch (the parent of
- * every point) is a fixed array compiled into the library: 2^22 points
- * (16 MiB), held on every GPU that loads the library until the process
- * exits.
- *   rho, dep, delta2: device arrays of n points as dpc_density /
- *            dpc_dependent produce them (dep = -1 and delta2 = INT64_MAX for
- *            the densest point); read only.
+ * variant of the labels step for callers that cannot allocate device memory
+ * when they call, e.g. code running on a device budget reserved up front, in
+ * a section that must not allocate, or under a memory pool that fails once
+ * exhausted. Its scratch (the parent of every point) is a fixed array
+ * compiled into the library: 2^22 points (16 MiB), held on every GPU that
+ * loads the library until the process exits.
+ *   rho, dep, delta2: device arrays of n points as dpc_density and
+ *            dpc_dependent (or dpc_dependent_approx) produce them (dep = -1
+ *            and delta2 = INT64_MAX for the densest point); read only. On
+ *            these inputs the labels and the center count equal dpc_label's.
+ *            S-Approx-DPC datasets are not covered (their points that are
+ *            not picked take their pick's label, which this call does not
+ *            model): use dpc_label for those.
  *   n:       0 <= n <= 4194304; larger n gives DPC_ERR_INVALID_ARG.
  *   rho_min, delta_min: as dpc_label; 1 <= delta_min <= 3037000499 (the
- *            caller keeps delta_min > d_cut).
- *   label_out: device array of n int32 (center's index, -1 noise).
- *   n_centers_out: NULL or one device int64.
+ *            caller keeps delta_min > d_cut), else DPC_ERR_INVALID_ARG.
+ *   label_out: device array of n int32: the center's index, -1 for noise,
+ *            -2 for a point whose chain of dependent points runs into a
+ *            rejected link (below).
+ *   n_centers_out: NULL or one device int64: the number of centers, or -1
+ *            when a link was rejected.
  *   cuda_stream: the cudaStream_t the work is queued on (NULL: the legacy
- *            default stream). The call returns once the work is queued.
+ *            default stream). The call returns once the work is queued, so
+ *            it returns DPC_OK before the links are checked: a caller that
+ *            passes links it did not get from this library reads
+ *            n_centers_out to learn whether they were accepted.
+ * A link of a point that is neither noise nor a center is accepted when dep
+ * lies in [0, n) and ranks strictly higher in (rho desc, index asc), as
+ * Definitions 2-3 make it; such links always form a forest. An out-of-range
+ * dep is never used to read memory.
  * The first call on a device looks up the scratch's device address for that
  * device (cudaGetSymbolAddress, with the device current); make that first
  * call before any stream capture. All calls share the scratch and it keeps
