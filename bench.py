@@ -63,6 +63,8 @@ def parse():
                     help="S-Approx-DPC: comma-separated eps values for a time / Rand-index curve")
     ap.add_argument("--cpu-sample", type=int, default=0, help="oracle sample size (0: automatic)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--rate", type=float, default=200.0,
+                    help="served_trace: offered jobs/s of the Poisson trace (200 by default)")
     ap.add_argument("--tune", default="",
                     help="tuning knobs for the timed context, key=value[,key=value...] (dpc_set_tuning)")
     return ap.parse_args()
@@ -609,7 +611,7 @@ def run_reference(args):
 # ------------------------------------------------- batched and served forms
 
 BATCH_METRIC = "batched exact DPC jobs/s (256 datasets, n 1k-200k, d 2-4)"
-SERVED_METRIC = "served exact DPC jobs/s (Poisson 200 jobs/s, n 10k-2M, d 2-8, 1-4 re-queries)"
+SERVED_METRIC = "served exact DPC jobs/s (Poisson {rate:g} jobs/s, n 10k-2M, d 2-8, 1-4 re-queries)"
 
 
 def run_batched(args):
@@ -777,7 +779,7 @@ def run_served(args):
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     dev = torch.device("cuda", local)
-    trace = workloads.served_trace()
+    trace = workloads.served_trace(rate_per_s=args.rate)
     warm = workloads.served_trace(seed=6, jobs=max(8, args.warmup * 8), pool=8)
 
     def serve(max_batch):
@@ -806,11 +808,12 @@ def run_served(args):
     value = whole_job_rate(ws, len(trace), 1, 1e3 * span)
     if rank == 0:
         line = {
-            "metric": SERVED_METRIC, "value": value, "unit": "jobs/s", "n_gpus": ws, "steps": 1,
+            "metric": SERVED_METRIC.format(rate=args.rate), "value": value, "unit": "jobs/s", "n_gpus": ws,
+            "steps": 1,
             "warmup": len(warm), "ms_per_step": 1e3 * span, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "int32",
             "data": "synthetic (seeded Poisson trace of Gaussian-blob mixtures, int32 coordinates)",
-            "config": {"workload": "served_trace", "jobs": len(trace), "offered_jobs_per_s": 200.0,
+            "config": {"workload": "served_trace", "jobs": len(trace), "offered_jobs_per_s": args.rate,
                        "trace_s": trace[-1].arrival_s, "points": pts, "hbm_cap_gb": 150,
                        "parallelism": f"replicas x{ws}",
                        "l2": "inputs are copied from host memory for every job",

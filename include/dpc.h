@@ -303,6 +303,8 @@ dpc_status dpc_set_profiling(dpc_ctx* ctx, int on);
  *             picks of a pick's neighbour blocks: 1 one thread per pick,
  *             0 one warp per pick (default 1)
  *   "max_batch_jobs"  served mode: jobs one batch admits at most, 1 .. 4096
+ *   "max_batch_points" served mode: points one batch admits at most, 1 .. 2^31 - 1 (a larger job
+ *                     runs in a batch of its own, so that it does not hold back small ones)
  *             (default 64; 1 runs the jobs one at a time)
  * DPC_ERR_INVALID_ARG for an unknown key or a value out of range. */
 dpc_status dpc_set_tuning(dpc_ctx* ctx, const char* key, int64_t value);
@@ -319,7 +321,10 @@ int64_t dpc_kernel_launches(void);
  * density kernel is compared against, in the form dpc_ds_info reports as
  * pair_mode: 0 the direct 32-bit form (sum of squared differences), 1 the
  * direct 64-bit form, 2 the expanded 32-bit form around a cell corner
- * (d <= 3). Other modes give DPC_ERR_INVALID_ARG. Writes pairs per
+ * (d <= 3); and mode 3, the dependent-point ring search's pair test in the
+ * expanded form (d <= 3: the same sum, a rank compare and the least packed
+ * (distance, index) key kept), the ceiling of the ring kernel. Other modes
+ * give DPC_ERR_INVALID_ARG. Writes pairs per
  * second (and the kernel's time in ms when ms is not NULL). Allocates and
  * frees a few bytes of device memory; synchronizes the device. */
 dpc_status dpc_probe_pair_rate(int device, int d, int mode, double* pairs_per_s, double* ms);
@@ -361,19 +366,29 @@ typedef struct {
     int64_t eps_num, eps_den;  /* method 2: eps = eps_num / eps_den, 1 .. 2^20 each; ignored otherwise */
     uint8_t* aux_out;          /* NULL or [n]: method 1, 1 where the dependent point is exact; method 2, 1 for
                                   the picks; unused for method 0 */
+    int32_t keep;              /* 1: keep the job's rho and dependent points on the device after it finishes,
+                                  for decision-graph re-queries (dpc_result.dataset); 0: free them */
 } dpc_job;
 
 typedef struct {
     dpc_status status;         /* DPC_OK, DPC_PENDING or the job's error */
     double queue_ms;           /* submit -> admitted */
-    double run_ms;             /* admitted -> results in host memory */
+    double run_ms;             /* admitted -> this job's results written */
+    dpc_ds* dataset;           /* a finished job submitted with keep = 1: a handle to its device state for
+                                  dpc_label (new (rho_min, delta_min) queries, labels only) and dpc_ds_info;
+                                  owned by the caller, freed with dpc_release. NULL otherwise. It is handed
+                                  out once, by the dpc_poll or dpc_wait that reports the job finished; a call
+                                  with out = NULL frees it. Until it is released, its device memory counts
+                                  against the served mode's hbm_cap_bytes. */
 } dpc_result;
 
 /* Queue a job; thread-safe. *ticket identifies it for dpc_poll. */
 dpc_status dpc_submit(dpc_ctx* ctx, const dpc_job* job, uint64_t* ticket);
 
 /* Non-blocking: DPC_PENDING until the job is done, then its final status
- * (also in out->status). A finished ticket is forgotten after it is polled. */
+ * (also in out->status). A finished ticket is forgotten after it is polled.
+ * A job is done as soon as its own outputs are written: in a batch, a job
+ * with fewer queries can finish before the others. */
 dpc_status dpc_poll(dpc_ctx* ctx, uint64_t ticket, dpc_result* out);
 
 /* Batched mode: run every job submitted so far as one batch and wait for it. */

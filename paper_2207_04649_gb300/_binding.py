@@ -61,13 +61,15 @@ class DpcJob(ctypes.Structure):
                 ("delta_min", ctypes.c_void_p), ("rho_out", ctypes.c_void_p), ("dep_out", ctypes.c_void_p),
                 ("delta2_out", ctypes.c_void_p), ("label_out", ctypes.c_void_p),
                 ("n_centers_out", ctypes.c_void_p), ("is_device", ctypes.c_int32), ("method", ctypes.c_int32),
-                ("eps_num", ctypes.c_int64), ("eps_den", ctypes.c_int64), ("aux_out", ctypes.c_void_p)]
+                ("eps_num", ctypes.c_int64), ("eps_den", ctypes.c_int64), ("aux_out", ctypes.c_void_p),
+                ("keep", ctypes.c_int32)]
 
 METHODS = {"exact": 0, "approx": 1, "sapprox": 2}
 
 
 class DpcResult(ctypes.Structure):
-    _fields_ = [("status", ctypes.c_int), ("queue_ms", ctypes.c_double), ("run_ms", ctypes.c_double)]
+    _fields_ = [("status", ctypes.c_int), ("queue_ms", ctypes.c_double), ("run_ms", ctypes.c_double),
+                ("dataset", ctypes.c_void_p)]
 
 
 _lib = None
@@ -290,6 +292,7 @@ class Context:
     def __init__(self, device: int = 0, stream=None, mode: int = 0, hbm_cap_bytes: int = 0,
                  max_inflight: int = 0, debug: bool = False, profiling: bool = False, tune_cache=None):
         self.device = device
+        self._kept = {}  # ticket -> Job submitted with keep
         self.stream = stream
         ptr = 0
         try:
@@ -387,16 +390,25 @@ class Context:
     def submit(self, job: "Job") -> int:
         t = dpc_submit(self.handle, job.c)
         job.ticket = t
+        if job.c.keep:
+            self._kept[t] = job
         return t
 
     def flush(self):
         return dpc_flush(self.handle)
 
+    def _adopt(self, ticket: int, s: int, r):
+        """A job submitted with keep: its device state becomes job.dataset."""
+        job = self._kept.pop(ticket, None) if s != DPC_PENDING else None
+        if job is not None and r.dataset:
+            job.dataset = Dataset(self, ctypes.c_void_p(r.dataset), job.n, job.is_device)
+        return s, r
+
     def poll(self, ticket: int):
-        return dpc_poll(self.handle, ticket)
+        return self._adopt(ticket, *dpc_poll(self.handle, ticket))
 
     def wait(self, ticket: int, timeout_ms: int = -1):
-        return dpc_wait(self.handle, ticket, timeout_ms)
+        return self._adopt(ticket, *dpc_wait(self.handle, ticket, timeout_ms))
 
     def last_batch_info(self) -> dict:
         return dpc_last_batch_info(self.handle)
@@ -455,7 +467,7 @@ class Job:
     tensors on its device) and a device-memory job. method: "exact",
     "approx" or "sapprox" (with eps as for Context.sapprox)."""
 
-    def __init__(self, points, d_cut: int, queries, method: str = "exact", eps=(4, 5)):
+    def __init__(self, points, d_cut: int, queries, method: str = "exact", eps=(4, 5), keep: bool = False):
         q = list(queries)
         self.rho_min = np.array([int(a) for a, _ in q], dtype=np.int64)
         self.delta_min = np.array([int(b) for _, b in q], dtype=np.int64)
@@ -492,6 +504,9 @@ class Job:
         self.c = DpcJob(p(self.points), n, d, int(d_cut), len(q), h(self.rho_min), h(self.delta_min),
                         p(self.rho), p(self.dep), p(self.delta2), p(self.label), h(self.n_centers), is_dev,
                         METHODS[method], num, den, p(self.aux))
+        self.c.keep = 1 if keep else 0
+        self.n, self.is_device = n, is_dev
+        self.dataset = None  # keep: the finished job's device state (Dataset), for re-queries
         self.ticket = None
 
 

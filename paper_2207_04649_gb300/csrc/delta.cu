@@ -315,9 +315,12 @@ __global__ void __launch_bounds__(256) k_ring_sparse(BatchView v, CellWork w) {
 }
 
 // Resolve the points whose ring-search result is provably final; queue the
-// others, in sorted (Morton) order within each warp, for the brute-force
-// pass (rank < bf_rank) or the tree search.
-__global__ void k_finalize(BatchView v, DeltaBufs db) {
+// others for the brute-force pass (rank < bf_rank) or the tree search: in
+// position (Morton) order when db.ocode is set (codes, block counts, scan,
+// k_emit_open), else in position order within each warp.
+constexpr int kFinThreads = 256;
+
+__global__ void __launch_bounds__(kFinThreads) k_finalize(BatchView v, DeltaBufs db) {
     const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const bool valid = p < v.N;
     bool to_tree = false, to_bf = false;
@@ -358,8 +361,29 @@ __global__ void k_finalize(BatchView v, DeltaBufs db) {
         }
     }
     const int lane = threadIdx.x & 31;
-    const unsigned lt = (1u << lane) - 1u;
     const unsigned mt = __ballot_sync(0xffffffffu, to_tree), mb = __ballot_sync(0xffffffffu, to_bf);
+    if (db.ocode) {
+        // ordered lists: a code per point and the block's counts; the lists
+        // are written in position order by k_emit_open after a scan
+        __shared__ uint32_t ct[kFinThreads / 32], cf[kFinThreads / 32];
+        if (valid) db.ocode[p] = to_tree ? 1 : (to_bf ? 2 : 0);
+        if (lane == 0) {
+            ct[threadIdx.x >> 5] = (uint32_t)__popc(mt);
+            cf[threadIdx.x >> 5] = (uint32_t)__popc(mb);
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            uint32_t a = 0, f = 0;
+            for (int w = 0; w < kFinThreads / 32; ++w) {
+                a += ct[w];
+                f += cf[w];
+            }
+            db.ocnt[blockIdx.x] = a;
+            db.ocnt[gridDim.x + blockIdx.x] = f;
+        }
+        return;
+    }
+    const unsigned lt = (1u << lane) - 1u;
     uint32_t bt = 0, bb = 0;
     if (lane == 0) {
         if (mt) bt = atomicAdd(&db.ucount[0], (uint32_t)__popc(mt));
@@ -369,6 +393,29 @@ __global__ void k_finalize(BatchView v, DeltaBufs db) {
     bb = __shfl_sync(0xffffffffu, bb, 0);
     if (to_tree) db.tree_list[bt + __popc(mt & lt)] = (uint32_t)p;
     if (to_bf) db.bf_list[bb + __popc(mb & lt)] = (uint32_t)p;
+}
+
+// The open lists in position order from the codes of k_finalize: block b's
+// entries start at the exclusive scans of the blocks' counts.
+__global__ void __launch_bounds__(kFinThreads) k_emit_open(BatchView v, DeltaBufs db) {
+    __shared__ uint32_t ct[kFinThreads / 32], cf[kFinThreads / 32];
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const uint8_t code = p < v.N ? db.ocode[p] : 0;
+    const unsigned mt = __ballot_sync(0xffffffffu, code == 1), mb = __ballot_sync(0xffffffffu, code == 2);
+    if (lane == 0) {
+        ct[w] = (uint32_t)__popc(mt);
+        cf[w] = (uint32_t)__popc(mb);
+    }
+    __syncthreads();
+    uint32_t ot = db.oofs[blockIdx.x], of = db.oofs[gridDim.x + blockIdx.x];
+    for (int u = 0; u < w; ++u) {
+        ot += ct[u];
+        of += cf[u];
+    }
+    const unsigned lt = (1u << lane) - 1u;
+    if (code == 1) db.tree_list[ot + __popc(mt & lt)] = (uint32_t)p;
+    if (code == 2) db.bf_list[of + __popc(mb & lt)] = (uint32_t)p;
 }
 
 // --------------------------------------------------------- brute force
@@ -520,9 +567,9 @@ cudaError_t launch_rank(const BatchView& v, const DeltaBufs& db, int rbits, void
     (k_rank_keys<<<grid_for(v.N, 256), 256, 0, st>>>(v, rbits, key64, kin, vin), note_launch());
     cudaError_t e;
     if (key64)
-        e = radix_sort_u64((uint64_t*)kin, vin, (uint64_t*)kout, v.order, (uint64_t*)ktmp, vtmp, v.N, nbits, sort_temp, st);
+        e = radix_sort_u64((uint64_t*)kin, vin, (uint64_t*)kout, v.order, (uint64_t*)ktmp, vtmp, v.N, nbits, sort_temp, st, v.err);
     else
-        e = radix_sort_u32((uint32_t*)kin, vin, (uint32_t*)kout, v.order, (uint32_t*)ktmp, vtmp, v.N, nbits, sort_temp, st);
+        e = radix_sort_u32((uint32_t*)kin, vin, (uint32_t*)kout, v.order, (uint32_t*)ktmp, vtmp, v.N, nbits, sort_temp, st, v.err);
     if (e != cudaSuccess) return e;
     (k_rank_from_order<<<grid_for(v.N, 256), 256, 0, st>>>(v), note_launch());
     (k_ro<<<grid_for(v.N, 256), 256, 0, st>>>(v), note_launch());
@@ -550,9 +597,31 @@ cudaError_t launch_ring(const BatchView& v, const CellWork& w, uint32_t class_ma
     return cudaGetLastError();
 }
 
-cudaError_t launch_finalize(const BatchView& v, const DeltaBufs& db, cudaStream_t st) {
+size_t finalize_temp_bytes(int64_t n) {
+    const int64_t nb = (n + kFinThreads - 1) / kFinThreads;
+    return (size_t)n + 4 * sizeof(uint32_t) * (size_t)nb + scan_temp_bytes(2 * nb) + 1024;
+}
+
+cudaError_t launch_finalize(const BatchView& v, DeltaBufs db, void* ordered_temp, cudaStream_t st) {
     if (v.N == 0) return cudaSuccess;
-    (k_finalize<<<grid_for(v.N, 256), 256, 0, st>>>(v, db), note_launch());
+    const int64_t nb = grid_for(v.N, kFinThreads);
+    if (ordered_temp) {
+        char* t = static_cast<char*>(ordered_temp);
+        db.ocnt = reinterpret_cast<uint32_t*>(t);
+        db.oofs = db.ocnt + 2 * nb;
+        void* stemp = db.oofs + 2 * nb;
+        db.ocode = reinterpret_cast<uint8_t*>(static_cast<char*>(stemp) + ((scan_temp_bytes(2 * nb) + 255) & ~(size_t)255));
+        (k_finalize<<<(unsigned)nb, kFinThreads, 0, st>>>(v, db), note_launch());
+        // offsets of the tree list, then of the brute-force list
+        cudaError_t e = exclusive_scan_u32(db.ocnt, db.oofs, nb, db.ucount, stemp, st);
+        if (e != cudaSuccess) return e;
+        e = exclusive_scan_u32(db.ocnt + nb, db.oofs + nb, nb, db.ucount + 1, stemp, st);
+        if (e != cudaSuccess) return e;
+        (k_emit_open<<<(unsigned)nb, kFinThreads, 0, st>>>(v, db), note_launch());
+        return cudaGetLastError();
+    }
+    db.ocode = nullptr;
+    (k_finalize<<<(unsigned)nb, kFinThreads, 0, st>>>(v, db), note_launch());
     return cudaGetLastError();
 }
 
@@ -567,7 +636,7 @@ cudaError_t launch_bruteforce(const BatchView& v, const DeltaBufs& db, uint32_t 
     // sort the open points by global rank position; the list length lives on
     // the device, so sort the bound and let the padding (key ~0) sink last
     cudaError_t e = radix_sort_u32(db.bf_keys, db.bf_list, db.bf_keys + bound, db.bf_sorted, db.bf_keys + 2 * bound,
-                                   db.bf_sorted + bound, bound, nbits > 0 ? nbits : 1, sort_temp, st);
+                                   db.bf_sorted + bound, bound, nbits > 0 ? nbits : 1, sort_temp, st, v.err);
     if (e != cudaSuccess) return e;
     const unsigned blocks = grid_for(bound, kBfThreads);
 #define DPC_BF_CLASS(D) \

@@ -59,6 +59,8 @@ struct DsDesc {
     int32_t ptree;        // 1: no grid; the point tree gives density and dependent points
     int32_t tb;           // point tree: Morton bits per dim of the sort key
     int32_t span[kMaxDims];  // point tree: max - min + 1 per dim
+    int32_t sbits;        // bits of a block's local Morton code in the block table (a block is 2^(sbits / k)
+                          // cells per gridded dim); 0: this dataset's neighbour runs use the cell hash
 };
 
 // Device views of a batch's buffers (all device pointers).
@@ -79,6 +81,11 @@ struct BatchView {
     uint32_t* ncells;          // device scalar
     int4* hash;                // open addressing: {key lo, key hi, start, count}
     uint64_t hmask;
+    // block table: aligned blocks of 2^(sbits / k) cells per gridded dim,
+    // open addressing over the non-empty blocks; slot = two int4:
+    // {key lo, key hi, first cell, 0}, {occupancy lo, occupancy hi, 0, 0}
+    int4* sbhash;
+    uint64_t sbmask;
     // rho
     int32_t* rho_s;            // sorted
     int32_t* rho;              // original
@@ -105,6 +112,7 @@ constexpr unsigned kErrStaging = 1u;   // candidate runs shorter than counted
 constexpr unsigned kErrTreeStack = 2u; // tree search stack full
 constexpr unsigned kErrChain = 4u;     // label chain longer than the dataset
 constexpr unsigned kErrBulkWait = 8u;  // a bulk copy into shared memory did not complete in time
+constexpr unsigned kErrSortWait = 16u; // a radix sort pass's look-back wait gave up
 
 // ---------------------------------------------------------------- helpers
 
@@ -127,6 +135,43 @@ __host__ __device__ inline uint64_t morton(const int32_t* c, int k, int mbits) {
     return code;
 }
 
+// The same Morton code by bit spreading, for k <= 4 gridded dims whose
+// codes fit 40 bits (at most 40, 20, 13 and 10 bits per dim for k = 1..4).
+__host__ __device__ inline uint64_t spread2(uint64_t x) {
+    x &= 0xffffffffull;
+    x = (x | (x << 16)) & 0x0000ffff0000ffffull;
+    x = (x | (x << 8)) & 0x00ff00ff00ff00ffull;
+    x = (x | (x << 4)) & 0x0f0f0f0f0f0f0f0full;
+    x = (x | (x << 2)) & 0x3333333333333333ull;
+    return (x | (x << 1)) & 0x5555555555555555ull;
+}
+__host__ __device__ inline uint64_t spread3(uint64_t x) {
+    x &= 0x1fffffull;
+    x = (x | (x << 32)) & 0x1f00000000ffffull;
+    x = (x | (x << 16)) & 0x1f0000ff0000ffull;
+    x = (x | (x << 8)) & 0x100f00f00f00f00full;
+    x = (x | (x << 4)) & 0x10c30c30c30c30c3ull;
+    return (x | (x << 2)) & 0x1249249249249249ull;
+}
+__host__ __device__ inline uint64_t spread4(uint64_t x) {
+    x &= 0xffffull;
+    x = (x | (x << 24)) & 0x000000ff000000ffull;
+    x = (x | (x << 12)) & 0x000f000f000f000full;
+    x = (x | (x << 6)) & 0x0303030303030303ull;
+    return (x | (x << 3)) & 0x1111111111111111ull;
+}
+__host__ __device__ inline uint64_t morton_k(const int32_t* c, int k) {
+    switch (k) {
+        case 1: return (uint64_t)(uint32_t)c[0];
+        case 2: return spread2((uint32_t)c[0]) | (spread2((uint32_t)c[1]) << 1);
+        case 3: return spread3((uint32_t)c[0]) | (spread3((uint32_t)c[1]) << 1) | (spread3((uint32_t)c[2]) << 2);
+        case 4:
+            return spread4((uint32_t)c[0]) | (spread4((uint32_t)c[1]) << 1) | (spread4((uint32_t)c[2]) << 2) |
+                   (spread4((uint32_t)c[3]) << 3);
+        default: return 0;
+    }
+}
+
 __device__ inline int find_ds(const int64_t* pt_off, int B, int64_t g) {
     int lo = 0, hi = B - 1;
     while (lo < hi) {
@@ -134,6 +179,32 @@ __device__ inline int find_ds(const int64_t* pt_off, int B, int64_t g) {
         if (pt_off[mid] <= g) lo = mid; else hi = mid - 1;
     }
     return lo;
+}
+
+// Key of the block of cell key `key` of dataset b in the block table.
+__host__ __device__ inline uint64_t block_key(int b, uint64_t key, uint64_t cbase, int sbits) {
+    return ((uint64_t)b << 40) | ((key - cbase) >> sbits);
+}
+
+// Block table lookup: the block's first cell (in the sorted cell order) and
+// its occupancy bitmap (bit i: the cell with local Morton code i is not
+// empty); occupancy 0 when the block is empty.
+__device__ inline uint32_t block_find(const int4* __restrict__ table, uint64_t mask, uint64_t key,
+                                      unsigned long long& occ) {
+    uint64_t h = mix64(key) & mask;
+    for (uint64_t probe = 0; probe <= mask; ++probe) {
+        const int4 e = __ldg(&table[2 * h]);
+        const int4 m = __ldg(&table[2 * h + 1]);  // same 32-byte sector
+        const uint64_t k = (uint64_t)(uint32_t)e.x | ((uint64_t)(uint32_t)e.y << 32);
+        if (k == key) {
+            occ = (unsigned long long)(uint32_t)m.x | ((unsigned long long)(uint32_t)m.y << 32);
+            return (uint32_t)e.z;
+        }
+        if (k == kEmptyKey) break;
+        h = (h + 1) & mask;
+    }
+    occ = 0ull;
+    return 0u;
 }
 
 // Hash lookup of a cell key: returns (start, count) or count 0.
@@ -157,14 +228,16 @@ long long launch_count();
 
 // sort.cu
 size_t radix_sort_temp_bytes(int64_t n);
-// Stable LSD radix sort of (key, value) pairs on bits [0, nbits).
-// Returns false on CUDA error. On return the sorted data is in (k_out, v_out).
+// Stable LSD radix sort of (key, value) pairs on bits [0, nbits), one
+// kernel per 8-bit pass (one-sweep, decoupled look-back). On return the
+// sorted data is in (k_out, v_out). err (nullable): kErrSortWait is set there
+// when a look-back wait gave up (the order is then not valid).
 cudaError_t radix_sort_u64(const uint64_t* k_in, const uint32_t* v_in, uint64_t* k_out, uint32_t* v_out,
                            uint64_t* k_tmp, uint32_t* v_tmp, int64_t n, int nbits, void* temp,
-                           cudaStream_t st);
+                           cudaStream_t st, unsigned int* err = nullptr);
 cudaError_t radix_sort_u32(const uint32_t* k_in, const uint32_t* v_in, uint32_t* k_out, uint32_t* v_out,
                            uint32_t* k_tmp, uint32_t* v_tmp, int64_t n, int nbits, void* temp,
-                           cudaStream_t st);
+                           cudaStream_t st, unsigned int* err = nullptr);
 size_t scan_temp_bytes(int64_t n);
 // Exclusive prefix sum of n uint32 values; writes the total to *total (device) if non-null.
 cudaError_t exclusive_scan_u32(const uint32_t* in, uint32_t* out, int64_t n, uint32_t* total, void* temp,

@@ -110,18 +110,23 @@ __global__ void k_cell_keys(BatchView v, K* __restrict__ keys, uint32_t* __restr
             q[k] = (int32_t)((((uint64_t)(uint32_t)(x[k] - ds.lo[k])) << ds.tb) / (uint64_t)(uint32_t)ds.span[k]);
         keys[g] = (K)(ds.cbase + morton(q, ds.d, ds.tb));
     } else {
-        int32_t c[kMaxGridDims];
-        for (int j = 0; j < ds.k; ++j)
-            c[j] = (int32_t)((uint32_t)(x[ds.gdim[j]] - ds.origin[j]) / (uint32_t)ds.s);
-        keys[g] = (K)(ds.cbase + morton(c, ds.k, ds.mbits));
+        int32_t c[kMaxGridDims] = {0, 0, 0, 0};
+        const int k = ds.k;
+        const uint32_t sd = (uint32_t)ds.s;
+#pragma unroll
+        for (int j = 0; j < kMaxGridDims; ++j)
+            if (j < k) c[j] = (int32_t)((uint32_t)(x[ds.gdim[j]] - ds.origin[j]) / sd);
+        keys[g] = (K)(ds.cbase + morton_k(c, k));
     }
     vals[g] = (uint32_t)g;
 }
 
-// Sorted records (dp int4 per point, zero-padded), inverse permutation and
-// cell-start flags.
+// Sorted records (dp int4 per point, zero-padded), inverse permutation,
+// cell-start flags and (bflag non-null) block-start flags of the datasets
+// that use the block table.
 template <typename K>
-__global__ void k_gather(BatchView v, const K* __restrict__ skeys, uint32_t* __restrict__ flag) {
+__global__ void k_gather(BatchView v, const K* __restrict__ skeys, uint32_t* __restrict__ flag,
+                         uint32_t* __restrict__ bflag) {
     const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= v.N) return;
     const int b = find_ds(v.pt_off, v.B, p);
@@ -137,7 +142,13 @@ __global__ void k_gather(BatchView v, const K* __restrict__ skeys, uint32_t* __r
     v.pos_of[g] = (uint32_t)p;
     v.key[p] = (uint64_t)skeys[p];
     // a point-tree dataset is one cell (its grid work is skipped)
-    flag[p] = (p == 0 || p == ds.pt_off || (!ds.ptree && skeys[p] != skeys[p - 1])) ? 1u : 0u;
+    const bool first = p == 0 || p == ds.pt_off;
+    flag[p] = (first || (!ds.ptree && skeys[p] != skeys[p - 1])) ? 1u : 0u;
+    if (bflag)
+        bflag[p] = ds.sbits > 0 && (first || (((uint64_t)skeys[p] - ds.cbase) >> ds.sbits) !=
+                                                 (((uint64_t)skeys[p - 1] - ds.cbase) >> ds.sbits))
+                       ? 1u
+                       : 0u;
 }
 
 __global__ void k_cells(BatchView v, const uint32_t* __restrict__ flag, const uint32_t* __restrict__ cidx) {
@@ -149,6 +160,45 @@ __global__ void k_cells(BatchView v, const uint32_t* __restrict__ flag, const ui
         const uint32_t nc = cidx[p] + flag[p];
         v.cell_start[nc] = (uint32_t)v.N;
         *v.ncells = nc;
+    }
+}
+
+// Blocks of the block table (after k_cells): every block's key and first
+// cell, and its occupancy bitmap (one bit per non-empty cell, at the cell's
+// local Morton code).
+__global__ void k_blocks_fill(BatchView v, const uint32_t* __restrict__ flag, const uint32_t* __restrict__ bflag,
+                              const uint32_t* __restrict__ bidx, uint64_t* __restrict__ bkey,
+                              uint32_t* __restrict__ bfirst, unsigned long long* __restrict__ bocc) {
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= v.N || !flag[p]) return;  // one thread per non-empty cell
+    const int b = find_ds(v.pt_off, v.B, p);
+    const DsDesc& ds = v.desc[b];
+    if (ds.sbits == 0) return;
+    const uint64_t key = v.key[p];
+    const uint32_t s = bidx[p] + bflag[p] - 1u;  // the block holding p
+    if (bflag[p]) {
+        bkey[s] = block_key(b, key, ds.cbase, ds.sbits);
+        bfirst[s] = v.cell_of[p];
+    }
+    atomicOr(&bocc[s], 1ull << ((key - ds.cbase) & ((1ull << ds.sbits) - 1ull)));
+}
+
+__global__ void k_blocks_insert(BatchView v, const uint32_t* __restrict__ nblocks, const uint64_t* __restrict__ bkey,
+                                const uint32_t* __restrict__ bfirst, const unsigned long long* __restrict__ bocc) {
+    const uint32_t nb = *nblocks;
+    for (uint32_t s = blockIdx.x * blockDim.x + threadIdx.x; s < nb; s += gridDim.x * blockDim.x) {
+        const uint64_t key = bkey[s];
+        uint64_t h = mix64(key) & v.sbmask;
+        for (uint64_t probe = 0; probe <= v.sbmask; ++probe) {
+            unsigned long long* slot = reinterpret_cast<unsigned long long*>(&v.sbhash[2 * h]);
+            if (atomicCAS(slot, (unsigned long long)kEmptyKey, (unsigned long long)key) == kEmptyKey) {
+                v.sbhash[2 * h].z = (int)bfirst[s];
+                const unsigned long long o = bocc[s];
+                v.sbhash[2 * h + 1] = make_int4((int)(uint32_t)o, (int)(uint32_t)(o >> 32), 0, 0);
+                break;
+            }
+            h = (h + 1) & v.sbmask;
+        }
     }
 }
 
@@ -191,15 +241,29 @@ cudaError_t launch_cell_keys(const BatchView& v, bool key32, void* keys, uint32_
 }
 
 cudaError_t launch_gather_cells(const BatchView& v, bool key32, const void* skeys, uint32_t* flag, uint32_t* cidx,
-                                void* scan_temp, cudaStream_t st) {
+                                uint32_t* bflag, uint32_t* bidx, uint32_t* nblocks, void* scan_temp, cudaStream_t st) {
     if (v.N == 0) return cudaSuccess;
     if (key32)
-        (k_gather<uint32_t><<<blocks_for(v.N, 256), 256, 0, st>>>(v, (const uint32_t*)skeys, flag), note_launch());
+        (k_gather<uint32_t><<<blocks_for(v.N, 256), 256, 0, st>>>(v, (const uint32_t*)skeys, flag, bflag), note_launch());
     else
-        (k_gather<uint64_t><<<blocks_for(v.N, 256), 256, 0, st>>>(v, (const uint64_t*)skeys, flag), note_launch());
+        (k_gather<uint64_t><<<blocks_for(v.N, 256), 256, 0, st>>>(v, (const uint64_t*)skeys, flag, bflag), note_launch());
     cudaError_t e = exclusive_scan_u32(flag, cidx, v.N, nullptr, scan_temp, st);
     if (e != cudaSuccess) return e;
+    if (bflag) {
+        e = exclusive_scan_u32(bflag, bidx, v.N, nblocks, scan_temp, st);
+        if (e != cudaSuccess) return e;
+    }
     (k_cells<<<blocks_for(v.N, 256), 256, 0, st>>>(v, flag, cidx), note_launch());
+    return cudaGetLastError();
+}
+
+cudaError_t launch_blocks(const BatchView& v, const uint32_t* flag, const uint32_t* bflag, const uint32_t* bidx,
+                          const uint32_t* nblocks, int64_t nblocks_bound, uint64_t* bkey, uint32_t* bfirst,
+                          unsigned long long* bocc, cudaStream_t st) {
+    if (v.N == 0 || nblocks_bound == 0) return cudaSuccess;
+    (k_blocks_fill<<<blocks_for(v.N, 256), 256, 0, st>>>(v, flag, bflag, bidx, bkey, bfirst, bocc), note_launch());
+    const unsigned blocks = (unsigned)std::min<int64_t>(blocks_for(nblocks_bound, 256), 152 * 16);
+    (k_blocks_insert<<<blocks, 256, 0, st>>>(v, nblocks, bkey, bfirst, bocc), note_launch());
     return cudaGetLastError();
 }
 

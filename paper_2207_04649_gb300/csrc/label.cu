@@ -18,9 +18,10 @@ namespace dpc {
 
 namespace {
 
-__global__ void k_parent(BatchView v) {
-    const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const bool valid = g < v.N;
+// Points [g0, g1) of the batch (all of them, or one dataset's).
+__global__ void k_parent(BatchView v, int64_t g0, int64_t g1) {
+    const int64_t g = g0 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const bool valid = g < g1;
     int b = -1;
     bool center = false;
     if (valid) {
@@ -45,9 +46,9 @@ __global__ void k_parent(BatchView v) {
         atomicAdd(&v.ncent[b], (unsigned long long)__popc(ctr));
 }
 
-__global__ void k_jump(BatchView v) {
-    const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (g >= v.N) return;
+__global__ void k_jump(BatchView v, int64_t g0, int64_t g1) {
+    const int64_t g = g0 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= g1) return;
     int32_t p = v.parent[g];
     if (p < 0) {
         v.label[g] = -1;
@@ -73,8 +74,16 @@ __global__ void k_jump(BatchView v) {
 cudaError_t launch_labels(const BatchView& v, cudaStream_t st) {
     cudaError_t e = cudaMemsetAsync(v.ncent, 0, sizeof(unsigned long long) * v.B, st);
     if (e != cudaSuccess || v.N == 0) return e;
-    (k_parent<<<grid_for(v.N, 256), 256, 0, st>>>(v), note_launch());
-    (k_jump<<<grid_for(v.N, 256), 256, 0, st>>>(v), note_launch());
+    (k_parent<<<grid_for(v.N, 256), 256, 0, st>>>(v, 0, v.N), note_launch());
+    (k_jump<<<grid_for(v.N, 256), 256, 0, st>>>(v, 0, v.N), note_launch());
+    return cudaGetLastError();
+}
+
+cudaError_t launch_labels_one(const BatchView& v, int b, int64_t g0, int64_t n, cudaStream_t st) {
+    cudaError_t e = cudaMemsetAsync(v.ncent + b, 0, sizeof(unsigned long long), st);
+    if (e != cudaSuccess || n == 0) return e;
+    (k_parent<<<grid_for(n, 256), 256, 0, st>>>(v, g0, g0 + n), note_launch());
+    (k_jump<<<grid_for(n, 256), 256, 0, st>>>(v, g0, g0 + n), note_launch());
     return cudaGetLastError();
 }
 

@@ -109,12 +109,71 @@ __global__ void __launch_bounds__(256) k_pair_probe_x(const int32_t* __restrict_
     if (cnt[0] + cnt[1] + cnt[2] + cnt[3] == 0xdeadbeefu) sink[0] = t;
 }
 
+// The dependent-point ring search's pair test in the expanded form: the
+// density test's sum, then the candidate counts only when it ranks higher,
+// and the packed key (squared distance << 32 | index) keeps the least. Each
+// candidate carries (rank, index) beside its coordinates, as the ring
+// kernel stages them; after each sweep the queries' operands and ranks move
+// by amounts that depend on the keys kept.
+template <int D>
+__global__ void __launch_bounds__(256) k_ring_probe_x(const int32_t* __restrict__ seed, int iters,
+                                                     unsigned long long* __restrict__ sink) {
+    int32_t qa[4][3], qn[4];
+    uint32_t qr[4];
+    int4 c[16];
+    uint2 ro[16];
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        int32_t n = 0;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            const int32_t x = k < D ? seed[(t * 7 + i * 3 + k) & 1023] : 0;
+            qa[i][k] = -2 * x;
+            n += x * x;
+        }
+        qn[i] = n;
+        qr[i] = (uint32_t)seed[(t * 5 + i) & 1023] * 7u;
+    }
+#pragma unroll
+    for (int j = 0; j < 16; ++j) {
+        const int32_t x = seed[(t * 13 + j * 3 + 512) & 1023];
+        const int32_t y = D > 1 ? seed[(t * 13 + j * 3 + 513) & 1023] : 0;
+        const int32_t z = D > 2 ? seed[(t * 13 + j * 3 + 514) & 1023] : 0;
+        c[j] = make_int4(x, y, z, x * x + y * y + z * z);
+        ro[j] = make_uint2((uint32_t)seed[(t * 11 + j) & 1023] * 7u, (uint32_t)(t * 16 + j));
+    }
+    unsigned long long best[4] = {~0ull, ~0ull, ~0ull, ~0ull};
+    for (int it = 0; it < iters; ++it) {
+#pragma unroll
+        for (int j = 0; j < 16; ++j)
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                int s = c[j].w + qn[i];
+                s += c[j].x * qa[i][0];
+                if (D > 1) s += c[j].y * qa[i][1];
+                if (D > 2) s += c[j].z * qa[i][2];
+                const unsigned long long key = ((unsigned long long)(uint32_t)s << 32) | ro[j].y;
+                if (ro[j].x < qr[i] && key < best[i]) best[i] = key;
+            }
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const int32_t m = (int32_t)(best[i] & 1ull);
+            qn[i] += m;
+            qr[i] += (uint32_t)m;
+#pragma unroll
+            for (int k = 0; k < D; ++k) qa[i][k] += m;
+        }
+    }
+    if ((best[0] ^ best[1] ^ best[2] ^ best[3]) == 0xdeadbeefull) sink[0] = t;
+}
+
 }  // namespace
 }  // namespace dpc
 
 extern "C" dpc_status dpc_probe_pair_rate(int device, int d, int mode, double* pairs_per_s, double* ms) {
     using namespace dpc;
-    if (!pairs_per_s || d < 1 || d > 8 || mode < 0 || mode > 2 || (mode == 2 && d > 3))
+    if (!pairs_per_s || d < 1 || d > 8 || mode < 0 || mode > 3 || (mode >= 2 && d > 3))
         return DPC_ERR_INVALID_ARG;
     if (cudaSetDevice(device) != cudaSuccess) return DPC_ERR_CUDA;
     int sms = 0;
@@ -134,7 +193,13 @@ extern "C" dpc_status dpc_probe_pair_rate(int device, int d, int mode, double* p
     cudaEventCreate(&a);
     cudaEventCreate(&b);
     auto launch = [&](int it) {
-        if (mode == 2) {
+        if (mode == 3) {
+            switch (d) {
+                case 1: k_ring_probe_x<1><<<blocks, threads>>>(seed, it, sink); break;
+                case 2: k_ring_probe_x<2><<<blocks, threads>>>(seed, it, sink); break;
+                default: k_ring_probe_x<3><<<blocks, threads>>>(seed, it, sink); break;
+            }
+        } else if (mode == 2) {
             switch (d) {
                 case 1: k_pair_probe_x<1><<<blocks, threads>>>(seed, it, 90000, sink); break;
                 case 2: k_pair_probe_x<2><<<blocks, threads>>>(seed, it, 90000, sink); break;

@@ -98,7 +98,7 @@ __global__ void __launch_bounds__(256) k_cell_runs(BatchView v, CellPrepBufs cb,
         const uint32_t cs = v.cell_start[c];
         const int b = find_ds(v.pt_off, v.B, cs);
         const DsDesc& ds = v.desc[b];
-        if (ds.k != K || ds.R != 1) continue;
+        if (ds.k != K || ds.R != 1 || ds.sbits != 0) continue;
         const int4* r0 = v.rec + ds.rec_off + ((int64_t)cs - ds.pt_off) * ds.dp;
         int32_t cc[K];
 #pragma unroll
@@ -144,6 +144,116 @@ __global__ void __launch_bounds__(256) k_cell_runs(BatchView v, CellPrepBufs cb,
                     cand += r.y;
                 }
             }
+        }
+        cb.nruns[c] = nr;
+        cb.cand[c] = cand;
+    }
+}
+
+// Local Morton codes of a block (K dims, L bits per dim, K * L <= 6) whose
+// coordinate along dim j is c: bit i of dim j sits at code bit i * K + j.
+__device__ __forceinline__ unsigned long long code_bit(int q) {
+    switch (q) {
+        case 0: return 0xAAAAAAAAAAAAAAAAull;
+        case 1: return 0xCCCCCCCCCCCCCCCCull;
+        case 2: return 0xF0F0F0F0F0F0F0F0ull;
+        case 3: return 0xFF00FF00FF00FF00ull;
+        case 4: return 0xFFFF0000FFFF0000ull;
+        default: return 0xFFFFFFFF00000000ull;
+    }
+}
+
+template <int K, int L>
+__device__ __forceinline__ unsigned long long coord_codes(int j, int c) {
+    unsigned long long m = K * L >= 6 ? ~0ull : ((1ull << (1 << (K * L))) - 1ull);  // 2^(K L) codes
+#pragma unroll
+    for (int i = 0; i < L; ++i) {
+        const unsigned long long p = code_bit(i * K + j);
+        m &= ((c >> i) & 1) ? p : ~p;
+    }
+    return m;
+}
+
+// Codes whose coordinate along dim j lies in [a, e] (e - a <= 2).
+template <int K, int L>
+__device__ __forceinline__ unsigned long long range_codes(int j, int a, int e) {
+    unsigned long long m = coord_codes<K, L>(j, a);
+    if (e > a) m |= coord_codes<K, L>(j, a + 1);
+    if (e > a + 1) m |= coord_codes<K, L>(j, a + 2);
+    return m;
+}
+
+// Neighbour runs from the block table, one thread per cell of a dataset
+// gridded in K dims with reach 1: the 3^K neighbourhood meets at most 2^K
+// aligned blocks of W = 2^L cells per dim; each is one table probe, whose
+// occupancy bitmap masked by the neighbourhood's box gives the non-empty
+// neighbour cells, and a cell's index in the sorted cell order is the
+// block's first cell plus the occupied codes below it. Neighbour cells whose
+// indices follow one another hold consecutive points and become one run.
+template <int K>
+__global__ void __launch_bounds__(256) k_cell_runs_blk(BatchView v, CellPrepBufs cb, int64_t ncells) {
+    constexpr int L = K == 1 ? 6 : (K == 2 ? 3 : (K == 3 ? 2 : 1));
+    constexpr int W = 1 << L;
+    constexpr int NB = 1 << K;  // blocks the neighbourhood can meet
+    for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < ncells; c += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t cs = v.cell_start[c];
+        const int b = find_ds(v.pt_off, v.B, cs);
+        const DsDesc& ds = v.desc[b];
+        if (ds.k != K || ds.sbits == 0) continue;
+        const int4* r0 = v.rec + ds.rec_off + ((int64_t)cs - ds.pt_off) * ds.dp;
+        int32_t lo[K], hi[K], cbk[K];
+#pragma unroll
+        for (int j = 0; j < K; ++j) {
+            const int32_t cc = (int32_t)((uint32_t)(rec_coord(r0, ds.gdim[j]) - ds.origin[j]) / (uint32_t)ds.s);
+            lo[j] = max(cc - 1, 0);
+            hi[j] = min(cc + 1, ds.ext[j] - 1);
+            cbk[j] = cc >> L;
+        }
+        const uint64_t own = (v.key[cs] - ds.cbase) >> (K * L);
+        uint2* runs = cb.runs + c * cb.nbs;
+        uint32_t nr = 0;
+        uint32_t first_ci = 0, last_ci = 0;
+        bool open = false;
+#pragma unroll
+        for (int t = 0; t < NB; ++t) {
+            bool ok = true;
+            uint64_t code = own;
+            unsigned long long box = ~0ull;
+#pragma unroll
+            for (int j = 0; j < K; ++j) {
+                const int blo = lo[j] >> L, bhi = hi[j] >> L;
+                const bool up = (t >> j) & 1;
+                if (up && bhi == blo) ok = false;
+                const int bj = up ? bhi : blo;
+                code = morton_step(code, ds.dmask[j] >> (K * L), bj - cbk[j]);
+                box &= range_codes<K, L>(j, max(lo[j], bj * W) - bj * W, min(hi[j], bj * W + W - 1) - bj * W);
+            }
+            if (!ok) continue;
+            unsigned long long occ;
+            const uint32_t f = block_find(v.sbhash, v.sbmask, ((uint64_t)b << 40) | code, occ);
+            unsigned long long sel = occ & box;
+            while (sel) {
+                const int bit = __ffsll((long long)sel) - 1;
+                sel &= sel - 1ull;
+                const uint32_t ci = f + (uint32_t)__popcll(occ & ((1ull << bit) - 1ull));
+                if (open && ci == last_ci + 1u) {
+                    last_ci = ci;
+                } else {
+                    if (open) runs[nr++] = make_uint2(first_ci, last_ci);
+                    first_ci = last_ci = ci;
+                    open = true;
+                }
+            }
+        }
+        if (open) runs[nr++] = make_uint2(first_ci, last_ci);
+        // cell index ranges -> point runs (independent loads)
+        uint32_t cand = 0;
+#pragma unroll 4
+        for (uint32_t r = 0; r < nr; ++r) {
+            const uint2 e = runs[r];
+            const uint32_t p0 = v.cell_start[e.x], p1 = v.cell_start[e.y + 1];
+            runs[r] = make_uint2(p0, p1 - p0);
+            cand += p1 - p0;
         }
         cb.nruns[c] = nr;
         cb.cand[c] = cand;
@@ -834,6 +944,10 @@ cudaError_t launch_cell_runs(const BatchView& v, const CellPrepBufs& cb, int64_t
     if (kmask & 4u) (k_cell_runs<2><<<blocks, 256, 0, st>>>(v, cb, ncells), note_launch());
     if (kmask & 8u) (k_cell_runs<3><<<blocks, 256, 0, st>>>(v, cb, ncells), note_launch());
     if (kmask & 16u) (k_cell_runs<4><<<blocks, 256, 0, st>>>(v, cb, ncells), note_launch());
+    if (kmask & (2u << 8)) (k_cell_runs_blk<1><<<blocks, 256, 0, st>>>(v, cb, ncells), note_launch());
+    if (kmask & (4u << 8)) (k_cell_runs_blk<2><<<blocks, 256, 0, st>>>(v, cb, ncells), note_launch());
+    if (kmask & (8u << 8)) (k_cell_runs_blk<3><<<blocks, 256, 0, st>>>(v, cb, ncells), note_launch());
+    if (kmask & (16u << 8)) (k_cell_runs_blk<4><<<blocks, 256, 0, st>>>(v, cb, ncells), note_launch());
     return cudaGetLastError();
 }
 

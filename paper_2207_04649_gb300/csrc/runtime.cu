@@ -139,6 +139,8 @@ struct Tune {
     int sapprox_ratio = 16;   // S-Approx-DPC: the pick path when the points' pairs exceed this many times the picks'
 };
 
+struct Batch;
+
 }  // namespace
 }  // namespace dpc
 
@@ -159,6 +161,8 @@ struct dpc_ctx {
         dpc_status status = DPC_PENDING;
         uint64_t bytes = 0;  // device footprint estimate
         std::chrono::steady_clock::time_point t_submit, t_admit, t_done;
+        std::shared_ptr<dpc::Batch> kept;  // job.keep: its batch, until the result hands it out
+        int kept_b = 0;                    // the job's dataset index in that batch
     };
     std::mutex mu;
     std::condition_variable cv;
@@ -169,6 +173,7 @@ struct dpc_ctx {
     std::vector<std::thread> workers;
     uint64_t held_bytes = 0;
     int max_batch_jobs = 64;  // served mode: jobs admitted into one batch at most
+    int64_t max_batch_points = 1 << 20;  // served mode: points one batch admits at most (a larger job runs alone)
     bool has_last = false;    // last_info holds the most recent finished batch of jobs
     dpc_info last_info{};
     std::string tune_cache;   // autotuner file ("" when none)
@@ -530,24 +535,59 @@ struct Batch {
         DPC_CK(keep.get(&v.cell_of, N));
         DPC_CK(launch_cell_keys(v, key32, k0, v0, st));
         if (key32)
-            DPC_CK(radix_sort_u32((uint32_t*)k0, v0, (uint32_t*)k2, v.perm, (uint32_t*)k1, v1, N, key_bits, temp, st));
+            DPC_CK(radix_sort_u32((uint32_t*)k0, v0, (uint32_t*)k2, v.perm, (uint32_t*)k1, v1, N, key_bits, temp, st, v.err));
         else
-            DPC_CK(radix_sort_u64((uint64_t*)k0, v0, (uint64_t*)k2, v.perm, (uint64_t*)k1, v1, N, key_bits, temp, st));
-        DPC_CK(launch_gather_cells(v, key32, k2, flag, cidx, temp, st));
-        uint32_t nc = 0;
+            DPC_CK(radix_sort_u64((uint64_t*)k0, v0, (uint64_t*)k2, v.perm, (uint64_t*)k1, v1, N, key_bits, temp, st, v.err));
+        // block-start flags for the datasets whose runs come from the block
+        // table; the cell hash serves the others (and the second ring)
+        bool any_blocks = false, need_hash = tune.ring2 != 0;
+        for (int b = 0; b < B; ++b) {
+            any_blocks |= hd[b].sbits > 0;
+            need_hash |= hd[b].sbits == 0 && !hd[b].ptree && hd[b].n > 0;
+        }
+        uint32_t *bflag = nullptr, *bidx = nullptr, *d_nblocks = nullptr;
+        if (any_blocks) {
+            DPC_CK(dens.get(&bflag, N));
+            DPC_CK(dens.get(&bidx, N));
+            DPC_CK(dens.get(&d_nblocks, 1));
+        }
+        DPC_CK(launch_gather_cells(v, key32, k2, flag, cidx, bflag, bidx, d_nblocks, temp, st));
+        uint32_t nc = 0, nblk = 0;
         if (N > 0) {
             DPC_CK(cudaMemcpyAsync(&nc, v.ncells, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
+            if (any_blocks) DPC_CK(cudaMemcpyAsync(&nblk, d_nblocks, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
             DPC_TRY(sync("cell count"));
         }
         ncells = nc;
         DPC_CK(launch_pt_build(v, pb, st));
 
+        // block table (load factor <= 1/2): 32-byte slots {key, first cell}, {occupancy}
+        v.sbhash = nullptr;
+        v.sbmask = 0;
+        if (any_blocks && nblk > 0) {
+            const int sb = ceil_log2((uint64_t)std::max<int64_t>(2 * (int64_t)nblk, 2));
+            DPC_CK(keep.get(&v.sbhash, (size_t)2 << sb));
+            v.sbmask = (1ull << sb) - 1;
+            DPC_CK(cudaMemsetAsync(v.sbhash, 0xff, sizeof(int4) << (sb + 1), st));
+            uint64_t* bkey = nullptr;
+            uint32_t* bfirst = nullptr;
+            unsigned long long* bocc = nullptr;
+            DPC_CK(dens.get(&bkey, nblk));
+            DPC_CK(dens.get(&bfirst, nblk));
+            DPC_CK(dens.get(&bocc, nblk));
+            DPC_CK(cudaMemsetAsync(bocc, 0, sizeof(unsigned long long) * nblk, st));
+            DPC_CK(launch_blocks(v, flag, bflag, bidx, d_nblocks, nblk, bkey, bfirst, bocc, st));
+        }
         // hash table of the non-empty cells (load factor <= 1/2)
-        const int hbits = ceil_log2((uint64_t)std::max<int64_t>(2 * ncells, 2));
-        DPC_CK(keep.get(&v.hash, (size_t)1 << hbits));
-        v.hmask = (1ull << hbits) - 1;
-        DPC_CK(cudaMemsetAsync(v.hash, 0xff, sizeof(int4) << hbits, st));
-        DPC_CK(launch_hash_insert(v, ncells, st));
+        v.hash = nullptr;
+        v.hmask = 0;
+        if (need_hash) {
+            const int hbits = ceil_log2((uint64_t)std::max<int64_t>(2 * ncells, 2));
+            DPC_CK(keep.get(&v.hash, (size_t)1 << hbits));
+            v.hmask = (1ull << hbits) - 1;
+            DPC_CK(cudaMemsetAsync(v.hash, 0xff, sizeof(int4) << hbits, st));
+            DPC_CK(launch_hash_insert(v, ncells, st));
+        }
 
         // dense / sparse cells and the dense work items
         CellPrepBufs cb{};
@@ -574,7 +614,8 @@ struct Batch {
         DPC_CK(keep.get(&cb.nruns, ncells + 1));
         DPC_CK(keep.get(&cb.cand, ncells + 1));
         uint32_t kmask = 0;
-        for (int b = 0; b < B; ++b) kmask |= (hd[b].R == 1 && hd[b].k >= 1) ? 1u << hd[b].k : 1u;
+        for (int b = 0; b < B; ++b)
+            kmask |= (hd[b].R == 1 && hd[b].k >= 1) ? (1u << hd[b].k) << (hd[b].sbits > 0 ? 8 : 0) : 1u;
         DPC_CK(launch_cell_runs(v, cb, ncells, kmask, st));
         DPC_CK(launch_classify_cells(v, cb, ncells, (uint32_t)tune.sparse_cand, temp, st));
         uint32_t cnts[2] = {0, 0};
@@ -709,6 +750,10 @@ struct Batch {
             if (maxsum >= (1ll << 31)) break;
         }
         ds.w32 = (maxsum < (1ll << 31) && ds.d_cut2 <= (1ll << 31)) ? 1 : 0;
+        // neighbour runs from the block table (blocks of 2^(6 / k) cells per
+        // dim, 2 for k = 4) unless some neighbours are left out or the reach
+        // is not 1; the block key packs the dataset index above 40 bits
+        ds.sbits = (ds.R == 1 && k >= 1 && !ds.prune && b < (1 << 23)) ? k * (k == 4 ? 1 : 6 / k) : 0;
         ds.rbits = bits_for((uint64_t)ds.n);
         // Expanded test around the query cell's corner: every coordinate
         // relative to it lies in [-s, 2s) (gridded dims, reach 1) or [0, s)
@@ -735,8 +780,11 @@ struct Batch {
         if (nc == 0) return DPC_OK;
         db.ncells = nc;
         db.dpb = 1;
-        for (int b = 0; b < B; ++b)
+        db.compact = 1;
+        for (int b = 0; b < B; ++b) {
             if (hd[b].dp == 2) db.dpb = 2;
+            if (hd[b].d > 3) db.compact = 0;
+        }
         DPC_CK(tmp.get(&db.cell_off, B + 1));
         DPC_CK(tmp.get(&db.ckey, nc));
         DPC_CK(tmp.get(&db.child, nc));
@@ -768,8 +816,8 @@ struct Batch {
         nbf = uc[1];
         if (ntree > 0) {
             // neighbouring lanes should search neighbouring points: sort the
-            // open list by sorted (Morton) position
-            {
+            // open list by sorted (Morton) position, unless it is in that order
+            if (!db.lists_sorted) {
                 uint32_t *ks = nullptr, *kt = nullptr, *vs = nullptr, *vt = nullptr;
                 void* t3 = nullptr;
                 DPC_CK(tmp.get(&ks, ntree));
@@ -778,7 +826,7 @@ struct Batch {
                 DPC_CK(tmp.get(&vt, ntree));
                 DPC_CK(tmp.get(&t3, radix_sort_temp_bytes(ntree)));
                 DPC_CK(radix_sort_u32(db.tree_list, db.tree_list, ks, vs, kt, vt, ntree, bits_for((uint64_t)N),
-                                      t3, st));
+                                      t3, st, v.err));
                 db.tree_list = ks;
             }
             const int64_t nc = ncells;
@@ -822,8 +870,11 @@ struct Batch {
             }
             if (!tree_ready) {
                 db.dpb = 1;
-                for (int b = 0; b < B; ++b)
+                db.compact = 1;
+                for (int b = 0; b < B; ++b) {
                     if (hd[b].dp == 2) db.dpb = 2;
+                    if (hd[b].d > 3) db.compact = 0;
+                }
                 DPC_CK(tmp.get(&db.cell_off, B + 1));
                 DPC_CK(tmp.get(&db.ckey, nc));
                 DPC_CK(tmp.get(&db.child, nc));
@@ -928,8 +979,12 @@ struct Batch {
         DPC_CK(cudaMemsetAsync(db.ucount, 0, 4 * sizeof(uint32_t), st));
         db.tcount = db.ucount;
         db.bf_rank = tune.bf_rank;
-        DPC_CK(launch_finalize(v, db, st));
+        void* fin_temp = nullptr;
+        DPC_CK(tmp.get(&fin_temp, finalize_temp_bytes(N)));
+        DPC_CK(launch_finalize(v, db, fin_temp, st));
+        db.lists_sorted = 1;  // written in position order
         DPC_TRY(open_points(tmp, "ring search", true));
+        db.lists_sorted = 0;
         mark(3);
         DPC_TRY(finish_stats("dependent points"));
         ms[2] = elapsed(0, 1);
@@ -1201,10 +1256,37 @@ struct Batch {
         return DPC_OK;
     }
 
+    // Labels of dataset b only (a re-query of one dataset of a batch).
+    dpc_status label_one(int b, int64_t rho_min, int64_t delta_min) {
+        if (dep_kind == 0) DPC_TRY(dependent());
+        if (!v.parent) {
+            DPC_CK(keep.get(&v.parent, N));
+            DPC_CK(keep.get(&v.label, N));
+            DPC_CK(keep.get(&v.ncent, B));
+        }
+        hd[b].rho_min = rho_min;
+        hd[b].delta_min2 = delta_min * delta_min;
+        DPC_TRY(upload_desc());
+        mark(0);
+        DPC_CK(launch_labels_one(v, b, hd[b].pt_off, hd[b].n, st));
+        mark(1);
+        return DPC_OK;
+    }
+
+    // After the batch's jobs are done: later work (re-queries of kept
+    // datasets, and the frees) goes to stream s.
+    void move_to(cudaStream_t s) {
+        st = s;
+        keep.st = s;
+        dens.st = s;
+    }
+
     dpc_status copy_out(void* dst, const void* src, size_t bytes) {
         if (dst && bytes) DPC_CK(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDefault, st));
         return DPC_OK;
     }
+
+    std::mutex qmu;  // re-queries of the batch's kept datasets from several threads
 };
 
 }  // namespace
@@ -1213,6 +1295,8 @@ struct Batch {
 struct dpc_ds {
     std::shared_ptr<dpc::Batch> batch;
     int b = 0;
+    dpc_ctx* served = nullptr;  // a kept job's dataset: its device bytes count against this context's cap
+    uint64_t held = 0;
 };
 
 using dpc::Batch;
@@ -1296,6 +1380,9 @@ dpc_status dpc_set_tuning(dpc_ctx* ctx, const char* key, int64_t value) {
     else if (k == "max_batch_jobs" && value >= 1 && value <= 4096) {
         std::lock_guard<std::mutex> lk(ctx->mu);
         ctx->max_batch_jobs = (int)value;
+    } else if (k == "max_batch_points" && value >= 1 && value <= (1ll << 31) - 1) {
+        std::lock_guard<std::mutex> lk(ctx->mu);
+        ctx->max_batch_points = value;
     } else return fail(DPC_ERR_INVALID_ARG, "unknown tuning key or value out of range: " + k);
     return DPC_OK;
 }
@@ -1322,6 +1409,9 @@ dpc_status dpc_get_tuning(dpc_ctx* ctx, const char* key, int64_t* value) {
     else if (k == "max_batch_jobs") {
         std::lock_guard<std::mutex> lk(ctx->mu);
         *value = ctx->max_batch_jobs;
+    } else if (k == "max_batch_points") {
+        std::lock_guard<std::mutex> lk(ctx->mu);
+        *value = ctx->max_batch_points;
     } else return fail(DPC_ERR_INVALID_ARG, "unknown tuning key: " + k);
     return DPC_OK;
 }
@@ -1469,8 +1559,8 @@ dpc_status dpc_label(dpc_ds* ds, int64_t rho_min, int64_t delta_min, int32_t* la
     if (delta_min <= h.d_cut || delta_min > dpc::kMaxDeltaMin)
         return fail(DPC_ERR_INVALID_ARG, "delta_min must be in (d_cut, 3037000499]");
     cudaSetDevice(bt.ctx->device);
-    std::vector<int64_t> rmin(bt.B, rho_min), dmin(bt.B, delta_min);
-    DPC_TRY(bt.label(rmin.data(), dmin.data()));
+    std::lock_guard<std::mutex> lk(bt.qmu);
+    DPC_TRY(bt.label_one(ds->b, rho_min, delta_min));
     DPC_TRY(bt.copy_out(label_out, bt.v.label + h.pt_off, sizeof(int32_t) * h.n));
     unsigned long long nc = 0;
     if (n_centers) DPC_TRY(bt.copy_out(&nc, bt.v.ncent + ds->b, sizeof(nc)));
@@ -1487,7 +1577,14 @@ dpc_status dpc_release(dpc_ds* ds) {
         cudaSetDevice(ds->batch->ctx->device);
         cudaStreamSynchronize(ds->batch->st);
     }
-    delete ds;
+    dpc_ctx* ctx = ds->served;
+    const uint64_t held = ds->held;
+    delete ds;  // the batch's memory goes with its last dataset
+    if (ctx) {
+        std::lock_guard<std::mutex> lk(ctx->mu);
+        ctx->held_bytes -= held;
+        ctx->cv.notify_all();
+    }
     return DPC_OK;
 }
 
@@ -1552,7 +1649,17 @@ uint64_t job_bytes(int64_t n, int32_t d, int32_t method) {
     return (uint64_t)n * (176 + 8 * (uint64_t)d + (method != 0 ? 96 : 0)) + (16ull << 20);
 }
 
-// Run a group of jobs as one batch on stream st; fills their outputs.
+// One job's outputs are written: its status, for dpc_poll and dpc_wait.
+void mark_done(dpc_ctx* ctx, const JobPtr& j, dpc_status s) {
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    if (j->status != DPC_PENDING) return;
+    j->status = s;
+    j->t_done = std::chrono::steady_clock::now();
+    ctx->cv.notify_all();
+}
+
+// Run a group of jobs as one batch on stream st; fills their outputs. Each
+// job is marked done as soon as its own outputs are written.
 dpc_status run_jobs(dpc_ctx* ctx, std::vector<JobPtr>& jobs, cudaStream_t st) {
     auto bt = std::make_shared<Batch>();
     bt->ctx = ctx;
@@ -1607,6 +1714,22 @@ dpc_status run_jobs(dpc_ctx* ctx, std::vector<JobPtr>& jobs, cudaStream_t st) {
         for (size_t b = 0; b < jobs.size(); ++b)
             if (q < jobs[b]->job.n_queries && jobs[b]->job.n_centers_out)
                 jobs[b]->job.n_centers_out[q] = (int64_t)nc[b];
+        // every job whose last query this was is done: its outputs are
+        // written (a kept job once the batch is no longer in use here)
+        for (size_t b = 0; b < jobs.size(); ++b)
+            if (jobs[b]->job.n_queries == q + 1 && !jobs[b]->job.keep) mark_done(ctx, jobs[b], DPC_OK);
+    }
+    // kept datasets: re-queries (and the frees) run on the context's stream
+    bool any_kept = false;
+    for (auto& j : jobs) any_kept |= j->job.keep != 0;
+    if (any_kept) {
+        bt->move_to(ctx->stream);
+        for (size_t b = 0; b < jobs.size(); ++b) {
+            if (!jobs[b]->job.keep) continue;
+            jobs[b]->kept = bt;
+            jobs[b]->kept_b = (int)b;
+            mark_done(ctx, jobs[b], DPC_OK);
+        }
     }
     // the batch's counters and stage times (the first dataset's per-dataset
     // fields, the batch's totals)
@@ -1621,13 +1744,21 @@ dpc_status run_jobs(dpc_ctx* ctx, std::vector<JobPtr>& jobs, cudaStream_t st) {
     return DPC_OK;
 }
 
+// The batch is over: jobs not yet done get its status (an error), and the
+// device bytes of every job not kept are released (a kept job's bytes stay
+// held until its dataset is released).
 void finish(dpc_ctx* ctx, std::vector<JobPtr>& group, dpc_status s) {
     std::lock_guard<std::mutex> lk(ctx->mu);
     const auto now = std::chrono::steady_clock::now();
     for (auto& j : group) {
-        j->status = s;
-        j->t_done = now;
-        ctx->held_bytes -= j->bytes;
+        if (j->status == DPC_PENDING) {
+            j->status = s == DPC_OK ? DPC_ERR_STATE : s;
+            j->t_done = now;
+        }
+        if (j->status != DPC_OK) j->kept.reset();
+        // a kept job's bytes are released with its dataset (or by the result
+        // call that frees it), never here
+        if (!(j->status == DPC_OK && j->job.keep)) ctx->held_bytes -= j->bytes;
     }
     ctx->cv.notify_all();
 }
@@ -1662,6 +1793,7 @@ void serve_loop(dpc_ctx* ctx) {
                 if (ctx->held_bytes + j->bytes > ctx->cap) break;
                 if (!group.empty() && j->job.method != group[0]->job.method) break;  // one method per batch
                 if (pts + j->job.n >= (1ll << 31) - 1) break;
+                if (!group.empty() && pts + j->job.n > ctx->max_batch_points) break;  // a large job runs alone
                 ctx->waiting.pop_front();
                 ctx->held_bytes += j->bytes;
                 pts += j->job.n;
@@ -1721,11 +1853,28 @@ dpc_status dpc_submit(dpc_ctx* ctx, const dpc_job* job, uint64_t* ticket) {
     return DPC_OK;
 }
 
-static void fill_result(const dpc_ctx::JobRec& j, dpc_result* out) {
+// The result of a finished job (ctx->mu held). A kept job's dataset is
+// handed out here, once; with out NULL it is freed instead.
+static void fill_result(dpc_ctx* ctx, dpc_ctx::JobRec& j, dpc_result* out) {
+    dpc_ds* ds = nullptr;
+    if (j.kept) {
+        if (out) {
+            ds = new dpc_ds;
+            ds->batch = std::move(j.kept);
+            ds->b = j.kept_b;
+            ds->served = ctx;
+            ds->held = j.bytes;
+        } else {
+            ctx->held_bytes -= j.bytes;
+            ctx->cv.notify_all();
+        }
+        j.kept.reset();
+    }
     if (!out) return;
     out->status = j.status;
     out->queue_ms = std::chrono::duration<double, std::milli>(j.t_admit - j.t_submit).count();
     out->run_ms = std::chrono::duration<double, std::milli>(j.t_done - j.t_admit).count();
+    out->dataset = ds;
 }
 
 dpc_status dpc_poll(dpc_ctx* ctx, uint64_t ticket, dpc_result* out) {
@@ -1737,7 +1886,7 @@ dpc_status dpc_poll(dpc_ctx* ctx, uint64_t ticket, dpc_result* out) {
         if (out) out->status = DPC_PENDING;
         return DPC_PENDING;
     }
-    fill_result(*it->second, out);
+    fill_result(ctx, *it->second, out);
     const dpc_status s = it->second->status;
     ctx->jobs.erase(it);
     return s;
@@ -1752,7 +1901,7 @@ dpc_status dpc_wait(dpc_ctx* ctx, uint64_t ticket, int64_t timeout_ms, dpc_resul
     const bool done = ctx->cv.wait_for(lk, std::chrono::milliseconds(timeout_ms < 0 ? 0 : timeout_ms),
                                        [&] { return rec->status != DPC_PENDING; });
     if (!done) return fail(DPC_ERR_TIMEOUT, "job not finished within the timeout");
-    fill_result(*rec, out);
+    fill_result(ctx, *rec, out);
     ctx->jobs.erase(ticket);
     return rec->status;
 }
@@ -1888,6 +2037,8 @@ dpc_status dpc_destroy(dpc_ctx* ctx) {
     }
     for (auto& t : ctx->workers) t.join();
     cudaSetDevice(ctx->device);
+    // kept datasets of jobs never collected: freed while their stream lives
+    ctx->jobs.clear();
     cudaStreamSynchronize(ctx->stream);
     if (ctx->copy_stream) {
         cudaStreamSynchronize(ctx->copy_stream);

@@ -395,9 +395,11 @@ __global__ void __launch_bounds__(128) k_sap_near(BatchView v, CellWork w, Sappr
         long long bd = INT64_MAX;
         uint32_t bj = 0xffffffffu;
         for (uint32_t ri = 0; ri < nr; ++ri) {
-            // the picks of the run's cell (a run is one whole cell)
-            const uint32_t c = v.cell_of[runs[ri].x];
-            for (uint32_t t = sb.pstart[c] + lane; t < sb.pstart[c + 1]; t += 32) {
+            // the picks of the run's cells (a run is one or more whole cells,
+            // consecutive in the sorted order, whose picks are consecutive too)
+            const uint2 run = runs[ri];
+            const uint32_t t1 = sb.pstart[v.cell_of[run.x + run.y - 1] + 1];
+            for (uint32_t t = sb.pstart[v.cell_of[run.x]] + lane; t < t1; t += 32) {
                 const uint32_t q = sb.plist[t];
                 const uint2 cr = v.ro_s[q];
                 if (cr.x >= ro.x) continue;
@@ -448,8 +450,9 @@ __global__ void __launch_bounds__(128) k_sap_near_t(BatchView v, CellWork w, Sap
         long long bd = INT64_MAX;
         uint32_t bj = 0xffffffffu;
         for (uint32_t ri = 0; ri < nr; ++ri) {
-            const uint32_t c = v.cell_of[runs[ri].x];
-            for (uint32_t t = sb.pstart[c], t1 = sb.pstart[c + 1]; t < t1; ++t) {
+            const uint2 run = runs[ri];  // one or more whole cells
+            for (uint32_t t = sb.pstart[v.cell_of[run.x]], t1 = sb.pstart[v.cell_of[run.x + run.y - 1] + 1]; t < t1;
+                 ++t) {
                 const uint32_t q = sb.plist[t];
                 const uint2 cr = v.ro_s[q];
                 if (cr.x >= ro.x) continue;
@@ -577,7 +580,7 @@ cudaError_t launch_sapprox_grid(const BatchView& v, const SapproxBufs& sb, int k
     for (int w = 0; w < words; ++w) {
         const int nbits = std::max(1, std::min(64, key_bits - 64 * w));
         (k_sap_keys<<<grid_for(N, 256), 256, 0, st>>>(v, prev, kin, vin, w, bshift), note_launch());
-        cudaError_t e = radix_sort_u64(kin, vin, kout, vout, ktmp, vtmp, N, nbits, temp, st);
+        cudaError_t e = radix_sort_u64(kin, vin, kout, vout, ktmp, vtmp, N, nbits, temp, st, v.err);
         if (e != cudaSuccess) return e;
         // the sorted order (vout) feeds the next pass; its values go to vin
         prev = vout;

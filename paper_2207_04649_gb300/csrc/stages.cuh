@@ -178,8 +178,16 @@ struct CandStream {
 // grid.cu
 cudaError_t launch_minmax(const BatchView& v, int32_t* mm, cudaStream_t st);
 cudaError_t launch_cell_keys(const BatchView& v, bool key32, void* keys, uint32_t* vals, cudaStream_t st);
+// bflag, bidx, nblocks: null, or the block-start flags, their exclusive scan
+// and the block count (device scalar) for the block table
 cudaError_t launch_gather_cells(const BatchView& v, bool key32, const void* skeys, uint32_t* flag, uint32_t* cidx,
-                                void* scan_temp, cudaStream_t st);
+                                uint32_t* bflag, uint32_t* bidx, uint32_t* nblocks, void* scan_temp, cudaStream_t st);
+// The block table of the datasets with sbits > 0 (after k_cells; v.sbhash
+// cleared to 0xff): keys, first cells and occupancy of every block, then
+// the hash over them. bocc must be zeroed.
+cudaError_t launch_blocks(const BatchView& v, const uint32_t* flag, const uint32_t* bflag, const uint32_t* bidx,
+                          const uint32_t* nblocks, int64_t nblocks_bound, uint64_t* bkey, uint32_t* bfirst,
+                          unsigned long long* bocc, cudaStream_t st);
 cudaError_t launch_hash_insert(const BatchView& v, int64_t ncells_bound, cudaStream_t st);
 
 // rho.cu
@@ -203,8 +211,9 @@ struct CellPrepBufs {
     unsigned long long* stats;  // [0] += candidate pairs
 };
 // Neighbour runs and candidate counts of every cell.
-// kmask: bit K (1..4) = a dataset gridded in K dims with reach 1 is in the
-// batch; bit 0 = one with another reach or no gridded dim.
+// kmask: bit K (1..4) = a dataset gridded in K dims with reach 1 that uses
+// the cell hash is in the batch, bit 8 + K = one that uses the block table;
+// bit 0 = one with another reach or no gridded dim.
 cudaError_t launch_cell_runs(const BatchView& v, const CellPrepBufs& cb, int64_t ncells, uint32_t kmask,
                             cudaStream_t st);
 // Dense and sparse cells (after the runs: a cell with more than sparse_cand
@@ -233,6 +242,10 @@ struct DeltaBufs {
     uint32_t* rvals;      // [N]
     uint32_t* ucount;     // [3] device counters: open list, brute list, open after the coarse ring
     uint32_t* tree_list;  // [N] points open after the ring search
+    uint8_t* ocode;       // ordered open lists: per point 0 resolved, 1 tree, 2 brute force (else null)
+    uint32_t* ocnt;       // their per-block counts [2][blocks] (tree, brute force)
+    uint32_t* oofs;       // and exclusive scans of those
+    int lists_sorted;     // 1: tree_list is in position order already
     const uint32_t* tcount;  // count of the list the tree search reads
     // coarse ring (coarse.cu): cells are aligned blocks of 2^clevel grid
     // cells per gridded dim, contiguous in the Morton-sorted order
@@ -255,6 +268,7 @@ struct DeltaBufs {
     // internal node i (i in [first cell, last cell) of its dataset) is
     // indexed by global cell index too. Boxes: 2 * dpb int4 (lo, then hi).
     int dpb;              // int4 per box corner: 1 (all d <= 4) or 2
+    int compact;          // 1 (all d <= 3): records of two int4, {lo, smallest rank}, {hi, link}; see tree.cu
     int64_t ncells;
     int64_t* cell_off;    // [B+1] first cell of each dataset
     uint64_t* ckey;       // [ncells] cell key
@@ -279,7 +293,10 @@ struct DeltaBufs {
 cudaError_t launch_rank(const BatchView& v, const DeltaBufs& db, int key_bits, void* sort_temp, cudaStream_t st);
 cudaError_t launch_ring(const BatchView& v, const CellWork& w, uint32_t class_mask, int64_t nitems_bound,
                         int64_t nsparse_bound, uint32_t* counters, cudaStream_t st);
-cudaError_t launch_finalize(const BatchView& v, const DeltaBufs& db, cudaStream_t st);
+// ordered_temp (finalize_temp_bytes(N), or null): the open lists come out in
+// position order (then the caller need not sort them)
+size_t finalize_temp_bytes(int64_t n);
+cudaError_t launch_finalize(const BatchView& v, DeltaBufs db, void* ordered_temp, cudaStream_t st);
 // coarse.cu: coarse cells (after the fine cell table), their hash, and the
 // coarse ring search of the open list (needs db.ncells, tree_list sorted)
 cudaError_t launch_coarse_cells(const BatchView& v, const DeltaBufs& db, void* scan_temp, cudaStream_t st);
@@ -398,6 +415,9 @@ cudaError_t launch_sapprox_rho_out(const BatchView& v, int32_t* out, cudaStream_
 
 // label.cu
 cudaError_t launch_labels(const BatchView& v, cudaStream_t st);
+// labels of dataset b only (its points [g0, g0 + n)); the other datasets'
+// labels and center counts are left as they are
+cudaError_t launch_labels_one(const BatchView& v, int b, int64_t g0, int64_t n, cudaStream_t st);
 
 inline unsigned grid_for(int64_t n, int threads) { return (unsigned)((n + threads - 1) / threads); }
 

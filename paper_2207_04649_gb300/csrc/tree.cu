@@ -125,6 +125,12 @@ constexpr uint32_t kLeafLane = 64;
 
 __device__ __forceinline__ void write_leaf(const DeltaBufs& db, int64_t c, const int32_t (&lo)[8],
                                            const int32_t (&hi)[8], uint32_t mr, uint32_t p0, uint32_t p1) {
+    if (db.compact) {  // {lo, smallest rank}, {hi, 0}: the points come from the cell starts
+        int4* lr = db.nodes + (db.ncells + c) * 2;
+        lr[0] = make_int4(lo[0], lo[1], lo[2], (int)mr);
+        lr[1] = make_int4(hi[0], hi[1], hi[2], 0);
+        return;
+    }
     const int dpb = db.dpb, ns = 2 * dpb + 1;
     int4* lr = db.nodes + (db.ncells + c) * ns;
     lr[0] = make_int4(lo[0], lo[1], lo[2], lo[3]);
@@ -208,6 +214,25 @@ __global__ void k_leaves(BatchView v, DeltaBufs db) {
     }
 }
 
+// Compact records (every dataset of the batch in at most 3 dims): two int4,
+// {lo, smallest rank} and {hi, link}. An internal node's children are cells
+// g and g + 1 of the radix tree (Karras), each an internal node or a leaf:
+// link = g << 2 | (left is a leaf) << 1 | (right is a leaf).
+__device__ __forceinline__ uint32_t compact_link(int2 ch) {
+    const uint32_t g = (uint32_t)(ch.x >= 0 ? ch.x : ~ch.x);
+    return (g << 2) | (ch.x < 0 ? 2u : 0u) | (ch.y < 0 ? 1u : 0u);
+}
+
+__device__ __forceinline__ int32_t link_left(uint32_t link) {
+    const int32_t g = (int32_t)(link >> 2);
+    return (link & 2u) ? ~g : g;
+}
+
+__device__ __forceinline__ int32_t link_right(uint32_t link) {
+    const int32_t g = (int32_t)(link >> 2) + 1;
+    return (link & 1u) ? ~g : g;
+}
+
 // Bottom-up refit from the leaf records: the second child to arrive at a
 // node writes the node's record.
 __global__ void k_refit(BatchView v, DeltaBufs db) {
@@ -220,6 +245,17 @@ __global__ void k_refit(BatchView v, DeltaBufs db) {
         if (atomicAdd(&db.flag[node], 1u) == 0u) return;
         __threadfence();
         const int2 ch = __ldcg(&db.child[node]);
+        if (db.compact) {
+            const int4* ca = db.nodes + rec_of(db, ch.x) * 2;
+            const int4* cb = db.nodes + rec_of(db, ch.y) * 2;
+            const int4 a0 = __ldcg(ca), a1 = __ldcg(ca + 1), b0 = __ldcg(cb), b1 = __ldcg(cb + 1);
+            int4* nr = db.nodes + (int64_t)node * 2;
+            nr[0] = make_int4(min(a0.x, b0.x), min(a0.y, b0.y), min(a0.z, b0.z),
+                              (int)min((uint32_t)a0.w, (uint32_t)b0.w));
+            nr[1] = make_int4(max(a1.x, b1.x), max(a1.y, b1.y), max(a1.z, b1.z), (int)compact_link(ch));
+            node = __ldcg(&db.iparent[node]);
+            continue;
+        }
         const int4* ca = db.nodes + rec_of(db, ch.x) * ns;
         const int4* cb = db.nodes + rec_of(db, ch.y) * ns;
         int4* nr = db.nodes + (int64_t)node * ns;
@@ -266,13 +302,67 @@ __device__ __forceinline__ bool out_of_reach(long long d, long long best) {
     return d == INT64_MAX || d > best;
 }
 
-constexpr int kStack = 96;
+// A stack entry keeps a lower bound of its node's squared distance (32
+// bits, saturated), so that a node the best distance has overtaken since it
+// was pushed is dropped without loading its record. The radix tree over
+// cell keys of at most 40 bits is at most 41 levels deep, and the search
+// holds at most one more entry than the depth.
+constexpr int kStack = 64;
+
+__device__ __forceinline__ uint32_t lb32(long long d) {
+    return d >= 0xffffffffll ? 0xffffffffu : (uint32_t)d;
+}
+
+// Squared distance from x to a compact record's box (INT64_MAX when nothing
+// in it ranks above `rank`); link receives the record's link word.
+template <int D>
+__device__ __forceinline__ long long node_test_c(const int4* rec, const int32_t (&x)[D], uint32_t rank,
+                                                 uint32_t& link) {
+    const int4 a = rec[0], h = rec[1];
+    link = (uint32_t)h.w;
+    if ((uint32_t)a.w >= rank) return INT64_MAX;
+    const int32_t lo[3] = {a.x, a.y, a.z}, hi[3] = {h.x, h.y, h.z};
+    long long s = 0;
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+        const long long dd = x[k] < lo[k] ? (long long)lo[k] - x[k] : (x[k] > hi[k] ? (long long)x[k] - hi[k] : 0);
+        s += dd * dd;
+    }
+    return s;
+}
+
+template <int D>
+__device__ __forceinline__ void scan_leaf(const BatchView& v, const DeltaBufs& db, const int4* recb, int64_t c,
+                                          int32_t t0, int32_t t1, const int32_t (&x)[D], uint32_t rank,
+                                          long long& bestD, uint32_t& bestJ, unsigned long long& tests) {
+    constexpr int DP = D <= 4 ? 1 : 2;
+    for (int32_t t = t0; t < t1; ++t) {
+        const uint32_t q = db.lplist ? db.lplist[t] : (uint32_t)t;
+        const uint2 cr = v.ro_s[q];
+        if (cr.x >= rank) continue;
+        ++tests;
+        int32_t cx[D];
+        t_load<D>(recb + (int64_t)q * DP, cx);
+        long long dd = 0;
+#pragma unroll
+        for (int k = 0; k < D; ++k) {
+            const long long e = (long long)x[k] - cx[k];
+            dd += e * e;
+        }
+        if (dd < bestD || (dd == bestD && cr.y < bestJ)) {
+            bestD = dd;
+            bestJ = cr.y;
+        }
+    }
+}
 
 template <int D>
 __global__ void __launch_bounds__(128) k_tree_search(BatchView v, DeltaBufs db) {
     constexpr int DP = D <= 4 ? 1 : 2;
+    constexpr bool CMP = D <= 3;  // compact records possible
     const uint32_t cnt = *db.tcount;
     const int dpb = db.dpb, ns = 2 * dpb + 1;
+    const bool compact = CMP && db.compact;
     unsigned long long visits = 0, tests = 0;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < cnt; i += (int64_t)gridDim.x * blockDim.x) {
         const uint32_t p = db.tree_list[i];
@@ -291,49 +381,91 @@ __global__ void __launch_bounds__(128) k_tree_search(BatchView v, DeltaBufs db) 
             bestJ = (uint32_t)bk;
         }
         int32_t stack[kStack];
+        uint32_t slb[kStack];
         const int64_t c0 = db.cell_off[b], c1 = db.cell_off[b + 1];
-        int sp = 0;
-        stack[sp++] = c1 - c0 >= 2 ? (int32_t)c0 : ~(int32_t)c0;  // the dataset's root
-        while (sp > 0) {
-            const int32_t nd = stack[--sp];
-            ++visits;
-            int4 meta;
-            if (out_of_reach(node_test<D>(db.nodes + rec_of(db, nd) * ns, dpb, x, ro.x, meta), bestD)) continue;
-            if (nd < 0) {  // a cell: scan its points
-                for (int32_t t = meta.y; t < meta.z; ++t) {
-                    const uint32_t q = db.lplist ? db.lplist[t] : (uint32_t)t;
-                    const uint2 cr = v.ro_s[q];
-                    if (cr.x >= ro.x) continue;
-                    ++tests;
-                    int32_t cx[D];
-                    t_load<D>(recb + (int64_t)q * DP, cx);
-                    long long dd = 0;
-#pragma unroll
-                    for (int k = 0; k < D; ++k) {
-                        const long long e = (long long)x[k] - cx[k];
-                        dd += e * e;
-                    }
-                    if (dd < bestD || (dd == bestD && cr.y < bestJ)) {
-                        bestD = dd;
-                        bestJ = cr.y;
-                    }
+        const int32_t root = c1 - c0 >= 2 ? (int32_t)c0 : ~(int32_t)c0;
+        if (compact) {
+            // entries are nodes already tested: (node, distance bound, link)
+            uint32_t slink[kStack];
+            uint32_t link;
+            const long long dr = node_test_c<D>(db.nodes + rec_of(db, root) * 2, x, ro.x, link);
+            int sp = 0;
+            if (!out_of_reach(dr, bestD)) {
+                stack[0] = root;
+                slb[0] = lb32(dr);
+                slink[0] = link;
+                sp = 1;
+            }
+            while (sp > 0) {
+                --sp;
+                const int32_t nd = stack[sp];
+                if ((long long)slb[sp] > bestD) continue;
+                ++visits;
+                if (nd < 0) {  // a cell: scan its points
+                    const int64_t c = ~nd;
+                    const uint32_t t0 = db.lplist ? db.lpstart[c] : v.cell_start[c];
+                    const uint32_t t1 = db.lplist ? db.lpstart[c + 1] : v.cell_start[c + 1];
+                    scan_leaf<D>(v, db, recb, c, (int32_t)t0, (int32_t)t1, x, ro.x, bestD, bestJ, tests);
+                    continue;
                 }
-                continue;
+                if (sp + 2 > kStack) {
+                    atomicOr(v.err, kErrTreeStack);
+                    continue;
+                }
+                const uint32_t lk = slink[sp];
+                const int32_t l = link_left(lk), r = link_right(lk);
+                uint32_t ll, rl;
+                const long long d0 = node_test_c<D>(db.nodes + rec_of(db, l) * 2, x, ro.x, ll);
+                const long long d1 = node_test_c<D>(db.nodes + rec_of(db, r) * 2, x, ro.x, rl);
+                // the nearer child on top
+                const bool swap = d1 < d0;
+                const long long dn = swap ? d1 : d0, df = swap ? d0 : d1;
+                const int32_t nn = swap ? r : l, nf = swap ? l : r;
+                const uint32_t ln = swap ? rl : ll, lf = swap ? ll : rl;
+                if (!out_of_reach(df, bestD)) {
+                    stack[sp] = nf;
+                    slb[sp] = lb32(df);
+                    slink[sp] = lf;
+                    ++sp;
+                }
+                if (!out_of_reach(dn, bestD)) {
+                    stack[sp] = nn;
+                    slb[sp] = lb32(dn);
+                    slink[sp] = ln;
+                    ++sp;
+                }
             }
-            if (sp + 2 > kStack) {
-                atomicOr(v.err, kErrTreeStack);
-                continue;
-            }
-            // both children's records in one round; the nearer is searched first
-            int4 m0, m1;
-            const long long d0 = node_test<D>(db.nodes + rec_of(db, meta.y) * ns, dpb, x, ro.x, m0);
-            const long long d1 = node_test<D>(db.nodes + rec_of(db, meta.z) * ns, dpb, x, ro.x, m1);
-            if (d1 < d0) {
-                if (!out_of_reach(d0, bestD)) stack[sp++] = meta.y;
-                if (!out_of_reach(d1, bestD)) stack[sp++] = meta.z;
-            } else {
-                if (!out_of_reach(d1, bestD)) stack[sp++] = meta.z;
-                if (!out_of_reach(d0, bestD)) stack[sp++] = meta.y;
+        } else {
+            int sp = 0;
+            stack[sp] = root;
+            slb[sp] = 0u;
+            ++sp;
+            while (sp > 0) {
+                --sp;
+                const int32_t nd = stack[sp];
+                if ((long long)slb[sp] > bestD) continue;
+                ++visits;
+                int4 meta;
+                if (out_of_reach(node_test<D>(db.nodes + rec_of(db, nd) * ns, dpb, x, ro.x, meta), bestD)) continue;
+                if (nd < 0) {  // a cell: scan its points
+                    scan_leaf<D>(v, db, recb, ~nd, meta.y, meta.z, x, ro.x, bestD, bestJ, tests);
+                    continue;
+                }
+                if (sp + 2 > kStack) {
+                    atomicOr(v.err, kErrTreeStack);
+                    continue;
+                }
+                // both children's records in one round; the nearer is searched first
+                int4 m0, m1;
+                const long long d0 = node_test<D>(db.nodes + rec_of(db, meta.y) * ns, dpb, x, ro.x, m0);
+                const long long d1 = node_test<D>(db.nodes + rec_of(db, meta.z) * ns, dpb, x, ro.x, m1);
+                if (d1 < d0) {
+                    if (!out_of_reach(d0, bestD)) { stack[sp] = meta.y; slb[sp++] = lb32(d0); }
+                    if (!out_of_reach(d1, bestD)) { stack[sp] = meta.z; slb[sp++] = lb32(d1); }
+                } else {
+                    if (!out_of_reach(d1, bestD)) { stack[sp] = meta.z; slb[sp++] = lb32(d1); }
+                    if (!out_of_reach(d0, bestD)) { stack[sp] = meta.y; slb[sp++] = lb32(d0); }
+                }
             }
         }
         const int64_t g = ds.pt_off + ro.y;

@@ -324,3 +324,98 @@ def test_autotune_keeps_results_and_writes_cache(dpc, tmp_path):
     for a, b in zip(again, ref):
         np.testing.assert_array_equal(a.label, b.label)
         np.testing.assert_array_equal(a.dep, b.dep)
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_kept_jobs_answer_requeries_after_they_return(dpc, mode):
+    """Jobs submitted with keep stay on the device after they finish: new
+    (rho_min, delta_min) queries on the returned dataset (labels only, the
+    decision-graph workflow of Section 2.1) give the oracle's labels, for
+    every job of a batch; releasing them frees their share of the cap."""
+    probs = small_problems(seed=45, count=8)
+    with dpc.Context(0, mode=mode, max_inflight=2) as ctx:
+        jobs = [dpc.Job(p, dc, qs, keep=(i % 3 != 2)) for i, (p, dc, qs) in enumerate(probs)]
+        for j in jobs:
+            ctx.submit(j)
+        if mode == 0:
+            ctx.flush()
+        for j in jobs:
+            s, res = ctx.wait(j.ticket, 120000)
+            assert s == dpc.DPC_OK
+            assert (j.dataset is not None) == bool(j.c.keep)
+        for j, (p, dc, qs) in zip(jobs, probs):
+            check_job(j, p, dc, qs)
+            if j.dataset is None:
+                continue
+            r, dep, d2, _ = expected(p, dc, qs)
+            for rmin, dmin in [(1, dc + 1), (3, 2 * dc + 7), (max(1, int(r.max()) if len(r) else 1), 50 * dc)]:
+                lab = np.full(len(p), -7, np.int32)
+                nc = j.dataset.label(rmin, dmin, lab)
+                olab, onc = oracle.label(r, dep, d2, rmin, dmin)
+                np.testing.assert_array_equal(lab, olab)
+                assert nc == onc
+            assert j.dataset.info()["n"] == len(p)
+        for j in jobs:
+            if j.dataset is not None:
+                j.dataset.release()
+
+
+def test_kept_dataset_holds_its_bytes_until_released(dpc):
+    """A kept dataset counts against the served cap: with a cap that fits
+    one job, a second job is admitted only after the first one's dataset is
+    released."""
+    import time
+    p = workloads.random_blobs(71, 20000, 3, 900, blobs=4, spread=0.05).points
+    q = [(2, 2000)]
+    with dpc.Context(0, mode=1, hbm_cap_bytes=24 << 20, max_inflight=1) as ctx:
+        a = dpc.Job(p, 900, q, keep=True)
+        ctx.submit(a)
+        assert ctx.wait(a.ticket, 60000)[0] == dpc.DPC_OK
+        b = dpc.Job(p, 900, q)
+        ctx.submit(b)
+        time.sleep(0.5)
+        assert ctx.poll(b.ticket)[0] == dpc.DPC_PENDING  # held back by a's dataset
+        a.dataset.release()
+        assert ctx.wait(b.ticket, 60000)[0] == dpc.DPC_OK
+    np.testing.assert_array_equal(a.label, b.label)
+
+
+def test_small_job_is_not_held_back_by_a_large_one(dpc):
+    """Served: a 2M x 8 request followed by a small one; the points cap puts
+    them in separate batches on separate workers, so the small one finishes
+    first, with the oracle's bits."""
+    big = workloads.served_problem(7, 2_000_000, 8)
+    small = workloads.random_blobs(72, 3000, 3, 700, blobs=3, spread=0.05, dup=4)
+    with dpc.Context(0, mode=1, max_inflight=2) as ctx:
+        assert ctx.tuning("max_batch_points") == 1 << 20
+        jb = dpc.Job(big.points, big.d_cut, [(big.rho_min, big.delta_min)])
+        js = dpc.Job(small.points, small.d_cut, [(small.rho_min, small.delta_min)])
+        ctx.submit(jb)
+        ctx.submit(js)
+        s_small, r_small = ctx.wait(js.ticket, 600000)
+        assert s_small == dpc.DPC_OK
+        s_big, r_big = ctx.wait(jb.ticket, 600000)
+        assert s_big == dpc.DPC_OK
+        done_small = r_small.queue_ms + r_small.run_ms
+        done_big = r_big.queue_ms + r_big.run_ms
+        assert done_small < done_big, (done_small, done_big)
+    check_job(js, small.points, small.d_cut, [(small.rho_min, small.delta_min)])
+
+
+def test_one_query_job_finishes_before_four_query_job_of_its_batch(dpc):
+    """In one batch, a job is done as soon as its own outputs are written."""
+    probs = small_problems(seed=46, count=2)
+    p0, dc0, _ = probs[0]
+    p1, dc1, _ = probs[1]
+    with dpc.Context(0, mode=0) as ctx:
+        a = dpc.Job(p0, dc0, [(2, dc0 + 1)])
+        b = dpc.Job(p1, dc1, [(2, dc1 + 1), (1, 2 * dc1), (3, 3 * dc1), (1, 9 * dc1)])
+        ctx.submit(a)
+        ctx.submit(b)
+        ctx.flush()
+        _, ra = ctx.poll(a.ticket)
+        _, rb = ctx.poll(b.ticket)
+        assert ra.status == rb.status == dpc.DPC_OK
+        assert ra.run_ms <= rb.run_ms
+    check_job(a, p0, dc0, [(2, dc0 + 1)])
+    check_job(b, p1, dc1, [(2, dc1 + 1), (1, 2 * dc1), (3, 3 * dc1), (1, 9 * dc1)])

@@ -266,6 +266,17 @@ def served_trace(seed: int = 5, jobs: int = 2000, rate_per_s: float = 200.0,
     return out
 
 
+def served_problem(seed: int = 6, n: int = 2_000_000, d: int = 8) -> Dataset:
+    """One request of the served trace's recipe at a chosen size (the trace
+    draws n up to 2M and d up to 8): a blob mixture + 5% noise with its own
+    cutoff (mean rho 20-200), rho_min and delta_min."""
+    rng = np.random.default_rng(seed)
+    target = float(rng.uniform(20, 200))
+    ds = _random_problem(rng, f"served_{n}_{d}d", n, d, target)
+    ds.seed = seed
+    return ds
+
+
 def random_blobs(seed: int, n: int, d: int, d_cut: int, domain: int = DOMAIN,
                  blobs: int = 4, spread: float = 0.05, dup: int = 0) -> Dataset:
     """Small seeded test problems: a few blobs + uniform noise in
