@@ -235,9 +235,9 @@ def hbm_peak():
 def e2e_roofline(n: int, d: int, info: dict, pair_rate: float, value: float) -> dict:
     """End-to-end points/s roofline: n over the sum of the stages' roofline
     times. Grid, rank sort and labels are HBM-bound, at algorithmic bytes per
-    point (kb = key bytes, P = radix passes = key bits / 8 rounded up, each
-    pass reading the keys twice and the values once and writing both:
-    3 kb + 8 bytes): grid = read the input 4d, write key and index kb + 4,
+    point (kb = key bytes, P = radix passes = key bits / 8 rounded up; one
+    histogram pass reads the keys, kb, and each pass reads the keys and the
+    values and writes both: 2 kb + 8 bytes): grid = read the input 4d, write key and index kb + 4,
     P passes, gather (index 4, input 4d, record 16 per 4 dims), cells and hash
     8; rank = keys kb + 4, P passes, rank and (rank, index) 20; labels = read
     rho, dep, delta2 (16), write parent and label (8), read parents (4). The
@@ -249,7 +249,7 @@ def e2e_roofline(n: int, d: int, info: dict, pair_rate: float, value: float) -> 
 
     def sort_bytes(bits):
         kb = 4 if bits <= 32 else 8
-        return kb, max(1, (bits + 7) // 8) * (3 * kb + 8)
+        return kb, kb + max(1, (bits + 7) // 8) * (2 * kb + 8)
 
     kb, gp = sort_bytes(info.get("grid_key_bits") or 32)
     grid_b = n * (4 * d + kb + 4 + gp + 4 + 4 * d + 16 * dp + 8)
@@ -267,7 +267,80 @@ def e2e_roofline(n: int, d: int, info: dict, pair_rate: float, value: float) -> 
             "bytes_per_point": {"grid": grid_b / n, "rank": rank_b / n, "labels": label_b / n}}
 
 
+def stage_rooflines(n: int, e2e: dict, stages: dict, work: dict, rho_rate: float, ring_rate, ring_src: str) -> dict:
+    """Each stage of one step against its own ceiling (the paper's split of
+    Ex-DPC's time into rho and delta, Table 6, taken stage by stage): the
+    HBM-bound stages at their algorithmic bytes per point (e2e_roofline's
+    model) over the stage's CUDA-event time, against the measured copy
+    bandwidth; the density and ring passes at candidate pairs over their
+    time, against the probe of their own pair test; the open points (tree
+    search and brute force, latency bound, no ceiling) as points and tree
+    node visits per second."""
+    gbs = e2e["hbm_gbs"]
+    bpp = e2e["bytes_per_point"]
+    pairs = work["cand_pairs"]
+
+    def hbm(key, ms):
+        gb = n * bpp[key] / (ms / 1e3) / 1e9 if ms > 0 else 0.0
+        return {"bound": "hbm", "ms": ms, "bytes_per_point": bpp[key], "achieved": gb, "peak": gbs,
+                "unit": "GB/s", "frac": gb / gbs}
+
+    def alu(ms, peak, src):
+        a = pairs / (ms / 1e3) if ms > 0 else 0.0
+        return {"bound": "alu", "ms": ms, "pairs": pairs, "achieved": a / 1e9,
+                "peak": peak / 1e9 if peak else None, "unit": "Gpair/s", "frac": a / peak if peak else None,
+                "peak_source": src}
+
+    rest = stages["ms_rest"]
+    return {
+        "grid": hbm("grid", stages["ms_grid"]),
+        "density": alu(stages["ms_rho"], rho_rate, "dpc_probe_pair_rate, the density kernel's pair form"),
+        "rank": hbm("rank", stages["ms_rank"]),
+        "ring": alu(stages["ms_ring"], ring_rate, ring_src),
+        "open_points": {"bound": "latency", "ms": rest, "points": work["open_after_ring"],
+                        "points_per_s": work["open_after_ring"] / (rest / 1e3) if rest > 0 else 0.0,
+                        "tree_visits": work["tree_visits"],
+                        "visits_per_s": work["tree_visits"] / (rest / 1e3) if rest > 0 else 0.0},
+        "labels": hbm("labels", stages["ms_label"]),
+    }
+
+
+GRID_SOURCES = ("grid.cu", "sort.cu", "rho.cu", "delta.cu", "label.cu", "stages.cuh", "dpc_internal.cuh")
+
+
+def kernel_hbm(workload: str):
+    """Achieved DRAM GB/s of the grid, sort, scatter and gather kernels from
+    the ncu capture summarized in profiles/ (dram__bytes_read + write over
+    gpu__time_duration of each launch, serialized and cold: a lower bound of
+    the kernel's rate inside a step), or None when that capture was of
+    another workload or another version of the kernels."""
+    tpath = os.path.join(ROOT, "profiles", "grid_traffic.json")
+    if not os.path.exists(tpath):
+        return None
+    with open(tpath) as f:
+        tj = json.load(f)
+    if tj.get("workload") != workload or tj.get("source_sha256") != source_digest(GRID_SOURCES):
+        return None
+    gbs, _ = hbm_peak()
+    out = {}
+    for k, e in tj["kernels"].items():
+        rate = e["dram_bytes"] / (e["ns"] * 1e-9) / 1e9
+        out[k] = {"dram_bytes": e["dram_bytes"], "us": e["ns"] / 1e3, "achieved": rate, "unit": "GB/s",
+                  "frac": rate / gbs}
+    return {"kernels": out, "peak": gbs, "summary": tj.get("summary")}
+
+
 RHO_SOURCES = ("rho.cu", "stages.cuh", "dpc_internal.cuh")
+
+
+def source_digest(names) -> str:
+    """sha256 over the named kernel sources (csrc/)."""
+    import hashlib
+    h = hashlib.sha256()
+    for name in names:
+        with open(os.path.join(ROOT, "paper_2207_04649_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()
 
 
 def rho_source_digest() -> str:
@@ -352,6 +425,13 @@ def run_ours(args):
     # anything is timed)
     pair_mode = winfo["pair_mode"] if winfo else 0
     probe_rate, _ = dpc.dpc_probe_pair_rate(local, d, pair_mode)
+    if pair_mode == 2:
+        ring_rate, _ = dpc.dpc_probe_pair_rate(local, d, 3)
+        ring_src = "measured: the ring search's pair test (expanded form, rank compare, least packed key) " \
+                   "with operands in registers on all SMs (dpc_probe_pair_rate mode 3), same run"
+    else:
+        ring_rate = probe_rate
+        ring_src = f"measured: the density pair test (form {pair_mode}) only, a ceiling above the ring's"
 
     clocks = ClockSampler(local)
     clocks.start()
@@ -492,6 +572,12 @@ def run_ours(args):
 
     if dist:
         dist.barrier()
+    e2e = e2e_roofline(n, d, infos[-1], probe_rate, value)
+    stages = {k: statistics.mean(i[k] for i in infos)
+              for k in ("ms_grid", "ms_rho", "ms_rank", "ms_ring", "ms_rest", "ms_label")}
+    work = {k: infos[-1][k] for k in ("cells", "dense_cells", "work_items", "cand_pairs", "dense_pairs",
+                                      "open_after_ring", "brute_points", "grid_dims", "pair_bits",
+                                      "tree_visits", "tree_pairs", "open_after_coarse")}
     if rank == 0:
         line = {
             "metric": metric_for(args), "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
@@ -508,12 +594,11 @@ def run_ours(args):
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": n * d * 4,
                     "d2h_bytes_per_step": n * (4 + 4 + 8 + 4 + (1 if sapprox else 0)) + 8},
             "roofline": roofline,
-            "e2e_roofline": e2e_roofline(n, d, infos[-1], probe_rate, value),
-            "stages_ms": {k: statistics.mean(i[k] for i in infos)
-                          for k in ("ms_grid", "ms_rho", "ms_rank", "ms_ring", "ms_rest", "ms_label")},
-            "work": {k: infos[-1][k] for k in ("cells", "dense_cells", "work_items", "cand_pairs", "dense_pairs",
-                                               "open_after_ring", "brute_points", "grid_dims", "pair_bits",
-                                               "tree_visits", "tree_pairs", "open_after_coarse")},
+            "e2e_roofline": e2e,
+            "stages_ms": stages,
+            "stage_rooflines": stage_rooflines(n, e2e, stages, work, probe_rate, ring_rate, ring_src),
+            "kernel_hbm": kernel_hbm(args.workload) if not knobs else None,
+            "work": work,
             "cpu_baseline": cpu,
             "clocks": clk,
             "gpu_launches": launches,

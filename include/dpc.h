@@ -257,6 +257,9 @@ dpc_status dpc_set_profiling(dpc_ctx* ctx, int on);
 /* Tuning knobs of a context (no counterpart in the paper; they change speed,
  * never results). Keys and ranges:
  *   "kch"     candidates per dense work item, 32 .. 2^20 (default 1024)
+ *   "qch"     queries per dense work item, 32, 64 or 128 (default 128): a
+ *             cell of m points is split into ceil(m / qch) query chunks, each
+ *             its own warp's work, so smaller values put more warps on a cell
  *   "kmax"    gridded dimensions at most, 1 .. 4 (default 4)
  *   "bf_rank" points still open after the ring search whose rank is below
  *             this take the brute-force pass (default 1024)
@@ -404,8 +407,10 @@ dpc_status dpc_last_batch_info(dpc_ctx* ctx, dpc_info* out);
 
 /* Autotuner (no counterpart in the paper). Runs the n_jobs sample jobs as
  * one batch under candidate settings of the knobs that change speed only
- * (kch, bf_rank, clevel; kmax when some d >= 4; tree_min_d when some
- * d >= 5): coordinate descent from the context's current knobs, each
+ * (kch and qch, the candidates and queries per dense work item, i.e. the
+ * warps per cell; bf_rank, clevel; hd_min_d with hd_cell_factor, the grid's
+ * cell factor, tried for every dataset's d; kmax when some d >= 4;
+ * tree_min_d when some d >= 5): coordinate descent from the context's current knobs, each
  * setting timed as the best of `repeats` (1 .. 100) synchronous runs, a
  * change kept only when it is at least 2% faster. The fastest setting
  * becomes the context's knobs and its entry for the sample's signature (the

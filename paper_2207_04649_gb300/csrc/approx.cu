@@ -289,7 +289,7 @@ cudaError_t launch_approx_keys(const BatchView& v, int key_bits, int bshift, uin
     for (int w = 0; w < words; ++w) {
         const int nbits = std::max(1, std::min(64, key_bits - 64 * w));
         (k_approx_keys<<<grid_for(N, 256), 256, 0, st>>>(v, prev, kin, vin, w, bshift), note_launch());
-        cudaError_t e = radix_sort_u64(kin, vin, kout, vout, ktmp, vtmp, N, nbits, temp, st, v.err);
+        cudaError_t e = radix_sort_u64(kin, vin, kout, vout, ktmp, vtmp, N, nbits, temp, st);
         if (e != cudaSuccess) return e;
         prev = vout;
         std::swap(vin, vout);

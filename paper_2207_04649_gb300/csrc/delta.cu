@@ -111,12 +111,14 @@ __global__ void k_ro(BatchView v) {
 // Q queries per lane against staged candidates grp, grp + G, ...: keeps the
 // least packed key (min(D, 2^32-1) << 32 | original index) of a higher point.
 // Forms: direct 32-bit (MODE 0), direct 64-bit saturated (MODE 1), and
-// expanded around the query cell's corner (MODE 2, d <= 3: a staged candidate
-// is (c', |c'|^2), a query keeps -2 q' and |q'|^2; D = |c'|^2 + |q'|^2 - 2 q'.c').
+// expanded (MODE 2, d <= 3: a record is (c, |c|^2 mod 2^32), a query keeps
+// -2 q and |q|^2; D = |c|^2 + |q|^2 - 2 q.c in wrapping 32-bit arithmetic,
+// exact because every candidate lies in the 3^k cells around the query's,
+// so 0 <= D < 4 d s^2 < 2^31).
 template <int D, int MODE, int Q>
 __device__ __forceinline__ void eval_ring(const int4* buf, const uint2* rbuf, int nb, int grp, int G,
-                                          const int32_t (&qx)[4][D], const int32_t (&qa)[4][3],
-                                          const int32_t (&qn)[4], const uint32_t (&qr)[4],
+                                          const int32_t (&qx)[4][D], const uint32_t (&qa)[4][3],
+                                          const uint32_t (&qn)[4], const uint32_t (&qr)[4],
                                           unsigned long long (&best)[4]) {
     constexpr int DP = D <= 4 ? 1 : 2;
 #pragma unroll 2
@@ -126,11 +128,11 @@ __device__ __forceinline__ void eval_ring(const int4* buf, const uint2* rbuf, in
             const int4 c = buf[j];
 #pragma unroll
             for (int t = 0; t < Q; ++t) {
-                int s = c.w + qn[t];
-                s += c.x * qa[t][0];
-                if (D > 1) s += c.y * qa[t][1];
-                if (D > 2) s += c.z * qa[t][2];
-                const unsigned long long key = ((unsigned long long)(uint32_t)s << 32) | ro.y;
+                uint32_t s = (uint32_t)c.w + qn[t];
+                s += (uint32_t)c.x * qa[t][0];
+                if (D > 1) s += (uint32_t)c.y * qa[t][1];
+                if (D > 2) s += (uint32_t)c.z * qa[t][2];
+                const unsigned long long key = ((unsigned long long)s << 32) | ro.y;
                 if (ro.x < qr[t] && key < best[t]) best[t] = key;
             }
         } else {
@@ -169,8 +171,8 @@ __global__ void __launch_bounds__(kRingThreads) k_ring_dense(BatchView v, CellWo
         const DsDesc& ds = v.desc[b];
         if (ds.d != D || ds.mode != MODE) continue;
         const int4* recb = v.rec + ds.rec_off - ds.pt_off * DP;
-        const int q0 = (int)qc * kQch;
-        const int nq = min(kQch, (int)m - q0);
+        const int q0 = (int)qc * w.qch;
+        const int nq = min(w.qch, (int)m - q0);
         int Q, Mq;
         lane_layout(nq, Q, Mq);
         const int G = 32 / Mq;
@@ -185,27 +187,16 @@ __global__ void __launch_bounds__(kRingThreads) k_ring_dense(BatchView v, CellWo
             qr[t] = v.ro_s[cs + q0 + qi].x;
             best[t] = kNoBest;
         }
-        int32_t org[3] = {0, 0, 0};
-        int32_t qa[4][3], qn[4];
+        uint32_t qa[4][3], qn[4];
         if (EXP) {
 #pragma unroll
-            for (int k = 0; k < D && k < 3; ++k) org[k] = ds.lo[k];
-            for (int j = 0; j < ds.k; ++j) {
-                const int g = ds.gdim[j];
-                const int32_t cc = cell_coord(ds, j, rec_coord(recb + (int64_t)cs * DP, g));
-                const int32_t corner = ds.origin[j] + cc * (int32_t)ds.s;
-#pragma unroll
-                for (int k = 0; k < 3; ++k)
-                    if (k == g) org[k] = corner;
-            }
-#pragma unroll
             for (int t = 0; t < 4; ++t) {
-                int32_t nrm = 0;
+                uint32_t nrm = 0u;
 #pragma unroll
                 for (int k = 0; k < 3; ++k) {
-                    const int32_t qk = k < D ? qx[t][k < D ? k : 0] - org[k] : 0;
-                    qa[t][k] = -2 * qk;
-                    nrm += qk * qk;
+                    const uint32_t x = k < D ? (uint32_t)qx[t][k < D ? k : 0] : 0u;
+                    qa[t][k] = 0u - 2u * x;
+                    nrm += x * x;
                 }
                 qn[t] = nrm;
             }
@@ -232,14 +223,8 @@ __global__ void __launch_bounds__(kRingThreads) k_ring_dense(BatchView v, CellWo
             for (int u = 0; u < 4; ++u) {
                 const int f = lane + 32 * u;
                 if (f < nb) {
-                    if (EXP) {
-                        const int4 r = cst.r[u][0];
-                        const int32_t cx = r.x - org[0], cy = D > 1 ? r.y - org[1] : 0, cz = D > 2 ? r.z - org[2] : 0;
-                        buf[f] = make_int4(cx, cy, cz, cx * cx + cy * cy + cz * cz);
-                    } else {
 #pragma unroll
-                        for (int q = 0; q < DP; ++q) buf[f * DP + q] = cst.r[u][q];
-                    }
+                    for (int q = 0; q < DP; ++q) buf[f * DP + q] = cst.r[u][q];
                     rbuf[f] = cst.ro[u];
                 }
             }
@@ -567,9 +552,9 @@ cudaError_t launch_rank(const BatchView& v, const DeltaBufs& db, int rbits, void
     (k_rank_keys<<<grid_for(v.N, 256), 256, 0, st>>>(v, rbits, key64, kin, vin), note_launch());
     cudaError_t e;
     if (key64)
-        e = radix_sort_u64((uint64_t*)kin, vin, (uint64_t*)kout, v.order, (uint64_t*)ktmp, vtmp, v.N, nbits, sort_temp, st, v.err);
+        e = radix_sort_u64((uint64_t*)kin, vin, (uint64_t*)kout, v.order, (uint64_t*)ktmp, vtmp, v.N, nbits, sort_temp, st);
     else
-        e = radix_sort_u32((uint32_t*)kin, vin, (uint32_t*)kout, v.order, (uint32_t*)ktmp, vtmp, v.N, nbits, sort_temp, st, v.err);
+        e = radix_sort_u32((uint32_t*)kin, vin, (uint32_t*)kout, v.order, (uint32_t*)ktmp, vtmp, v.N, nbits, sort_temp, st);
     if (e != cudaSuccess) return e;
     (k_rank_from_order<<<grid_for(v.N, 256), 256, 0, st>>>(v), note_launch());
     (k_ro<<<grid_for(v.N, 256), 256, 0, st>>>(v), note_launch());
@@ -636,7 +621,7 @@ cudaError_t launch_bruteforce(const BatchView& v, const DeltaBufs& db, uint32_t 
     // sort the open points by global rank position; the list length lives on
     // the device, so sort the bound and let the padding (key ~0) sink last
     cudaError_t e = radix_sort_u32(db.bf_keys, db.bf_list, db.bf_keys + bound, db.bf_sorted, db.bf_keys + 2 * bound,
-                                   db.bf_sorted + bound, bound, nbits > 0 ? nbits : 1, sort_temp, st, v.err);
+                                   db.bf_sorted + bound, bound, nbits > 0 ? nbits : 1, sort_temp, st);
     if (e != cudaSuccess) return e;
     const unsigned blocks = grid_for(bound, kBfThreads);
 #define DPC_BF_CLASS(D) \

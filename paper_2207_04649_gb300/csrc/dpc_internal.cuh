@@ -112,7 +112,6 @@ constexpr unsigned kErrStaging = 1u;   // candidate runs shorter than counted
 constexpr unsigned kErrTreeStack = 2u; // tree search stack full
 constexpr unsigned kErrChain = 4u;     // label chain longer than the dataset
 constexpr unsigned kErrBulkWait = 8u;  // a bulk copy into shared memory did not complete in time
-constexpr unsigned kErrSortWait = 16u; // a radix sort pass's look-back wait gave up
 
 // ---------------------------------------------------------------- helpers
 
@@ -228,16 +227,15 @@ long long launch_count();
 
 // sort.cu
 size_t radix_sort_temp_bytes(int64_t n);
-// Stable LSD radix sort of (key, value) pairs on bits [0, nbits), one
-// kernel per 8-bit pass (one-sweep, decoupled look-back). On return the
-// sorted data is in (k_out, v_out). err (nullable): kErrSortWait is set there
-// when a look-back wait gave up (the order is then not valid).
+// Stable LSD radix sort of (key, value) pairs on bits [0, nbits), 8-bit
+// digits (per pass: tile counts, a scan, a stable scatter). On return the
+// sorted data is in (k_out, v_out).
 cudaError_t radix_sort_u64(const uint64_t* k_in, const uint32_t* v_in, uint64_t* k_out, uint32_t* v_out,
                            uint64_t* k_tmp, uint32_t* v_tmp, int64_t n, int nbits, void* temp,
-                           cudaStream_t st, unsigned int* err = nullptr);
+                           cudaStream_t st);
 cudaError_t radix_sort_u32(const uint32_t* k_in, const uint32_t* v_in, uint32_t* k_out, uint32_t* v_out,
                            uint32_t* k_tmp, uint32_t* v_tmp, int64_t n, int nbits, void* temp,
-                           cudaStream_t st, unsigned int* err = nullptr);
+                           cudaStream_t st);
 size_t scan_temp_bytes(int64_t n);
 // Exclusive prefix sum of n uint32 values; writes the total to *total (device) if non-null.
 cudaError_t exclusive_scan_u32(const uint32_t* in, uint32_t* out, int64_t n, uint32_t* total, void* temp,

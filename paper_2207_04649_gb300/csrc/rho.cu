@@ -214,6 +214,21 @@ __global__ void __launch_bounds__(256) k_cell_runs_blk(BatchView v, CellPrepBufs
         uint32_t nr = 0;
         uint32_t first_ci = 0, last_ci = 0;
         bool open = false;
+        // per dim: the one or two blocks the neighbourhood meets, the codes
+        // of its cells in each, and the step from the cell's own block
+        unsigned long long dmask_codes[K][2];
+        int dstep[K][2], nb[K];
+        uint64_t bmask[K];
+#pragma unroll
+        for (int j = 0; j < K; ++j) {
+            const int blo = lo[j] >> L, bhi = hi[j] >> L;
+            nb[j] = bhi != blo ? 2 : 1;
+            dstep[j][0] = blo - cbk[j];
+            dstep[j][1] = bhi - cbk[j];
+            dmask_codes[j][0] = range_codes<K, L>(j, lo[j] - blo * W, min(hi[j], blo * W + W - 1) - blo * W);
+            dmask_codes[j][1] = range_codes<K, L>(j, max(lo[j], bhi * W) - bhi * W, hi[j] - bhi * W);
+            bmask[j] = ds.dmask[j] >> (K * L);
+        }
 #pragma unroll
         for (int t = 0; t < NB; ++t) {
             bool ok = true;
@@ -221,12 +236,10 @@ __global__ void __launch_bounds__(256) k_cell_runs_blk(BatchView v, CellPrepBufs
             unsigned long long box = ~0ull;
 #pragma unroll
             for (int j = 0; j < K; ++j) {
-                const int blo = lo[j] >> L, bhi = hi[j] >> L;
-                const bool up = (t >> j) & 1;
-                if (up && bhi == blo) ok = false;
-                const int bj = up ? bhi : blo;
-                code = morton_step(code, ds.dmask[j] >> (K * L), bj - cbk[j]);
-                box &= range_codes<K, L>(j, max(lo[j], bj * W) - bj * W, min(hi[j], bj * W + W - 1) - bj * W);
+                const int up = (t >> j) & 1;
+                if (up >= nb[j]) ok = false;
+                code = morton_step(code, bmask[j], dstep[j][up]);
+                box &= dmask_codes[j][up];
             }
             if (!ok) continue;
             unsigned long long occ;
@@ -298,7 +311,8 @@ __global__ void k_item_count(BatchView v, CellPrepBufs cb, int kch) {
         const uint32_t c = cb.dense[dc];
         const uint32_t m = v.cell_start[c + 1] - v.cell_start[c];
         const uint32_t cand = cb.cand[c];
-        const uint32_t nq = (m + kQch - 1) / kQch, nk = cand == 0u ? 1u : (cand + kch - 1) / kch;
+        const uint32_t qch = (uint32_t)cb.qch;
+        const uint32_t nq = (m + qch - 1) / qch, nk = cand == 0u ? 1u : (cand + kch - 1) / kch;
         cb.nitem_c[dc] = nq * nk;
     }
 }
@@ -309,7 +323,7 @@ __global__ void k_fill_items(BatchView v, CellPrepBufs cb, int kch) {
     for (int64_t dc = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; dc < nd; dc += (int64_t)gridDim.x * blockDim.x) {
         const uint32_t c = cb.dense[dc];
         const uint32_t m = v.cell_start[c + 1] - v.cell_start[c];
-        const uint32_t nq = (m + kQch - 1) / kQch;
+        const uint32_t nq = (m + (uint32_t)cb.qch - 1) / (uint32_t)cb.qch;
         const uint32_t cand = cb.cand[c];
         const uint32_t nk = cand == 0u ? 1u : (cand + kch - 1) / kch;
         uint4* out = cb.items + cb.item_off[dc];
@@ -366,26 +380,41 @@ __device__ __forceinline__ void eval_rho(const int4* buf, int nb, int grp, int G
     }
 }
 
-// Expanded test (d <= 3). Coordinates are relative to the query cell's
-// corner; a staged candidate is (c'_0, c'_1, c'_2, |c'|^2) and a query keeps
-// a_k = -2 q'_k and b = |q'|^2 - d_cut^2, so that
-//   |q - c|^2 - d_cut^2 = |c'|^2 + b + sum_k c'_k a_k,
-// whose sign bit is the pair test: one add and d multiply-adds.
+// Expanded test (d <= 3). A record is (c_0, c_1, c_2, |c|^2 mod 2^32) and a
+// query keeps a_k = -2 q_k and b = |q|^2 - d_cut^2 (mod 2^32), so that
+//   |q - c|^2 - d_cut^2 = |c|^2 + b + sum_k c_k a_k   (mod 2^32):
+// one add and d multiply-adds in wrapping 32-bit arithmetic. Candidates come
+// from the 3^k cells around the query's, so |q - c|^2 < 4 d s^2 <= 2^31 (the
+// form is chosen only when 9 d s^2 < 2^31): the true value lies in
+// [-2^31, 2^31), and the sign bit of the wrapped sum is the pair test.
 template <int D, int Q>
-__device__ __forceinline__ void eval_rho_x(const int4* buf, int nb, int grp, int G, const int32_t (&qa)[4][3],
-                                           const int32_t (&qb)[4], uint32_t (&cnt)[4]) {
+__device__ __forceinline__ void eval_rho_x(const int4* buf, int nb, int grp, int G, const uint32_t (&qa)[4][3],
+                                           const uint32_t (&qb)[4], uint32_t (&cnt)[4]) {
 #pragma unroll 4
     for (int j = grp; j < nb; j += G) {
         const int4 c = buf[j];
 #pragma unroll
         for (int t = 0; t < Q; ++t) {
-            int s = c.w + qb[t];
-            s += c.x * qa[t][0];
-            if (D > 1) s += c.y * qa[t][1];
-            if (D > 2) s += c.z * qa[t][2];
-            cnt[t] += (uint32_t)s >> 31;
+            uint32_t s = (uint32_t)c.w + qb[t];
+            s += (uint32_t)c.x * qa[t][0];
+            if (D > 1) s += (uint32_t)c.y * qa[t][1];
+            if (D > 2) s += (uint32_t)c.z * qa[t][2];
+            cnt[t] += s >> 31;
         }
     }
+}
+
+// The expanded form's query terms: a_k = -2 q_k, b = |q|^2 - T (mod 2^32).
+template <int D>
+__device__ __forceinline__ void expand_query(const int32_t (&q)[D], uint32_t T, uint32_t (&a)[3], uint32_t& b) {
+    uint32_t n = 0u - T;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        const uint32_t x = k < D ? (uint32_t)q[k < D ? k : 0] : 0u;
+        a[k] = 0u - 2u * x;
+        n += x * x;
+    }
+    b = n;
 }
 
 
@@ -449,8 +478,8 @@ __global__ void __launch_bounds__(kRhoThreads) k_rho_dense(BatchView v, CellWork
             continue;
         }
         const int4* recb = v.rec + ds.rec_off - ds.pt_off * DP;  // indexed by global sorted position
-        const int q0 = (int)qc * kQch;
-        const int nq = min(kQch, (int)m - q0);
+        const int q0 = (int)qc * w.qch;
+        const int nq = min(w.qch, (int)m - q0);
         int Q, Mq;
         lane_layout(nq, Q, Mq);
         const int G = 32 / Mq;
@@ -465,31 +494,11 @@ __global__ void __launch_bounds__(kRhoThreads) k_rho_dense(BatchView v, CellWork
             if (QL) qpos[t] = qlist[qs + i];
             load_point<D>(recb + (int64_t)(QL ? qpos[t] : cs + i) * DP, qx[t]);
         }
-        // expanded form: coordinates relative to the query cell's corner
-        int32_t org[3] = {0, 0, 0};
-        int32_t qa[4][3], qb[4];
+        // expanded form: the queries' terms (the records carry |c|^2)
+        uint32_t qa[4][3], qb[4];
         if (EXP) {
 #pragma unroll
-            for (int k = 0; k < D && k < 3; ++k) org[k] = ds.lo[k];
-            for (int j = 0; j < ds.k; ++j) {
-                const int g = ds.gdim[j];
-                const int32_t cc = cell_coord(ds, j, rec_coord(recb + (int64_t)cs * DP, g));
-                const int32_t corner = ds.origin[j] + cc * (int32_t)ds.s;
-#pragma unroll
-                for (int k = 0; k < 3; ++k)
-                    if (k == g) org[k] = corner;
-            }
-#pragma unroll
-            for (int t = 0; t < 4; ++t) {
-                int32_t nrm = -(int32_t)ds.d_cut2;
-#pragma unroll
-                for (int k = 0; k < 3; ++k) {
-                    const int32_t qk = k < D ? qx[t][k < D ? k : 0] - org[k] : 0;
-                    qa[t][k] = -2 * qk;
-                    nrm += qk * qk;
-                }
-                qb[t] = nrm;
-            }
+            for (int t = 0; t < 4; ++t) expand_query<D>(qx[t], (uint32_t)ds.d_cut2, qa[t], qb[t]);
         }
         uint32_t cnt[4] = {0u, 0u, 0u, 0u};
         // the cell's runs into shared memory, then the candidate stream
@@ -517,14 +526,8 @@ __global__ void __launch_bounds__(kRhoThreads) k_rho_dense(BatchView v, CellWork
             for (int u = 0; u < 4; ++u) {
                 const int f = lane + 32 * u;
                 if (f < nb) {
-                    if (EXP) {
-                        const int4 r = cst.r[u][0];
-                        const int32_t cx = r.x - org[0], cy = D > 1 ? r.y - org[1] : 0, cz = D > 2 ? r.z - org[2] : 0;
-                        buf[f] = make_int4(cx, cy, cz, cx * cx + cy * cy + cz * cz);
-                    } else {
 #pragma unroll
-                        for (int q = 0; q < DP; ++q) buf[f * DP + q] = cst.r[u][q];
-                    }
+                    for (int q = 0; q < DP; ++q) buf[f * DP + q] = cst.r[u][q];
                 }
             }
             __syncwarp();
@@ -757,8 +760,8 @@ __global__ void __launch_bounds__(kRhoThreads) k_rho_dense_bulk(BatchView v, Cel
             continue;
         }
         const int4* recb = v.rec + ds.rec_off - ds.pt_off;  // indexed by global sorted position
-        const int q0 = (int)qc * kQch;
-        const int nq = min(kQch, (int)m - q0);
+        const int q0 = (int)qc * w.qch;
+        const int nq = min(w.qch, (int)m - q0);
         int Q, Mq;
         lane_layout(nq, Q, Mq);
         const int G = 32 / Mq;
@@ -766,30 +769,10 @@ __global__ void __launch_bounds__(kRhoThreads) k_rho_dense_bulk(BatchView v, Cel
         int32_t qx[4][D];
 #pragma unroll
         for (int t = 0; t < 4; ++t) load_point<D>(recb + ((int64_t)cs + q0 + min(ql * Q + t, nq - 1)), qx[t]);
-        int32_t org[3] = {0, 0, 0};
-        int32_t qa[4][3], qb[4];
+        uint32_t qa[4][3], qb[4];
         if (EXP) {
 #pragma unroll
-            for (int k = 0; k < D && k < 3; ++k) org[k] = ds.lo[k];
-            for (int j = 0; j < ds.k; ++j) {
-                const int g = ds.gdim[j];
-                const int32_t cc = cell_coord(ds, j, rec_coord(recb + (int64_t)cs, g));
-                const int32_t corner = ds.origin[j] + cc * (int32_t)ds.s;
-#pragma unroll
-                for (int k = 0; k < 3; ++k)
-                    if (k == g) org[k] = corner;
-            }
-#pragma unroll
-            for (int t = 0; t < 4; ++t) {
-                int32_t nrm = -(int32_t)ds.d_cut2;
-#pragma unroll
-                for (int k = 0; k < 3; ++k) {
-                    const int32_t qk = k < D ? qx[t][k < D ? k : 0] - org[k] : 0;
-                    qa[t][k] = -2 * qk;
-                    nrm += qk * qk;
-                }
-                qb[t] = nrm;
-            }
+            for (int t = 0; t < 4; ++t) expand_query<D>(qx[t], (uint32_t)ds.d_cut2, qa[t], qb[t]);
         }
         uint32_t cnt[4] = {0u, 0u, 0u, 0u};
         const uint32_t nr = nr_c, ctot = ctot_c;
@@ -819,19 +802,6 @@ __global__ void __launch_bounds__(kRhoThreads) k_rho_dense_bulk(BatchView v, Cel
             }
             int4* buf = sbuf[wid][sb];
             const int nb = (int)cur;
-            if (EXP) {
-                // relative to the cell corner, |c'|^2 in the w lane
-#pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                    const int f = lane + 32 * u;
-                    if (f < nb) {
-                        const int4 r = buf[f];
-                        const int32_t cx = r.x - org[0], cy = D > 1 ? r.y - org[1] : 0, cz = D > 2 ? r.z - org[2] : 0;
-                        buf[f] = make_int4(cx, cy, cz, cx * cx + cy * cy + cz * cz);
-                    }
-                }
-                __syncwarp();
-            }
             if (pf < 3) stage(pf++);
             if (EXP) {
                 switch (Q) {

@@ -121,6 +121,7 @@ struct Input {
 
 struct Tune {
     int kch = 1024;         // candidates per dense work item
+    int qch = 128;          // queries per dense work item: 128, 64 or 32 (more warps per cell)
     int kmax = 4;           // gridded dims at most
     uint32_t bf_rank = 1024;  // open points ranked below this take the brute-force pass
     int clevel = 0;           // coarse ring: blocks of 2^clevel cells per gridded dim (0: off)
@@ -210,7 +211,7 @@ std::string tune_line(const std::pair<int, int>& sig, const Tune& t) {
     std::ostringstream o;
     o << "dmax=" << sig.first << " nlog=" << sig.second << " kch=" << t.kch << " kmax=" << t.kmax
       << " bf_rank=" << t.bf_rank << " clevel=" << t.clevel << " ccap=" << t.ccap << " tree_min_d=" << t.tree_min_d
-      << " hd_cell_factor=" << t.hd_cell_factor << " hd_min_d=" << t.hd_min_d;
+      << " hd_cell_factor=" << t.hd_cell_factor << " hd_min_d=" << t.hd_min_d << " qch=" << t.qch;
     return o.str();
 }
 
@@ -220,17 +221,19 @@ void load_tune_cache(dpc_ctx* ctx) {
     std::ifstream f(ctx->tune_cache);
     std::string line;
     while (std::getline(f, line)) {
-        int dmax, nlog, kch, kmax, clevel, tmd, hf, hm;
+        int dmax, nlog, kch, kmax, clevel, tmd, hf, hm, qch;
         unsigned bf, ccap;
         if (std::sscanf(line.c_str(),
                         "dmax=%d nlog=%d kch=%d kmax=%d bf_rank=%u clevel=%d ccap=%u tree_min_d=%d hd_cell_factor=%d "
-                        "hd_min_d=%d",
-                        &dmax, &nlog, &kch, &kmax, &bf, &clevel, &ccap, &tmd, &hf, &hm) != 10)
+                        "hd_min_d=%d qch=%d",
+                        &dmax, &nlog, &kch, &kmax, &bf, &clevel, &ccap, &tmd, &hf, &hm, &qch) != 11)
             continue;
         if (kch < 32 || kch > (1 << 20) || kmax < 1 || kmax > kMaxGridDims || clevel < 0 || clevel > 8 ||
-            ccap < 1 || tmd < 1 || tmd > 9 || hf < 1 || hf > 3 || hm < 1 || hm > 9)
+            ccap < 1 || tmd < 1 || tmd > 9 || hf < 1 || hf > 3 || hm < 1 || hm > 9 ||
+            (qch != 32 && qch != 64 && qch != 128))
             continue;
         Tune t;
+        t.qch = qch;
         t.kch = kch;
         t.kmax = kmax;
         t.bf_rank = bf;
@@ -535,9 +538,9 @@ struct Batch {
         DPC_CK(keep.get(&v.cell_of, N));
         DPC_CK(launch_cell_keys(v, key32, k0, v0, st));
         if (key32)
-            DPC_CK(radix_sort_u32((uint32_t*)k0, v0, (uint32_t*)k2, v.perm, (uint32_t*)k1, v1, N, key_bits, temp, st, v.err));
+            DPC_CK(radix_sort_u32((uint32_t*)k0, v0, (uint32_t*)k2, v.perm, (uint32_t*)k1, v1, N, key_bits, temp, st));
         else
-            DPC_CK(radix_sort_u64((uint64_t*)k0, v0, (uint64_t*)k2, v.perm, (uint64_t*)k1, v1, N, key_bits, temp, st, v.err));
+            DPC_CK(radix_sort_u64((uint64_t*)k0, v0, (uint64_t*)k2, v.perm, (uint64_t*)k1, v1, N, key_bits, temp, st));
         // block-start flags for the datasets whose runs come from the block
         // table; the cell hash serves the others (and the second ring)
         bool any_blocks = false, need_hash = tune.ring2 != 0;
@@ -610,6 +613,7 @@ struct Batch {
             nbs = std::max(nbs, t);
         }
         cb.nbs = nbs;
+        cb.qch = tune.qch;
         DPC_CK(keep.get(&cb.runs, (size_t)std::max<int64_t>(ncells, 1) * nbs));
         DPC_CK(keep.get(&cb.nruns, ncells + 1));
         DPC_CK(keep.get(&cb.cand, ncells + 1));
@@ -650,6 +654,7 @@ struct Batch {
         w.items = cb.items;
         w.nitems = cb.nitems;
         w.kch = tune.kch;
+        w.qch = tune.qch;
         w.nbs = nbs;
         w.stats = d_stats;
         mark(1);
@@ -826,7 +831,7 @@ struct Batch {
                 DPC_CK(tmp.get(&vt, ntree));
                 DPC_CK(tmp.get(&t3, radix_sort_temp_bytes(ntree)));
                 DPC_CK(radix_sort_u32(db.tree_list, db.tree_list, ks, vs, kt, vt, ntree, bits_for((uint64_t)N),
-                                      t3, st, v.err));
+                                      t3, st));
                 db.tree_list = ks;
             }
             const int64_t nc = ncells;
@@ -1175,6 +1180,7 @@ struct Batch {
                 DPC_CK(tmp.get(&pn, 1));
                 DPC_CK(launch_sapprox_items(v, w, sb, ncells, tune.kch, nitem_c, item_off, pitems, pn, cap, temp, st));
                 CellWork wp = w;
+                wp.qch = kQch;  // pick items hold up to kQch picks each
                 wp.items = pitems;
                 wp.nitems = pn;
                 mark(4);
@@ -1363,6 +1369,7 @@ dpc_status dpc_set_tuning(dpc_ctx* ctx, const char* key, int64_t value) {
     const std::string k(key);
     dpc::Tune& t = ctx->tune;
     if (k == "kch" && value >= 32 && value <= (1 << 20)) t.kch = (int)value;
+    else if (k == "qch" && (value == 32 || value == 64 || value == 128)) t.qch = (int)value;
     else if (k == "kmax" && value >= 1 && value <= dpc::kMaxGridDims) t.kmax = (int)value;
     else if (k == "bf_rank" && value >= 0 && value <= UINT32_MAX) t.bf_rank = (uint32_t)value;
     else if (k == "clevel" && value >= 0 && value <= 8) t.clevel = (int)value;
@@ -1392,6 +1399,7 @@ dpc_status dpc_get_tuning(dpc_ctx* ctx, const char* key, int64_t* value) {
     const std::string k(key);
     const dpc::Tune& t = ctx->tune;
     if (k == "kch") *value = t.kch;
+    else if (k == "qch") *value = t.qch;
     else if (k == "kmax") *value = t.kmax;
     else if (k == "bf_rank") *value = t.bf_rank;
     else if (k == "clevel") *value = t.clevel;
@@ -1982,12 +1990,18 @@ dpc_status dpc_autotune(dpc_ctx* ctx, const dpc_job* jobs, int32_t n_jobs, int32
         const char* name;
         std::vector<int64_t> values;
     };
-    std::vector<Knob> knobs = {{"kch", {1024, 2048, 4096}}, {"bf_rank", {256, 1024, 4096}}, {"clevel", {0, 2}}};
+    // kch, qch: candidates and queries per dense work item (queries per item
+    // set the warps per cell); hd_min_d with the cell factor: cells of side
+    // d_cut / f from that many dims up (2: every dataset, the low-d cell factor)
+    std::vector<Knob> knobs = {{"kch", {1024, 2048, 4096}}, {"qch", {128, 64, 32}},
+                               {"bf_rank", {256, 1024, 4096}}, {"clevel", {0, 2}}, {"hd_min_d", {7, 2}}};
     if (sig.first >= 4) knobs.push_back({"kmax", {3, 4}});
     if (sig.first >= 5) knobs.push_back({"tree_min_d", {9, 5}});
-    if (sig.first >= 5) knobs.push_back({"hd_cell_factor", {1, 2}});
+    knobs.push_back({"hd_cell_factor", {1, 2}});
     auto with = [](dpc::Tune t, const std::string& k, int64_t v) {
         if (k == "kch") t.kch = (int)v;
+        else if (k == "qch") t.qch = (int)v;
+        else if (k == "hd_min_d") t.hd_min_d = (int)v;
         else if (k == "bf_rank") t.bf_rank = (uint32_t)v;
         else if (k == "clevel") t.clevel = (int)v;
         else if (k == "kmax") t.kmax = (int)v;

@@ -85,33 +85,28 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_tiles(const uint32_t* __r
 
 __global__ void k_set_zero(uint32_t* p) { *p = 0u; }
 
-// ------------------------------------------------ one-sweep radix sort
+// ------------------------------------------------------------ radix sort
 //
-// Each 8-bit pass is one kernel: a block takes the next tile of kOsTile keys
-// (tiles numbered in the order blocks start, from an atomic counter), ranks
-// its keys stably by digit (warp-private digit counters, in index order),
-// publishes its digit counts, and finds the counts of all earlier tiles by
-// looking back through their published words (decoupled look-back: a tile
-// whose inclusive prefix is published ends the walk). Every earlier tile
-// belongs to a block that has already started, so a walk only waits for
-// blocks that are running; the waits are bounded (kOsSpin polls), after
-// which the block sets the error word and stops waiting. The digit offsets
-// of every pass come from one histogram pass over the keys before the
-// first pass.
+// LSD radix sort, 8-bit digits, three steps per pass: per-tile digit counts
+// (k_rs_up), one exclusive scan of the counts in digit-major order (every
+// tile's first slot for every digit), and the scatter (k_rs_down), which
+// ranks a tile's keys stably by digit (warp-private digit counters in index
+// order, then the warps' offsets per digit) and writes each key and value to
+// its slot. A histogram of every pass's digits over all keys, taken once
+// before the first pass, marks passes in which all keys share a digit: such
+// a pass keeps the order and is a copy.
 
-constexpr int kOsThreads = 256;
-constexpr int kOsItems = 8;
-constexpr int kOsTile = kOsThreads * kOsItems;   // 2048 keys
-constexpr int kOsMaxPasses = 8;
-constexpr int kOsSpin = 1 << 22;                 // look-back polls before a wait gives up
-constexpr int kOsWin = 16;                       // earlier tiles read per look-back round
+constexpr int kRsThreads = 256;
+constexpr int kRsItems = 16;
+constexpr int kRsTile = kRsThreads * kRsItems;   // 4096 keys
+constexpr int kRsMaxPasses = 8;
 
 // Global digit histograms of every pass, [pass][256].
 template <typename K>
-__global__ void __launch_bounds__(256) k_os_hist(const K* __restrict__ keys, int64_t n, int passes,
-                                                  uint32_t* __restrict__ hist) {
-    __shared__ uint32_t h[kOsMaxPasses][256];
-    for (int i = threadIdx.x; i < kOsMaxPasses * 256; i += blockDim.x) (&h[0][0])[i] = 0u;
+__global__ void __launch_bounds__(256) k_rs_hist_all(const K* __restrict__ keys, int64_t n, int passes,
+                                                      uint32_t* __restrict__ hist) {
+    __shared__ uint32_t h[kRsMaxPasses][256];
+    for (int i = threadIdx.x; i < kRsMaxPasses * 256; i += blockDim.x) (&h[0][0])[i] = 0u;
     __syncthreads();
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         const K k = keys[i];
@@ -124,140 +119,94 @@ __global__ void __launch_bounds__(256) k_os_hist(const K* __restrict__ keys, int
     }
 }
 
-__device__ __forceinline__ unsigned long long os_load(const unsigned long long* p) {
-    unsigned long long v;
-    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
-    return v;
+__device__ __forceinline__ bool trivial_pass(const uint32_t* hist, int pass, int64_t n) {
+    return __syncthreads_or(hist[pass * 256 + threadIdx.x] == (uint32_t)n) != 0;
 }
 
-__device__ __forceinline__ void os_store(unsigned long long* p, unsigned long long v) {
-    asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
-}
-
-// One pass over bits [8 pass, 8 pass + 8). status: [tiles][256] words
-// (flag << 32 | count), flags 2 pass + 1 (the tile's own count) and
-// 2 pass + 2 (the count of this and every earlier tile); words of earlier
-// passes read as "not yet".
+// Digit counts of one tile: counts[digit * tiles + tile].
 template <typename K>
-__global__ void __launch_bounds__(kOsThreads) k_os_pass(const K* __restrict__ kin, const uint32_t* __restrict__ vin,
+__global__ void __launch_bounds__(kRsThreads) k_rs_up(const K* __restrict__ kin, int64_t n, int pass,
+                                                       const uint32_t* __restrict__ hist, uint32_t* __restrict__ counts,
+                                                       int64_t tiles) {
+    __shared__ uint32_t h[256];
+    h[threadIdx.x] = 0u;
+    if (trivial_pass(hist, pass, n)) return;  // also orders the clear before the counts
+    const int shift = 8 * pass;
+    const int64_t base = (int64_t)blockIdx.x * kRsTile;
+#pragma unroll 4
+    for (int i = 0; i < kRsItems; ++i) {
+        const int64_t idx = base + i * kRsThreads + threadIdx.x;
+        if (idx < n) atomicAdd(&h[(uint32_t)(kin[idx] >> shift) & 255u], 1u);
+    }
+    __syncthreads();
+    counts[(int64_t)threadIdx.x * tiles + blockIdx.x] = h[threadIdx.x];
+}
+
+// Stable scatter of one tile: element order inside the tile is (warp, item,
+// lane), which is index order.
+template <typename K>
+__global__ void __launch_bounds__(kRsThreads) k_rs_down(const K* __restrict__ kin, const uint32_t* __restrict__ vin,
                                                          K* __restrict__ kout, uint32_t* __restrict__ vout, int64_t n,
                                                          int pass, const uint32_t* __restrict__ hist,
-                                                         unsigned long long* __restrict__ status,
-                                                         uint32_t* __restrict__ tile_ctr, unsigned int* __restrict__ err) {
-    __shared__ uint32_t wcnt[kOsThreads / 32][256];
+                                                         const uint32_t* __restrict__ offs, int64_t tiles) {
+    __shared__ uint32_t wcnt[kRsThreads / 32][256];
     __shared__ uint32_t sbase[256];
-    __shared__ uint32_t s_tile;
     const int t = threadIdx.x, w = t >> 5, lane = t & 31;
     const unsigned lt = (1u << lane) - 1u;
-    if (t == 0) s_tile = atomicAdd(&tile_ctr[pass], 1u);
 #pragma unroll
-    for (int ww = 0; ww < kOsThreads / 32; ++ww) wcnt[ww][t] = 0u;
-    // exclusive scan of this pass's global histogram: the digit's first slot
-    {
-        const uint32_t c = hist[pass * 256 + t];
-        uint32_t incl = c;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
-            if (lane >= o) incl += y;
-        }
-        if (lane == 31) sbase[w] = incl;
-        __syncthreads();
-        uint32_t off = 0;
-        for (int ww = 0; ww < w; ++ww) off += sbase[ww];
-        __syncthreads();
-        sbase[t] = off + incl - c;
-    }
-    // a pass in which every key has the same digit keeps the order: copy
-    const int trivial = __syncthreads_or(hist[pass * 256 + t] == (uint32_t)n);
-    const uint32_t tile = s_tile;
-    if (trivial) {
-        for (int64_t i = (int64_t)tile * kOsTile + t; i < min(n, (int64_t)(tile + 1) * kOsTile); i += kOsThreads) {
+    for (int ww = 0; ww < kRsThreads / 32; ++ww) wcnt[ww][t] = 0u;
+    sbase[t] = offs[(int64_t)t * tiles + blockIdx.x];
+    const int64_t tile0 = (int64_t)blockIdx.x * kRsTile;
+    if (trivial_pass(hist, pass, n)) {  // every key has the same digit: the order stays
+        for (int64_t i = tile0 + t; i < min(n, tile0 + kRsTile); i += kRsThreads) {
             kout[i] = kin[i];
             vout[i] = vin[i];
         }
         return;
     }
-    const int64_t base = (int64_t)tile * kOsTile + (int64_t)w * 32 * kOsItems;
+    const int64_t base = tile0 + (int64_t)w * 32 * kRsItems;
     const int shift = 8 * pass;
-    K key[kOsItems];
-    uint32_t val[kOsItems], dig[kOsItems], rnk[kOsItems];
+    K key[kRsItems];
+    uint32_t val[kRsItems], dig[kRsItems], rnk[kRsItems];
 #pragma unroll
-    for (int i = 0; i < kOsItems; ++i) {
+    for (int i = 0; i < kRsItems; ++i) {
         const int64_t idx = base + i * 32 + lane;
         const bool valid = idx < n;
         key[i] = valid ? kin[idx] : K(0);
         val[i] = valid ? vin[idx] : 0u;
         dig[i] = valid ? ((uint32_t)(key[i] >> shift) & 255u) : 256u;
     }
-    // stable ranks within the warp's run of 32 * kOsItems keys
+    // stable ranks within the warp's run of 32 * kRsItems keys: the lanes of
+    // one step sharing a digit take consecutive ranks after the warp's count
+    // of that digit so far, which the step's lowest such lane advances with
+    // one shared-memory atomic. Every lane waits in the step's shuffle for
+    // the value of that atomic, so the steps' atomics take effect in step
+    // order. The matches of all steps go out first.
+    unsigned peers[kRsItems];
 #pragma unroll
-    for (int i = 0; i < kOsItems; ++i) {
-        const unsigned peers = __match_any_sync(0xffffffffu, dig[i]);
-        const uint32_t before = dig[i] < 256u ? wcnt[w][dig[i]] : 0u;
-        rnk[i] = before + (uint32_t)__popc(peers & lt);
-        __syncwarp();
-        if (dig[i] < 256u && (peers & lt) == 0u) wcnt[w][dig[i]] = before + (uint32_t)__popc(peers);
-        __syncwarp();
+    for (int i = 0; i < kRsItems; ++i) peers[i] = __match_any_sync(0xffffffffu, dig[i]);
+#pragma unroll
+    for (int i = 0; i < kRsItems; ++i) {
+        const int leader = __ffs(peers[i]) - 1;
+        uint32_t before = 0u;
+        if (lane == leader && dig[i] < 256u) before = atomicAdd(&wcnt[w][dig[i]], (uint32_t)__popc(peers[i]));
+        before = __shfl_sync(0xffffffffu, before, leader);
+        rnk[i] = before + (uint32_t)__popc(peers[i] & lt);
     }
     __syncthreads();
-    // thread t = digit t: warps' exclusive offsets, the tile's count, look-back
-    uint32_t cnt = 0;
+    // thread t = digit t: the warps' exclusive offsets
+    {
+        uint32_t run = 0;
 #pragma unroll
-    for (int ww = 0; ww < kOsThreads / 32; ++ww) {
-        const uint32_t c = wcnt[ww][t];
-        wcnt[ww][t] = cnt;
-        cnt += c;
-    }
-    const unsigned long long agg = (unsigned long long)(2 * pass + 1) << 32;
-    const unsigned long long inc = (unsigned long long)(2 * pass + 2) << 32;
-    unsigned long long* my = status + (int64_t)tile * 256 + t;
-    uint32_t prefix = 0;
-    if (tile == 0) {
-        os_store(my, inc | cnt);
-    } else {
-        os_store(my, agg | cnt);
-        // the walk reads kOsWin earlier tiles' words per round trip: their
-        // own counts are summed down to the first tile with an inclusive count
-        int64_t j = (int64_t)tile - 1;
-        int spins = 0;
-        bool done = false;
-        while (!done) {
-            unsigned long long wv[kOsWin];
-#pragma unroll
-            for (int u = 0; u < kOsWin; ++u) wv[u] = j - u >= 0 ? os_load(status + (j - u) * 256 + t) : inc;
-            bool stop = false;
-            int adv = 0;
-#pragma unroll
-            for (int u = 0; u < kOsWin; ++u) {
-                if (stop) continue;
-                const unsigned long long f = wv[u] & 0xffffffff00000000ull;
-                if (f == inc) {
-                    prefix += (uint32_t)wv[u];
-                    done = stop = true;
-                } else if (f == agg) {
-                    prefix += (uint32_t)wv[u];
-                    ++adv;
-                } else {
-                    stop = true;  // not published yet: read it again next round
-                }
-            }
-            if (done) break;
-            j -= adv;
-            if (adv == 0) {
-                if (++spins > kOsSpin) {
-                    atomicOr(err, kErrSortWait);
-                    break;
-                }
-                __nanosleep(32);
-            }
+        for (int ww = 0; ww < kRsThreads / 32; ++ww) {
+            const uint32_t c = wcnt[ww][t];
+            wcnt[ww][t] = run;
+            run += c;
         }
-        os_store(my, inc | (prefix + cnt));
     }
-    sbase[t] += prefix;
     __syncthreads();
 #pragma unroll
-    for (int i = 0; i < kOsItems; ++i) {
+    for (int i = 0; i < kRsItems; ++i) {
         if (dig[i] < 256u) {
             const uint32_t pos = sbase[dig[i]] + wcnt[w][dig[i]] + rnk[i];
             kout[pos] = key[i];
@@ -268,7 +217,7 @@ __global__ void __launch_bounds__(kOsThreads) k_os_pass(const K* __restrict__ ki
 
 template <typename K>
 cudaError_t radix_sort_impl(const K* k_in, const uint32_t* v_in, K* k_out, uint32_t* v_out, K* k_tmp,
-                            uint32_t* v_tmp, int64_t n, int nbits, void* temp, cudaStream_t st, unsigned int* err) {
+                            uint32_t* v_tmp, int64_t n, int nbits, void* temp, cudaStream_t st) {
     if (n <= 0) return cudaSuccess;
     const int passes = (nbits + 7) / 8;
     if (passes == 0) {
@@ -276,25 +225,26 @@ cudaError_t radix_sort_impl(const K* k_in, const uint32_t* v_in, K* k_out, uint3
         if (e != cudaSuccess) return e;
         return cudaMemcpyAsync(v_out, v_in, n * sizeof(uint32_t), cudaMemcpyDeviceToDevice, st);
     }
-    const int64_t tiles = ceil_div(n, kOsTile);
-    // temp: hist [8][256], tile counters [8], error word, pad, status [tiles][256]
+    const int64_t tiles = ceil_div(n, kRsTile);
+    // temp: hist [8][256], counts [256][tiles], offsets [256][tiles], scan scratch
     uint32_t* hist = reinterpret_cast<uint32_t*>(temp);
-    uint32_t* tile_ctr = hist + kOsMaxPasses * 256;
-    unsigned int* own_err = tile_ctr + kOsMaxPasses;
-    unsigned long long* status = reinterpret_cast<unsigned long long*>(hist + kOsMaxPasses * 256 + 64);
-    const size_t clear = (kOsMaxPasses * 256 + 64) * sizeof(uint32_t) + (size_t)tiles * 256 * sizeof(unsigned long long);
-    cudaError_t e = cudaMemsetAsync(temp, 0, clear, st);
+    uint32_t* counts = hist + kRsMaxPasses * 256;
+    uint32_t* offs = counts + align256(256 * tiles * sizeof(uint32_t)) / sizeof(uint32_t);
+    void* stemp = offs + align256(256 * tiles * sizeof(uint32_t)) / sizeof(uint32_t);
+    cudaError_t e = cudaMemsetAsync(hist, 0, kRsMaxPasses * 256 * sizeof(uint32_t), st);
     if (e != cudaSuccess) return e;
-    if (!err) err = own_err;
     const unsigned hb = (unsigned)std::min<int64_t>(ceil_div(n, 256 * 16), 152 * 8);
-    (k_os_hist<K><<<hb, 256, 0, st>>>(k_in, n, passes, hist), note_launch());
+    (k_rs_hist_all<K><<<hb, 256, 0, st>>>(k_in, n, passes, hist), note_launch());
     const K* src_k = k_in;
     const uint32_t* src_v = v_in;
     for (int p = 0; p < passes; ++p) {
         const bool to_out = ((passes - 1 - p) % 2) == 0;
         K* dk = to_out ? k_out : k_tmp;
         uint32_t* dv = to_out ? v_out : v_tmp;
-        (k_os_pass<K><<<(unsigned)tiles, kOsThreads, 0, st>>>(src_k, src_v, dk, dv, n, p, hist, status, tile_ctr, err),
+        (k_rs_up<K><<<(unsigned)tiles, kRsThreads, 0, st>>>(src_k, n, p, hist, counts, tiles), note_launch());
+        e = exclusive_scan_u32(counts, offs, 256 * tiles, nullptr, stemp, st);
+        if (e != cudaSuccess) return e;
+        (k_rs_down<K><<<(unsigned)tiles, kRsThreads, 0, st>>>(src_k, src_v, dk, dv, n, p, hist, offs, tiles),
          note_launch());
         src_k = dk;
         src_v = dv;
@@ -335,20 +285,21 @@ cudaError_t exclusive_scan_u32(const uint32_t* in, uint32_t* out, int64_t n, uin
 }
 
 size_t radix_sort_temp_bytes(int64_t n) {
-    const int64_t tiles = ceil_div(n > 0 ? n : 1, kOsTile);
-    return (kOsMaxPasses * 256 + 64) * sizeof(uint32_t) + (size_t)tiles * 256 * sizeof(unsigned long long) + 256;
+    const int64_t tiles = ceil_div(n > 0 ? n : 1, kRsTile);
+    return kRsMaxPasses * 256 * sizeof(uint32_t) + 2 * align256(256 * tiles * sizeof(uint32_t)) +
+           scan_temp_bytes(256 * tiles) + 256;
 }
 
 cudaError_t radix_sort_u64(const uint64_t* k_in, const uint32_t* v_in, uint64_t* k_out, uint32_t* v_out,
                            uint64_t* k_tmp, uint32_t* v_tmp, int64_t n, int nbits, void* temp,
-                           cudaStream_t st, unsigned int* err) {
-    return radix_sort_impl<uint64_t>(k_in, v_in, k_out, v_out, k_tmp, v_tmp, n, nbits, temp, st, err);
+                           cudaStream_t st) {
+    return radix_sort_impl<uint64_t>(k_in, v_in, k_out, v_out, k_tmp, v_tmp, n, nbits, temp, st);
 }
 
 cudaError_t radix_sort_u32(const uint32_t* k_in, const uint32_t* v_in, uint32_t* k_out, uint32_t* v_out,
                            uint32_t* k_tmp, uint32_t* v_tmp, int64_t n, int nbits, void* temp,
-                           cudaStream_t st, unsigned int* err) {
-    return radix_sort_impl<uint32_t>(k_in, v_in, k_out, v_out, k_tmp, v_tmp, n, nbits, temp, st, err);
+                           cudaStream_t st) {
+    return radix_sort_impl<uint32_t>(k_in, v_in, k_out, v_out, k_tmp, v_tmp, n, nbits, temp, st);
 }
 
 }  // namespace dpc

@@ -5,7 +5,7 @@
 namespace dpc {
 
 constexpr int kSparseMax = 4;     // cells with at most this many points take the thread-per-cell path
-constexpr int kQch = 128;         // queries per dense work item (4 per lane)
+constexpr int kQch = 128;         // queries per dense work item at most (4 per lane)
 constexpr int kMaxNb = 81;        // neighbour cells per cell for R = 1, k <= 4
 
 // Dense-cell work description produced by the cell preparation kernels.
@@ -20,6 +20,8 @@ struct CellWork {
     const uint4* items;         // (dense index, query chunk, candidate chunk, 0)
     const uint32_t* nitems;     // device scalar
     int kch;                    // candidates per dense work item
+    int qch;                    // queries per dense work item (32, 64 or 128): a cell of m points is
+                                // ceil(m / qch) query chunks, each its own warp's items
     int nbs;                    // run slots per cell: max over the batch of (2R+1)^k
     unsigned long long* stats;  // [0] candidate pairs of all cells
 };
@@ -208,6 +210,7 @@ struct CellPrepBufs {
     uint4* items;         // [nitems_bound]
     uint32_t* nitems;     // scalar
     int nbs;
+    int qch;              // queries per dense work item (CellWork::qch)
     unsigned long long* stats;  // [0] += candidate pairs
 };
 // Neighbour runs and candidate counts of every cell.

@@ -385,87 +385,99 @@ __global__ void __launch_bounds__(128) k_tree_search(BatchView v, DeltaBufs db) 
         const int64_t c0 = db.cell_off[b], c1 = db.cell_off[b + 1];
         const int32_t root = c1 - c0 >= 2 ? (int32_t)c0 : ~(int32_t)c0;
         if (compact) {
-            // entries are nodes already tested: (node, distance bound, link)
+            // the current node (tested, in reach) walks to its nearer child
+            // in reach; the farther child in reach is stacked as (node,
+            // distance bound, link); a node whose children are both out of
+            // reach, or a scanned cell, takes the next stacked node still in
+            // reach
             uint32_t slink[kStack];
-            uint32_t link;
-            const long long dr = node_test_c<D>(db.nodes + rec_of(db, root) * 2, x, ro.x, link);
+            uint32_t cur_link;
+            int32_t cur = root;
             int sp = 0;
-            if (!out_of_reach(dr, bestD)) {
-                stack[0] = root;
-                slb[0] = lb32(dr);
-                slink[0] = link;
-                sp = 1;
-            }
-            while (sp > 0) {
-                --sp;
-                const int32_t nd = stack[sp];
-                if ((long long)slb[sp] > bestD) continue;
+            bool have = !out_of_reach(node_test_c<D>(db.nodes + rec_of(db, root) * 2, x, ro.x, cur_link), bestD);
+            while (have) {
                 ++visits;
-                if (nd < 0) {  // a cell: scan its points
-                    const int64_t c = ~nd;
+                bool next = false;
+                if (cur < 0) {  // a cell: scan its points
+                    const int64_t c = ~cur;
                     const uint32_t t0 = db.lplist ? db.lpstart[c] : v.cell_start[c];
                     const uint32_t t1 = db.lplist ? db.lpstart[c + 1] : v.cell_start[c + 1];
                     scan_leaf<D>(v, db, recb, c, (int32_t)t0, (int32_t)t1, x, ro.x, bestD, bestJ, tests);
-                    continue;
+                } else {
+                    const int32_t l = link_left(cur_link), r = link_right(cur_link);
+                    uint32_t ll, rl;
+                    const long long d0 = node_test_c<D>(db.nodes + rec_of(db, l) * 2, x, ro.x, ll);
+                    const long long d1 = node_test_c<D>(db.nodes + rec_of(db, r) * 2, x, ro.x, rl);
+                    const bool swap = d1 < d0;
+                    const long long dn = swap ? d1 : d0, df = swap ? d0 : d1;
+                    if (!out_of_reach(df, bestD)) {
+                        if (sp < kStack) {
+                            stack[sp] = swap ? l : r;
+                            slb[sp] = lb32(df);
+                            slink[sp] = swap ? ll : rl;
+                            ++sp;
+                        } else {
+                            atomicOr(v.err, kErrTreeStack);
+                        }
+                    }
+                    if (!out_of_reach(dn, bestD)) {
+                        cur = swap ? r : l;
+                        cur_link = swap ? rl : ll;
+                        next = true;
+                    }
                 }
-                if (sp + 2 > kStack) {
-                    atomicOr(v.err, kErrTreeStack);
-                    continue;
+                while (!next && sp > 0) {
+                    --sp;
+                    if ((long long)slb[sp] > bestD) continue;  // overtaken since it was stacked
+                    cur = stack[sp];
+                    cur_link = slink[sp];
+                    next = true;
                 }
-                const uint32_t lk = slink[sp];
-                const int32_t l = link_left(lk), r = link_right(lk);
-                uint32_t ll, rl;
-                const long long d0 = node_test_c<D>(db.nodes + rec_of(db, l) * 2, x, ro.x, ll);
-                const long long d1 = node_test_c<D>(db.nodes + rec_of(db, r) * 2, x, ro.x, rl);
-                // the nearer child on top
-                const bool swap = d1 < d0;
-                const long long dn = swap ? d1 : d0, df = swap ? d0 : d1;
-                const int32_t nn = swap ? r : l, nf = swap ? l : r;
-                const uint32_t ln = swap ? rl : ll, lf = swap ? ll : rl;
-                if (!out_of_reach(df, bestD)) {
-                    stack[sp] = nf;
-                    slb[sp] = lb32(df);
-                    slink[sp] = lf;
-                    ++sp;
-                }
-                if (!out_of_reach(dn, bestD)) {
-                    stack[sp] = nn;
-                    slb[sp] = lb32(dn);
-                    slink[sp] = ln;
-                    ++sp;
-                }
+                have = next;
             }
         } else {
+            // as above; the current node's meta word comes with it (the
+            // nearer child's from its test), a stacked node's is reloaded
+            int4 meta;
+            int32_t cur = root;
             int sp = 0;
-            stack[sp] = root;
-            slb[sp] = 0u;
-            ++sp;
-            while (sp > 0) {
-                --sp;
-                const int32_t nd = stack[sp];
-                if ((long long)slb[sp] > bestD) continue;
+            bool have = !out_of_reach(node_test<D>(db.nodes + rec_of(db, root) * ns, dpb, x, ro.x, meta), bestD);
+            while (have) {
                 ++visits;
-                int4 meta;
-                if (out_of_reach(node_test<D>(db.nodes + rec_of(db, nd) * ns, dpb, x, ro.x, meta), bestD)) continue;
-                if (nd < 0) {  // a cell: scan its points
-                    scan_leaf<D>(v, db, recb, ~nd, meta.y, meta.z, x, ro.x, bestD, bestJ, tests);
-                    continue;
-                }
-                if (sp + 2 > kStack) {
-                    atomicOr(v.err, kErrTreeStack);
-                    continue;
-                }
-                // both children's records in one round; the nearer is searched first
-                int4 m0, m1;
-                const long long d0 = node_test<D>(db.nodes + rec_of(db, meta.y) * ns, dpb, x, ro.x, m0);
-                const long long d1 = node_test<D>(db.nodes + rec_of(db, meta.z) * ns, dpb, x, ro.x, m1);
-                if (d1 < d0) {
-                    if (!out_of_reach(d0, bestD)) { stack[sp] = meta.y; slb[sp++] = lb32(d0); }
-                    if (!out_of_reach(d1, bestD)) { stack[sp] = meta.z; slb[sp++] = lb32(d1); }
+                bool next = false;
+                if (cur < 0) {  // a cell: scan its points
+                    scan_leaf<D>(v, db, recb, ~cur, meta.y, meta.z, x, ro.x, bestD, bestJ, tests);
                 } else {
-                    if (!out_of_reach(d1, bestD)) { stack[sp] = meta.z; slb[sp++] = lb32(d1); }
-                    if (!out_of_reach(d0, bestD)) { stack[sp] = meta.y; slb[sp++] = lb32(d0); }
+                    // both children's records in one round; the nearer is searched first
+                    int4 m0, m1;
+                    const long long d0 = node_test<D>(db.nodes + rec_of(db, meta.y) * ns, dpb, x, ro.x, m0);
+                    const long long d1 = node_test<D>(db.nodes + rec_of(db, meta.z) * ns, dpb, x, ro.x, m1);
+                    const bool swap = d1 < d0;
+                    const long long dn = swap ? d1 : d0, df = swap ? d0 : d1;
+                    const int32_t nn = swap ? meta.z : meta.y, nf = swap ? meta.y : meta.z;
+                    if (!out_of_reach(df, bestD)) {
+                        if (sp < kStack) {
+                            stack[sp] = nf;
+                            slb[sp] = lb32(df);
+                            ++sp;
+                        } else {
+                            atomicOr(v.err, kErrTreeStack);
+                        }
+                    }
+                    if (!out_of_reach(dn, bestD)) {
+                        cur = nn;
+                        meta = swap ? m1 : m0;
+                        next = true;
+                    }
                 }
+                while (!next && sp > 0) {
+                    --sp;
+                    if ((long long)slb[sp] > bestD) continue;  // overtaken since it was stacked
+                    cur = stack[sp];
+                    // reload: its meta word, and a test against the best so far
+                    next = !out_of_reach(node_test<D>(db.nodes + rec_of(db, cur) * ns, dpb, x, ro.x, meta), bestD);
+                }
+                have = next;
             }
         }
         const int64_t g = ds.pt_off + ro.y;

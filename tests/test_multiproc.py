@@ -107,10 +107,28 @@ def test_e2e_roofline_model():
     import bench
     info = {"grid_key_bits": 30, "rank_key_bits": 23, "cand_pairs": 3_694_000_000}
     r = bench.e2e_roofline(5_800_000, 3, info, 5.1e12, 5.27e8)
-    # 3-d: 4 grid passes of 32-bit keys (20 B each), 3 rank passes
-    assert r["bytes_per_point"]["grid"] == 12 + 8 + 80 + 4 + 12 + 16 + 8
-    assert r["bytes_per_point"]["rank"] == 8 + 60 + 20
+    # 3-d: a histogram read of the 32-bit keys (4 B), then 4 grid passes
+    # (key and value read and written, 16 B each); 3 rank passes
+    assert r["bytes_per_point"]["grid"] == 12 + 8 + 4 + 64 + 4 + 12 + 16 + 8
+    assert r["bytes_per_point"]["rank"] == 8 + 4 + 48 + 20
     assert abs(r["stages_ms"]["rho_alu"] - 3.694e9 / 5.1e12 * 1e3) < 1e-9
     assert r["stages_ms"]["open_points"] == 0.0
     assert abs(r["points_per_s"] - 5_800_000 / (sum(r["stages_ms"].values()) / 1e3)) < 1e-3
     assert 0 < r["frac"] < 1
+
+
+def test_stage_rooflines_model():
+    sys.path.insert(0, ROOT)
+    import bench
+    info = {"grid_key_bits": 30, "rank_key_bits": 23, "cand_pairs": 3_694_000_000}
+    e2e = bench.e2e_roofline(5_800_000, 3, info, 5.1e12, 5.27e8)
+    stages = {"ms_grid": 1.5, "ms_rho": 1.85, "ms_rank": 0.3, "ms_ring": 2.6, "ms_rest": 2.4, "ms_label": 0.2}
+    work = {"cand_pairs": 3_694_000_000, "open_after_ring": 986_000, "tree_visits": 60_000_000}
+    r = bench.stage_rooflines(5_800_000, e2e, stages, work, 5.1e12, 4.0e12, "probe")
+    g = r["grid"]
+    assert g["bound"] == "hbm" and abs(g["achieved"] - 5_800_000 * g["bytes_per_point"] / 1.5e-3 / 1e9) < 1e-6
+    assert abs(g["frac"] - g["achieved"] / e2e["hbm_gbs"]) < 1e-12
+    assert abs(r["density"]["achieved"] - 3.694e9 / 1.85e-3 / 1e9) < 1e-6
+    assert abs(r["ring"]["frac"] - 3.694e9 / 2.6e-3 / 4.0e12) < 1e-12
+    assert abs(r["open_points"]["visits_per_s"] - 6e7 / 2.4e-3) < 1e-3
+    assert r["labels"]["bytes_per_point"] == 28
