@@ -97,9 +97,14 @@ __global__ void k_set_zero(uint32_t* p) { *p = 0u; }
 // a pass keeps the order and is a copy.
 
 constexpr int kRsThreads = 256;
-constexpr int kRsItems = 16;
-constexpr int kRsTile = kRsThreads * kRsItems;   // 4096 keys
 constexpr int kRsMaxPasses = 8;
+// keys per thread and per tile: 16 and 4096 for 32-bit keys, 8 and 2048 for
+// 64-bit keys (the tile's keys and values are staged in shared memory)
+template <typename K>
+constexpr int rs_items() { return sizeof(K) == 8 ? 8 : 16; }
+template <typename K>
+constexpr int rs_tile() { return kRsThreads * rs_items<K>(); }
+constexpr int kRsMinTile = kRsThreads * 8;
 
 // Global digit histograms of every pass, [pass][256].
 template <typename K>
@@ -131,6 +136,7 @@ __global__ void __launch_bounds__(kRsThreads) k_rs_up(const K* __restrict__ kin,
     __shared__ uint32_t h[256];
     h[threadIdx.x] = 0u;
     if (trivial_pass(hist, pass, n)) return;  // also orders the clear before the counts
+    constexpr int kRsItems = rs_items<K>(), kRsTile = rs_tile<K>();
     const int shift = 8 * pass;
     const int64_t base = (int64_t)blockIdx.x * kRsTile;
 #pragma unroll 4
@@ -143,14 +149,21 @@ __global__ void __launch_bounds__(kRsThreads) k_rs_up(const K* __restrict__ kin,
 }
 
 // Stable scatter of one tile: element order inside the tile is (warp, item,
-// lane), which is index order.
+// lane), which is index order. The tile's keys and values are first placed
+// in shared memory in digit order, then written out so that consecutive
+// threads write consecutive slots of a digit's run.
 template <typename K>
 __global__ void __launch_bounds__(kRsThreads) k_rs_down(const K* __restrict__ kin, const uint32_t* __restrict__ vin,
                                                          K* __restrict__ kout, uint32_t* __restrict__ vout, int64_t n,
                                                          int pass, const uint32_t* __restrict__ hist,
                                                          const uint32_t* __restrict__ offs, int64_t tiles) {
+    constexpr int kRsItems = rs_items<K>(), kRsTile = rs_tile<K>();
     __shared__ uint32_t wcnt[kRsThreads / 32][256];
-    __shared__ uint32_t sbase[256];
+    __shared__ uint32_t sbase[256];   // the digit's first global slot for this tile
+    __shared__ uint32_t tbase[256];   // the digit's first slot inside the tile
+    __shared__ uint32_t wsum[kRsThreads / 32];
+    __shared__ K skey[kRsTile];
+    __shared__ uint32_t sval[kRsTile];
     const int t = threadIdx.x, w = t >> 5, lane = t & 31;
     const unsigned lt = (1u << lane) - 1u;
 #pragma unroll
@@ -194,24 +207,43 @@ __global__ void __launch_bounds__(kRsThreads) k_rs_down(const K* __restrict__ ki
         rnk[i] = before + (uint32_t)__popc(peers[i] & lt);
     }
     __syncthreads();
-    // thread t = digit t: the warps' exclusive offsets
-    {
-        uint32_t run = 0;
+    // thread t = digit t: the warps' exclusive offsets, and the digit's first
+    // slot in the tile (an exclusive scan of the tile's counts over digits)
+    uint32_t cnt = 0;
 #pragma unroll
-        for (int ww = 0; ww < kRsThreads / 32; ++ww) {
-            const uint32_t c = wcnt[ww][t];
-            wcnt[ww][t] = run;
-            run += c;
-        }
+    for (int ww = 0; ww < kRsThreads / 32; ++ww) {
+        const uint32_t c = wcnt[ww][t];
+        wcnt[ww][t] = cnt;
+        cnt += c;
     }
+    uint32_t incl = cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
+    }
+    if (lane == 31) wsum[w] = incl;
+    __syncthreads();
+    uint32_t wo = 0;
+    for (int ww = 0; ww < w; ++ww) wo += wsum[ww];
+    tbase[t] = wo + incl - cnt;
     __syncthreads();
 #pragma unroll
     for (int i = 0; i < kRsItems; ++i) {
         if (dig[i] < 256u) {
-            const uint32_t pos = sbase[dig[i]] + wcnt[w][dig[i]] + rnk[i];
-            kout[pos] = key[i];
-            vout[pos] = val[i];
+            const uint32_t lp = tbase[dig[i]] + wcnt[w][dig[i]] + rnk[i];
+            skey[lp] = key[i];
+            sval[lp] = val[i];
         }
+    }
+    __syncthreads();
+    const int nvalid = (int)min((int64_t)kRsTile, n - tile0);
+    for (int j = t; j < nvalid; j += kRsThreads) {
+        const K k = skey[j];
+        const uint32_t d = (uint32_t)(k >> shift) & 255u;
+        const uint32_t pos = sbase[d] + (uint32_t)j - tbase[d];
+        kout[pos] = k;
+        vout[pos] = sval[j];
     }
 }
 
@@ -225,7 +257,7 @@ cudaError_t radix_sort_impl(const K* k_in, const uint32_t* v_in, K* k_out, uint3
         if (e != cudaSuccess) return e;
         return cudaMemcpyAsync(v_out, v_in, n * sizeof(uint32_t), cudaMemcpyDeviceToDevice, st);
     }
-    const int64_t tiles = ceil_div(n, kRsTile);
+    const int64_t tiles = ceil_div(n, rs_tile<K>());
     // temp: hist [8][256], counts [256][tiles], offsets [256][tiles], scan scratch
     uint32_t* hist = reinterpret_cast<uint32_t*>(temp);
     uint32_t* counts = hist + kRsMaxPasses * 256;
@@ -285,7 +317,7 @@ cudaError_t exclusive_scan_u32(const uint32_t* in, uint32_t* out, int64_t n, uin
 }
 
 size_t radix_sort_temp_bytes(int64_t n) {
-    const int64_t tiles = ceil_div(n > 0 ? n : 1, kRsTile);
+    const int64_t tiles = ceil_div(n > 0 ? n : 1, kRsMinTile);
     return kRsMaxPasses * 256 * sizeof(uint32_t) + 2 * align256(256 * tiles * sizeof(uint32_t)) +
            scan_temp_bytes(256 * tiles) + 256;
 }
