@@ -323,9 +323,9 @@ int64_t dpc_kernel_launches(void);
  * registers on every SM of `device`, i.e. the integer-ALU ceiling that the
  * density kernel is compared against, in the form dpc_ds_info reports as
  * pair_mode: 0 the direct 32-bit form (sum of squared differences), 1 the
- * direct 64-bit form, 2 the expanded 32-bit form around a cell corner
- * (d <= 3); and mode 3, the dependent-point ring search's pair test in the
- * expanded form (d <= 3: the same sum, a rank compare and the least packed
+ * direct 64-bit form, 2 the expanded 32-bit form (d <= 4); and mode 3, the
+ * dependent-point ring search's pair test in the expanded form (d <= 4: the
+ * same sum, a rank compare and the least packed
  * (distance, index) key kept), the ceiling of the ring kernel. Other modes
  * give DPC_ERR_INVALID_ARG. Writes pairs per
  * second (and the kernel's time in ms when ms is not NULL). Allocates and

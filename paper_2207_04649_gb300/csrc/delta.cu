@@ -116,8 +116,8 @@ __global__ void k_ro(BatchView v) {
 // exact because every candidate lies in the 3^k cells around the query's,
 // so 0 <= D < 4 d s^2 < 2^31).
 template <int D, int MODE, int Q>
-__device__ __forceinline__ void eval_ring(const int4* buf, const uint2* rbuf, int nb, int grp, int G,
-                                          const int32_t (&qx)[4][D], const uint32_t (&qa)[4][3],
+__device__ __forceinline__ void eval_ring(const int4* buf, const uint32_t* nrm, const uint2* rbuf, int nb, int grp,
+                                          int G, const int32_t (&qx)[4][D], const uint32_t (&qa)[4][4],
                                           const uint32_t (&qn)[4], const uint32_t (&qr)[4],
                                           unsigned long long (&best)[4]) {
     constexpr int DP = D <= 4 ? 1 : 2;
@@ -126,12 +126,14 @@ __device__ __forceinline__ void eval_ring(const int4* buf, const uint2* rbuf, in
         const uint2 ro = rbuf[j];
         if (MODE == 2) {
             const int4 c = buf[j];
+            const uint32_t cn = D == 4 ? nrm[j] : (uint32_t)c.w;  // 4 dims: staged beside the record
 #pragma unroll
             for (int t = 0; t < Q; ++t) {
-                uint32_t s = (uint32_t)c.w + qn[t];
+                uint32_t s = cn + qn[t];
                 s += (uint32_t)c.x * qa[t][0];
                 if (D > 1) s += (uint32_t)c.y * qa[t][1];
                 if (D > 2) s += (uint32_t)c.z * qa[t][2];
+                if (D > 3) s += (uint32_t)c.w * qa[t][3];
                 const unsigned long long key = ((unsigned long long)s << 32) | ro.y;
                 if (ro.x < qr[t] && key < best[t]) best[t] = key;
             }
@@ -153,6 +155,7 @@ __global__ void __launch_bounds__(kRingThreads) k_ring_dense(BatchView v, CellWo
     constexpr int DP = D <= 4 ? 1 : 2;
     constexpr bool EXP = MODE == 2;
     __shared__ int4 sbuf[kRingThreads / 32][2][kChunk * DP];
+    __shared__ uint32_t snrm[kRingThreads / 32][2][EXP && D == 4 ? kChunk : 1];  // 4-d expanded form: |c|^2
     __shared__ uint2 srb[kRingThreads / 32][2][kChunk];
     __shared__ uint2 sruns[kRingThreads / 32][kMaxNb];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -187,13 +190,13 @@ __global__ void __launch_bounds__(kRingThreads) k_ring_dense(BatchView v, CellWo
             qr[t] = v.ro_s[cs + q0 + qi].x;
             best[t] = kNoBest;
         }
-        uint32_t qa[4][3], qn[4];
+        uint32_t qa[4][4], qn[4];
         if (EXP) {
 #pragma unroll
             for (int t = 0; t < 4; ++t) {
                 uint32_t nrm = 0u;
 #pragma unroll
-                for (int k = 0; k < 3; ++k) {
+                for (int k = 0; k < 4; ++k) {
                     const uint32_t x = k < D ? (uint32_t)qx[t][k < D ? k : 0] : 0u;
                     qa[t][k] = 0u - 2u * x;
                     nrm += x * x;
@@ -217,6 +220,7 @@ __global__ void __launch_bounds__(kRingThreads) k_ring_dense(BatchView v, CellWo
         int sb = 0;
         while (have) {
             int4* buf = sbuf[wid][sb];
+            uint32_t* nbuf = snrm[wid][EXP && D == 4 ? sb : 0];
             uint2* rbuf = srb[wid][sb];
             const int nb = (int)cst.cnt;
 #pragma unroll
@@ -225,6 +229,11 @@ __global__ void __launch_bounds__(kRingThreads) k_ring_dense(BatchView v, CellWo
                 if (f < nb) {
 #pragma unroll
                     for (int q = 0; q < DP; ++q) buf[f * DP + q] = cst.r[u][q];
+                    if (EXP && D == 4) {
+                        const int4 r = cst.r[u][0];
+                        nbuf[f] = (uint32_t)r.x * (uint32_t)r.x + (uint32_t)r.y * (uint32_t)r.y +
+                                  (uint32_t)r.z * (uint32_t)r.z + (uint32_t)r.w * (uint32_t)r.w;
+                    }
                     rbuf[f] = cst.ro[u];
                 }
             }
@@ -232,10 +241,10 @@ __global__ void __launch_bounds__(kRingThreads) k_ring_dense(BatchView v, CellWo
             have = cst.prep(lane, recb, v.ro_s, &bad);
             sb ^= 1;
             switch (Q) {
-                case 1: eval_ring<D, MODE, 1>(buf, rbuf, nb, grp, G, qx, qa, qn, qr, best); break;
-                case 2: eval_ring<D, MODE, 2>(buf, rbuf, nb, grp, G, qx, qa, qn, qr, best); break;
-                case 3: eval_ring<D, MODE, 3>(buf, rbuf, nb, grp, G, qx, qa, qn, qr, best); break;
-                default: eval_ring<D, MODE, 4>(buf, rbuf, nb, grp, G, qx, qa, qn, qr, best); break;
+                case 1: eval_ring<D, MODE, 1>(buf, nbuf, rbuf, nb, grp, G, qx, qa, qn, qr, best); break;
+                case 2: eval_ring<D, MODE, 2>(buf, nbuf, rbuf, nb, grp, G, qx, qa, qn, qr, best); break;
+                case 3: eval_ring<D, MODE, 3>(buf, nbuf, rbuf, nb, grp, G, qx, qa, qn, qr, best); break;
+                default: eval_ring<D, MODE, 4>(buf, nbuf, rbuf, nb, grp, G, qx, qa, qn, qr, best); break;
             }
         }
         if (bad && lane == 0) atomicOr(v.err, kErrStaging);
@@ -255,47 +264,73 @@ __global__ void __launch_bounds__(kRingThreads) k_ring_dense(BatchView v, CellWo
     }
 }
 
+// Sparse cells: kRingSparseLanes lanes per cell, each with all of the
+// cell's queries, take every kRingSparseLanes-th candidate of each run; the
+// least keys are combined with warp shuffles (the cell loop is warp-uniform).
+constexpr int kRingSparseLanes = 4;
+
 template <int D, bool W64>
 __global__ void __launch_bounds__(256) k_ring_sparse(BatchView v, CellWork w) {
     constexpr int DP = D <= 4 ? 1 : 2;
+    constexpr int G = kRingSparseLanes, CPW = 32 / G;
     const uint32_t ns = *w.nsparse;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < ns; i += (int64_t)gridDim.x * blockDim.x) {
-        const uint32_t c = w.sparse[i];
-        const uint32_t cs = v.cell_start[c], m = v.cell_start[c + 1] - cs;
-        const int b = find_ds(v.pt_off, v.B, cs);
-        const DsDesc& ds = v.desc[b];
-        if (ds.d != D || (ds.w32 == 0) != W64) continue;
-        const int4* recb = v.rec + ds.rec_off - ds.pt_off * DP;
-        int32_t qx[kSparseMax][D];
-        uint32_t qr[kSparseMax];
+    const int lane = threadIdx.x & 31, sl = lane & (G - 1), grp = lane / G;
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t base = warp * CPW; base < ns; base += nwarps * CPW) {
+        const int64_t i = base + grp;
         unsigned long long best[kSparseMax];
 #pragma unroll
-        for (int t = 0; t < kSparseMax; ++t) {
-            const uint32_t qi = min((uint32_t)t, m - 1);
-            load_pt<D>(recb + ((int64_t)cs + qi) * DP, qx[t]);
-            qr[t] = v.ro_s[cs + qi].x;
-            best[t] = kNoBest;
-        }
-        const uint2* runs = w.runs + (int64_t)c * w.nbs;
-        const uint32_t nr = w.nruns[c];
-        for (uint32_t r = 0; r < nr; ++r) {
-            const uint2 e = runs[r];
-#pragma unroll 2
-            for (uint32_t j = 0; j < e.y; ++j) {
-                int32_t cj[D];
-                load_pt<D>(recb + ((int64_t)e.x + j) * DP, cj);
-                const uint2 ro = v.ro_s[e.x + j];
+        for (int t = 0; t < kSparseMax; ++t) best[t] = kNoBest;
+        uint32_t cs = 0, m = 0;
+        bool mine = false;
+        if (i < ns) {
+            const uint32_t c = w.sparse[i];
+            cs = v.cell_start[c];
+            m = v.cell_start[c + 1] - cs;
+            const DsDesc& ds = v.desc[find_ds(v.pt_off, v.B, cs)];
+            mine = ds.d == D && (ds.w32 == 0) == W64;
+            if (mine) {
+                const int4* recb = v.rec + ds.rec_off - ds.pt_off * DP;
+                int32_t qx[kSparseMax][D];
+                uint32_t qr[kSparseMax];
 #pragma unroll
-                for (int q = 0; q < kSparseMax; ++q) {
-                    const uint32_t dd = dist_sat<D, W64>(qx[q], cj);
-                    const unsigned long long key = ((unsigned long long)dd << 32) | ro.y;
-                    if (ro.x < qr[q] && key < best[q]) best[q] = key;
+                for (int t = 0; t < kSparseMax; ++t) {
+                    const uint32_t qi = min((uint32_t)t, m - 1);
+                    load_pt<D>(recb + ((int64_t)cs + qi) * DP, qx[t]);
+                    qr[t] = v.ro_s[cs + qi].x;
+                }
+                const uint2* runs = w.runs + (int64_t)c * w.nbs;
+                const uint32_t nr = w.nruns[c];
+                for (uint32_t r = 0; r < nr; ++r) {
+                    const uint2 e = runs[r];
+#pragma unroll 2
+                    for (uint32_t j = sl; j < e.y; j += G) {
+                        int32_t cj[D];
+                        load_pt<D>(recb + ((int64_t)e.x + j) * DP, cj);
+                        const uint2 ro = v.ro_s[e.x + j];
+#pragma unroll
+                        for (int q = 0; q < kSparseMax; ++q) {
+                            const uint32_t dd = dist_sat<D, W64>(qx[q], cj);
+                            const unsigned long long key = ((unsigned long long)dd << 32) | ro.y;
+                            if (ro.x < qr[q] && key < best[q]) best[q] = key;
+                        }
+                    }
                 }
             }
         }
 #pragma unroll
         for (int q = 0; q < kSparseMax; ++q)
-            if ((uint32_t)q < m) v.best_s[cs + q] = best[q];
+#pragma unroll
+            for (int o = 1; o < G; o <<= 1) {
+                const unsigned long long y = __shfl_xor_sync(0xffffffffu, best[q], o);
+                if (y < best[q]) best[q] = y;
+            }
+        if (mine && sl == 0) {
+#pragma unroll
+            for (int q = 0; q < kSparseMax; ++q)
+                if ((uint32_t)q < m) v.best_s[cs + q] = best[q];
+        }
     }
 }
 
@@ -528,7 +563,7 @@ void launch_ring_dense(const BatchView& v, const CellWork& w, int64_t nitems_bou
 template <int D, bool W64>
 void launch_ring_sparse(const BatchView& v, const CellWork& w, int64_t nsparse_bound, cudaStream_t st) {
     if (nsparse_bound <= 0) return;
-    const unsigned blocks = (unsigned)std::min<int64_t>(152 * 32, grid_for(nsparse_bound, 256));
+    const unsigned blocks = (unsigned)std::min<int64_t>(152 * 32, grid_for(nsparse_bound * kRingSparseLanes, 256));
     (k_ring_sparse<D, W64><<<blocks, 256, 0, st>>>(v, w), note_launch());
 }
 
@@ -575,7 +610,7 @@ cudaError_t launch_ring(const BatchView& v, const CellWork& w, uint32_t class_ma
     if (DPC_BIT(D, 2)) launch_ring_dense<D, 2>(v, w, nitems_bound, counters + 3 * (D - 1) + 2, st);
     DPC_RING_CLASS(1) DPC_RING_CLASS(2) DPC_RING_CLASS(3) DPC_RING_CLASS(4)
     DPC_RING_CLASS(5) DPC_RING_CLASS(6) DPC_RING_CLASS(7) DPC_RING_CLASS(8)
-    DPC_RING_X(1) DPC_RING_X(2) DPC_RING_X(3)
+    DPC_RING_X(1) DPC_RING_X(2) DPC_RING_X(3) DPC_RING_X(4)
 #undef DPC_RING_X
 #undef DPC_RING_CLASS
 #undef DPC_BIT

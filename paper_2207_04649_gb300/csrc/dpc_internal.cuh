@@ -44,7 +44,7 @@ struct DsDesc {
     int32_t R;            // neighbour reach in cells
     int32_t w32;          // all candidate pair sums fit 31 bits
     int32_t mode;         // density pair test: 0 direct 32-bit, 1 direct 64-bit,
-                          // 2 expanded 32-bit around the query cell's corner (d <= 3)
+                          // 2 expanded 32-bit, |c|^2 + |q|^2 - T - 2 q.c wrapping mod 2^32 (d <= 4)
     int32_t lo[kMaxDims]; // smallest coordinate per dim
     int32_t h;            // point tree height: 2^h leaf slots
     int32_t nleaf;        // point tree leaves (ceil(n / kLeaf))

@@ -137,8 +137,9 @@ __global__ void k_gather(BatchView v, const K* __restrict__ skeys, uint32_t* __r
 #pragma unroll
     for (int k = 0; k < 8; ++k) c[k] = k < ds.d ? x[k] : 0;
     int4* r = v.rec + ds.rec_off + (p - ds.pt_off) * ds.dp;
-    // the expanded pair form (d <= 3) keeps |x|^2 mod 2^32 in the w lane
-    if (ds.mode == 2)
+    // the expanded pair form keeps |x|^2 mod 2^32 in the w lane for d <= 3
+    // (4-d records have no spare lane: the kernels compute it when staging)
+    if (ds.mode == 2 && ds.d <= 3)
         c[3] = (int32_t)((uint32_t)c[0] * (uint32_t)c[0] + (uint32_t)c[1] * (uint32_t)c[1] +
                          (uint32_t)c[2] * (uint32_t)c[2]);
     r[0] = make_int4(c[0], c[1], c[2], c[3]);

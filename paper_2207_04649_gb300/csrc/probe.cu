@@ -5,7 +5,8 @@
 // of the kernel's three forms:
 //   direct   (mode 0): sign of sum_k (q_k - c_k)^2 - d_cut^2 in 32 bits;
 //   direct   (mode 1): sum_k (q_k - c_k)^2 < d_cut^2 in 64 bits;
-//   expanded (mode 2, d <= 3): sign of |c'|^2 + (|q'|^2 - d_cut^2) + sum_k c'_k (-2 q'_k).
+//   expanded (mode 2, d <= 4): sign of |c|^2 + (|q|^2 - d_cut^2) + sum_k c_k (-2 q_k)
+//                              in wrapping 32-bit arithmetic (|c|^2 beside the record in 4 dims).
 // After each sweep every query operand moves by an amount that depends on
 // the counts, so no part of a pair test can be hoisted out of the loop (this
 // costs d + 1 adds per query per 16 pairs, charged to the probe). The rate it
@@ -65,42 +66,48 @@ __global__ void __launch_bounds__(256) k_pair_probe(const int32_t* __restrict__ 
 template <int D>
 __global__ void __launch_bounds__(256) k_pair_probe_x(const int32_t* __restrict__ seed, int iters, int T,
                                                      unsigned long long* __restrict__ sink) {
-    int32_t qa[4][3], qb[4];
+    uint32_t qa[4][4], qb[4];
     int4 c[16];
+    uint32_t cn[16];
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
-        int32_t n = -T;
+        uint32_t n = 0u - (uint32_t)T;
 #pragma unroll
-        for (int k = 0; k < 3; ++k) {
-            const int32_t x = k < D ? seed[(t * 7 + i * 3 + k) & 1023] : 0;
-            qa[i][k] = -2 * x;
+        for (int k = 0; k < 4; ++k) {
+            const uint32_t x = k < D ? (uint32_t)seed[(t * 7 + i * 4 + k) & 1023] : 0u;
+            qa[i][k] = 0u - 2u * x;
             n += x * x;
         }
         qb[i] = n;
     }
 #pragma unroll
     for (int j = 0; j < 16; ++j) {
-        const int32_t x = seed[(t * 13 + j * 3 + 512) & 1023];
-        const int32_t y = D > 1 ? seed[(t * 13 + j * 3 + 513) & 1023] : 0;
-        const int32_t z = D > 2 ? seed[(t * 13 + j * 3 + 514) & 1023] : 0;
-        c[j] = make_int4(x, y, z, x * x + y * y + z * z);
+        const int32_t x = seed[(t * 13 + j * 4 + 512) & 1023];
+        const int32_t y = D > 1 ? seed[(t * 13 + j * 4 + 513) & 1023] : 0;
+        const int32_t z = D > 2 ? seed[(t * 13 + j * 4 + 514) & 1023] : 0;
+        const int32_t u = D > 3 ? seed[(t * 13 + j * 4 + 515) & 1023] : 0;
+        cn[j] = (uint32_t)(x * x + y * y + z * z + u * u);
+        c[j] = make_int4(x, y, z, D > 3 ? u : (int32_t)cn[j]);
     }
     uint32_t cnt[4] = {0u, 0u, 0u, 0u};
     for (int it = 0; it < iters; ++it) {
 #pragma unroll
-        for (int j = 0; j < 16; ++j)
+        for (int j = 0; j < 16; ++j) {
+            const uint32_t nj = D == 4 ? cn[j] : (uint32_t)c[j].w;
 #pragma unroll
             for (int i = 0; i < 4; ++i) {
-                int s = c[j].w + qb[i];
-                s += c[j].x * qa[i][0];
-                if (D > 1) s += c[j].y * qa[i][1];
-                if (D > 2) s += c[j].z * qa[i][2];
-                cnt[i] += (uint32_t)s >> 31;
+                uint32_t s = nj + qb[i];
+                s += (uint32_t)c[j].x * qa[i][0];
+                if (D > 1) s += (uint32_t)c[j].y * qa[i][1];
+                if (D > 2) s += (uint32_t)c[j].z * qa[i][2];
+                if (D > 3) s += (uint32_t)c[j].w * qa[i][3];
+                cnt[i] += s >> 31;
             }
+        }
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
-            const int32_t m = (int32_t)(cnt[i] & 1u);
+            const uint32_t m = cnt[i] & 1u;
             qb[i] += m;
 #pragma unroll
             for (int k = 0; k < D; ++k) qa[i][k] += m;
@@ -118,18 +125,19 @@ __global__ void __launch_bounds__(256) k_pair_probe_x(const int32_t* __restrict_
 template <int D>
 __global__ void __launch_bounds__(256) k_ring_probe_x(const int32_t* __restrict__ seed, int iters,
                                                      unsigned long long* __restrict__ sink) {
-    int32_t qa[4][3], qn[4];
+    uint32_t qa[4][4], qn[4];
     uint32_t qr[4];
     int4 c[16];
+    uint32_t cn[16];
     uint2 ro[16];
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
-        int32_t n = 0;
+        uint32_t n = 0u;
 #pragma unroll
-        for (int k = 0; k < 3; ++k) {
-            const int32_t x = k < D ? seed[(t * 7 + i * 3 + k) & 1023] : 0;
-            qa[i][k] = -2 * x;
+        for (int k = 0; k < 4; ++k) {
+            const uint32_t x = k < D ? (uint32_t)seed[(t * 7 + i * 4 + k) & 1023] : 0u;
+            qa[i][k] = 0u - 2u * x;
             n += x * x;
         }
         qn[i] = n;
@@ -137,30 +145,35 @@ __global__ void __launch_bounds__(256) k_ring_probe_x(const int32_t* __restrict_
     }
 #pragma unroll
     for (int j = 0; j < 16; ++j) {
-        const int32_t x = seed[(t * 13 + j * 3 + 512) & 1023];
-        const int32_t y = D > 1 ? seed[(t * 13 + j * 3 + 513) & 1023] : 0;
-        const int32_t z = D > 2 ? seed[(t * 13 + j * 3 + 514) & 1023] : 0;
-        c[j] = make_int4(x, y, z, x * x + y * y + z * z);
+        const int32_t x = seed[(t * 13 + j * 4 + 512) & 1023];
+        const int32_t y = D > 1 ? seed[(t * 13 + j * 4 + 513) & 1023] : 0;
+        const int32_t z = D > 2 ? seed[(t * 13 + j * 4 + 514) & 1023] : 0;
+        const int32_t u = D > 3 ? seed[(t * 13 + j * 4 + 515) & 1023] : 0;
+        cn[j] = (uint32_t)(x * x + y * y + z * z + u * u);
+        c[j] = make_int4(x, y, z, D > 3 ? u : (int32_t)cn[j]);
         ro[j] = make_uint2((uint32_t)seed[(t * 11 + j) & 1023] * 7u, (uint32_t)(t * 16 + j));
     }
     unsigned long long best[4] = {~0ull, ~0ull, ~0ull, ~0ull};
     for (int it = 0; it < iters; ++it) {
 #pragma unroll
-        for (int j = 0; j < 16; ++j)
+        for (int j = 0; j < 16; ++j) {
+            const uint32_t nj = D == 4 ? cn[j] : (uint32_t)c[j].w;
 #pragma unroll
             for (int i = 0; i < 4; ++i) {
-                int s = c[j].w + qn[i];
-                s += c[j].x * qa[i][0];
-                if (D > 1) s += c[j].y * qa[i][1];
-                if (D > 2) s += c[j].z * qa[i][2];
-                const unsigned long long key = ((unsigned long long)(uint32_t)s << 32) | ro[j].y;
+                uint32_t s = nj + qn[i];
+                s += (uint32_t)c[j].x * qa[i][0];
+                if (D > 1) s += (uint32_t)c[j].y * qa[i][1];
+                if (D > 2) s += (uint32_t)c[j].z * qa[i][2];
+                if (D > 3) s += (uint32_t)c[j].w * qa[i][3];
+                const unsigned long long key = ((unsigned long long)s << 32) | ro[j].y;
                 if (ro[j].x < qr[i] && key < best[i]) best[i] = key;
             }
+        }
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
-            const int32_t m = (int32_t)(best[i] & 1ull);
+            const uint32_t m = (uint32_t)(best[i] & 1ull);
             qn[i] += m;
-            qr[i] += (uint32_t)m;
+            qr[i] += m;
 #pragma unroll
             for (int k = 0; k < D; ++k) qa[i][k] += m;
         }
@@ -173,7 +186,7 @@ __global__ void __launch_bounds__(256) k_ring_probe_x(const int32_t* __restrict_
 
 extern "C" dpc_status dpc_probe_pair_rate(int device, int d, int mode, double* pairs_per_s, double* ms) {
     using namespace dpc;
-    if (!pairs_per_s || d < 1 || d > 8 || mode < 0 || mode > 3 || (mode >= 2 && d > 3))
+    if (!pairs_per_s || d < 1 || d > 8 || mode < 0 || mode > 3 || (mode >= 2 && d > 4))
         return DPC_ERR_INVALID_ARG;
     if (cudaSetDevice(device) != cudaSuccess) return DPC_ERR_CUDA;
     int sms = 0;
@@ -197,13 +210,15 @@ extern "C" dpc_status dpc_probe_pair_rate(int device, int d, int mode, double* p
             switch (d) {
                 case 1: k_ring_probe_x<1><<<blocks, threads>>>(seed, it, sink); break;
                 case 2: k_ring_probe_x<2><<<blocks, threads>>>(seed, it, sink); break;
-                default: k_ring_probe_x<3><<<blocks, threads>>>(seed, it, sink); break;
+                case 3: k_ring_probe_x<3><<<blocks, threads>>>(seed, it, sink); break;
+                default: k_ring_probe_x<4><<<blocks, threads>>>(seed, it, sink); break;
             }
         } else if (mode == 2) {
             switch (d) {
                 case 1: k_pair_probe_x<1><<<blocks, threads>>>(seed, it, 90000, sink); break;
                 case 2: k_pair_probe_x<2><<<blocks, threads>>>(seed, it, 90000, sink); break;
-                default: k_pair_probe_x<3><<<blocks, threads>>>(seed, it, 90000, sink); break;
+                case 3: k_pair_probe_x<3><<<blocks, threads>>>(seed, it, 90000, sink); break;
+                default: k_pair_probe_x<4><<<blocks, threads>>>(seed, it, 90000, sink); break;
             }
         } else if (mode == 1) {
             switch (d) {

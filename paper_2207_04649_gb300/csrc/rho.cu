@@ -387,18 +387,22 @@ __device__ __forceinline__ void eval_rho(const int4* buf, int nb, int grp, int G
 // from the 3^k cells around the query's, so |q - c|^2 < 4 d s^2 <= 2^31 (the
 // form is chosen only when 9 d s^2 < 2^31): the true value lies in
 // [-2^31, 2^31), and the sign bit of the wrapped sum is the pair test.
+// In 4 dims the record's spare lane is taken: |c|^2 is computed when the
+// candidate is staged and kept beside it (nrm).
 template <int D, int Q>
-__device__ __forceinline__ void eval_rho_x(const int4* buf, int nb, int grp, int G, const uint32_t (&qa)[4][3],
-                                           const uint32_t (&qb)[4], uint32_t (&cnt)[4]) {
+__device__ __forceinline__ void eval_rho_x(const int4* buf, const uint32_t* nrm, int nb, int grp, int G,
+                                           const uint32_t (&qa)[4][4], const uint32_t (&qb)[4], uint32_t (&cnt)[4]) {
 #pragma unroll 4
     for (int j = grp; j < nb; j += G) {
         const int4 c = buf[j];
+        const uint32_t cn = D == 4 ? nrm[j] : (uint32_t)c.w;
 #pragma unroll
         for (int t = 0; t < Q; ++t) {
-            uint32_t s = (uint32_t)c.w + qb[t];
+            uint32_t s = cn + qb[t];
             s += (uint32_t)c.x * qa[t][0];
             if (D > 1) s += (uint32_t)c.y * qa[t][1];
             if (D > 2) s += (uint32_t)c.z * qa[t][2];
+            if (D > 3) s += (uint32_t)c.w * qa[t][3];
             cnt[t] += s >> 31;
         }
     }
@@ -406,15 +410,21 @@ __device__ __forceinline__ void eval_rho_x(const int4* buf, int nb, int grp, int
 
 // The expanded form's query terms: a_k = -2 q_k, b = |q|^2 - T (mod 2^32).
 template <int D>
-__device__ __forceinline__ void expand_query(const int32_t (&q)[D], uint32_t T, uint32_t (&a)[3], uint32_t& b) {
+__device__ __forceinline__ void expand_query(const int32_t (&q)[D], uint32_t T, uint32_t (&a)[4], uint32_t& b) {
     uint32_t n = 0u - T;
 #pragma unroll
-    for (int k = 0; k < 3; ++k) {
+    for (int k = 0; k < 4; ++k) {
         const uint32_t x = k < D ? (uint32_t)q[k < D ? k : 0] : 0u;
         a[k] = 0u - 2u * x;
         n += x * x;
     }
     b = n;
+}
+
+// |c|^2 mod 2^32 of a 4-d record (the expanded form's candidate norm).
+__device__ __forceinline__ uint32_t norm4(const int4 r) {
+    return (uint32_t)r.x * (uint32_t)r.x + (uint32_t)r.y * (uint32_t)r.y + (uint32_t)r.z * (uint32_t)r.z +
+           (uint32_t)r.w * (uint32_t)r.w;
 }
 
 
@@ -430,6 +440,7 @@ __global__ void __launch_bounds__(kRhoThreads) k_rho_dense(BatchView v, CellWork
     constexpr bool W64 = MODE == 1;
     constexpr bool EXP = MODE == 2;
     __shared__ int4 sbuf[kRhoThreads / 32][2][kChunk * DP];  // double buffer per warp
+    __shared__ uint32_t snrm[kRhoThreads / 32][2][EXP && D == 4 ? kChunk : 1];  // 4-d expanded form: |c|^2
     __shared__ uint2 sruns[kRhoThreads / 32][kMaxNb];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     uint2* srun = sruns[wid];
@@ -495,7 +506,7 @@ __global__ void __launch_bounds__(kRhoThreads) k_rho_dense(BatchView v, CellWork
             load_point<D>(recb + (int64_t)(QL ? qpos[t] : cs + i) * DP, qx[t]);
         }
         // expanded form: the queries' terms (the records carry |c|^2)
-        uint32_t qa[4][3], qb[4];
+        uint32_t qa[4][4], qb[4];
         if (EXP) {
 #pragma unroll
             for (int t = 0; t < 4; ++t) expand_query<D>(qx[t], (uint32_t)ds.d_cut2, qa[t], qb[t]);
@@ -521,6 +532,7 @@ __global__ void __launch_bounds__(kRhoThreads) k_rho_dense(BatchView v, CellWork
             // store the loaded chunk (relative to the cell corner in the
             // expanded form), then put the next chunk's loads in flight
             int4* buf = sbuf[wid][sb];
+            uint32_t* nbuf = snrm[wid][EXP && D == 4 ? sb : 0];
             const int nb = (int)cst.cnt;
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
@@ -528,6 +540,7 @@ __global__ void __launch_bounds__(kRhoThreads) k_rho_dense(BatchView v, CellWork
                 if (f < nb) {
 #pragma unroll
                     for (int q = 0; q < DP; ++q) buf[f * DP + q] = cst.r[u][q];
+                    if (EXP && D == 4) nbuf[f] = norm4(cst.r[u][0]);
                 }
             }
             __syncwarp();
@@ -536,10 +549,10 @@ __global__ void __launch_bounds__(kRhoThreads) k_rho_dense(BatchView v, CellWork
             if (pf < 3) stage(pf++);
             if (EXP) {
                 switch (Q) {
-                    case 1: eval_rho_x<D, 1>(buf, nb, grp, G, qa, qb, cnt); break;
-                    case 2: eval_rho_x<D, 2>(buf, nb, grp, G, qa, qb, cnt); break;
-                    case 3: eval_rho_x<D, 3>(buf, nb, grp, G, qa, qb, cnt); break;
-                    default: eval_rho_x<D, 4>(buf, nb, grp, G, qa, qb, cnt); break;
+                    case 1: eval_rho_x<D, 1>(buf, nbuf, nb, grp, G, qa, qb, cnt); break;
+                    case 2: eval_rho_x<D, 2>(buf, nbuf, nb, grp, G, qa, qb, cnt); break;
+                    case 3: eval_rho_x<D, 3>(buf, nbuf, nb, grp, G, qa, qb, cnt); break;
+                    default: eval_rho_x<D, 4>(buf, nbuf, nb, grp, G, qa, qb, cnt); break;
                 }
             } else {
                 switch (Q) {
@@ -705,7 +718,7 @@ struct BulkWalk {
 
 template <int D, int MODE>
 __global__ void __launch_bounds__(kRhoThreads) k_rho_dense_bulk(BatchView v, CellWork w, uint32_t* counter) {
-    static_assert(D <= 4 && (MODE == 0 || MODE == 2), "one int4 per record, 32-bit forms");
+    static_assert(D <= 4 && (MODE == 0 || (MODE == 2 && D <= 3)), "one int4 per record, 32-bit forms");
     constexpr bool EXP = MODE == 2;
     __shared__ __align__(128) int4 sbuf[kRhoThreads / 32][2][kChunk];  // double buffer per warp
     __shared__ uint2 sruns[kRhoThreads / 32][kMaxNb];
@@ -769,7 +782,7 @@ __global__ void __launch_bounds__(kRhoThreads) k_rho_dense_bulk(BatchView v, Cel
         int32_t qx[4][D];
 #pragma unroll
         for (int t = 0; t < 4; ++t) load_point<D>(recb + ((int64_t)cs + q0 + min(ql * Q + t, nq - 1)), qx[t]);
-        uint32_t qa[4][3], qb[4];
+        uint32_t qa[4][4], qb[4];
         if (EXP) {
 #pragma unroll
             for (int t = 0; t < 4; ++t) expand_query<D>(qx[t], (uint32_t)ds.d_cut2, qa[t], qb[t]);
@@ -801,14 +814,15 @@ __global__ void __launch_bounds__(kRhoThreads) k_rho_dense_bulk(BatchView v, Cel
                 break;
             }
             int4* buf = sbuf[wid][sb];
+            const uint32_t* nbuf = nullptr;  // the norm is the record's w lane (d <= 3)
             const int nb = (int)cur;
             if (pf < 3) stage(pf++);
             if (EXP) {
                 switch (Q) {
-                    case 1: eval_rho_x<D, 1>(buf, nb, grp, G, qa, qb, cnt); break;
-                    case 2: eval_rho_x<D, 2>(buf, nb, grp, G, qa, qb, cnt); break;
-                    case 3: eval_rho_x<D, 3>(buf, nb, grp, G, qa, qb, cnt); break;
-                    default: eval_rho_x<D, 4>(buf, nb, grp, G, qa, qb, cnt); break;
+                    case 1: eval_rho_x<D, 1>(buf, nbuf, nb, grp, G, qa, qb, cnt); break;
+                    case 2: eval_rho_x<D, 2>(buf, nbuf, nb, grp, G, qa, qb, cnt); break;
+                    case 3: eval_rho_x<D, 3>(buf, nbuf, nb, grp, G, qa, qb, cnt); break;
+                    default: eval_rho_x<D, 4>(buf, nbuf, nb, grp, G, qa, qb, cnt); break;
                 }
             } else {
                 switch (Q) {
@@ -839,42 +853,65 @@ __global__ void __launch_bounds__(kRhoThreads) k_rho_dense_bulk(BatchView v, Cel
     }
 }
 
+// Sparse cells (at most kSparseMax points, few candidates): kSparseLanes
+// lanes per cell, each with all of the cell's queries, take every
+// kSparseLanes-th candidate of each run; their counts are added with warp
+// shuffles. (One thread per cell left most lanes of a warp idle: cells in a
+// warp have very different candidate counts.) The loop over cells is
+// warp-uniform, so that every lane reaches the shuffles.
+constexpr int kSparseLanes = 4;
+
 template <int D, bool W64>
 __global__ void __launch_bounds__(256) k_rho_sparse(BatchView v, CellWork w) {
     constexpr int DP = D <= 4 ? 1 : 2;
+    constexpr int G = kSparseLanes, CPW = 32 / G;  // lanes per cell, cells per warp
     const uint32_t ns = *w.nsparse;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < ns; i += (int64_t)gridDim.x * blockDim.x) {
-        const uint32_t c = w.sparse[i];
-        const uint32_t cs = v.cell_start[c], m = v.cell_start[c + 1] - cs;
-        const int b = find_ds(v.pt_off, v.B, cs);
-        const DsDesc& ds = v.desc[b];
-        if (ds.d != D || (ds.w32 == 0) != W64) continue;
-        const int4* recb = v.rec + ds.rec_off - ds.pt_off * DP;
-        int32_t qx[kSparseMax][D];
+    const int lane = threadIdx.x & 31, sl = lane & (G - 1), grp = lane / G;
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t base = warp * CPW; base < ns; base += nwarps * CPW) {
+        const int64_t i = base + grp;
+        uint32_t cnt[kSparseMax] = {0u, 0u, 0u, 0u};
+        uint32_t cs = 0, m = 0;
+        bool mine = false;
+        if (i < ns) {
+            const uint32_t c = w.sparse[i];
+            cs = v.cell_start[c];
+            m = v.cell_start[c + 1] - cs;
+            const DsDesc& ds = v.desc[find_ds(v.pt_off, v.B, cs)];
+            mine = ds.d == D && (ds.w32 == 0) == W64;
+            if (mine) {
+                const int4* recb = v.rec + ds.rec_off - ds.pt_off * DP;
+                int32_t qx[kSparseMax][D];
 #pragma unroll
-        for (int t = 0; t < kSparseMax; ++t) load_point<D>(recb + ((int64_t)cs + min((uint32_t)t, m - 1)) * DP, qx[t]);
-        uint32_t cnt[kSparseMax];
+                for (int t = 0; t < kSparseMax; ++t)
+                    load_point<D>(recb + ((int64_t)cs + min((uint32_t)t, m - 1)) * DP, qx[t]);
+                const int64_t T = ds.d_cut2;
+                const uint2* runs = w.runs + (int64_t)c * w.nbs;
+                const uint32_t nr = w.nruns[c];
+                for (uint32_t r = 0; r < nr; ++r) {
+                    const uint2 e = runs[r];
+#pragma unroll 2
+                    for (uint32_t j = sl; j < e.y; j += G) {
+                        int32_t cj[D];
+                        load_point<D>(recb + ((int64_t)e.x + j) * DP, cj);
 #pragma unroll
-        for (int t = 0; t < kSparseMax; ++t) cnt[t] = 0u;
-        const int64_t T = ds.d_cut2;
-        const uint2* runs = w.runs + (int64_t)c * w.nbs;
-        const uint32_t nr = w.nruns[c];
-        for (uint32_t r = 0; r < nr; ++r) {
-            const uint2 e = runs[r];
-#pragma unroll 4
-            for (uint32_t j = 0; j < e.y; ++j) {
-                int32_t cj[D];
-                load_point<D>(recb + ((int64_t)e.x + j) * DP, cj);
-#pragma unroll
-                for (int q = 0; q < kSparseMax; ++q) cnt[q] += inside<D, W64>(qx[q], cj, T);
+                        for (int q = 0; q < kSparseMax; ++q) cnt[q] += inside<D, W64>(qx[q], cj, T);
+                    }
+                }
             }
         }
 #pragma unroll
         for (int q = 0; q < kSparseMax; ++q)
-            if ((uint32_t)q < m) v.rho_s[cs + q] = (int32_t)cnt[q];
+#pragma unroll
+            for (int o = 1; o < G; o <<= 1) cnt[q] += __shfl_xor_sync(0xffffffffu, cnt[q], o);
+        if (mine && sl == 0) {
+#pragma unroll
+            for (int q = 0; q < kSparseMax; ++q)
+                if ((uint32_t)q < m) v.rho_s[cs + q] = (int32_t)cnt[q];
+        }
     }
 }
-
 __global__ void k_rho_scatter(BatchView v) {
     const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (p < v.N) v.rho[v.perm[p]] = v.rho_s[p];
@@ -899,7 +936,7 @@ void launch_rho_dense_bulk(const BatchView& v, const CellWork& w, int64_t nitems
 template <int D, bool W64>
 void launch_rho_sparse(const BatchView& v, const CellWork& w, int64_t nsparse_bound, cudaStream_t st) {
     if (nsparse_bound <= 0) return;
-    const unsigned blocks = (unsigned)std::min<int64_t>(152 * 32, grid_for(nsparse_bound, 256));
+    const unsigned blocks = (unsigned)std::min<int64_t>(152 * 32, grid_for(nsparse_bound * kSparseLanes, 256));
     (k_rho_sparse<D, W64><<<blocks, 256, 0, st>>>(v, w), note_launch());
 }
 
@@ -955,7 +992,7 @@ cudaError_t launch_fill_items(const BatchView& v, const CellPrepBufs& cb, int64_
 template <int D, int M>
 void launch_dense_class(const BatchView& v, const CellWork& w, int64_t nitems_bound, uint32_t* counter, bool bulk,
                         cudaStream_t st) {
-    if constexpr (D <= 4 && M != 1) {
+    if constexpr (D <= 4 && M != 1 && !(M == 2 && D == 4)) {
         if (bulk) {
             launch_rho_dense_bulk<D, M>(v, w, nitems_bound, counter, st);
             return;
@@ -983,7 +1020,7 @@ cudaError_t launch_rho(const BatchView& v, const CellWork& w, uint32_t class_mas
     if ((parts & 1) && DPC_BIT(D, 2)) launch_dense_class<D, 2>(v, w, nitems_bound, counters + 3 * (D - 1) + 2, bulk, st);
     DPC_RHO_CLASS(1) DPC_RHO_CLASS(2) DPC_RHO_CLASS(3) DPC_RHO_CLASS(4)
     DPC_RHO_CLASS(5) DPC_RHO_CLASS(6) DPC_RHO_CLASS(7) DPC_RHO_CLASS(8)
-    DPC_RHO_X(1) DPC_RHO_X(2) DPC_RHO_X(3)
+    DPC_RHO_X(1) DPC_RHO_X(2) DPC_RHO_X(3) DPC_RHO_X(4)
 #undef DPC_RHO_X
 #undef DPC_RHO_CLASS
 #undef DPC_BIT
@@ -1000,7 +1037,7 @@ cudaError_t launch_rho_picks(const BatchView& v, const CellWork& w, uint32_t cla
 #define DPC_RHOP_CLASS(D) DPC_RHOP(D, 0) DPC_RHOP(D, 1)
     DPC_RHOP_CLASS(1) DPC_RHOP_CLASS(2) DPC_RHOP_CLASS(3) DPC_RHOP_CLASS(4)
     DPC_RHOP_CLASS(5) DPC_RHOP_CLASS(6) DPC_RHOP_CLASS(7) DPC_RHOP_CLASS(8)
-    DPC_RHOP(1, 2) DPC_RHOP(2, 2) DPC_RHOP(3, 2)
+    DPC_RHOP(1, 2) DPC_RHOP(2, 2) DPC_RHOP(3, 2) DPC_RHOP(4, 2)
 #undef DPC_RHOP_CLASS
 #undef DPC_RHOP
 #undef DPC_BIT

@@ -760,10 +760,11 @@ struct Batch {
         // is not 1; the block key packs the dataset index above 40 bits
         ds.sbits = (ds.R == 1 && k >= 1 && !ds.prune && b < (1 << 23)) ? k * (k == 4 ? 1 : 6 / k) : 0;
         ds.rbits = bits_for((uint64_t)ds.n);
-        // Expanded test around the query cell's corner: every coordinate
-        // relative to it lies in [-s, 2s) (gridded dims, reach 1) or [0, s)
-        // (a dim narrower than one cell), and |c'|^2 + |q'|^2 - T - 2 q'.c'
-        // stays inside 9 d s^2 < 2^31 for every partial sum.
+        // Expanded test in wrapping 32-bit arithmetic (d <= 4): with reach 1
+        // every candidate differs from its query by less than 2s in each
+        // gridded dim and by less than s in a dim narrower than one cell, so
+        // |q - c|^2 - T lies in [-T, 4 d s^2) inside [-2^31, 2^31) when
+        // 9 d s^2 < 2^31, and the wrapped sum's sign bit is exact.
         bool narrow = true;
         for (int c = 0; c < ds.d; ++c) {
             ds.lo[c] = ds.n > 0 ? mm[2 * c] : 0;
@@ -772,7 +773,7 @@ struct Batch {
             for (int j = 0; j < k; ++j) gridded |= ds.gdim[j] == c;
             if (!gridded && ds.n > 0 && (int64_t)mm[2 * c + 1] - mm[2 * c] >= ds.s) narrow = false;
         }
-        const bool expand = ds.d <= 3 && ds.R == 1 && narrow && ds.d_cut2 <= ds.s * ds.s &&
+        const bool expand = ds.d <= 4 && ds.R == 1 && narrow && ds.d_cut2 <= ds.s * ds.s &&
                             9 * (int64_t)ds.d * ds.s * ds.s < (1ll << 31);
         ds.mode = expand ? 2 : (ds.w32 ? 0 : 1);
         return DPC_OK;

@@ -19,7 +19,7 @@ def dpc():
 
 def test_probe_forms(dpc):
     rates = {}
-    for d, mode in [(3, 0), (3, 1), (3, 2), (8, 0), (8, 1), (3, 3), (2, 3)]:
+    for d, mode in [(3, 0), (3, 1), (3, 2), (8, 0), (8, 1), (3, 3), (2, 3), (4, 2), (4, 3)]:
         r, ms = dpc.dpc_probe_pair_rate(0, d, mode)
         assert 1e10 < r < 1e14 and ms > 0
         rates[(d, mode)] = r
@@ -27,6 +27,6 @@ def test_probe_forms(dpc):
     assert rates[(3, 1)] <= 1.05 * rates[(3, 0)]
     # the ring search's test does the density test's work and more
     assert rates[(3, 3)] <= 1.05 * rates[(3, 2)]
-    for d, mode in [(4, 2), (4, 3), (3, 4), (0, 0), (9, 1)]:
+    for d, mode in [(5, 2), (5, 3), (3, 4), (0, 0), (9, 1)]:
         with pytest.raises(dpc.DpcError):
             dpc.dpc_probe_pair_rate(0, d, mode)
