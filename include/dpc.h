@@ -306,8 +306,10 @@ dpc_status dpc_set_profiling(dpc_ctx* ctx, int on);
  *             picks of a pick's neighbour blocks: 1 one thread per pick,
  *             0 one warp per pick (default 1)
  *   "max_batch_jobs"  served mode: jobs one batch admits at most, 1 .. 4096
- *   "max_batch_points" served mode: points one batch admits at most, 1 .. 2^31 - 1 (a larger job
- *                     runs in a batch of its own, so that it does not hold back small ones)
+ *   "max_batch_points" served mode: points one batch admits at most, 1 .. 2^31 - 1 (default
+ *                     2^20; a larger job runs in a batch of its own, so that it does not hold
+ *                     back small ones). With a backlog, a batch may take up to the waiting
+ *                     points divided by the number of workers instead.
  *             (default 64; 1 runs the jobs one at a time)
  * DPC_ERR_INVALID_ARG for an unknown key or a value out of range. */
 dpc_status dpc_set_tuning(dpc_ctx* ctx, const char* key, int64_t value);

@@ -454,101 +454,52 @@ __global__ void k_bf_prefix(BatchView v, DeltaBufs db) {
     db.rorig[pos] = (uint32_t)(g - ds.pt_off);
 }
 
-__global__ void k_bf_keys(BatchView v, DeltaBufs db) {
-    const uint32_t cnt = db.ucount[1];
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < cnt; i += (int64_t)gridDim.x * blockDim.x) {
-        const uint32_t p = db.bf_list[i];
-        const int b = find_ds(v.pt_off, v.B, p);
-        db.bf_keys[i] = (uint32_t)(v.pt_off[b] + v.ro_s[p].x);
-    }
-}
-
 constexpr int kBfThreads = 128;
-constexpr int kBfTile = 256;
 
-// One thread per open point, the block's points consecutive in global rank
-// order (so grouped by dataset). For each dataset in the block, the longest
-// higher-ranked prefix among the block's points of that dataset streams
-// through shared memory in tiles, and every thread of that dataset keeps the
-// candidates of its own prefix.
+// One warp per open point of the list: the lanes stride through the point's
+// higher-ranked prefix of its dataset in rank order (the records rrec[pt_off
+// .. pt_off + rank), gathered by k_bf_prefix), each keeping the least
+// (distance, original index), then a warp reduction.
 template <int D>
 __global__ void __launch_bounds__(kBfThreads) k_bruteforce(BatchView v, DeltaBufs db) {
-    __shared__ int4 tile[kBfTile * 2];
-    __shared__ uint32_t torig[kBfTile];
-    __shared__ int32_t s_b[kBfThreads];
-    __shared__ int64_t s_hi[kBfThreads];
-    __shared__ int32_t seg_b[kBfThreads];
-    __shared__ int64_t seg_hi[kBfThreads];
-    __shared__ int s_nseg;
     const uint32_t cnt = db.ucount[1];
-    const int64_t i = (int64_t)blockIdx.x * kBfThreads + threadIdx.x;
-    if ((int64_t)blockIdx.x * kBfThreads >= cnt) return;
-    const bool valid = i < cnt;
-    uint32_t p = 0;
-    int b = -1;
-    int64_t my_hi = 0;  // candidates: global rank-order positions [pt_off[b], my_hi)
-    if (valid) {
-        p = db.bf_sorted[i];
-        b = find_ds(v.pt_off, v.B, p);
-        my_hi = v.pt_off[b] + v.ro_s[p].x;
-    }
-    s_b[threadIdx.x] = b;
-    s_hi[threadIdx.x] = my_hi;
-    __syncthreads();
-    if (threadIdx.x == 0) {  // the block's datasets of dimension D and their longest prefixes
-        int ns = 0;
-        for (int t = 0; t < kBfThreads; ++t) {
-            const int bt = s_b[t];
-            if (bt < 0 || v.desc[bt].d != D) continue;
-            if (ns == 0 || seg_b[ns - 1] != bt) {
-                seg_b[ns] = bt;
-                seg_hi[ns] = s_hi[t];
-                ++ns;
-            } else {
-                seg_hi[ns - 1] = max(seg_hi[ns - 1], s_hi[t]);
-            }
-        }
-        s_nseg = ns;
-    }
-    __syncthreads();
-    const bool mine = valid && v.desc[b].d == D;
-    int32_t x[D];
-    if (mine) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t i = warp; i < cnt; i += nwarps) {
+        const uint32_t p = db.bf_list[i];
+        const int b = find_ds(v.pt_off, v.B, p);
         const DsDesc& ds = v.desc[b];
-        const int4* r = v.rec + ds.rec_off + ((int64_t)p - ds.pt_off) * ds.dp;
-        load_pt<D>(r, x);
-    }
-    long long bestD = INT64_MAX;
-    uint32_t bestJ = 0xffffffffu;
-    const int nseg = s_nseg;
-    for (int sg = 0; sg < nseg; ++sg) {
-        const int sb = seg_b[sg];
-        const int64_t lo = v.pt_off[sb], hi = seg_hi[sg];
-        for (int64_t base = lo; base < hi; base += kBfTile) {
-            const int64_t nt = min((int64_t)kBfTile, hi - base);
-            for (int t = threadIdx.x; t < nt * 2; t += kBfThreads) tile[t] = db.rrec[base * 2 + t];
-            for (int t = threadIdx.x; t < nt; t += kBfThreads) torig[t] = db.rorig[base + t];
-            __syncthreads();
-            if (mine && b == sb) {
-                const int64_t j1 = min(nt, my_hi - base);
-                for (int64_t j = 0; j < j1; ++j) {
-                    int32_t c[D];
-                    load_pt<D>(tile + 2 * j, c);
-                    const long long dd = dist64<D>(x, c);
-                    const uint32_t o = torig[j];
-                    if (dd < bestD || (dd == bestD && o < bestJ)) {
-                        bestD = dd;
-                        bestJ = o;
-                    }
-                }
+        if (ds.d != D) continue;  // warp-uniform
+        int32_t x[D];
+        load_pt<D>(v.rec + ds.rec_off + ((int64_t)p - ds.pt_off) * ds.dp, x);
+        const uint2 ro = v.ro_s[p];
+        const int64_t lo = v.pt_off[b], hi = lo + ro.x;
+        long long bestD = INT64_MAX;
+        uint32_t bestJ = 0xffffffffu;
+        for (int64_t j = lo + lane; j < hi; j += 32) {
+            int32_t c[D];
+            load_pt<D>(db.rrec + 2 * j, c);
+            const long long dd = dist64<D>(x, c);
+            const uint32_t o = db.rorig[j];
+            if (dd < bestD || (dd == bestD && o < bestJ)) {
+                bestD = dd;
+                bestJ = o;
             }
-            __syncthreads();
         }
-    }
-    if (mine) {
-        const int64_t g = v.pt_off[b] + v.ro_s[p].y;
-        v.dep[g] = (int32_t)bestJ;
-        v.delta2[g] = bestD;
+        for (int o = 16; o > 0; o >>= 1) {
+            const long long d2 = __shfl_xor_sync(0xffffffffu, bestD, o);
+            const uint32_t j2 = __shfl_xor_sync(0xffffffffu, bestJ, o);
+            if (d2 < bestD || (d2 == bestD && j2 < bestJ)) {
+                bestD = d2;
+                bestJ = j2;
+            }
+        }
+        if (lane == 0) {
+            const int64_t g = ds.pt_off + ro.y;
+            v.dep[g] = (int32_t)bestJ;
+            v.delta2[g] = bestD;
+        }
     }
 }
 
@@ -646,19 +597,10 @@ cudaError_t launch_finalize(const BatchView& v, DeltaBufs db, void* ordered_temp
 }
 
 cudaError_t launch_bruteforce(const BatchView& v, const DeltaBufs& db, uint32_t dim_mask, int64_t bound,
-                              void* sort_temp, cudaStream_t st) {
+                              cudaStream_t st) {
     if (bound <= 0 || v.N == 0) return cudaSuccess;
     (k_bf_prefix<<<grid_for(v.N, 256), 256, 0, st>>>(v, db), note_launch());
-    const unsigned kblocks = (unsigned)std::min<int64_t>(152 * 16, grid_for(bound, 256));
-    (k_bf_keys<<<kblocks, 256, 0, st>>>(v, db), note_launch());
-    int nbits = 0;
-    while ((1ll << nbits) < v.N) ++nbits;
-    // sort the open points by global rank position; the list length lives on
-    // the device, so sort the bound and let the padding (key ~0) sink last
-    cudaError_t e = radix_sort_u32(db.bf_keys, db.bf_list, db.bf_keys + bound, db.bf_sorted, db.bf_keys + 2 * bound,
-                                   db.bf_sorted + bound, bound, nbits > 0 ? nbits : 1, sort_temp, st);
-    if (e != cudaSuccess) return e;
-    const unsigned blocks = grid_for(bound, kBfThreads);
+    const unsigned blocks = (unsigned)std::min<int64_t>(152 * 16, grid_for(bound * 32, kBfThreads));
 #define DPC_BF_CLASS(D) \
     if (dim_mask & (1u << (D - 1))) (k_bruteforce<D><<<blocks, kBfThreads, 0, st>>>(v, db), note_launch());
     DPC_BF_CLASS(1) DPC_BF_CLASS(2) DPC_BF_CLASS(3) DPC_BF_CLASS(4)

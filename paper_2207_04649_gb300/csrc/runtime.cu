@@ -896,13 +896,9 @@ struct Batch {
             DPC_CK(launch_tree_search(v, db, dim_mask, ntree, st));
         }
         if (nbf > 0) {
-            DPC_CK(tmp.get(&db.bf_keys, 3 * nbf));
-            DPC_CK(tmp.get(&db.bf_sorted, 2 * nbf));
             DPC_CK(tmp.get(&db.rrec, 2 * N));
             DPC_CK(tmp.get(&db.rorig, N));
-            void* t2 = nullptr;
-            DPC_CK(tmp.get(&t2, std::max(radix_sort_temp_bytes(nbf), scan_temp_bytes(nbf))));
-            DPC_CK(launch_bruteforce(v, db, dim_mask, nbf, t2, st));
+            DPC_CK(launch_bruteforce(v, db, dim_mask, nbf, st));
         }
         return DPC_OK;
     }
@@ -1791,6 +1787,16 @@ void serve_loop(dpc_ctx* ctx) {
                 return it == ctx->jobs.end() || ctx->held_bytes + it->second->bytes <= ctx->cap;
             });
             if (ctx->stop && ctx->waiting.empty()) break;
+            // the points cap keeps a small job out of a large job's batch; with
+            // a backlog every worker's share of it may go in one batch instead
+            // (larger batches, fewer fixed costs, while all of them wait anyway)
+            int64_t backlog = 0;
+            for (uint64_t t : ctx->waiting) {
+                auto jt = ctx->jobs.find(t);
+                if (jt != ctx->jobs.end()) backlog += jt->second->job.n;
+            }
+            const int64_t cap_points =
+                std::max<int64_t>(ctx->max_batch_points, backlog / std::max(1, ctx->max_inflight));
             int64_t pts = 0;
             while (!ctx->waiting.empty() && (int)group.size() < ctx->max_batch_jobs) {
                 auto it = ctx->jobs.find(ctx->waiting.front());
@@ -1802,7 +1808,7 @@ void serve_loop(dpc_ctx* ctx) {
                 if (ctx->held_bytes + j->bytes > ctx->cap) break;
                 if (!group.empty() && j->job.method != group[0]->job.method) break;  // one method per batch
                 if (pts + j->job.n >= (1ll << 31) - 1) break;
-                if (!group.empty() && pts + j->job.n > ctx->max_batch_points) break;  // a large job runs alone
+                if (!group.empty() && pts + j->job.n > cap_points) break;  // a large job runs alone
                 ctx->waiting.pop_front();
                 ctx->held_bytes += j->bytes;
                 pts += j->job.n;

@@ -262,8 +262,6 @@ struct DeltaBufs {
     uint64_t chmask;
     uint32_t* open2;      // [N] points still open after the coarse ring
     uint32_t* bf_list;    // [N]
-    uint32_t* bf_keys;    // [N]
-    uint32_t* bf_sorted;  // [N]
     int4* rrec;           // [N * 2] records in rank order (prefix only)
     uint32_t* rorig;      // [N]
     uint32_t bf_rank;     // points with rank below this go to the brute-force pass
@@ -314,7 +312,7 @@ cudaError_t launch_tree_build(const BatchView& v, const DeltaBufs& db, cudaStrea
 cudaError_t launch_tree_search(const BatchView& v, const DeltaBufs& db, uint32_t dim_mask, int64_t bound,
                                cudaStream_t st);
 cudaError_t launch_bruteforce(const BatchView& v, const DeltaBufs& db, uint32_t dim_mask, int64_t bound,
-                              void* sort_temp, cudaStream_t st);
+                              cudaStream_t st);
 
 // ptree.cu: the point tree of datasets with ungridded dims (DsDesc::ptree).
 // Each such dataset's points are sorted by the Morton code of all their
