@@ -339,6 +339,7 @@ __global__ void __launch_bounds__(256) k_ring_sparse(BatchView v, CellWork w) {
 // position (Morton) order when db.ocode is set (codes, block counts, scan,
 // k_emit_open), else in position order within each warp.
 constexpr int kFinThreads = 256;
+constexpr int kOpenCodes = kMaxDims + 2;  // 0 resolved, 1..8 tree search in that many dims, 9 brute force
 
 __global__ void __launch_bounds__(kFinThreads) k_finalize(BatchView v, DeltaBufs db) {
     const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -383,23 +384,25 @@ __global__ void __launch_bounds__(kFinThreads) k_finalize(BatchView v, DeltaBufs
     const int lane = threadIdx.x & 31;
     const unsigned mt = __ballot_sync(0xffffffffu, to_tree), mb = __ballot_sync(0xffffffffu, to_bf);
     if (db.ocode) {
-        // ordered lists: a code per point and the block's counts; the lists
-        // are written in position order by k_emit_open after a scan
-        __shared__ uint32_t ct[kFinThreads / 32], cf[kFinThreads / 32];
-        if (valid) db.ocode[p] = to_tree ? 1 : (to_bf ? 2 : 0);
-        if (lane == 0) {
-            ct[threadIdx.x >> 5] = (uint32_t)__popc(mt);
-            cf[threadIdx.x >> 5] = (uint32_t)__popc(mb);
+        // ordered lists: a code per point (0 resolved, d: tree search in d
+        // dims, 9: brute force) and the block's counts per code; the lists
+        // are written by k_emit_open after a scan, the tree list grouped by
+        // dimension and in position order within each group
+        __shared__ uint32_t cc[kFinThreads / 32][kOpenCodes];
+        int code = 0;
+        if (to_tree) code = v.desc[find_ds(v.pt_off, v.B, p)].d;
+        else if (to_bf) code = kOpenCodes - 1;
+        if (valid) db.ocode[p] = (uint8_t)code;
+#pragma unroll
+        for (int c = 1; c < kOpenCodes; ++c) {
+            const unsigned m = __ballot_sync(0xffffffffu, code == c);
+            if (lane == 0) cc[threadIdx.x >> 5][c] = (uint32_t)__popc(m);
         }
         __syncthreads();
-        if (threadIdx.x == 0) {
-            uint32_t a = 0, f = 0;
-            for (int w = 0; w < kFinThreads / 32; ++w) {
-                a += ct[w];
-                f += cf[w];
-            }
-            db.ocnt[blockIdx.x] = a;
-            db.ocnt[gridDim.x + blockIdx.x] = f;
+        if (threadIdx.x >= 1 && threadIdx.x < kOpenCodes) {
+            uint32_t a = 0;
+            for (int w = 0; w < kFinThreads / 32; ++w) a += cc[w][threadIdx.x];
+            db.ocnt[(int64_t)(threadIdx.x - 1) * gridDim.x + blockIdx.x] = a;
         }
         return;
     }
@@ -415,27 +418,35 @@ __global__ void __launch_bounds__(kFinThreads) k_finalize(BatchView v, DeltaBufs
     if (to_bf) db.bf_list[bb + __popc(mb & lt)] = (uint32_t)p;
 }
 
-// The open lists in position order from the codes of k_finalize: block b's
-// entries start at the exclusive scans of the blocks' counts.
+// The open lists from the codes of k_finalize: a point of code c of block b
+// goes to the exclusive scan of the (code, block) counts (code-major) plus
+// the warps before its own and the lanes before it with the same code.
 __global__ void __launch_bounds__(kFinThreads) k_emit_open(BatchView v, DeltaBufs db) {
-    __shared__ uint32_t ct[kFinThreads / 32], cf[kFinThreads / 32];
+    __shared__ uint32_t cc[kFinThreads / 32][kOpenCodes];
     const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const uint8_t code = p < v.N ? db.ocode[p] : 0;
-    const unsigned mt = __ballot_sync(0xffffffffu, code == 1), mb = __ballot_sync(0xffffffffu, code == 2);
-    if (lane == 0) {
-        ct[w] = (uint32_t)__popc(mt);
-        cf[w] = (uint32_t)__popc(mb);
+    const int code = p < v.N ? db.ocode[p] : 0;
+    const unsigned peers = __match_any_sync(0xffffffffu, code);
+#pragma unroll
+    for (int c = 1; c < kOpenCodes; ++c) {
+        const unsigned m = __ballot_sync(0xffffffffu, code == c);
+        if (lane == 0) cc[w][c] = (uint32_t)__popc(m);
     }
     __syncthreads();
-    uint32_t ot = db.oofs[blockIdx.x], of = db.oofs[gridDim.x + blockIdx.x];
-    for (int u = 0; u < w; ++u) {
-        ot += ct[u];
-        of += cf[u];
-    }
-    const unsigned lt = (1u << lane) - 1u;
-    if (code == 1) db.tree_list[ot + __popc(mt & lt)] = (uint32_t)p;
-    if (code == 2) db.bf_list[of + __popc(mb & lt)] = (uint32_t)p;
+    if (code == 0) return;
+    uint32_t off = db.oofs[(int64_t)(code - 1) * gridDim.x + blockIdx.x];
+    for (int u = 0; u < w; ++u) off += cc[u][code];
+    off += (uint32_t)__popc(peers & ((1u << lane) - 1u));
+    if (code < kOpenCodes - 1) db.tree_list[off] = (uint32_t)p;
+    else db.bf_list[off] = (uint32_t)p;
+}
+
+// Where the tree list's group of each dimension starts: tclass[d - 1], and
+// tclass[8] = the list's length.
+__global__ void k_open_classes(DeltaBufs db, int64_t nb) {
+    const int c = threadIdx.x;
+    if (c < kMaxDims) db.tclass[c] = db.oofs[(int64_t)c * nb];
+    if (c == kMaxDims) db.tclass[c] = db.ucount[0];
 }
 
 // --------------------------------------------------------- brute force
@@ -570,7 +581,8 @@ cudaError_t launch_ring(const BatchView& v, const CellWork& w, uint32_t class_ma
 
 size_t finalize_temp_bytes(int64_t n) {
     const int64_t nb = (n + kFinThreads - 1) / kFinThreads;
-    return (size_t)n + 4 * sizeof(uint32_t) * (size_t)nb + scan_temp_bytes(2 * nb) + 1024;
+    return (size_t)n + 2 * (kOpenCodes - 1) * sizeof(uint32_t) * (size_t)nb + scan_temp_bytes(kMaxDims * nb) +
+           1024;
 }
 
 cudaError_t launch_finalize(const BatchView& v, DeltaBufs db, void* ordered_temp, cudaStream_t st) {
@@ -579,16 +591,19 @@ cudaError_t launch_finalize(const BatchView& v, DeltaBufs db, void* ordered_temp
     if (ordered_temp) {
         char* t = static_cast<char*>(ordered_temp);
         db.ocnt = reinterpret_cast<uint32_t*>(t);
-        db.oofs = db.ocnt + 2 * nb;
-        void* stemp = db.oofs + 2 * nb;
-        db.ocode = reinterpret_cast<uint8_t*>(static_cast<char*>(stemp) + ((scan_temp_bytes(2 * nb) + 255) & ~(size_t)255));
+        db.oofs = db.ocnt + (kOpenCodes - 1) * nb;
+        void* stemp = db.oofs + (kOpenCodes - 1) * nb;
+        db.ocode = reinterpret_cast<uint8_t*>(static_cast<char*>(stemp) +
+                                              ((scan_temp_bytes(kMaxDims * nb) + 255) & ~(size_t)255));
         (k_finalize<<<(unsigned)nb, kFinThreads, 0, st>>>(v, db), note_launch());
-        // offsets of the tree list, then of the brute-force list
-        cudaError_t e = exclusive_scan_u32(db.ocnt, db.oofs, nb, db.ucount, stemp, st);
+        // offsets in the tree list (code-major over the dims), then in the
+        // brute-force list
+        cudaError_t e = exclusive_scan_u32(db.ocnt, db.oofs, kMaxDims * nb, db.ucount, stemp, st);
         if (e != cudaSuccess) return e;
-        e = exclusive_scan_u32(db.ocnt + nb, db.oofs + nb, nb, db.ucount + 1, stemp, st);
+        e = exclusive_scan_u32(db.ocnt + kMaxDims * nb, db.oofs + kMaxDims * nb, nb, db.ucount + 1, stemp, st);
         if (e != cudaSuccess) return e;
         (k_emit_open<<<(unsigned)nb, kFinThreads, 0, st>>>(v, db), note_launch());
+        if (db.tclass) (k_open_classes<<<1, 32, 0, st>>>(db, nb), note_launch());
         return cudaGetLastError();
     }
     db.ocode = nullptr;

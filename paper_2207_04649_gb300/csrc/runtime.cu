@@ -866,6 +866,7 @@ struct Batch {
                 DPC_CK(launch_coarse_ring(v, db, dim_mask, ntree, st));
                 db.tree_list = db.open2;
                 db.tcount = db.ucount + 2;
+                db.tclass = nullptr;  // the second list is not grouped by dimension
             } else if (allow_coarse && tune.ring2) {
                 // the second ring on the fine grid; the first ring's unproven
                 // best (v.best_s) is part of its search
@@ -873,6 +874,7 @@ struct Batch {
                 DPC_CK(launch_ring2(v, db, dim_mask, ntree, st));
                 db.tree_list = db.open2;
                 db.tcount = db.ucount + 2;
+                db.tclass = nullptr;  // the second list is not grouped by dimension
             }
             if (!tree_ready) {
                 db.dpb = 1;
@@ -983,10 +985,12 @@ struct Batch {
         db.bf_rank = tune.bf_rank;
         void* fin_temp = nullptr;
         DPC_CK(tmp.get(&fin_temp, finalize_temp_bytes(N)));
+        DPC_CK(tmp.get(&db.tclass, kMaxDims + 1));
         DPC_CK(launch_finalize(v, db, fin_temp, st));
-        db.lists_sorted = 1;  // written in position order
+        db.lists_sorted = 1;  // written in position order, grouped by dimension
         DPC_TRY(open_points(tmp, "ring search", true));
         db.lists_sorted = 0;
+        db.tclass = nullptr;
         mark(3);
         DPC_TRY(finish_stats("dependent points"));
         ms[2] = elapsed(0, 1);

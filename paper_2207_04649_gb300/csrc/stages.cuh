@@ -249,6 +249,7 @@ struct DeltaBufs {
     uint32_t* ocnt;       // their per-block counts [2][blocks] (tree, brute force)
     uint32_t* oofs;       // and exclusive scans of those
     int lists_sorted;     // 1: tree_list is in position order already
+    uint32_t* tclass;     // [9] or null: tree_list grouped by dimension, group d at [tclass[d-1], tclass[d])
     const uint32_t* tcount;  // count of the list the tree search reads
     // coarse ring (coarse.cu): cells are aligned blocks of 2^clevel grid
     // cells per gridded dim, contiguous in the Morton-sorted order

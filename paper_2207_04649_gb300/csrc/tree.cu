@@ -360,11 +360,14 @@ template <int D>
 __global__ void __launch_bounds__(128) k_tree_search(BatchView v, DeltaBufs db) {
     constexpr int DP = D <= 4 ? 1 : 2;
     constexpr bool CMP = D <= 3;  // compact records possible
-    const uint32_t cnt = *db.tcount;
+    // the list's group of dimension D when it is grouped, else all of it
+    const uint32_t i0 = db.tclass ? db.tclass[D - 1] : 0u;
+    const uint32_t cnt = db.tclass ? db.tclass[D] : *db.tcount;
     const int dpb = db.dpb, ns = 2 * dpb + 1;
     const bool compact = CMP && db.compact;
     unsigned long long visits = 0, tests = 0;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < cnt; i += (int64_t)gridDim.x * blockDim.x) {
+    for (int64_t i = i0 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < cnt;
+         i += (int64_t)gridDim.x * blockDim.x) {
         const uint32_t p = db.tree_list[i];
         const int b = find_ds(v.pt_off, v.B, p);
         const DsDesc& ds = v.desc[b];
