@@ -293,7 +293,12 @@ struct Batch {
     int out_is_device = 0;
     float ms[6] = {0, 0, 0, 0, 0, 0};
     int refs = 0;
-    cudaEvent_t ev[8] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+    // stage events (profiling): density 0-2 and 4, S-Approx-DPC 0-7, the
+    // dependent points 8-11, labels 12-13
+    cudaEvent_t ev[16] = {};
+    // statistics read back at the next point where the host waits for the
+    // stream anyway (no round trip of their own): 1 density, 2 dependent points
+    int stats_pending = 0;
     int64_t dense_pairs = 0;
     float ms_rho_dense = 0.f;
 
@@ -347,19 +352,38 @@ struct Batch {
     dpc_status density(const std::vector<Input>& in) {
         DPC_TRY(build_grid(in));
         DPC_TRY(rho_all());
-        unsigned long long pairs[2] = {0, 0}, ptst[4] = {0, 0, 0, 0};
-        DPC_CK(cudaMemcpyAsync(pairs, d_stats, sizeof(pairs), cudaMemcpyDeviceToHost, st));
-        if (pb.m > 0) DPC_CK(cudaMemcpyAsync(ptst, pb.stats, sizeof(ptst), cudaMemcpyDeviceToHost, st));
-        DPC_TRY(sync("density"));
-        cand_pairs = (int64_t)(pairs[0] + pairs[1] + ptst[1]);
-        dense_pairs = (int64_t)pairs[0];
-        DPC_TRY(check_err("density"));
-        ms[0] = elapsed(0, 1);
-        ms[1] = elapsed(1, 2);
-        ms_rho_dense = elapsed(1, 4);
         dens.release();
         has_density = true;
+        stats_pending |= 1;  // read at the next wait (settle)
         return DPC_OK;
+    }
+
+    // Reads the statistics (and the error word) of the stages that ran since
+    // the last wait; one wait for the stream when any are pending.
+    dpc_status settle() {
+        if (!stats_pending) return DPC_OK;
+        unsigned long long s8[8] = {0, 0, 0, 0, 0, 0, 0, 0}, ptst[4] = {0, 0, 0, 0};
+        DPC_CK(cudaMemcpyAsync(s8, d_stats, sizeof(s8), cudaMemcpyDeviceToHost, st));
+        if (pb.m > 0) DPC_CK(cudaMemcpyAsync(ptst, pb.stats, sizeof(ptst), cudaMemcpyDeviceToHost, st));
+        DPC_TRY(sync("statistics"));
+        const int pend = stats_pending;
+        stats_pending = 0;
+        if (pend & 1) {
+            cand_pairs = (int64_t)(s8[0] + s8[1] + ptst[1]);
+            dense_pairs = (int64_t)s8[0];
+            ms[0] = elapsed(0, 1);
+            ms[1] = elapsed(1, 2);
+            ms_rho_dense = elapsed(1, 4);
+        }
+        if (pend & 2) {
+            tree_visits = (int64_t)(s8[4] + ptst[2]);
+            tree_pairs = (int64_t)(s8[5] + ptst[3]);
+            ntree2 = (int64_t)s8[6];
+            ms[2] = elapsed(8, 9);
+            ms[3] = elapsed(9, 10);
+            ms[4] = elapsed(10, 11);
+        }
+        return check_err("statistics");
     }
 
     // The dense cells' work items, once (the density and ring passes over
@@ -516,9 +540,9 @@ struct Batch {
         DPC_CK(keep.get(&v.ncells, 1));
         DPC_CK(keep.get(&v.err, 1));
         DPC_CK(cudaMemsetAsync(v.err, 0, sizeof(unsigned int), st));
-        DPC_CK(keep.get(&d_stats, 4));
+        DPC_CK(keep.get(&d_stats, 8));
         DPC_CK(keep.get(&d_counters, 64));
-        DPC_CK(cudaMemsetAsync(d_stats, 0, 4 * sizeof(unsigned long long), st));
+        DPC_CK(cudaMemsetAsync(d_stats, 0, 8 * sizeof(unsigned long long), st));
 
         // cell keys, sort, cells
         const size_t kb = key32 ? 4 : 8;
@@ -818,6 +842,7 @@ struct Batch {
         uint32_t uc[2] = {0, 0};
         DPC_CK(cudaMemcpyAsync(uc, db.ucount, sizeof(uc), cudaMemcpyDeviceToHost, st));
         DPC_TRY(sync(what));
+        DPC_TRY(settle());  // the stream is idle: the density statistics cost no extra wait
         ntree = uc[0];
         nbf = uc[1];
         if (ntree > 0) {
@@ -905,20 +930,16 @@ struct Batch {
         return DPC_OK;
     }
 
-    dpc_status finish_stats(const char* what) {
-        unsigned long long tstat[2] = {0, 0};
-        uint32_t open2 = 0;
+    // The open-point statistics, kept on the device (the lists' buffers are
+    // freed before they are read) and read by settle().
+    dpc_status finish_stats(const char*) {
+        DPC_CK(cudaMemsetAsync(d_stats + 4, 0, 3 * sizeof(unsigned long long), st));
         if (ntree > 0) {
-            DPC_CK(cudaMemcpyAsync(tstat, db.stats, sizeof(tstat), cudaMemcpyDeviceToHost, st));
-            DPC_CK(cudaMemcpyAsync(&open2, db.tcount, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
+            DPC_CK(cudaMemcpyAsync(d_stats + 4, db.stats, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToDevice,
+                                   st));
+            DPC_CK(cudaMemcpyAsync(d_stats + 6, db.tcount, sizeof(uint32_t), cudaMemcpyDeviceToDevice, st));
         }
-        unsigned long long ptst[4] = {0, 0, 0, 0};
-        if (pb.m > 0) DPC_CK(cudaMemcpyAsync(ptst, pb.stats, sizeof(ptst), cudaMemcpyDeviceToHost, st));
-        DPC_TRY(sync(what));
-        tree_visits = (int64_t)(tstat[0] + ptst[2]);
-        tree_pairs = (int64_t)(tstat[1] + ptst[3]);
-        ntree2 = open2;
-        DPC_TRY(check_err(what));
+        stats_pending |= 2;
         return DPC_OK;
     }
 
@@ -948,7 +969,7 @@ struct Batch {
     dpc_status dependent() {
         if (dep_kind == 1 || dep_kind == 3) return DPC_OK;  // S-Approx-DPC keeps its own
         if (!has_density) return fail(DPC_ERR_STATE, "dataset has no density");
-        mark(0);
+        mark(8);
         Arena tmp;
         tmp.st = st;
         // on every way out, st waits for the tree built on the side stream
@@ -963,7 +984,7 @@ struct Batch {
         void* temp = nullptr;
         DPC_CK(tmp.get(&temp, std::max(radix_sort_temp_bytes(N), scan_temp_bytes(N))));
         DPC_TRY(ensure_rank(tmp, temp));
-        mark(1);
+        mark(9);
 
         DPC_CK(tmp.get(&v.best_s, N));
         DPC_CK(cudaMemsetAsync(v.best_s, 0xff, sizeof(unsigned long long) * std::max<int64_t>(N, 1), st));
@@ -975,7 +996,7 @@ struct Batch {
             for (int d = 1; d <= kMaxDims; ++d)
                 DPC_CK(launch_delta_ptree(v, pb, d, pt_range[d][0], pt_range[d][1], st));
         }
-        mark(2);
+        mark(10);
 
         DPC_CK(tmp.get(&db.ucount, 4));
         DPC_CK(tmp.get(&db.tree_list, N));
@@ -991,11 +1012,8 @@ struct Batch {
         DPC_TRY(open_points(tmp, "ring search", true));
         db.lists_sorted = 0;
         db.tclass = nullptr;
-        mark(3);
+        mark(11);
         DPC_TRY(finish_stats("dependent points"));
-        ms[2] = elapsed(0, 1);
-        ms[3] = elapsed(1, 2);
-        ms[4] = elapsed(2, 3);
         tmp.release();  // after open_points, whose stream waited for the side stream's tree
         dep_kind = 1;
         return DPC_OK;
@@ -1030,13 +1048,13 @@ struct Batch {
         }
         const int key_bits = bshift + bits_for((uint64_t)(B - 1));
         DPC_TRY(upload_desc());
-        mark(0);
+        mark(8);
         Arena tmp;
         tmp.st = st;
         void* temp = nullptr;
         DPC_CK(tmp.get(&temp, std::max(radix_sort_temp_bytes(N), scan_temp_bytes(N))));
         DPC_TRY(ensure_rank(tmp, temp));
-        mark(1);
+        mark(9);
         ApproxBufs ab{};
         uint64_t* kbuf = nullptr;
         uint32_t* obuf = nullptr;
@@ -1065,13 +1083,10 @@ struct Batch {
         db.tcount = db.ucount;
         db.bf_rank = tune.bf_rank;
         DPC_CK(launch_approx_rules(v, w, ab, db, dim_mask, N, st));
-        mark(2);
+        mark(10);
         DPC_TRY(open_points(tmp, "approximate rules", false));
-        mark(3);
+        mark(11);
         DPC_TRY(finish_stats("approximate dependent points"));
-        ms[2] = elapsed(0, 1);
-        ms[3] = elapsed(1, 2);
-        ms[4] = elapsed(2, 3);
         tmp.release();
         dep_kind = 2;
         return DPC_OK;
@@ -1228,6 +1243,7 @@ struct Batch {
         DPC_CK(cudaMemcpyAsync(sst, sb.stats, sizeof(sst), cudaMemcpyDeviceToHost, st));
         DPC_CK(cudaMemcpyAsync(pairs, d_stats, sizeof(pairs), cudaMemcpyDeviceToHost, st));
         DPC_TRY(finish_stats("S-Approx-DPC dependent points"));
+        DPC_TRY(settle());  // waits for the copies above too
         sap_pairs = pick_items ? pick_pairs : (int64_t)sst[0];
         nsecond = (int64_t)sst[1];
         cand_pairs = all_points ? (int64_t)(pairs[0] + pairs[1]) : sap_pairs;
@@ -1257,9 +1273,9 @@ struct Batch {
             hd[b].delta_min2 = delta_min[b] * delta_min[b];
         }
         DPC_TRY(upload_desc());
-        mark(0);
+        mark(12);
         DPC_CK(launch_labels(v, st));
-        mark(1);
+        mark(13);
         return DPC_OK;
     }
 
@@ -1274,9 +1290,9 @@ struct Batch {
         hd[b].rho_min = rho_min;
         hd[b].delta_min2 = delta_min * delta_min;
         DPC_TRY(upload_desc());
-        mark(0);
+        mark(12);
         DPC_CK(launch_labels_one(v, b, hd[b].pt_off, hd[b].n, st));
-        mark(1);
+        mark(13);
         return DPC_OK;
     }
 
@@ -1444,10 +1460,8 @@ dpc_status dpc_density(dpc_ctx* ctx, const int32_t* points, int64_t n, int32_t d
     b->ctx = ctx;
     std::vector<dpc::Input> in{{points, n, d, d_cut, is_device}};
     DPC_TRY(b->density(in));
-    if (rho_out) {
-        DPC_TRY(b->copy_out(rho_out, b->v.rho, sizeof(int32_t) * n));
-        DPC_TRY(b->sync("copy rho"));
-    }
+    if (rho_out) DPC_TRY(b->copy_out(rho_out, b->v.rho, sizeof(int32_t) * n));
+    DPC_TRY(b->settle());  // the statistics, the error word, and the copy done
     auto* ds = new dpc_ds();
     ds->batch = b;
     ds->b = 0;
@@ -1533,6 +1547,7 @@ dpc_status dpc_cluster(dpc_ctx* ctx, const int32_t* points, int64_t n, int32_t d
     DPC_TRY(bt.sync("labels"));
     e = cudaStreamSynchronize(cs);
     if (e != cudaSuccess) return cuda_fail(e, "copies");
+    DPC_TRY(bt.settle());
     DPC_TRY(bt.check_err("labels"));
     if (n_centers) *n_centers = (int64_t)nc;
     return DPC_OK;
@@ -1546,7 +1561,8 @@ dpc_status dpc_dependent(dpc_ds* ds, int32_t* dep_out, int64_t* delta2_out) {
     const dpc::DsDesc& h = bt.hd[ds->b];
     DPC_TRY(bt.copy_out(dep_out, bt.v.dep + h.pt_off, sizeof(int32_t) * h.n));
     DPC_TRY(bt.copy_out(delta2_out, bt.v.delta2 + h.pt_off, sizeof(int64_t) * h.n));
-    return bt.sync("copy dependent");
+    DPC_TRY(bt.sync("copy dependent"));
+    return bt.settle();
 }
 
 dpc_status dpc_dependent_approx(dpc_ds* ds, int32_t* dep_out, int64_t* delta2_out, uint8_t* exact_out) {
@@ -1558,7 +1574,8 @@ dpc_status dpc_dependent_approx(dpc_ds* ds, int32_t* dep_out, int64_t* delta2_ou
     DPC_TRY(bt.copy_out(dep_out, bt.v.dep + h.pt_off, sizeof(int32_t) * h.n));
     DPC_TRY(bt.copy_out(delta2_out, bt.v.delta2 + h.pt_off, sizeof(int64_t) * h.n));
     DPC_TRY(bt.copy_out(exact_out, bt.v.exact + h.pt_off, sizeof(uint8_t) * h.n));
-    return bt.sync("copy approximate dependent");
+    DPC_TRY(bt.sync("copy approximate dependent"));
+    return bt.settle();
 }
 
 dpc_status dpc_label(dpc_ds* ds, int64_t rho_min, int64_t delta_min, int32_t* label_out, int64_t* n_centers) {
@@ -1574,8 +1591,9 @@ dpc_status dpc_label(dpc_ds* ds, int64_t rho_min, int64_t delta_min, int32_t* la
     unsigned long long nc = 0;
     if (n_centers) DPC_TRY(bt.copy_out(&nc, bt.v.ncent + ds->b, sizeof(nc)));
     DPC_TRY(bt.sync("labels"));
+    DPC_TRY(bt.settle());
     DPC_TRY(bt.check_err("labels"));
-    bt.ms[5] = bt.elapsed(0, 1);
+    bt.ms[5] = bt.elapsed(12, 13);
     if (n_centers) *n_centers = (int64_t)nc;
     return DPC_OK;
 }
@@ -1630,6 +1648,11 @@ static void fill_info(const Batch& bt, int b, dpc_info* out) {
 
 dpc_status dpc_ds_info(const dpc_ds* ds, dpc_info* out) {
     if (!ds || !ds->batch || !out) return fail(DPC_ERR_INVALID_ARG, "NULL argument");
+    {
+        std::lock_guard<std::mutex> lk(ds->batch->qmu);
+        cudaSetDevice(ds->batch->ctx->device);
+        DPC_TRY(ds->batch->settle());
+    }
     fill_info(*ds->batch, ds->b, out);
     return DPC_OK;
 }
@@ -1742,6 +1765,7 @@ dpc_status run_jobs(dpc_ctx* ctx, std::vector<JobPtr>& jobs, cudaStream_t st) {
     }
     // the batch's counters and stage times (the first dataset's per-dataset
     // fields, the batch's totals)
+    DPC_TRY(bt->settle());
     dpc_info info;
     fill_info(*bt, 0, &info);
     int64_t n = 0;
