@@ -577,7 +577,7 @@ def run_ours(args):
               for k in ("ms_grid", "ms_rho", "ms_rank", "ms_ring", "ms_rest", "ms_label")}
     work = {k: infos[-1][k] for k in ("cells", "dense_cells", "work_items", "cand_pairs", "dense_pairs",
                                       "open_after_ring", "brute_points", "grid_dims", "pair_bits",
-                                      "tree_visits", "tree_pairs", "open_after_coarse")}
+                                      "tree_visits", "tree_pairs")}
     if rank == 0:
         line = {
             "metric": metric_for(args), "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,

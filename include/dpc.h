@@ -236,7 +236,6 @@ typedef struct {
     float ms_grid, ms_rho, ms_rank, ms_ring, ms_rest, ms_label;  /* stage times when profiling is on */
     int64_t tree_visits;      /* tree nodes visited by the search for open points */
     int64_t tree_pairs;       /* point pairs it tested */
-    int64_t open_after_coarse;  /* points the coarse ring left for the tree search */
     int32_t pair_mode;        /* density pair test: 0 direct 32-bit, 1 direct 64-bit, 2 expanded 32-bit */
     int32_t grid_key_bits;    /* width of the grid's sort key (radix passes: bits / 8, rounded up) */
     int64_t dense_pairs;      /* of cand_pairs, those of dense cells (one warp per work item) */
@@ -263,9 +262,6 @@ dpc_status dpc_set_profiling(dpc_ctx* ctx, int on);
  *   "kmax"    gridded dimensions at most, 1 .. 4 (default 4)
  *   "bf_rank" points still open after the ring search whose rank is below
  *             this take the brute-force pass (default 1024)
- *   "clevel"  coarse ring over blocks of 2^clevel cells per gridded dim,
- *             0 .. 8 (default 0: off)
- *   "ccap"    coarse cells with more points are not scanned (default 512)
  *   "tree_min_d"  datasets with at least this many dimensions skip the grid
  *             and take the point tree (a kd-tree-like search over all
  *             dimensions), 1 .. 9 (default 9: never; on the blob workloads
@@ -275,10 +271,6 @@ dpc_status dpc_set_profiling(dpc_ctx* ctx, int on);
  *             grid, fewer candidate pairs, more neighbour cells), 1 .. 3
  *             (default 2)
  *   "hd_min_d"  smallest d that takes hd_cell_factor, 1 .. 9 (default 7)
- *   "ring2"   1: points the first ring leaves open scan the cells at
- *             distance 2 before the tree search, 0: straight to the tree
- *             (default 0: on 5.8M x 3 it resolves 56% of them but costs more
- *             than the tree search it saves)
  *   "sparse_cand"  a cell of at most 4 points takes one thread (the sparse
  *             kernels) only if it has at most this many candidates, else one
  *             warp per work item like the larger cells, 0 .. 2^31 (default
@@ -410,7 +402,7 @@ dpc_status dpc_last_batch_info(dpc_ctx* ctx, dpc_info* out);
 /* Autotuner (no counterpart in the paper). Runs the n_jobs sample jobs as
  * one batch under candidate settings of the knobs that change speed only
  * (kch and qch, the candidates and queries per dense work item, i.e. the
- * warps per cell; bf_rank, clevel; hd_min_d with hd_cell_factor, the grid's
+ * warps per cell; bf_rank; hd_min_d with hd_cell_factor, the grid's
  * cell factor, tried for every dataset's d; kmax when some d >= 4;
  * tree_min_d when some d >= 5): coordinate descent from the context's current knobs, each
  * setting timed as the best of `repeats` (1 .. 100) synchronous runs, a

@@ -47,7 +47,7 @@ class DpcInfo(ctypes.Structure):
                 ("ms_grid", ctypes.c_float), ("ms_rho", ctypes.c_float), ("ms_rank", ctypes.c_float),
                 ("ms_ring", ctypes.c_float), ("ms_rest", ctypes.c_float), ("ms_label", ctypes.c_float),
                 ("tree_visits", ctypes.c_int64), ("tree_pairs", ctypes.c_int64),
-                ("open_after_coarse", ctypes.c_int64), ("pair_mode", ctypes.c_int32), ("grid_key_bits", ctypes.c_int32),
+                ("pair_mode", ctypes.c_int32), ("grid_key_bits", ctypes.c_int32),
                 ("dense_pairs", ctypes.c_int64), ("ms_rho_dense", ctypes.c_float), ("rank_key_bits", ctypes.c_int32),
                 ("picks", ctypes.c_int64), ("second_phase", ctypes.c_int64), ("density_path", ctypes.c_int32)]
 

@@ -305,9 +305,15 @@ __global__ void __launch_bounds__(256) k_cell_runs_any(BatchView v, CellPrepBufs
     }
 }
 
-__global__ void k_item_count(BatchView v, CellPrepBufs cb, int kch) {
+// Work items per dense cell; zero for the slots in [ndense, bound) that the
+// scan after it also reads.
+__global__ void k_item_count(BatchView v, CellPrepBufs cb, int kch, int64_t bound) {
     const uint32_t nd = *cb.ndense;
-    for (int64_t dc = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; dc < nd; dc += (int64_t)gridDim.x * blockDim.x) {
+    for (int64_t dc = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; dc < bound; dc += (int64_t)gridDim.x * blockDim.x) {
+        if (dc >= nd) {
+            cb.nitem_c[dc] = 0u;
+            continue;
+        }
         const uint32_t c = cb.dense[dc];
         const uint32_t m = v.cell_start[c + 1] - v.cell_start[c];
         const uint32_t cand = cb.cand[c];
@@ -975,7 +981,7 @@ cudaError_t launch_item_prep(const BatchView& v, const CellPrepBufs& cb, int64_t
                              void* scan_temp, cudaStream_t st) {
     if (ndense_bound <= 0) return cudaMemsetAsync(cb.nitems, 0, sizeof(uint32_t), st);
     const unsigned blocks = (unsigned)std::min<int64_t>(152 * 16, grid_for(ndense_bound, 256));
-    (k_item_count<<<blocks, 256, 0, st>>>(v, cb, kch), note_launch());
+    (k_item_count<<<blocks, 256, 0, st>>>(v, cb, kch, ndense_bound), note_launch());
     return exclusive_scan_u32(cb.nitem_c, cb.item_off, ndense_bound, cb.nitems, scan_temp, st);
 }
 

@@ -124,12 +124,9 @@ struct Tune {
     int qch = 128;          // queries per dense work item: 128, 64 or 32 (more warps per cell)
     int kmax = 4;           // gridded dims at most
     uint32_t bf_rank = 1024;  // open points ranked below this take the brute-force pass
-    int clevel = 0;           // coarse ring: blocks of 2^clevel cells per gridded dim (0: off)
-    uint32_t ccap = 512;      // coarse cells holding more points are not scanned
     int tree_min_d = 9;       // datasets with at least this many dims take the point tree (9: none)
     int hd_cell_factor = 2;   // datasets with d >= hd_min_d: cells of side d_cut / f searched to reach f
     int hd_min_d = 7;
-    int ring2 = 0;            // second ring (cells at distance 2) before the tree search
     int sparse_cand = 512;    // cells of at most 4 points with more candidates than this take the dense path
     int sapprox_path = 0;     // S-Approx-DPC: 0 by the pair counts, 1 all points, 2 picks only
     int sapprox_rho_cells = 2;  // S-Approx-DPC pick path: density by cell (1), one warp per pick (0), the
@@ -210,7 +207,7 @@ Tune tune_for(dpc_ctx* ctx, const std::vector<Input>& in) {
 std::string tune_line(const std::pair<int, int>& sig, const Tune& t) {
     std::ostringstream o;
     o << "dmax=" << sig.first << " nlog=" << sig.second << " kch=" << t.kch << " kmax=" << t.kmax
-      << " bf_rank=" << t.bf_rank << " clevel=" << t.clevel << " ccap=" << t.ccap << " tree_min_d=" << t.tree_min_d
+      << " bf_rank=" << t.bf_rank << " tree_min_d=" << t.tree_min_d
       << " hd_cell_factor=" << t.hd_cell_factor << " hd_min_d=" << t.hd_min_d << " qch=" << t.qch;
     return o.str();
 }
@@ -221,15 +218,14 @@ void load_tune_cache(dpc_ctx* ctx) {
     std::ifstream f(ctx->tune_cache);
     std::string line;
     while (std::getline(f, line)) {
-        int dmax, nlog, kch, kmax, clevel, tmd, hf, hm, qch;
-        unsigned bf, ccap;
+        int dmax, nlog, kch, kmax, tmd, hf, hm, qch;
+        unsigned bf;
         if (std::sscanf(line.c_str(),
-                        "dmax=%d nlog=%d kch=%d kmax=%d bf_rank=%u clevel=%d ccap=%u tree_min_d=%d hd_cell_factor=%d "
-                        "hd_min_d=%d qch=%d",
-                        &dmax, &nlog, &kch, &kmax, &bf, &clevel, &ccap, &tmd, &hf, &hm, &qch) != 11)
+                        "dmax=%d nlog=%d kch=%d kmax=%d bf_rank=%u tree_min_d=%d hd_cell_factor=%d hd_min_d=%d qch=%d",
+                        &dmax, &nlog, &kch, &kmax, &bf, &tmd, &hf, &hm, &qch) != 9)
             continue;
-        if (kch < 32 || kch > (1 << 20) || kmax < 1 || kmax > kMaxGridDims || clevel < 0 || clevel > 8 ||
-            ccap < 1 || tmd < 1 || tmd > 9 || hf < 1 || hf > 3 || hm < 1 || hm > 9 ||
+        if (kch < 32 || kch > (1 << 20) || kmax < 1 || kmax > kMaxGridDims ||
+            tmd < 1 || tmd > 9 || hf < 1 || hf > 3 || hm < 1 || hm > 9 ||
             (qch != 32 && qch != 64 && qch != 128))
             continue;
         Tune t;
@@ -237,8 +233,6 @@ void load_tune_cache(dpc_ctx* ctx) {
         t.kch = kch;
         t.kmax = kmax;
         t.bf_rank = bf;
-        t.clevel = clevel;
-        t.ccap = ccap;
         t.tree_min_d = tmd;
         t.hd_cell_factor = hf;
         t.hd_min_d = hm;
@@ -283,7 +277,7 @@ struct Batch {
     uint32_t class_mask = 0, dim_mask = 0;
     int64_t ncells = 0, ndense = 0, nsparse = 0, nitems = 0, ntree = 0, nbf = 0;
     int64_t cand_pairs = 0;
-    int64_t tree_visits = 0, tree_pairs = 0, ntree2 = 0;
+    int64_t tree_visits = 0, tree_pairs = 0;
     // point tree (datasets with DsDesc::ptree)
     std::vector<int> pt_ds;
     int64_t pt_range[kMaxDims + 1][2] = {};  // per d: [t0, t1) in the point-tree concatenation
@@ -378,7 +372,6 @@ struct Batch {
         if (pend & 2) {
             tree_visits = (int64_t)(s8[4] + ptst[2]);
             tree_pairs = (int64_t)(s8[5] + ptst[3]);
-            ntree2 = (int64_t)s8[6];
             ms[2] = elapsed(8, 9);
             ms[3] = elapsed(9, 10);
             ms[4] = elapsed(10, 11);
@@ -567,7 +560,7 @@ struct Batch {
             DPC_CK(radix_sort_u64((uint64_t*)k0, v0, (uint64_t*)k2, v.perm, (uint64_t*)k1, v1, N, key_bits, temp, st));
         // block-start flags for the datasets whose runs come from the block
         // table; the cell hash serves the others (and the second ring)
-        bool any_blocks = false, need_hash = tune.ring2 != 0;
+        bool any_blocks = false, need_hash = false;
         for (int b = 0; b < B; ++b) {
             any_blocks |= hd[b].sbits > 0;
             need_hash |= hd[b].sbits == 0 && !hd[b].ptree && hd[b].n > 0;
@@ -646,25 +639,21 @@ struct Batch {
             kmask |= (hd[b].R == 1 && hd[b].k >= 1) ? (1u << hd[b].k) << (hd[b].sbits > 0 ? 8 : 0) : 1u;
         DPC_CK(launch_cell_runs(v, cb, ncells, kmask, st));
         DPC_CK(launch_classify_cells(v, cb, ncells, (uint32_t)tune.sparse_cand, temp, st));
-        uint32_t cnts[2] = {0, 0};
+        // the work items of the dense cells, counted over a bound of ncells
+        // slots, so that one wait reads the classes and the items together
+        DPC_CK(dens.get(&cb.nitem_c, ncells + 1));
+        DPC_CK(dens.get(&cb.item_off, ncells + 1));
+        DPC_CK(launch_item_prep(v, cb, ncells, tune.kch, temp, st));
+        uint32_t cnts[3] = {0, 0, 0};
         if (ncells > 0) {
             DPC_CK(cudaMemcpyAsync(&cnts[0], cb.ndense, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
             DPC_CK(cudaMemcpyAsync(&cnts[1], cb.nsparse, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
-            DPC_TRY(sync("cell classes"));
+            DPC_CK(cudaMemcpyAsync(&cnts[2], cb.nitems, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
+            DPC_TRY(sync("cell classes and work items"));
         }
         ndense = cnts[0];
         nsparse = cnts[1];
-        DPC_CK(dens.get(&cb.nitem_c, ndense + 1));
-        DPC_CK(dens.get(&cb.item_off, ndense + 1));
-        DPC_CK(launch_item_prep(v, cb, ndense, tune.kch, temp, st));
-        uint32_t ni = 0;
-        if (ndense > 0) {
-            DPC_CK(cudaMemcpyAsync(&ni, cb.nitems, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
-            DPC_TRY(sync("work items"));
-        } else {
-            DPC_CK(cudaMemsetAsync(cb.nitems, 0, sizeof(uint32_t), st));
-        }
-        nitems = ni;
+        nitems = cnts[2];
         DPC_CK(keep.get(&cb.items, nitems + 1));
         items_filled = false;  // written by the first pass that runs them
         item_prep = cb;
@@ -837,7 +826,7 @@ struct Batch {
 
     // The open points of db.tree_list / db.bf_list (counts in db.ucount[0..1],
     // filled by the stream's previous kernels): tree search and brute force.
-    dpc_status open_points(Arena& tmp, const char* what, bool allow_coarse) {
+    dpc_status open_points(Arena& tmp, const char* what) {
         if (tree_ready) DPC_CK(cudaStreamWaitEvent(st, side_ev[1], 0));  // the tree built ahead
         uint32_t uc[2] = {0, 0};
         DPC_CK(cudaMemcpyAsync(uc, db.ucount, sizeof(uc), cudaMemcpyDeviceToHost, st));
@@ -862,45 +851,6 @@ struct Batch {
             }
             const int64_t nc = ncells;
             db.ncells = nc;
-            // coarse ring over blocks of 2^clevel cells per gridded dim
-            if (allow_coarse && tune.clevel > 0) {
-                db.clevel = tune.clevel;
-                db.ccap = tune.ccap;
-                uint32_t* d_nco = nullptr;
-                void* t4 = nullptr;
-                DPC_CK(tmp.get(&db.cflag, nc));
-                DPC_CK(tmp.get(&db.cidx, nc));
-                DPC_CK(tmp.get(&db.cfirst, nc + 1));
-                DPC_CK(tmp.get(&d_nco, 1));
-                DPC_CK(tmp.get(&t4, scan_temp_bytes(nc)));
-                DPC_CK(launch_coarse_cells(v, db, t4, st));
-                uint32_t nco = 0;
-                {
-                    uint32_t last[2] = {0, 0};
-                    DPC_CK(cudaMemcpyAsync(&last[0], db.cidx + nc - 1, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
-                    DPC_TRY(sync("coarse cells"));
-                    nco = last[0] + 1;  // coarse index of the last cell, plus one
-                }
-                db.ncoarse = nco;
-                const int cbits = ceil_log2((uint64_t)std::max<int64_t>(2 * (int64_t)nco, 2));
-                DPC_CK(tmp.get(&db.chash, (size_t)1 << cbits));
-                db.chmask = (1ull << cbits) - 1;
-                DPC_CK(cudaMemsetAsync(db.chash, 0xff, sizeof(int4) << cbits, st));
-                DPC_CK(launch_coarse_hash(v, db, st));
-                DPC_CK(tmp.get(&db.open2, ntree));
-                DPC_CK(launch_coarse_ring(v, db, dim_mask, ntree, st));
-                db.tree_list = db.open2;
-                db.tcount = db.ucount + 2;
-                db.tclass = nullptr;  // the second list is not grouped by dimension
-            } else if (allow_coarse && tune.ring2) {
-                // the second ring on the fine grid; the first ring's unproven
-                // best (v.best_s) is part of its search
-                DPC_CK(tmp.get(&db.open2, ntree));
-                DPC_CK(launch_ring2(v, db, dim_mask, ntree, st));
-                db.tree_list = db.open2;
-                db.tcount = db.ucount + 2;
-                db.tclass = nullptr;  // the second list is not grouped by dimension
-            }
             if (!tree_ready) {
                 db.dpb = 1;
                 db.compact = 1;
@@ -1009,7 +959,7 @@ struct Batch {
         DPC_CK(tmp.get(&db.tclass, kMaxDims + 1));
         DPC_CK(launch_finalize(v, db, fin_temp, st));
         db.lists_sorted = 1;  // written in position order, grouped by dimension
-        DPC_TRY(open_points(tmp, "ring search", true));
+        DPC_TRY(open_points(tmp, "ring search"));
         db.lists_sorted = 0;
         db.tclass = nullptr;
         mark(11);
@@ -1084,7 +1034,7 @@ struct Batch {
         db.bf_rank = tune.bf_rank;
         DPC_CK(launch_approx_rules(v, w, ab, db, dim_mask, N, st));
         mark(10);
-        DPC_TRY(open_points(tmp, "approximate rules", false));
+        DPC_TRY(open_points(tmp, "approximate rules"));
         mark(11);
         DPC_TRY(finish_stats("approximate dependent points"));
         tmp.release();
@@ -1233,7 +1183,7 @@ struct Batch {
         // that ranks above a pick is a pick (the others have rho 0)
         db.lplist = all_points ? nullptr : sb.plist;
         db.lpstart = all_points ? nullptr : sb.pstart;
-        const dpc_status ost = open_points(tmp, "S-Approx-DPC first phase", false);
+        const dpc_status ost = open_points(tmp, "S-Approx-DPC first phase");
         db.lplist = db.lpstart = nullptr;
         DPC_TRY(ost);
         mark(6);
@@ -1389,12 +1339,9 @@ dpc_status dpc_set_tuning(dpc_ctx* ctx, const char* key, int64_t value) {
     else if (k == "qch" && (value == 32 || value == 64 || value == 128)) t.qch = (int)value;
     else if (k == "kmax" && value >= 1 && value <= dpc::kMaxGridDims) t.kmax = (int)value;
     else if (k == "bf_rank" && value >= 0 && value <= UINT32_MAX) t.bf_rank = (uint32_t)value;
-    else if (k == "clevel" && value >= 0 && value <= 8) t.clevel = (int)value;
-    else if (k == "ccap" && value >= 1 && value <= (1 << 24)) t.ccap = (uint32_t)value;
     else if (k == "tree_min_d" && value >= 1 && value <= 9) t.tree_min_d = (int)value;
     else if (k == "hd_cell_factor" && value >= 1 && value <= 3) t.hd_cell_factor = (int)value;
     else if (k == "hd_min_d" && value >= 1 && value <= 9) t.hd_min_d = (int)value;
-    else if (k == "ring2" && value >= 0 && value <= 1) t.ring2 = (int)value;
     else if (k == "sapprox_path" && value >= 0 && value <= 2) t.sapprox_path = (int)value;
     else if (k == "sapprox_ratio" && value >= 1 && value <= 1024) t.sapprox_ratio = (int)value;
     else if (k == "sapprox_rho_cells" && value >= 0 && value <= 3) t.sapprox_rho_cells = (int)value;
@@ -1419,12 +1366,9 @@ dpc_status dpc_get_tuning(dpc_ctx* ctx, const char* key, int64_t* value) {
     else if (k == "qch") *value = t.qch;
     else if (k == "kmax") *value = t.kmax;
     else if (k == "bf_rank") *value = t.bf_rank;
-    else if (k == "clevel") *value = t.clevel;
-    else if (k == "ccap") *value = t.ccap;
     else if (k == "tree_min_d") *value = t.tree_min_d;
     else if (k == "hd_cell_factor") *value = t.hd_cell_factor;
     else if (k == "hd_min_d") *value = t.hd_min_d;
-    else if (k == "ring2") *value = t.ring2;
     else if (k == "sparse_cand") *value = t.sparse_cand;
     else if (k == "sapprox_path") *value = t.sapprox_path;
     else if (k == "sapprox_ratio") *value = t.sapprox_ratio;
@@ -1635,7 +1579,6 @@ static void fill_info(const Batch& bt, int b, dpc_info* out) {
     out->cand_pairs = bt.cand_pairs;
     out->tree_visits = bt.tree_visits;
     out->tree_pairs = bt.tree_pairs;
-    out->open_after_coarse = bt.ntree2;
     out->pair_mode = h.mode;
     out->dense_pairs = bt.dense_pairs;
     out->ms_rho_dense = bt.ms_rho_dense;
@@ -2029,7 +1972,7 @@ dpc_status dpc_autotune(dpc_ctx* ctx, const dpc_job* jobs, int32_t n_jobs, int32
     // set the warps per cell); hd_min_d with the cell factor: cells of side
     // d_cut / f from that many dims up (2: every dataset, the low-d cell factor)
     std::vector<Knob> knobs = {{"kch", {1024, 2048, 4096}}, {"qch", {128, 64, 32}},
-                               {"bf_rank", {256, 1024, 4096}}, {"clevel", {0, 2}}, {"hd_min_d", {7, 2}}};
+                               {"bf_rank", {256, 1024, 4096}}, {"hd_min_d", {7, 2}}};
     if (sig.first >= 4) knobs.push_back({"kmax", {3, 4}});
     if (sig.first >= 5) knobs.push_back({"tree_min_d", {9, 5}});
     knobs.push_back({"hd_cell_factor", {1, 2}});
@@ -2038,7 +1981,6 @@ dpc_status dpc_autotune(dpc_ctx* ctx, const dpc_job* jobs, int32_t n_jobs, int32
         else if (k == "qch") t.qch = (int)v;
         else if (k == "hd_min_d") t.hd_min_d = (int)v;
         else if (k == "bf_rank") t.bf_rank = (uint32_t)v;
-        else if (k == "clevel") t.clevel = (int)v;
         else if (k == "kmax") t.kmax = (int)v;
         else if (k == "tree_min_d") t.tree_min_d = (int)v;
         else if (k == "hd_cell_factor") t.hd_cell_factor = (int)v;

@@ -243,7 +243,7 @@ cudaError_t launch_rho_picks(const BatchView& v, const CellWork& w, uint32_t cla
 struct DeltaBufs {
     uint32_t* rkeys;      // rank sort keys [N] (u32 or u64 storage)
     uint32_t* rvals;      // [N]
-    uint32_t* ucount;     // [3] device counters: open list, brute list, open after the coarse ring
+    uint32_t* ucount;     // [2] device counters: open list, brute-force list
     uint32_t* tree_list;  // [N] points open after the ring search
     uint8_t* ocode;       // ordered open lists: per point 0 resolved, 1 tree, 2 brute force (else null)
     uint32_t* ocnt;       // their per-block counts [2][blocks] (tree, brute force)
@@ -251,17 +251,6 @@ struct DeltaBufs {
     int lists_sorted;     // 1: tree_list is in position order already
     uint32_t* tclass;     // [9] or null: tree_list grouped by dimension, group d at [tclass[d-1], tclass[d])
     const uint32_t* tcount;  // count of the list the tree search reads
-    // coarse ring (coarse.cu): cells are aligned blocks of 2^clevel grid
-    // cells per gridded dim, contiguous in the Morton-sorted order
-    int clevel;
-    uint32_t ccap;        // coarse cells holding more points are not scanned
-    int64_t ncoarse;
-    uint32_t* cflag;      // [ncells] first fine cell of a coarse cell
-    uint32_t* cidx;       // [ncells] coarse cell of each fine cell
-    uint32_t* cfirst;     // [ncoarse + 1] first fine cell of each coarse cell
-    int4* chash;          // {key lo, key hi, point start, point count}
-    uint64_t chmask;
-    uint32_t* open2;      // [N] points still open after the coarse ring
     uint32_t* bf_list;    // [N]
     int4* rrec;           // [N * 2] records in rank order (prefix only)
     uint32_t* rorig;      // [N]
@@ -299,15 +288,6 @@ cudaError_t launch_ring(const BatchView& v, const CellWork& w, uint32_t class_ma
 // position order (then the caller need not sort them)
 size_t finalize_temp_bytes(int64_t n);
 cudaError_t launch_finalize(const BatchView& v, DeltaBufs db, void* ordered_temp, cudaStream_t st);
-// coarse.cu: coarse cells (after the fine cell table), their hash, and the
-// coarse ring search of the open list (needs db.ncells, tree_list sorted)
-cudaError_t launch_coarse_cells(const BatchView& v, const DeltaBufs& db, void* scan_temp, cudaStream_t st);
-cudaError_t launch_coarse_hash(const BatchView& v, const DeltaBufs& db, cudaStream_t st);
-cudaError_t launch_coarse_ring(const BatchView& v, const DeltaBufs& db, uint32_t dim_mask, int64_t bound,
-                               cudaStream_t st);
-// Second ring on the fine grid (cells at distance 2) for the open list db.tree_list
-// (count db.ucount[0]); the still-open points go to db.open2 (count db.ucount[2]).
-cudaError_t launch_ring2(const BatchView& v, const DeltaBufs& db, uint32_t dim_mask, int64_t bound, cudaStream_t st);
 // tree.cu: build (cell ranges, keys, radix tree, refit) and search
 cudaError_t launch_tree_build(const BatchView& v, const DeltaBufs& db, cudaStream_t st);
 cudaError_t launch_tree_search(const BatchView& v, const DeltaBufs& db, uint32_t dim_mask, int64_t bound,

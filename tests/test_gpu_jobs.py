@@ -302,7 +302,7 @@ def test_autotune_keeps_results_and_writes_cache(dpc, tmp_path):
         jobs = [dpc.Job(ds.points, ds.d_cut, [(ds.rho_min, ds.delta_min)]) for ds in probs]
         rep = ctx.autotune(jobs, repeats=1)
         assert "kch=" in rep and "dmax=" in rep
-        for k in ("kch", "bf_rank", "clevel"):
+        for k in ("kch", "qch", "bf_rank"):
             assert f"{k}={ctx.tuning(k)}" in rep
         with pytest.raises(dpc.DpcError):
             ctx.autotune(jobs, repeats=0)

@@ -174,14 +174,13 @@ SMALL_CUTOFFS = [
 ]
 
 
-@pytest.mark.parametrize("ring2", [0, 1])
 @pytest.mark.parametrize("shape", SMALL_CUTOFFS, ids=lambda s: f"n{s[1]}_d{s[2]}_dc{s[3]}")
-def test_small_cutoffs_bit_exact(dpc, shape, ring2):
+def test_small_cutoffs_bit_exact(dpc, shape):
     """Cutoffs so small that the neighbour runs leave out in-reach cells (no
     point there is within d_cut, but one may be the nearest higher point)."""
     seed, n, d, dc, dom, blobs, spread, dup = shape
     ds = workloads.random_blobs(seed, n, d, dc, domain=dom, blobs=blobs, spread=spread, dup=dup)
-    assert_full_parity(dpc, ds.points, dc, [(1, dc + 1), (2, 3 * dc + 1)], dict(ring2=ring2))
+    assert_full_parity(dpc, ds.points, dc, [(1, dc + 1), (2, 3 * dc + 1)])
 
 
 def test_all_points_identical(dpc):
@@ -327,10 +326,10 @@ def test_plain_5p8m_3d_sampled(dpc):
 
 # ------------------------------------------------------- tuning knobs
 
-@pytest.mark.parametrize("knobs", [dict(clevel=2, ccap=512), dict(clevel=1, ccap=64, bf_rank=0),
-                                   dict(kch=64, bf_rank=100000), dict(kmax=2), dict(kmax=1, clevel=3),
-                                   dict(tree_min_d=3), dict(tree_min_d=1, bf_rank=0), dict(ring2=0),
-                                   dict(ring2=1, bf_rank=0), dict(sparse_cand=0), dict(sparse_cand=2147483647),
+@pytest.mark.parametrize("knobs", [dict(qch=32), dict(qch=64, kch=4096, bf_rank=0),
+                                   dict(kch=64, bf_rank=100000), dict(kmax=2), dict(kmax=1, qch=32),
+                                   dict(tree_min_d=3), dict(tree_min_d=1, bf_rank=0),
+                                   dict(sparse_cand=0), dict(sparse_cand=2147483647),
                                    dict(sparse_cand=20, kch=64), dict(rho_bulk=1)],
                          ids=lambda k: ",".join(f"{a}={b}" for a, b in k.items()))
 def test_tuning_knobs_do_not_change_results(dpc, knobs):
