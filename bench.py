@@ -718,6 +718,9 @@ def run_batched(args):
     dev = torch.device("cuda", local)
     n_tot = sum(p.n for p in probs)
     ctx = dpc.Context(device=local, mode=0, profiling=True)
+    knobs = parse_tune(args.tune)
+    if knobs:
+        ctx.tune(**knobs)
     st = ctx.stream
     djobs = [dpc.Job(torch.from_numpy(p.points).to(dev), p.d_cut, [(p.rho_min, p.delta_min)]) for p in probs]
     hjobs = [dpc.Job(torch.from_numpy(p.points).pin_memory().numpy(), p.d_cut, [(p.rho_min, p.delta_min)])
@@ -790,6 +793,7 @@ def run_batched(args):
             "config": {"workload": "batch_256", "jobs": len(probs), "points": n_tot,
                        "parallelism": f"replicas x{ws}", "l2": "flushed between steps (256 MB write)",
                        "points_per_s": value * n_tot / len(probs), "autotuned": tuned,
+                       **({"tune": knobs} if knobs else {}),
                        "one_at_a_time_jobs_per_s": len(probs) / (alone_ms / 1e3),
                        "batched_over_one_at_a_time": (len(probs) / (total_ms / args.steps / 1e3))
                        / (len(probs) / (alone_ms / 1e3))},

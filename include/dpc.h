@@ -119,9 +119,7 @@ dpc_status dpc_dependent(dpc_ds* ds, int32_t* dep_out, int64_t* delta2_out);
  *               approximated point).
  *   exact_out:  NULL or n uint8: 1 where the dependent point is exact.
  * Host or device memory, as for dpc_density's is_device. Later dpc_label
- * calls use these dependent points until dpc_dependent is called.
- * Errors: DPC_ERR_STATE for a dataset on the point tree (tree_min_d at or
- * below its d). */
+ * calls use these dependent points until dpc_dependent is called. */
 dpc_status dpc_dependent_approx(dpc_ds* ds, int32_t* dep_out, int64_t* delta2_out, uint8_t* exact_out);
 
 /* S-Approx-DPC (Section 5): local densities and dependent points of one
@@ -145,8 +143,7 @@ dpc_status dpc_dependent_approx(dpc_ds* ds, int32_t* dep_out, int64_t* delta2_ou
  *   dep_out, delta2_out: NULL or n int32 / int64, as for dpc_dependent.
  *   pick_out:   NULL or n uint8: 1 for the picks.
  * Host or device memory, as for is_device.
- * Errors: those of dpc_density; DPC_ERR_STATE when tree_min_d is at or
- * below d (no grid). */
+ * Errors: those of dpc_density. */
 dpc_status dpc_sapprox(dpc_ctx* ctx, const int32_t* points, int64_t n, int32_t d, int64_t d_cut, int64_t eps_num,
                        int64_t eps_den, int is_device, dpc_ds** out, int32_t* rho_out, int32_t* dep_out,
                        int64_t* delta2_out, uint8_t* pick_out);
@@ -262,10 +259,11 @@ dpc_status dpc_set_profiling(dpc_ctx* ctx, int on);
  *   "kmax"    gridded dimensions at most, 1 .. 4 (default 4)
  *   "bf_rank" points still open after the ring search whose rank is below
  *             this take the brute-force pass (default 1024)
- *   "tree_min_d"  datasets with at least this many dimensions skip the grid
- *             and take the point tree (a kd-tree-like search over all
- *             dimensions), 1 .. 9 (default 9: never; on the blob workloads
- *             the projected grid is faster at every d measured, 5 to 8)
+ *   "tree_warp"  the tree search for the other open points: 1 the 32 lanes
+ *             of a warp walk the tree together over 32 neighbouring open
+ *             points, 0 one lane per point, 2 the first for d >= 5 and the
+ *             second below (default 2: on 1M x 8 the warp form takes 22 ms
+ *             against 29, on 5.8M x 3 6.0 ms against 2.5)
  *   "hd_cell_factor"  f for datasets with d >= hd_min_d: grid cells of
  *             side ceil(d_cut / f), neighbours searched f cells away (a finer
  *             grid, fewer candidate pairs, more neighbour cells), 1 .. 3
@@ -403,8 +401,8 @@ dpc_status dpc_last_batch_info(dpc_ctx* ctx, dpc_info* out);
  * one batch under candidate settings of the knobs that change speed only
  * (kch and qch, the candidates and queries per dense work item, i.e. the
  * warps per cell; bf_rank; hd_min_d with hd_cell_factor, the grid's
- * cell factor, tried for every dataset's d; kmax when some d >= 4;
- * tree_min_d when some d >= 5): coordinate descent from the context's current knobs, each
+ * cell factor, tried for every dataset's d; kmax when some d >= 4):
+ * coordinate descent from the context's current knobs, each
  * setting timed as the best of `repeats` (1 .. 100) synchronous runs, a
  * change kept only when it is at least 2% faster. The fastest setting
  * becomes the context's knobs and its entry for the sample's signature (the

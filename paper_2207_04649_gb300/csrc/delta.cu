@@ -350,9 +350,7 @@ __global__ void __launch_bounds__(kFinThreads) k_finalize(BatchView v, DeltaBufs
         const DsDesc& ds = v.desc[b];
         const uint2 ro = v.ro_s[p];
         const int64_t g = ds.pt_off + ro.y;
-        if (ds.ptree) {
-            // the point-tree search handles all of this dataset's points
-        } else if (ro.x == 0u) {  // the densest point: no dependent point, delta = infinity
+        if (ro.x == 0u) {  // the densest point: no dependent point, delta = infinity
             v.dep[g] = -1;
             v.delta2[g] = INT64_MAX;
         } else {

@@ -19,7 +19,6 @@ namespace dpc {
 constexpr int kMaxDims = 8;
 constexpr int kMaxGridDims = 4;
 constexpr uint64_t kEmptyKey = ~0ull;
-constexpr int kLeaf = 16;          // points per leaf of the point tree
 
 // Per-dataset description, shared by host and device.
 struct DsDesc {
@@ -32,8 +31,6 @@ struct DsDesc {
     uint64_t cbase;       // cell-key base of this dataset
     int64_t rho_min;      // label query
     int64_t delta_min2;   // delta_min^2
-    int64_t leaf_off;     // point tree: first leaf slot of this dataset in the batch
-    int64_t node_off;     // point tree: first node (heap index 0) of this dataset
     int32_t n, d;
     int32_t dp;           // int4 records per point: 1 (d <= 4) or 2 (d <= 8)
     int32_t k;            // gridded dims
@@ -46,8 +43,6 @@ struct DsDesc {
     int32_t mode;         // density pair test: 0 direct 32-bit, 1 direct 64-bit,
                           // 2 expanded 32-bit, |c|^2 + |q|^2 - T - 2 q.c wrapping mod 2^32 (d <= 4)
     int32_t lo[kMaxDims]; // smallest coordinate per dim
-    int32_t h;            // point tree height: 2^h leaf slots
-    int32_t nleaf;        // point tree leaves (ceil(n / kLeaf))
     int32_t rbits;        // bits of the density key in the rank sort
     uint64_t dmask[kMaxGridDims];  // Morton bits of each gridded dim
     int32_t a_side;       // Approx-DPC grid: integer side max(1, floor(d_cut / sqrt(d)));
@@ -56,9 +51,7 @@ struct DsDesc {
     int32_t prune;        // 1: the neighbour runs may leave out in-reach cells whose box is at least
                           // d_cut away (no point there counts in rho, but one may be nearer than the
                           // searched block's outside for the dependent-point search)
-    int32_t ptree;        // 1: no grid; the point tree gives density and dependent points
-    int32_t tb;           // point tree: Morton bits per dim of the sort key
-    int32_t span[kMaxDims];  // point tree: max - min + 1 per dim
+    int32_t span[kMaxDims];  // largest - smallest coordinate + 1 per dim
     int32_t sbits;        // bits of a block's local Morton code in the block table (a block is 2^(sbits / k)
                           // cells per gridded dim); 0: this dataset's neighbour runs use the cell hash
 };

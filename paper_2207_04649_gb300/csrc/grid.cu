@@ -93,10 +93,7 @@ __global__ void __launch_bounds__(256) k_minmax(BatchView v, int32_t* __restrict
 }
 
 // Cell key of every input point: key base of its dataset + Morton code of
-// its cell coordinates in the gridded dimensions. A dataset on the point
-// tree instead takes the Morton code of all its coordinates, each quantized
-// to tb bits over the dataset's span, so that runs of kLeaf consecutive
-// sorted points are compact leaves.
+// its cell coordinates in the gridded dimensions.
 template <typename K>
 __global__ void k_cell_keys(BatchView v, K* __restrict__ keys, uint32_t* __restrict__ vals) {
     const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -104,20 +101,13 @@ __global__ void k_cell_keys(BatchView v, K* __restrict__ keys, uint32_t* __restr
     const int b = find_ds(v.pt_off, v.B, g);
     const DsDesc& ds = v.desc[b];
     const int32_t* x = v.in + ds.in_off + (g - ds.pt_off) * ds.d;
-    if (ds.ptree) {
-        int32_t q[kMaxDims];
-        for (int k = 0; k < ds.d; ++k)
-            q[k] = (int32_t)((((uint64_t)(uint32_t)(x[k] - ds.lo[k])) << ds.tb) / (uint64_t)(uint32_t)ds.span[k]);
-        keys[g] = (K)(ds.cbase + morton(q, ds.d, ds.tb));
-    } else {
-        int32_t c[kMaxGridDims] = {0, 0, 0, 0};
-        const int k = ds.k;
-        const uint32_t sd = (uint32_t)ds.s;
+    int32_t c[kMaxGridDims] = {0, 0, 0, 0};
+    const int k = ds.k;
+    const uint32_t sd = (uint32_t)ds.s;
 #pragma unroll
-        for (int j = 0; j < kMaxGridDims; ++j)
-            if (j < k) c[j] = (int32_t)((uint32_t)(x[ds.gdim[j]] - ds.origin[j]) / sd);
-        keys[g] = (K)(ds.cbase + morton_k(c, k));
-    }
+    for (int j = 0; j < kMaxGridDims; ++j)
+        if (j < k) c[j] = (int32_t)((uint32_t)(x[ds.gdim[j]] - ds.origin[j]) / sd);
+    keys[g] = (K)(ds.cbase + morton_k(c, k));
     vals[g] = (uint32_t)g;
 }
 
@@ -146,9 +136,8 @@ __global__ void k_gather(BatchView v, const K* __restrict__ skeys, uint32_t* __r
     if (ds.dp == 2) r[1] = make_int4(c[4], c[5], c[6], c[7]);
     v.pos_of[g] = (uint32_t)p;
     v.key[p] = (uint64_t)skeys[p];
-    // a point-tree dataset is one cell (its grid work is skipped)
     const bool first = p == 0 || p == ds.pt_off;
-    flag[p] = (first || (!ds.ptree && skeys[p] != skeys[p - 1])) ? 1u : 0u;
+    flag[p] = (first || skeys[p] != skeys[p - 1]) ? 1u : 0u;
     if (bflag)
         bflag[p] = ds.sbits > 0 && (first || (((uint64_t)skeys[p] - ds.cbase) >> ds.sbits) !=
                                                  (((uint64_t)skeys[p - 1] - ds.cbase) >> ds.sbits))

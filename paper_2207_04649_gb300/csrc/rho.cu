@@ -47,14 +47,12 @@ __global__ void k_classify(BatchView v, CellPrepBufs cb, int64_t bound, uint32_t
     for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < bound; c += (int64_t)gridDim.x * blockDim.x) {
         uint32_t dense = 0, sparse = 0;
         if (c < nc) {
-            const uint32_t cs = v.cell_start[c], m = v.cell_start[c + 1] - cs;
-            if (!v.desc[find_ds(v.pt_off, v.B, cs)].ptree) {  // point-tree datasets have no grid work
-                const uint32_t cand = cb.cand[c];
-                dense = m > (uint32_t)kSparseMax || cand > sparse_cand;
-                sparse = !dense;
-                if (dense) pairs += (unsigned long long)m * cand;
-                else spairs += (unsigned long long)m * cand;
-            }
+            const uint32_t m = v.cell_start[c + 1] - v.cell_start[c];
+            const uint32_t cand = cb.cand[c];
+            dense = m > (uint32_t)kSparseMax || cand > sparse_cand;
+            sparse = !dense;
+            if (dense) pairs += (unsigned long long)m * cand;
+            else spairs += (unsigned long long)m * cand;
         }
         cb.dflag[c] = dense;
         cb.sflag[c] = sparse;
@@ -280,11 +278,6 @@ __global__ void __launch_bounds__(256) k_cell_runs_any(BatchView v, CellPrepBufs
         const int b = find_ds(v.pt_off, v.B, cs);
         const DsDesc& ds = v.desc[b];
         if (ds.R == 1 && ds.k >= 1) continue;
-        if (ds.ptree) {
-            cb.nruns[c] = 0;
-            cb.cand[c] = 0;
-            continue;
-        }
         const int4* r0 = v.rec + ds.rec_off + ((int64_t)cs - ds.pt_off) * ds.dp;
         int32_t cc[kMaxGridDims];
         for (int j = 0; j < ds.k; ++j) cc[j] = cell_coord(ds, j, rec_coord(r0, ds.gdim[j]));

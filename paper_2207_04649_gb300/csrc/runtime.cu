@@ -124,7 +124,7 @@ struct Tune {
     int qch = 128;          // queries per dense work item: 128, 64 or 32 (more warps per cell)
     int kmax = 4;           // gridded dims at most
     uint32_t bf_rank = 1024;  // open points ranked below this take the brute-force pass
-    int tree_min_d = 9;       // datasets with at least this many dims take the point tree (9: none)
+    int tree_warp = 2;        // tree search: 1 warp-cooperative, 0 one lane per point, 2 warp for d >= 5
     int hd_cell_factor = 2;   // datasets with d >= hd_min_d: cells of side d_cut / f searched to reach f
     int hd_min_d = 7;
     int sparse_cand = 512;    // cells of at most 4 points with more candidates than this take the dense path
@@ -207,7 +207,7 @@ Tune tune_for(dpc_ctx* ctx, const std::vector<Input>& in) {
 std::string tune_line(const std::pair<int, int>& sig, const Tune& t) {
     std::ostringstream o;
     o << "dmax=" << sig.first << " nlog=" << sig.second << " kch=" << t.kch << " kmax=" << t.kmax
-      << " bf_rank=" << t.bf_rank << " tree_min_d=" << t.tree_min_d
+      << " bf_rank=" << t.bf_rank
       << " hd_cell_factor=" << t.hd_cell_factor << " hd_min_d=" << t.hd_min_d << " qch=" << t.qch;
     return o.str();
 }
@@ -218,14 +218,12 @@ void load_tune_cache(dpc_ctx* ctx) {
     std::ifstream f(ctx->tune_cache);
     std::string line;
     while (std::getline(f, line)) {
-        int dmax, nlog, kch, kmax, tmd, hf, hm, qch;
+        int dmax, nlog, kch, kmax, hf, hm, qch;
         unsigned bf;
-        if (std::sscanf(line.c_str(),
-                        "dmax=%d nlog=%d kch=%d kmax=%d bf_rank=%u tree_min_d=%d hd_cell_factor=%d hd_min_d=%d qch=%d",
-                        &dmax, &nlog, &kch, &kmax, &bf, &tmd, &hf, &hm, &qch) != 9)
+        if (std::sscanf(line.c_str(), "dmax=%d nlog=%d kch=%d kmax=%d bf_rank=%u hd_cell_factor=%d hd_min_d=%d qch=%d",
+                        &dmax, &nlog, &kch, &kmax, &bf, &hf, &hm, &qch) != 8)
             continue;
-        if (kch < 32 || kch > (1 << 20) || kmax < 1 || kmax > kMaxGridDims ||
-            tmd < 1 || tmd > 9 || hf < 1 || hf > 3 || hm < 1 || hm > 9 ||
+        if (kch < 32 || kch > (1 << 20) || kmax < 1 || kmax > kMaxGridDims || hf < 1 || hf > 3 || hm < 1 || hm > 9 ||
             (qch != 32 && qch != 64 && qch != 128))
             continue;
         Tune t;
@@ -233,7 +231,6 @@ void load_tune_cache(dpc_ctx* ctx) {
         t.kch = kch;
         t.kmax = kmax;
         t.bf_rank = bf;
-        t.tree_min_d = tmd;
         t.hd_cell_factor = hf;
         t.hd_min_d = hm;
         ctx->tuned[{dmax, nlog}] = t;
@@ -278,10 +275,6 @@ struct Batch {
     int64_t ncells = 0, ndense = 0, nsparse = 0, nitems = 0, ntree = 0, nbf = 0;
     int64_t cand_pairs = 0;
     int64_t tree_visits = 0, tree_pairs = 0;
-    // point tree (datasets with DsDesc::ptree)
-    std::vector<int> pt_ds;
-    int64_t pt_range[kMaxDims + 1][2] = {};  // per d: [t0, t1) in the point-tree concatenation
-    PtBufs pb{};
     unsigned long long* d_stats = nullptr;
     uint32_t* d_counters = nullptr;  // [32] rho + [32] ring work counters
     int out_is_device = 0;
@@ -356,22 +349,21 @@ struct Batch {
     // the last wait; one wait for the stream when any are pending.
     dpc_status settle() {
         if (!stats_pending) return DPC_OK;
-        unsigned long long s8[8] = {0, 0, 0, 0, 0, 0, 0, 0}, ptst[4] = {0, 0, 0, 0};
+        unsigned long long s8[8] = {0, 0, 0, 0, 0, 0, 0, 0};
         DPC_CK(cudaMemcpyAsync(s8, d_stats, sizeof(s8), cudaMemcpyDeviceToHost, st));
-        if (pb.m > 0) DPC_CK(cudaMemcpyAsync(ptst, pb.stats, sizeof(ptst), cudaMemcpyDeviceToHost, st));
         DPC_TRY(sync("statistics"));
         const int pend = stats_pending;
         stats_pending = 0;
         if (pend & 1) {
-            cand_pairs = (int64_t)(s8[0] + s8[1] + ptst[1]);
+            cand_pairs = (int64_t)(s8[0] + s8[1]);
             dense_pairs = (int64_t)s8[0];
             ms[0] = elapsed(0, 1);
             ms[1] = elapsed(1, 2);
             ms_rho_dense = elapsed(1, 4);
         }
         if (pend & 2) {
-            tree_visits = (int64_t)(s8[4] + ptst[2]);
-            tree_pairs = (int64_t)(s8[5] + ptst[3]);
+            tree_visits = (int64_t)s8[4];
+            tree_pairs = (int64_t)s8[5];
             ms[2] = elapsed(8, 9);
             ms[3] = elapsed(9, 10);
             ms[4] = elapsed(10, 11);
@@ -396,8 +388,6 @@ struct Batch {
         DPC_CK(launch_rho(v, w, class_mask, nitems, nsparse, d_counters, 1 | (tune.rho_bulk ? 4 : 0), st));
         mark(4);
         DPC_CK(launch_rho(v, w, class_mask, nitems, nsparse, d_counters, 2, st));
-        for (int d = 1; d <= kMaxDims; ++d)
-            DPC_CK(launch_rho_ptree(v, pb, d, pt_range[d][0], pt_range[d][1], st));
         mark(2);
         DPC_CK(launch_rho_scatter(v, st));
         return DPC_OK;
@@ -466,7 +456,6 @@ struct Batch {
         DPC_CK(cudaMemcpyAsync(mm.data(), d_mm, mm.size() * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
         DPC_TRY(sync("bounding boxes"));
         uint64_t cbase = 0;
-        int64_t leaf_slots = 0;
         h_slot_off.assign(B + 1, 0);
         for (int b = 0; b < B; ++b) {
             DsDesc& ds = hd[b];
@@ -476,47 +465,8 @@ struct Batch {
                     return fail(DPC_ERR_INVALID_ARG, "coordinates must lie in [0, 2^30)");
             }
             DPC_TRY(plan(b, mm.data() + (size_t)b * kMaxDims * 2, cbase));
-            if (ds.ptree) continue;
             class_mask |= 1u << (3 * (ds.d - 1) + ds.mode);
             dim_mask |= 1u << (ds.d - 1);
-        }
-        // point-tree datasets, grouped by dimension: leaf slots and nodes
-        pt_ds.clear();
-        for (int d = 1; d <= kMaxDims; ++d)
-            for (int b = 0; b < B; ++b)
-                if (hd[b].ptree && hd[b].d == d) pt_ds.push_back(b);
-        std::vector<int64_t> pt_leaf(pt_ds.size() + 1, 0), pt_pts(pt_ds.size() + 1, 0);
-        for (int d = 0; d <= kMaxDims; ++d) pt_range[d][0] = pt_range[d][1] = 0;
-        for (size_t j = 0; j < pt_ds.size(); ++j) {
-            DsDesc& ds = hd[pt_ds[j]];
-            ds.leaf_off = pt_leaf[j];
-            ds.node_off = 2 * pt_leaf[j];
-            pt_leaf[j + 1] = pt_leaf[j] + (1ll << ds.h);
-            pt_pts[j + 1] = pt_pts[j] + ds.n;
-            if (pt_range[ds.d][1] == 0) pt_range[ds.d][0] = pt_pts[j];
-            pt_range[ds.d][1] = pt_pts[j + 1];
-        }
-        leaf_slots = pt_leaf.back();
-        pb = PtBufs{};
-        pb.m = (int)pt_ds.size();
-        pb.nslots = leaf_slots;
-        if (pb.m > 0) {
-            int32_t* d_idx = nullptr;
-            int64_t *d_leaf = nullptr, *d_pts = nullptr;
-            DPC_CK(keep.get(&d_idx, pb.m));
-            DPC_CK(keep.get(&d_leaf, pb.m + 1));
-            DPC_CK(keep.get(&d_pts, pb.m + 1));
-            DPC_CK(keep.get(&pb.nodes, (size_t)2 * leaf_slots * kPtRec));
-            DPC_CK(keep.get(&pb.flag, leaf_slots));
-            DPC_CK(keep.get(&pb.stats, 4));
-            DPC_CK(cudaMemcpyAsync(d_idx, pt_ds.data(), sizeof(int32_t) * pb.m, cudaMemcpyHostToDevice, st));
-            DPC_CK(cudaMemcpyAsync(d_leaf, pt_leaf.data(), sizeof(int64_t) * (pb.m + 1), cudaMemcpyHostToDevice, st));
-            DPC_CK(cudaMemcpyAsync(d_pts, pt_pts.data(), sizeof(int64_t) * (pb.m + 1), cudaMemcpyHostToDevice, st));
-            DPC_CK(cudaMemsetAsync(pb.flag, 0, sizeof(uint32_t) * leaf_slots, st));
-            DPC_CK(cudaMemsetAsync(pb.stats, 0, 4 * sizeof(unsigned long long), st));
-            pb.ds_idx = d_idx;
-            pb.leaf_off = d_leaf;
-            pb.pt_off = d_pts;
         }
         DPC_TRY(upload_desc());
         const int key_bits = bits_for(cbase > 0 ? cbase - 1 : 0);
@@ -563,7 +513,7 @@ struct Batch {
         bool any_blocks = false, need_hash = false;
         for (int b = 0; b < B; ++b) {
             any_blocks |= hd[b].sbits > 0;
-            need_hash |= hd[b].sbits == 0 && !hd[b].ptree && hd[b].n > 0;
+            need_hash |= hd[b].sbits == 0 && hd[b].n > 0;
         }
         uint32_t *bflag = nullptr, *bidx = nullptr, *d_nblocks = nullptr;
         if (any_blocks) {
@@ -579,7 +529,6 @@ struct Batch {
             DPC_TRY(sync("cell count"));
         }
         ncells = nc;
-        DPC_CK(launch_pt_build(v, pb, st));
 
         // block table (load factor <= 1/2): 32-byte slots {key, first cell}, {occupancy}
         v.sbhash = nullptr;
@@ -685,33 +634,6 @@ struct Batch {
         const int f = ds.d >= tn.hd_min_d ? tn.hd_cell_factor : 1;
         ds.R = f;
         ds.s = (ds.d_cut + f - 1) / f;
-        ds.ptree = 0;
-        if (ds.n > 0 && ds.d >= tn.tree_min_d) {
-            // point tree: no grid; the sort key is the Morton code of all d
-            // coordinates, tb bits each (at most 48 bits per dataset)
-            ds.ptree = 1;
-            ds.k = 0;
-            ds.mbits = 0;
-            ds.tb = std::min(10, 48 / ds.d);
-            for (int c = 0; c < ds.d; ++c) {
-                ds.lo[c] = mm[2 * c];
-                ds.span[c] = mm[2 * c + 1] - mm[2 * c] + 1;
-            }
-            for (int j = 0; j < kMaxGridDims; ++j) {
-                ds.dmask[j] = 0;
-                ds.gdim[j] = 0;
-                ds.origin[j] = 0;
-                ds.ext[j] = 1;
-            }
-            ds.cbase = cbase;
-            cbase += 1ull << (ds.d * ds.tb);
-            ds.w32 = 0;
-            ds.mode = 1;
-            ds.rbits = bits_for((uint64_t)ds.n);
-            ds.nleaf = (int32_t)((ds.n + kLeaf - 1) / kLeaf);
-            ds.h = ceil_log2((uint64_t)ds.nleaf);
-            return DPC_OK;
-        }
         // grid the dims with the most cells (a dim with one cell filters nothing)
         struct Dim {
             int dim;
@@ -870,7 +792,7 @@ struct Batch {
             }
             DPC_CK(tmp.get(&db.stats, 2));
             DPC_CK(cudaMemsetAsync(db.stats, 0, 2 * sizeof(unsigned long long), st));
-            DPC_CK(launch_tree_search(v, db, dim_mask, ntree, st));
+            DPC_CK(launch_tree_search(v, db, dim_mask, ntree, tune.tree_warp, st));
         }
         if (nbf > 0) {
             DPC_CK(tmp.get(&db.rrec, 2 * N));
@@ -940,12 +862,6 @@ struct Batch {
         DPC_CK(cudaMemsetAsync(v.best_s, 0xff, sizeof(unsigned long long) * std::max<int64_t>(N, 1), st));
         DPC_TRY(prebuild_tree(tmp));
         DPC_CK(launch_ring(v, w, class_mask, nitems, nsparse, d_counters + 32, st));
-        if (pb.m > 0) {
-            DPC_CK(cudaMemsetAsync(pb.flag, 0, sizeof(uint32_t) * pb.nslots, st));
-            DPC_CK(launch_pt_minrank(v, pb, st));
-            for (int d = 1; d <= kMaxDims; ++d)
-                DPC_CK(launch_delta_ptree(v, pb, d, pt_range[d][0], pt_range[d][1], st));
-        }
         mark(10);
 
         DPC_CK(tmp.get(&db.ucount, 4));
@@ -983,7 +899,6 @@ struct Batch {
         int bshift = 0;
         for (int b = 0; b < B; ++b) {
             DsDesc& ds = hd[b];
-            if (ds.ptree) return fail(DPC_ERR_STATE, "Approx-DPC needs the grid: set tree_min_d above the dimension");
             const int64_t q = ds.d_cut2 / ds.d;
             int64_t s = (int64_t)std::sqrt((double)q);
             while (s > 0 && s * s > q) --s;
@@ -1053,8 +968,6 @@ struct Batch {
         int bshift = 0;
         for (int b = 0; b < B; ++b) {
             DsDesc& ds = hd[b];
-            if (ds.ptree)
-                return fail(DPC_ERR_STATE, "S-Approx-DPC needs the grid: set tree_min_d above the dimension");
             ds.a_side = (int32_t)std::min<int64_t>(sapprox_side(ds.d_cut, ds.d, eps_num[b], eps_den[b]), 1ll << 30);
             int off = 0;
             for (int k = 0; k < kMaxDims; ++k) {
@@ -1339,7 +1252,7 @@ dpc_status dpc_set_tuning(dpc_ctx* ctx, const char* key, int64_t value) {
     else if (k == "qch" && (value == 32 || value == 64 || value == 128)) t.qch = (int)value;
     else if (k == "kmax" && value >= 1 && value <= dpc::kMaxGridDims) t.kmax = (int)value;
     else if (k == "bf_rank" && value >= 0 && value <= UINT32_MAX) t.bf_rank = (uint32_t)value;
-    else if (k == "tree_min_d" && value >= 1 && value <= 9) t.tree_min_d = (int)value;
+    else if (k == "tree_warp" && value >= 0 && value <= 2) t.tree_warp = (int)value;
     else if (k == "hd_cell_factor" && value >= 1 && value <= 3) t.hd_cell_factor = (int)value;
     else if (k == "hd_min_d" && value >= 1 && value <= 9) t.hd_min_d = (int)value;
     else if (k == "sapprox_path" && value >= 0 && value <= 2) t.sapprox_path = (int)value;
@@ -1366,7 +1279,7 @@ dpc_status dpc_get_tuning(dpc_ctx* ctx, const char* key, int64_t* value) {
     else if (k == "qch") *value = t.qch;
     else if (k == "kmax") *value = t.kmax;
     else if (k == "bf_rank") *value = t.bf_rank;
-    else if (k == "tree_min_d") *value = t.tree_min_d;
+    else if (k == "tree_warp") *value = t.tree_warp;
     else if (k == "hd_cell_factor") *value = t.hd_cell_factor;
     else if (k == "hd_min_d") *value = t.hd_min_d;
     else if (k == "sparse_cand") *value = t.sparse_cand;
@@ -1974,7 +1887,6 @@ dpc_status dpc_autotune(dpc_ctx* ctx, const dpc_job* jobs, int32_t n_jobs, int32
     std::vector<Knob> knobs = {{"kch", {1024, 2048, 4096}}, {"qch", {128, 64, 32}},
                                {"bf_rank", {256, 1024, 4096}}, {"hd_min_d", {7, 2}}};
     if (sig.first >= 4) knobs.push_back({"kmax", {3, 4}});
-    if (sig.first >= 5) knobs.push_back({"tree_min_d", {9, 5}});
     knobs.push_back({"hd_cell_factor", {1, 2}});
     auto with = [](dpc::Tune t, const std::string& k, int64_t v) {
         if (k == "kch") t.kch = (int)v;
@@ -1982,7 +1894,6 @@ dpc_status dpc_autotune(dpc_ctx* ctx, const dpc_job* jobs, int32_t n_jobs, int32
         else if (k == "hd_min_d") t.hd_min_d = (int)v;
         else if (k == "bf_rank") t.bf_rank = (uint32_t)v;
         else if (k == "kmax") t.kmax = (int)v;
-        else if (k == "tree_min_d") t.tree_min_d = (int)v;
         else if (k == "hd_cell_factor") t.hd_cell_factor = (int)v;
         return t;
     };

@@ -290,36 +290,12 @@ size_t finalize_temp_bytes(int64_t n);
 cudaError_t launch_finalize(const BatchView& v, DeltaBufs db, void* ordered_temp, cudaStream_t st);
 // tree.cu: build (cell ranges, keys, radix tree, refit) and search
 cudaError_t launch_tree_build(const BatchView& v, const DeltaBufs& db, cudaStream_t st);
+// warp: 1 the warp-cooperative search, 0 one lane per open point, 2 the
+// warp-cooperative search for d >= 5 only
 cudaError_t launch_tree_search(const BatchView& v, const DeltaBufs& db, uint32_t dim_mask, int64_t bound,
-                               cudaStream_t st);
+                               int warp, cudaStream_t st);
 cudaError_t launch_bruteforce(const BatchView& v, const DeltaBufs& db, uint32_t dim_mask, int64_t bound,
                               cudaStream_t st);
-
-// ptree.cu: the point tree of datasets with ungridded dims (DsDesc::ptree).
-// Each such dataset's points are sorted by the Morton code of all their
-// coordinates; leaf j holds sorted points [j * kLeaf, (j + 1) * kLeaf) and
-// the tree over the 2^h leaf slots is complete, in heap order (node i has
-// children 2i + 1 and 2i + 2, leaves at 2^h - 1 + j).
-constexpr int kPtRec = 5;  // int4 per node: lo (2), hi (2), {smallest rank, count, first point, 0}
-struct PtBufs {
-    int m;                   // point-tree datasets in the batch
-    const int32_t* ds_idx;   // [m] their dataset indices, in order of d
-    const int64_t* leaf_off; // [m+1] prefix of their leaf slots (2^h)
-    const int64_t* pt_off;   // [m+1] prefix of their point counts
-    int64_t nslots;          // leaf slots in all
-    int4* nodes;             // node records, dataset b's heap at node_off
-    uint32_t* flag;          // [nslots] refit arrival counters (zeroed before each refit)
-    unsigned long long* stats;  // [4] density: nodes, pair tests; dependent: nodes, pair tests
-};
-// Boxes and counts (after the sorted records exist).
-cudaError_t launch_pt_build(const BatchView& v, const PtBufs& pb, cudaStream_t st);
-// Smallest rank per node (after ro_s exists).
-cudaError_t launch_pt_minrank(const BatchView& v, const PtBufs& pb, cudaStream_t st);
-// Density and dependent points of the point-tree datasets of dimension d,
-// whose points are [t0, t1) in the concatenation the prefix pt_off counts.
-cudaError_t launch_rho_ptree(const BatchView& v, const PtBufs& pb, int d, int64_t t0, int64_t t1, cudaStream_t st);
-cudaError_t launch_delta_ptree(const BatchView& v, const PtBufs& pb, int d, int64_t t0, int64_t t1,
-                               cudaStream_t st);
 
 // approx.cu: Approx-DPC's dependent points (Section 4.3) on the grid of side
 // d_cut / sqrt(d). The points are sorted again by that grid's keys; per cell

@@ -163,15 +163,12 @@ __global__ void k_leaves(BatchView v, DeltaBufs db) {
         const bool valid = c < db.ncells;
         int b = 0;
         uint32_t p0 = 0, p1 = 0;
-        bool big = false, pt = false;
+        bool big = false;
         if (valid) {
             b = find_off(db.cell_off, v.B, c);
             p0 = db.lplist ? db.lpstart[c] : v.cell_start[c];
             p1 = db.lplist ? db.lpstart[c + 1] : v.cell_start[c + 1];
-            // a point-tree dataset's single cell stays empty here (its points
-            // are never searched through this tree)
-            pt = v.desc[b].ptree != 0;
-            big = !pt && p1 - p0 > kLeafLane;
+            big = p1 - p0 > kLeafLane;
         }
         if (valid && !big) {
             const DsDesc& ds = v.desc[b];
@@ -182,7 +179,7 @@ __global__ void k_leaves(BatchView v, DeltaBufs db) {
                 hi[k] = INT32_MIN;
             }
             uint32_t mr = 0xffffffffu;
-            for (uint32_t p = p0; p < p1 && !pt; ++p) leaf_add(v, ds, db.lplist ? db.lplist[p] : p, lo, hi, mr);
+            for (uint32_t p = p0; p < p1; ++p) leaf_add(v, ds, db.lplist ? db.lplist[p] : p, lo, hi, mr);
             write_leaf(db, c, lo, hi, mr, p0, p1);
         }
         unsigned bigm = __ballot_sync(0xffffffffu, big);
@@ -497,6 +494,199 @@ __global__ void __launch_bounds__(128) k_tree_search(BatchView v, DeltaBufs db) 
     }
 }
 
+// Warp-cooperative form of the same search. The 32 lanes of a warp take 32
+// consecutive entries of the open list (in position order, so mostly
+// neighbouring points) and walk their dataset's tree together: a node record
+// is loaded once for the warp (every lane reads the same address) and every
+// lane tests it against its own point, rank and best distance; the warp
+// enters a subtree when any lane has it in reach, and a lane takes part only
+// in the subtrees in its own reach, so every lane's result is that of its own
+// pruned search. Of two children both in reach, the one nearer for more of
+// the lanes is entered first; the other is stacked with the lanes' mask and
+// each lane's distance bound (shared memory). A leaf's points are loaded by
+// the lanes together and broadcast by shuffles.
+constexpr int kWStack = 42;  // cell keys have at most 40 bits: at most 40 internal levels
+constexpr int kWWarps = 4;   // warps per block
+
+template <int D>
+__device__ __forceinline__ long long w_test(const DeltaBufs& db, bool compact, int dpb, int32_t ref,
+                                            const int32_t (&x)[D], uint32_t rank, int4& meta) {
+    if (compact) {
+        uint32_t link;
+        const long long d = node_test_c<D>(db.nodes + rec_of(db, ref) * 2, x, rank, link);
+        meta = make_int4(0, (int)link, 0, 0);
+        return d;
+    }
+    return node_test<D>(db.nodes + rec_of(db, ref) * (2 * dpb + 1), dpb, x, rank, meta);
+}
+
+template <int D>
+__global__ void __launch_bounds__(kWWarps * 32) k_tree_search_warp(BatchView v, DeltaBufs db) {
+    constexpr int DP = D <= 4 ? 1 : 2;
+    constexpr bool CMP = D <= 3;
+    constexpr unsigned kAll = 0xffffffffu;
+    __shared__ uint32_t s_lb[kWWarps][kWStack][32];
+    __shared__ int4 s_ent[kWWarps][kWStack];  // {node, meta y, meta z, lane mask}
+    const int wi = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const uint32_t i0 = db.tclass ? db.tclass[D - 1] : 0u;
+    const uint32_t cnt = db.tclass ? db.tclass[D] : *db.tcount;
+    const int dpb = db.dpb;
+    const bool compact = CMP && db.compact;
+    unsigned long long visits = 0, tests = 0;
+    for (int64_t base = i0 + ((int64_t)blockIdx.x * kWWarps + wi) * 32; base < cnt;
+         base += (int64_t)gridDim.x * kWWarps * 32) {
+        const int64_t i = base + lane;
+        int b = -1;
+        uint32_t p = 0;
+        int32_t x[D];
+#pragma unroll
+        for (int k = 0; k < D; ++k) x[k] = 0;
+        uint2 ro = make_uint2(0u, 0u);
+        long long bestD = INT64_MAX;
+        uint32_t bestJ = 0xffffffffu;
+        if (i < cnt) {
+            p = db.tree_list[i];
+            b = find_ds(v.pt_off, v.B, p);
+            const DsDesc& ds = v.desc[b];
+            if (ds.d == D) {
+                t_load<D>(v.rec + ds.rec_off + ((int64_t)p - ds.pt_off) * DP, x);
+                ro = v.ro_s[p];
+                const unsigned long long bk = v.best_s[p];  // unproven ring-search result: a valid start
+                if (bk != ~0ull && (uint32_t)(bk >> 32) != 0xffffffffu) {
+                    bestD = (long long)(bk >> 32);
+                    bestJ = (uint32_t)bk;
+                }
+            } else {
+                b = -1;
+            }
+        }
+        // the lanes of one dataset search its tree together
+        unsigned todo = __ballot_sync(kAll, b >= 0);
+        while (todo) {
+            const int bl = __shfl_sync(kAll, b, __ffs(todo) - 1);
+            const unsigned grp = __ballot_sync(kAll, b == bl) & todo;
+            todo &= ~grp;
+            const bool mine = (grp >> lane) & 1u;
+            const DsDesc& ds = v.desc[bl];
+            const int4* recg = v.rec + ds.rec_off - ds.pt_off * DP;
+            const int64_t c0 = db.cell_off[bl], c1 = db.cell_off[bl + 1];
+            int32_t cur = c1 - c0 >= 2 ? (int32_t)c0 : ~(int32_t)c0;
+            int4 cm;
+            const long long dr = w_test<D>(db, compact, dpb, cur, x, ro.x, cm);
+            unsigned m = __ballot_sync(kAll, mine && !out_of_reach(dr, bestD));
+            int sp = 0;
+            while (m) {
+                ++visits;
+                const bool act = (m >> lane) & 1u;
+                bool next = false;
+                if (cur < 0) {  // a cell: its points, 32 at a time, broadcast to the lanes
+                    const int64_t c = ~cur;
+                    uint32_t t0, t1;
+                    if (compact) {
+                        t0 = db.lplist ? db.lpstart[c] : v.cell_start[c];
+                        t1 = db.lplist ? db.lpstart[c + 1] : v.cell_start[c + 1];
+                    } else {
+                        t0 = (uint32_t)cm.y;
+                        t1 = (uint32_t)cm.z;
+                    }
+                    for (uint32_t j = t0; j < t1; j += 32) {
+                        const uint32_t t = j + lane;
+                        int32_t cx[D];
+#pragma unroll
+                        for (int k = 0; k < D; ++k) cx[k] = 0;
+                        uint2 cr = make_uint2(0xffffffffu, 0u);
+                        if (t < t1) {
+                            const uint32_t q = db.lplist ? db.lplist[t] : t;
+                            cr = v.ro_s[q];
+                            t_load<D>(recg + (int64_t)q * DP, cx);
+                        }
+                        const int nk = (int)min(32u, t1 - j);
+                        for (int k = 0; k < nk; ++k) {
+                            const uint32_t rk = __shfl_sync(kAll, cr.x, k);
+                            const uint32_t ok = __shfl_sync(kAll, cr.y, k);
+                            long long dd = 0;
+#pragma unroll
+                            for (int e = 0; e < D; ++e) {
+                                const long long f = (long long)x[e] - __shfl_sync(kAll, cx[e], k);
+                                dd += f * f;
+                            }
+                            if (act && rk < ro.x) {
+                                ++tests;
+                                if (dd < bestD || (dd == bestD && ok < bestJ)) {
+                                    bestD = dd;
+                                    bestJ = ok;
+                                }
+                            }
+                        }
+                    }
+                } else {
+                    const int32_t l = compact ? link_left((uint32_t)cm.y) : cm.y;
+                    const int32_t r = compact ? link_right((uint32_t)cm.y) : cm.z;
+                    int4 ml, mr;
+                    const long long dl = w_test<D>(db, compact, dpb, l, x, ro.x, ml);
+                    const long long dr2 = w_test<D>(db, compact, dpb, r, x, ro.x, mr);
+                    const bool inl = act && !out_of_reach(dl, bestD), inr = act && !out_of_reach(dr2, bestD);
+                    const unsigned bl_ = __ballot_sync(kAll, inl), br_ = __ballot_sync(kAll, inr);
+                    if (bl_ && br_) {
+                        const unsigned pr = __ballot_sync(kAll, inl && inr && dr2 < dl);
+                        const unsigned pl = __ballot_sync(kAll, inl && inr && !(dr2 < dl));
+                        const bool rfirst = __popc(pr) > __popc(pl);
+                        if (sp < kWStack) {
+                            s_lb[wi][sp][lane] = lb32(rfirst ? dl : dr2);
+                            if (lane == 0) {
+                                const int4 fm = rfirst ? ml : mr;
+                                s_ent[wi][sp] = make_int4(rfirst ? l : r, fm.y, fm.z, (int)(rfirst ? bl_ : br_));
+                            }
+                            ++sp;
+                        } else if (lane == 0) {
+                            atomicOr(v.err, kErrTreeStack);
+                        }
+                        cur = rfirst ? r : l;
+                        cm = rfirst ? mr : ml;
+                        m = rfirst ? br_ : bl_;
+                        next = true;
+                    } else if (bl_) {
+                        cur = l;
+                        cm = ml;
+                        m = bl_;
+                        next = true;
+                    } else if (br_) {
+                        cur = r;
+                        cm = mr;
+                        m = br_;
+                        next = true;
+                    }
+                }
+                while (!next && sp > 0) {
+                    --sp;
+                    __syncwarp();
+                    const int4 e = s_ent[wi][sp];
+                    const uint32_t lb = s_lb[wi][sp][lane];
+                    const unsigned mm = __ballot_sync(kAll, (((unsigned)e.w >> lane) & 1u) && (long long)lb <= bestD);
+                    if (mm) {
+                        cur = e.x;
+                        cm = make_int4(0, e.y, e.z, 0);
+                        m = mm;
+                        next = true;
+                    }
+                }
+                if (!next) m = 0;
+                __syncwarp();
+            }
+        }
+        if (b >= 0) {
+            const int64_t g = v.desc[b].pt_off + ro.y;
+            v.dep[g] = (int32_t)bestJ;
+            v.delta2[g] = bestD;
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) tests += __shfl_xor_sync(kAll, tests, o);
+    if (lane == 0 && db.stats) {
+        atomicAdd(&db.stats[0], visits);
+        atomicAdd(&db.stats[1], tests);
+    }
+}
+
 }  // namespace
 
 cudaError_t launch_tree_build(const BatchView& v, const DeltaBufs& db, cudaStream_t st) {
@@ -510,12 +700,19 @@ cudaError_t launch_tree_build(const BatchView& v, const DeltaBufs& db, cudaStrea
 }
 
 cudaError_t launch_tree_search(const BatchView& v, const DeltaBufs& db, uint32_t dim_mask, int64_t bound,
-                               cudaStream_t st) {
+                               int warp, cudaStream_t st) {
     if (bound <= 0) return cudaSuccess;
-    // 32 blocks per SM of grid-stride threads (16 and 64 measured slower)
+    // one lane per point: 32 blocks per SM of grid-stride threads (16 and 64
+    // measured slower); warp-cooperative: 8 blocks of 4 warps per SM
     const unsigned blocks = (unsigned)std::min<int64_t>(152 * 32, grid_for(bound, 128));
-#define DPC_TREE_CLASS(D) \
-    if (dim_mask & (1u << (D - 1))) (k_tree_search<D><<<blocks, 128, 0, st>>>(v, db), note_launch());
+    const unsigned wblocks = (unsigned)std::min<int64_t>(152 * 8, grid_for(bound, kWWarps * 32));
+#define DPC_TREE_CLASS(D)                                                                  \
+    if (dim_mask & (1u << (D - 1))) {                                                      \
+        if (warp == 1 || (warp == 2 && D >= 5))                                            \
+            (k_tree_search_warp<D><<<wblocks, kWWarps * 32, 0, st>>>(v, db), note_launch()); \
+        else                                                                               \
+            (k_tree_search<D><<<blocks, 128, 0, st>>>(v, db), note_launch());              \
+    }
     DPC_TREE_CLASS(1) DPC_TREE_CLASS(2) DPC_TREE_CLASS(3) DPC_TREE_CLASS(4)
     DPC_TREE_CLASS(5) DPC_TREE_CLASS(6) DPC_TREE_CLASS(7) DPC_TREE_CLASS(8)
 #undef DPC_TREE_CLASS

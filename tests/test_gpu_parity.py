@@ -113,15 +113,6 @@ def test_random_shapes_bit_exact(dpc, shape):
     assert_full_parity(dpc, ds.points, dc, queries)
 
 
-@pytest.mark.parametrize("shape", SHAPES, ids=lambda s: f"n{s[1]}_d{s[2]}_dc{s[3]}")
-def test_random_shapes_point_tree(dpc, shape):
-    """The point tree (every dimension, no grid) on the same shapes."""
-    seed, n, d, dc, dom, blobs, spread, dup = shape
-    ds = workloads.random_blobs(seed, n, d, dc, domain=dom, blobs=blobs, spread=spread, dup=dup)
-    info = assert_full_parity(dpc, ds.points, dc, [(2, dc + 1), (5, 10 * dc)], dict(tree_min_d=1))
-    assert info["grid_dims"] == 0
-
-
 @pytest.mark.parametrize("knobs", [dict(rho_bulk=1), dict(rho_bulk=1, sparse_cand=0, kch=64),
                                    dict(rho_bulk=1, hd_min_d=1, hd_cell_factor=2, sparse_cand=0)],
                          ids=["bulk", "bulk_all_dense_small_items", "bulk_reach2"])
@@ -140,28 +131,36 @@ def test_random_shapes_bulk_staging(dpc, shape, knobs):
 @pytest.mark.parametrize("d", [5, 6, 7, 8])
 @pytest.mark.parametrize("f", [1, 2, 3])
 def test_high_dims_grid_path(dpc, d, f, sparse_cand):
-    """The projected grid for d > 4 (the point tree switched off), with
+    """The projected grid for d > 4, with
     cells of side d_cut / f searched f cells away; small cells on the warp
     path by their candidate count (sparse_cand 0: every cell)."""
     ds = workloads.random_blobs(60 + d, 2500, d, 9000, blobs=4, spread=0.05, dup=10)
     info = assert_full_parity(dpc, ds.points, 9000, [(3, 27001)],
-                              dict(tree_min_d=9, hd_cell_factor=f, hd_min_d=5, sparse_cand=sparse_cand))
+                              dict(hd_cell_factor=f, hd_min_d=5, sparse_cand=sparse_cand))
     assert 1 <= info["grid_dims"] <= 4
 
 
-def test_point_tree_edge_cases(dpc):
-    knobs = dict(tree_min_d=1)
-    assert_full_parity(dpc, np.full((777, 3), 4242, np.int32), 10, [(1, 11), (778, 11)], knobs)
+@pytest.mark.parametrize("d", [5, 6, 7, 8])
+def test_high_dims_one_lane_tree_search(dpc, d):
+    """d > 4 with the tree search one lane per open point (the default there
+    is the warp-cooperative form) and every open point on the tree."""
+    ds = workloads.random_blobs(80 + d, 2500, d, 9000, blobs=4, spread=0.05, dup=10)
+    assert_full_parity(dpc, ds.points, 9000, [(3, 27001)], dict(tree_warp=0, bf_rank=0))
+
+
+def test_cutoff_spanning_the_box_and_wide_8d_blobs(dpc):
+    """A cutoff larger than the whole box (one cell), far-apart 8-d blobs
+    over the full coordinate range, and tiny 5-d sets."""
     rng = np.random.default_rng(99)
     pts = rng.integers(0, 50, size=(3000, 2)).astype(np.int32)
-    assert_full_parity(dpc, pts, 10_000_000, [(1, 10_000_001)], knobs)
+    assert_full_parity(dpc, pts, 10_000_000, [(1, 10_000_001)])
     base = rng.integers(0, (1 << 30) - 1, size=(4, 8))
     pts = np.concatenate([np.clip(b + rng.normal(0, 3e6, size=(300, 8)), 0, (1 << 30) - 1)
                           for b in base]).astype(np.int32)
-    assert_full_parity(dpc, pts, 2_000_000, [(2, 50_000_000)], knobs)
+    assert_full_parity(dpc, pts, 2_000_000, [(2, 50_000_000)])
     for n in (1, 2, 16, 17, 33):
         pts = rng.integers(0, 1000, size=(n, 5)).astype(np.int32)
-        assert_full_parity(dpc, pts, 300, [(1, 301)], dict(tree_min_d=5))
+        assert_full_parity(dpc, pts, 300, [(1, 301)])
 
 
 SMALL_CUTOFFS = [
@@ -328,7 +327,8 @@ def test_plain_5p8m_3d_sampled(dpc):
 
 @pytest.mark.parametrize("knobs", [dict(qch=32), dict(qch=64, kch=4096, bf_rank=0),
                                    dict(kch=64, bf_rank=100000), dict(kmax=2), dict(kmax=1, qch=32),
-                                   dict(tree_min_d=3), dict(tree_min_d=1, bf_rank=0),
+                                   dict(hd_min_d=3, hd_cell_factor=3), dict(hd_min_d=1, bf_rank=0),
+                                   dict(tree_warp=0), dict(tree_warp=1, bf_rank=0, hd_min_d=1),
                                    dict(sparse_cand=0), dict(sparse_cand=2147483647),
                                    dict(sparse_cand=20, kch=64), dict(rho_bulk=1)],
                          ids=lambda k: ",".join(f"{a}={b}" for a, b in k.items()))
@@ -394,8 +394,8 @@ def test_one_call_cluster_matches_the_separate_calls(dpc):
 
 def test_errors_mid_call_leave_the_context_usable(dpc):
     """Calls that fail after device work has started (coordinates out of
-    range found on the device, S-Approx-DPC and Approx-DPC refused on the
-    point tree) release their buffers and leave the context working."""
+    range found on the device) release their buffers and leave the context
+    working."""
     bad = np.array([[0, 0], [5, (1 << 30) + 3]], np.int32)
     good = workloads.random_blobs(95, 3000, 3, 900, blobs=4, spread=0.05)
     ref = run_host(dpc, good.points, 900, [(2, 2000)])
@@ -403,15 +403,9 @@ def test_errors_mid_call_leave_the_context_usable(dpc):
         for _ in range(20):
             with pytest.raises(dpc.DpcError):
                 ctx.density(bad, 10)
-        ctx.tune(tree_min_d=2)
         for _ in range(5):
             with pytest.raises(dpc.DpcError):
-                ctx.sapprox(good.points, 900, (4, 5))
-            h = ctx.density(good.points, 900)
-            with pytest.raises(dpc.DpcError):
-                h.dependent_approx()
-            h.release()
-        ctx.tune(tree_min_d=9)
+                ctx.sapprox(bad, 10, (4, 5))
         out = [np.empty(good.n, t) for t in (np.int32, np.int32, np.int64, np.int32)]
         nc = ctx.cluster(good.points, 900, 2, 2000, *out)
     np.testing.assert_array_equal(out[0], ref[0])
