@@ -13,6 +13,7 @@
 // threads. Every value ever stored is an ancestor of the slot's point, so the
 // roots found are exact, whatever the interleaving.
 #include "stages.cuh"
+#include <algorithm>
 
 namespace dpc {
 
@@ -69,7 +70,44 @@ __global__ void k_jump(BatchView v, int64_t g0, int64_t g1) {
     v.label[g] = (int32_t)(p - v.pt_off[b]);
 }
 
+// Every device-resident job's outputs in one pass: thread t of the
+// concatenation of the jobs' points (job j's at [dst_off_j, dst_off_j + n_j))
+// copies its point's values from the batch's arrays to the job's buffers.
+// what 0: rho, dep, delta2 and aux; 1: the labels of query q into
+// label + q n (jobs with q queries or fewer are skipped).
+__global__ void k_job_outputs(const OutJob* __restrict__ jobs, int J, int64_t total, const int32_t* __restrict__ rho,
+                              const int32_t* __restrict__ dep, const int64_t* __restrict__ delta2,
+                              const uint8_t* __restrict__ aux, const int32_t* __restrict__ label, int what, int q) {
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        int lo = 0, hi = J - 1;  // the last job with dst_off <= t
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (jobs[mid].dst_off <= t) lo = mid; else hi = mid - 1;
+        }
+        const OutJob& o = jobs[lo];
+        const int64_t i = t - o.dst_off, g = o.src_off + i;
+        if (what == 0) {
+            if (o.rho) o.rho[i] = rho[g];
+            if (o.dep) o.dep[i] = dep[g];
+            if (o.delta2) o.delta2[i] = delta2[g];
+            if (o.aux) o.aux[i] = aux[g];
+        } else if (o.label && q < o.nq) {
+            o.label[(int64_t)q * o.n + i] = label[g];
+        }
+    }
+}
+
 }  // namespace
+
+cudaError_t launch_job_outputs(const OutJob* jobs, int J, int64_t total, const int32_t* rho, const int32_t* dep,
+                               const int64_t* delta2, const uint8_t* aux, const int32_t* label, int what, int q,
+                               cudaStream_t st) {
+    if (J <= 0 || total <= 0) return cudaSuccess;
+    const unsigned blocks = (unsigned)std::min<int64_t>(152 * 16, grid_for(total, 256));
+    (k_job_outputs<<<blocks, 256, 0, st>>>(jobs, J, total, rho, dep, delta2, aux, label, what, q), note_launch());
+    return cudaGetLastError();
+}
 
 cudaError_t launch_labels(const BatchView& v, cudaStream_t st) {
     cudaError_t e = cudaMemsetAsync(v.ncent, 0, sizeof(unsigned long long) * v.B, st);

@@ -1572,14 +1572,42 @@ dpc_status run_jobs(dpc_ctx* ctx, std::vector<JobPtr>& jobs, cudaStream_t st) {
         if (method == 1) DPC_TRY(bt->dependent_approx());
         else DPC_TRY(bt->dependent());
     }
+    // outputs: the device-resident jobs' in one kernel pass per kind, the
+    // host jobs' by one copy per array
+    const int32_t* rho_src = method == 2 ? bt->rho_pub : bt->v.rho;
+    const uint8_t* aux_src = method == 2 ? bt->v.pick : (method == 1 ? bt->v.exact : nullptr);
+    std::vector<OutJob> oj;
+    int64_t dtot = 0;
     for (size_t b = 0; b < jobs.size(); ++b) {
         const dpc_job& jb = jobs[b]->job;
         const DsDesc& h = bt->hd[b];
-        DPC_TRY(bt->copy_out(jb.rho_out, (method == 2 ? bt->rho_pub : bt->v.rho) + h.pt_off, sizeof(int32_t) * h.n));
+        if (jb.is_device) {
+            if (h.n == 0) continue;
+            OutJob o{};
+            o.src_off = h.pt_off;
+            o.dst_off = dtot;
+            o.n = h.n;
+            o.rho = jb.rho_out;
+            o.dep = jb.dep_out;
+            o.delta2 = jb.delta2_out;
+            o.aux = method != 0 ? jb.aux_out : nullptr;
+            o.label = jb.label_out;
+            o.nq = jb.n_queries;
+            oj.push_back(o);
+            dtot += h.n;
+            continue;
+        }
+        DPC_TRY(bt->copy_out(jb.rho_out, rho_src + h.pt_off, sizeof(int32_t) * h.n));
         DPC_TRY(bt->copy_out(jb.dep_out, bt->v.dep + h.pt_off, sizeof(int32_t) * h.n));
         DPC_TRY(bt->copy_out(jb.delta2_out, bt->v.delta2 + h.pt_off, sizeof(int64_t) * h.n));
-        if (method != 0)
-            DPC_TRY(bt->copy_out(jb.aux_out, (method == 2 ? bt->v.pick : bt->v.exact) + h.pt_off, h.n));
+        if (method != 0) DPC_TRY(bt->copy_out(jb.aux_out, aux_src + h.pt_off, h.n));
+    }
+    OutJob* d_oj = nullptr;
+    if (!oj.empty()) {
+        DPC_CK(bt->keep.get(&d_oj, oj.size()));
+        DPC_CK(cudaMemcpyAsync(d_oj, oj.data(), sizeof(OutJob) * oj.size(), cudaMemcpyHostToDevice, st));
+        DPC_CK(launch_job_outputs(d_oj, (int)oj.size(), dtot, rho_src, bt->v.dep, bt->v.delta2, aux_src, nullptr, 0,
+                                  0, st));
     }
     std::vector<int64_t> rmin(jobs.size()), dmin(jobs.size());
     std::vector<unsigned long long> nc(jobs.size());
@@ -1591,9 +1619,12 @@ dpc_status run_jobs(dpc_ctx* ctx, std::vector<JobPtr>& jobs, cudaStream_t st) {
         }
         DPC_TRY(bt->label(rmin.data(), dmin.data()));
         DPC_TRY(bt->copy_out(nc.data(), bt->v.ncent, sizeof(unsigned long long) * jobs.size()));
+        if (d_oj)
+            DPC_CK(launch_job_outputs(d_oj, (int)oj.size(), dtot, nullptr, nullptr, nullptr, nullptr, bt->v.label, 1, q,
+                                      bt->st));
         for (size_t b = 0; b < jobs.size(); ++b) {
             const dpc_job& jb = jobs[b]->job;
-            if (q >= jb.n_queries || !jb.label_out) continue;
+            if (jb.is_device || q >= jb.n_queries || !jb.label_out) continue;
             const DsDesc& h = bt->hd[b];
             DPC_TRY(bt->copy_out(jb.label_out + (int64_t)q * h.n, bt->v.label + h.pt_off, sizeof(int32_t) * h.n));
         }

@@ -376,6 +376,21 @@ cudaError_t launch_labels(const BatchView& v, cudaStream_t st);
 // labels of dataset b only (its points [g0, g0 + n)); the other datasets'
 // labels and center counts are left as they are
 cudaError_t launch_labels_one(const BatchView& v, int b, int64_t g0, int64_t n, cudaStream_t st);
+// The outputs of the device-resident jobs of a batch (null pointers skipped):
+// job j's n points are the batch's [src_off, src_off + n) and the
+// concatenation's [dst_off, dst_off + n) (dst_off ascending)
+struct OutJob {
+    int64_t src_off, dst_off, n;
+    int32_t* rho;
+    int32_t* dep;
+    int64_t* delta2;
+    uint8_t* aux;
+    int32_t* label;  // [nq * n], query-major
+    int32_t nq;
+};
+cudaError_t launch_job_outputs(const OutJob* jobs, int J, int64_t total, const int32_t* rho, const int32_t* dep,
+                               const int64_t* delta2, const uint8_t* aux, const int32_t* label, int what, int q,
+                               cudaStream_t st);
 
 inline unsigned grid_for(int64_t n, int threads) { return (unsigned)((n + threads - 1) / threads); }
 
