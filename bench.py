@@ -723,7 +723,8 @@ def run_batched(args):
         ctx.tune(**knobs)
     st = ctx.stream
     djobs = [dpc.Job(torch.from_numpy(p.points).to(dev), p.d_cut, [(p.rho_min, p.delta_min)]) for p in probs]
-    hjobs = [dpc.Job(torch.from_numpy(p.points).pin_memory().numpy(), p.d_cut, [(p.rho_min, p.delta_min)])
+    hjobs = [dpc.Job(torch.from_numpy(p.points).pin_memory().numpy(), p.d_cut, [(p.rho_min, p.delta_min)],
+                     pinned=True)
              for p in probs]
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     torch.cuda.synchronize()

@@ -356,7 +356,10 @@ typedef struct {
     int64_t* delta2_out;       /* NULL or [n] */
     int32_t* label_out;        /* NULL or [n_queries * n], query-major */
     int64_t* n_centers_out;    /* NULL or [n_queries] */
-    int32_t is_device;         /* 0: points and outputs in host memory; 1: in device memory */
+    int32_t is_device;         /* 0: points and outputs in host memory; 1: in device memory. In a batch of
+                                  several jobs, host points and outputs in page-locked memory (pinned or
+                                  registered) are read and written by the device directly, all such jobs
+                                  in one pass; pageable ones take one copy per array */
     int32_t method;            /* 0 exact (Definitions 2-3), 1 Approx-DPC (Section 4.3), 2 S-Approx-DPC (Section 5) */
     int64_t eps_num, eps_den;  /* method 2: eps = eps_num / eps_den, 1 .. 2^20 each; ignored otherwise */
     uint8_t* aux_out;          /* NULL or [n]: method 1, 1 where the dependent point is exact; method 2, 1 for

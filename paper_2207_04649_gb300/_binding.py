@@ -467,7 +467,8 @@ class Job:
     tensors on its device) and a device-memory job. method: "exact",
     "approx" or "sapprox" (with eps as for Context.sapprox)."""
 
-    def __init__(self, points, d_cut: int, queries, method: str = "exact", eps=(4, 5), keep: bool = False):
+    def __init__(self, points, d_cut: int, queries, method: str = "exact", eps=(4, 5), keep: bool = False,
+                 pinned: bool = False):
         q = list(queries)
         self.rho_min = np.array([int(a) for a, _ in q], dtype=np.int64)
         self.delta_min = np.array([int(b) for _, b in q], dtype=np.int64)
@@ -489,11 +490,20 @@ class Job:
         else:
             self.points = np.ascontiguousarray(points, dtype=np.int32)
             n, d = self.points.shape
-            self.rho = np.empty(n, np.int32)
-            self.dep = np.empty(n, np.int32)
-            self.delta2 = np.empty(n, np.int64)
-            self.label = np.empty((len(q), n), np.int32)
-            self.aux = np.empty(n, np.uint8)
+            if pinned:
+                # page-locked host outputs: in a batch the device writes them
+                # directly (one pass for all such jobs) instead of one copy each
+                import torch
+                e = lambda shape, dt: torch.empty(shape, dtype=dt, pin_memory=True).numpy()
+                self.rho, self.dep = e(n, torch.int32), e(n, torch.int32)
+                self.delta2, self.label = e(n, torch.int64), e((len(q), n), torch.int32)
+                self.aux = e(n, torch.uint8)
+            else:
+                self.rho = np.empty(n, np.int32)
+                self.dep = np.empty(n, np.int32)
+                self.delta2 = np.empty(n, np.int64)
+                self.label = np.empty((len(q), n), np.int32)
+                self.aux = np.empty(n, np.uint8)
             p = lambda a: a.ctypes.data_as(ctypes.c_void_p)
             is_dev = 0
         h = lambda a: a.ctypes.data_as(ctypes.c_void_p)

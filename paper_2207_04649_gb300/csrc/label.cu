@@ -98,7 +98,30 @@ __global__ void k_job_outputs(const OutJob* __restrict__ jobs, int J, int64_t to
     }
 }
 
+// The inputs of a batch's jobs whose points the device can read (device or
+// page-locked host memory) into the batch's input buffer, one pass over its
+// elements (job j's at [dst_off_j, dst_off_j + len_j); the others are left).
+__global__ void k_job_inputs(const InJob* __restrict__ jobs, int J, int64_t total, int32_t* __restrict__ dst) {
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        int lo = 0, hi = J - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (jobs[mid].dst_off <= t) lo = mid; else hi = mid - 1;
+        }
+        const int64_t i = t - jobs[lo].dst_off;
+        if (i >= 0 && i < jobs[lo].len) dst[t] = jobs[lo].src[i];
+    }
+}
+
 }  // namespace
+
+cudaError_t launch_job_inputs(const InJob* jobs, int J, int64_t total, int32_t* dst, cudaStream_t st) {
+    if (J <= 0 || total <= 0) return cudaSuccess;
+    const unsigned blocks = (unsigned)std::min<int64_t>(152 * 16, grid_for(total, 256));
+    (k_job_inputs<<<blocks, 256, 0, st>>>(jobs, J, total, dst), note_launch());
+    return cudaGetLastError();
+}
 
 cudaError_t launch_job_outputs(const OutJob* jobs, int J, int64_t total, const int32_t* rho, const int32_t* dep,
                                const int64_t* delta2, const uint8_t* aux, const int32_t* label, int what, int q,

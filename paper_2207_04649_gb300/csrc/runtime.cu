@@ -1,6 +1,7 @@
 // Host runtime of libdpc: planning of the grid, device memory, the order of
 // the stages, the C ABI, and the batched / served job modes.
 #include <algorithm>
+#include <type_traits>
 #include <atomic>
 #include <chrono>
 #include <cmath>
@@ -110,6 +111,21 @@ struct Arena {
     Arena(const Arena&) = delete;
     Arena& operator=(const Arena&) = delete;
 };
+
+// The device's address of memory the kernels can read and write: device
+// memory, or page-locked host memory (pinned or registered); null for
+// pageable host memory.
+inline void* device_view(const void* p) {
+    if (!p) return nullptr;
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    if (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged) return const_cast<void*>(p);
+    if (a.type == cudaMemoryTypeHost) return a.devicePointer;
+    return nullptr;
+}
 
 struct Input {
     const int32_t* pts;
@@ -435,10 +451,25 @@ struct Batch {
         } else {
             int32_t* buf = nullptr;
             DPC_CK(dens.get(&buf, (size_t)in_total));
-            for (int b = 0; b < B; ++b)
-                if (in[b].n > 0)
-                    DPC_CK(cudaMemcpyAsync(buf + hd[b].in_off, in[b].pts, sizeof(int32_t) * in[b].n * in[b].d,
-                                           in[b].is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
+            // a batch: the points the device can read (device or page-locked
+            // host memory) in one gather pass, the others by one copy each
+            std::vector<InJob> ij;
+            for (int b = 0; b < B; ++b) {
+                if (in[b].n == 0) continue;
+                const void* dv = B > 1 ? (in[b].is_device ? in[b].pts : device_view(in[b].pts)) : nullptr;
+                if (dv) {
+                    ij.push_back({static_cast<const int32_t*>(dv), hd[b].in_off, in[b].n * in[b].d});
+                    continue;
+                }
+                DPC_CK(cudaMemcpyAsync(buf + hd[b].in_off, in[b].pts, sizeof(int32_t) * in[b].n * in[b].d,
+                                       in[b].is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
+            }
+            if (!ij.empty()) {
+                InJob* d_ij = nullptr;
+                DPC_CK(dens.get(&d_ij, ij.size()));
+                DPC_CK(cudaMemcpyAsync(d_ij, ij.data(), sizeof(InJob) * ij.size(), cudaMemcpyHostToDevice, st));
+                DPC_CK(launch_job_inputs(d_ij, (int)ij.size(), in_total, buf, st));
+            }
             d_in = buf;
         }
         v.B = B;
@@ -1572,26 +1603,45 @@ dpc_status run_jobs(dpc_ctx* ctx, std::vector<JobPtr>& jobs, cudaStream_t st) {
         if (method == 1) DPC_TRY(bt->dependent_approx());
         else DPC_TRY(bt->dependent());
     }
-    // outputs: the device-resident jobs' in one kernel pass per kind, the
-    // host jobs' by one copy per array
+    // outputs: those the device can write (device memory; in a batch of
+    // several jobs, page-locked host memory too) in one kernel pass per kind,
+    // the others by one copy per array
     const int32_t* rho_src = method == 2 ? bt->rho_pub : bt->v.rho;
     const uint8_t* aux_src = method == 2 ? bt->v.pick : (method == 1 ? bt->v.exact : nullptr);
     std::vector<OutJob> oj;
+    std::vector<char> by_kernel(jobs.size(), 0);
     int64_t dtot = 0;
     for (size_t b = 0; b < jobs.size(); ++b) {
         const dpc_job& jb = jobs[b]->job;
         const DsDesc& h = bt->hd[b];
-        if (jb.is_device) {
-            if (h.n == 0) continue;
-            OutJob o{};
-            o.src_off = h.pt_off;
-            o.dst_off = dtot;
-            o.n = h.n;
+        OutJob o{};
+        bool kern = jb.is_device != 0;
+        if (kern) {
             o.rho = jb.rho_out;
             o.dep = jb.dep_out;
             o.delta2 = jb.delta2_out;
             o.aux = method != 0 ? jb.aux_out : nullptr;
             o.label = jb.label_out;
+        } else if (jobs.size() > 1) {
+            kern = true;
+            auto view = [&kern](auto* p) {
+                using T = std::remove_pointer_t<decltype(p)>;
+                T* d = static_cast<T*>(device_view(p));
+                kern = kern && (p == nullptr || d != nullptr);
+                return d;
+            };
+            o.rho = view(jb.rho_out);
+            o.dep = view(jb.dep_out);
+            o.delta2 = view(jb.delta2_out);
+            o.aux = method != 0 ? view(jb.aux_out) : nullptr;
+            o.label = view(jb.label_out);
+        }
+        if (kern) {
+            by_kernel[b] = 1;
+            if (h.n == 0) continue;
+            o.src_off = h.pt_off;
+            o.dst_off = dtot;
+            o.n = h.n;
             o.nq = jb.n_queries;
             oj.push_back(o);
             dtot += h.n;
@@ -1624,7 +1674,7 @@ dpc_status run_jobs(dpc_ctx* ctx, std::vector<JobPtr>& jobs, cudaStream_t st) {
                                       bt->st));
         for (size_t b = 0; b < jobs.size(); ++b) {
             const dpc_job& jb = jobs[b]->job;
-            if (jb.is_device || q >= jb.n_queries || !jb.label_out) continue;
+            if (by_kernel[b] || q >= jb.n_queries || !jb.label_out) continue;
             const DsDesc& h = bt->hd[b];
             DPC_TRY(bt->copy_out(jb.label_out + (int64_t)q * h.n, bt->v.label + h.pt_off, sizeof(int32_t) * h.n));
         }

@@ -391,6 +391,14 @@ struct OutJob {
 cudaError_t launch_job_outputs(const OutJob* jobs, int J, int64_t total, const int32_t* rho, const int32_t* dep,
                                const int64_t* delta2, const uint8_t* aux, const int32_t* label, int what, int q,
                                cudaStream_t st);
+// The inputs the device can read (device or page-locked host memory): job j's
+// points (len = n d ints at src) into dst[dst_off .. dst_off + len) (dst_off
+// ascending; the ints of dst in no job's range, of total, are not written)
+struct InJob {
+    const int32_t* src;
+    int64_t dst_off, len;
+};
+cudaError_t launch_job_inputs(const InJob* jobs, int J, int64_t total, int32_t* dst, cudaStream_t st);
 
 inline unsigned grid_for(int64_t n, int threads) { return (unsigned)((n + threads - 1) / threads); }
 

@@ -265,6 +265,38 @@ def test_device_jobs_match_host_jobs(dpc):
         check_job(b, p, dc, qs)
 
 
+def test_page_locked_host_jobs(dpc):
+    """Host jobs in page-locked memory (points, outputs or both), which a
+    batch reads and writes from the device directly, mixed with pageable
+    host jobs and device jobs: the oracle's bits for every job."""
+    import torch
+    probs = small_problems(seed=47, count=12)
+    jobs = []
+    with dpc.Context(0, mode=0) as ctx:
+        for i, (p, dc, qs) in enumerate(probs):
+            kind = i % 4
+            if kind == 0:    # pinned points and outputs
+                j = dpc.Job(torch.from_numpy(np.ascontiguousarray(p)).pin_memory().numpy(), dc, qs, pinned=True)
+            elif kind == 1:  # pinned points, pageable outputs
+                j = dpc.Job(torch.from_numpy(np.ascontiguousarray(p)).pin_memory().numpy(), dc, qs)
+            elif kind == 2:  # pageable points, pinned outputs
+                j = dpc.Job(p, dc, qs, pinned=True)
+            else:
+                j = dpc.Job(torch.from_numpy(np.ascontiguousarray(p)).cuda(), dc, qs)
+            jobs.append(j)
+        torch.cuda.synchronize()
+        for j in jobs:
+            ctx.submit(j)
+        ctx.flush()
+        for j in jobs:
+            assert ctx.poll(j.ticket)[0] == dpc.DPC_OK
+    for j, (p, dc, qs) in zip(jobs, probs):
+        if j.is_device:
+            for name in ("rho", "dep", "delta2", "label"):
+                setattr(j, name, getattr(j, name).cpu().numpy())
+        check_job(j, p, dc, qs)
+
+
 def test_served_one_job_per_batch(dpc):
     """max_batch_jobs = 1 serves the jobs one at a time with the same results."""
     probs = small_problems(seed=44, count=6)
