@@ -437,8 +437,11 @@ __global__ void __launch_bounds__(128) k_tree_search(BatchView v, DeltaBufs db) 
             }
         } else {
             // as above; the current node's meta word comes with it (the
-            // nearer child's from its test), a stacked node's is reloaded
+            // nearer child's from its test); a stacked node keeps its
+            // children as a link word (a cell's points come from the cell
+            // starts), so that a pop loads nothing
             int4 meta;
+            uint32_t slink[kStack];
             int32_t cur = root;
             int sp = 0;
             bool have = !out_of_reach(node_test<D>(db.nodes + rec_of(db, root) * ns, dpb, x, ro.x, meta), bestD);
@@ -457,8 +460,10 @@ __global__ void __launch_bounds__(128) k_tree_search(BatchView v, DeltaBufs db) 
                     const int32_t nn = swap ? meta.z : meta.y, nf = swap ? meta.y : meta.z;
                     if (!out_of_reach(df, bestD)) {
                         if (sp < kStack) {
+                            const int4 mf = swap ? m0 : m1;
                             stack[sp] = nf;
                             slb[sp] = lb32(df);
+                            slink[sp] = nf >= 0 ? compact_link(make_int2(mf.y, mf.z)) : 0u;
                             ++sp;
                         } else {
                             atomicOr(v.err, kErrTreeStack);
@@ -474,8 +479,15 @@ __global__ void __launch_bounds__(128) k_tree_search(BatchView v, DeltaBufs db) 
                     --sp;
                     if ((long long)slb[sp] > bestD) continue;  // overtaken since it was stacked
                     cur = stack[sp];
-                    // reload: its meta word, and a test against the best so far
-                    next = !out_of_reach(node_test<D>(db.nodes + rec_of(db, cur) * ns, dpb, x, ro.x, meta), bestD);
+                    if (cur >= 0) {
+                        meta.y = link_left(slink[sp]);
+                        meta.z = link_right(slink[sp]);
+                    } else {
+                        const int64_t c = ~cur;
+                        meta.y = (int)(db.lplist ? db.lpstart[c] : v.cell_start[c]);
+                        meta.z = (int)(db.lplist ? db.lpstart[c + 1] : v.cell_start[c + 1]);
+                    }
+                    next = true;
                 }
                 have = next;
             }
