@@ -823,6 +823,8 @@ struct Batch {
             }
             DPC_CK(tmp.get(&db.stats, 2));
             DPC_CK(cudaMemsetAsync(db.stats, 0, 2 * sizeof(unsigned long long), st));
+            db.key_bits = 1;
+            for (int b = 0; b < B; ++b) db.key_bits = std::max(db.key_bits, hd[b].k * hd[b].mbits);
             DPC_CK(launch_tree_search(v, db, dim_mask, ntree, tune.tree_warp, st));
         }
         if (nbf > 0) {

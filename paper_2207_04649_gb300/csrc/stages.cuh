@@ -280,6 +280,7 @@ struct DeltaBufs {
     const uint32_t* lpstart;
     uint32_t* flag;       // [ncells] refit arrival counters
     unsigned long long* stats;  // [0] tree nodes visited, [1] point pairs tested in leaves
+    int key_bits;         // widest cell key of the batch's trees (bits; a tree is at most key_bits + 1 deep)
 };
 cudaError_t launch_rank(const BatchView& v, const DeltaBufs& db, int key_bits, void* sort_temp, cudaStream_t st);
 cudaError_t launch_ring(const BatchView& v, const CellWork& w, uint32_t class_mask, int64_t nitems_bound,

@@ -353,7 +353,9 @@ __device__ __forceinline__ void scan_leaf(const BatchView& v, const DeltaBufs& d
     }
 }
 
-template <int D>
+// S stack entries per lane (local memory): 32 when every tree is at most 31
+// levels deep (cell keys of at most 30 bits), else 64.
+template <int D, int S>
 __global__ void __launch_bounds__(128) k_tree_search(BatchView v, DeltaBufs db) {
     constexpr int DP = D <= 4 ? 1 : 2;
     constexpr bool CMP = D <= 3;  // compact records possible
@@ -380,8 +382,8 @@ __global__ void __launch_bounds__(128) k_tree_search(BatchView v, DeltaBufs db) 
             bestD = (long long)(bk >> 32);
             bestJ = (uint32_t)bk;
         }
-        int32_t stack[kStack];
-        uint32_t slb[kStack];
+        int32_t stack[S];
+        uint32_t slb[S];
         const int64_t c0 = db.cell_off[b], c1 = db.cell_off[b + 1];
         const int32_t root = c1 - c0 >= 2 ? (int32_t)c0 : ~(int32_t)c0;
         if (compact) {
@@ -390,7 +392,7 @@ __global__ void __launch_bounds__(128) k_tree_search(BatchView v, DeltaBufs db) 
             // distance bound, link); a node whose children are both out of
             // reach, or a scanned cell, takes the next stacked node still in
             // reach
-            uint32_t slink[kStack];
+            uint32_t slink[S];
             uint32_t cur_link;
             int32_t cur = root;
             int sp = 0;
@@ -411,7 +413,7 @@ __global__ void __launch_bounds__(128) k_tree_search(BatchView v, DeltaBufs db) 
                     const bool swap = d1 < d0;
                     const long long dn = swap ? d1 : d0, df = swap ? d0 : d1;
                     if (!out_of_reach(df, bestD)) {
-                        if (sp < kStack) {
+                        if (sp < S) {
                             stack[sp] = swap ? l : r;
                             slb[sp] = lb32(df);
                             slink[sp] = swap ? ll : rl;
@@ -441,7 +443,7 @@ __global__ void __launch_bounds__(128) k_tree_search(BatchView v, DeltaBufs db) 
             // children as a link word (a cell's points come from the cell
             // starts), so that a pop loads nothing
             int4 meta;
-            uint32_t slink[kStack];
+            uint32_t slink[S];
             int32_t cur = root;
             int sp = 0;
             bool have = !out_of_reach(node_test<D>(db.nodes + rec_of(db, root) * ns, dpb, x, ro.x, meta), bestD);
@@ -459,7 +461,7 @@ __global__ void __launch_bounds__(128) k_tree_search(BatchView v, DeltaBufs db) 
                     const long long dn = swap ? d1 : d0, df = swap ? d0 : d1;
                     const int32_t nn = swap ? meta.z : meta.y, nf = swap ? meta.y : meta.z;
                     if (!out_of_reach(df, bestD)) {
-                        if (sp < kStack) {
+                        if (sp < S) {
                             const int4 mf = swap ? m0 : m1;
                             stack[sp] = nf;
                             slb[sp] = lb32(df);
@@ -711,6 +713,12 @@ cudaError_t launch_tree_build(const BatchView& v, const DeltaBufs& db, cudaStrea
     return cudaGetLastError();
 }
 
+template <int D>
+static void k_tree_search_launch(const BatchView& v, const DeltaBufs& db, unsigned blocks, cudaStream_t st) {
+    if (db.key_bits <= 30) (k_tree_search<D, 32><<<blocks, 128, 0, st>>>(v, db), note_launch());
+    else (k_tree_search<D, kStack><<<blocks, 128, 0, st>>>(v, db), note_launch());
+}
+
 cudaError_t launch_tree_search(const BatchView& v, const DeltaBufs& db, uint32_t dim_mask, int64_t bound,
                                int warp, cudaStream_t st) {
     if (bound <= 0) return cudaSuccess;
@@ -723,7 +731,7 @@ cudaError_t launch_tree_search(const BatchView& v, const DeltaBufs& db, uint32_t
         if (warp == 1 || (warp == 2 && D >= 5))                                            \
             (k_tree_search_warp<D><<<wblocks, kWWarps * 32, 0, st>>>(v, db), note_launch()); \
         else                                                                               \
-            (k_tree_search<D><<<blocks, 128, 0, st>>>(v, db), note_launch());              \
+            k_tree_search_launch<D>(v, db, blocks, st);                                    \
     }
     DPC_TREE_CLASS(1) DPC_TREE_CLASS(2) DPC_TREE_CLASS(3) DPC_TREE_CLASS(4)
     DPC_TREE_CLASS(5) DPC_TREE_CLASS(6) DPC_TREE_CLASS(7) DPC_TREE_CLASS(8)
