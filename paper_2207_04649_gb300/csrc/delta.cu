@@ -265,9 +265,13 @@ __global__ void __launch_bounds__(kRingThreads) k_ring_dense(BatchView v, CellWo
 }
 
 // Sparse cells: kRingSparseLanes lanes per cell, each with all of the
-// cell's queries, take every kRingSparseLanes-th candidate of each run; the
-// least keys are combined with warp shuffles (the cell loop is warp-uniform).
+// cell's queries, take every kRingSparseLanes-th candidate of the cell's
+// concatenated runs, kRingSparseBatch of them found before their records
+// and ranks are loaded together (overlapping latencies, as in the sparse
+// density pass); the least keys are combined with warp shuffles (the cell
+// loop is warp-uniform).
 constexpr int kRingSparseLanes = 4;
+constexpr int kRingSparseBatch = 4;
 
 template <int D, bool W64>
 __global__ void __launch_bounds__(256) k_ring_sparse(BatchView v, CellWork w) {
@@ -300,22 +304,35 @@ __global__ void __launch_bounds__(256) k_ring_sparse(BatchView v, CellWork w) {
                     load_pt<D>(recb + ((int64_t)cs + qi) * DP, qx[t]);
                     qr[t] = v.ro_s[cs + qi].x;
                 }
-                const uint2* runs = w.runs + (int64_t)c * w.nbs;
-                const uint32_t nr = w.nruns[c];
-                for (uint32_t r = 0; r < nr; ++r) {
-                    const uint2 e = runs[r];
-#pragma unroll 2
-                    for (uint32_t j = sl; j < e.y; j += G) {
-                        int32_t cj[D];
-                        load_pt<D>(recb + ((int64_t)e.x + j) * DP, cj);
-                        const uint2 ro = v.ro_s[e.x + j];
+                RunCursor rc;
+                rc.init(w.runs + (int64_t)c * w.nbs, w.nruns[c], (uint32_t)sl);
+                bool more = true;
+                while (more) {
+                    // positions first (a lane past its last candidate reads
+                    // the cell's own first point and keeps nothing from it)
+                    uint32_t p[kRingSparseBatch];
+                    bool ok[kRingSparseBatch];
+#pragma unroll
+                    for (int u = 0; u < kRingSparseBatch; ++u) {
+                        ok[u] = rc.next((uint32_t)G, p[u]);
+                        if (!ok[u]) p[u] = cs;
+                    }
+                    more = ok[kRingSparseBatch - 1];
+                    int32_t cj[kRingSparseBatch][D];
+                    uint2 ro[kRingSparseBatch];
+#pragma unroll
+                    for (int u = 0; u < kRingSparseBatch; ++u) {
+                        load_pt<D>(recb + (int64_t)p[u] * DP, cj[u]);
+                        ro[u] = v.ro_s[p[u]];
+                    }
+#pragma unroll
+                    for (int u = 0; u < kRingSparseBatch; ++u)
 #pragma unroll
                         for (int q = 0; q < kSparseMax; ++q) {
-                            const uint32_t dd = dist_sat<D, W64>(qx[q], cj);
-                            const unsigned long long key = ((unsigned long long)dd << 32) | ro.y;
-                            if (ro.x < qr[q] && key < best[q]) best[q] = key;
+                            const uint32_t dd = dist_sat<D, W64>(qx[q], cj[u]);
+                            const unsigned long long key = ((unsigned long long)dd << 32) | ro[u].y;
+                            if (ok[u] && ro[u].x < qr[q] && key < best[q]) best[q] = key;
                         }
-                    }
                 }
             }
         }
@@ -449,18 +466,20 @@ __global__ void k_open_classes(DeltaBufs db, int64_t nb) {
 
 // --------------------------------------------------------- brute force
 
+// The records of every dataset's bf_rank highest-ranked points, in rank
+// order, with their original indices (one thread per sorted position).
 __global__ void k_bf_prefix(BatchView v, DeltaBufs db) {
-    const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (g >= v.N) return;
-    const uint32_t r = v.rank[g];
-    if (r >= db.bf_rank) return;
-    const int b = find_ds(v.pt_off, v.B, g);
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= v.N) return;
+    const uint2 ro = v.ro_s[p];  // (rank, original local index)
+    if (ro.x >= db.bf_rank) return;
+    const int b = find_ds(v.pt_off, v.B, p);
     const DsDesc& ds = v.desc[b];
-    const int64_t pos = ds.pt_off + r;
-    const int4* src = v.rec + ds.rec_off + ((int64_t)v.pos_of[g] - ds.pt_off) * ds.dp;
+    const int64_t pos = ds.pt_off + ro.x;
+    const int4* src = v.rec + ds.rec_off + (p - ds.pt_off) * ds.dp;
     db.rrec[pos * 2] = src[0];
     db.rrec[pos * 2 + 1] = ds.dp == 2 ? src[1] : make_int4(0, 0, 0, 0);
-    db.rorig[pos] = (uint32_t)(g - ds.pt_off);
+    db.rorig[pos] = ro.y;
 }
 
 constexpr int kBfThreads = 128;

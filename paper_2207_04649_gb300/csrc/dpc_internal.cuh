@@ -66,7 +66,7 @@ struct BatchView {
     const int32_t* in;         // input points, row-major per dataset
     int4* rec;                 // sorted records (dp int4 per point)
     uint32_t* perm;            // p -> g
-    uint32_t* pos_of;          // g -> p
+    uint32_t* pos_of;          // g -> p (S-Approx-DPC only, else null)
     // grid
     uint64_t* key;             // cell key per sorted point
     uint32_t* cell_start;      // [ncells + 1]

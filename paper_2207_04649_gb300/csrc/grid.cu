@@ -134,7 +134,6 @@ __global__ void k_gather(BatchView v, const K* __restrict__ skeys, uint32_t* __r
                          (uint32_t)c[2] * (uint32_t)c[2]);
     r[0] = make_int4(c[0], c[1], c[2], c[3]);
     if (ds.dp == 2) r[1] = make_int4(c[4], c[5], c[6], c[7]);
-    v.pos_of[g] = (uint32_t)p;
     v.key[p] = (uint64_t)skeys[p];
     const bool first = p == 0 || p == ds.pt_off;
     flag[p] = (first || skeys[p] != skeys[p - 1]) ? 1u : 0u;
@@ -231,6 +230,20 @@ cudaError_t launch_cell_keys(const BatchView& v, bool key32, void* keys, uint32_
         (k_cell_keys<uint32_t><<<blocks_for(v.N, 256), 256, 0, st>>>(v, (uint32_t*)keys, vals), note_launch());
     else
         (k_cell_keys<uint64_t><<<blocks_for(v.N, 256), 256, 0, st>>>(v, (uint64_t*)keys, vals), note_launch());
+    return cudaGetLastError();
+}
+
+// Inverse of the sort permutation (pos_of[perm[p]] = p), for the passes
+// that start from original indices (S-Approx-DPC's grid G').
+__global__ void k_pos_of(BatchView v) {
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= v.N) return;
+    v.pos_of[v.perm[p]] = (uint32_t)p;
+}
+
+cudaError_t launch_pos_of(const BatchView& v, cudaStream_t st) {
+    if (v.N == 0) return cudaSuccess;
+    (k_pos_of<<<blocks_for(v.N, 256), 256, 0, st>>>(v), note_launch());
     return cudaGetLastError();
 }
 

@@ -188,11 +188,19 @@ __device__ __forceinline__ unsigned long long range_codes(int j, int a, int e) {
 // neighbour cells, and a cell's index in the sorted cell order is the
 // block's first cell plus the occupied codes below it. Neighbour cells whose
 // indices follow one another hold consecutive points and become one run.
+// The cell-index runs wait in shared memory (K <= 3: at most 3^K of them per
+// cell, one column per thread) until their point ranges are looked up, so
+// each run is written to global memory once.
+constexpr int kRunsBlkThreads = 128;
+
 template <int K>
-__global__ void __launch_bounds__(256) k_cell_runs_blk(BatchView v, CellPrepBufs cb, int64_t ncells) {
+__global__ void __launch_bounds__(kRunsBlkThreads) k_cell_runs_blk(BatchView v, CellPrepBufs cb, int64_t ncells) {
     constexpr int L = K == 1 ? 6 : (K == 2 ? 3 : (K == 3 ? 2 : 1));
     constexpr int W = 1 << L;
     constexpr int NB = 1 << K;  // blocks the neighbourhood can meet
+    constexpr bool SM = K <= 3;
+    constexpr int MAXR = K == 1 ? 3 : (K == 2 ? 9 : 27);
+    __shared__ uint2 sruns[SM ? MAXR : 1][kRunsBlkThreads];
     for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < ncells; c += (int64_t)gridDim.x * blockDim.x) {
         const uint32_t cs = v.cell_start[c];
         const int b = find_ds(v.pt_off, v.B, cs);
@@ -250,18 +258,26 @@ __global__ void __launch_bounds__(256) k_cell_runs_blk(BatchView v, CellPrepBufs
                 if (open && ci == last_ci + 1u) {
                     last_ci = ci;
                 } else {
-                    if (open) runs[nr++] = make_uint2(first_ci, last_ci);
+                    if (open) {
+                        if (SM) sruns[nr][threadIdx.x] = make_uint2(first_ci, last_ci);
+                        else runs[nr] = make_uint2(first_ci, last_ci);
+                        ++nr;
+                    }
                     first_ci = last_ci = ci;
                     open = true;
                 }
             }
         }
-        if (open) runs[nr++] = make_uint2(first_ci, last_ci);
+        if (open) {
+            if (SM) sruns[nr][threadIdx.x] = make_uint2(first_ci, last_ci);
+            else runs[nr] = make_uint2(first_ci, last_ci);
+            ++nr;
+        }
         // cell index ranges -> point runs (independent loads)
         uint32_t cand = 0;
 #pragma unroll 4
         for (uint32_t r = 0; r < nr; ++r) {
-            const uint2 e = runs[r];
+            const uint2 e = SM ? sruns[r][threadIdx.x] : runs[r];
             const uint32_t p0 = v.cell_start[e.x], p1 = v.cell_start[e.y + 1];
             runs[r] = make_uint2(p0, p1 - p0);
             cand += p1 - p0;
@@ -854,11 +870,15 @@ __global__ void __launch_bounds__(kRhoThreads) k_rho_dense_bulk(BatchView v, Cel
 
 // Sparse cells (at most kSparseMax points, few candidates): kSparseLanes
 // lanes per cell, each with all of the cell's queries, take every
-// kSparseLanes-th candidate of each run; their counts are added with warp
-// shuffles. (One thread per cell left most lanes of a warp idle: cells in a
-// warp have very different candidate counts.) The loop over cells is
-// warp-uniform, so that every lane reaches the shuffles.
+// kSparseLanes-th candidate of the cell's concatenated runs; their counts
+// are added with warp shuffles. (One thread per cell left most lanes of a
+// warp idle: cells in a warp have very different candidate counts.) A lane
+// finds its next kSparseBatch candidates first and then loads their records
+// together, so that their latencies overlap (the runs hold 2-3 points each
+// in sparse regions: a loop per run kept one load in flight). The loop over
+// cells is warp-uniform, so that every lane reaches the shuffles.
 constexpr int kSparseLanes = 4;
+constexpr int kSparseBatch = 4;
 
 template <int D, bool W64>
 __global__ void __launch_bounds__(256) k_rho_sparse(BatchView v, CellWork w) {
@@ -886,17 +906,28 @@ __global__ void __launch_bounds__(256) k_rho_sparse(BatchView v, CellWork w) {
                 for (int t = 0; t < kSparseMax; ++t)
                     load_point<D>(recb + ((int64_t)cs + min((uint32_t)t, m - 1)) * DP, qx[t]);
                 const int64_t T = ds.d_cut2;
-                const uint2* runs = w.runs + (int64_t)c * w.nbs;
-                const uint32_t nr = w.nruns[c];
-                for (uint32_t r = 0; r < nr; ++r) {
-                    const uint2 e = runs[r];
-#pragma unroll 2
-                    for (uint32_t j = sl; j < e.y; j += G) {
-                        int32_t cj[D];
-                        load_point<D>(recb + ((int64_t)e.x + j) * DP, cj);
+                RunCursor rc;
+                rc.init(w.runs + (int64_t)c * w.nbs, w.nruns[c], (uint32_t)sl);
+                bool more = true;
+                while (more) {
+                    // positions first (a lane past its last candidate reads
+                    // the cell's own first record and counts nothing)
+                    uint32_t p[kSparseBatch];
+                    bool ok[kSparseBatch];
 #pragma unroll
-                        for (int q = 0; q < kSparseMax; ++q) cnt[q] += inside<D, W64>(qx[q], cj, T);
+                    for (int u = 0; u < kSparseBatch; ++u) {
+                        ok[u] = rc.next((uint32_t)G, p[u]);
+                        if (!ok[u]) p[u] = cs;
                     }
+                    more = ok[kSparseBatch - 1];
+                    int32_t cj[kSparseBatch][D];
+#pragma unroll
+                    for (int u = 0; u < kSparseBatch; ++u) load_point<D>(recb + (int64_t)p[u] * DP, cj[u]);
+#pragma unroll
+                    for (int u = 0; u < kSparseBatch; ++u)
+#pragma unroll
+                        for (int q = 0; q < kSparseMax; ++q)
+                            cnt[q] += ok[u] ? inside<D, W64>(qx[q], cj[u], T) : 0u;
                 }
             }
         }
@@ -950,10 +981,11 @@ cudaError_t launch_cell_runs(const BatchView& v, const CellPrepBufs& cb, int64_t
     if (kmask & 4u) (k_cell_runs<2><<<blocks, 256, 0, st>>>(v, cb, ncells), note_launch());
     if (kmask & 8u) (k_cell_runs<3><<<blocks, 256, 0, st>>>(v, cb, ncells), note_launch());
     if (kmask & 16u) (k_cell_runs<4><<<blocks, 256, 0, st>>>(v, cb, ncells), note_launch());
-    if (kmask & (2u << 8)) (k_cell_runs_blk<1><<<blocks, 256, 0, st>>>(v, cb, ncells), note_launch());
-    if (kmask & (4u << 8)) (k_cell_runs_blk<2><<<blocks, 256, 0, st>>>(v, cb, ncells), note_launch());
-    if (kmask & (8u << 8)) (k_cell_runs_blk<3><<<blocks, 256, 0, st>>>(v, cb, ncells), note_launch());
-    if (kmask & (16u << 8)) (k_cell_runs_blk<4><<<blocks, 256, 0, st>>>(v, cb, ncells), note_launch());
+    const unsigned bblocks = (unsigned)std::min<int64_t>(152 * 32, grid_for(ncells, kRunsBlkThreads));
+    if (kmask & (2u << 8)) (k_cell_runs_blk<1><<<bblocks, kRunsBlkThreads, 0, st>>>(v, cb, ncells), note_launch());
+    if (kmask & (4u << 8)) (k_cell_runs_blk<2><<<bblocks, kRunsBlkThreads, 0, st>>>(v, cb, ncells), note_launch());
+    if (kmask & (8u << 8)) (k_cell_runs_blk<3><<<bblocks, kRunsBlkThreads, 0, st>>>(v, cb, ncells), note_launch());
+    if (kmask & (16u << 8)) (k_cell_runs_blk<4><<<bblocks, kRunsBlkThreads, 0, st>>>(v, cb, ncells), note_launch());
     return cudaGetLastError();
 }
 

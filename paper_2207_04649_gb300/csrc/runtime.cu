@@ -507,7 +507,7 @@ struct Batch {
         // persistent per-point state
         DPC_CK(keep.get(&v.rec, (size_t)std::max<int64_t>(rec_total, 1)));
         DPC_CK(keep.get(&v.perm, N));
-        DPC_CK(keep.get(&v.pos_of, N));
+        v.pos_of = nullptr;  // S-Approx-DPC allocates and fills it
         DPC_CK(keep.get(&v.rho, N));
         DPC_CK(keep.get(&v.rho_s, N));
         DPC_CK(keep.get(&v.key, N));
@@ -996,6 +996,8 @@ struct Batch {
     dpc_status sapprox(const std::vector<Input>& in, const std::vector<int64_t>& eps_num,
                        const std::vector<int64_t>& eps_den) {
         DPC_TRY(build_grid(in));
+        DPC_CK(keep.get(&v.pos_of, N));
+        DPC_CK(launch_pos_of(v, st));
         // key of G': every dim's cell coordinate at its own bit offset, the
         // dataset's index above them (any width: sorted 64 bits at a time)
         int bshift = 0;

@@ -175,6 +175,40 @@ struct CandStream {
     }
 };
 
+// Walk of a sparse cell's concatenated runs in steps of `step`: a lane that
+// starts at offset `first` takes candidates first, first + step, ... of the
+// flat list. The current run is held in registers; the walk loads a run
+// only when it crosses into it, so a lane can find its next few candidates
+// before any of their records arrive.
+struct RunCursor {
+    const uint2* runs;
+    uint32_t nr, r, off;
+    uint2 cur;
+
+    __device__ __forceinline__ void init(const uint2* runs_, uint32_t nr_, uint32_t first) {
+        runs = runs_;
+        nr = nr_;
+        r = 0;
+        off = first;
+        cur = nr_ > 0u ? runs_[0] : make_uint2(0u, 0u);
+        settle();
+    }
+    __device__ __forceinline__ void settle() {
+        while (r < nr && off >= cur.y) {
+            off -= cur.y;
+            if (++r < nr) cur = runs[r];
+        }
+    }
+    // The sorted position of the lane's next candidate; false when none is left.
+    __device__ __forceinline__ bool next(uint32_t step, uint32_t& p) {
+        if (r >= nr) return false;
+        p = cur.x + off;
+        off += step;
+        settle();
+        return true;
+    }
+};
+
 // ------------------------------------------------------------- launchers
 
 // grid.cu
@@ -184,6 +218,8 @@ cudaError_t launch_cell_keys(const BatchView& v, bool key32, void* keys, uint32_
 // and the block count (device scalar) for the block table
 cudaError_t launch_gather_cells(const BatchView& v, bool key32, const void* skeys, uint32_t* flag, uint32_t* cidx,
                                 uint32_t* bflag, uint32_t* bidx, uint32_t* nblocks, void* scan_temp, cudaStream_t st);
+// v.pos_of from v.perm (only the passes that need it allocate v.pos_of)
+cudaError_t launch_pos_of(const BatchView& v, cudaStream_t st);
 // The block table of the datasets with sbits > 0 (after k_cells; v.sbhash
 // cleared to 0xff): keys, first cells and occupancy of every block, then
 // the hash over them. bocc must be zeroed.

@@ -328,28 +328,50 @@ __device__ __forceinline__ long long node_test_c(const int4* rec, const int32_t 
     return s;
 }
 
+// The points of a cell (or of its range of the leaf point list) against the
+// best so far. Two points at a time: both ranks and both records are loaded
+// before either is tested (a record is read whether or not its point ranks
+// higher), so that a long scan waits for one memory round trip per pair of
+// points instead of two per point.
+template <int D>
+__device__ __forceinline__ void leaf_point(const int32_t (&x)[D], const int32_t (&cx)[D], uint2 cr, uint32_t rank,
+                                           long long& bestD, uint32_t& bestJ, unsigned long long& tests) {
+    if (cr.x >= rank) return;
+    ++tests;
+    long long dd = 0;
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+        const long long e = (long long)x[k] - cx[k];
+        dd += e * e;
+    }
+    if (dd < bestD || (dd == bestD && cr.y < bestJ)) {
+        bestD = dd;
+        bestJ = cr.y;
+    }
+}
+
 template <int D>
 __device__ __forceinline__ void scan_leaf(const BatchView& v, const DeltaBufs& db, const int4* recb, int64_t c,
                                           int32_t t0, int32_t t1, const int32_t (&x)[D], uint32_t rank,
                                           long long& bestD, uint32_t& bestJ, unsigned long long& tests) {
     constexpr int DP = D <= 4 ? 1 : 2;
-    for (int32_t t = t0; t < t1; ++t) {
+    int32_t t = t0;
+    for (; t + 1 < t1; t += 2) {
+        const uint32_t q0 = db.lplist ? db.lplist[t] : (uint32_t)t;
+        const uint32_t q1 = db.lplist ? db.lplist[t + 1] : (uint32_t)(t + 1);
+        const uint2 c0 = v.ro_s[q0], c1 = v.ro_s[q1];
+        int32_t x0[D], x1[D];
+        t_load<D>(recb + (int64_t)q0 * DP, x0);
+        t_load<D>(recb + (int64_t)q1 * DP, x1);
+        leaf_point<D>(x, x0, c0, rank, bestD, bestJ, tests);
+        leaf_point<D>(x, x1, c1, rank, bestD, bestJ, tests);
+    }
+    if (t < t1) {
         const uint32_t q = db.lplist ? db.lplist[t] : (uint32_t)t;
         const uint2 cr = v.ro_s[q];
-        if (cr.x >= rank) continue;
-        ++tests;
         int32_t cx[D];
         t_load<D>(recb + (int64_t)q * DP, cx);
-        long long dd = 0;
-#pragma unroll
-        for (int k = 0; k < D; ++k) {
-            const long long e = (long long)x[k] - cx[k];
-            dd += e * e;
-        }
-        if (dd < bestD || (dd == bestD && cr.y < bestJ)) {
-            bestD = dd;
-            bestJ = cr.y;
-        }
+        leaf_point<D>(x, cx, cr, rank, bestD, bestJ, tests);
     }
 }
 
