@@ -270,7 +270,7 @@ __global__ void __launch_bounds__(kRingThreads) k_ring_dense(BatchView v, CellWo
 // and ranks are loaded together (overlapping latencies, as in the sparse
 // density pass); the least keys are combined with warp shuffles (the cell
 // loop is warp-uniform).
-constexpr int kRingSparseLanes = 4;
+constexpr int kRingSparseLanes = 2;
 constexpr int kRingSparseBatch = 4;
 
 template <int D, bool W64>

@@ -877,7 +877,7 @@ __global__ void __launch_bounds__(kRhoThreads) k_rho_dense_bulk(BatchView v, Cel
 // together, so that their latencies overlap (the runs hold 2-3 points each
 // in sparse regions: a loop per run kept one load in flight). The loop over
 // cells is warp-uniform, so that every lane reaches the shuffles.
-constexpr int kSparseLanes = 4;
+constexpr int kSparseLanes = 2;
 constexpr int kSparseBatch = 4;
 
 template <int D, bool W64>

@@ -179,7 +179,31 @@ __global__ void k_leaves(BatchView v, DeltaBufs db) {
                 hi[k] = INT32_MIN;
             }
             uint32_t mr = 0xffffffffu;
-            for (uint32_t p = p0; p < p1; ++p) leaf_add(v, ds, db.lplist ? db.lplist[p] : p, lo, hi, mr);
+            // four points in flight at a time; past the cell's end the last
+            // point is read again (min and max are unchanged by a repeat)
+            for (uint32_t p = p0; p < p1; p += 4) {
+                int4 ra[4], rb[4];
+                uint32_t rk[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const uint32_t pu = min(p + (uint32_t)u, p1 - 1u);
+                    const uint32_t q = db.lplist ? db.lplist[pu] : pu;
+                    const int4* r = v.rec + ds.rec_off + ((int64_t)q - ds.pt_off) * ds.dp;
+                    ra[u] = r[0];
+                    rb[u] = ds.dp == 2 ? r[1] : make_int4(0, 0, 0, 0);
+                    rk[u] = v.ro_s[q].x;
+                }
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int32_t x[8] = {ra[u].x, ra[u].y, ra[u].z, ra[u].w, rb[u].x, rb[u].y, rb[u].z, rb[u].w};
+#pragma unroll
+                    for (int k = 0; k < 8; ++k) {
+                        lo[k] = min(lo[k], x[k]);
+                        hi[k] = max(hi[k], x[k]);
+                    }
+                    mr = min(mr, rk[u]);
+                }
+            }
             write_leaf(db, c, lo, hi, mr, p0, p1);
         }
         unsigned bigm = __ballot_sync(0xffffffffu, big);
@@ -329,10 +353,12 @@ __device__ __forceinline__ long long node_test_c(const int4* rec, const int32_t 
 }
 
 // The points of a cell (or of its range of the leaf point list) against the
-// best so far. Two points at a time: both ranks and both records are loaded
-// before either is tested (a record is read whether or not its point ranks
-// higher), so that a long scan waits for one memory round trip per pair of
-// points instead of two per point.
+// best so far, kLeafBatch points at a time: their ranks and records are all
+// loaded before any is tested (a record is read whether or not its point
+// ranks higher), so that a long scan waits for one memory round trip per
+// kLeafBatch points instead of two per point.
+constexpr int kLeafBatch = 2;
+
 template <int D>
 __device__ __forceinline__ void leaf_point(const int32_t (&x)[D], const int32_t (&cx)[D], uint2 cr, uint32_t rank,
                                            long long& bestD, uint32_t& bestJ, unsigned long long& tests) {
@@ -356,22 +382,34 @@ __device__ __forceinline__ void scan_leaf(const BatchView& v, const DeltaBufs& d
                                           long long& bestD, uint32_t& bestJ, unsigned long long& tests) {
     constexpr int DP = D <= 4 ? 1 : 2;
     int32_t t = t0;
-    for (; t + 1 < t1; t += 2) {
-        const uint32_t q0 = db.lplist ? db.lplist[t] : (uint32_t)t;
-        const uint32_t q1 = db.lplist ? db.lplist[t + 1] : (uint32_t)(t + 1);
-        const uint2 c0 = v.ro_s[q0], c1 = v.ro_s[q1];
-        int32_t x0[D], x1[D];
-        t_load<D>(recb + (int64_t)q0 * DP, x0);
-        t_load<D>(recb + (int64_t)q1 * DP, x1);
-        leaf_point<D>(x, x0, c0, rank, bestD, bestJ, tests);
-        leaf_point<D>(x, x1, c1, rank, bestD, bestJ, tests);
+    for (; t + kLeafBatch <= t1; t += kLeafBatch) {
+        uint32_t q[kLeafBatch];
+        uint2 cr[kLeafBatch];
+        int32_t cx[kLeafBatch][D];
+#pragma unroll
+        for (int u = 0; u < kLeafBatch; ++u) q[u] = db.lplist ? db.lplist[t + u] : (uint32_t)(t + u);
+#pragma unroll
+        for (int u = 0; u < kLeafBatch; ++u) {
+            cr[u] = v.ro_s[q[u]];
+            t_load<D>(recb + (int64_t)q[u] * DP, cx[u]);
+        }
+#pragma unroll
+        for (int u = 0; u < kLeafBatch; ++u) leaf_point<D>(x, cx[u], cr[u], rank, bestD, bestJ, tests);
     }
-    if (t < t1) {
-        const uint32_t q = db.lplist ? db.lplist[t] : (uint32_t)t;
-        const uint2 cr = v.ro_s[q];
-        int32_t cx[D];
-        t_load<D>(recb + (int64_t)q * DP, cx);
-        leaf_point<D>(x, cx, cr, rank, bestD, bestJ, tests);
+    if (t < t1) {  // the last t1 - t < kLeafBatch points, loaded together as well
+        uint32_t q[kLeafBatch - 1];
+        uint2 cr[kLeafBatch - 1];
+        int32_t cx[kLeafBatch - 1][D];
+#pragma unroll
+        for (int u = 0; u < kLeafBatch - 1; ++u) {
+            const int32_t tu = min(t + u, t1 - 1);
+            q[u] = db.lplist ? db.lplist[tu] : (uint32_t)tu;
+            cr[u] = v.ro_s[q[u]];
+            t_load<D>(recb + (int64_t)q[u] * DP, cx[u]);
+        }
+#pragma unroll
+        for (int u = 0; u < kLeafBatch - 1; ++u)
+            if (t + u < t1) leaf_point<D>(x, cx[u], cr[u], rank, bestD, bestJ, tests);
     }
 }
 
