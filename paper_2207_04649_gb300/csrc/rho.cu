@@ -250,20 +250,29 @@ __global__ void __launch_bounds__(kRunsBlkThreads) k_cell_runs_blk(BatchView v, 
             if (!ok) continue;
             unsigned long long occ;
             const uint32_t f = block_find(v.sbhash, v.sbmask, ((uint64_t)b << 40) | code, occ);
+            // the selected cells a piece at a time: a piece runs from the
+            // lowest selected code up to the next occupied code outside the
+            // box, so its cells have consecutive indices
             unsigned long long sel = occ & box;
+            const unsigned long long gaps = occ & ~box;
             while (sel) {
-                const int bit = __ffsll((long long)sel) - 1;
-                sel &= sel - 1ull;
-                const uint32_t ci = f + (uint32_t)__popcll(occ & ((1ull << bit) - 1ull));
+                const int a = __ffsll((long long)sel) - 1;
+                const unsigned long long above = ~0ull << a;
+                const unsigned long long g = gaps & above;
+                const unsigned long long seg = g ? (((g & (0ull - g)) - 1ull) & above) : above;
+                sel &= ~seg;
+                const uint32_t ci = f + (uint32_t)__popcll(occ & ~above);
+                const uint32_t ce = ci + (uint32_t)__popcll(occ & box & seg) - 1u;
                 if (open && ci == last_ci + 1u) {
-                    last_ci = ci;
+                    last_ci = ce;
                 } else {
                     if (open) {
                         if (SM) sruns[nr][threadIdx.x] = make_uint2(first_ci, last_ci);
                         else runs[nr] = make_uint2(first_ci, last_ci);
                         ++nr;
                     }
-                    first_ci = last_ci = ci;
+                    first_ci = ci;
+                    last_ci = ce;
                     open = true;
                 }
             }
