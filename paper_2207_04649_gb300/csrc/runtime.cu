@@ -757,6 +757,7 @@ struct Batch {
             if (hd[b].dp == 2) db.dpb = 2;
             if (hd[b].d > 3) db.compact = 0;
         }
+        if (nc >= (1ll << 29)) db.compact = 0;  // stacked link words must stay non-negative
         DPC_CK(tmp.get(&db.cell_off, B + 1));
         DPC_CK(tmp.get(&db.ckey, nc));
         DPC_CK(tmp.get(&db.child, nc));
@@ -811,6 +812,7 @@ struct Batch {
                     if (hd[b].dp == 2) db.dpb = 2;
                     if (hd[b].d > 3) db.compact = 0;
                 }
+                if (nc >= (1ll << 29)) db.compact = 0;  // stacked link words must stay non-negative
                 DPC_CK(tmp.get(&db.cell_off, B + 1));
                 DPC_CK(tmp.get(&db.ckey, nc));
                 DPC_CK(tmp.get(&db.child, nc));

@@ -448,11 +448,11 @@ __global__ void __launch_bounds__(128) k_tree_search(BatchView v, DeltaBufs db) 
         const int32_t root = c1 - c0 >= 2 ? (int32_t)c0 : ~(int32_t)c0;
         if (compact) {
             // the current node (tested, in reach) walks to its nearer child
-            // in reach; the farther child in reach is stacked as (node,
-            // distance bound, link); a node whose children are both out of
-            // reach, or a scanned cell, takes the next stacked node still in
-            // reach
-            uint32_t slink[S];
+            // in reach; the farther child in reach is stacked as (entry,
+            // distance bound), the entry being a cell's reference (~c < 0)
+            // or an internal node's link word (its children, >= 0: fewer
+            // than 2^29 cells); a node whose children are both out of reach,
+            // or a scanned cell, takes the next stacked node still in reach
             uint32_t cur_link;
             int32_t cur = root;
             int sp = 0;
@@ -474,9 +474,9 @@ __global__ void __launch_bounds__(128) k_tree_search(BatchView v, DeltaBufs db) 
                     const long long dn = swap ? d1 : d0, df = swap ? d0 : d1;
                     if (!out_of_reach(df, bestD)) {
                         if (sp < S) {
-                            stack[sp] = swap ? l : r;
+                            const int32_t fr = swap ? l : r;
+                            stack[sp] = fr < 0 ? fr : (int32_t)(swap ? ll : rl);
                             slb[sp] = lb32(df);
-                            slink[sp] = swap ? ll : rl;
                             ++sp;
                         } else {
                             atomicOr(v.err, kErrTreeStack);
@@ -491,8 +491,9 @@ __global__ void __launch_bounds__(128) k_tree_search(BatchView v, DeltaBufs db) 
                 while (!next && sp > 0) {
                     --sp;
                     if ((long long)slb[sp] > bestD) continue;  // overtaken since it was stacked
-                    cur = stack[sp];
-                    cur_link = slink[sp];
+                    const int32_t e = stack[sp];
+                    cur = e < 0 ? e : 0;  // an internal node is known by its link word
+                    cur_link = (uint32_t)e;
                     next = true;
                 }
                 have = next;
