@@ -294,7 +294,8 @@ dpc_status dpc_set_profiling(dpc_ctx* ctx, int on);
  *             piece), 0 by 128-bit loads through registers (default 0)
  *   "sapprox_near_threads"  the pick path's first-phase scan over the
  *             picks of a pick's neighbour blocks: 1 one thread per pick,
- *             0 one warp per pick (default 1)
+ *             0 one warp per pick, 2 one thread while the grid's cells hold
+ *             fewer than 6 picks on average, else one warp (default 2)
  *   "max_batch_jobs"  served mode: jobs one batch admits at most, 1 .. 4096
  *   "max_batch_points" served mode: points one batch admits at most, 1 .. 2^31 - 1 (default
  *                     2^20; a larger job runs in a batch of its own, so that it does not hold

@@ -149,7 +149,8 @@ struct Tune {
                                 //   dense kernels over pick items (3), 1 or 3 by the candidates per pick (2)
     int rho_bulk = 0;              // dense density kernels (d <= 4, 32-bit forms): candidates staged by bulk
                                    //   copies (cp.async.bulk) instead of 128-bit loads through registers
-    int sapprox_near_threads = 1;  // S-Approx-DPC pick path: near pass one thread (1) or one warp (0) per pick
+    int sapprox_near_threads = 2;  // S-Approx-DPC pick path: near pass one thread (1) or one warp (0) per pick,
+                                   //   2 by the picks per grid cell
     int sapprox_ratio = 16;   // S-Approx-DPC: the pick path when the points' pairs exceed this many times the picks'
 };
 
@@ -1127,7 +1128,13 @@ struct Batch {
         DPC_CK(cudaMemsetAsync(db.ucount, 0, 4 * sizeof(uint32_t), st));
         db.tcount = db.ucount;
         db.bf_rank = tune.bf_rank;
-        DPC_CK(launch_sapprox_first(v, w, sb, db, dim_mask, npicks, npicks, !all_points, tune.sapprox_near_threads != 0,
+        // near pass: a thread per pick while the neighbour cells hold few
+        // picks, a warp per pick from 6 picks per cell on average (dense
+        // 5.8M x 3: the warp form wins at eps 0.2-0.4, 7-12 picks per cell;
+        // the thread form at eps 0.6-1.0, 2-5 picks per cell)
+        const bool near_threads = tune.sapprox_near_threads == 2 ? npicks < 6 * std::max<int64_t>(ncells, 1)
+                                                                 : tune.sapprox_near_threads != 0;
+        DPC_CK(launch_sapprox_first(v, w, sb, db, dim_mask, npicks, npicks, !all_points, near_threads,
                                     st));
         // the pick path's tree leaves hold the cells' picks only: every point
         // that ranks above a pick is a pick (the others have rho 0)
@@ -1295,7 +1302,7 @@ dpc_status dpc_set_tuning(dpc_ctx* ctx, const char* key, int64_t value) {
     else if (k == "sapprox_path" && value >= 0 && value <= 2) t.sapprox_path = (int)value;
     else if (k == "sapprox_ratio" && value >= 1 && value <= 1024) t.sapprox_ratio = (int)value;
     else if (k == "sapprox_rho_cells" && value >= 0 && value <= 3) t.sapprox_rho_cells = (int)value;
-    else if (k == "sapprox_near_threads" && value >= 0 && value <= 1) t.sapprox_near_threads = (int)value;
+    else if (k == "sapprox_near_threads" && value >= 0 && value <= 2) t.sapprox_near_threads = (int)value;
     else if (k == "rho_bulk" && value >= 0 && value <= 1) t.rho_bulk = (int)value;
     else if (k == "sparse_cand" && value >= 0 && value <= (1ll << 31)) t.sparse_cand = (int)std::min<int64_t>(value, INT32_MAX);
     else if (k == "max_batch_jobs" && value >= 1 && value <= 4096) {

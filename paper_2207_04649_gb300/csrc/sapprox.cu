@@ -425,7 +425,13 @@ __global__ void __launch_bounds__(128) k_sap_near(BatchView v, CellWork w, Sappr
 }
 
 // The same near pass with one thread per pick (a pick's block holds few
-// picks on dense data: tens, against thousands of points).
+// picks on dense data: tens, against thousands of points). The candidate
+// picks are taken kNearBatch at a time: their list entries first, then their
+// ranks and records together (a record is read whether or not its pick ranks
+// higher), so that a thread waits for two memory round trips per batch
+// instead of three per candidate.
+constexpr int kNearBatch = 4;
+
 template <int D>
 __global__ void __launch_bounds__(128) k_sap_near_t(BatchView v, CellWork w, SapproxBufs sb) {
     constexpr int DP = D <= 4 ? 1 : 2;
@@ -451,14 +457,23 @@ __global__ void __launch_bounds__(128) k_sap_near_t(BatchView v, CellWork w, Sap
         uint32_t bj = 0xffffffffu;
         for (uint32_t ri = 0; ri < nr; ++ri) {
             const uint2 run = runs[ri];  // one or more whole cells
-            for (uint32_t t = sb.pstart[v.cell_of[run.x]], t1 = sb.pstart[v.cell_of[run.x + run.y - 1] + 1]; t < t1;
-                 ++t) {
-                const uint32_t q = sb.plist[t];
-                const uint2 cr = v.ro_s[q];
-                if (cr.x >= ro.x) continue;
-                int32_t y[D];
-                sx_load<D>(recb + (int64_t)q * DP, y);
-                keep_min(bd, bj, sx_dist<D>(x, y), cr.y);
+            const uint32_t t1 = sb.pstart[v.cell_of[run.x + run.y - 1] + 1];
+            for (uint32_t t = sb.pstart[v.cell_of[run.x]]; t < t1; t += kNearBatch) {
+                // past the run's last pick the batch repeats it, and a
+                // repeated candidate changes nothing
+                uint32_t q[kNearBatch];
+#pragma unroll
+                for (int u = 0; u < kNearBatch; ++u) q[u] = sb.plist[min(t + (uint32_t)u, t1 - 1u)];
+                uint2 cr[kNearBatch];
+                int32_t y[kNearBatch][D];
+#pragma unroll
+                for (int u = 0; u < kNearBatch; ++u) {
+                    cr[u] = v.ro_s[q[u]];
+                    sx_load<D>(recb + (int64_t)q[u] * DP, y[u]);
+                }
+#pragma unroll
+                for (int u = 0; u < kNearBatch; ++u)
+                    if (cr[u].x < ro.x) keep_min(bd, bj, sx_dist<D>(x, y[u]), cr[u].y);
             }
         }
         if (bj != 0xffffffffu && bd < ds.d_cut2) {
