@@ -361,6 +361,12 @@ __global__ void k_sap_resolve(BatchView v, SapproxBufs sb) {
     sb.scan[atomicAdd(&sb.nscan[0], 1u)] = p;
 }
 
+// Both near-pass forms take a lane's candidate picks kNearBatch at a time:
+// their list entries first, then their ranks and records together (a record
+// is read whether or not its pick ranks higher), so that a lane waits for two
+// memory round trips per batch instead of three per candidate.
+constexpr int kNearBatch = 4;
+
 // Pick path, every pick, one warp each: the nearest higher pick among the
 // picks of its searched block (through the cells' pick lists: only the
 // picks' own records are read). When
@@ -398,14 +404,24 @@ __global__ void __launch_bounds__(128) k_sap_near(BatchView v, CellWork w, Sappr
             // the picks of the run's cells (a run is one or more whole cells,
             // consecutive in the sorted order, whose picks are consecutive too)
             const uint2 run = runs[ri];
+            const uint32_t t0 = sb.pstart[v.cell_of[run.x]];
             const uint32_t t1 = sb.pstart[v.cell_of[run.x + run.y - 1] + 1];
-            for (uint32_t t = sb.pstart[v.cell_of[run.x]] + lane; t < t1; t += 32) {
-                const uint32_t q = sb.plist[t];
-                const uint2 cr = v.ro_s[q];
-                if (cr.x >= ro.x) continue;
-                int32_t y[D];
-                sx_load<D>(recb + (int64_t)q * DP, y);
-                keep_min(bd, bj, sx_dist<D>(x, y), cr.y);
+            // kNearBatch candidates per lane in flight (lane + 32 u); past
+            // the run's last pick a lane repeats it, which changes nothing
+            for (uint32_t t = t0 + lane; t < t1; t += 32 * kNearBatch) {
+                uint32_t q[kNearBatch];
+#pragma unroll
+                for (int u = 0; u < kNearBatch; ++u) q[u] = sb.plist[min(t + 32u * u, t1 - 1u)];
+                uint2 cr[kNearBatch];
+                int32_t y[kNearBatch][D];
+#pragma unroll
+                for (int u = 0; u < kNearBatch; ++u) {
+                    cr[u] = v.ro_s[q[u]];
+                    sx_load<D>(recb + (int64_t)q[u] * DP, y[u]);
+                }
+#pragma unroll
+                for (int u = 0; u < kNearBatch; ++u)
+                    if (cr[u].x < ro.x) keep_min(bd, bj, sx_dist<D>(x, y[u]), cr[u].y);
             }
         }
         for (int o = 16; o > 0; o >>= 1) {
@@ -425,12 +441,8 @@ __global__ void __launch_bounds__(128) k_sap_near(BatchView v, CellWork w, Sappr
 }
 
 // The same near pass with one thread per pick (a pick's block holds few
-// picks on dense data: tens, against thousands of points). The candidate
-// picks are taken kNearBatch at a time: their list entries first, then their
-// ranks and records together (a record is read whether or not its pick ranks
-// higher), so that a thread waits for two memory round trips per batch
-// instead of three per candidate.
-constexpr int kNearBatch = 4;
+// picks on dense data: tens, against thousands of points), its candidates
+// kNearBatch at a time as in the warp form.
 
 template <int D>
 __global__ void __launch_bounds__(128) k_sap_near_t(BatchView v, CellWork w, SapproxBufs sb) {
