@@ -243,6 +243,8 @@ typedef struct {
     int32_t density_path;     /* the density's path: 0 every point (exact, Approx-DPC, S-Approx-DPC's
                                  all-point path); S-Approx-DPC's pick path: 1 one warp per pick,
                                  2 one warp per grid cell, 3 the dense kernels over pick items */
+    int64_t device_bytes_peak; /* the most device memory the run's batch held at once: its allocations and
+                                  frees counted in the order of its stream (they are all on it) */
 } dpc_info;
 
 dpc_status dpc_ds_info(const dpc_ds* ds, dpc_info* out);
@@ -389,6 +391,14 @@ dpc_status dpc_submit(dpc_ctx* ctx, const dpc_job* job, uint64_t* ticket);
  * A job is done as soon as its own outputs are written: in a batch, a job
  * with fewer queries can finish before the others. */
 dpc_status dpc_poll(dpc_ctx* ctx, uint64_t ticket, dpc_result* out);
+
+/* Device bytes the served mode reserves for a job of n points in d dims
+ * (1 .. 8) run with `method` (0 exact, 1 Approx-DPC, 2 S-Approx-DPC) under
+ * ctx's tuning knobs (NULL: the defaults): the admission estimate by which
+ * the jobs in flight share hbm_cap_bytes. It bounds the run's peak,
+ * dpc_info.device_bytes_peak, with one run slot per neighbour cell of the
+ * grid for every point. No counterpart in the paper. */
+uint64_t dpc_job_footprint(dpc_ctx* ctx, int64_t n, int32_t d, int32_t method);
 
 /* Batched mode: run every job submitted so far as one batch and wait for it. */
 dpc_status dpc_flush(dpc_ctx* ctx);

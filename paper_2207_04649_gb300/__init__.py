@@ -18,5 +18,5 @@ from ._binding import (  # noqa: F401
     dpc_create, dpc_destroy, dpc_density, dpc_dependent, dpc_label, dpc_release, dpc_ds_info,
     dpc_last_batch_info, dpc_autotune, dpc_dependent_approx, dpc_sapprox, dpc_cluster, eps_fraction,
     dpc_set_profiling, dpc_submit, dpc_poll, dpc_flush, dpc_wait, dpc_last_error, library_path,
-    dpc_kernel_launches, dpc_probe_pair_rate, dpc_set_tuning, dpc_get_tuning,
+    dpc_kernel_launches, dpc_probe_pair_rate, dpc_set_tuning, dpc_get_tuning, dpc_job_footprint,
 )

@@ -49,7 +49,8 @@ class DpcInfo(ctypes.Structure):
                 ("tree_visits", ctypes.c_int64), ("tree_pairs", ctypes.c_int64),
                 ("pair_mode", ctypes.c_int32), ("grid_key_bits", ctypes.c_int32),
                 ("dense_pairs", ctypes.c_int64), ("ms_rho_dense", ctypes.c_float), ("rank_key_bits", ctypes.c_int32),
-                ("picks", ctypes.c_int64), ("second_phase", ctypes.c_int64), ("density_path", ctypes.c_int32)]
+                ("picks", ctypes.c_int64), ("second_phase", ctypes.c_int64), ("density_path", ctypes.c_int32),
+                ("device_bytes_peak", ctypes.c_int64)]
 
     def as_dict(self) -> dict:
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -110,6 +111,7 @@ def lib():
             "dpc_flush": ([vp], st),
             "dpc_wait": ([vp, ctypes.c_uint64, i64, ctypes.POINTER(DpcResult)], st),
             "dpc_kernel_launches": ([], i64),
+            "dpc_job_footprint": ([vp, i64, i32, i32], ctypes.c_uint64),
             "dpc_set_tuning": ([vp, ctypes.c_char_p, i64], st),
             "dpc_get_tuning": ([vp, ctypes.c_char_p, ctypes.POINTER(i64)], st),
             "dpc_probe_pair_rate": ([ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
@@ -125,6 +127,14 @@ def lib():
 
 def dpc_kernel_launches() -> int:
     return int(lib().dpc_kernel_launches())
+
+
+def dpc_job_footprint(n: int, d: int, method: int = 0, ctx=None) -> int:
+    """Device bytes the served mode reserves for a job of n points in d dims
+    (method 0 exact, 1 Approx-DPC, 2 S-Approx-DPC) under ctx's tuning knobs
+    (a Context, a raw handle, or None for the defaults)."""
+    handle = getattr(ctx, "handle", ctx)
+    return int(lib().dpc_job_footprint(handle, int(n), int(d), int(method)))
 
 
 def dpc_probe_pair_rate(device: int, d: int, mode: int = 0):

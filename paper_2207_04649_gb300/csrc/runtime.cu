@@ -82,9 +82,16 @@ inline int ceil_log2(uint64_t x) {  // smallest b with 2^b >= x
     return b;
 }
 
+// Device bytes a batch holds, counted in stream order (every allocation and
+// free of a batch is on its stream), and the most it held at once.
+struct Meter {
+    size_t live = 0, peak = 0;
+};
+
 // Stream-ordered device allocations released together.
 struct Arena {
     cudaStream_t st = nullptr;
+    Meter* meter = nullptr;  // the batch's meter, or null
     std::vector<void*> ptrs;
     size_t bytes = 0;
     cudaError_t get(void** p, size_t n) {
@@ -93,6 +100,10 @@ struct Arena {
         if (e == cudaSuccess) {
             ptrs.push_back(*p);
             bytes += n;
+            if (meter) {
+                meter->live += n;
+                meter->peak = std::max(meter->peak, meter->live);
+            }
         }
         return e;
     }
@@ -103,6 +114,7 @@ struct Arena {
     void release() {
         for (void* p : ptrs) cudaFreeAsync(p, st);
         ptrs.clear();
+        if (meter) meter->live -= bytes;
         bytes = 0;
     }
     // an early return frees the buffers too (stream-ordered on st)
@@ -270,6 +282,7 @@ struct Batch {
     std::vector<DsDesc> hd;
     std::vector<int64_t> h_pt_off;
     std::vector<int64_t> h_slot_off;
+    Meter meter;  // declared before the arenas, which count into it until they are released
     Arena keep, dens;
     BatchView v{};
     CellWork w{};
@@ -418,6 +431,7 @@ struct Batch {
         if (!st) st = ctx->stream;
         tune = tune_for(ctx, in);
         keep.st = dens.st = st;
+        keep.meter = dens.meter = &meter;
         B = (int)in.size();
         hd.assign(B, DsDesc{});
         h_pt_off.assign(B + 1, 0);
@@ -880,6 +894,7 @@ struct Batch {
         mark(8);
         Arena tmp;
         tmp.st = st;
+        tmp.meter = &meter;
         // on every way out, st waits for the tree built on the side stream
         // before tmp (which holds its buffers) is freed
         struct SideWait {
@@ -952,6 +967,7 @@ struct Batch {
         mark(8);
         Arena tmp;
         tmp.st = st;
+        tmp.meter = &meter;
         void* temp = nullptr;
         DPC_CK(tmp.get(&temp, std::max(radix_sort_temp_bytes(N), scan_temp_bytes(N))));
         DPC_TRY(ensure_rank(tmp, temp));
@@ -1018,6 +1034,7 @@ struct Batch {
         DPC_TRY(upload_desc());
         Arena tmp;
         tmp.st = st;
+        tmp.meter = &meter;
         SapproxBufs sb{};
         void* temp = nullptr;
         DPC_CK(tmp.get(&temp, std::max(radix_sort_temp_bytes(N), scan_temp_bytes(N))));
@@ -1544,6 +1561,7 @@ static void fill_info(const Batch& bt, int b, dpc_info* out) {
     out->picks = bt.npicks;
     out->second_phase = bt.nsecond;
     out->density_path = bt.density_path;
+    out->device_bytes_peak = (int64_t)bt.meter.peak;
 }
 
 dpc_status dpc_ds_info(const dpc_ds* ds, dpc_info* out) {
@@ -1574,12 +1592,33 @@ namespace {
 
 using JobPtr = std::shared_ptr<dpc_ctx::JobRec>;
 
-// Device bytes one job holds while it runs (points, sorted records, per-point
-// state, sort buffers, hash table), with slack.
-uint64_t job_bytes(int64_t n, int32_t d, int32_t method) {
-    // the approximate methods add a second grid's sort buffers and lists
-    return (uint64_t)n * (176 + 8 * (uint64_t)d + (method != 0 ? 96 : 0)) + (16ull << 20);
+// Device bytes one job holds at its peak: per point a base for the records,
+// the per-point state, the sort buffers and the cell tree, 8 bytes per
+// dimension, one 8-byte run slot per neighbour cell of the grid (a cell keeps
+// (2R+1)^k slots, and there is at most one cell per point), and the second
+// grid of the approximate methods; plus 16 MB. Measured peaks of the served
+// trace's problems lie below it: 180-290 bytes per point in 2-3 dims,
+// 390-680 in 4-6 (81 slots), 2.7-4.3 KB in 7-8 (625 slots, cell factor 2),
+// and up to 465 (S-Approx-DPC) in 3 dims.
+uint64_t job_bytes(int64_t n, int32_t d, int32_t method, const Tune& t) {
+    const int k = std::min(std::min<int>(d, t.kmax), kMaxGridDims);
+    const int R = d >= t.hd_min_d ? t.hd_cell_factor : 1;
+    uint64_t slots = 1;
+    for (int j = 0; j < k; ++j) slots *= (uint64_t)(2 * R + 1);
+    const uint64_t per = 176 + 8 * (uint64_t)d + 8 * slots + (method == 1 ? 96 : (method == 2 ? 160 : 0));
+    return (uint64_t)n * per + (16ull << 20);
 }
+
+}  // namespace
+}  // namespace dpc
+
+extern "C" uint64_t dpc_job_footprint(dpc_ctx* ctx, int64_t n, int32_t d, int32_t method) {
+    const dpc::Tune t = ctx ? ctx->tune : dpc::Tune{};
+    return dpc::job_bytes(n < 0 ? 0 : n, d < 1 ? 1 : (d > 8 ? 8 : d), method, t);
+}
+
+namespace dpc {
+namespace {
 
 // One job's outputs are written: its status, for dpc_poll and dpc_wait.
 void mark_done(dpc_ctx* ctx, const JobPtr& j, dpc_status s) {
@@ -1831,7 +1870,7 @@ dpc_status dpc_submit(dpc_ctx* ctx, const dpc_job* job, uint64_t* ticket) {
     rec->job = *job;
     rec->rmin.assign(job->rho_min, job->rho_min + job->n_queries);
     rec->dmin.assign(job->delta_min, job->delta_min + job->n_queries);
-    rec->bytes = dpc::job_bytes(job->n, job->d, job->method);
+    rec->bytes = dpc::job_bytes(job->n, job->d, job->method, ctx->tune);
     rec->t_submit = std::chrono::steady_clock::now();
     if (ctx->mode == 1 && rec->bytes > ctx->cap) return fail(DPC_ERR_CAPACITY, "job exceeds the memory cap");
     std::lock_guard<std::mutex> lk(ctx->mu);

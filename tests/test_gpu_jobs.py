@@ -205,7 +205,7 @@ def test_served_admission_under_small_cap(dpc):
     """A cap that fits about one job at a time still finishes every job;
     a job that can never fit is refused at submit."""
     probs = small_problems(seed=42, count=6)
-    cap = 40 << 20
+    cap = max(dpc.dpc_job_footprint(len(p), p.shape[1] if p.ndim == 2 and p.size else 1, 0) for p, _, _ in probs) + (4 << 20)
     with dpc.Context(0, mode=1, hbm_cap_bytes=cap, max_inflight=2) as ctx:
         jobs = [dpc.Job(p, dc, qs) for p, dc, qs in probs]
         for j in jobs:
@@ -399,7 +399,8 @@ def test_kept_dataset_holds_its_bytes_until_released(dpc):
     import time
     p = workloads.random_blobs(71, 20000, 3, 900, blobs=4, spread=0.05).points
     q = [(2, 2000)]
-    with dpc.Context(0, mode=1, hbm_cap_bytes=24 << 20, max_inflight=1) as ctx:
+    cap = dpc.dpc_job_footprint(20000, 3, 0) * 3 // 2  # one job's reservation fits, two do not
+    with dpc.Context(0, mode=1, hbm_cap_bytes=cap, max_inflight=1) as ctx:
         a = dpc.Job(p, 900, q, keep=True)
         ctx.submit(a)
         assert ctx.wait(a.ticket, 60000)[0] == dpc.DPC_OK
