@@ -888,9 +888,11 @@ __global__ void __launch_bounds__(kRhoThreads) k_rho_dense_bulk(BatchView v, Cel
 // cells is warp-uniform, so that every lane reaches the shuffles.
 constexpr int kSparseLanes = 2;
 constexpr int kSparseBatch = 4;
+// (5 blocks of 256 threads per SM: density 1.74 -> 1.70 ms at 5.8M x 3; the
+// ring search's sparse kernel spills under the same bound and ran slower)
 
 template <int D, bool W64>
-__global__ void __launch_bounds__(256) k_rho_sparse(BatchView v, CellWork w) {
+__global__ void __launch_bounds__(256, 5) k_rho_sparse(BatchView v, CellWork w) {
     constexpr int DP = D <= 4 ? 1 : 2;
     constexpr int G = kSparseLanes, CPW = 32 / G;  // lanes per cell, cells per warp
     const uint32_t ns = *w.nsparse;
