@@ -91,3 +91,24 @@ def test_tuning_keys_documented():
     doc = open(os.path.join(ROOT, "include", "dpc.h")).read()
     documented = set(re.findall(r'^ \*\s+"([a-z_0-9]+)"', doc, flags=re.M))
     assert accepted and accepted == documented, (accepted ^ documented)
+
+
+def test_job_footprint_counts_run_slots():
+    """The served mode's per-job reservation (host logic, no device):
+    n (176 + 8 d + 8 (2R+1)^k) + 16 MB with the default knobs (k = min(d,
+    4) gridded dims, reach R = 1 below 7 dims and 2 from 7 on), plus 96 or
+    160 bytes per point for the approximate methods' second grid."""
+    import paper_2207_04649_gb300 as dpc
+    mb16 = 16 << 20
+    for d in range(1, 9):
+        k = min(d, 4)
+        slots = (5 if d >= 7 else 3) ** k
+        for n in (0, 1, 1000, 2_000_000):
+            base = n * (176 + 8 * d + 8 * slots) + mb16
+            assert dpc.dpc_job_footprint(n, d, 0) == base
+            assert dpc.dpc_job_footprint(n, d, 1) == base + 96 * n
+            assert dpc.dpc_job_footprint(n, d, 2) == base + 160 * n
+    # out-of-range arguments are clamped, never negative
+    assert dpc.dpc_job_footprint(-5, 3, 0) == mb16
+    assert dpc.dpc_job_footprint(10, 0, 0) == dpc.dpc_job_footprint(10, 1, 0)
+    assert dpc.dpc_job_footprint(10, 99, 0) == dpc.dpc_job_footprint(10, 8, 0)
